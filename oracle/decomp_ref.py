@@ -1,0 +1,157 @@
+"""Decompositions (oracle; test infrastructure).
+
+tsvd            Theorem 2.6 computed through Eq. (circ1): SVD of every Fourier
+                frontal slice, economy size m = min(n1, n2), singular values
+                descending, conjugate-symmetric slices filled from the half
+                spectrum so that U, S, V are real.
+tsvd_randomized Randomized low-tubal-rank t-SVD: per Fourier slice the
+                range finder with q power iterations of Halko, Martinsson and
+                Tropp (SIAM Review 2011, Algorithms 4.3/5.1), test matrix
+                passed in.  The paper names randomized approximations
+                (Section 5.2) without fixing one; this is the reading used.
+tproject, tcx   Algorithm 3 (t-project) and Algorithm 4 (t-CX).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg
+
+from . import sampling_ref
+from .tensor_ref import fft3, ifft3, half_spectrum, hermitian_fill
+
+
+def _real_slice(k: int, n3: int) -> bool:
+    return k == 0 or (n3 % 2 == 0 and k == n3 // 2)
+
+
+def tsvd_hat(X: np.ndarray):
+    """Half-spectrum facewise SVD: returns (Uh, s, Vh) with Uh n1 x m x h,
+    s m x h (descending), Vh n2 x m x h, and X_hat_k = Uh_k diag(s_k) Vh_k^H."""
+    n1, n2, n3 = X.shape
+    m = min(n1, n2)
+    h = n3 // 2 + 1
+    Xh = half_spectrum(fft3(X))
+    Uh = np.zeros((n1, m, h), dtype=np.complex128)
+    Vh = np.zeros((n2, m, h), dtype=np.complex128)
+    s = np.zeros((m, h))
+    for k in range(h):
+        M = Xh[:, :, k]
+        if _real_slice(k, n3):
+            M = M.real
+        u, sv, vt = scipy.linalg.svd(M, full_matrices=False, lapack_driver="gesvd")
+        Uh[:, :, k] = u
+        s[:, k] = sv
+        Vh[:, :, k] = np.conj(vt).T
+    return Uh, s, Vh
+
+
+def tsvd(X: np.ndarray):
+    """t-SVD X = U * S * V^T (Theorem 2.6), economy: U n1 x m x n3,
+    S m x m x n3 (f-diagonal), V n2 x m x n3."""
+    n1, n2, n3 = X.shape
+    m = min(n1, n2)
+    Uh, s, Vh = tsvd_hat(X)
+    Sh = np.zeros((m, m, s.shape[1]), dtype=np.complex128)
+    for k in range(s.shape[1]):
+        Sh[:, :, k] = np.diag(s[:, k])
+    U = ifft3(hermitian_fill(Uh, n3)).real
+    S = ifft3(hermitian_fill(Sh, n3)).real
+    V = ifft3(hermitian_fill(Vh, n3)).real
+    return U, S, V
+
+
+def truncate_error_sq(s: np.ndarray, n3: int, r: int) -> float:
+    """||X - X_r||_F^2 for the tubal-rank-r truncation of the t-SVD:
+    (1/n3) sum over all n3 slices of sum_{i>r} sigma_{i,k}^2 (Parseval), with
+    the half spectrum counted twice for its conjugate partners."""
+    h = s.shape[1]
+    tot = 0.0
+    for k in range(h):
+        w = 1.0 if _real_slice(k, n3) else 2.0
+        tot += w * float(np.sum(s[r:, k] ** 2))
+    return tot / n3
+
+
+def _orth(Y: np.ndarray) -> np.ndarray:
+    """Orthonormal basis of range(Y) (economy Householder QR)."""
+    Q, _ = np.linalg.qr(Y)
+    return Q
+
+
+def tsvd_randomized_hat(X: np.ndarray, k: int, p: int, q: int, Omega: np.ndarray):
+    """Per half-spectrum slice: Y = X_hat Omega; q power iterations
+    Q <- orth(X_hat^H Q), Q <- orth(X_hat Q); B = Q^H X_hat; SVD of B; keep k.
+    Omega is n2 x (k+p) x h.  Returns (Uh n1 x k x h, s k x h, Vh n2 x k x h)."""
+    n1, n2, n3 = X.shape
+    h = n3 // 2 + 1
+    ell = k + p
+    assert Omega.shape == (n2, ell, h)
+    Xh = half_spectrum(fft3(X))
+    Uh = np.zeros((n1, k, h), dtype=np.complex128)
+    Vh = np.zeros((n2, k, h), dtype=np.complex128)
+    s = np.zeros((k, h))
+    for f in range(h):
+        M = Xh[:, :, f]
+        if _real_slice(f, n3):
+            M = M.real.astype(np.complex128)
+        Q = _orth(M @ Omega[:, :, f])
+        for _ in range(q):
+            Q = _orth(np.conj(M).T @ Q)
+            Q = _orth(M @ Q)
+        Bm = np.conj(Q).T @ M
+        ub, sb, vbt = scipy.linalg.svd(Bm, full_matrices=False, lapack_driver="gesvd")
+        Uh[:, :, f] = (Q @ ub)[:, :k]
+        s[:, f] = sb[:k]
+        Vh[:, :, f] = np.conj(vbt).T[:, :k]
+    return Uh, s, Vh
+
+
+def tsvd_randomized(X: np.ndarray, k: int, p: int, q: int, Omega: np.ndarray):
+    """Randomized tubal-rank-k t-SVD; same output form as ``tsvd`` with m = k."""
+    n3 = X.shape[2]
+    Uh, s, Vh = tsvd_randomized_hat(X, k, p, q, Omega)
+    Sh = np.zeros((k, k, s.shape[1]), dtype=np.complex128)
+    for f in range(s.shape[1]):
+        Sh[:, :, f] = np.diag(s[:, f])
+    U = ifft3(hermitian_fill(Uh, n3)).real
+    S = ifft3(hermitian_fill(Sh, n3)).real
+    V = ifft3(hermitian_fill(Vh, n3)).real
+    return U, S, V
+
+
+def pinv_matlab(M: np.ndarray) -> np.ndarray:
+    """Moore-Penrose pseudo-inverse with MATLAB's default cut-off
+    max(size) * eps(sigma_max)."""
+    u, sv, vt = np.linalg.svd(M, full_matrices=False)
+    if sv.size == 0:
+        return np.zeros((M.shape[1], M.shape[0]), dtype=M.dtype)
+    tol = max(M.shape) * np.spacing(sv[0])
+    inv = np.where(sv > tol, 1.0 / np.where(sv > tol, sv, 1.0), 0.0)
+    return (np.conj(vt).T * inv) @ np.conj(u).T
+
+
+def tproject(X: np.ndarray, C: np.ndarray) -> np.ndarray:
+    """t-project Pi_C(X) = C * C^dagger * X, Algorithm 3 (all n3 slices)."""
+    Xh = fft3(X)
+    Ch = fft3(C)
+    Zh = np.empty_like(Xh)
+    for f in range(X.shape[2]):
+        Zh[:, :, f] = Ch[:, :, f] @ (pinv_matlab(Ch[:, :, f]) @ Xh[:, :, f])
+    return ifft3(Zh).real
+
+
+def tcx(A: np.ndarray, c: int, seed: int, mode: int = sampling_ref.PROB_A2,
+        p_given: np.ndarray | None = None):
+    """t-CX, Algorithm 4: draw lateral slices with probability min{1, c p_i},
+    C = rescaled picked slices, Z = Pi_C(A).  Returns (Z, idx, q)."""
+    A = np.asarray(A, dtype=np.float64)
+    if mode == sampling_ref.PROB_GIVEN:
+        p = np.asarray(p_given, dtype=np.float64)
+    else:
+        p = sampling_ref.probabilities(sampling_ref.lateral_norms_sq(A), None,
+                                       sampling_ref.PROB_A2)
+    idx, q = sampling_ref.draw(p, c, seed)
+    if len(idx) == 0:
+        return np.zeros_like(A), idx, q
+    C = A[:, idx, :] / np.sqrt(q[idx])[None, :, None]
+    return tproject(A, C), idx, q

@@ -1,0 +1,187 @@
+"""Pins of the decomposition oracles: t-SVD (Theorem 2.6), the randomized
+t-SVD, t-project / t-CX (Algorithms 3-4) and the completion ADMM (Algorithm 7)."""
+import numpy as np
+import pytest
+
+from oracle import completion_ref as Cm
+from oracle import decomp_ref as D
+from oracle import philox_ref as P
+from oracle import tensor_ref as T
+
+
+def rs(seed):
+    return np.random.default_rng(seed)
+
+
+@pytest.mark.parametrize("shape", [(5, 3, 4), (3, 5, 5), (4, 4, 1), (6, 2, 2)])
+def test_tsvd_reconstruction_and_orthogonality(shape):
+    X = rs(sum(shape)).standard_normal(shape)
+    U, S, V = D.tsvd(X)
+    n1, n2, n3 = shape
+    m = min(n1, n2)
+    assert U.shape == (n1, m, n3) and S.shape == (m, m, n3) and V.shape == (n2, m, n3)
+    # X = U * S * V^T through the block-circulant definition (not Algorithm 1)
+    np.testing.assert_allclose(T.tprod_circ(T.tprod_circ(U, S), T.ttranspose(V)), X, atol=1e-12)
+    # U^T * U = I and V^T * V = I (Def. 2.4, economy form)
+    np.testing.assert_allclose(T.tprod_circ(T.ttranspose(U), U), T.identity(m, n3), atol=1e-12)
+    np.testing.assert_allclose(T.tprod_circ(T.ttranspose(V), V), T.identity(m, n3), atol=1e-12)
+    # S is f-diagonal (Def. 2.5)
+    for t in range(n3):
+        assert np.allclose(S[:, :, t] - np.diag(np.diag(S[:, :, t])), 0, atol=1e-13)
+
+
+def test_tsvd_spectrum_is_spectrum_of_circ():
+    # Eq. circ1: the singular values of circ(X) are the union over all n3
+    # Fourier slices of their singular values.
+    X = rs(11).standard_normal((6, 4, 5))
+    _, s, _ = D.tsvd_hat(X)
+    full = np.concatenate([s[:, 0], s[:, 1], s[:, 2], s[:, 2], s[:, 1]])
+    ref = np.linalg.svd(T.circ(X), compute_uv=False)
+    np.testing.assert_allclose(np.sort(full), np.sort(ref[: full.size]), atol=1e-12)
+    assert np.all(ref[full.size:] < 1e-10)
+
+
+def test_tsvd_matrix_case():
+    X = rs(12).standard_normal((7, 5, 1))
+    U, S, V = D.tsvd(X)
+    np.testing.assert_allclose(np.diag(S[:, :, 0]), np.linalg.svd(X[:, :, 0], compute_uv=False), atol=1e-13)
+
+
+def test_eckart_young_truncation():
+    X = rs(13).standard_normal((6, 5, 4))
+    Uh, s, Vh = D.tsvd_hat(X)
+    U, S, V = D.tsvd(X)
+    r = 2
+    Xr = T.tprod(T.tprod(U[:, :r, :], S[:r, :r, :]), T.ttranspose(V[:, :r, :]))
+    err = np.sum((X - Xr) ** 2)
+    assert abs(err - D.truncate_error_sq(s, 4, r)) < 1e-10
+    # no random tubal-rank-r tensor P*Q does better
+    for seed in range(20):
+        Pm = rs(100 + seed).standard_normal((6, r, 4))
+        Qm = rs(200 + seed).standard_normal((r, 5, 4))
+        assert np.sum((X - T.tprod(Pm, Qm)) ** 2) >= err - 1e-9
+
+
+def _lowrank(n1, n2, n3, r, seed):
+    return T.tprod(rs(seed).standard_normal((n1, r, n3)), rs(seed + 1).standard_normal((r, n2, n3)))
+
+
+def test_randomized_tsvd_exact_on_low_rank():
+    X = _lowrank(20, 16, 6, 3, 20)
+    k, p = 3, 4
+    Om = P.sketch_signs(16, k + p, 4, 6, seed=5)
+    U, S, V = D.tsvd_randomized(X, k, p, 1, Om)
+    Xr = T.tprod(T.tprod(U, S), T.ttranspose(V))
+    np.testing.assert_allclose(Xr, X, atol=1e-10)
+    _, s_exact, _ = D.tsvd_hat(X)
+    _, s_rand, _ = D.tsvd_randomized_hat(X, k, p, 1, Om)
+    np.testing.assert_allclose(s_rand, s_exact[:k], rtol=1e-10)
+
+
+def test_randomized_tsvd_full_sketch_is_exact_topk():
+    # ell >= n2: the sketch spans the whole row space, so the result is the
+    # exact top-k truncation whatever the test matrix.
+    X = rs(21).standard_normal((12, 6, 5))
+    k, p = 3, 3
+    Om = P.sketch_signs(6, k + p, 3, 5, seed=1)
+    _, s_rand, _ = D.tsvd_randomized_hat(X, k, p, 0, Om)
+    _, s_exact, _ = D.tsvd_hat(X)
+    np.testing.assert_allclose(s_rand, s_exact[:k], rtol=1e-10)
+
+
+def test_randomized_tsvd_near_optimal_with_power_iterations():
+    X = _lowrank(40, 30, 4, 5, 30) + 1e-3 * rs(31).standard_normal((40, 30, 4))
+    k, p = 5, 5
+    Om = P.sketch_signs(30, k + p, 3, 4, seed=2)
+    U, S, V = D.tsvd_randomized(X, k, p, 2, Om)
+    err = np.sum((X - T.tprod(T.tprod(U, S), T.ttranspose(V))) ** 2)
+    _, s, _ = D.tsvd_hat(X)
+    opt = D.truncate_error_sq(s, 4, k)
+    assert err <= 1.01 * opt
+
+
+def test_sketch_signs_values():
+    Om = P.sketch_signs(5, 3, 3, 4, seed=0)
+    assert np.all(np.abs(Om) > 0)
+    np.testing.assert_allclose(np.abs(Om), 1.0, atol=1e-15)
+    assert np.all(Om[:, :, 0].imag == 0) and np.all(Om[:, :, 2].imag == 0)  # DC, Nyquist
+
+
+def test_tproject_least_squares_optimality():
+    # Eq. ell2reg: Pi_C(X) is the best approximation of X by C * Y
+    X = rs(40).standard_normal((6, 8, 3))
+    C = X[:, [1, 4, 6], :]
+    Z = D.tproject(X, C)
+    best = np.sum((X - Z) ** 2)
+    for s in range(20):
+        Y = rs(300 + s).standard_normal((3, 8, 3))
+        assert np.sum((X - T.tprod(C, Y)) ** 2) >= best - 1e-10
+    np.testing.assert_allclose(D.tproject(Z, C), Z, atol=1e-10)  # idempotent
+    np.testing.assert_allclose(D.tproject(C, C), C, atol=1e-10)
+
+
+def test_tcx_all_slices_kept_is_exact():
+    X = rs(41).standard_normal((7, 5, 4))
+    Z, idx, q = D.tcx(X, c=10 ** 6, seed=0)
+    assert len(idx) == 5
+    np.testing.assert_allclose(Z, X, atol=1e-10)
+
+
+def test_tcx_low_rank_recovered():
+    X = _lowrank(10, 30, 4, 2, 42)
+    Z, idx, q = D.tcx(X, c=12, seed=3)
+    assert len(idx) >= 2
+    np.testing.assert_allclose(Z, X, atol=1e-8 * np.abs(X).max())
+
+
+def test_pinv_matches_numpy():
+    M = rs(43).standard_normal((5, 3)) + 1j * rs(44).standard_normal((5, 3))
+    np.testing.assert_allclose(D.pinv_matlab(M), np.linalg.pinv(M), atol=1e-12)
+
+
+def test_svt_matrix_is_prox_of_nuclear_norm():
+    M = rs(50).standard_normal((6, 4))
+    tau = 0.7
+    L = Cm.svt_matrix(M, tau)
+    f = lambda Z: tau * np.linalg.svd(Z, compute_uv=False).sum() + 0.5 * np.sum((Z - M) ** 2)
+    best = f(L)
+    for s in range(50):
+        assert f(L + 1e-3 * rs(500 + s).standard_normal(L.shape)) >= best - 1e-12
+
+
+def test_svt_tensor_is_prox_of_tnn():
+    # prox of ||.||_TNN with weight 1/tau: argmin ||L||_TNN + 1/(2 tau) ||L - M||_F^2,
+    # with ||L||_TNN evaluated as ||circ(L)||_* / n3 (independent of the SVT code).
+    M = rs(51).standard_normal((4, 3, 5))
+    tau = 0.9
+    L = Cm.svt_tensor(M, tau)
+    tnn = lambda Z: np.linalg.svd(T.circ(Z), compute_uv=False).sum() / 5
+    f = lambda Z: tnn(Z) + 0.5 / tau * np.sum((Z - M) ** 2)
+    best = f(L)
+    for s in range(40):
+        assert f(L + 1e-3 * rs(600 + s).standard_normal(L.shape)) >= best - 1e-12
+    # n3 = 1 reduces to matrix SVT
+    M1 = M[:, :, :1]
+    np.testing.assert_allclose(Cm.svt_tensor(M1, tau)[:, :, 0], Cm.svt_matrix(M1[:, :, 0], tau), atol=1e-12)
+
+
+def test_admm_completion_recovers_low_rank():
+    X = _lowrank(20, 20, 6, 2, 60)
+    mask = rs(61).random(X.shape) < 0.6
+    L, E, Y, mu = Cm.tcomplete_svt(X, mask, iters=150)
+    assert np.all(E[mask] == 0)
+    rse = np.linalg.norm(L - X) / np.linalg.norm(X)
+    assert rse < 1e-3
+    # constraint residual L + E - P_Omega(X) is small at the end
+    assert np.abs(L + E - np.where(mask, X, 0)).max() < 1e-5 * np.abs(X).max()
+    assert abs(mu - min(1e-3 * 1.1 ** 150, 1e10)) < 1e-9 * mu
+
+
+def test_admm_resume_equals_continuous_run():
+    X = _lowrank(8, 7, 4, 2, 70)
+    mask = rs(71).random(X.shape) < 0.5
+    a = Cm.tcomplete_svt(X, mask, iters=10)
+    b = Cm.tcomplete_svt(X, mask, iters=4)
+    b = Cm.tcomplete_svt(X, mask, iters=6, state=b)
+    for x, y in zip(a[:3], b[:3]):
+        np.testing.assert_allclose(x, y, atol=1e-12)

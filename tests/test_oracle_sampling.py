@@ -1,0 +1,146 @@
+"""Pins of the sampling oracle: Philox, probabilities, Algorithm 2 (rt-product)."""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import philox_ref as P
+from oracle import sampling_ref as S
+from oracle import tensor_ref as T
+
+
+def test_philox_uniformity_and_avalanche():
+    n = 1 << 16
+    U = P.uniform53(np.arange(n, dtype=np.uint64), 0, 12345).astype(np.float64) / 2.0 ** 53
+    assert abs(U.mean() - 0.5) < 0.01
+    assert abs(U.var() - 1.0 / 12) < 0.005
+    counts, _ = np.histogram(U, bins=64, range=(0, 1))
+    chi2 = np.sum((counts - n / 64) ** 2 / (n / 64))
+    assert chi2 < 120  # 63 dof: p ~ 1e-5 cut-off
+    # flipping one counter bit changes about half of the 128 output bits
+    base = np.array(P.philox4x32_10(7, 0, 0, 0, 1, 2), dtype=np.uint64)
+    flips = []
+    for b in range(32):
+        o = np.array(P.philox4x32_10(7 ^ (1 << b), 0, 0, 0, 1, 2), dtype=np.uint64)
+        flips.append(sum(bin(int(x)).count("1") for x in (base ^ o)))
+    assert 50 < np.mean(flips) < 78
+    # different streams and seeds give unrelated numbers
+    a = P.uniform53(np.arange(1000, dtype=np.uint64), 0, 1)
+    b = P.uniform53(np.arange(1000, dtype=np.uint64), 1, 1)
+    c = P.uniform53(np.arange(1000, dtype=np.uint64), 0, 2)
+    assert np.count_nonzero(a == b) == 0 and np.count_nonzero(a == c) == 0
+
+
+def test_threshold_exact_edges():
+    Q = P.threshold53(np.array([0.0, 1.0, 0.5, 2.0 ** -53, 1 - 2.0 ** -53]))
+    assert list(Q) == [0, 2 ** 53, 2 ** 52, 1, 2 ** 53 - 1]
+    # q = 1 is always picked, q = 0 never
+    idx = P.bernoulli_pick(np.array([1.0, 0.0, 1.0, 0.0]), seed=3)
+    assert list(idx) == [0, 2]
+
+
+def test_probabilities_definitions():
+    rs = np.random.default_rng(0)
+    A = rs.standard_normal((3, 6, 4))
+    B = rs.standard_normal((6, 2, 4))
+    a2 = S.lateral_norms_sq(A)
+    b2 = S.horizontal_norms_sq(B)
+    for j in range(6):
+        assert abs(a2[j] - np.linalg.norm(A[:, j, :]) ** 2) < 1e-12
+        assert abs(b2[j] - np.linalg.norm(B[j, :, :]) ** 2) < 1e-12
+    p = S.probabilities(a2, b2, S.PROB_AB)
+    assert abs(p.sum() - 1) < 1e-15
+    w = np.array([np.linalg.norm(A[:, j, :]) * np.linalg.norm(B[j, :, :]) for j in range(6)])
+    np.testing.assert_allclose(p, w / w.sum(), rtol=1e-14)
+    p2 = S.probabilities(a2, None, S.PROB_A2)
+    np.testing.assert_allclose(p2, a2 / np.linalg.norm(A) ** 2, rtol=1e-14)
+    assert np.all(S.probabilities(np.zeros(3), np.zeros(3), S.PROB_AB) == 0)
+
+
+def test_pick_count_statistics():
+    q = np.linspace(0.05, 0.95, 40)
+    counts = np.array([len(P.bernoulli_pick(q, seed=s)) for s in range(2000)])
+    mean, var = q.sum(), np.sum(q * (1 - q))
+    assert abs(counts.mean() - mean) < 4 * np.sqrt(var / 2000)
+    assert abs(counts.var() - var) < 0.15 * var
+
+
+def _all_outcomes(A, B, q):
+    """Exact expectation over all 2^n2 Bernoulli outcomes of C*R and of the
+    squared error, by enumeration."""
+    n2 = A.shape[1]
+    exact = T.tprod(A, B)
+    EZ = np.zeros_like(exact)
+    Eerr = 0.0
+    for bits in itertools.product([0, 1], repeat=n2):
+        pr = 1.0
+        idx = []
+        for j, b in enumerate(bits):
+            pr *= q[j] if b else 1 - q[j]
+            if b:
+                idx.append(j)
+        if pr == 0.0:
+            continue
+        if idx:
+            C, R = S.sample_CR(A, B, np.array(idx), q)
+            Z = T.tprod_circ(C, R)   # definition route, independent of Algorithm 1
+        else:
+            Z = np.zeros_like(exact)
+        EZ += pr * Z
+        Eerr += pr * np.sum((exact - Z) ** 2)
+    return exact, EZ, Eerr
+
+
+def test_rt_product_unbiased_brute_force():
+    # Algorithm 2 with rescale 1/sqrt(q) is unbiased: E[C*R] = A*B, and the
+    # squared error has the closed form sum_j (1/q_j - 1)||A_{:j:} * B_{j::}||^2.
+    rs = np.random.default_rng(1)
+    A = rs.standard_normal((3, 8, 3))
+    B = rs.standard_normal((8, 2, 3))
+    p = S.probabilities(S.lateral_norms_sq(A), S.horizontal_norms_sq(B), S.PROB_AB)
+    q = S.keep_probabilities(p, 3)
+    exact, EZ, Eerr = _all_outcomes(A, B, q)
+    np.testing.assert_allclose(EZ, exact, atol=1e-11)
+    assert abs(Eerr - S.sampled_error_sq_expectation(A, B, q)) < 1e-9 * max(1, Eerr)
+
+
+def test_rt_product_deterministic_when_all_kept():
+    # c p_j >= 1 for all j => q = 1 => exact product (Algorithm 2)
+    rs = np.random.default_rng(2)
+    A = rs.standard_normal((4, 5, 6))
+    B = rs.standard_normal((5, 3, 6))
+    Z, idx, q = S.tprod_sampled(A, B, c=10 ** 6, seed=0)
+    assert list(idx) == list(range(5)) and np.all(q == 1)
+    np.testing.assert_allclose(Z, T.tprod_circ(A, B), atol=1e-12)
+
+
+def test_rt_product_matrix_case():
+    # n3 = 1: column/row sampling of Drineas, Kannan and Mahoney (2006)
+    rs = np.random.default_rng(3)
+    A = rs.standard_normal((6, 10, 1))
+    B = rs.standard_normal((10, 4, 1))
+    Z, idx, q = S.tprod_sampled(A, B, c=4, seed=9)
+    Am, Bm = A[:, :, 0], B[:, :, 0]
+    expect = sum(np.outer(Am[:, j], Bm[j, :]) / q[j] for j in idx)
+    np.testing.assert_allclose(Z[:, :, 0], expect, atol=1e-12)
+
+
+def test_rt_product_zero_input():
+    A = np.zeros((3, 4, 2))
+    B = np.ones((4, 2, 2))
+    Z, idx, q = S.tprod_sampled(A, B, c=2, seed=0)
+    assert len(idx) == 0 and np.all(Z == 0)
+
+
+def test_monte_carlo_error_matches_expectation():
+    rs = np.random.default_rng(4)
+    A = rs.standard_normal((5, 30, 4))
+    B = rs.standard_normal((30, 3, 4))
+    exact = T.tprod(A, B)
+    errs = []
+    q = None
+    for s in range(300):
+        Z, idx, q = S.tprod_sampled(A, B, c=8, seed=s)
+        errs.append(np.sum((Z - exact) ** 2))
+    expect = S.sampled_error_sq_expectation(A, B, q)
+    assert abs(np.mean(errs) / expect - 1) < 0.2
