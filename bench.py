@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Throughput of the sampled t-product hot path (Algorithm 2) on one GB300.
+
+Workload (synthetic, seeded): A 2000 x 4000 x 64 and B 4000 x 1500 x 64, each
+the t-product of N(0,1) factors at tubal rank 20 plus Gaussian noise of 1% of
+its RMS; c = 400, probabilities proportional to ||A(:,j,:)|| ||B(j,:,:)||,
+Philox seed 0.  One step = one tprod_sampled call: slice norms of A and B,
+probabilities and Bernoulli picks, rescaled gathers fused into the mode-3
+DFTs, facewise complex GEMMs of the 33 half-spectrum slices, inverse DFT.
+
+metric  "t-product TFLOP/s": nominal facewise-GEMM flops of the step
+        (8 n1 c' n4 per complex slice, 2 n1 c' n4 per real slice) divided by
+        the step time; inputs (3.6 GB) are larger than L2 and are streamed
+        every step.
+e2e     the same metric through the C entry point with host buffers: the
+        step's A and B copied from pinned host memory and Z copied back inside
+        the timed region.
+Multi-GPU: every rank runs its own replica (weak scaling, no collective).
+--impl reference times the float64 oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N1, N2, N4, N3, RANK_T, NOISE, C_SAMPLES, SEED = 2000, 4000, 1500, 64, 20, 0.01, 400, 0
+CPU_SAMPLE = 640   # rows of A and columns of B the CPU baseline sample keeps
+
+
+def gemm_flops(n1, cprime, n4, n3):
+    h = n3 // 2 + 1
+    real = 2 if n3 % 2 == 0 else 1
+    return 8.0 * n1 * cprime * n4 * (h - real) + 2.0 * n1 * cprime * n4 * real
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0)), "src": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "src": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        # samples under load: the upper half by power draw
+        order = sorted(range(len(sm)), key=lambda i: power[i])
+        loaded = [sm[i] for i in order[len(order) // 2:]] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power)}
+
+
+def host_array(x):
+    """Column-major torch tensor (n1, n2, n3) -> float64 numpy (n1, n2, n3)."""
+    return x.permute(2, 1, 0).contiguous().cpu().numpy().astype(np.float64).transpose(2, 1, 0)
+
+
+def run_oracle_sample(A, B, seed):
+    """Times the float64 oracle on the bounded sample A[:S], B[:, :S] (same
+    inner dimension n2 = 4000, n3 = 64, c = 400).  Returns (seconds, flops)."""
+    from oracle import sampling_ref
+    S = CPU_SAMPLE
+    As = host_array(A[:S])
+    Bs = host_array(B[:, :S])
+    t0 = time.perf_counter()
+    _, idx, _ = sampling_ref.tprod_sampled(As, Bs, C_SAMPLES, seed)
+    dt = time.perf_counter() - t0
+    return dt, gemm_flops(S, len(idx), S, N3)
+
+
+def make_inputs(device):
+    from paper_1704_04362_gb300 import synth
+    A = synth.lowrank_torch(N1, N2, N3, RANK_T, seed=1000, noise=NOISE, device=device)
+    B = synth.lowrank_torch(N2, N4, N3, RANK_T, seed=2000, noise=NOISE, device=device)
+    return A, B
+
+
+def gpu_uuid(torch, dev):
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        return str(dev)
+
+
+def roofline_for(name, ms_avg, cprime, peaks, sm_mhz):
+    """Algorithmic work per launch of the named kernel and its roofline."""
+    h = N3 // 2 + 1
+    fl = gemm_flops(N1, cprime, N4, N3)
+    if name == "cgemm_fp32":
+        # FP32 SIMT: 152 SMs x 128 lanes x 2 flops per FMA x clock
+        peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        ach = fl / (ms_avg * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_src": "derived: 152 SM x 128 FP32 lanes x 2 x sm_max_mhz"}
+    if name == "cgemm_tc":
+        peak = peaks["bf16_tflops"] / 2.0   # tf32 dense = bf16 / 2 (nominal ratio)
+        ach = 3 * fl / (ms_avg * 1e-3) / 1e12
+        return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "peak_src": peaks["src"]}
+    bytes_per = {
+        "norms_lateral": 4.0 * N1 * N2 * N3,
+        "norms_horizontal": 4.0 * N2 * N4 * N3,
+        "irdft": 8.0 * N1 * N4 * h + 4.0 * N1 * N4 * N3,
+    }.get(name)
+    if bytes_per is None:
+        return None
+    ach = bytes_per / (ms_avg * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_src": peaks["src"]}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3", "bf16x3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    import torch
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import paper_1704_04362_gb300 as tp
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    prec = {"fp32": tp.TP_FP32, "tf32x3": tp.TP_TF32X3, "bf16x3": tp.TP_BF16X3}[args.precision]
+    peaks = load_peaks()
+
+    A, B = make_inputs("cuda")
+    Z = tp.empty_tensor(N1, N4, N3)
+    idx = torch.empty(N2, dtype=torch.int32, device="cuda")
+    cnt = torch.empty(1, dtype=torch.int64, device="cuda")
+
+    def step():
+        tp.tprod_sampled(A, B, C_SAMPLES, seed=SEED, precision=prec, Z=Z, idx=idx, count=cnt)
+
+    sampler = ClockSampler(gpu_uuid(torch, local_rank))
+    sampler.start()
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    cprime = int(cnt.item())
+
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    n_launch0 = tp.launch_count()
+    tp.profile_start()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    prof = tp.profile_stop()
+    launches = tp.launch_count() - n_launch0
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    flops = gemm_flops(N1, cprime, N4, N3)
+    value = world * flops / (ms * 1e-3) / 1e12
+
+    # per-kernel breakdown and roofline of the dominant kernel
+    kernels = {k: {"ms_per_launch": v[0] / max(1, v[1]), "launches": v[1],
+                   "share": v[0] / max(1e-9, sum(x[0] for x in prof.values()))}
+               for k, v in prof.items()}
+    dom = max(prof, key=lambda k: prof[k][0]) if prof else None
+    roof = roofline_for(dom, prof[dom][0] / prof[dom][1], cprime, peaks, clocks.get("sm_mhz")) if dom else None
+    if roof is not None:
+        roof["kernel"] = dom
+
+    # end to end through the C entry point with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        Ah = torch.empty((N3, N2, N1), dtype=torch.float32, pin_memory=True)
+        Bh = torch.empty((N3, N4, N2), dtype=torch.float32, pin_memory=True)
+        Zh = torch.empty((N3, N4, N1), dtype=torch.float32, pin_memory=True)
+        Ah.copy_(A.permute(2, 1, 0))
+        Bh.copy_(B.permute(2, 1, 0))
+        Ad = tp.empty_tensor(N1, N2, N3)
+        Bd = tp.empty_tensor(N2, N4, N3)
+        torch.cuda.synchronize()
+
+        def e2e_step():
+            Ad.permute(2, 1, 0).copy_(Ah, non_blocking=True)
+            Bd.permute(2, 1, 0).copy_(Bh, non_blocking=True)
+            tp.tprod_sampled(Ad, Bd, C_SAMPLES, seed=SEED, precision=prec, Z=Z, idx=idx, count=cnt)
+            Zh.copy_(Z.permute(2, 1, 0), non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ev0.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ems = ev0.elapsed_time(ev1) / args.e2e_steps
+        if dist:
+            t = torch.tensor([ems], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * flops / (ems * 1e-3) / 1e12, "unit": "TFLOP/s",
+               "ms_per_step": ems,
+               "h2d_bytes_per_step": int(Ah.numel() * 4 + Bh.numel() * 4),
+               "d2h_bytes_per_step": int(Zh.numel() * 4)}
+        del Ah, Bh, Zh, Ad, Bd
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            dt, fl = run_oracle_sample(A, B, SEED)
+            cpu = {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
+                   "kind": "oracle",
+                   "sample": (f"float64 oracle rt-product of A[:{CPU_SAMPLE}] and "
+                              f"B[:, :{CPU_SAMPLE}] (n2=4000, n3=64, c=400), one run, "
+                              f"{dt:.1f} s")}
+        except Exception as e:  # reported, never fatal
+            cpu = {"value": None, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"failed: {e!r}"}
+
+    if rank == 0:
+        line = {
+            "metric": "t-product TFLOP/s (sampled rt-product, Algorithm 2)",
+            "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "tf32x3": "tf32x3 (f32 accumulate)",
+                      "bf16x3": "bf16x3 (f32 accumulate)"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": "rt-product A 2000x4000x64 * B 4000x1500x64, tubal rank 20 "
+                                   "+1% noise, c=400, p ~ ||A(:,j,:)|| ||B(j,:,:)||",
+                       "c_prime": cprime, "precision": args.precision,
+                       "l2": "inputs (3.58 GB) larger than L2, streamed every step",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+            "kernels": kernels, "cpu_baseline": cpu, "clocks": clocks,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def reference_arm(args, rank, world):
+    """--impl reference: the float64 oracle on the host cores, per step one
+    bounded sample of the same workload.  Rank 0 only."""
+    if rank != 0:
+        return
+    import torch
+    torch.cuda.set_device(0)
+    A, B = make_inputs("cuda")
+    times, fls = [], []
+    for i in range(args.warmup + args.steps):
+        dt, fl = run_oracle_sample(A, B, SEED)
+        if i >= args.warmup:
+            times.append(dt)
+            fls.append(fl)
+    sec = sum(times) / len(times)
+    val = (sum(fls) / len(fls)) / sec / 1e12
+    line = {
+        "impl": "reference", "metric": "t-product TFLOP/s (sampled rt-product, Algorithm 2)",
+        "value": val, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "rt-product A 2000x4000x64 * B 4000x1500x64, tubal rank 20 "
+                               "+1% noise, c=400, p ~ ||A(:,j,:)|| ||B(j,:,:)||",
+                   "parallelism": "host cores"},
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"float64 oracle on A[:{CPU_SAMPLE}], B[:, :{CPU_SAMPLE}] per step"},
+        "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,222 @@
+/*
+ * tprod.h -- C ABI of libtprod.so, a GB300 (sm_103a) implementation of the
+ * t-product tensor methods of Tarzanagh & Michailidis, "Fast Randomized
+ * Algorithms for t-Product Based Tensor Operations and Decompositions with
+ * Applications to Imaging Data" (arXiv 1704.04362).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Tensors.  A real n1 x n2 x n3 tensor X (Section 2, "Tensor indexing") is a
+ *   float32 device array with X(i,j,t) at X[i + n1*(j + n2*t)]: column-major,
+ *   frontal slices contiguous (the storage order of MATLAB, which the paper
+ *   uses).  The base address must be 16-byte aligned unless noted.
+ * Fourier domain.  The transform along mode 3 is MATLAB's fft(X,[],3)
+ *   (unnormalised, kernel exp(-2*pi*i*k*t/n3)); the inverse carries 1/n3.
+ *   Only the half spectrum k = 0..h-1, h = n3/2 + 1 (integer division), is
+ *   ever formed; slice n3-k is the conjugate of slice k for real data.  A
+ *   half-spectrum tensor is stored planar: real and imaginary float32 arrays,
+ *   each [k][column][row] with rows fastest.
+ * Pointers.  Unless said otherwise every array argument is a DEVICE pointer
+ *   on the current CUDA device, owned by the caller.  The library never
+ *   frees or keeps caller memory.
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *   default stream).  Every entry point validates its arguments on the host,
+ *   enqueues kernels on `stream` and returns without synchronising.
+ * Errors.  Every entry point returns a tp_status.  Argument errors are found
+ *   before anything is enqueued and leave outputs untouched.  A CUDA launch
+ *   error returns TP_ECUDA.  Conditions found on the device (an iteration
+ *   cap reached, a Cholesky breakdown) are OR-ed as TP_DEV_* bits into
+ *   opts->status when the caller supplies that word; the call itself still
+ *   returns TP_OK.  tp_last_error() gives a message for the calling thread.
+ * Workspace.  Scratch memory comes from opts->workspace (caller-owned device
+ *   buffer of opts->workspace_bytes, 256-byte aligned) when given.  With no
+ *   workspace the library allocates once per device and keeps the buffer,
+ *   growing it when a larger call needs it (that growth synchronises the
+ *   device); tp_release() frees it.  tp_workspace_query() gives the size a
+ *   call needs.  Calls that share a workspace must be ordered on one stream.
+ */
+#ifndef TPROD_H
+#define TPROD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TP_OK = 0,
+  TP_EINVAL = -1,        /* a size or mode is out of range */
+  TP_ENULL = -2,         /* a required pointer is NULL */
+  TP_EALIGN = -3,        /* a pointer is not aligned as required */
+  TP_ENOMEM = -4,        /* the library could not allocate its workspace */
+  TP_ECUDA = -5,         /* a CUDA runtime call or kernel launch failed */
+  TP_EWORKSPACE = -9,    /* opts->workspace is smaller than tp_workspace_query() */
+  TP_EUNSUPPORTED = -10  /* valid but not supported by this build (see message) */
+} tp_status;
+
+/* Device status bits OR-ed into opts->status. */
+#define TP_DEV_NOCONV     0x1  /* Jacobi sweeps reached opts->max_sweeps */
+#define TP_DEV_BREAKDOWN  0x2  /* CholeskyQR: Gram matrix not positive definite after shift */
+
+typedef enum {
+  TP_FP32 = 0,   /* plain FP32 SIMT arithmetic */
+  TP_TF32X3 = 1, /* facewise GEMMs on tcgen05 tensor cores, 3xTF32 split, FP32 accumulate */
+  TP_BF16X3 = 2  /* facewise GEMMs on tcgen05 tensor cores, BF16 hi/lo split (3 products), FP32 accumulate */
+} tp_precision;
+
+typedef enum {
+  TP_PROB_AB = 0,    /* p_j proportional to ||A(:,j,:)||_F ||B(j,:,:)||_F (eq. nearly_optimal_probs, beta=1) */
+  TP_PROB_A2 = 1,    /* p_j proportional to ||A(:,j,:)||_F^2          (eq. nonoptimal_probs, beta=1) */
+  TP_PROB_GIVEN = 2  /* p_j supplied by the caller (device float64[n2]) */
+} tp_prob_mode;
+
+typedef struct {
+  int precision;          /* tp_precision of the facewise GEMMs (default TP_FP32) */
+  int max_sweeps;         /* Jacobi sweep cap, 0 = default (30) */
+  void* workspace;        /* device scratch or NULL (library-managed) */
+  size_t workspace_bytes; /* size of `workspace` */
+  int32_t* status;        /* device int32 receiving TP_DEV_* bits, or NULL */
+} tp_opts;
+
+/* Operation codes for tp_workspace_query(). */
+typedef enum {
+  TP_OP_TPROD = 1,           /* dims: n1, n2, n4, n3 */
+  TP_OP_TPROD_SAMPLED = 2,   /* dims: n1, n2, n4, n3 */
+  TP_OP_TSVD = 3,            /* dims: n1, n2, n3 */
+  TP_OP_TSVD_RANDOMIZED = 4, /* dims: n1, n2, n3, k, p */
+  TP_OP_TCOMPLETE_SVT = 5,   /* dims: n1, n2, n3 */
+  TP_OP_SLICE_NORMS = 6      /* dims: n1, n2, n3 */
+} tp_op;
+
+/* ---------------------------------------------------------------- t-product
+ * tprod: C = A * B, the t-product of Def. 2.1 computed as Algorithm 1 (DFT
+ * along mode 3, facewise complex products of the half spectrum, inverse DFT).
+ *   A  n1 x n2 x n3 (input), B  n2 x n4 x n3 (input), C  n1 x n4 x n3 (output).
+ * Sizes must be >= 1 (n3 <= 4096).  C must not overlap A or B.            */
+int tprod(const float* A, const float* B, float* C,
+          int64_t n1, int64_t n2, int64_t n4, int64_t n3,
+          const tp_opts* opts, void* stream);
+
+/* tprod_sampled: the rt-product of Algorithm 2, Z = C * R ~ A * B.
+ * Slice j of n2 is kept with probability q_j = min{1, c p_j} (Bernoulli,
+ * decided in index order), p from `prob_mode` (see tp_prob_mode; p_given is
+ * a device float64[n2] summing to 1 when prob_mode == TP_PROB_GIVEN, else
+ * ignored).  Kept lateral slices A(:,j,:) and horizontal slices B(j,:,:)
+ * are scaled by 1/sqrt(q_j) (the rescale 1/min{1, sqrt(c p_j)} of
+ * Algorithm 2), transformed and multiplied facewise; S and D are never
+ * formed.  The coin for slice j is Philox4x32-10 (Salmon et al., SC'11) with
+ * counter (j mod 2^32, j >> 32, 0, 0) and key (seed mod 2^32, seed >> 32):
+ * j is kept iff ((x0 >> 5) * 2^26 + (x1 >> 6)) < floor(q_j * 2^53).
+ *   idx_out    device int32[n2] or NULL: kept indices, ascending, first c' valid
+ *   count_out  device int64 or NULL: c', the number kept
+ *   Z          n1 x n4 x n3 output (zero when nothing is kept)
+ * c >= 1.  The count stays on the device: no host synchronisation.          */
+int tprod_sampled(const float* A, const float* B, float* Z,
+                  int64_t n1, int64_t n2, int64_t n4, int64_t n3,
+                  int64_t c, uint64_t seed, int prob_mode, const double* p_given,
+                  int32_t* idx_out, int64_t* count_out,
+                  const tp_opts* opts, void* stream);
+
+/* ---------------------------------------------------------------- t-SVD
+ * tsvd: X = U * S * V^T (Theorem 2.6), computed as in Eq. circ1: an SVD of
+ * every half-spectrum Fourier slice (one-sided Jacobi, singular values
+ * descending), the conjugate slices implied, then the inverse DFT.
+ * Economy form with m = min(n1, n2):
+ *   U  n1 x m x n3,  S  m x m x n3 (f-diagonal),  V  n2 x m x n3 (outputs).
+ * Singular vectors are unique only up to a unit phase per column (and a
+ * rotation inside repeated singular values).  Limits: m <= 512, n3 <= 4096. */
+int tsvd(const float* X, int64_t n1, int64_t n2, int64_t n3,
+         float* U, float* S, float* V, const tp_opts* opts, void* stream);
+
+/* tsvd_randomized: rank-k approximation X ~ U * S * V^T of tubal rank k.
+ * Per half-spectrum slice: Y = X_hat Omega with an n2 x (k+p) random-sign
+ * test matrix from Philox stream 2 (entries (s0 + i s1)/sqrt(2), real
+ * signs on the real slices; entry (r,c,f) uses counter r + n2*(c + (k+p)*f)),
+ * q power iterations Q <- orth(X_hat^H Q), Q <- orth(X_hat Q), each orth a
+ * CholeskyQR2 with float64 Gram and Cholesky, then B = Q^H X_hat, a float64
+ * SVD of B and U = Q U_B truncated to k.
+ *   U  n1 x k x n3,  S  k x k x n3,  V  n2 x k x n3 (outputs).
+ * Requires 1 <= k, k + p <= min(n1, n2, 128), q >= 0.                     */
+int tsvd_randomized(const float* X, int64_t n1, int64_t n2, int64_t n3,
+                    int k, int p, int q, uint64_t seed,
+                    float* U, float* S, float* V, const tp_opts* opts, void* stream);
+
+/* ---------------------------------------------------------------- completion
+ * tcomplete_svt: `iters` iterations of the ADMM of Algorithm 7 in the
+ * completion form of problem (tlow6): minimise ||L||_TNN subject to
+ * L + E = X, E = 0 on the observed set.  Per iteration, with tau = 1/mu:
+ *   L <- SVT_tau(X - E - Y/mu)  (tensor singular value thresholding: every
+ *                                Fourier slice's singular values shrunk by tau)
+ *   E <- (X - L - Y/mu) where mask == 0, 0 where mask != 0
+ *   Y <- Y + mu (L + E - X);    mu <- min(rho mu, mu_max)
+ *   X     n1 x n2 x n3 observed data (entries off the mask are ignored)
+ *   mask  uint8 n1 x n2 x n3, nonzero = observed
+ *   L, E, Y  n1 x n2 x n3 state, read as the starting point and overwritten
+ *            (zeros and *mu = mu0 start Algorithm 7 afresh; passing the
+ *            previous outputs resumes it)
+ *   mu    device float64 scalar, read and updated in place
+ * Paper constants: mu0 = 1e-3, rho = 1.1, mu_max = 1e10.  Limits as tsvd.  */
+int tcomplete_svt(const float* X, const uint8_t* mask,
+                  int64_t n1, int64_t n2, int64_t n3, int iters,
+                  double rho, double mu_max,
+                  float* L, float* E, float* Y, double* mu,
+                  const tp_opts* opts, void* stream);
+
+/* ---------------------------------------------------------------- stages
+ * The steps of the paths above, exposed for callers that compose their own.
+ *
+ * tp_rdft3: half-spectrum DFT along mode 3 of a real rows x n3 array
+ *   (X[r + rows*t]) into planar Xr, Xi [k][r], k < h (Section 2, fft(X,[],3)).
+ * tp_irdft3: its inverse (ifft(.,[],3) of the conjugate-symmetric spectrum
+ *   whose half is given); writes real Out[r + rows*t].                     */
+int tp_rdft3(const float* X, int64_t rows, int64_t n3, float* Xr, float* Xi, void* stream);
+int tp_irdft3(const float* Xr, const float* Xi, int64_t rows, int64_t n3, float* Out, void* stream);
+
+/* tp_slice_norms: squared Frobenius norms of slices, accumulated in (at
+ * least) float64 precision in a fixed order (deterministic), as used by the
+ * sampling probabilities of Section 3.1.
+ *   which = 0: out[j] = ||X(:,j,:)||_F^2, j < n2 (lateral slices)
+ *   which = 1: out[i] = ||X(i,:,:)||_F^2, i < n1 (horizontal slices)
+ *   out   device float64 array.                                            */
+int tp_slice_norms(const float* X, int64_t n1, int64_t n2, int64_t n3, int which,
+                   double* out, const tp_opts* opts, void* stream);
+
+/* tp_sample_draw: Algorithm 2's picking loop on the device.  From weights
+ * w (device float64[n]; mode TP_PROB_AB: w = a2, w2 = b2 and
+ * p_j = sqrt(a2_j b2_j)/sum; TP_PROB_A2: p_j = a2_j / sum a2; TP_PROB_GIVEN:
+ * p = w) computes q_j = min{1, c p_j}, draws with Philox as in tprod_sampled
+ * (counter word 2 = `stream_id`), and writes the kept indices ascending to
+ * idx (int32[n]), 1/sqrt(q) of each kept index to scale (float32[n]) and
+ * the count to count (int64).  q_out (float64[n]) receives q when non-NULL. */
+int tp_sample_draw(const double* w, const double* w2, int64_t n, int64_t c,
+                   uint64_t seed, int prob_mode, uint32_t stream_id,
+                   int32_t* idx, float* scale, int64_t* count, double* q_out,
+                   void* stream);
+
+/* ---------------------------------------------------------------- runtime */
+size_t tp_workspace_query(int op, const int64_t* dims, int ndims, const tp_opts* opts);
+const char* tp_status_string(int status);
+const char* tp_last_error(void);
+/* Frees the library-managed workspace of the current device (synchronises it). */
+int tp_release(void);
+/* Number of kernels this library has launched in this process. */
+uint64_t tp_launch_count(void);
+int tp_version(void);
+
+/* Per-kernel timing.  Between tp_profile_start() and tp_profile_stop() every
+ * kernel launch of this library is bracketed by a CUDA event pair recorded on
+ * the launch stream.  tp_profile_stop() synchronises the device and adds the
+ * elapsed times into per-kernel totals; tp_profile_entry(i, ...) reads total
+ * i (name into name[name_len], total milliseconds, launch count) and returns
+ * TP_EINVAL past the last one; tp_profile_reset() clears the totals.      */
+int tp_profile_start(void);
+int tp_profile_stop(void);
+int tp_profile_entry(int i, char* name, int name_len, double* total_ms, int64_t* launches);
+int tp_profile_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TPROD_H */

@@ -1,0 +1,369 @@
+"""ctypes binding of libtprod.so (declared in include/tprod.h).
+
+Argument marshalling only: every step of every path runs in the library's
+CUDA kernels.  Tensors are torch CUDA tensors of logical shape (n1, n2, n3)
+stored column-major (strides (1, n1, n1*n2)), as produced by
+``empty_tensor`` / ``as_tprod_layout``.  The library's scratch memory is a
+torch-allocated buffer passed through tp_opts, so the library itself does
+not allocate when called from here.  There is no CPU fallback: a missing
+library or a CUDA-less process raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = [
+    "TP_FP32", "TP_TF32X3", "TP_BF16X3", "TP_PROB_AB", "TP_PROB_A2", "TP_PROB_GIVEN",
+    "TprodError", "lib", "lib_path", "empty_tensor", "as_tprod_layout",
+    "tprod", "tprod_sampled", "tsvd", "tsvd_randomized", "tcomplete_svt",
+    "rdft3", "irdft3", "slice_norms", "sample_draw", "launch_count", "exported_symbols",
+    "profile_start", "profile_stop",
+]
+
+TP_FP32, TP_TF32X3, TP_BF16X3 = 0, 1, 2
+TP_PROB_AB, TP_PROB_A2, TP_PROB_GIVEN = 0, 1, 2
+TP_OP_TPROD, TP_OP_TPROD_SAMPLED, TP_OP_TSVD, TP_OP_TSVD_RANDOMIZED, TP_OP_TCOMPLETE_SVT, \
+    TP_OP_SLICE_NORMS = 1, 2, 3, 4, 5, 6
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_c_i64, _c_u64, _c_int, _c_u32 = ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32
+_vp, _dbl = ctypes.c_void_p, ctypes.c_double
+
+
+class TprodError(RuntimeError):
+    pass
+
+
+class TpOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("max_sweeps", ctypes.c_int),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
+                ("status", ctypes.c_void_p)]
+
+
+# Every symbol include/tprod.h declares, with its ctypes signature.
+_SIGS = {
+    "tprod": (_c_int, [_vp, _vp, _vp, _c_i64, _c_i64, _c_i64, _c_i64, _vp, _vp]),
+    "tprod_sampled": (_c_int, [_vp, _vp, _vp, _c_i64, _c_i64, _c_i64, _c_i64, _c_i64, _c_u64,
+                               _c_int, _vp, _vp, _vp, _vp, _vp]),
+    "tsvd": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _vp, _vp, _vp, _vp, _vp]),
+    "tsvd_randomized": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_int, _c_int, _c_int, _c_u64,
+                                 _vp, _vp, _vp, _vp, _vp]),
+    "tcomplete_svt": (_c_int, [_vp, _vp, _c_i64, _c_i64, _c_i64, _c_int, _dbl, _dbl,
+                               _vp, _vp, _vp, _vp, _vp, _vp]),
+    "tp_rdft3": (_c_int, [_vp, _c_i64, _c_i64, _vp, _vp, _vp]),
+    "tp_irdft3": (_c_int, [_vp, _vp, _c_i64, _c_i64, _vp, _vp]),
+    "tp_slice_norms": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_int, _vp, _vp, _vp]),
+    "tp_sample_draw": (_c_int, [_vp, _vp, _c_i64, _c_i64, _c_u64, _c_int, _c_u32, _vp, _vp,
+                                _vp, _vp, _vp]),
+    "tp_workspace_query": (ctypes.c_size_t, [_c_int, _vp, _c_int, _vp]),
+    "tp_status_string": (ctypes.c_char_p, [_c_int]),
+    "tp_last_error": (ctypes.c_char_p, []),
+    "tp_release": (_c_int, []),
+    "tp_launch_count": (_c_u64, []),
+    "tp_version": (_c_int, []),
+    "tp_profile_start": (_c_int, []),
+    "tp_profile_stop": (_c_int, []),
+    "tp_profile_entry": (_c_int, [_c_int, ctypes.c_char_p, _c_int, _vp, _vp]),
+    "tp_profile_reset": (_c_int, []),
+}
+
+_LIB = None
+_LOCK = threading.Lock()
+
+
+def lib_path() -> str:
+    return os.environ.get("TPROD_LIB", os.path.join(_HERE, "libtprod.so"))
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    with _LOCK:
+        if _LIB is None:
+            path = lib_path()
+            if not os.path.exists(path):
+                raise TprodError(f"{path} is missing: build it with "
+                                 "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _LIB = L
+    return _LIB
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def launch_count() -> int:
+    return int(lib().tp_launch_count())
+
+
+def profile_start():
+    L = lib()
+    L.tp_profile_reset()
+    _check(L.tp_profile_start(), "tp_profile_start")
+
+
+def profile_stop() -> dict:
+    """Stops timing; returns {kernel name: (total ms, launches)}."""
+    L = lib()
+    _check(L.tp_profile_stop(), "tp_profile_stop")
+    out = {}
+    i = 0
+    buf = ctypes.create_string_buffer(128)
+    while True:
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        if L.tp_profile_entry(i, buf, 128, ctypes.cast(ctypes.byref(ms), ctypes.c_void_p),
+                              ctypes.cast(ctypes.byref(n), ctypes.c_void_p)) != 0:
+            break
+        out[buf.value.decode()] = (ms.value, n.value)
+        i += 1
+    return out
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        L = lib()
+        raise TprodError(f"{what}: {L.tp_status_string(rc).decode()}: "
+                         f"{L.tp_last_error().decode()}")
+
+
+# ---------------------------------------------------------------- torch plumbing
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise TprodError("libtprod needs a CUDA device; there is no CPU path")
+    return torch
+
+
+def empty_tensor(n1, n2, n3, dtype=None, device=None):
+    """Uninitialised column-major tensor of logical shape (n1, n2, n3)."""
+    torch = _torch()
+    dtype = dtype or torch.float32
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    return torch.empty((n3, n2, n1), dtype=dtype, device=device).permute(2, 1, 0)
+
+
+def as_tprod_layout(x, dtype=None):
+    """Column-major device copy of a (n1, n2, n3) array or tensor (no copy when
+    it already is one)."""
+    torch = _torch()
+    dtype = dtype or torch.float32
+    if isinstance(x, np.ndarray):
+        x = torch.from_numpy(np.ascontiguousarray(np.transpose(x, (2, 1, 0))))
+        x = x.to(device="cuda", dtype=dtype).permute(2, 1, 0)
+        return x
+    x = x.to(device="cuda", dtype=dtype)
+    if _is_colmajor(x):
+        return x
+    return x.permute(2, 1, 0).contiguous().permute(2, 1, 0)
+
+
+def _is_colmajor(x) -> bool:
+    if x.dim() != 3:
+        return False
+    n1, n2, n3 = x.shape
+    want = (1, n1, n1 * n2)
+    return all(s == w or d == 1 for s, w, d in zip(x.stride(), want, x.shape))
+
+
+def _tensor_arg(x, name, dtype=None):
+    torch = _torch()
+    dtype = dtype or torch.float32
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TprodError(f"{name} must be a CUDA torch tensor")
+    if x.dtype != dtype:
+        raise TprodError(f"{name} must be {dtype}, got {x.dtype}")
+    if x.dim() == 3 and not _is_colmajor(x):
+        raise TprodError(f"{name} must be column-major (use as_tprod_layout)")
+    if x.dim() != 3 and not x.is_contiguous():
+        raise TprodError(f"{name} must be contiguous")
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _stream():
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+_WS = {}
+
+
+def _opts(op, dims, precision=TP_FP32, status=None, max_sweeps=0):
+    """tp_opts with a torch-allocated workspace large enough for this call."""
+    torch = _torch()
+    L = lib()
+    d = (ctypes.c_int64 * len(dims))(*[int(v) for v in dims])
+    o = TpOpts(int(precision), int(max_sweeps), None, 0, None)
+    need = int(L.tp_workspace_query(op, ctypes.cast(d, ctypes.c_void_p), len(dims), ctypes.byref(o)))
+    dev = torch.cuda.current_device()
+    buf = _WS.get(dev)
+    if need > 0 and (buf is None or buf.numel() < need):
+        _WS[dev] = buf = torch.empty(max(need, 1 << 20), dtype=torch.uint8, device="cuda")
+    if buf is not None and need > 0:
+        o.workspace = buf.data_ptr()
+        o.workspace_bytes = buf.numel()
+    if status is not None:
+        o.status = status.data_ptr()
+    return o
+
+
+# ---------------------------------------------------------------- entry points
+
+def tprod(A, B, C=None, precision=TP_FP32):
+    """C = A * B (Def. 2.1 / Algorithm 1)."""
+    n1, n2, n3 = A.shape
+    n2b, n4, n3b = B.shape
+    if n2b != n2 or n3b != n3:
+        raise TprodError(f"tprod: shapes {tuple(A.shape)} and {tuple(B.shape)} do not chain")
+    if C is None:
+        C = empty_tensor(n1, n4, n3, device=A.device)
+    o = _opts(TP_OP_TPROD, (n1, n2, n4, n3), precision)
+    rc = lib().tprod(_tensor_arg(A, "A"), _tensor_arg(B, "B"), _tensor_arg(C, "C"),
+                     n1, n2, n4, n3, ctypes.byref(o), _stream())
+    _check(rc, "tprod")
+    return C
+
+
+def tprod_sampled(A, B, c, seed=0, prob_mode=TP_PROB_AB, p_given=None, precision=TP_FP32,
+                  Z=None, idx=None, count=None):
+    """rt-product (Algorithm 2).  Returns (Z, idx int32[n2], count int64[1]);
+    idx[:count] are the kept slice indices, ascending."""
+    torch = _torch()
+    n1, n2, n3 = A.shape
+    n2b, n4, n3b = B.shape
+    if n2b != n2 or n3b != n3:
+        raise TprodError("tprod_sampled: shapes do not chain")
+    if Z is None:
+        Z = empty_tensor(n1, n4, n3, device=A.device)
+    if idx is None:
+        idx = torch.empty(n2, dtype=torch.int32, device=A.device)
+    if count is None:
+        count = torch.empty(1, dtype=torch.int64, device=A.device)
+    pg = None
+    if prob_mode == TP_PROB_GIVEN:
+        if p_given is None or p_given.numel() != n2:
+            raise TprodError("tprod_sampled: TP_PROB_GIVEN needs p_given of length n2")
+        pg = _tensor_arg(p_given, "p_given", torch.float64)
+    o = _opts(TP_OP_TPROD_SAMPLED, (n1, n2, n4, n3), precision)
+    rc = lib().tprod_sampled(_tensor_arg(A, "A"), _tensor_arg(B, "B"), _tensor_arg(Z, "Z"),
+                             n1, n2, n4, n3, int(c), int(seed) & ((1 << 64) - 1), int(prob_mode),
+                             pg, _tensor_arg(idx, "idx", torch.int32),
+                             _tensor_arg(count, "count", torch.int64), ctypes.byref(o), _stream())
+    _check(rc, "tprod_sampled")
+    return Z, idx, count
+
+
+def tsvd(X, max_sweeps=0, status=None):
+    """Economy t-SVD (Theorem 2.6): returns (U, S, V)."""
+    n1, n2, n3 = X.shape
+    m = min(n1, n2)
+    U = empty_tensor(n1, m, n3, device=X.device)
+    S = empty_tensor(m, m, n3, device=X.device)
+    V = empty_tensor(n2, m, n3, device=X.device)
+    o = _opts(TP_OP_TSVD, (n1, n2, n3), TP_FP32, status, max_sweeps)
+    rc = lib().tsvd(_tensor_arg(X, "X"), n1, n2, n3, _tensor_arg(U, "U"), _tensor_arg(S, "S"),
+                    _tensor_arg(V, "V"), ctypes.byref(o), _stream())
+    _check(rc, "tsvd")
+    return U, S, V
+
+
+def tsvd_randomized(X, k, p=10, q=2, seed=0, status=None, max_sweeps=0):
+    """Randomized tubal-rank-k t-SVD: returns (U, S, V)."""
+    n1, n2, n3 = X.shape
+    U = empty_tensor(n1, k, n3, device=X.device)
+    S = empty_tensor(k, k, n3, device=X.device)
+    V = empty_tensor(n2, k, n3, device=X.device)
+    o = _opts(TP_OP_TSVD_RANDOMIZED, (n1, n2, n3, k, p), TP_FP32, status, max_sweeps)
+    rc = lib().tsvd_randomized(_tensor_arg(X, "X"), n1, n2, n3, int(k), int(p), int(q),
+                               int(seed) & ((1 << 64) - 1), _tensor_arg(U, "U"),
+                               _tensor_arg(S, "S"), _tensor_arg(V, "V"), ctypes.byref(o),
+                               _stream())
+    _check(rc, "tsvd_randomized")
+    return U, S, V
+
+
+def tcomplete_svt(X, mask, iters, L=None, E=None, Y=None, mu=None, mu0=1e-3, rho=1.1,
+                  mu_max=1e10, status=None, max_sweeps=0):
+    """ADMM completion (Algorithm 7, problem tlow6).  State (L, E, Y, mu) is
+    updated in place and returned."""
+    torch = _torch()
+    n1, n2, n3 = X.shape
+    if L is None:
+        L = torch.zeros_like(X)
+        E = torch.zeros_like(X)
+        Y = torch.zeros_like(X)
+    if mu is None:
+        mu = torch.full((1,), float(mu0), dtype=torch.float64, device=X.device)
+    o = _opts(TP_OP_TCOMPLETE_SVT, (n1, n2, n3), TP_FP32, status, max_sweeps)
+    rc = lib().tcomplete_svt(_tensor_arg(X, "X"), _tensor_arg(mask, "mask", torch.uint8),
+                             n1, n2, n3, int(iters), float(rho), float(mu_max),
+                             _tensor_arg(L, "L"), _tensor_arg(E, "E"), _tensor_arg(Y, "Y"),
+                             _tensor_arg(mu, "mu", torch.float64), ctypes.byref(o), _stream())
+    _check(rc, "tcomplete_svt")
+    return L, E, Y, mu
+
+
+def rdft3(X):
+    """Half-spectrum DFT along mode 3: returns (Xr, Xi), each (n1, n2, h)."""
+    n1, n2, n3 = X.shape
+    h = n3 // 2 + 1
+    Xr = empty_tensor(n1, n2, h, device=X.device)
+    Xi = empty_tensor(n1, n2, h, device=X.device)
+    rc = lib().tp_rdft3(_tensor_arg(X, "X"), n1 * n2, n3, _tensor_arg(Xr, "Xr"),
+                        _tensor_arg(Xi, "Xi"), _stream())
+    _check(rc, "tp_rdft3")
+    return Xr, Xi
+
+
+def irdft3(Xr, Xi, n3):
+    n1, n2, h = Xr.shape
+    if h != n3 // 2 + 1:
+        raise TprodError("irdft3: spectrum length does not match n3")
+    out = empty_tensor(n1, n2, n3, device=Xr.device)
+    rc = lib().tp_irdft3(_tensor_arg(Xr, "Xr"), _tensor_arg(Xi, "Xi"), n1 * n2, n3,
+                         _tensor_arg(out, "out"), _stream())
+    _check(rc, "tp_irdft3")
+    return out
+
+
+def slice_norms(X, which):
+    """Squared Frobenius norms: which=0 lateral (n2 values), 1 horizontal (n1)."""
+    torch = _torch()
+    n1, n2, n3 = X.shape
+    out = torch.empty(n2 if which == 0 else n1, dtype=torch.float64, device=X.device)
+    o = _opts(TP_OP_SLICE_NORMS, (n1, n2, n3))
+    rc = lib().tp_slice_norms(_tensor_arg(X, "X"), n1, n2, n3, int(which),
+                              _tensor_arg(out, "out", torch.float64), ctypes.byref(o), _stream())
+    _check(rc, "tp_slice_norms")
+    return out
+
+
+def sample_draw(w, w2, c, seed, prob_mode, stream_id=0):
+    """Picking loop of Algorithm 2.  Returns (idx, scale, count, q)."""
+    torch = _torch()
+    n = w.numel()
+    idx = torch.empty(n, dtype=torch.int32, device=w.device)
+    scale = torch.empty(n, dtype=torch.float32, device=w.device)
+    count = torch.empty(1, dtype=torch.int64, device=w.device)
+    q = torch.empty(n, dtype=torch.float64, device=w.device)
+    rc = lib().tp_sample_draw(_tensor_arg(w, "w", torch.float64),
+                              _tensor_arg(w2, "w2", torch.float64) if w2 is not None else None,
+                              n, int(c), int(seed) & ((1 << 64) - 1), int(prob_mode),
+                              int(stream_id), _tensor_arg(idx, "idx", torch.int32),
+                              _tensor_arg(scale, "scale", torch.float32),
+                              _tensor_arg(count, "count", torch.int64),
+                              _tensor_arg(q, "q", torch.float64), _stream())
+    _check(rc, "tp_sample_draw")
+    return idx, scale, count, q
