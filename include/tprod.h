@@ -183,6 +183,30 @@ int tp_irdft3(const float* Xr, const float* Xi, int64_t rows, int64_t n3, float*
 int tp_slice_norms(const float* X, int64_t n1, int64_t n2, int64_t n3, int which,
                    double* out, const tp_opts* opts, void* stream);
 
+/* tp_slice_norms_noalloc: the same norms as tp_slice_norms, computed by the
+ * same kernels, for callers that cannot allocate device memory (a framework
+ * that owns the whole memory pool, a real-time caller that forbids
+ * allocation after start-up, or one that cannot afford the device-wide
+ * synchronisation cudaMalloc/cudaFree may cause).  The paper has no
+ * counterpart: this is a deployment variant, not a step of the method.
+ *   No allocation: the partial sums live in a fixed 8 MiB array of device
+ *   global memory inside the library (tp_slice_norms_noalloc_capacity()
+ *   doubles), which every GPU that loads the library holds until exit.
+ *   Limit: the call needs n2*n3 partial sums for which == 0 and about
+ *   min(n1, 1216*256) for which == 1; a call needing more than the capacity
+ *   returns TP_EINVAL with a message and enqueues nothing.
+ *   The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   Every call shares the one array: calls that may run at the same time on
+ *   the GPU (different streams, different host threads) race and give wrong
+ *   norms; order them on one stream.  Nothing in the array needs clearing:
+ *   each call writes every slot it reads.
+ *   X, out: as tp_slice_norms (device pointers; out float64).             */
+int tp_slice_norms_noalloc(const float* X, int64_t n1, int64_t n2, int64_t n3, int which,
+                           double* out, void* stream);
+size_t tp_slice_norms_noalloc_capacity(void);
+
 /* tp_sample_draw: Algorithm 2's picking loop on the device.  From weights
  * w (device float64[n]; mode TP_PROB_AB: w = a2, w2 = b2 and
  * p_j = sqrt(a2_j b2_j)/sum; TP_PROB_A2: p_j = a2_j / sum a2; TP_PROB_GIVEN:

@@ -21,7 +21,7 @@ __all__ = [
     "TprodError", "lib", "lib_path", "empty_tensor", "as_tprod_layout",
     "tprod", "tprod_sampled", "tsvd", "tsvd_randomized", "tcomplete_svt",
     "rdft3", "irdft3", "slice_norms", "sample_draw", "launch_count", "exported_symbols",
-    "profile_start", "profile_stop",
+    "profile_start", "profile_stop", "slice_norms_noalloc",
 ]
 
 TP_FP32, TP_TF32X3, TP_BF16X3 = 0, 1, 2
@@ -69,6 +69,8 @@ _SIGS = {
     "tp_profile_stop": (_c_int, []),
     "tp_profile_entry": (_c_int, [_c_int, ctypes.c_char_p, _c_int, _vp, _vp]),
     "tp_profile_reset": (_c_int, []),
+    "tp_slice_norms_noalloc": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_int, _vp, _vp]),
+    "tp_slice_norms_noalloc_capacity": (ctypes.c_size_t, []),
 }
 
 _LIB = None
@@ -347,6 +349,21 @@ def slice_norms(X, which):
     rc = lib().tp_slice_norms(_tensor_arg(X, "X"), n1, n2, n3, int(which),
                               _tensor_arg(out, "out", torch.float64), ctypes.byref(o), _stream())
     _check(rc, "tp_slice_norms")
+    return out
+
+
+def slice_norms_noalloc(X, which, out=None):
+    """Slice norms through tp_slice_norms_noalloc: the library allocates
+    nothing (its scratch is a fixed device array), for callers that cannot
+    allocate; ``out`` may be passed in so that this call allocates nothing
+    either."""
+    torch = _torch()
+    n1, n2, n3 = X.shape
+    if out is None:
+        out = torch.empty(n2 if which == 0 else n1, dtype=torch.float64, device=X.device)
+    rc = lib().tp_slice_norms_noalloc(_tensor_arg(X, "X"), n1, n2, n3, int(which),
+                                      _tensor_arg(out, "out", torch.float64), _stream())
+    _check(rc, "tp_slice_norms_noalloc")
     return out
 
 
