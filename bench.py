@@ -34,7 +34,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N1, N2, N4, N3, RANK_T, NOISE, C_SAMPLES, SEED = 2000, 4000, 1500, 64, 20, 0.01, 400, 0
-CPU_SAMPLE = 640   # rows of A and columns of B the CPU baseline sample keeps
+CPU_SAMPLE = 1000  # rows of A and columns of B the CPU baseline sample keeps
+
+
+def use_small_case():
+    """--small: a 1000 x 2000 x 64 * 2000 x 750 x 64 case (inputs still larger
+    than L2) for profiler captures only; never a bench number."""
+    global N1, N2, N4, CPU_SAMPLE
+    N1, N2, N4, CPU_SAMPLE = 1000, 2000, 750, 200
 
 
 def gemm_flops(n1, cprime, n4, n3):
@@ -68,7 +75,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -170,13 +177,18 @@ def roofline_for(name, ms_avg, cprime, peaks, sm_mhz):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3", "bf16x3"])
+    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3", "bf16x3"])
+    ap.add_argument("--compare", default="fp32",
+                    help="also time this precision (the plain FP32 form) unless 'none'")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--small", action="store_true", help="profiling case, not a bench number")
     args = ap.parse_args()
+    if args.small:
+        use_small_case()
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -192,48 +204,66 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    prec = {"fp32": tp.TP_FP32, "tf32x3": tp.TP_TF32X3, "bf16x3": tp.TP_BF16X3}[args.precision]
+    PREC = {"fp32": tp.TP_FP32, "tf32x3": tp.TP_TF32X3, "bf16x3": tp.TP_BF16X3}
+    prec = PREC[args.precision]
     peaks = load_peaks()
 
     A, B = make_inputs("cuda")
     Z = tp.empty_tensor(N1, N4, N3)
     idx = torch.empty(N2, dtype=torch.int32, device="cuda")
     cnt = torch.empty(1, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    def step():
-        tp.tprod_sampled(A, B, C_SAMPLES, seed=SEED, precision=prec, Z=Z, idx=idx, count=cnt)
+    def timed(pr, Zout):
+        """W warm-up steps, then K steps between CUDA events with per-kernel
+        event timing; returns (ms per step, profile, launches)."""
+        def step():
+            tp.tprod_sampled(A, B, C_SAMPLES, seed=SEED, precision=pr, Z=Zout, idx=idx, count=cnt)
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        n0 = tp.launch_count()
+        tp.profile_start()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        pf = tp.profile_stop()
+        nl = tp.launch_count() - n0
+        if dist:
+            dist.barrier()
+        t_ms = ev0.elapsed_time(ev1) / args.steps
+        if dist:
+            t = torch.tensor([t_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_ms = float(t.item())
+        return t_ms, pf, nl
+
+    compare = None
+    if args.compare != "none" and args.compare != args.precision:
+        Zc = tp.empty_tensor(N1, N4, N3)
+        c_ms, _, _ = timed(PREC[args.compare], Zc)
+        compare = {"precision": args.compare, "ms_per_step": c_ms}
 
     sampler = ClockSampler(gpu_uuid(torch, local_rank))
     sampler.start()
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    cprime = int(cnt.item())
-
-    stream = torch.cuda.current_stream()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    n_launch0 = tp.launch_count()
-    tp.profile_start()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    prof = tp.profile_stop()
-    launches = tp.launch_count() - n_launch0
-    if dist:
-        dist.barrier()
+    ms, prof, launches = timed(prec, Z)
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    cprime = int(cnt.item())
     flops = gemm_flops(N1, cprime, N4, N3)
     value = world * flops / (ms * 1e-3) / 1e12
+    if compare is not None:
+        compare["value"] = world * flops / (compare["ms_per_step"] * 1e-3) / 1e12
+        # agreement of the two GPU forms (each is checked against the float64
+        # oracle in tests/test_gpu_fullsize.py)
+        compare["rel_fro_diff"] = float(torch.linalg.vector_norm((Z - Zc).double()) /
+                                        torch.linalg.vector_norm(Zc.double()))
+        del Zc
 
     # per-kernel breakdown and roofline of the dominant kernel
     kernels = {k: {"ms_per_launch": v[0] / max(1, v[1]), "launches": v[1],
@@ -311,6 +341,7 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": launches, "roofline": roof,
             "kernels": kernels, "cpu_baseline": cpu, "clocks": clocks,
+            "compare": compare,
         }
         print(json.dumps(line))
     if dist:

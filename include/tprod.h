@@ -59,6 +59,7 @@ typedef enum {
 /* Device status bits OR-ed into opts->status. */
 #define TP_DEV_NOCONV     0x1  /* Jacobi sweeps reached opts->max_sweeps */
 #define TP_DEV_BREAKDOWN  0x2  /* CholeskyQR: Gram matrix not positive definite after shift */
+#define TP_DEV_TIMEOUT    0x4  /* a pipeline wait inside a kernel gave up (results invalid) */
 
 typedef enum {
   TP_FP32 = 0,   /* plain FP32 SIMT arithmetic */

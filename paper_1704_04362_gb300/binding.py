@@ -223,15 +223,16 @@ def _opts(op, dims, precision=TP_FP32, status=None, max_sweeps=0):
 
 # ---------------------------------------------------------------- entry points
 
-def tprod(A, B, C=None, precision=TP_FP32):
-    """C = A * B (Def. 2.1 / Algorithm 1)."""
+def tprod(A, B, C=None, precision=TP_FP32, status=None):
+    """C = A * B (Def. 2.1 / Algorithm 1).  ``status``: optional device int32
+    tensor that receives TP_DEV_* bits."""
     n1, n2, n3 = A.shape
     n2b, n4, n3b = B.shape
     if n2b != n2 or n3b != n3:
         raise TprodError(f"tprod: shapes {tuple(A.shape)} and {tuple(B.shape)} do not chain")
     if C is None:
         C = empty_tensor(n1, n4, n3, device=A.device)
-    o = _opts(TP_OP_TPROD, (n1, n2, n4, n3), precision)
+    o = _opts(TP_OP_TPROD, (n1, n2, n4, n3), precision, status)
     rc = lib().tprod(_tensor_arg(A, "A"), _tensor_arg(B, "B"), _tensor_arg(C, "C"),
                      n1, n2, n4, n3, ctypes.byref(o), _stream())
     _check(rc, "tprod")
@@ -239,7 +240,7 @@ def tprod(A, B, C=None, precision=TP_FP32):
 
 
 def tprod_sampled(A, B, c, seed=0, prob_mode=TP_PROB_AB, p_given=None, precision=TP_FP32,
-                  Z=None, idx=None, count=None):
+                  Z=None, idx=None, count=None, status=None):
     """rt-product (Algorithm 2).  Returns (Z, idx int32[n2], count int64[1]);
     idx[:count] are the kept slice indices, ascending."""
     torch = _torch()
@@ -258,7 +259,7 @@ def tprod_sampled(A, B, c, seed=0, prob_mode=TP_PROB_AB, p_given=None, precision
         if p_given is None or p_given.numel() != n2:
             raise TprodError("tprod_sampled: TP_PROB_GIVEN needs p_given of length n2")
         pg = _tensor_arg(p_given, "p_given", torch.float64)
-    o = _opts(TP_OP_TPROD_SAMPLED, (n1, n2, n4, n3), precision)
+    o = _opts(TP_OP_TPROD_SAMPLED, (n1, n2, n4, n3), precision, status)
     rc = lib().tprod_sampled(_tensor_arg(A, "A"), _tensor_arg(B, "B"), _tensor_arg(Z, "Z"),
                              n1, n2, n4, n3, int(c), int(seed) & ((1 << 64) - 1), int(prob_mode),
                              pg, _tensor_arg(idx, "idx", torch.int32),

@@ -6,11 +6,6 @@ size_t workspace_for(int op, const int64_t* d, int nd) {
   (void)op; (void)d; (void)nd;
   return 0;
 }
-int launch_cgemm_tc(const CGemm& g, cudaStream_t st) {
-  (void)g; (void)st;
-  set_error("tensor-core GEMM not built yet");
-  return TP_EUNSUPPORTED;
-}
 }  // namespace tp
 
 using namespace tp;

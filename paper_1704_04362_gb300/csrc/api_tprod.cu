@@ -10,7 +10,11 @@ int launch_cgemm_tc(const CGemm& g, cudaStream_t st);
 
 int launch_cgemm(const CGemm& g, cudaStream_t st) {
   if (g.precision == TP_FP32) return launch_cgemm_simt(g, st);
-  if (g.precision == TP_TF32X3 || g.precision == TP_BF16X3) return launch_cgemm_tc(g, st);
+  if (g.precision == TP_TF32X3) return launch_cgemm_tc(g, st);
+  if (g.precision == TP_BF16X3) {
+    set_error("BF16x3 facewise GEMM is not built yet");
+    return TP_EUNSUPPORTED;
+  }
   set_error("unknown precision %d", g.precision);
   return TP_EINVAL;
 }
@@ -31,20 +35,49 @@ bool dims_ok(std::initializer_list<int64_t> d) {
 
 int opt_precision(const tp_opts* o) { return o ? o->precision : TP_FP32; }
 
-size_t tprod_ws(int64_t n1, int64_t n2, int64_t n4, int64_t n3) {
+inline int64_t pad4(int64_t v) { return (v + 3) / 4 * 4; }
+bool is_tc(int prec) { return prec == TP_TF32X3 || prec == TP_BF16X3; }
+
+// Fourier-domain operand storage of one call: plain planar FP32 for the SIMT
+// GEMM, or the 3xTF32 split (hi/lo planes) with leading dimensions padded to
+// 4 floats for the tensor-core GEMM's TMA tiles.
+struct Planes {
+  float *re, *im, *re_lo, *im_lo;
+};
+size_t planes_bytes(size_t elems, bool tc) { return (tc ? 4 : 2) * ws_bytes(elems, 4); }
+Planes take_planes(Arena& ws, size_t elems, bool tc) {
+  Planes p{};
+  p.re = ws.take<float>(elems);
+  p.im = ws.take<float>(elems);
+  if (tc) {
+    p.re_lo = ws.take<float>(elems);
+    p.im_lo = ws.take<float>(elems);
+  }
+  return p;
+}
+
+// Operand layouts.  SIMT: A_hat_k is n1 x K column-major (leading dimension
+// n1).  Tensor cores: A_hat_k is stored K-major, element (i, kk) at
+// kk + pad4(K)*i.  B_hat_k is K-major in both (leading dimension K, padded to
+// 4 for the tensor cores).
+size_t tprod_ws(int64_t n1, int64_t n2, int64_t n4, int64_t n3, int prec) {
   const size_t h = size_t(half_len(n3));
-  return 2 * ws_bytes(size_t(n1) * n2 * h, 4) + 2 * ws_bytes(size_t(n2) * n4 * h, 4) +
+  const bool tc = is_tc(prec);
+  const int64_t lk = tc ? pad4(n2) : n2;
+  return planes_bytes(size_t(tc ? lk : n2) * n1 * h, tc) + planes_bytes(size_t(lk) * n4 * h, tc) +
          2 * ws_bytes(size_t(n1) * n4 * h, 4);
 }
 
-size_t sampled_ws(int64_t n1, int64_t n2, int64_t n4, int64_t n3) {
+size_t sampled_ws(int64_t n1, int64_t n2, int64_t n4, int64_t n3, int prec) {
   const size_t h = size_t(half_len(n3));
+  const bool tc = is_tc(prec);
+  const int64_t lk = tc ? pad4(n2) : n2;
   size_t part = norms_partial_count(n1, n2, n3, 0);
   const size_t p2 = norms_partial_count(n2, n4, n3, 1);
   if (p2 > part) part = p2;
   return 2 * ws_bytes(size_t(n2), 8) + ws_bytes(part, 8) + ws_bytes(size_t(n2), 4) +
-         ws_bytes(size_t(n2), 4) + ws_bytes(1, 8) + 2 * ws_bytes(size_t(n1) * n2 * h, 4) +
-         2 * ws_bytes(size_t(n2) * n4 * h, 4) + 2 * ws_bytes(size_t(n1) * n4 * h, 4);
+         ws_bytes(size_t(n2), 4) + ws_bytes(1, 8) + planes_bytes(size_t(lk) * n1 * h, tc) +
+         planes_bytes(size_t(lk) * n4 * h, tc) + 2 * ws_bytes(size_t(n1) * n4 * h, 4);
 }
 
 }  // namespace
@@ -66,26 +99,30 @@ int tprod(const float* A, const float* B, float* C, int64_t n1, int64_t n2, int6
     return TP_EINVAL;
   }
   if (n3 > 512) { set_error("tprod: n3 = %lld > 512 not supported", (long long)n3); return TP_EUNSUPPORTED; }
+  const int prec = opt_precision(opts);
+  if (prec < TP_FP32 || prec > TP_BF16X3) { set_error("tprod: unknown precision %d", prec); return TP_EINVAL; }
+  const bool tc = is_tc(prec);
   cudaStream_t st = as_stream(stream);
   Arena ws;
-  int rc = acquire_workspace(opts, tprod_ws(n1, n2, n4, n3), &ws);
+  int rc = acquire_workspace(opts, tprod_ws(n1, n2, n4, n3, prec), &ws);
   if (rc) return rc;
   const int64_t h = half_len(n3);
-  float* Ar = ws.take<float>(size_t(n1) * n2 * h);
-  float* Ai = ws.take<float>(size_t(n1) * n2 * h);
-  float* Br = ws.take<float>(size_t(n2) * n4 * h);
-  float* Bi = ws.take<float>(size_t(n2) * n4 * h);
+  const int64_t lk = tc ? pad4(n2) : n2;          // K leading dimension
+  const int64_t la = tc ? lk : n1;                 // A leading dimension
+  Planes Ah = take_planes(ws, size_t(lk) * n1 * h, tc);
+  Planes Bh = take_planes(ws, size_t(lk) * n4 * h, tc);
   float* Cr = ws.take<float>(size_t(n1) * n4 * h);
   float* Ci = ws.take<float>(size_t(n1) * n4 * h);
 
-  DftGather ga{A, n1 * n2, 1, 1, 0, n1 * n2, nullptr, nullptr, nullptr, 0, n3,
-               Ar, Ai, n1 * n2, n1 * n2};
+  DftGather ga{A, n1, n2, 1, n1, n1 * n2, nullptr, nullptr, nullptr, 0, n3,
+               Ah.re, Ah.im, la, la * (tc ? n1 : n2), Ah.re_lo, Ah.im_lo, tc ? 1 : 0};
   if ((rc = launch_rdft(ga, st))) return rc;
-  DftGather gb{B, n2 * n4, 1, 1, 0, n2 * n4, nullptr, nullptr, nullptr, 0, n3,
-               Br, Bi, n2 * n4, n2 * n4};
+  DftGather gb{B, n2, n4, 1, n2, n2 * n4, nullptr, nullptr, nullptr, 0, n3,
+               Bh.re, Bh.im, lk, lk * n4, Bh.re_lo, Bh.im_lo, 0};
   if ((rc = launch_rdft(gb, st))) return rc;
-  CGemm g{Ar, Ai, Br, Bi, Cr, Ci, n1, n4, n2, nullptr,
-          n1, n2, n1, n1 * n2, n2 * n4, n1 * n4, h, n3, opt_precision(opts)};
+  CGemm g{Ah.re, Ah.im, Bh.re, Bh.im, Cr, Ci, n1, n4, n2, nullptr,
+          la, lk, n1, la * (tc ? n1 : n2), lk * n4, n1 * n4, h, n3, prec,
+          Ah.re_lo, Ah.im_lo, Bh.re_lo, Bh.im_lo, n2, opts ? opts->status : nullptr};
   if ((rc = launch_cgemm(g, st))) return rc;
   return launch_irdft(Cr, Ci, n1 * n4, n1 * n4, n3, C, st);
 }
@@ -108,11 +145,16 @@ int tprod_sampled(const float* A, const float* B, float* Z, int64_t n1, int64_t 
     return TP_ENULL;
   }
   if (n3 > 512) { set_error("tprod_sampled: n3 > 512 not supported"); return TP_EUNSUPPORTED; }
+  const int prec = opt_precision(opts);
+  if (prec < TP_FP32 || prec > TP_BF16X3) { set_error("tprod_sampled: unknown precision %d", prec); return TP_EINVAL; }
+  const bool tc = is_tc(prec);
   cudaStream_t st = as_stream(stream);
   Arena ws;
-  int rc = acquire_workspace(opts, sampled_ws(n1, n2, n4, n3), &ws);
+  int rc = acquire_workspace(opts, sampled_ws(n1, n2, n4, n3, prec), &ws);
   if (rc) return rc;
   const int64_t h = half_len(n3);
+  const int64_t lk = tc ? pad4(n2) : n2;          // K (picked-slice) leading dimension capacity
+  const int64_t la = tc ? lk : n1;
   size_t part_n = norms_partial_count(n1, n2, n3, 0);
   const size_t p2 = norms_partial_count(n2, n4, n3, 1);
   if (p2 > part_n) part_n = p2;
@@ -122,10 +164,8 @@ int tprod_sampled(const float* A, const float* B, float* Z, int64_t n1, int64_t 
   int32_t* idx_ws = ws.take<int32_t>(n2);
   float* scale = ws.take<float>(n2);
   int64_t* cnt_ws = ws.take<int64_t>(1);
-  float* Cr = ws.take<float>(size_t(n1) * n2 * h);
-  float* Ci = ws.take<float>(size_t(n1) * n2 * h);
-  float* Rr = ws.take<float>(size_t(n2) * n4 * h);
-  float* Ri = ws.take<float>(size_t(n2) * n4 * h);
+  Planes Ch = take_planes(ws, size_t(lk) * n1 * h, tc);
+  Planes Rh = take_planes(ws, size_t(lk) * n4 * h, tc);
   float* Zr = ws.take<float>(size_t(n1) * n4 * h);
   float* Zi = ws.take<float>(size_t(n1) * n4 * h);
   int32_t* idx = idx_out ? idx_out : idx_ws;
@@ -140,15 +180,19 @@ int tprod_sampled(const float* A, const float* B, float* Z, int64_t n1, int64_t 
   const double* w = prob_mode == TP_PROB_GIVEN ? p_given : a2;
   if ((rc = launch_draw(w, b2, n2, c, seed, prob_mode, 0u, idx, scale, cnt, nullptr, st))) return rc;
   // S5 + S1: rescaled gathers fused into the forward transforms.
-  // C_hat_k is n1 x c' with leading dimension n1 (capacity n2 columns).
-  DftGather gc{A, n1, n2, 1, n1, n1 * n2, idx, scale, cnt, 2, n3, Cr, Ci, n1, n1 * n2};
+  // C_hat_k is n1 x c' (capacity n2 columns): column-major for the SIMT GEMM,
+  // K-major (picked index contiguous) for the tensor cores.
+  DftGather gc{A, n1, n2, 1, n1, n1 * n2, idx, scale, cnt, 2, n3,
+               Ch.re, Ch.im, la, la * (tc ? n1 : n2), Ch.re_lo, Ch.im_lo, tc ? 1 : 0};
   if ((rc = launch_rdft(gc, st))) return rc;
-  // R_hat_k is c' x n4 with leading dimension n2 (capacity n2 rows).
-  DftGather gr{B, n2, n4, 1, n2, n2 * n4, idx, scale, cnt, 1, n3, Rr, Ri, n2, n2 * n4};
+  // R_hat_k is c' x n4 (leading dimension lk, capacity n2 rows).
+  DftGather gr{B, n2, n4, 1, n2, n2 * n4, idx, scale, cnt, 1, n3,
+               Rh.re, Rh.im, lk, lk * n4, Rh.re_lo, Rh.im_lo, 0};
   if ((rc = launch_rdft(gr, st))) return rc;
   // S6: facewise products with inner dimension c' read on the device
-  CGemm g{Cr, Ci, Rr, Ri, Zr, Zi, n1, n4, 0, cnt,
-          n1, n2, n1, n1 * n2, n2 * n4, n1 * n4, h, n3, opt_precision(opts)};
+  CGemm g{Ch.re, Ch.im, Rh.re, Rh.im, Zr, Zi, n1, n4, 0, cnt,
+          la, lk, n1, la * (tc ? n1 : n2), lk * n4, n1 * n4, h, n3, prec,
+          Ch.re_lo, Ch.im_lo, Rh.re_lo, Rh.im_lo, n2, opts ? opts->status : nullptr};
   if ((rc = launch_cgemm(g, st))) return rc;
   // S7: inverse transform
   return launch_irdft(Zr, Zi, n1 * n4, n1 * n4, n3, Z, st);
@@ -157,7 +201,8 @@ int tprod_sampled(const float* A, const float* B, float* Z, int64_t n1, int64_t 
 int tp_rdft3(const float* X, int64_t rows, int64_t n3, float* Xr, float* Xi, void* stream) {
   if (!X || !Xr || !Xi) { set_error("tp_rdft3: NULL pointer"); return TP_ENULL; }
   if (!dims_ok({rows, n3})) { set_error("tp_rdft3: invalid sizes"); return TP_EINVAL; }
-  DftGather g{X, rows, 1, 1, 0, rows, nullptr, nullptr, nullptr, 0, n3, Xr, Xi, rows, rows};
+  DftGather g{X, rows, 1, 1, 0, rows, nullptr, nullptr, nullptr, 0, n3, Xr, Xi, rows, rows,
+              nullptr, nullptr, 0};
   return launch_rdft(g, as_stream(stream));
 }
 
@@ -192,11 +237,11 @@ int tp_sample_draw(const double* w, const double* w2, int64_t n, int64_t c, uint
 }
 
 size_t tp_workspace_query(int op, const int64_t* d, int nd, const tp_opts* opts) {
-  (void)opts;
   if (!d) return 0;
   switch (op) {
-    case TP_OP_TPROD: return nd >= 4 ? tprod_ws(d[0], d[1], d[2], d[3]) : 0;
-    case TP_OP_TPROD_SAMPLED: return nd >= 4 ? sampled_ws(d[0], d[1], d[2], d[3]) : 0;
+    case TP_OP_TPROD: return nd >= 4 ? tprod_ws(d[0], d[1], d[2], d[3], opt_precision(opts)) : 0;
+    case TP_OP_TPROD_SAMPLED:
+      return nd >= 4 ? sampled_ws(d[0], d[1], d[2], d[3], opt_precision(opts)) : 0;
     case TP_OP_SLICE_NORMS:
       if (nd < 3) return 0;
       {

@@ -1,0 +1,405 @@
+// Facewise complex GEMM of the half spectrum on the tcgen05 tensor cores
+// (Algorithm 1 / Algorithm 2 loop over k: C_hat_k = A_hat_k B_hat_k) with the
+// 3xTF32 split: every float operand x is held as x_hi = tf32(x) (round to
+// nearest) and x_lo = x - x_hi, and a*b is formed as a_hi b_hi + a_hi b_lo +
+// a_lo b_hi with float32 accumulation in tensor memory.  Complex products take
+// four real products (Re = ArBr - AiBi, Im = ArBi + AiBr); the minus sign is
+// the instruction descriptor's negate-A bit.
+//
+// One CTA computes a 128 x 128 output tile of one frequency slice:
+//   warp 0 lane 0   TMA producer: 8 operand planes per K block into a
+//                   3-stage shared-memory ring (mbarrier complete_tx)
+//   warp 1 lane 0   MMA issuer: 12 tcgen05.mma (K = 8) per 8-deep K step into
+//                   three TMEM accumulators: Re(A)Re(B) at columns 0..127,
+//                   Im(A)Im(B) at 128..255, Im at 256..383; tcgen05.commit
+//                   frees a stage and finally signals the epilogue
+//   warps 0-3       epilogue: tcgen05.ld 32x32b, Re = first - second,
+//                   bounds-checked coalesced stores
+// Both operands are K-major (kind::tf32 takes no transposed operand): A
+// planes hold element (m, kk) at kk + lda*m, B planes (kk, n) at kk + ldb*n,
+// read as 64-byte-swizzled 128 x 16 tiles.  Every mbarrier wait is bounded:
+// on timeout the CTA records TP_DEV_TIMEOUT, waits (bounded) for its own
+// copies in flight, frees its tensor memory and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "tp_internal.cuh"
+
+namespace tp {
+namespace {
+
+constexpr int TM = 128, TN = 128, TBK = 16, STAGES = 3, NTHR = 128;
+constexpr uint32_t A_PLANE_BYTES = TM * TBK * 4;        // 8 KB
+constexpr uint32_t B_PLANE_BYTES = TN * TBK * 4;        // 8 KB
+constexpr uint32_t STAGE_BYTES = 4 * A_PLANE_BYTES + 4 * B_PLANE_BYTES;   // 64 KB
+constexpr uint32_t TMEM_COLS = 4 * TN;   // three accumulators used, allocation is a power of 2
+constexpr size_t SMEM_BYTES = size_t(STAGES) * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr long long WAIT_LIMIT = 4000000000LL;           // clock64 ticks (~2 s)
+
+struct TcParams {
+  CUtensorMap a[4];   // A planes: re_hi, re_lo, im_hi, im_lo
+  CUtensorMap b[4];   // B planes: re_hi, re_lo, im_hi, im_lo
+  float* zr;
+  float* zi;
+  int64_t M, N, ldz, sZ;
+  const int64_t* dynK;
+  int64_t K;
+  int64_t h, n3;
+  int32_t* status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > WAIT_LIMIT) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading and
+// stride byte offsets (16-byte units), descriptor version 1, swizzle mode.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo,
+                                              uint32_t layout) {
+  uint64_t d = uint64_t((saddr & 0x3FFFFu) >> 4);
+  d |= uint64_t((lbo >> 4) & 0x3FFFu) << 16;
+  d |= uint64_t((sbo >> 4) & 0x3FFFu) << 32;
+  d |= uint64_t(1) << 46;
+  d |= uint64_t(layout & 7u) << 61;
+  return d;
+}
+constexpr uint32_t LAYOUT_SW64 = 4;
+
+// Instruction descriptor, kind::tf32: F32 accumulate, TF32 A and B, both
+// K-major, N = TN, M = TM.
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(TN >> 3) << 17) |
+                           (uint32_t(TM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(NTHR, 1) cgemm_tc_kernel(const __grid_constant__ TcParams p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + size_t(STAGES) * STAGE_BYTES);
+  // bars[0..S-1] full, bars[S..2S-1] empty, bars[2S] accumulator ready; then TMEM slot
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t f = blockIdx.z;
+  const int64_t m0 = int64_t(blockIdx.x) * TM, n0 = int64_t(blockIdx.y) * TN;
+  const int64_t K = p.dynK ? *p.dynK : p.K;
+  const int nkb = int((K + TBK - 1) / TBK);
+  const bool real_slice = (f == 0) || ((p.n3 % 2 == 0) && f == p.h - 1);
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&bars[s]), 1);
+      mbar_init(smem_u32(&bars[STAGES + s]), 1);
+    }
+    mbar_init(smem_u32(&bars[2 * STAGES]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int i = 0; i < 4; ++i) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&p.a[i])) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&p.b[i])) : "memory");
+    }
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0 && nkb > 0) {
+    // ---------------- TMA producer
+    int issued = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES, r = kb / STAGES;
+      if (r > 0 && !mbar_wait(smem_u32(&bars[STAGES + s]), uint32_t((r - 1) & 1))) {
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      if (*(volatile int*)&abort_flag) break;
+      const uint32_t full = smem_u32(&bars[s]);
+      const uint32_t st = smem_u32(smem + size_t(s) * STAGE_BYTES);
+      mbar_expect_tx(full, STAGE_BYTES);
+      const int k0 = kb * TBK;
+      for (int pl = 0; pl < 4; ++pl) {
+        tma_load_3d(st + pl * A_PLANE_BYTES, &p.a[pl], k0, int(m0), int(f), full);
+        tma_load_3d(st + 4 * A_PLANE_BYTES + pl * B_PLANE_BYTES, &p.b[pl], k0, int(n0), int(f),
+                    full);
+      }
+      issued = kb + 1;
+    }
+    // drain: every issued stage's copies must have landed before the CTA may exit
+    for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb) {
+      const int s = kb % STAGES, r = kb / STAGES;
+      if (!mbar_wait(smem_u32(&bars[s]), uint32_t(r & 1))) break;
+    }
+  } else if (warp == 1 && lane == 0 && nkb > 0) {
+    // ---------------- MMA issuer
+    const uint32_t dp = tmem, dn = tmem + TN, di = tmem + 2 * TN;
+    bool ok = true;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES, r = kb / STAGES;
+      if (!mbar_wait(smem_u32(&bars[s]), uint32_t(r & 1))) {
+        ok = false;
+        break;
+      }
+      if (*(volatile int*)&abort_flag) { ok = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t st = smem_u32(smem + size_t(s) * STAGE_BYTES);
+#pragma unroll
+      for (int sub = 0; sub < TBK / 8; ++sub) {
+        uint64_t a[4], b[4];
+#pragma unroll
+        for (int pl = 0; pl < 4; ++pl) {
+          a[pl] = smem_desc(st + pl * A_PLANE_BYTES + sub * 32, 16, 512, LAYOUT_SW64);
+          b[pl] = smem_desc(st + 4 * A_PLANE_BYTES + pl * B_PLANE_BYTES + sub * 32, 16, 512,
+                            LAYOUT_SW64);
+        }
+        const uint32_t first = (kb == 0 && sub == 0) ? 0u : 1u;
+        // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
+        mma_tf32(dp, a[0], b[0], IDESC, first);
+        mma_tf32(dp, a[0], b[1], IDESC, 1);
+        mma_tf32(dp, a[1], b[0], IDESC, 1);
+        if (!real_slice) {
+          mma_tf32(dn, a[2], b[2], IDESC, first);
+          mma_tf32(dn, a[2], b[3], IDESC, 1);
+          mma_tf32(dn, a[3], b[2], IDESC, 1);
+          mma_tf32(di, a[0], b[2], IDESC, first);
+          mma_tf32(di, a[0], b[3], IDESC, 1);
+          mma_tf32(di, a[1], b[2], IDESC, 1);
+          mma_tf32(di, a[2], b[0], IDESC, 1);
+          mma_tf32(di, a[2], b[1], IDESC, 1);
+          mma_tf32(di, a[3], b[0], IDESC, 1);
+        }
+      }
+      mma_commit(smem_u32(&bars[STAGES + s]));   // stage s free once these MMAs finish
+    }
+    if (!ok) atomicExch(&abort_flag, 1);
+    mma_commit(smem_u32(&bars[2 * STAGES]));      // accumulators final (or abandoned)
+  }
+  __syncwarp();
+
+  // ---------------- epilogue (all four warps)
+  bool have = nkb > 0;
+  if (have) {
+    if (!mbar_wait(smem_u32(&bars[2 * STAGES]), 0u)) {
+      atomicExch(&abort_flag, 1);
+      have = false;
+    }
+  }
+  have = __all_sync(0xffffffffu, have);   // tcgen05.ld below is warp-collective
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int64_t m = m0 + warp * 32 + lane;
+  float* zr = p.zr + f * p.sZ;
+  float* zi = p.zi + f * p.sZ;
+  for (int c0 = 0; c0 < TN; c0 += 32) {
+    uint32_t vp[32], vn[32], vi[32];
+    if (have) {
+      const uint32_t lane_base = uint32_t(warp * 32) << 16;
+      tmem_ld32(tmem + lane_base + uint32_t(c0), vp);
+      if (!real_slice) {
+        tmem_ld32(tmem + lane_base + uint32_t(TN + c0), vn);
+        tmem_ld32(tmem + lane_base + uint32_t(2 * TN + c0), vi);
+      }
+    }
+    if (m < p.M) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int64_t n = n0 + c0 + j;
+        if (n < p.N) {
+          float re = 0.f, im = 0.f;
+          if (have) {
+            re = __uint_as_float(vp[j]);
+            if (!real_slice) {
+              re -= __uint_as_float(vn[j]);
+              im = __uint_as_float(vi[j]);
+            }
+          }
+          zr[m + p.ldz * n] = re;
+          zi[m + p.ldz * n] = im;
+        }
+      }
+    }
+  }
+
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0 && abort_flag && p.status) atomicOr(p.status, TP_DEV_TIMEOUT);
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- host side
+// The driver's tensor-map encoder, looked up through the runtime so that the
+// library has no link-time dependency on libcuda (it loads on GPU-less hosts).
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+int encode_map(CUtensorMap* map, const float* base, uint64_t d0, uint64_t d1, uint64_t d2,
+               uint64_t s1_bytes, uint64_t s2_bytes, uint32_t b0, uint32_t b1,
+               CUtensorMapSwizzle sw) {
+  const cuuint64_t dims[3] = {d0, d1, d2};
+  const cuuint64_t strides[2] = {s1_bytes, s2_bytes};
+  const cuuint32_t box[3] = {b0, b1, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return TP_ECUDA;
+  }
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed with CUresult %d", int(r));
+    return TP_ECUDA;
+  }
+  return TP_OK;
+}
+
+}  // namespace
+
+// Operands for the tensor-core path come as split planes: g.ar/g.ai are the
+// hi planes and g.ar_lo/g.ai_lo (likewise b) the lo planes; A planes have
+// element (m, kk) at kk + lda*m, B planes (kk, n) at kk + ldb*n (lda, ldb
+// multiples of 4); K capacity g.kcap (zero-padded past K up to a multiple of
+// 32 or to the capacity).
+int launch_cgemm_tc(const CGemm& g, cudaStream_t st) {
+  if (g.M == 0 || g.N == 0 || g.h == 0) return TP_OK;
+  if (!g.ar_lo || !g.ai_lo || !g.br_lo || !g.bi_lo) {
+    set_error("cgemm_tc: split operand planes missing");
+    return TP_EINVAL;
+  }
+  if ((g.lda % 4) || (g.ldb % 4) || (g.sA % 4) || (g.sB % 4)) {
+    set_error("cgemm_tc: leading dimensions must be multiples of 4 floats");
+    return TP_EALIGN;
+  }
+  if (g.M > 0x7fffffff || g.N > 0x7fffffff || g.kcap > 0x7fffffff || g.h > 65535) {
+    set_error("cgemm_tc: sizes too large for one launch");
+    return TP_EUNSUPPORTED;
+  }
+  TcParams p;
+  const float* ap[4] = {g.ar, g.ar_lo, g.ai, g.ai_lo};
+  const float* bp[4] = {g.br, g.br_lo, g.bi, g.bi_lo};
+  for (int i = 0; i < 4; ++i) {
+    if (!aligned16(ap[i]) || !aligned16(bp[i])) {
+      set_error("cgemm_tc: operand planes must be 16-byte aligned");
+      return TP_EALIGN;
+    }
+    int rc = encode_map(&p.a[i], ap[i], uint64_t(g.kcap), uint64_t(g.M), uint64_t(g.h),
+                        uint64_t(g.lda) * 4, uint64_t(g.sA) * 4, TBK, TM,
+                        CU_TENSOR_MAP_SWIZZLE_64B);
+    if (rc) return rc;
+    rc = encode_map(&p.b[i], bp[i], uint64_t(g.kcap), uint64_t(g.N), uint64_t(g.h),
+                    uint64_t(g.ldb) * 4, uint64_t(g.sB) * 4, TBK, TN, CU_TENSOR_MAP_SWIZZLE_64B);
+    if (rc) return rc;
+  }
+  p.zr = g.cr;
+  p.zi = g.ci;
+  p.M = g.M;
+  p.N = g.N;
+  p.ldz = g.ldc;
+  p.sZ = g.sC;
+  p.dynK = g.dynK;
+  p.K = g.K;
+  p.h = g.h;
+  p.n3 = g.n3;
+  p.status = g.status;
+  cudaFuncSetAttribute(cgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       int(SMEM_BYTES));
+  const dim3 grid(unsigned((g.M + TM - 1) / TM), unsigned((g.N + TN - 1) / TN), unsigned(g.h));
+  {
+    KernelScope ks("cgemm_tc", st);
+    cgemm_tc_kernel<<<grid, NTHR, SMEM_BYTES, st>>>(p);
+  }
+  return launch_status("cgemm_tc_kernel");
+}
+
+}  // namespace tp

@@ -62,6 +62,9 @@ struct DftGather {
   float* out_re;
   float* out_im;
   int64_t out_ld, out_slice;
+  float* out_re_lo;            // non-null: write the 3xTF32 split, hi to out_re/out_im
+  float* out_im_lo;            //   (tf32 round-to-nearest) and lo = x - hi here
+  int out_transposed;          // 1: element (r, c) of slice k at k*out_slice + c + out_ld*r
 };
 int launch_rdft(const DftGather& g, cudaStream_t st);
 
@@ -83,6 +86,11 @@ struct CGemm {
   int64_t lda, ldb, ldc, sA, sB, sC;
   int64_t h, n3;
   int precision;
+  // tensor-core path only: lo planes of the 3xTF32 split, K capacity of the
+  // operand planes, device status word (may be null)
+  const float *ar_lo, *ai_lo, *br_lo, *bi_lo;
+  int64_t kcap;
+  int32_t* status;
 };
 int launch_cgemm(const CGemm& g, cudaStream_t st);
 

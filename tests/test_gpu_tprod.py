@@ -47,12 +47,23 @@ SHAPES = [
 ]
 
 
+PRECISIONS = [tp.TP_FP32, tp.TP_TF32X3]
+
+
+def status_word():
+    import torch
+    return torch.zeros(1, dtype=torch.int32, device="cuda")
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
 @pytest.mark.parametrize("n1,n2,n4,n3", SHAPES)
-def test_tprod_matches_oracle(n1, n2, n4, n3):
+def test_tprod_matches_oracle(n1, n2, n4, n3, prec):
     A = synth.iid_normal((n1, n2, n3), seed=1)
     B = synth.iid_normal((n2, n4, n3), seed=2)
-    C = tp.tprod(dev(A), dev(B))
+    st = status_word()
+    C = tp.tprod(dev(A), dev(B), precision=prec, status=st)
     ref = tensor_ref.tprod(A.astype(np.float64), B.astype(np.float64))
+    assert int(st.item()) == 0
     assert rel_fro(to_np(C), ref) < TOL_FP32
 
 
@@ -106,13 +117,18 @@ def test_draw_edge_cases():
     assert torch.all(scale[:9] == 1)
 
 
+@pytest.mark.parametrize("prec", PRECISIONS)
 @pytest.mark.parametrize("mode", [tp.TP_PROB_AB, tp.TP_PROB_A2])
 @pytest.mark.parametrize("n1,n2,n4,n3,c", [(64, 48, 32, 16, 12), (50, 300, 41, 7, 60),
-                                           (33, 130, 20, 64, 400), (20, 9, 5, 4, 1)])
-def test_tprod_sampled_matches_oracle(mode, n1, n2, n4, n3, c):
+                                           (33, 130, 20, 64, 400), (20, 9, 5, 4, 1),
+                                           (260, 500, 300, 8, 100)])
+def test_tprod_sampled_matches_oracle(mode, n1, n2, n4, n3, c, prec):
     A = synth.lowrank_np(n1, n2, n3, 4, seed=6, noise=0.01)
     B = synth.lowrank_np(n2, n4, n3, 4, seed=7, noise=0.01)
-    Z, idx, count = tp.tprod_sampled(dev(A), dev(B), c, seed=123, prob_mode=mode)
+    st = status_word()
+    Z, idx, count = tp.tprod_sampled(dev(A), dev(B), c, seed=123, prob_mode=mode,
+                                     precision=prec, status=st)
+    assert int(st.item()) == 0
     cnt = int(count.item())
     Zref, ref_idx, q = sampling_ref.tprod_sampled(A, B, c, 123, mode=mode)
     # index draws: the float64 probabilities agree to rounding, so the picks agree
