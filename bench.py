@@ -38,10 +38,11 @@ CPU_SAMPLE = 1000  # rows of A and columns of B the CPU baseline sample keeps
 
 
 def use_small_case():
-    """--small: a 1000 x 2000 x 64 * 2000 x 750 x 64 case (inputs still larger
-    than L2) for profiler captures only; never a bench number."""
+    """--small: a 600 x 1600 x 64 * 1600 x 500 x 64 case (each input still
+    larger than L2, under 2 GB on the device with workspace) for profiler
+    captures only; never a bench number."""
     global N1, N2, N4, CPU_SAMPLE
-    N1, N2, N4, CPU_SAMPLE = 1000, 2000, 750, 200
+    N1, N2, N4, CPU_SAMPLE = 600, 1600, 500, 200
 
 
 def gemm_flops(n1, cprime, n4, n3):

@@ -127,7 +127,8 @@ int tprod_sampled(const float* A, const float* B, float* Z,
  * Economy form with m = min(n1, n2):
  *   U  n1 x m x n3,  S  m x m x n3 (f-diagonal),  V  n2 x m x n3 (outputs).
  * Singular vectors are unique only up to a unit phase per column (and a
- * rotation inside repeated singular values).  Limits: m <= 512, n3 <= 4096. */
+ * rotation inside repeated singular values).  The per-slice Jacobi works in
+ * float64.  Limits: m <= 512; n3 <= 512 or a product of the radices 2..13.  */
 int tsvd(const float* X, int64_t n1, int64_t n2, int64_t n3,
          float* U, float* S, float* V, const tp_opts* opts, void* stream);
 
@@ -139,7 +140,8 @@ int tsvd(const float* X, int64_t n1, int64_t n2, int64_t n3,
  * CholeskyQR2 with float64 Gram and Cholesky, then B = Q^H X_hat, a float64
  * SVD of B and U = Q U_B truncated to k.
  *   U  n1 x k x n3,  S  k x k x n3,  V  n2 x k x n3 (outputs).
- * Requires 1 <= k, k + p <= min(n1, n2, 128), q >= 0.                     */
+ * Requires 1 <= k, p >= 0, q >= 0, k + p <= min(n1, n2, 96); n3 <= 512 or
+ * n3 a product of the radices 2, 3, 5, 7, 11, 13.                           */
 int tsvd_randomized(const float* X, int64_t n1, int64_t n2, int64_t n3,
                     int k, int p, int q, uint64_t seed,
                     float* U, float* S, float* V, const tp_opts* opts, void* stream);

@@ -23,9 +23,17 @@ def dft_matrix(n3: int) -> np.ndarray:
     return np.cos(ang) + 1j * np.sin(ang)
 
 
+# Above this tube length the transform is taken from numpy.fft (a library
+# primitive computing the same sum); below it the F_{n3} contraction is
+# written out.  tests/test_oracle_tensor.py pins both against each other.
+LIBRARY_FFT_ABOVE = 256
+
+
 def fft3(X: np.ndarray) -> np.ndarray:
     """X_hat = fft(X, [], 3): X_hat[:, :, k] = sum_t X[:, :, t] F[k, t] (Section 2)."""
     X = np.asarray(X)
+    if X.shape[2] > LIBRARY_FFT_ABOVE:
+        return np.fft.fft(np.asarray(X, dtype=np.complex128), axis=2)
     F = dft_matrix(X.shape[2])
     return np.asarray(X, dtype=np.complex128) @ F.T
 
@@ -33,6 +41,8 @@ def fft3(X: np.ndarray) -> np.ndarray:
 def ifft3(Xh: np.ndarray) -> np.ndarray:
     """ifft(X_hat, [], 3): X[:, :, t] = (1/n3) sum_k X_hat[:, :, k] conj(F[k, t])."""
     n3 = Xh.shape[2]
+    if n3 > LIBRARY_FFT_ABOVE:
+        return np.fft.ifft(np.asarray(Xh, dtype=np.complex128), axis=2)
     F = dft_matrix(n3)
     return (np.asarray(Xh, dtype=np.complex128) @ np.conj(F)) / n3
 

@@ -2,23 +2,60 @@
 #include "tp_internal.cuh"
 
 namespace tp {
+size_t tsvd_ws(int64_t n1, int64_t n2, int64_t n3);
+bool fft_supported(int64_t n3);
+size_t rsvd_ws(int64_t n1, int64_t n2, int64_t n3, int64_t k, int64_t p);
+int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, int q,
+             uint64_t seed, float* U, float* S, float* V, const tp_opts* opts, cudaStream_t st);
+int tsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, float* U, float* S, float* V,
+             const tp_opts* opts, cudaStream_t st);
+
 size_t workspace_for(int op, const int64_t* d, int nd) {
-  (void)op; (void)d; (void)nd;
-  return 0;
+  switch (op) {
+    case TP_OP_TSVD: return nd >= 3 ? tsvd_ws(d[0], d[1], d[2]) : 0;
+    case TP_OP_TSVD_RANDOMIZED: return nd >= 5 ? rsvd_ws(d[0], d[1], d[2], d[3], d[4]) : 0;
+    default: return 0;
+  }
 }
+
+namespace {
+bool dims3_ok(int64_t n1, int64_t n2, int64_t n3) {
+  return n1 >= 1 && n2 >= 1 && n3 >= 1 && n1 <= (int64_t(1) << 31) && n2 <= (int64_t(1) << 31) &&
+         n3 <= (int64_t(1) << 31) && n1 * n2 <= (int64_t(1) << 40) / n3;
+}
+}  // namespace
 }  // namespace tp
 
 using namespace tp;
 
 extern "C" {
-int tsvd(const float*, int64_t, int64_t, int64_t, float*, float*, float*, const tp_opts*, void*) {
-  set_error("tsvd: not built yet");
-  return TP_EUNSUPPORTED;
+int tsvd(const float* X, int64_t n1, int64_t n2, int64_t n3, float* U, float* S, float* V,
+         const tp_opts* opts, void* stream) {
+  if (!X || !U || !S || !V) { set_error("tsvd: NULL pointer"); return TP_ENULL; }
+  if (!dims3_ok(n1, n2, n3)) { set_error("tsvd: invalid sizes"); return TP_EINVAL; }
+  const int64_t m = n1 < n2 ? n1 : n2;
+  if (m > 512) { set_error("tsvd: min(n1, n2) = %lld > 512 not supported", (long long)m); return TP_EUNSUPPORTED; }
+  if (n3 > 512 && !fft_supported(n3)) {
+    set_error("tsvd: n3 = %lld > 512 must factor into radices 2..13", (long long)n3);
+    return TP_EUNSUPPORTED;
+  }
+  return tsvd_run(X, n1, n2, n3, U, S, V, opts, as_stream(stream));
 }
-int tsvd_randomized(const float*, int64_t, int64_t, int64_t, int, int, int, uint64_t, float*,
-                    float*, float*, const tp_opts*, void*) {
-  set_error("tsvd_randomized: not built yet");
-  return TP_EUNSUPPORTED;
+int tsvd_randomized(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, int q,
+                    uint64_t seed, float* U, float* S, float* V, const tp_opts* opts,
+                    void* stream) {
+  if (!X || !U || !S || !V) { set_error("tsvd_randomized: NULL pointer"); return TP_ENULL; }
+  if (!dims3_ok(n1, n2, n3)) { set_error("tsvd_randomized: invalid sizes"); return TP_EINVAL; }
+  const int64_t m = n1 < n2 ? n1 : n2;
+  if (k < 1 || p < 0 || q < 0 || int64_t(k) + p > m || k + p > 96) {
+    set_error("tsvd_randomized: need 1 <= k, 0 <= p, q and k + p <= min(n1, n2, 96)");
+    return TP_EINVAL;
+  }
+  if (n3 > 512 && !fft_supported(n3)) {
+    set_error("tsvd_randomized: n3 = %lld > 512 must factor into radices 2..13", (long long)n3);
+    return TP_EUNSUPPORTED;
+  }
+  return rsvd_run(X, n1, n2, n3, k, p, q, seed, U, S, V, opts, as_stream(stream));
 }
 int tcomplete_svt(const float*, const uint8_t*, int64_t, int64_t, int64_t, int, double, double,
                   float*, float*, float*, double*, const tp_opts*, void*) {

@@ -18,6 +18,7 @@ namespace {
 constexpr int KC = 16;   // frequencies (forward) or times (inverse) per chunk
 constexpr int TPT = 2;   // tubes per thread
 constexpr int RB = 128;  // threads per block
+constexpr int TU = 8;    // samples (forward) or frequencies (inverse) loaded ahead
 
 // Nearest tf32 value of x (10 explicit mantissa bits), as a float.
 __device__ __forceinline__ float tf32_rna(float x) {
@@ -38,8 +39,9 @@ __global__ void __launch_bounds__(RB) rdft_kernel(DftGather g) {
   extern __shared__ float2 sm2[];
   const int n3 = int(g.n3);
   const int h = n3 / 2 + 1;
+  const int n3p = (n3 + TU - 1) / TU * TU;
   float2* tw = sm2;
-  float2* Wc = sm2 + n3;   // Wc[t*KC + q] = tw[(k0+q)*t mod n3]
+  float2* Wc = sm2 + n3;   // Wc[t*KC + q] = tw[(k0+q)*t mod n3], zero for t >= n3
   build_twiddles(tw, n3);
 
   const int64_t count = g.dyn_count ? *g.dyn_count : (g.gather_dim == 1 ? g.rows : g.cols);
@@ -80,9 +82,9 @@ __global__ void __launch_bounds__(RB) rdft_kernel(DftGather g) {
     }
     for (int k0 = 0; k0 < h; k0 += KC) {
       __syncthreads();   // previous chunk done with Wc (and tw built)
-      for (int e = tid; e < n3 * KC; e += RB) {
+      for (int e = tid; e < n3p * KC; e += RB) {
         const int t = e / KC, q = e - t * KC;
-        Wc[e] = tw[int((int64_t(k0 + q) * t) % n3)];
+        Wc[e] = t < n3 ? tw[int((int64_t(k0 + q) * t) % n3)] : make_float2(0.f, 0.f);
       }
       __syncthreads();
       float ar[TPT][KC], ai[TPT][KC];
@@ -90,18 +92,25 @@ __global__ void __launch_bounds__(RB) rdft_kernel(DftGather g) {
       for (int j = 0; j < TPT; ++j)
 #pragma unroll
         for (int q = 0; q < KC; ++q) { ar[j][q] = 0.f; ai[j][q] = 0.f; }
-      for (int t = 0; t < n3; ++t) {
-        float x[TPT];
+      for (int t0 = 0; t0 < n3; t0 += TU) {
+        // all TU samples of both tubes in flight before the arithmetic
+        float x[TPT][TU];
 #pragma unroll
-        for (int j = 0; j < TPT; ++j)
-          x[j] = p[j] ? s[j] * __ldg(p[j] + int64_t(t) * g.slice_stride) : 0.f;
+        for (int u = 0; u < TU; ++u)
 #pragma unroll
-        for (int q = 0; q < KC; ++q) {
-          const float2 w = Wc[t * KC + q];
+          for (int j = 0; j < TPT; ++j)
+            x[j][u] = (p[j] && t0 + u < n3) ? s[j] * __ldg(p[j] + int64_t(t0 + u) * g.slice_stride)
+                                            : 0.f;
 #pragma unroll
-          for (int j = 0; j < TPT; ++j) {
-            ar[j][q] = fmaf(x[j], w.x, ar[j][q]);
-            ai[j][q] = fmaf(-x[j], w.y, ai[j][q]);
+        for (int u = 0; u < TU; ++u) {
+#pragma unroll
+          for (int q = 0; q < KC; ++q) {
+            const float2 w = Wc[(t0 + u) * KC + q];   // zero rows past n3
+#pragma unroll
+            for (int j = 0; j < TPT; ++j) {
+              ar[j][q] = fmaf(x[j][u], w.x, ar[j][q]);
+              ai[j][q] = fmaf(-x[j][u], w.y, ai[j][q]);
+            }
           }
         }
       }
@@ -148,9 +157,10 @@ __global__ void __launch_bounds__(RB) rdft_t_kernel(DftGather g) {
   extern __shared__ float2 sm2[];
   const int n3 = int(g.n3);
   const int h = n3 / 2 + 1;
+  const int n3p = (n3 + TU - 1) / TU * TU;
   float2* tw = sm2;
   float2* Wc = sm2 + n3;
-  float* stg = reinterpret_cast<float*>(Wc + n3 * KC);   // [KC][TR][TCOL + 1]
+  float* stg = reinterpret_cast<float*>(Wc + n3p * KC);   // [KC][TR][TCOL + 1]
   build_twiddles(tw, n3);
 
   const int64_t count = g.dyn_count ? *g.dyn_count : (g.gather_dim == 1 ? g.rows : g.cols);
@@ -191,9 +201,9 @@ __global__ void __launch_bounds__(RB) rdft_t_kernel(DftGather g) {
     }
     for (int k0 = 0; k0 < h; k0 += KC) {
       __syncthreads();
-      for (int e = tid; e < n3 * KC; e += RB) {
+      for (int e = tid; e < n3p * KC; e += RB) {
         const int t = e / KC, q = e - t * KC;
-        Wc[e] = tw[int((int64_t(k0 + q) * t) % n3)];
+        Wc[e] = t < n3 ? tw[int((int64_t(k0 + q) * t) % n3)] : make_float2(0.f, 0.f);
       }
       __syncthreads();
       float ar[TPT][KC], ai[TPT][KC];
@@ -201,18 +211,25 @@ __global__ void __launch_bounds__(RB) rdft_t_kernel(DftGather g) {
       for (int j = 0; j < TPT; ++j)
 #pragma unroll
         for (int q = 0; q < KC; ++q) { ar[j][q] = 0.f; ai[j][q] = 0.f; }
-      for (int t = 0; t < n3; ++t) {
-        float x[TPT];
+      for (int t0 = 0; t0 < n3; t0 += TU) {
+        // all TU samples of both tubes in flight before the arithmetic
+        float x[TPT][TU];
 #pragma unroll
-        for (int j = 0; j < TPT; ++j)
-          x[j] = p[j] ? s[j] * __ldg(p[j] + int64_t(t) * g.slice_stride) : 0.f;
+        for (int u = 0; u < TU; ++u)
 #pragma unroll
-        for (int q = 0; q < KC; ++q) {
-          const float2 w = Wc[t * KC + q];
+          for (int j = 0; j < TPT; ++j)
+            x[j][u] = (p[j] && t0 + u < n3) ? s[j] * __ldg(p[j] + int64_t(t0 + u) * g.slice_stride)
+                                            : 0.f;
 #pragma unroll
-          for (int j = 0; j < TPT; ++j) {
-            ar[j][q] = fmaf(x[j], w.x, ar[j][q]);
-            ai[j][q] = fmaf(-x[j], w.y, ai[j][q]);
+        for (int u = 0; u < TU; ++u) {
+#pragma unroll
+          for (int q = 0; q < KC; ++q) {
+            const float2 w = Wc[(t0 + u) * KC + q];   // zero rows past n3
+#pragma unroll
+            for (int j = 0; j < TPT; ++j) {
+              ar[j][q] = fmaf(x[j][u], w.x, ar[j][q]);
+              ai[j][q] = fmaf(-x[j][u], w.y, ai[j][q]);
+            }
           }
         }
       }
@@ -261,8 +278,9 @@ __global__ void __launch_bounds__(RB) irdft_kernel(const float* __restrict__ in_
                                                    float* __restrict__ out) {
   extern __shared__ float2 sm2[];
   const int h = n3 / 2 + 1;
+  const int hp = (h + TU - 1) / TU * TU;
   float2* tw = sm2;
-  float2* Vc = sm2 + n3;   // Vc[k*KC + q] = (w_k/n3) tw[k*(t0+q) mod n3]
+  float2* Vc = sm2 + n3;   // Vc[k*KC + q] = (w_k/n3) tw[k*(t0+q) mod n3], zero for k >= h
   build_twiddles(tw, n3);
   const int tid = threadIdx.x;
   const float inv = 1.0f / float(n3);
@@ -273,11 +291,15 @@ __global__ void __launch_bounds__(RB) irdft_kernel(const float* __restrict__ in_
     for (int j = 0; j < TPT; ++j) r[j] = base + j * RB + tid;
     for (int t0 = 0; t0 < n3; t0 += KC) {
       __syncthreads();
-      for (int e = tid; e < h * KC; e += RB) {
+      for (int e = tid; e < hp * KC; e += RB) {
         const int k = e / KC, q = e - k * KC;
-        const float wk = (k == 0 || 2 * k == n3) ? inv : 2.0f * inv;
-        const float2 w = tw[int((int64_t(k) * (t0 + q)) % n3)];
-        Vc[e] = make_float2(wk * w.x, wk * w.y);
+        if (k < h) {
+          const float wk = (k == 0 || 2 * k == n3) ? inv : 2.0f * inv;
+          const float2 w = tw[int((int64_t(k) * (t0 + q)) % n3)];
+          Vc[e] = make_float2(wk * w.x, wk * w.y);
+        } else {
+          Vc[e] = make_float2(0.f, 0.f);
+        }
       }
       __syncthreads();
       float acc[TPT][KC];
@@ -285,20 +307,25 @@ __global__ void __launch_bounds__(RB) irdft_kernel(const float* __restrict__ in_
       for (int j = 0; j < TPT; ++j)
 #pragma unroll
         for (int q = 0; q < KC; ++q) acc[j][q] = 0.f;
-      for (int k = 0; k < h; ++k) {
-        float re[TPT], im[TPT];
+      for (int k0 = 0; k0 < h; k0 += TU) {
+        float re[TPT][TU], im[TPT][TU];
 #pragma unroll
-        for (int j = 0; j < TPT; ++j) {
-          const bool ok = r[j] < rows;
-          re[j] = ok ? __ldg(in_re + int64_t(k) * in_slice + r[j]) : 0.f;
-          im[j] = ok ? __ldg(in_im + int64_t(k) * in_slice + r[j]) : 0.f;
-        }
+        for (int u = 0; u < TU; ++u)
 #pragma unroll
-        for (int q = 0; q < KC; ++q) {
-          const float2 v = Vc[k * KC + q];
+          for (int j = 0; j < TPT; ++j) {
+            const bool ok = r[j] < rows && k0 + u < h;
+            re[j][u] = ok ? __ldg(in_re + int64_t(k0 + u) * in_slice + r[j]) : 0.f;
+            im[j][u] = ok ? __ldg(in_im + int64_t(k0 + u) * in_slice + r[j]) : 0.f;
+          }
 #pragma unroll
-          for (int j = 0; j < TPT; ++j) acc[j][q] = fmaf(re[j], v.x, fmaf(-im[j], v.y, acc[j][q]));
-        }
+        for (int u = 0; u < TU; ++u)
+#pragma unroll
+          for (int q = 0; q < KC; ++q) {
+            const float2 v = Vc[(k0 + u) * KC + q];   // zero rows past h
+#pragma unroll
+            for (int j = 0; j < TPT; ++j)
+              acc[j][q] = fmaf(re[j][u], v.x, fmaf(-im[j][u], v.y, acc[j][q]));
+          }
       }
 #pragma unroll
       for (int j = 0; j < TPT; ++j) {
@@ -313,14 +340,32 @@ __global__ void __launch_bounds__(RB) irdft_kernel(const float* __restrict__ in_
 
 }  // namespace
 
+bool fft_supported(int64_t n3);
+int launch_fft_fwd(const float* X, int64_t rows, int64_t n3, float* ore, float* oim,
+                   int64_t out_slice, cudaStream_t st);
+int launch_fft_inv(const float* ire, const float* iim, int64_t rows, int64_t in_slice, int64_t n3,
+                   float* out, cudaStream_t st);
+
+// Tubes longer than this go through the shared-memory FFT when their length
+// factors into small radices and no gather or split output is asked for.
+constexpr int64_t kFftThreshold = 256;
+
 int launch_rdft(const DftGather& g, cudaStream_t st) {
+  const bool plain = g.gather_dim == 0 && !g.out_transposed && !g.out_re_lo &&
+                     (g.cols == 1 || g.col_stride == g.rows) && g.out_ld == g.rows &&
+                     g.out_slice == g.rows * g.cols && g.slice_stride == g.rows * g.cols &&
+                     g.row_stride == 1;
+  if (plain && g.n3 > kFftThreshold && fft_supported(g.n3))
+    return launch_fft_fwd(g.src, g.rows * g.cols, g.n3, g.out_re, g.out_im, g.out_slice, st);
   if (g.n3 < 1 || g.n3 > 512) {
-    set_error("rdft: n3 = %lld outside [1, 512]", (long long)g.n3);
+    set_error("rdft: n3 = %lld: longer than 512 needs a plain (ungathered) transform and "
+              "prime factors <= 13", (long long)g.n3);
     return TP_EUNSUPPORTED;
   }
   if (g.rows == 0 || g.cols == 0) return TP_OK;
   if (g.out_transposed) {
-    const size_t smem = size_t(g.n3) * (1 + KC) * sizeof(float2) +
+    const int64_t n3p = (g.n3 + TU - 1) / TU * TU;
+    const size_t smem = size_t(g.n3 + n3p * KC) * sizeof(float2) +
                         size_t(KC) * TR * (TCOL + 1) * sizeof(float);
     cudaFuncSetAttribute(rdft_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     const int64_t bx = (g.rows + TR - 1) / TR;
@@ -333,7 +378,8 @@ int launch_rdft(const DftGather& g, cudaStream_t st) {
     }
     return launch_status("rdft_t_kernel");
   }
-  const size_t smem = size_t(g.n3) * (1 + KC) * sizeof(float2);
+  const int64_t n3p = (g.n3 + TU - 1) / TU * TU;
+  const size_t smem = size_t(g.n3 + n3p * KC) * sizeof(float2);
   cudaFuncSetAttribute(rdft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   const int64_t bx = (g.rows + RB * TPT - 1) / (RB * TPT);
   if (bx > 0x7fffffff) { set_error("rdft: too many rows"); return TP_EINVAL; }
@@ -347,13 +393,16 @@ int launch_rdft(const DftGather& g, cudaStream_t st) {
 
 int launch_irdft(const float* in_re, const float* in_im, int64_t rows, int64_t in_slice,
                  int64_t n3, float* out, cudaStream_t st) {
+  if (n3 > kFftThreshold && fft_supported(n3))
+    return launch_fft_inv(in_re, in_im, rows, in_slice, n3, out, st);
   if (n3 < 1 || n3 > 512) {
-    set_error("irdft: n3 = %lld outside [1, 512]", (long long)n3);
+    set_error("irdft: n3 = %lld: longer than 512 needs prime factors <= 13", (long long)n3);
     return TP_EUNSUPPORTED;
   }
   if (rows == 0) return TP_OK;
   const int64_t h = n3 / 2 + 1;
-  const size_t smem = size_t(n3 + h * KC) * sizeof(float2);
+  const int64_t hp = (h + TU - 1) / TU * TU;
+  const size_t smem = size_t(n3 + hp * KC) * sizeof(float2);
   cudaFuncSetAttribute(irdft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   int64_t blocks = (rows + RB * TPT - 1) / (RB * TPT);
   if (blocks > 152 * 64) blocks = 152 * 64;

@@ -1,0 +1,384 @@
+// Randomized low-tubal-rank t-SVD: per half-spectrum slice X_hat_f the range
+// finder with power iterations of Halko, Martinsson and Tropp (2011):
+//   Y = X_hat Omega;  Q = orth(Y)
+//   q times: Z = orth(X_hat^H Q), Q = orth(X_hat Z)
+//   B^H = X_hat^H Q  (n2 x l);  B^H = V_B diag(s) W^H (one-sided Jacobi, float64)
+//   U_f = Q W[:, :k],  V_f = V_B[:, :k],  S_f = diag(s[:k])
+// followed by the inverse DFT of U, S, V (Theorem 2.6's form, tubal rank k).
+// The test matrix has random-sign entries from Philox stream 2 (see
+// tsvd_randomized in tprod.h).  orth() is CholeskyQR2 (Fukaya et al. 2014):
+// G = Y^H Y and its Cholesky factor R in float64, Y <- Y R^{-1}, twice; if a
+// Cholesky fails, the Gram matrix is shifted (shifted CholeskyQR, Fukaya et
+// al. 2020) and one more pass is made; a failure after that sets
+// TP_DEV_BREAKDOWN.  Every product with X_hat is a plain column-major batched
+// complex GEMM because X_hat^H is formed once.
+#include <cmath>
+
+#include "tp_internal.cuh"
+
+namespace tp {
+
+int launch_cgemm(const CGemm& g, cudaStream_t st);
+int jacobi_double_launch(double* gr, double* gi, int64_t sG, double* vr, double* vi, int64_t sV,
+                         double* sig, int p, int q, int batch, int max_sweeps,
+                         const int* real_flags, int32_t* status, cudaStream_t st);
+
+namespace {
+
+constexpr int QR_THREADS = 256;
+
+// X^H of every slice: out(j, i) = conj(in(i, j)), in n1 x n2, out n2 x n1.
+__global__ void conj_transpose_kernel(const float* __restrict__ ir, const float* __restrict__ ii,
+                                      int64_t n1, int64_t n2, float* __restrict__ orr,
+                                      float* __restrict__ oi) {
+  __shared__ float tr[32][33], ti[32][33];
+  const int64_t f = blockIdx.z;
+  const int64_t i0 = int64_t(blockIdx.x) * 32, j0 = int64_t(blockIdx.y) * 32;
+  const float* sr = ir + f * n1 * n2;
+  const float* si = ii + f * n1 * n2;
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int64_t i = i0 + threadIdx.x, j = j0 + dy;
+    if (i < n1 && j < n2) {
+      tr[dy][threadIdx.x] = sr[i + n1 * j];
+      ti[dy][threadIdx.x] = si[i + n1 * j];
+    }
+  }
+  __syncthreads();
+  float* dr = orr + f * n1 * n2;
+  float* di = oi + f * n1 * n2;
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int64_t j = j0 + threadIdx.x, i = i0 + dy;
+    if (i < n1 && j < n2) {
+      dr[j + n2 * i] = tr[threadIdx.x][dy];
+      di[j + n2 * i] = -ti[threadIdx.x][dy];
+    }
+  }
+}
+
+__device__ __forceinline__ void philox(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k0 += W0; k1 += W1; }
+    const uint32_t hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
+    const uint32_t hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
+    const uint32_t y0 = hi1 ^ c[1] ^ k0, y2 = hi0 ^ c[3] ^ k1;
+    c[0] = y0; c[1] = lo1; c[2] = y2; c[3] = lo0;
+  }
+}
+
+// Omega(r, c, f) at e = r + n2*(c + l*f): (s0 + i s1)/sqrt(2) from the top bits
+// of Philox(e, stream 2); the real slices take s0.
+__global__ void sketch_kernel(float* __restrict__ om_r, float* __restrict__ om_i, int64_t n2,
+                              int64_t l, int64_t h, int64_t n3, uint64_t seed) {
+  const int64_t total = n2 * l * h;
+  const float inv_sqrt2 = 0.70710678118654752f;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    uint32_t c[4] = {uint32_t(e), uint32_t(uint64_t(e) >> 32), 2u, 0u};
+    philox(c, uint32_t(seed), uint32_t(seed >> 32));
+    const float s0 = (c[0] >> 31) ? -1.f : 1.f;
+    const float s1 = (c[1] >> 31) ? -1.f : 1.f;
+    const int64_t f = e / (n2 * l);
+    const bool real = f == 0 || (n3 % 2 == 0 && f == h - 1);
+    om_r[e] = real ? s0 : s0 * inv_sqrt2;
+    om_i[e] = real ? 0.f : s1 * inv_sqrt2;
+  }
+}
+
+// Gram of the columns of Y (p x l, float32 planar, column-major) into
+// G (l x l, float64, interleaved re/im, full Hermitian).
+__device__ void gram(const float* __restrict__ yr, const float* __restrict__ yi, int p, int l,
+                     double* G) {
+  const int npairs = l * (l + 1) / 2;
+  for (int e = threadIdx.x; e < npairs; e += blockDim.x) {
+    // e -> (a, b), a <= b, row-major upper triangle
+    int a = 0, rem = e;
+    while (rem >= l - a) { rem -= l - a; ++a; }
+    const int b = a + rem;
+    const float* xa_r = yr + int64_t(a) * p;
+    const float* xa_i = yi + int64_t(a) * p;
+    const float* xb_r = yr + int64_t(b) * p;
+    const float* xb_i = yi + int64_t(b) * p;
+    double sr = 0.0, si = 0.0;
+    for (int r = 0; r < p; ++r) {
+      const double ar = xa_r[r], ai = xa_i[r], br = xb_r[r], bi = xb_i[r];
+      sr += ar * br + ai * bi;
+      si += ar * bi - ai * br;
+    }
+    G[2 * (a * l + b)] = sr;
+    G[2 * (a * l + b) + 1] = si;
+    G[2 * (b * l + a)] = sr;
+    G[2 * (b * l + a) + 1] = -si;
+  }
+}
+
+// In-place upper Cholesky G = R^H R (R in the upper triangle of G).
+// Returns false on a non-positive pivot.
+__device__ bool cholesky(double* G, int l, int* fail) {
+  for (int j = 0; j < l; ++j) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double d = G[2 * (j * l + j)];
+      for (int i = 0; i < j; ++i) {
+        const double rr = G[2 * (i * l + j)], ri = G[2 * (i * l + j) + 1];
+        d -= rr * rr + ri * ri;
+      }
+      if (!(d > 0.0) || !isfinite(d)) *fail = 1;
+      G[2 * (j * l + j)] = (d > 0.0 && isfinite(d)) ? sqrt(d) : 1.0;
+      G[2 * (j * l + j) + 1] = 0.0;
+    }
+    __syncthreads();
+    const double djj = G[2 * (j * l + j)];
+    for (int k = j + 1 + threadIdx.x; k < l; k += blockDim.x) {
+      double sr = G[2 * (j * l + k)], si = G[2 * (j * l + k) + 1];
+      for (int i = 0; i < j; ++i) {
+        // subtract conj(R_ij) R_ik
+        const double ar = G[2 * (i * l + j)], ai = G[2 * (i * l + j) + 1];
+        const double br = G[2 * (i * l + k)], bi = G[2 * (i * l + k) + 1];
+        sr -= ar * br + ai * bi;
+        si -= ar * bi - ai * br;
+      }
+      G[2 * (j * l + k)] = sr / djj;
+      G[2 * (j * l + k) + 1] = si / djj;
+    }
+  }
+  __syncthreads();
+  return *fail == 0;
+}
+
+// Y <- Y R^{-1}, row by row (x R = y by forward substitution), in place.
+__device__ void right_solve(float* yr, float* yi, int p, int l, const double* R) {
+  for (int r = threadIdx.x; r < p; r += blockDim.x) {
+    for (int j = 0; j < l; ++j) {
+      double sr = yr[r + int64_t(p) * j], si = yi[r + int64_t(p) * j];
+      for (int i = 0; i < j; ++i) {
+        const double xr = yr[r + int64_t(p) * i], xi = yi[r + int64_t(p) * i];
+        const double ar = R[2 * (i * l + j)], ai = R[2 * (i * l + j) + 1];
+        sr -= xr * ar - xi * ai;
+        si -= xr * ai + xi * ar;
+      }
+      const double d = R[2 * (j * l + j)];
+      yr[r + int64_t(p) * j] = float(sr / d);
+      yi[r + int64_t(p) * j] = float(si / d);
+    }
+  }
+}
+
+// CholeskyQR2 (with a shifted retry) of every slice's p x l block.
+__global__ void __launch_bounds__(QR_THREADS) cholqr2_kernel(float* y_re, float* y_im, int64_t sY,
+                                                             int p, int l, int32_t* status) {
+  extern __shared__ double G[];   // 2 * l * l
+  __shared__ int fail;
+  float* yr = y_re + int64_t(blockIdx.x) * sY;
+  float* yi = y_im + int64_t(blockIdx.x) * sY;
+  int passes_left = 2;
+  bool shifted = false;
+  for (int it = 0; it < 4 && passes_left > 0; ++it) {
+    if (threadIdx.x == 0) fail = 0;
+    gram(yr, yi, p, l, G);
+    __syncthreads();
+    if (shifted) {
+      // shift s = 11 (p l + l (l + 1)) u ||Y||_F^2 on the diagonal
+      if (threadIdx.x == 0) {
+        double tr = 0.0;
+        for (int j = 0; j < l; ++j) tr += G[2 * (j * l + j)];
+        const double s = 11.0 * (double(p) * l + double(l) * (l + 1)) * 1.1102230246251565e-16 * tr;
+        for (int j = 0; j < l; ++j) G[2 * (j * l + j)] += s;
+      }
+      __syncthreads();
+    }
+    const bool ok = cholesky(G, l, &fail);
+    if (!ok) {
+      if (shifted) {
+        if (threadIdx.x == 0 && status) atomicOr(status, TP_DEV_BREAKDOWN);
+        return;
+      }
+      shifted = true;   // retry this pass with a shift, then two plain passes
+      passes_left = 3;
+      continue;
+    }
+    __syncthreads();
+    right_solve(yr, yi, p, l, G);
+    __syncthreads();
+    shifted = false;
+    --passes_left;
+  }
+}
+
+// Sorts the l Jacobi singular triplets of every slice, keeps the top k and
+// writes: Wk (l x k, float32 planar; right factor of the small problem, the
+// columns of W), Vk (n2 x k, float32; left singular vectors of B^H = right
+// ones of X_hat), S (k x k diagonal).
+__global__ void pick_topk_kernel(const double* __restrict__ gr, const double* __restrict__ gi,
+                                 int64_t sG, const double* __restrict__ wr,
+                                 const double* __restrict__ wi, int64_t sW,
+                                 const double* __restrict__ sig, int p, int l, int k,
+                                 float* __restrict__ wkr, float* __restrict__ wki,
+                                 float* __restrict__ vkr, float* __restrict__ vki,
+                                 float* __restrict__ sr, float* __restrict__ si) {
+  extern __shared__ int order[];
+  const int64_t f = blockIdx.x;
+  const double* s = sig + f * l;
+  for (int j = threadIdx.x; j < l; j += blockDim.x) {
+    const double sj = s[j];
+    int rank = 0;
+    for (int m = 0; m < l; ++m) rank += (s[m] > sj) || (s[m] == sj && m < j);
+    order[rank] = j;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < l * k; e += blockDim.x) {
+    const int i = e % l, c = e / l;
+    const int j = order[c];
+    wkr[f * l * k + e] = float(wr[f * sW + i + int64_t(l) * j]);
+    wki[f * l * k + e] = float(wi[f * sW + i + int64_t(l) * j]);
+  }
+  for (int64_t e = threadIdx.x; e < int64_t(p) * k; e += blockDim.x) {
+    const int64_t i = e % p, c = e / p;
+    const int j = order[c];
+    vkr[f * p * k + e] = float(gr[f * sG + i + int64_t(p) * j]);
+    vki[f * p * k + e] = float(gi[f * sG + i + int64_t(p) * j]);
+  }
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int i = e % k, c = e / k;
+    sr[f * k * k + e] = (i == c) ? float(s[order[c]]) : 0.f;
+    si[f * k * k + e] = 0.f;
+  }
+}
+
+__global__ void to_double_kernel(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n;
+       e += int64_t(gridDim.x) * blockDim.x)
+    b[e] = a[e];
+}
+
+__global__ void real_flags2_kernel(int* flags, int64_t h, int64_t n3) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k < h) flags[k] = (k == 0 || (n3 % 2 == 0 && k == h - 1)) ? 1 : 0;
+}
+
+unsigned grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  return unsigned(b);
+}
+
+}  // namespace
+
+size_t rsvd_ws(int64_t n1, int64_t n2, int64_t n3, int64_t k, int64_t p) {
+  const size_t h = size_t(half_len(n3));
+  const size_t l = size_t(k + p);
+  return 2 * ws_bytes(size_t(n1) * n2 * h, 4)   // X_hat
+         + 2 * ws_bytes(size_t(n1) * n2 * h, 4) // X_hat^H
+         + 2 * ws_bytes(size_t(n2) * l * h, 4)  // Omega
+         + 2 * ws_bytes(size_t(n1) * l * h, 4)  // Y / Q
+         + 2 * ws_bytes(size_t(n2) * l * h, 4)  // Z / B^H
+         + 2 * ws_bytes(size_t(n2) * l * h, 8)  // Jacobi G (float64)
+         + 2 * ws_bytes(l * l * h, 8)           // Jacobi W (float64)
+         + ws_bytes(l * h, 8) + ws_bytes(h, 4)  // singular values, real flags
+         + 2 * ws_bytes(l * size_t(k) * h, 4)   // W_k
+         + 2 * ws_bytes(size_t(n1) * k * h, 4)  // U_hat
+         + 2 * ws_bytes(size_t(k) * k * h, 4)   // S_hat
+         + 2 * ws_bytes(size_t(n2) * k * h, 4); // V_hat
+}
+
+int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, int q,
+             uint64_t seed, float* U, float* S, float* V, const tp_opts* opts, cudaStream_t st) {
+  const int64_t h = half_len(n3);
+  const int64_t l = k + p;
+  Arena ws;
+  int rc = acquire_workspace(opts, rsvd_ws(n1, n2, n3, k, p), &ws);
+  if (rc) return rc;
+  int32_t* status = opts ? opts->status : nullptr;
+  float* Xr = ws.take<float>(size_t(n1) * n2 * h);
+  float* Xi = ws.take<float>(size_t(n1) * n2 * h);
+  float* Hr = ws.take<float>(size_t(n1) * n2 * h);
+  float* Hi = ws.take<float>(size_t(n1) * n2 * h);
+  float* Or = ws.take<float>(size_t(n2) * l * h);
+  float* Oi = ws.take<float>(size_t(n2) * l * h);
+  float* Yr = ws.take<float>(size_t(n1) * l * h);
+  float* Yi = ws.take<float>(size_t(n1) * l * h);
+  float* Zr = ws.take<float>(size_t(n2) * l * h);
+  float* Zi = ws.take<float>(size_t(n2) * l * h);
+  double* Gr = ws.take<double>(size_t(n2) * l * h);
+  double* Gi = ws.take<double>(size_t(n2) * l * h);
+  double* Wr = ws.take<double>(size_t(l) * l * h);
+  double* Wi = ws.take<double>(size_t(l) * l * h);
+  double* sig = ws.take<double>(size_t(l) * h);
+  int* flags = ws.take<int>(size_t(h));
+  float* Wkr = ws.take<float>(size_t(l) * k * h);
+  float* Wki = ws.take<float>(size_t(l) * k * h);
+  float* Ur = ws.take<float>(size_t(n1) * k * h);
+  float* Ui = ws.take<float>(size_t(n1) * k * h);
+  float* Sr = ws.take<float>(size_t(k) * k * h);
+  float* Si = ws.take<float>(size_t(k) * k * h);
+  float* Vr = ws.take<float>(size_t(n2) * k * h);
+  float* Vi = ws.take<float>(size_t(n2) * k * h);
+
+  // X_hat and X_hat^H
+  DftGather gx{X, n1 * n2, 1, 1, 0, n1 * n2, nullptr, nullptr, nullptr, 0, n3, Xr, Xi,
+               n1 * n2, n1 * n2, nullptr, nullptr, 0};
+  if ((rc = launch_rdft(gx, st))) return rc;
+  {
+    KernelScope ks("conj_transpose", st);
+    conj_transpose_kernel<<<dim3(unsigned((n1 + 31) / 32), unsigned((n2 + 31) / 32), unsigned(h)),
+                            dim3(32, 8), 0, st>>>(Xr, Xi, n1, n2, Hr, Hi);
+  }
+  {
+    KernelScope ks("sketch", st);
+    sketch_kernel<<<grid_for(n2 * l * h), 256, 0, st>>>(Or, Oi, n2, l, h, n3, seed);
+  }
+  if ((rc = launch_status("sketch"))) return rc;
+
+  auto gemm = [&](const float* ar, const float* ai, int64_t M, int64_t K, const float* br,
+                  const float* bi, int64_t N, float* cr, float* ci) {
+    CGemm g{ar, ai, br, bi, cr, ci, M, N, K, nullptr, M, K, M, M * K, K * N, M * N, h, n3,
+            TP_FP32, nullptr, nullptr, nullptr, nullptr, K, status};
+    return launch_cgemm(g, st);
+  };
+  const size_t qr_smem = size_t(2) * l * l * sizeof(double);
+  cudaFuncSetAttribute(cholqr2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(qr_smem));
+  auto orth = [&](float* yr, float* yi, int64_t rows) {
+    {
+      KernelScope ks("cholqr2", st);
+      cholqr2_kernel<<<unsigned(h), QR_THREADS, qr_smem, st>>>(yr, yi, rows * l, int(rows),
+                                                               int(l), status);
+    }
+    return launch_status("cholqr2_kernel");
+  };
+
+  if ((rc = gemm(Xr, Xi, n1, n2, Or, Oi, l, Yr, Yi))) return rc;     // Y = X_hat Omega
+  if ((rc = orth(Yr, Yi, n1))) return rc;
+  for (int it = 0; it < q; ++it) {
+    if ((rc = gemm(Hr, Hi, n2, n1, Yr, Yi, l, Zr, Zi))) return rc;   // Z = X_hat^H Q
+    if ((rc = orth(Zr, Zi, n2))) return rc;
+    if ((rc = gemm(Xr, Xi, n1, n2, Zr, Zi, l, Yr, Yi))) return rc;   // Y = X_hat Z
+    if ((rc = orth(Yr, Yi, n1))) return rc;
+  }
+  if ((rc = gemm(Hr, Hi, n2, n1, Yr, Yi, l, Zr, Zi))) return rc;     // B^H = X_hat^H Q
+  {
+    KernelScope ks("to_double", st);
+    to_double_kernel<<<grid_for(n2 * l * h), 256, 0, st>>>(Zr, Gr, n2 * l * h);
+    to_double_kernel<<<grid_for(n2 * l * h), 256, 0, st>>>(Zi, Gi, n2 * l * h);
+    real_flags2_kernel<<<unsigned((h + 255) / 256), 256, 0, st>>>(flags, h, n3);
+  }
+  note_launches(2);
+  if ((rc = launch_status("to_double"))) return rc;
+  const int sweeps = (opts && opts->max_sweeps > 0) ? opts->max_sweeps : 30;
+  if ((rc = jacobi_double_launch(Gr, Gi, n2 * l, Wr, Wi, l * l, sig, int(n2), int(l), int(h),
+                                 sweeps, flags, status, st)))
+    return rc;
+  {
+    KernelScope ks("pick_topk", st);
+    pick_topk_kernel<<<unsigned(h), 256, size_t(l) * sizeof(int), st>>>(
+        Gr, Gi, n2 * l, Wr, Wi, l * l, sig, int(n2), int(l), k, Wkr, Wki, Vr, Vi, Sr, Si);
+  }
+  if ((rc = launch_status("pick_topk_kernel"))) return rc;
+  if ((rc = gemm(Yr, Yi, n1, l, Wkr, Wki, k, Ur, Ui))) return rc;    // U_hat = Q W_k
+  if ((rc = launch_irdft(Ur, Ui, n1 * k, n1 * k, n3, U, st))) return rc;
+  if ((rc = launch_irdft(Sr, Si, int64_t(k) * k, int64_t(k) * k, n3, S, st))) return rc;
+  return launch_irdft(Vr, Vi, n2 * k, n2 * k, n3, V, st);
+}
+
+}  // namespace tp

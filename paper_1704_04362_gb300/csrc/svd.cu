@@ -1,0 +1,313 @@
+// Facewise SVD of the half spectrum for the t-SVD (Theorem 2.6 computed as in
+// Eq. circ1): every Fourier slice X_hat_k = U_k diag(s_k) V_k^H.  The float32
+// slice is copied into a float64 work matrix so that the accumulated
+// rotations keep the factors orthogonal to float32 accuracy.
+//
+// One CTA per slice runs the one-sided (Hestenes) Jacobi method on the
+// columns of a p x q work matrix G (p >= q): pairs of columns (a, b) are
+// rotated by a 2 x 2 unitary until every pair is orthogonal to a relative
+// tolerance; the same rotations accumulate in V (q x q).  Then s_j = ||G_j||,
+// U_j = G_j / s_j.  Pairs are scheduled by the round-robin (circle) ordering
+// so that the q/2 pairs of a step are disjoint and run on separate warps.
+// The complex rotation: with gamma = a^H b = |gamma| e^{i phi}, b~ = e^{-i phi} b
+// makes the pair real; zeta = (||b||^2 - ||a||^2) / (2|gamma|),
+// t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t,
+// a' = c a - s b~, b' = s a + c b~.  Sweeps are capped (opts->max_sweeps); a
+// slice that reaches the cap sets TP_DEV_NOCONV.
+#include "tp_internal.cuh"
+
+namespace tp {
+namespace {
+
+constexpr int SVD_THREADS = 256;
+
+template <class T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <class T> struct Eps;
+template <> struct Eps<float> { static constexpr float v = 5.96e-8f; };
+template <> struct Eps<double> { static constexpr double v = 1.12e-16; };
+
+// Batched one-sided Jacobi.  Item b: G (p x q, column-major, ld p) at
+// g_re/g_im + b*sG, V (q x q) at v_re/v_im + b*sV.  On exit G holds U
+// (unit columns, unsorted), sig[b*q + j] the singular values (unsorted).
+template <class T>
+__global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(T* g_re, T* g_im, int64_t sG, T* v_re,
+                                                             T* v_im, int64_t sV, T* sig, int p,
+                                                             int q, int max_sweeps,
+                                                             const int* real_flags,
+                                                             int32_t* status) {
+  const int64_t b = blockIdx.x;
+  T* Gr = g_re + b * sG;
+  T* Gi = g_im + b * sG;
+  T* Vr = v_re + b * sV;
+  T* Vi = v_im + b * sV;
+  const bool real = real_flags ? real_flags[b] != 0 : false;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = SVD_THREADS / 32;
+  __shared__ int rotated;
+
+  for (int e = tid; e < q * q; e += SVD_THREADS) {
+    Vr[e] = (e % (q + 1) == 0) ? T(1) : T(0);
+    Vi[e] = T(0);
+  }
+  if (real)
+    for (int64_t e = tid; e < int64_t(p) * q; e += SVD_THREADS) Gi[e] = T(0);
+  __syncthreads();
+
+  T tol = T(8) * Eps<T>::v * sqrt(T(p));
+  if (tol < T(sizeof(T) == 4 ? 1e-6 : 1e-13)) tol = T(sizeof(T) == 4 ? 1e-6 : 1e-13);
+  const int qq = q + (q & 1);
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    for (int step = 0; step < qq - 1; ++step) {
+      for (int i = warp; i < qq / 2; i += nw) {
+        int a, c2;
+        if (i == 0) {
+          a = qq - 1;
+          c2 = step;
+        } else {
+          a = (step + i) % (qq - 1);
+          c2 = (step - i + (qq - 1)) % (qq - 1);
+        }
+        if (a >= q || c2 >= q) continue;
+        if (a > c2) { const int t = a; a = c2; c2 = t; }
+        T* ar = Gr + int64_t(a) * p;
+        T* ai = Gi + int64_t(a) * p;
+        T* br = Gr + int64_t(c2) * p;
+        T* bi = Gi + int64_t(c2) * p;
+        T alpha = 0, beta = 0, gr = 0, gi = 0;
+        for (int r = lane; r < p; r += 32) {
+          const T xr = ar[r], xi = ai[r], yr = br[r], yi = bi[r];
+          alpha += xr * xr + xi * xi;
+          beta += yr * yr + yi * yi;
+          gr += xr * yr + xi * yi;    // Re(conj(x) y)
+          gi += xr * yi - xi * yr;    // Im(conj(x) y)
+        }
+        alpha = warp_sum_t(alpha);
+        beta = warp_sum_t(beta);
+        gr = warp_sum_t(gr);
+        gi = warp_sum_t(gi);
+        const T g = sqrt(gr * gr + gi * gi);
+        if (!(g > tol * sqrt(alpha * beta)) || g == T(0)) continue;
+        if (lane == 0) rotated = 1;
+        const T zeta = (beta - alpha) / (T(2) * g);
+        const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+        const T cs = T(1) / sqrt(T(1) + t * t);
+        const T sn = cs * t;
+        const T er = gr / g, ei = -gi / g;   // e^{-i phi}
+        for (int r = lane; r < p; r += 32) {
+          const T xr = ar[r], xi = ai[r];
+          const T yr = br[r] * er - bi[r] * ei, yi = br[r] * ei + bi[r] * er;   // b~
+          ar[r] = cs * xr - sn * yr;
+          ai[r] = cs * xi - sn * yi;
+          br[r] = sn * xr + cs * yr;
+          bi[r] = sn * xi + cs * yi;
+        }
+        T* var = Vr + int64_t(a) * q;
+        T* vai = Vi + int64_t(a) * q;
+        T* vbr = Vr + int64_t(c2) * q;
+        T* vbi = Vi + int64_t(c2) * q;
+        for (int r = lane; r < q; r += 32) {
+          const T xr = var[r], xi = vai[r];
+          const T yr = vbr[r] * er - vbi[r] * ei, yi = vbr[r] * ei + vbi[r] * er;
+          var[r] = cs * xr - sn * yr;
+          vai[r] = cs * xi - sn * yi;
+          vbr[r] = sn * xr + cs * yr;
+          vbi[r] = sn * xi + cs * yi;
+        }
+      }
+      __syncthreads();
+    }
+    const int any = rotated;
+    __syncthreads();
+    if (!any) break;
+  }
+  if (sweep >= max_sweeps && tid == 0 && status) atomicOr(status, TP_DEV_NOCONV);
+  // singular values and unit left vectors
+  for (int j = warp; j < q; j += nw) {
+    T* xr = Gr + int64_t(j) * p;
+    T* xi = Gi + int64_t(j) * p;
+    T nrm = 0;
+    for (int r = lane; r < p; r += 32) nrm += xr[r] * xr[r] + xi[r] * xi[r];
+    nrm = sqrt(warp_sum_t(nrm));
+    if (lane == 0) sig[b * q + j] = nrm;
+    const T inv = nrm > T(0) ? T(1) / nrm : T(0);
+    for (int r = lane; r < p; r += 32) {
+      xr[r] *= inv;
+      xi[r] *= inv;
+    }
+  }
+}
+
+// Gathers slice b of the half spectrum into the (float64) work matrix:
+// G = X_hat_k (n1 x n2) when n1 >= n2, else G = X_hat_k^H (n2 x n1).
+__global__ void load_work_kernel(const float* __restrict__ xr, const float* __restrict__ xi,
+                                 int64_t n1, int64_t n2, int64_t h, bool transpose,
+                                 double* __restrict__ gr, double* __restrict__ gi) {
+  const int64_t per = n1 * n2;
+  const int64_t total = per * h;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t k = e / per, r = e - k * per;
+    const int64_t i = r % n1, j = r / n1;
+    const float vr = xr[e], vi = xi[e];
+    if (!transpose) {
+      gr[e] = vr;
+      gi[e] = vi;
+    } else {   // G(j, i) = conj(X(i, j)), G is n2 x n1
+      const int64_t o = k * per + j + n2 * i;
+      gr[o] = vr;
+      gi[o] = -vi;
+    }
+  }
+}
+
+// Sorts each slice's singular triplets by descending value and writes the
+// half-spectrum factors: Uh (n1 x m), Sh (m x m, diagonal), Vh (n2 x m).
+// `left` is the matrix holding the n1-side vectors (G or V of the Jacobi),
+// `right` the n2-side one; `left_ld`/`right_ld` their leading dimensions.
+__global__ void write_factors_kernel(const double* __restrict__ lr, const double* __restrict__ li,
+                                     int64_t sL, int64_t left_ld,
+                                     const double* __restrict__ rr, const double* __restrict__ ri,
+                                     int64_t sR, int64_t right_ld, const double* __restrict__ sig,
+                                     int q, int64_t n1, int64_t n2, int m,
+                                     float* __restrict__ ur, float* __restrict__ ui,
+                                     float* __restrict__ sr, float* __restrict__ si,
+                                     float* __restrict__ vr, float* __restrict__ vi) {
+  extern __shared__ int order[];   // order[rank] = column
+  const int64_t k = blockIdx.x;
+  const double* s = sig + k * q;
+  for (int j = threadIdx.x; j < q; j += blockDim.x) {
+    const double sj = s[j];
+    int rank = 0;
+    for (int l = 0; l < q; ++l) {
+      const double sl = s[l];
+      rank += (sl > sj) || (sl == sj && l < j);
+    }
+    order[rank] = j;
+  }
+  __syncthreads();
+  const double* Lr = lr + k * sL;
+  const double* Li = li + k * sL;
+  const double* Rr = rr + k * sR;
+  const double* Ri = ri + k * sR;
+  for (int64_t e = threadIdx.x; e < n1 * m; e += blockDim.x) {
+    const int64_t i = e % n1, c = e / n1;
+    const int j = order[c];
+    ur[k * n1 * m + e] = float(Lr[i + left_ld * j]);
+    ui[k * n1 * m + e] = float(Li[i + left_ld * j]);
+  }
+  for (int64_t e = threadIdx.x; e < n2 * m; e += blockDim.x) {
+    const int64_t i = e % n2, c = e / n2;
+    const int j = order[c];
+    vr[k * n2 * m + e] = float(Rr[i + right_ld * j]);
+    vi[k * n2 * m + e] = float(Ri[i + right_ld * j]);
+  }
+  for (int64_t e = threadIdx.x; e < int64_t(m) * m; e += blockDim.x) {
+    const int64_t i = e % m, c = e / m;
+    sr[k * m * m + e] = (i == c) ? float(s[order[c]]) : 0.f;
+    si[k * m * m + e] = 0.f;
+  }
+}
+
+__global__ void real_flags_kernel(int* flags, int64_t h, int64_t n3) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k < h) flags[k] = (k == 0 || (n3 % 2 == 0 && k == h - 1)) ? 1 : 0;
+}
+
+}  // namespace
+
+int jacobi_double_launch(double* gr, double* gi, int64_t sG, double* vr, double* vi, int64_t sV,
+                         double* sig, int p, int q, int batch, int max_sweeps,
+                         const int* real_flags, int32_t* status, cudaStream_t st) {
+  if (batch <= 0) return TP_OK;
+  {
+    KernelScope ks("jacobi_svd", st);
+    jacobi_kernel<double><<<unsigned(batch), SVD_THREADS, 0, st>>>(
+        gr, gi, sG, vr, vi, sV, sig, p, q, max_sweeps, real_flags, status);
+  }
+  return launch_status("jacobi_kernel");
+}
+
+size_t tsvd_ws(int64_t n1, int64_t n2, int64_t n3) {
+  const size_t h = size_t(half_len(n3));
+  const size_t m = size_t(n1 < n2 ? n1 : n2);
+  const size_t p = size_t(n1 < n2 ? n2 : n1);
+  return 2 * ws_bytes(size_t(n1) * n2 * h, 4)      // X_hat
+         + 2 * ws_bytes(p * m * h, 8)              // G (float64)
+         + 2 * ws_bytes(m * m * h, 8)              // V of the Jacobi (float64)
+         + ws_bytes(m * h, 8)                      // singular values
+         + ws_bytes(h, 4)                          // real-slice flags
+         + 2 * ws_bytes(size_t(n1) * m * h, 4)     // U_hat
+         + 2 * ws_bytes(m * m * h, 4)              // S_hat
+         + 2 * ws_bytes(size_t(n2) * m * h, 4);    // V_hat
+}
+
+int tsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, float* U, float* S, float* V,
+             const tp_opts* opts, cudaStream_t st) {
+  const int64_t h = half_len(n3);
+  const int64_t m = n1 < n2 ? n1 : n2;
+  const int64_t p = n1 < n2 ? n2 : n1;
+  const bool transpose = n1 < n2;
+  Arena ws;
+  int rc = acquire_workspace(opts, tsvd_ws(n1, n2, n3), &ws);
+  if (rc) return rc;
+  float* Xr = ws.take<float>(size_t(n1) * n2 * h);
+  float* Xi = ws.take<float>(size_t(n1) * n2 * h);
+  double* Gr = ws.take<double>(size_t(p) * m * h);
+  double* Gi = ws.take<double>(size_t(p) * m * h);
+  double* Wr = ws.take<double>(size_t(m) * m * h);
+  double* Wi = ws.take<double>(size_t(m) * m * h);
+  double* sig = ws.take<double>(size_t(m) * h);
+  int* flags = ws.take<int>(size_t(h));
+  float* Ur = ws.take<float>(size_t(n1) * m * h);
+  float* Ui = ws.take<float>(size_t(n1) * m * h);
+  float* Sr = ws.take<float>(size_t(m) * m * h);
+  float* Si = ws.take<float>(size_t(m) * m * h);
+  float* Vr = ws.take<float>(size_t(n2) * m * h);
+  float* Vi = ws.take<float>(size_t(n2) * m * h);
+
+  DftGather gx{X, n1 * n2, 1, 1, 0, n1 * n2, nullptr, nullptr, nullptr, 0, n3, Xr, Xi,
+               n1 * n2, n1 * n2, nullptr, nullptr, 0};
+  if ((rc = launch_rdft(gx, st))) return rc;
+  {
+    KernelScope ks("svd_prep", st);
+    int64_t blocks = (n1 * n2 * h + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    load_work_kernel<<<unsigned(blocks), 256, 0, st>>>(Xr, Xi, n1, n2, h, transpose, Gr, Gi);
+    real_flags_kernel<<<unsigned((h + 255) / 256), 256, 0, st>>>(flags, h, n3);
+  }
+  note_launches(1);
+  if ((rc = launch_status("svd_prep"))) return rc;
+  const int sweeps = (opts && opts->max_sweeps > 0) ? opts->max_sweeps : 30;
+  {
+    KernelScope ks("jacobi_svd", st);
+    jacobi_kernel<double><<<unsigned(h), SVD_THREADS, 0, st>>>(
+        Gr, Gi, p * m, Wr, Wi, m * m, sig, int(p), int(m), sweeps, flags,
+        opts ? opts->status : nullptr);
+  }
+  if ((rc = launch_status("jacobi_kernel"))) return rc;
+  {
+    KernelScope ks("svd_factors", st);
+    // n1 >= n2: G holds U (n1 x m), Jacobi V holds V (n2 x m).  n1 < n2: the
+    // roles swap (the Jacobi ran on X_hat^H).
+    if (!transpose)
+      write_factors_kernel<<<unsigned(h), 256, size_t(m) * sizeof(int), st>>>(
+          Gr, Gi, p * m, p, Wr, Wi, m * m, m, sig, int(m), n1, n2, int(m), Ur, Ui, Sr, Si, Vr, Vi);
+    else
+      write_factors_kernel<<<unsigned(h), 256, size_t(m) * sizeof(int), st>>>(
+          Wr, Wi, m * m, m, Gr, Gi, p * m, p, sig, int(m), n1, n2, int(m), Ur, Ui, Sr, Si, Vr, Vi);
+  }
+  if ((rc = launch_status("write_factors_kernel"))) return rc;
+  if ((rc = launch_irdft(Ur, Ui, n1 * m, n1 * m, n3, U, st))) return rc;
+  if ((rc = launch_irdft(Sr, Si, m * m, m * m, n3, S, st))) return rc;
+  return launch_irdft(Vr, Vi, n2 * m, n2 * m, n3, V, st);
+}
+
+}  // namespace tp

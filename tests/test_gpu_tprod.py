@@ -15,7 +15,8 @@ def dev(x):
     return tp.as_tprod_layout(x)
 
 
-@pytest.mark.parametrize("n3", [1, 2, 3, 5, 16, 17, 64, 120, 257, 512])
+@pytest.mark.parametrize("n3", [1, 2, 3, 5, 16, 17, 64, 120, 257, 260, 512, 600, 1001, 2000,
+                                4096])
 def test_rdft_irdft_match_oracle(n3):
     X = synth.iid_normal((37, 5, n3), seed=n3)
     Xr, Xi = tp.rdft3(dev(X))

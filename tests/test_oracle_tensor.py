@@ -24,6 +24,15 @@ def test_dft_matches_numpy_fft():
         np.testing.assert_allclose(T.fft3(Y), np.fft.fft(Y, axis=2), atol=1e-10 * n3)
 
 
+def test_contraction_and_library_routes_agree():
+    # the explicit F_{n3} contraction (used up to 256) and numpy.fft (above)
+    X = rng(11).standard_normal((2, 3, 300))
+    F = T.dft_matrix(300)
+    np.testing.assert_allclose(T.fft3(X), X.astype(complex) @ F.T, atol=1e-9)
+    Y = rng(12).standard_normal((2, 2, 2000))
+    np.testing.assert_allclose(T.ifft3(T.fft3(Y)).real, Y, atol=1e-12)
+
+
 def test_tube_circular_convolution_by_hand():
     # Def. 2.1 with n1 = n2 = n4 = 1: circ of the tube (1,2,3) is
     # [[1,3,2],[2,1,3],[3,2,1]]; times (4,5,6): (4+15+12, 8+5+18, 12+10+6).
