@@ -88,7 +88,8 @@ typedef enum {
   TP_OP_TSVD = 3,            /* dims: n1, n2, n3 */
   TP_OP_TSVD_RANDOMIZED = 4, /* dims: n1, n2, n3, k, p */
   TP_OP_TCOMPLETE_SVT = 5,   /* dims: n1, n2, n3 */
-  TP_OP_SLICE_NORMS = 6      /* dims: n1, n2, n3 */
+  TP_OP_SLICE_NORMS = 6,     /* dims: n1, n2, n3 */
+  TP_OP_TCX = 7              /* dims: n1, n2, n3 */
 } tp_op;
 
 /* ---------------------------------------------------------------- t-product
@@ -146,6 +147,21 @@ int tsvd_randomized(const float* X, int64_t n1, int64_t n2, int64_t n3,
                     int k, int p, int q, uint64_t seed,
                     float* U, float* S, float* V, const tp_opts* opts, void* stream);
 
+/* tcx: t-CX of Algorithm 4 with the t-project of Algorithm 3.  Lateral
+ * slice j of A (n1 x n2 x n3) is picked with probability min{1, c p_j}
+ * (p from TP_PROB_A2: ||A(:,j,:)||_F^2 / ||A||_F^2, or TP_PROB_GIVEN), by
+ * the same Philox coins as tprod_sampled; C = picked slices / sqrt(q_j).
+ * Z = C * C^dagger * A (n1 x n2 x n3 output), computed per half-spectrum
+ * slice as P_k A_hat_k with P_k the projector onto range(C_hat_k), whose
+ * basis is the left singular vectors of C_hat_k (float64 Jacobi) above
+ * MATLAB's pinv cut-off max(n1, c') eps(s_max).
+ *   idx_out / count_out: as tprod_sampled.
+ * Reads the pick count back to the host once (synchronises `stream`).
+ * Limits: min(n1, n2) <= 512, n2 <= 4096, n3 <= 512.                        */
+int tcx(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, uint64_t seed,
+        int prob_mode, const double* p_given, float* Z, int32_t* idx_out, int64_t* count_out,
+        const tp_opts* opts, void* stream);
+
 /* ---------------------------------------------------------------- completion
  * tcomplete_svt: `iters` iterations of the ADMM of Algorithm 7 in the
  * completion form of problem (tlow6): minimise ||L||_TNN subject to
@@ -160,7 +176,8 @@ int tsvd_randomized(const float* X, int64_t n1, int64_t n2, int64_t n3,
  *            (zeros and *mu = mu0 start Algorithm 7 afresh; passing the
  *            previous outputs resumes it)
  *   mu    device float64 scalar, read and updated in place
- * Paper constants: mu0 = 1e-3, rho = 1.1, mu_max = 1e10.  Limits as tsvd.  */
+ * Paper constants: mu0 = 1e-3, rho = 1.1, mu_max = 1e10.  The slice SVT
+ * runs the float64 one-sided Jacobi.  Limits as tsvd.                      */
 int tcomplete_svt(const float* X, const uint8_t* mask,
                   int64_t n1, int64_t n2, int64_t n3, int iters,
                   double rho, double mu_max,

@@ -19,7 +19,7 @@ import numpy as np
 __all__ = [
     "TP_FP32", "TP_TF32X3", "TP_BF16X3", "TP_PROB_AB", "TP_PROB_A2", "TP_PROB_GIVEN",
     "TprodError", "lib", "lib_path", "empty_tensor", "as_tprod_layout",
-    "tprod", "tprod_sampled", "tsvd", "tsvd_randomized", "tcomplete_svt",
+    "tprod", "tprod_sampled", "tsvd", "tsvd_randomized", "tcomplete_svt", "tcx",
     "rdft3", "irdft3", "slice_norms", "sample_draw", "launch_count", "exported_symbols",
     "profile_start", "profile_stop", "slice_norms_noalloc",
 ]
@@ -27,7 +27,7 @@ __all__ = [
 TP_FP32, TP_TF32X3, TP_BF16X3 = 0, 1, 2
 TP_PROB_AB, TP_PROB_A2, TP_PROB_GIVEN = 0, 1, 2
 TP_OP_TPROD, TP_OP_TPROD_SAMPLED, TP_OP_TSVD, TP_OP_TSVD_RANDOMIZED, TP_OP_TCOMPLETE_SVT, \
-    TP_OP_SLICE_NORMS = 1, 2, 3, 4, 5, 6
+    TP_OP_SLICE_NORMS, TP_OP_TCX = 1, 2, 3, 4, 5, 6, 7
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _c_i64, _c_u64, _c_int, _c_u32 = ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32
@@ -54,6 +54,8 @@ _SIGS = {
                                  _vp, _vp, _vp, _vp, _vp]),
     "tcomplete_svt": (_c_int, [_vp, _vp, _c_i64, _c_i64, _c_i64, _c_int, _dbl, _dbl,
                                _vp, _vp, _vp, _vp, _vp, _vp]),
+    "tcx": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_i64, _c_u64, _c_int, _vp, _vp, _vp, _vp,
+                     _vp, _vp]),
     "tp_rdft3": (_c_int, [_vp, _c_i64, _c_i64, _vp, _vp, _vp]),
     "tp_irdft3": (_c_int, [_vp, _vp, _c_i64, _c_i64, _vp, _vp]),
     "tp_slice_norms": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_int, _vp, _vp, _vp]),
@@ -316,6 +318,22 @@ def tcomplete_svt(X, mask, iters, L=None, E=None, Y=None, mu=None, mu0=1e-3, rho
                              _tensor_arg(mu, "mu", torch.float64), ctypes.byref(o), _stream())
     _check(rc, "tcomplete_svt")
     return L, E, Y, mu
+
+
+def tcx(A, c, seed=0, prob_mode=TP_PROB_A2, p_given=None, status=None):
+    """t-CX (Algorithm 4): returns (Z = C * C^dagger * A, idx, count)."""
+    torch = _torch()
+    n1, n2, n3 = A.shape
+    Z = empty_tensor(n1, n2, n3, device=A.device)
+    idx = torch.empty(n2, dtype=torch.int32, device=A.device)
+    count = torch.empty(1, dtype=torch.int64, device=A.device)
+    pg = _tensor_arg(p_given, "p_given", torch.float64) if prob_mode == TP_PROB_GIVEN else None
+    o = _opts(TP_OP_TCX, (n1, n2, n3), TP_FP32, status)
+    rc = lib().tcx(_tensor_arg(A, "A"), n1, n2, n3, int(c), int(seed) & ((1 << 64) - 1),
+                   int(prob_mode), pg, _tensor_arg(Z, "Z"), _tensor_arg(idx, "idx", torch.int32),
+                   _tensor_arg(count, "count", torch.int64), ctypes.byref(o), _stream())
+    _check(rc, "tcx")
+    return Z, idx, count
 
 
 def rdft3(X):

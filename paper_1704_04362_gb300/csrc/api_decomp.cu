@@ -5,6 +5,14 @@ namespace tp {
 size_t tsvd_ws(int64_t n1, int64_t n2, int64_t n3);
 bool fft_supported(int64_t n3);
 size_t rsvd_ws(int64_t n1, int64_t n2, int64_t n3, int64_t k, int64_t p);
+size_t svt_ws(int64_t n1, int64_t n2, int64_t n3);
+int svt_run(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t n3, int iters,
+            double rho, double mu_max, float* L, float* E, float* Y, double* mu,
+            const tp_opts* opts, cudaStream_t st);
+size_t tcx_ws(int64_t n1, int64_t n2, int64_t n3);
+int tcx_run(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, uint64_t seed,
+            int prob_mode, const double* p_given, float* Z, int32_t* idx_out, int64_t* count_out,
+            const tp_opts* opts, cudaStream_t st);
 int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, int q,
              uint64_t seed, float* U, float* S, float* V, const tp_opts* opts, cudaStream_t st);
 int tsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, float* U, float* S, float* V,
@@ -14,6 +22,8 @@ size_t workspace_for(int op, const int64_t* d, int nd) {
   switch (op) {
     case TP_OP_TSVD: return nd >= 3 ? tsvd_ws(d[0], d[1], d[2]) : 0;
     case TP_OP_TSVD_RANDOMIZED: return nd >= 5 ? rsvd_ws(d[0], d[1], d[2], d[3], d[4]) : 0;
+    case TP_OP_TCOMPLETE_SVT: return nd >= 3 ? svt_ws(d[0], d[1], d[2]) : 0;
+    case TP_OP_TCX: return nd >= 3 ? tcx_ws(d[0], d[1], d[2]) : 0;
     default: return 0;
   }
 }
@@ -57,9 +67,39 @@ int tsvd_randomized(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, i
   }
   return rsvd_run(X, n1, n2, n3, k, p, q, seed, U, S, V, opts, as_stream(stream));
 }
-int tcomplete_svt(const float*, const uint8_t*, int64_t, int64_t, int64_t, int, double, double,
-                  float*, float*, float*, double*, const tp_opts*, void*) {
-  set_error("tcomplete_svt: not built yet");
-  return TP_EUNSUPPORTED;
+int tcomplete_svt(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t n3,
+                  int iters, double rho, double mu_max, float* L, float* E, float* Y, double* mu,
+                  const tp_opts* opts, void* stream) {
+  if (!X || !mask || !L || !E || !Y || !mu) { set_error("tcomplete_svt: NULL pointer"); return TP_ENULL; }
+  if (!dims3_ok(n1, n2, n3) || iters < 0 || !(rho > 0.0) || !(mu_max > 0.0)) {
+    set_error("tcomplete_svt: invalid sizes or constants");
+    return TP_EINVAL;
+  }
+  const int64_t m = n1 < n2 ? n1 : n2;
+  if (m > 512) { set_error("tcomplete_svt: min(n1, n2) > 512 not supported"); return TP_EUNSUPPORTED; }
+  if (n3 > 512 && !fft_supported(n3)) {
+    set_error("tcomplete_svt: n3 > 512 must factor into radices 2..13");
+    return TP_EUNSUPPORTED;
+  }
+  return svt_run(X, mask, n1, n2, n3, iters, rho, mu_max, L, E, Y, mu, opts, as_stream(stream));
+}
+
+int tcx(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, uint64_t seed,
+        int prob_mode, const double* p_given, float* Z, int32_t* idx_out, int64_t* count_out,
+        const tp_opts* opts, void* stream) {
+  if (!A || !Z) { set_error("tcx: NULL tensor"); return TP_ENULL; }
+  if (!dims3_ok(n1, n2, n3) || c < 1) { set_error("tcx: invalid sizes"); return TP_EINVAL; }
+  if (prob_mode != TP_PROB_A2 && prob_mode != TP_PROB_GIVEN) {
+    set_error("tcx: prob_mode must be TP_PROB_A2 or TP_PROB_GIVEN");
+    return TP_EINVAL;
+  }
+  if (prob_mode == TP_PROB_GIVEN && !p_given) { set_error("tcx: TP_PROB_GIVEN needs p_given"); return TP_ENULL; }
+  if ((n1 < n2 ? n1 : n2) > 512 || n2 > 4096) {
+    set_error("tcx: needs min(n1, n2) <= 512 and n2 <= 4096");
+    return TP_EUNSUPPORTED;
+  }
+  if (n3 > 512) { set_error("tcx: n3 > 512 not supported (the gathered transform is direct)"); return TP_EUNSUPPORTED; }
+  return tcx_run(A, n1, n2, n3, c, seed, prob_mode, p_given, Z, idx_out, count_out, opts,
+                 as_stream(stream));
 }
 }
