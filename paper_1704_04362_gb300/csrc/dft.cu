@@ -2,23 +2,31 @@
 // (Section 2, "Operators": fft(X,[],3) / ifft(X,[],3); Algorithm 1 steps 2-3
 // and the final inverse).
 //
-// Both directions are small dense contractions per tube (n3 x h complex
-// coefficients), computed as register-blocked SIMT products: each thread owns
-// TPT tubes and KC output frequencies (or times) at a time, and the KC
-// columns of the transform matrix it needs are built once per block and
-// chunk in shared memory from the n3-entry twiddle table
-// exp(-2 pi i m / n3), m = k*t mod n3.  Tube samples are read straight from
-// global memory (coalesced across the warp; L1 serves the re-reads of later
-// chunks).
+// Both directions are small dense contractions per tube, computed as
+// register-blocked SIMT products.  The t <-> n3 - t symmetry halves them:
+// with e_t = x_t + x_{n3-t} and o_t = x_t - x_{n3-t} (t = 1 .. n3/2; e_0 = x_0
+// and, for even n3, e_{n3/2} = x_{n3/2}, o = 0 there),
+//     Re X_k = sum_{t <= n3/2} e_t cos(2 pi k t / n3),
+//     Im X_k = -sum_{t <= n3/2} o_t sin(2 pi k t / n3);
+// and for the inverse, with P_t = sum_k w_k Re X_k cos, Q_t = sum_k w_k Im X_k sin
+// (w_k = 1/n3 at k = 0 and k = n3/2, else 2/n3), x_t = P_t - Q_t and
+// x_{n3-t} = P_t + Q_t.  Each thread owns TPT tubes and KC frequencies (or
+// output times) per chunk; the KC columns of the transform matrix a chunk
+// needs are built once per block in shared memory from the n3-entry twiddle
+// table exp(-2 pi i m / n3), m = k t mod n3.  KC is chosen per call to
+// minimise padding.
 #include "tp_internal.cuh"
 
 namespace tp {
 namespace {
 
-constexpr int KC = 16;   // frequencies (forward) or times (inverse) per chunk
-constexpr int TPT = 2;   // tubes per thread
-constexpr int RB = 128;  // threads per block
-constexpr int TU = 8;    // samples (forward) or frequencies (inverse) loaded ahead
+#ifndef TP_DFT_TPT
+#define TP_DFT_TPT 2
+#endif
+constexpr int TPT = TP_DFT_TPT;  // tubes per thread
+constexpr int RB = 128;          // threads per block
+constexpr int TU = 8;            // samples (forward) or frequencies (inverse) loaded ahead
+constexpr int STAGE_BYTES_MAX = 64 * 1024;
 
 // Nearest tf32 value of x (10 explicit mantissa bits), as a float.
 __device__ __forceinline__ float tf32_rna(float x) {
@@ -35,108 +43,150 @@ __device__ __forceinline__ void build_twiddles(float2* tw, int n3) {
   }
 }
 
-__global__ void __launch_bounds__(RB) rdft_kernel(DftGather g) {
+// Folded pair (e_t, o_t) of one tube; t <= n3/2.
+__device__ __forceinline__ void fold(float x0, float x1, int t, int n3, float& e, float& o) {
+  if (t == 0 || 2 * t == n3) {
+    e = x0;
+    o = 0.f;
+  } else {
+    e = x0 + x1;
+    o = x0 - x1;
+  }
+}
+
+struct Extent {
+  int64_t rows_eff, cols_eff, rows_pad, cols_pad;
+};
+__device__ __forceinline__ Extent extent_of(const DftGather& g) {
+  const int64_t count = g.dyn_count ? *g.dyn_count : (g.gather_dim == 1 ? g.rows : g.cols);
+  Extent x{g.rows, g.cols, g.rows, g.cols};
+  if (g.gather_dim == 1) {
+    x.rows_eff = count;
+    x.rows_pad = min(g.rows, (count + 31) / 32 * 32);   // zero tail for tiled consumers
+  } else if (g.gather_dim == 2) {
+    x.cols_eff = count;
+    x.cols_pad = min(g.cols, (count + 31) / 32 * 32);
+  }
+  return x;
+}
+
+__device__ __forceinline__ const float* tube_ptr(const DftGather& g, const Extent& x, int64_t r,
+                                                 int64_t c, float& s) {
+  s = 0.f;
+  if (r >= x.rows_eff || c >= x.cols_eff) return nullptr;
+  int64_t ro = r, co = c;
+  s = 1.0f;
+  if (g.gather_dim == 1) {
+    ro = g.idx[r];
+    if (g.scale) s = g.scale[r];
+  } else if (g.gather_dim == 2) {
+    co = g.idx[c];
+    if (g.scale) s = g.scale[c];
+  }
+  return g.src + ro * g.row_stride + co * g.col_stride;
+}
+
+// Wc[t*KC + q] = (cos, sin)(2 pi (k0+q) t / n3) for t <= nh, zero above.
+template <int KC>
+__device__ __forceinline__ void build_fwd_cols(float2* Wc, const float2* tw, int n3, int nh,
+                                               int nhp, int k0) {
+  for (int e = threadIdx.x; e < nhp * KC; e += blockDim.x) {
+    const int t = e / KC, q = e - t * KC;
+    Wc[e] = t <= nh ? tw[int((int64_t(k0 + q) * t) % n3)] : make_float2(0.f, 0.f);
+  }
+}
+
+template <int KC>
+__global__ void __launch_bounds__(RB) rdft_kernel(DftGather g, int stage) {
   extern __shared__ float2 sm2[];
   const int n3 = int(g.n3);
-  const int h = n3 / 2 + 1;
-  const int n3p = (n3 + TU - 1) / TU * TU;
+  const int h = n3 / 2 + 1, nh = n3 / 2;
+  const int nhp = (nh + 1 + TU - 1) / TU * TU;
   float2* tw = sm2;
-  float2* Wc = sm2 + n3;   // Wc[t*KC + q] = tw[(k0+q)*t mod n3], zero for t >= n3
+  float2* Wc = sm2 + n3;
+  float* xs = reinterpret_cast<float*>(Wc + nhp * KC);   // staging [n3][RB*TPT] when stage
   build_twiddles(tw, n3);
-
-  const int64_t count = g.dyn_count ? *g.dyn_count : (g.gather_dim == 1 ? g.rows : g.cols);
-  int64_t rows_eff = g.rows, cols_eff = g.cols, rows_pad = g.rows, cols_pad = g.cols;
-  if (g.gather_dim == 1) {
-    rows_eff = count;
-    rows_pad = min(g.rows, (count + 31) / 32 * 32);   // zero tail for tiled consumers
-  } else if (g.gather_dim == 2) {
-    cols_eff = count;
-    cols_pad = min(g.cols, (count + 31) / 32 * 32);
-  }
+  const Extent ex = extent_of(g);
   const int64_t base = int64_t(blockIdx.x) * (RB * TPT);
-  if (base >= rows_pad) return;   // uniform over the block
+  if (base >= ex.rows_pad) return;   // uniform over the block
   const int tid = threadIdx.x;
 
-  for (int64_t c = blockIdx.y; c < cols_pad; c += gridDim.y) {
+  for (int64_t c = blockIdx.y; c < ex.cols_pad; c += gridDim.y) {
     const float* p[TPT];
     float s[TPT];
     bool act[TPT];
 #pragma unroll
     for (int j = 0; j < TPT; ++j) {
       const int64_t r = base + j * RB + tid;
-      act[j] = r < rows_pad;
-      p[j] = nullptr;
-      s[j] = 0.f;
-      if (act[j] && r < rows_eff && c < cols_eff) {
-        int64_t ro = r, co = c;
-        s[j] = 1.0f;
-        if (g.gather_dim == 1) {
-          ro = g.idx[r];
-          if (g.scale) s[j] = g.scale[r];
-        } else if (g.gather_dim == 2) {
-          co = g.idx[c];
-          if (g.scale) s[j] = g.scale[c];
-        }
-        p[j] = g.src + ro * g.row_stride + co * g.col_stride;
-      }
+      act[j] = r < ex.rows_pad;
+      p[j] = act[j] ? tube_ptr(g, ex, r, c, s[j]) : nullptr;
+    }
+    if (stage) {
+      // every sample of this thread's tubes, read once (all loads in flight)
+      for (int t = 0; t < n3; ++t)
+#pragma unroll
+        for (int j = 0; j < TPT; ++j)
+          xs[t * (RB * TPT) + j * RB + tid] =
+              p[j] ? s[j] * __ldg(p[j] + int64_t(t) * g.slice_stride) : 0.f;
     }
     for (int k0 = 0; k0 < h; k0 += KC) {
-      __syncthreads();   // previous chunk done with Wc (and tw built)
-      for (int e = tid; e < n3p * KC; e += RB) {
-        const int t = e / KC, q = e - t * KC;
-        Wc[e] = t < n3 ? tw[int((int64_t(k0 + q) * t) % n3)] : make_float2(0.f, 0.f);
-      }
+      __syncthreads();
+      build_fwd_cols<KC>(Wc, tw, n3, nh, nhp, k0);
       __syncthreads();
       float ar[TPT][KC], ai[TPT][KC];
 #pragma unroll
       for (int j = 0; j < TPT; ++j)
 #pragma unroll
         for (int q = 0; q < KC; ++q) { ar[j][q] = 0.f; ai[j][q] = 0.f; }
-      for (int t0 = 0; t0 < n3; t0 += TU) {
-        // all TU samples of both tubes in flight before the arithmetic
-        float x[TPT][TU];
+      for (int t0 = 0; t0 <= nh; t0 += TU) {
+        float ev[TPT][TU], ov[TPT][TU];
 #pragma unroll
         for (int u = 0; u < TU; ++u)
 #pragma unroll
-          for (int j = 0; j < TPT; ++j)
-            x[j][u] = (p[j] && t0 + u < n3) ? s[j] * __ldg(p[j] + int64_t(t0 + u) * g.slice_stride)
-                                            : 0.f;
+          for (int j = 0; j < TPT; ++j) {
+            const int t = t0 + u;
+            float x0 = 0.f, x1 = 0.f;
+            if (t <= nh) {
+              if (stage) {
+                x0 = xs[t * (RB * TPT) + j * RB + tid];
+                x1 = xs[((n3 - t) % n3) * (RB * TPT) + j * RB + tid];
+              } else if (p[j]) {
+                x0 = s[j] * __ldg(p[j] + int64_t(t) * g.slice_stride);
+                if (t > 0 && 2 * t != n3)
+                  x1 = s[j] * __ldg(p[j] + int64_t(n3 - t) * g.slice_stride);
+              }
+            }
+            fold(x0, x1, t, n3, ev[j][u], ov[j][u]);
+          }
 #pragma unroll
-        for (int u = 0; u < TU; ++u) {
+        for (int u = 0; u < TU; ++u)
 #pragma unroll
           for (int q = 0; q < KC; ++q) {
-            const float2 w = Wc[(t0 + u) * KC + q];   // zero rows past n3
+            const float2 w = Wc[(t0 + u) * KC + q];   // zero rows past nh
 #pragma unroll
             for (int j = 0; j < TPT; ++j) {
-              ar[j][q] = fmaf(x[j][u], w.x, ar[j][q]);
-              ai[j][q] = fmaf(-x[j][u], w.y, ai[j][q]);
+              ar[j][q] = fmaf(ev[j][u], w.x, ar[j][q]);
+              ai[j][q] = fmaf(-ov[j][u], w.y, ai[j][q]);
             }
           }
-        }
       }
 #pragma unroll
       for (int j = 0; j < TPT; ++j) {
         if (!act[j]) continue;
-        const int64_t r = base + j * RB + tid;
-        const int64_t o = r + g.out_ld * c;
-        if (g.out_re_lo) {
+        const int64_t o = base + j * RB + tid + g.out_ld * c;
 #pragma unroll
-          for (int q = 0; q < KC; ++q) {
-            if (k0 + q < h) {
-              const int64_t oo = o + int64_t(k0 + q) * g.out_slice;
+        for (int q = 0; q < KC; ++q) {
+          if (k0 + q < h) {
+            const int64_t oo = o + int64_t(k0 + q) * g.out_slice;
+            if (g.out_re_lo) {
               const float hr = tf32_rna(ar[j][q]), hi = tf32_rna(ai[j][q]);
               g.out_re[oo] = hr;
               g.out_re_lo[oo] = ar[j][q] - hr;
               g.out_im[oo] = hi;
               g.out_im_lo[oo] = ai[j][q] - hi;
-            }
-          }
-        } else {
-#pragma unroll
-          for (int q = 0; q < KC; ++q) {
-            if (k0 + q < h) {
-              g.out_re[o + int64_t(k0 + q) * g.out_slice] = ar[j][q];
-              g.out_im[o + int64_t(k0 + q) * g.out_slice] = ai[j][q];
+            } else {
+              g.out_re[oo] = ar[j][q];
+              g.out_im[oo] = ai[j][q];
             }
           }
         }
@@ -150,55 +200,34 @@ __global__ void __launch_bounds__(RB) rdft_kernel(DftGather g) {
 // facewise product's inner dimension) is contiguous.  A block owns a tile of
 // 32 rows x 8 columns (rows fastest, so tube reads stay coalesced); each
 // frequency chunk is staged through shared memory and stored as 32-byte runs
-// along the column index.
+// along the column index.  This kernel runs the plain (unfolded) contraction:
+// the folded form's extra live registers cost more occupancy than the
+// arithmetic it saves here.
 constexpr int TR = 32, TCOL = 8;
+constexpr int TPTT = TCOL / (RB / TR);   // columns per thread in the transposed kernel (2)
 
+template <int KC>
 __global__ void __launch_bounds__(RB) rdft_t_kernel(DftGather g) {
   extern __shared__ float2 sm2[];
   const int n3 = int(g.n3);
   const int h = n3 / 2 + 1;
   const int n3p = (n3 + TU - 1) / TU * TU;
   float2* tw = sm2;
-  float2* Wc = sm2 + n3;
+  float2* Wc = sm2 + n3;   // Wc[t*KC + q] = tw[(k0+q) t mod n3], zero for t >= n3
   float* stg = reinterpret_cast<float*>(Wc + n3p * KC);   // [KC][TR][TCOL + 1]
   build_twiddles(tw, n3);
-
-  const int64_t count = g.dyn_count ? *g.dyn_count : (g.gather_dim == 1 ? g.rows : g.cols);
-  int64_t rows_eff = g.rows, cols_eff = g.cols, rows_pad = g.rows, cols_pad = g.cols;
-  if (g.gather_dim == 1) {
-    rows_eff = count;
-    rows_pad = min(g.rows, (count + 31) / 32 * 32);
-  } else if (g.gather_dim == 2) {
-    cols_eff = count;
-    cols_pad = min(g.cols, (count + 31) / 32 * 32);
-  }
+  const Extent ex = extent_of(g);
   const int64_t r0 = int64_t(blockIdx.x) * TR;
-  if (r0 >= rows_pad) return;   // uniform over the block
+  if (r0 >= ex.rows_pad) return;   // uniform over the block
   const int tid = threadIdx.x;
   const int lr = tid % TR, lc = tid / TR;   // this thread: row lr, columns lc and lc + 4
   const int64_t r = r0 + lr;
 
-  for (int64_t c0 = int64_t(blockIdx.y) * TCOL; c0 < cols_pad; c0 += int64_t(gridDim.y) * TCOL) {
-    const float* p[TPT];
-    float s[TPT];
+  for (int64_t c0 = int64_t(blockIdx.y) * TCOL; c0 < ex.cols_pad; c0 += int64_t(gridDim.y) * TCOL) {
+    const float* p[TPTT];
+    float s[TPTT];
 #pragma unroll
-    for (int j = 0; j < TPT; ++j) {
-      const int64_t c = c0 + lc + 4 * j;
-      p[j] = nullptr;
-      s[j] = 0.f;
-      if (r < rows_eff && c < cols_eff) {
-        int64_t ro = r, co = c;
-        s[j] = 1.0f;
-        if (g.gather_dim == 1) {
-          ro = g.idx[r];
-          if (g.scale) s[j] = g.scale[r];
-        } else if (g.gather_dim == 2) {
-          co = g.idx[c];
-          if (g.scale) s[j] = g.scale[c];
-        }
-        p[j] = g.src + ro * g.row_stride + co * g.col_stride;
-      }
-    }
+    for (int j = 0; j < TPTT; ++j) p[j] = tube_ptr(g, ex, r, c0 + lc + 4 * j, s[j]);
     for (int k0 = 0; k0 < h; k0 += KC) {
       __syncthreads();
       for (int e = tid; e < n3p * KC; e += RB) {
@@ -206,39 +235,37 @@ __global__ void __launch_bounds__(RB) rdft_t_kernel(DftGather g) {
         Wc[e] = t < n3 ? tw[int((int64_t(k0 + q) * t) % n3)] : make_float2(0.f, 0.f);
       }
       __syncthreads();
-      float ar[TPT][KC], ai[TPT][KC];
+      float ar[TPTT][KC], ai[TPTT][KC];
 #pragma unroll
-      for (int j = 0; j < TPT; ++j)
+      for (int j = 0; j < TPTT; ++j)
 #pragma unroll
         for (int q = 0; q < KC; ++q) { ar[j][q] = 0.f; ai[j][q] = 0.f; }
       for (int t0 = 0; t0 < n3; t0 += TU) {
-        // all TU samples of both tubes in flight before the arithmetic
-        float x[TPT][TU];
+        float x[TPTT][TU];
 #pragma unroll
         for (int u = 0; u < TU; ++u)
 #pragma unroll
-          for (int j = 0; j < TPT; ++j)
+          for (int j = 0; j < TPTT; ++j)
             x[j][u] = (p[j] && t0 + u < n3) ? s[j] * __ldg(p[j] + int64_t(t0 + u) * g.slice_stride)
                                             : 0.f;
 #pragma unroll
-        for (int u = 0; u < TU; ++u) {
+        for (int u = 0; u < TU; ++u)
 #pragma unroll
           for (int q = 0; q < KC; ++q) {
-            const float2 w = Wc[(t0 + u) * KC + q];   // zero rows past n3
+            const float2 w = Wc[(t0 + u) * KC + q];
 #pragma unroll
-            for (int j = 0; j < TPT; ++j) {
+            for (int j = 0; j < TPTT; ++j) {
               ar[j][q] = fmaf(x[j][u], w.x, ar[j][q]);
               ai[j][q] = fmaf(-x[j][u], w.y, ai[j][q]);
             }
           }
-        }
       }
       // planes: 0 re (hi), 1 im (hi), 2 re lo, 3 im lo
       const int nplanes = g.out_re_lo ? 4 : 2;
       for (int pl = 0; pl < nplanes; ++pl) {
         __syncthreads();   // staging buffer free
 #pragma unroll
-        for (int j = 0; j < TPT; ++j)
+        for (int j = 0; j < TPTT; ++j)
 #pragma unroll
           for (int q = 0; q < KC; ++q) {
             const float v = (pl & 1) ? ai[j][q] : ar[j][q];
@@ -253,13 +280,13 @@ __global__ void __launch_bounds__(RB) rdft_t_kernel(DftGather g) {
         // thread -> (column wc, row wr); 16 rows per pass, two passes
         const int wc = tid % TCOL, wr = tid / TCOL;
         const int64_t c = c0 + wc;
-        if (c < cols_pad) {
+        if (c < ex.cols_pad) {
           for (int q = 0; q < KC && k0 + q < h; ++q) {
 #pragma unroll
             for (int pass = 0; pass < TR / (RB / TCOL); ++pass) {
               const int rr = wr + pass * (RB / TCOL);
               const int64_t rg = r0 + rr;
-              if (rg < rows_pad)
+              if (rg < ex.rows_pad)
                 dst[int64_t(k0 + q) * g.out_slice + c + g.out_ld * rg] =
                     stg[(q * TR + rr) * (TCOL + 1) + wc];
             }
@@ -270,17 +297,17 @@ __global__ void __launch_bounds__(RB) rdft_t_kernel(DftGather g) {
   }
 }
 
-// out[r + rows*t] = sum_k (w_k/n3) (Re X_k cos(2 pi k t/n3) - Im X_k sin(2 pi k t/n3)),
-// w_k = 1 for k = 0 and k = n3/2, else 2 (conjugate partners folded in).
+// Inverse: x_t = P_t - Q_t, x_{n3-t} = P_t + Q_t over output-time chunks t <= n3/2.
+template <int KC>
 __global__ void __launch_bounds__(RB) irdft_kernel(const float* __restrict__ in_re,
                                                    const float* __restrict__ in_im, int64_t rows,
                                                    int64_t in_slice, int n3,
                                                    float* __restrict__ out) {
   extern __shared__ float2 sm2[];
-  const int h = n3 / 2 + 1;
+  const int h = n3 / 2 + 1, nh = n3 / 2;
   const int hp = (h + TU - 1) / TU * TU;
   float2* tw = sm2;
-  float2* Vc = sm2 + n3;   // Vc[k*KC + q] = (w_k/n3) tw[k*(t0+q) mod n3], zero for k >= h
+  float2* Vc = sm2 + n3;   // Vc[k*KC + q] = (w_k/n3) tw[k*(t0+q) mod n3], zero past h or nh
   build_twiddles(tw, n3);
   const int tid = threadIdx.x;
   const float inv = 1.0f / float(n3);
@@ -289,53 +316,129 @@ __global__ void __launch_bounds__(RB) irdft_kernel(const float* __restrict__ in_
     int64_t r[TPT];
 #pragma unroll
     for (int j = 0; j < TPT; ++j) r[j] = base + j * RB + tid;
-    for (int t0 = 0; t0 < n3; t0 += KC) {
+    for (int t0 = 0; t0 <= nh; t0 += KC) {
       __syncthreads();
       for (int e = tid; e < hp * KC; e += RB) {
         const int k = e / KC, q = e - k * KC;
-        if (k < h) {
+        const int t = t0 + q;
+        if (k < h && t <= nh) {
           const float wk = (k == 0 || 2 * k == n3) ? inv : 2.0f * inv;
-          const float2 w = tw[int((int64_t(k) * (t0 + q)) % n3)];
+          const float2 w = tw[int((int64_t(k) * t) % n3)];
           Vc[e] = make_float2(wk * w.x, wk * w.y);
         } else {
           Vc[e] = make_float2(0.f, 0.f);
         }
       }
       __syncthreads();
-      float acc[TPT][KC];
+      float P[TPT][KC], Q[TPT][KC];
 #pragma unroll
       for (int j = 0; j < TPT; ++j)
 #pragma unroll
-        for (int q = 0; q < KC; ++q) acc[j][q] = 0.f;
+        for (int q = 0; q < KC; ++q) { P[j][q] = 0.f; Q[j][q] = 0.f; }
       for (int k0 = 0; k0 < h; k0 += TU) {
         float re[TPT][TU], im[TPT][TU];
 #pragma unroll
         for (int u = 0; u < TU; ++u)
 #pragma unroll
           for (int j = 0; j < TPT; ++j) {
-            const bool ok = r[j] < rows && k0 + u < h;
-            re[j][u] = ok ? __ldg(in_re + int64_t(k0 + u) * in_slice + r[j]) : 0.f;
-            im[j][u] = ok ? __ldg(in_im + int64_t(k0 + u) * in_slice + r[j]) : 0.f;
+            const int k = k0 + u;
+            const bool ok = r[j] < rows && k < h;
+            re[j][u] = ok ? __ldg(in_re + int64_t(k) * in_slice + r[j]) : 0.f;
+            // the imaginary parts of the real slices are ignored
+            im[j][u] = (ok && k > 0 && 2 * k != n3) ? __ldg(in_im + int64_t(k) * in_slice + r[j])
+                                                    : 0.f;
           }
 #pragma unroll
         for (int u = 0; u < TU; ++u)
 #pragma unroll
           for (int q = 0; q < KC; ++q) {
-            const float2 v = Vc[(k0 + u) * KC + q];   // zero rows past h
+            const float2 v = Vc[(k0 + u) * KC + q];
 #pragma unroll
-            for (int j = 0; j < TPT; ++j)
-              acc[j][q] = fmaf(re[j][u], v.x, fmaf(-im[j][u], v.y, acc[j][q]));
+            for (int j = 0; j < TPT; ++j) {
+              P[j][q] = fmaf(re[j][u], v.x, P[j][q]);
+              Q[j][q] = fmaf(im[j][u], v.y, Q[j][q]);
+            }
           }
       }
 #pragma unroll
       for (int j = 0; j < TPT; ++j) {
         if (r[j] >= rows) continue;
 #pragma unroll
-        for (int q = 0; q < KC; ++q)
-          if (t0 + q < n3) out[r[j] + rows * int64_t(t0 + q)] = acc[j][q];
+        for (int q = 0; q < KC; ++q) {
+          const int t = t0 + q;
+          if (t <= nh) {
+            out[r[j] + rows * int64_t(t)] = P[j][q] - Q[j][q];
+            if (t > 0 && n3 - t > nh) out[r[j] + rows * int64_t(n3 - t)] = P[j][q] + Q[j][q];
+          }
+        }
       }
     }
   }
+}
+
+// Chunk size among {16, 12, 8} that pads n the least (ties: larger).
+int pick_kc(int64_t n) {
+  const int cands[3] = {16, 12, 8};
+  int best = 16;
+  int64_t best_cost = -1;
+  for (int kc : cands) {
+    const int64_t cost = (n + kc - 1) / kc * kc;
+    if (best_cost < 0 || cost < best_cost) {
+      best = kc;
+      best_cost = cost;
+    }
+  }
+  return best;
+}
+
+template <int KC>
+int launch_rdft_kc(const DftGather& g, cudaStream_t st) {
+  const int64_t nh = g.n3 / 2;
+  const int64_t nhp = (nh + 1 + TU - 1) / TU * TU;
+  if (g.out_transposed) {
+    const int64_t n3p = (g.n3 + TU - 1) / TU * TU;
+    const size_t smem = size_t(g.n3 + n3p * KC) * sizeof(float2) +
+                        size_t(KC) * TR * (TCOL + 1) * sizeof(float);
+    cudaFuncSetAttribute(rdft_t_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    const int64_t bx = (g.rows + TR - 1) / TR;
+    if (bx > 0x7fffffff) { set_error("rdft: too many rows"); return TP_EINVAL; }
+    int64_t by = (g.cols + TCOL - 1) / TCOL;
+    if (by > 65535) by = 65535;
+    {
+      KernelScope ks("rdft_t", st);
+      rdft_t_kernel<KC><<<dim3(unsigned(bx), unsigned(by)), RB, smem, st>>>(g);
+    }
+    return launch_status("rdft_t_kernel");
+  }
+  // stage the scattered row gathers so that each sample is read once
+  const size_t stage_bytes = size_t(g.n3) * RB * TPT * sizeof(float);
+  const int stage = (g.gather_dim == 1 && stage_bytes <= size_t(STAGE_BYTES_MAX)) ? 1 : 0;
+  const size_t smem = size_t(g.n3 + nhp * KC) * sizeof(float2) + (stage ? stage_bytes : 0);
+  cudaFuncSetAttribute(rdft_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  const int64_t bx = (g.rows + RB * TPT - 1) / (RB * TPT);
+  if (bx > 0x7fffffff) { set_error("rdft: too many rows"); return TP_EINVAL; }
+  const int64_t by = g.cols < 65535 ? g.cols : 65535;
+  {
+    KernelScope ks("rdft", st);
+    rdft_kernel<KC><<<dim3(unsigned(bx), unsigned(by)), RB, smem, st>>>(g, stage);
+  }
+  return launch_status("rdft_kernel");
+}
+
+template <int KC>
+int launch_irdft_kc(const float* in_re, const float* in_im, int64_t rows, int64_t in_slice,
+                    int64_t n3, float* out, cudaStream_t st) {
+  const int64_t h = n3 / 2 + 1;
+  const int64_t hp = (h + TU - 1) / TU * TU;
+  const size_t smem = size_t(n3 + hp * KC) * sizeof(float2);
+  cudaFuncSetAttribute(irdft_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  int64_t blocks = (rows + RB * TPT - 1) / (RB * TPT);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  {
+    KernelScope ks("irdft", st);
+    irdft_kernel<KC><<<unsigned(blocks), RB, smem, st>>>(in_re, in_im, rows, in_slice, int(n3), out);
+  }
+  return launch_status("irdft_kernel");
 }
 
 }  // namespace
@@ -348,7 +451,10 @@ int launch_fft_inv(const float* ire, const float* iim, int64_t rows, int64_t in_
 
 // Tubes longer than this go through the shared-memory FFT when their length
 // factors into small radices and no gather or split output is asked for.
-constexpr int64_t kFftThreshold = 256;
+#ifndef TP_FFT_THRESHOLD
+#define TP_FFT_THRESHOLD 256
+#endif
+constexpr int64_t kFftThreshold = TP_FFT_THRESHOLD;
 
 int launch_rdft(const DftGather& g, cudaStream_t st) {
   const bool plain = g.gather_dim == 0 && !g.out_transposed && !g.out_re_lo &&
@@ -363,32 +469,11 @@ int launch_rdft(const DftGather& g, cudaStream_t st) {
     return TP_EUNSUPPORTED;
   }
   if (g.rows == 0 || g.cols == 0) return TP_OK;
-  if (g.out_transposed) {
-    const int64_t n3p = (g.n3 + TU - 1) / TU * TU;
-    const size_t smem = size_t(g.n3 + n3p * KC) * sizeof(float2) +
-                        size_t(KC) * TR * (TCOL + 1) * sizeof(float);
-    cudaFuncSetAttribute(rdft_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    const int64_t bx = (g.rows + TR - 1) / TR;
-    if (bx > 0x7fffffff) { set_error("rdft: too many rows"); return TP_EINVAL; }
-    int64_t by = (g.cols + TCOL - 1) / TCOL;
-    if (by > 65535) by = 65535;
-    {
-      KernelScope ks("rdft_t", st);
-      rdft_t_kernel<<<dim3(unsigned(bx), unsigned(by)), RB, smem, st>>>(g);
-    }
-    return launch_status("rdft_t_kernel");
+  switch (pick_kc(g.n3 / 2 + 1)) {
+    case 8: return launch_rdft_kc<8>(g, st);
+    case 12: return launch_rdft_kc<12>(g, st);
+    default: return launch_rdft_kc<16>(g, st);
   }
-  const int64_t n3p = (g.n3 + TU - 1) / TU * TU;
-  const size_t smem = size_t(g.n3 + n3p * KC) * sizeof(float2);
-  cudaFuncSetAttribute(rdft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  const int64_t bx = (g.rows + RB * TPT - 1) / (RB * TPT);
-  if (bx > 0x7fffffff) { set_error("rdft: too many rows"); return TP_EINVAL; }
-  const int64_t by = g.cols < 65535 ? g.cols : 65535;
-  {
-    KernelScope ks("rdft", st);
-    rdft_kernel<<<dim3(unsigned(bx), unsigned(by)), RB, smem, st>>>(g);
-  }
-  return launch_status("rdft_kernel");
 }
 
 int launch_irdft(const float* in_re, const float* in_im, int64_t rows, int64_t in_slice,
@@ -400,17 +485,11 @@ int launch_irdft(const float* in_re, const float* in_im, int64_t rows, int64_t i
     return TP_EUNSUPPORTED;
   }
   if (rows == 0) return TP_OK;
-  const int64_t h = n3 / 2 + 1;
-  const int64_t hp = (h + TU - 1) / TU * TU;
-  const size_t smem = size_t(n3 + hp * KC) * sizeof(float2);
-  cudaFuncSetAttribute(irdft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  int64_t blocks = (rows + RB * TPT - 1) / (RB * TPT);
-  if (blocks > 152 * 64) blocks = 152 * 64;
-  {
-    KernelScope ks("irdft", st);
-    irdft_kernel<<<unsigned(blocks), RB, smem, st>>>(in_re, in_im, rows, in_slice, int(n3), out);
+  switch (pick_kc(n3 / 2 + 1)) {
+    case 8: return launch_irdft_kc<8>(in_re, in_im, rows, in_slice, n3, out, st);
+    case 12: return launch_irdft_kc<12>(in_re, in_im, rows, in_slice, n3, out, st);
+    default: return launch_irdft_kc<16>(in_re, in_im, rows, in_slice, n3, out, st);
   }
-  return launch_status("irdft_kernel");
 }
 
 }  // namespace tp

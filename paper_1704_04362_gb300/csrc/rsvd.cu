@@ -206,6 +206,279 @@ __global__ void __launch_bounds__(QR_THREADS) cholqr2_kernel(float* y_re, float*
   }
 }
 
+// ---------------------------------------------------------------- shared-memory forms
+// a*b added to the unevaluated float pair (hi, lo): the product's rounding
+// error comes from the FMA residual, the sum's from Knuth's two-sum, so the
+// pair carries about 44 significant bits at float32 speed.
+__device__ __forceinline__ void acc2(float& hi, float& lo, float a, float b) {
+  const float p = a * b;
+  const float e = fmaf(a, b, -p);
+  const float s = hi + p;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (p - bb);
+  hi = s;
+  lo += err + e;
+}
+
+// G(a, b) = sum_r conj(Y(r, a)) Y(r, b) for a <= b (Hermitian fill), Y in
+// shared memory as float2 column-major p x l; G float64 interleaved.
+__device__ void gram_smem(const float2* __restrict__ Ys, int p, int l, double* G) {
+  const int npairs = l * (l + 1) / 2;
+  for (int e = threadIdx.x; e < npairs; e += blockDim.x) {
+    int a = 0, rem = e;
+    while (rem >= l - a) { rem -= l - a; ++a; }
+    const int b = a + rem;
+    const float2* xa = Ys + a * p;
+    const float2* xb = Ys + b * p;
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    for (int r = 0; r < p; ++r) {
+      const float2 u = xa[r], v = xb[r];
+      acc2(rh, rl, u.x, v.x);
+      acc2(rh, rl, u.y, v.y);
+      acc2(ih, il, u.x, v.y);
+      acc2(ih, il, -u.y, v.x);
+    }
+    const double sr = double(rh) + double(rl), si = double(ih) + double(il);
+    G[2 * (a * l + b)] = sr;
+    G[2 * (a * l + b) + 1] = si;
+    G[2 * (b * l + a)] = sr;
+    G[2 * (b * l + a) + 1] = -si;
+  }
+}
+
+// Inverse of the upper-triangular R (upper triangle of G, float64) into Ri
+// (float32 interleaved, l x l, upper).  One thread per column.
+__device__ void upper_inverse(const double* R, int l, float2* Ri) {
+  for (int j = threadIdx.x; j < l; j += blockDim.x) {
+    // x = R^{-1} e_j by back substitution, kept in Ri's column j
+    for (int i = l - 1; i >= 0; --i) {
+      if (i > j) { Ri[i * l + j] = make_float2(0.f, 0.f); continue; }
+      double sr = (i == j) ? 1.0 : 0.0, si = 0.0;
+      for (int k = i + 1; k <= j; ++k) {
+        const double ar = R[2 * (i * l + k)], ai = R[2 * (i * l + k) + 1];
+        const float2 x = Ri[k * l + j];
+        sr -= ar * x.x - ai * x.y;
+        si -= ar * x.y + ai * x.x;
+      }
+      const double d = R[2 * (i * l + i)];
+      Ri[i * l + j] = make_float2(float(sr / d), float(si / d));
+    }
+  }
+}
+
+// CholeskyQR2 with Y held in shared memory: compensated float32 Gram,
+// float64 Cholesky and triangular inverse, float32 Y R^{-1}.  The second pass
+// restores orthogonality to float32 accuracy (the first pass's float32
+// product leaves an error ~ eps_32 cond(Y)).  Shifted retry as cholqr2_kernel.
+__global__ void __launch_bounds__(QR_THREADS) cholqr2_smem_kernel(float* y_re, float* y_im,
+                                                                  int64_t sY, int p, int l,
+                                                                  int32_t* status) {
+  extern __shared__ double dyn[];
+  double* G = dyn;                                          // 2 l^2 doubles
+  float2* Ri = reinterpret_cast<float2*>(G + 2 * l * l);    // l^2 float2
+  float2* Ys = Ri + l * l;                                  // p l float2
+  __shared__ int fail;
+  float* yr = y_re + int64_t(blockIdx.x) * sY;
+  float* yi = y_im + int64_t(blockIdx.x) * sY;
+  for (int e = threadIdx.x; e < p * l; e += blockDim.x) Ys[e] = make_float2(yr[e], yi[e]);
+  __syncthreads();
+  int passes_left = 2;
+  bool shifted = false;
+  bool ok_all = true;
+  for (int it = 0; it < 4 && passes_left > 0; ++it) {
+    if (threadIdx.x == 0) fail = 0;
+    gram_smem(Ys, p, l, G);
+    __syncthreads();
+    if (shifted) {
+      if (threadIdx.x == 0) {
+        double tr = 0.0;
+        for (int j = 0; j < l; ++j) tr += G[2 * (j * l + j)];
+        const double sft = 11.0 * (double(p) * l + double(l) * (l + 1)) * 1.1102230246251565e-16 * tr;
+        for (int j = 0; j < l; ++j) G[2 * (j * l + j)] += sft;
+      }
+      __syncthreads();
+    }
+    const bool ok = cholesky(G, l, &fail);
+    if (!ok) {
+      if (shifted) {
+        ok_all = false;
+        break;
+      }
+      shifted = true;
+      passes_left = 3;
+      continue;
+    }
+    upper_inverse(G, l, Ri);
+    __syncthreads();
+    // Y <- Y R^{-1}: entry (r, j) = sum_{i <= j} Y(r, i) Ri(i, j); rows of Y
+    // are overwritten in place, one thread per row (all columns)
+    for (int r = threadIdx.x; r < p; r += blockDim.x) {
+      for (int j = l - 1; j >= 0; --j) {   // descending j: Y(r, i <= j) still unmodified
+        float sr = 0.f, si = 0.f;
+        for (int i = 0; i <= j; ++i) {
+          const float2 y = Ys[i * p + r];
+          const float2 w = Ri[i * l + j];
+          sr = fmaf(y.x, w.x, fmaf(-y.y, w.y, sr));
+          si = fmaf(y.x, w.y, fmaf(y.y, w.x, si));
+        }
+        Ys[j * p + r] = make_float2(sr, si);
+      }
+    }
+    __syncthreads();
+    shifted = false;
+    --passes_left;
+  }
+  if (!ok_all && threadIdx.x == 0 && status) atomicOr(status, TP_DEV_BREAKDOWN);
+  __syncthreads();
+  for (int e = threadIdx.x; e < p * l; e += blockDim.x) {
+    yr[e] = Ys[e].x;
+    yi[e] = Ys[e].y;
+  }
+}
+
+// Core SVD through the l x l Gram of B^H (n2 x l, shared memory):
+// G = B B^H = W diag(s^2) W^H by the cyclic two-sided Jacobi method in
+// float64 (disjoint round-robin pairs per step: parameters, then all row
+// rotations, then all column rotations and the eigenvector update).  The top
+// k eigenpairs give W_k (left singular vectors of B), S = sqrt of the
+// eigenvalues, and V_k = B^H W_k S^{-1}.
+__global__ void __launch_bounds__(QR_THREADS) core_eig_kernel(
+    const float* __restrict__ bh_re, const float* __restrict__ bh_im, int p, int l, int k,
+    int max_sweeps, float* __restrict__ wkr, float* __restrict__ wki, float* __restrict__ vkr,
+    float* __restrict__ vki, float* __restrict__ sr_out, float* __restrict__ si_out,
+    int32_t* status) {
+  extern __shared__ double dyn[];
+  double2* G = reinterpret_cast<double2*>(dyn);             // l x l row-major
+  double2* W = G + l * l;                                   // l x l, columns = eigenvectors
+  float2* Bs = reinterpret_cast<float2*>(W + l * l);        // p x l column-major
+  double* rot = reinterpret_cast<double*>(Bs + p * l);      // per pair: c, s, er, ei
+  int* pq = reinterpret_cast<int*>(rot + 4 * ((l + 1) / 2));
+  __shared__ int rotated;
+  __shared__ int order[128];
+  const int64_t f = blockIdx.x;
+  const float* br = bh_re + f * int64_t(p) * l;
+  const float* bi = bh_im + f * int64_t(p) * l;
+  for (int e = threadIdx.x; e < p * l; e += blockDim.x) Bs[e] = make_float2(br[e], bi[e]);
+  __syncthreads();
+  gram_smem(Bs, p, l, reinterpret_cast<double*>(G));
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x)
+    W[e] = make_double2((e / l == e % l) ? 1.0 : 0.0, 0.0);
+  __syncthreads();
+  const int ll = l + (l & 1), npairs = ll / 2;
+  const double tol = 1e-14;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int step = 0; step < ll - 1; ++step) {
+      for (int i = threadIdx.x; i < npairs; i += blockDim.x) {
+        int a, b;
+        if (i == 0) { a = ll - 1; b = step; }
+        else { a = (step + i) % (ll - 1); b = (step - i + (ll - 1)) % (ll - 1); }
+        if (a > b) { const int t = a; a = b; b = t; }
+        pq[2 * i] = a;
+        pq[2 * i + 1] = b;
+        double cs = 1.0, sn = 0.0, er = 1.0, ei = 0.0;
+        bool act = false;
+        if (b < l) {
+          const double al = G[a * l + a].x, be = G[b * l + b].x;
+          const double2 ga = G[a * l + b];
+          const double g = sqrt(ga.x * ga.x + ga.y * ga.y);
+          if (g > tol * sqrt(fabs(al * be)) && g > 0.0) {
+            act = true;
+            const double zeta = (be - al) / (2.0 * g);
+            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            cs = 1.0 / sqrt(1.0 + t * t);
+            sn = cs * t;
+            er = ga.x / g;
+            ei = -ga.y / g;   // e^{-i phi}
+          }
+        }
+        rot[4 * i] = act ? cs : 1.0;
+        rot[4 * i + 1] = act ? sn : 0.0;
+        rot[4 * i + 2] = er;
+        rot[4 * i + 3] = ei;
+        if (act) rotated = 1;
+      }
+      __syncthreads();
+      // rows: row_a' = c row_a - s e^{i phi} row_b ; row_b' = s row_a + c e^{i phi} row_b
+      for (int e = threadIdx.x; e < npairs * l; e += blockDim.x) {
+        const int i = e / l, j = e - i * l;
+        const int a = pq[2 * i], b = pq[2 * i + 1];
+        if (b >= l || rot[4 * i + 1] == 0.0) continue;
+        const double c = rot[4 * i], s = rot[4 * i + 1], er = rot[4 * i + 2], ei = -rot[4 * i + 3];
+        const double2 x = G[a * l + j], y = G[b * l + j];
+        const double yr = y.x * er - y.y * ei, yi = y.x * ei + y.y * er;   // e^{i phi} y
+        G[a * l + j] = make_double2(c * x.x - s * yr, c * x.y - s * yi);
+        G[b * l + j] = make_double2(s * x.x + c * yr, s * x.y + c * yi);
+      }
+      __syncthreads();
+      // columns of G and W: col_a' = c col_a - s e^{-i phi} col_b ; col_b' = s col_a + c e^{-i phi} col_b
+      for (int e = threadIdx.x; e < 2 * npairs * l; e += blockDim.x) {
+        const int which = e / (npairs * l), rest = e - which * npairs * l;
+        const int i = rest / l, j = rest - i * l;
+        const int a = pq[2 * i], b = pq[2 * i + 1];
+        if (b >= l || rot[4 * i + 1] == 0.0) continue;
+        const double c = rot[4 * i], s = rot[4 * i + 1], er = rot[4 * i + 2], ei = rot[4 * i + 3];
+        double2* M = which ? W : G;
+        const double2 x = M[j * l + a], y = M[j * l + b];
+        const double yr = y.x * er - y.y * ei, yi = y.x * ei + y.y * er;   // e^{-i phi} y
+        M[j * l + a] = make_double2(c * x.x - s * yr, c * x.y - s * yi);
+        M[j * l + b] = make_double2(s * x.x + c * yr, s * x.y + c * yi);
+      }
+      __syncthreads();
+    }
+    const int any = rotated;
+    __syncthreads();
+    if (!any) break;
+  }
+  if (sweep >= max_sweeps && threadIdx.x == 0 && status) atomicOr(status, TP_DEV_NOCONV);
+  // sort eigenvalues descending
+  for (int j = threadIdx.x; j < l; j += blockDim.x) {
+    const double lj = G[j * l + j].x;
+    int rank = 0;
+    for (int m = 0; m < l; ++m) {
+      const double lm = G[m * l + m].x;
+      rank += (lm > lj) || (lm == lj && m < j);
+    }
+    order[rank] = j;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < l * k; e += blockDim.x) {
+    const int i = e % l, c = e / l;
+    const double2 w = W[i * l + order[c]];
+    wkr[f * l * k + e] = float(w.x);
+    wki[f * l * k + e] = float(w.y);
+  }
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int i = e % k, c = e / k;
+    const double lam = G[order[c] * l + order[c]].x;
+    sr_out[f * k * k + e] = (i == c) ? float(sqrt(fmax(lam, 0.0))) : 0.f;
+    si_out[f * k * k + e] = 0.f;
+  }
+  // V_k = B^H W_k S^{-1}
+  for (int64_t e = threadIdx.x; e < int64_t(p) * k; e += blockDim.x) {
+    const int r = int(e % p), c = int(e / p);
+    const int j = order[c];
+    const double lam = G[j * l + j].x;
+    const double sg = sqrt(fmax(lam, 0.0));
+    float vr = 0.f, vi = 0.f;
+    if (sg > 0.0) {
+      for (int m = 0; m < l; ++m) {
+        const float2 b = Bs[m * p + r];
+        const double2 w = W[m * l + j];
+        vr = fmaf(b.x, float(w.x), fmaf(-b.y, float(w.y), vr));
+        vi = fmaf(b.x, float(w.y), fmaf(b.y, float(w.x), vi));
+      }
+      const float inv = float(1.0 / sg);
+      vr *= inv;
+      vi *= inv;
+    }
+    vkr[f * int64_t(p) * k + e] = vr;
+    vki[f * int64_t(p) * k + e] = vi;
+  }
+}
+
 // Sorts the l Jacobi singular triplets of every slice, keeps the top k and
 // writes: Wk (l x k, float32 planar; right factor of the small problem, the
 // columns of W), Vk (n2 x k, float32; left singular vectors of B^H = right
@@ -339,8 +612,16 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
   };
   const size_t qr_smem = size_t(2) * l * l * sizeof(double);
   cudaFuncSetAttribute(cholqr2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(qr_smem));
+  constexpr size_t kSmemCap = 200 * 1024;
   auto orth = [&](float* yr, float* yi, int64_t rows) {
-    {
+    const size_t fast_smem = size_t(l) * l * (16 + 8) + size_t(rows) * l * 8;
+    if (fast_smem <= kSmemCap) {
+      cudaFuncSetAttribute(cholqr2_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(fast_smem));
+      KernelScope ks("cholqr2", st);
+      cholqr2_smem_kernel<<<unsigned(h), QR_THREADS, fast_smem, st>>>(yr, yi, rows * l, int(rows),
+                                                                     int(l), status);
+    } else {
       KernelScope ks("cholqr2", st);
       cholqr2_kernel<<<unsigned(h), QR_THREADS, qr_smem, st>>>(yr, yi, rows * l, int(rows),
                                                                int(l), status);
@@ -357,6 +638,18 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
     if ((rc = orth(Yr, Yi, n1))) return rc;
   }
   if ((rc = gemm(Hr, Hi, n2, n1, Yr, Yi, l, Zr, Zi))) return rc;     // B^H = X_hat^H Q
+  const int sweeps = (opts && opts->max_sweeps > 0) ? opts->max_sweeps : 30;
+  const size_t eig_smem = size_t(l) * l * 32 + size_t(n2) * l * 8 + size_t((l + 1) / 2) * 40;
+  if (eig_smem <= kSmemCap && l <= 128) {
+    cudaFuncSetAttribute(core_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(eig_smem));
+    {
+      KernelScope ks("core_eig", st);
+      core_eig_kernel<<<unsigned(h), QR_THREADS, eig_smem, st>>>(
+          Zr, Zi, int(n2), int(l), k, sweeps, Wkr, Wki, Vr, Vi, Sr, Si, status);
+    }
+    if ((rc = launch_status("core_eig_kernel"))) return rc;
+  } else {
   {
     KernelScope ks("to_double", st);
     to_double_kernel<<<grid_for(n2 * l * h), 256, 0, st>>>(Zr, Gr, n2 * l * h);
@@ -365,7 +658,6 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
   }
   note_launches(2);
   if ((rc = launch_status("to_double"))) return rc;
-  const int sweeps = (opts && opts->max_sweeps > 0) ? opts->max_sweeps : 30;
   if ((rc = jacobi_double_launch(Gr, Gi, n2 * l, Wr, Wi, l * l, sig, int(n2), int(l), int(h),
                                  sweeps, flags, status, st)))
     return rc;
@@ -375,6 +667,7 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
         Gr, Gi, n2 * l, Wr, Wi, l * l, sig, int(n2), int(l), k, Wkr, Wki, Vr, Vi, Sr, Si);
   }
   if ((rc = launch_status("pick_topk_kernel"))) return rc;
+  }
   if ((rc = gemm(Yr, Yi, n1, l, Wkr, Wki, k, Ur, Ui))) return rc;    // U_hat = Q W_k
   if ((rc = launch_irdft(Ur, Ui, n1 * k, n1 * k, n3, U, st))) return rc;
   if ((rc = launch_irdft(Sr, Si, int64_t(k) * k, int64_t(k) * k, n3, S, st))) return rc;
