@@ -20,7 +20,6 @@ namespace {
 
 constexpr int FFT_WARPS_MAX = 4;
 constexpr int MAX_STAGES = 16;
-constexpr int MAX_RADIX = 16;
 
 struct FftPlan {
   int n;
@@ -33,7 +32,9 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 
 // One Stockham FFT of length plan.n on buffers owned by the calling warp.
-// Returns the buffer holding the result.
+// Returns the buffer holding the result.  Radices 2, 3, 4 and 5 use fixed
+// butterflies in registers; other radices (7, 11, 13) an on-the-fly R-point
+// DFT read straight from shared memory.
 __device__ float2* stockham(const FftPlan& plan, const float2* __restrict__ tw, float2* b0,
                             float2* b1, int lane) {
   const int N = plan.n;
@@ -45,51 +46,74 @@ __device__ float2* stockham(const FftPlan& plan, const float2* __restrict__ tw, 
     const int NR = N / R;
     const int step_tw = N / (Ns * R);
     for (int j = lane; j < NR; j += 32) {
-      float2 v[MAX_RADIX];
       const int k = j % Ns;
+      const int base = (j / Ns) * Ns * R + k;
+      if (R <= 5) {
+        float2 v[5];
 #pragma unroll
-      for (int r = 0; r < MAX_RADIX; ++r) {
-        if (r < R) {
-          float2 x = src[j + r * NR];
-          if (r > 0 && k > 0) x = cmul(x, tw[(k * r * step_tw) % N]);
-          v[r] = x;
-        }
-      }
-      float2 out[MAX_RADIX];
-      if (R == 2) {
-        out[0] = make_float2(v[0].x + v[1].x, v[0].y + v[1].y);
-        out[1] = make_float2(v[0].x - v[1].x, v[0].y - v[1].y);
-      } else if (R == 4) {
-        const float2 a = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
-        const float2 b = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
-        const float2 c = make_float2(v[1].x + v[3].x, v[1].y + v[3].y);
-        const float2 d = make_float2(v[1].x - v[3].x, v[1].y - v[3].y);   // times -i below
-        out[0] = make_float2(a.x + c.x, a.y + c.y);
-        out[2] = make_float2(a.x - c.x, a.y - c.y);
-        out[1] = make_float2(b.x + d.y, b.y - d.x);
-        out[3] = make_float2(b.x - d.y, b.y + d.x);
-      } else {
-        // R-point DFT with the table: exp(-2 pi i r q / R) = tw[(r q N/R) mod N]
-#pragma unroll
-        for (int q = 0; q < MAX_RADIX; ++q) {
-          if (q < R) {
-            float2 acc = v[0];
-#pragma unroll
-            for (int r = 1; r < MAX_RADIX; ++r) {
-              if (r < R) {
-                const float2 w = tw[(r * q % R) * NR];
-                acc.x += v[r].x * w.x - v[r].y * w.y;
-                acc.y += v[r].x * w.y + v[r].y * w.x;
-              }
-            }
-            out[q] = acc;
+        for (int r = 0; r < 5; ++r) {
+          if (r < R) {
+            float2 x = src[j + r * NR];
+            if (r > 0 && k > 0) x = cmul(x, tw[k * r * step_tw]);
+            v[r] = x;
           }
         }
-      }
-      const int base = (j / Ns) * Ns * R + k;
+        float2 out[5];
+        if (R == 2) {
+          out[0] = make_float2(v[0].x + v[1].x, v[0].y + v[1].y);
+          out[1] = make_float2(v[0].x - v[1].x, v[0].y - v[1].y);
+        } else if (R == 4) {
+          const float2 a = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
+          const float2 b = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
+          const float2 c = make_float2(v[1].x + v[3].x, v[1].y + v[3].y);
+          const float2 d = make_float2(v[1].x - v[3].x, v[1].y - v[3].y);   // times -i below
+          out[0] = make_float2(a.x + c.x, a.y + c.y);
+          out[2] = make_float2(a.x - c.x, a.y - c.y);
+          out[1] = make_float2(b.x + d.y, b.y - d.x);
+          out[3] = make_float2(b.x - d.y, b.y + d.x);
+        } else if (R == 3) {
+          // w = exp(-2 pi i / 3) = -1/2 - i sqrt(3)/2
+          const float c1 = -0.5f, s1 = -0.86602540378443865f;
+          const float2 t = make_float2(v[1].x + v[2].x, v[1].y + v[2].y);
+          const float2 d = make_float2(v[1].x - v[2].x, v[1].y - v[2].y);
+          out[0] = make_float2(v[0].x + t.x, v[0].y + t.y);
+          const float2 m = make_float2(v[0].x + c1 * t.x, v[0].y + c1 * t.y);
+          out[1] = make_float2(m.x - s1 * d.y, m.y + s1 * d.x);   // m + i s1 d
+          out[2] = make_float2(m.x + s1 * d.y, m.y - s1 * d.x);   // m - i s1 d
+        } else {   // R == 5: cos/sin of -72 and -144 degrees
+          const float c1 = 0.30901699437494742f, s1 = -0.95105651629515357f;
+          const float c2 = -0.80901699437494742f, s2 = -0.58778525229247313f;
+          const float2 t1 = make_float2(v[1].x + v[4].x, v[1].y + v[4].y);
+          const float2 d1 = make_float2(v[1].x - v[4].x, v[1].y - v[4].y);
+          const float2 t2 = make_float2(v[2].x + v[3].x, v[2].y + v[3].y);
+          const float2 d2 = make_float2(v[2].x - v[3].x, v[2].y - v[3].y);
+          out[0] = make_float2(v[0].x + t1.x + t2.x, v[0].y + t1.y + t2.y);
+          const float2 m1 = make_float2(v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y);
+          const float2 m2 = make_float2(v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y);
+          const float2 n1 = make_float2(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y);
+          const float2 n2 = make_float2(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y);
+          out[1] = make_float2(m1.x - n1.y, m1.y + n1.x);
+          out[4] = make_float2(m1.x + n1.y, m1.y - n1.x);
+          out[2] = make_float2(m2.x - n2.y, m2.y + n2.x);
+          out[3] = make_float2(m2.x + n2.y, m2.y - n2.x);
+        }
 #pragma unroll
-      for (int r = 0; r < MAX_RADIX; ++r)
-        if (r < R) dst[base + r * Ns] = out[r];
+        for (int r = 0; r < 5; ++r)
+          if (r < R) dst[base + r * Ns] = out[r];
+      } else {
+        // R-point DFT of the twiddled inputs: exp(-2 pi i r q / R) = tw[(r q mod R) N/R]
+        for (int q = 0; q < R; ++q) {
+          float2 acc = src[j];
+          for (int r = 1; r < R; ++r) {
+            float2 x = src[j + r * NR];
+            if (k > 0) x = cmul(x, tw[k * r * step_tw]);
+            const float2 w = tw[(r * q % R) * NR];
+            acc.x += x.x * w.x - x.y * w.y;
+            acc.y += x.x * w.y + x.y * w.x;
+          }
+          dst[base + q * Ns] = acc;
+        }
+      }
     }
     __syncwarp();
     float2* t = src;

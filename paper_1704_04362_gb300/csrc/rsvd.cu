@@ -221,15 +221,17 @@ __device__ __forceinline__ void acc2(float& hi, float& lo, float a, float b) {
 }
 
 // G(a, b) = sum_r conj(Y(r, a)) Y(r, b) for a <= b (Hermitian fill), Y in
-// shared memory as float2 column-major p x l; G float64 interleaved.
-__device__ void gram_smem(const float2* __restrict__ Ys, int p, int l, double* G) {
+// shared memory as float2 column-major p x l with column stride ps (p + 1:
+// the odd stride spreads the threads' different columns over the banks);
+// G float64 interleaved.
+__device__ void gram_smem(const float2* __restrict__ Ys, int ps, int p, int l, double* G) {
   const int npairs = l * (l + 1) / 2;
   for (int e = threadIdx.x; e < npairs; e += blockDim.x) {
     int a = 0, rem = e;
     while (rem >= l - a) { rem -= l - a; ++a; }
     const int b = a + rem;
-    const float2* xa = Ys + a * p;
-    const float2* xb = Ys + b * p;
+    const float2* xa = Ys + a * ps;
+    const float2* xb = Ys + b * ps;
     float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
     for (int r = 0; r < p; ++r) {
       const float2 u = xa[r], v = xb[r];
@@ -246,24 +248,40 @@ __device__ void gram_smem(const float2* __restrict__ Ys, int p, int l, double* G
   }
 }
 
-// Inverse of the upper-triangular R (upper triangle of G, float64) into Ri
-// (float32 interleaved, l x l, upper).  One thread per column.
-__device__ void upper_inverse(const double* R, int l, float2* Ri) {
-  for (int j = threadIdx.x; j < l; j += blockDim.x) {
-    // x = R^{-1} e_j by back substitution, kept in Ri's column j
-    for (int i = l - 1; i >= 0; --i) {
-      if (i > j) { Ri[i * l + j] = make_float2(0.f, 0.f); continue; }
-      double sr = (i == j) ? 1.0 : 0.0, si = 0.0;
-      for (int k = i + 1; k <= j; ++k) {
-        const double ar = R[2 * (i * l + k)], ai = R[2 * (i * l + k) + 1];
-        const float2 x = Ri[k * l + j];
-        sr -= ar * x.x - ai * x.y;
-        si -= ar * x.y + ai * x.x;
-      }
-      const double d = R[2 * (i * l + i)];
-      Ri[i * l + j] = make_float2(float(sr / d), float(si / d));
+// Right-looking Cholesky G = R^H R on the upper triangle of G (float64
+// interleaved, l x l): for each j the pivot, row j of R, then the trailing
+// update G(i, k) -= conj(R(j, i)) R(j, k), i <= k, spread over the block.
+// Returns false on a non-positive pivot (block-uniform).
+__device__ bool cholesky_rl(double* G, int l, int* fail) {
+  __shared__ double inv_d;
+  for (int j = 0; j < l; ++j) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double d = G[2 * (j * l + j)];
+      if (!(d > 0.0) || !isfinite(d)) *fail = 1;
+      const double r = (d > 0.0 && isfinite(d)) ? sqrt(d) : 1.0;
+      G[2 * (j * l + j)] = r;
+      G[2 * (j * l + j) + 1] = 0.0;
+      inv_d = 1.0 / r;
+    }
+    __syncthreads();
+    for (int k = j + 1 + threadIdx.x; k < l; k += blockDim.x) {
+      G[2 * (j * l + k)] *= inv_d;
+      G[2 * (j * l + k) + 1] *= inv_d;
+    }
+    __syncthreads();
+    const int m = l - j - 1;   // trailing size
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = j + 1 + e / m, k = j + 1 + e % m;
+      if (i > k) continue;
+      const double ar = G[2 * (j * l + i)], ai = G[2 * (j * l + i) + 1];   // R(j, i)
+      const double br = G[2 * (j * l + k)], bi = G[2 * (j * l + k) + 1];   // R(j, k)
+      G[2 * (i * l + k)] -= ar * br + ai * bi;
+      G[2 * (i * l + k) + 1] -= ar * bi - ai * br;
     }
   }
+  __syncthreads();
+  return *fail == 0;
 }
 
 // CholeskyQR2 with Y held in shared memory: compensated float32 Gram,
@@ -276,18 +294,20 @@ __global__ void __launch_bounds__(QR_THREADS) cholqr2_smem_kernel(float* y_re, f
   extern __shared__ double dyn[];
   double* G = dyn;                                          // 2 l^2 doubles
   float2* Ri = reinterpret_cast<float2*>(G + 2 * l * l);    // l^2 float2
-  float2* Ys = Ri + l * l;                                  // p l float2
+  float2* Ys = Ri + l * l;                                  // (p + 1) l float2
+  const int ps = p + 1;
   __shared__ int fail;
   float* yr = y_re + int64_t(blockIdx.x) * sY;
   float* yi = y_im + int64_t(blockIdx.x) * sY;
-  for (int e = threadIdx.x; e < p * l; e += blockDim.x) Ys[e] = make_float2(yr[e], yi[e]);
+  for (int e = threadIdx.x; e < p * l; e += blockDim.x)
+    Ys[(e / p) * ps + e % p] = make_float2(yr[e], yi[e]);
   __syncthreads();
   int passes_left = 2;
   bool shifted = false;
   bool ok_all = true;
   for (int it = 0; it < 4 && passes_left > 0; ++it) {
     if (threadIdx.x == 0) fail = 0;
-    gram_smem(Ys, p, l, G);
+    gram_smem(Ys, ps, p, l, G);
     __syncthreads();
     if (shifted) {
       if (threadIdx.x == 0) {
@@ -298,7 +318,7 @@ __global__ void __launch_bounds__(QR_THREADS) cholqr2_smem_kernel(float* y_re, f
       }
       __syncthreads();
     }
-    const bool ok = cholesky(G, l, &fail);
+    const bool ok = cholesky_rl(G, l, &fail);
     if (!ok) {
       if (shifted) {
         ok_all = false;
@@ -308,20 +328,23 @@ __global__ void __launch_bounds__(QR_THREADS) cholqr2_smem_kernel(float* y_re, f
       passes_left = 3;
       continue;
     }
-    upper_inverse(G, l, Ri);
+    // R in float32 (its float64 Gram made the factor accurate; the product
+    // below needs only float32), then Y <- Y R^{-1} row by row by forward
+    // substitution x R = y, in place
+    for (int e = threadIdx.x; e < l * l; e += blockDim.x)
+      Ri[e] = make_float2(float(G[2 * e]), float(G[2 * e + 1]));
     __syncthreads();
-    // Y <- Y R^{-1}: entry (r, j) = sum_{i <= j} Y(r, i) Ri(i, j); rows of Y
-    // are overwritten in place, one thread per row (all columns)
     for (int r = threadIdx.x; r < p; r += blockDim.x) {
-      for (int j = l - 1; j >= 0; --j) {   // descending j: Y(r, i <= j) still unmodified
-        float sr = 0.f, si = 0.f;
-        for (int i = 0; i <= j; ++i) {
-          const float2 y = Ys[i * p + r];
+      for (int j = 0; j < l; ++j) {
+        float2 acc = Ys[j * ps + r];
+        for (int i = 0; i < j; ++i) {
+          const float2 x = Ys[i * ps + r];
           const float2 w = Ri[i * l + j];
-          sr = fmaf(y.x, w.x, fmaf(-y.y, w.y, sr));
-          si = fmaf(y.x, w.y, fmaf(y.y, w.x, si));
+          acc.x -= x.x * w.x - x.y * w.y;
+          acc.y -= x.x * w.y + x.y * w.x;
         }
-        Ys[j * p + r] = make_float2(sr, si);
+        const float d = Ri[j * l + j].x;
+        Ys[j * ps + r] = make_float2(acc.x / d, acc.y / d);
       }
     }
     __syncthreads();
@@ -331,44 +354,32 @@ __global__ void __launch_bounds__(QR_THREADS) cholqr2_smem_kernel(float* y_re, f
   if (!ok_all && threadIdx.x == 0 && status) atomicOr(status, TP_DEV_BREAKDOWN);
   __syncthreads();
   for (int e = threadIdx.x; e < p * l; e += blockDim.x) {
-    yr[e] = Ys[e].x;
-    yi[e] = Ys[e].y;
+    const float2 v = Ys[(e / p) * ps + e % p];
+    yr[e] = v.x;
+    yi[e] = v.y;
   }
 }
 
-// Core SVD through the l x l Gram of B^H (n2 x l, shared memory):
-// G = B B^H = W diag(s^2) W^H by the cyclic two-sided Jacobi method in
-// float64 (disjoint round-robin pairs per step: parameters, then all row
-// rotations, then all column rotations and the eigenvector update).  The top
-// k eigenpairs give W_k (left singular vectors of B), S = sqrt of the
-// eigenvalues, and V_k = B^H W_k S^{-1}.
-__global__ void __launch_bounds__(QR_THREADS) core_eig_kernel(
-    const float* __restrict__ bh_re, const float* __restrict__ bh_im, int p, int l, int k,
-    int max_sweeps, float* __restrict__ wkr, float* __restrict__ wki, float* __restrict__ vkr,
-    float* __restrict__ vki, float* __restrict__ sr_out, float* __restrict__ si_out,
-    int32_t* status) {
-  extern __shared__ double dyn[];
-  double2* G = reinterpret_cast<double2*>(dyn);             // l x l row-major
-  double2* W = G + l * l;                                   // l x l, columns = eigenvectors
-  float2* Bs = reinterpret_cast<float2*>(W + l * l);        // p x l column-major
-  double* rot = reinterpret_cast<double*>(Bs + p * l);      // per pair: c, s, er, ei
-  int* pq = reinterpret_cast<int*>(rot + 4 * ((l + 1) / 2));
-  __shared__ int rotated;
-  __shared__ int order[128];
-  const int64_t f = blockIdx.x;
-  const float* br = bh_re + f * int64_t(p) * l;
-  const float* bi = bh_im + f * int64_t(p) * l;
-  for (int e = threadIdx.x; e < p * l; e += blockDim.x) Bs[e] = make_float2(br[e], bi[e]);
-  __syncthreads();
-  gram_smem(Bs, p, l, reinterpret_cast<double*>(G));
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x)
-    W[e] = make_double2((e / l == e % l) ? 1.0 : 0.0, 0.0);
-  __syncthreads();
+// Cyclic two-sided Jacobi sweeps on the Hermitian l x l matrix G (row-major),
+// accumulating the rotations into W (W <- W K).  Each step takes ll/2
+// disjoint round-robin pairs: their parameters from the current G, then all
+// row rotations, then all column rotations (of G and W).  Pair (a, b) with
+// g = G(a,b) = |g| e^{i phi}: zeta = (G(b,b) - G(a,a)) / (2|g|),
+// t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t;
+// K = [[c, s], [-s e^{-i phi}, c e^{-i phi}]] zeroes G(a,b) in K^H G K.
+// Row stride ls (odd) keeps the column accesses free of bank conflicts.
+// A pair is rotated only while |G(a,b)| exceeds both tol sqrt(|G(a,a) G(b,b)|)
+// and the rounding floor `floor_abs` (entries below the working precision's
+// noise level of ||G|| cannot be resolved further).  Returns the number of
+// sweeps that rotated something (stops after a quiet sweep or at max_sweeps).
+template <class T, class C2>
+__device__ int jacobi2(C2* G, C2* W, int l, int ls, T tol, T floor_abs, int max_sweeps, T* rot,
+                       int* pq, int* rotated) {
   const int ll = l + (l & 1), npairs = ll / 2;
-  const double tol = 1e-14;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) *rotated = 0;
     __syncthreads();
     for (int step = 0; step < ll - 1; ++step) {
       for (int i = threadIdx.x; i < npairs; i += blockDim.x) {
@@ -378,67 +389,153 @@ __global__ void __launch_bounds__(QR_THREADS) core_eig_kernel(
         if (a > b) { const int t = a; a = b; b = t; }
         pq[2 * i] = a;
         pq[2 * i + 1] = b;
-        double cs = 1.0, sn = 0.0, er = 1.0, ei = 0.0;
-        bool act = false;
+        T cs = 1, sn = 0, er = 1, ei = 0;
         if (b < l) {
-          const double al = G[a * l + a].x, be = G[b * l + b].x;
-          const double2 ga = G[a * l + b];
-          const double g = sqrt(ga.x * ga.x + ga.y * ga.y);
-          if (g > tol * sqrt(fabs(al * be)) && g > 0.0) {
-            act = true;
-            const double zeta = (be - al) / (2.0 * g);
-            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            cs = 1.0 / sqrt(1.0 + t * t);
+          const T al = G[a * ls + a].x, be = G[b * ls + b].x;
+          const C2 ga = G[a * ls + b];
+          const T g = sqrt(ga.x * ga.x + ga.y * ga.y);
+          if (g > tol * sqrt(fabs(al * be)) && g > floor_abs && g > T(0)) {
+            const T zeta = (be - al) / (T(2) * g);
+            const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+            cs = T(1) / sqrt(T(1) + t * t);
             sn = cs * t;
             er = ga.x / g;
             ei = -ga.y / g;   // e^{-i phi}
+            *rotated = 1;
           }
         }
-        rot[4 * i] = act ? cs : 1.0;
-        rot[4 * i + 1] = act ? sn : 0.0;
+        rot[4 * i] = cs;
+        rot[4 * i + 1] = sn;
         rot[4 * i + 2] = er;
         rot[4 * i + 3] = ei;
-        if (act) rotated = 1;
       }
       __syncthreads();
-      // rows: row_a' = c row_a - s e^{i phi} row_b ; row_b' = s row_a + c e^{i phi} row_b
       for (int e = threadIdx.x; e < npairs * l; e += blockDim.x) {
         const int i = e / l, j = e - i * l;
         const int a = pq[2 * i], b = pq[2 * i + 1];
-        if (b >= l || rot[4 * i + 1] == 0.0) continue;
-        const double c = rot[4 * i], s = rot[4 * i + 1], er = rot[4 * i + 2], ei = -rot[4 * i + 3];
-        const double2 x = G[a * l + j], y = G[b * l + j];
-        const double yr = y.x * er - y.y * ei, yi = y.x * ei + y.y * er;   // e^{i phi} y
-        G[a * l + j] = make_double2(c * x.x - s * yr, c * x.y - s * yi);
-        G[b * l + j] = make_double2(s * x.x + c * yr, s * x.y + c * yi);
+        if (b >= l || rot[4 * i + 1] == T(0)) continue;
+        const T c = rot[4 * i], s = rot[4 * i + 1], er = rot[4 * i + 2], ei = -rot[4 * i + 3];
+        const C2 x = G[a * ls + j], y = G[b * ls + j];
+        const T yr = y.x * er - y.y * ei, yi = y.x * ei + y.y * er;   // e^{i phi} y
+        G[a * ls + j].x = c * x.x - s * yr;
+        G[a * ls + j].y = c * x.y - s * yi;
+        G[b * ls + j].x = s * x.x + c * yr;
+        G[b * ls + j].y = s * x.y + c * yi;
       }
       __syncthreads();
-      // columns of G and W: col_a' = c col_a - s e^{-i phi} col_b ; col_b' = s col_a + c e^{-i phi} col_b
       for (int e = threadIdx.x; e < 2 * npairs * l; e += blockDim.x) {
         const int which = e / (npairs * l), rest = e - which * npairs * l;
         const int i = rest / l, j = rest - i * l;
         const int a = pq[2 * i], b = pq[2 * i + 1];
-        if (b >= l || rot[4 * i + 1] == 0.0) continue;
-        const double c = rot[4 * i], s = rot[4 * i + 1], er = rot[4 * i + 2], ei = rot[4 * i + 3];
-        double2* M = which ? W : G;
-        const double2 x = M[j * l + a], y = M[j * l + b];
-        const double yr = y.x * er - y.y * ei, yi = y.x * ei + y.y * er;   // e^{-i phi} y
-        M[j * l + a] = make_double2(c * x.x - s * yr, c * x.y - s * yi);
-        M[j * l + b] = make_double2(s * x.x + c * yr, s * x.y + c * yi);
+        if (b >= l || rot[4 * i + 1] == T(0)) continue;
+        const T c = rot[4 * i], s = rot[4 * i + 1], er = rot[4 * i + 2], ei = rot[4 * i + 3];
+        C2* M = which ? W : G;
+        const C2 x = M[j * ls + a], y = M[j * ls + b];
+        const T yr = y.x * er - y.y * ei, yi = y.x * ei + y.y * er;   // e^{-i phi} y
+        M[j * ls + a].x = c * x.x - s * yr;
+        M[j * ls + a].y = c * x.y - s * yi;
+        M[j * ls + b].x = s * x.x + c * yr;
+        M[j * ls + b].y = s * x.y + c * yi;
       }
       __syncthreads();
     }
-    const int any = rotated;
+    const int any = *rotated;
     __syncthreads();
     if (!any) break;
   }
-  if (sweep >= max_sweeps && threadIdx.x == 0 && status) atomicOr(status, TP_DEV_NOCONV);
-  // sort eigenvalues descending
+  return sweep;
+}
+
+// Core SVD through the l x l Gram of B^H (n2 x l, held in shared memory):
+// G = B B^H = W diag(s^2) W^H.  A float32 two-sided Jacobi converges first;
+// then, in float64, the Rayleigh-Ritz projection G' = W^H G W of the float64
+// Gram (nearly diagonal) and float64 Jacobi sweeps on G' (updating W in
+// float64) finish the eigendecomposition to float64 accuracy.  The top k
+// eigenpairs give W_k (left singular vectors of B), S = sqrt(eigenvalues)
+// and V_k = B^H W_k S^{-1}.
+constexpr int EIG_THREADS = 512;
+
+__global__ void __launch_bounds__(EIG_THREADS) core_eig_kernel(
+    const float* __restrict__ bh_re, const float* __restrict__ bh_im, int p, int l, int k,
+    int max_sweeps, float* __restrict__ wkr, float* __restrict__ wki, float* __restrict__ vkr,
+    float* __restrict__ vki, float* __restrict__ sr_out, float* __restrict__ si_out,
+    int32_t* status) {
+  extern __shared__ double dyn[];
+  const int ls = l | 1;                                     // odd row stride
+  const int L2 = l * ls;
+  double2* G = reinterpret_cast<double2*>(dyn);             // l x l float64 Gram, then G'
+  double2* W = G + L2;                                      // l x l float64 eigenvectors
+  double2* T = W + L2;                                      // l x l scratch; float32 phase: Gf, Wf
+  float2* Gf = reinterpret_cast<float2*>(T);
+  float2* Wf = Gf + L2;
+  float2* Bs = reinterpret_cast<float2*>(T + L2);           // p x l, column stride p + 1
+  const int ps = p + 1;
+  double* rot = reinterpret_cast<double*>(Bs + ps * l);     // per pair: c, s, er, ei
+  int* pq = reinterpret_cast<int*>(rot + 4 * ((l + 1) / 2));
+  float* rotf = reinterpret_cast<float*>(rot);
+  __shared__ int rotated;
+  __shared__ int order[128];
+  const int64_t f = blockIdx.x;
+  const float* br = bh_re + f * int64_t(p) * l;
+  const float* bi = bh_im + f * int64_t(p) * l;
+  for (int e = threadIdx.x; e < p * l; e += blockDim.x)
+    Bs[(e / p) * ps + e % p] = make_float2(br[e], bi[e]);
+  __syncthreads();
+  gram_smem(Bs, ps, p, l, reinterpret_cast<double*>(T));   // dense l x l into T first
+  __syncthreads();
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) G[(e / l) * ls + e % l] = T[e];
+  __syncthreads();
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int i = e / l, j = e % l;
+    Gf[i * ls + j] = make_float2(float(G[i * ls + j].x), float(G[i * ls + j].y));
+    Wf[i * ls + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
+  }
+  __shared__ double gmax;
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int j = 0; j < l; ++j) m = fmax(m, G[j * ls + j].x);
+    gmax = m;
+  }
+  __syncthreads();
+  const int s32 = jacobi2<float, float2>(Gf, Wf, l, ls, 1e-6f, float(4e-7 * gmax), max_sweeps,
+                                         rotf, pq, &rotated);
+  // float64 Rayleigh-Ritz: W = Wf, T = G W, G' = W^H T
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int i = e / l, j = e % l;
+    W[i * ls + j] = make_double2(Wf[i * ls + j].x, Wf[i * ls + j].y);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int i = e / l, j = e % l;
+    double tr = 0.0, ti = 0.0;
+    for (int m = 0; m < l; ++m) {
+      const double2 g = G[i * ls + m], w = W[m * ls + j];
+      tr += g.x * w.x - g.y * w.y;
+      ti += g.x * w.y + g.y * w.x;
+    }
+    T[i * ls + j] = make_double2(tr, ti);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int i = e / l, j = e % l;
+    double gr = 0.0, gi = 0.0;
+    for (int m = 0; m < l; ++m) {
+      const double2 w = W[m * ls + i], t = T[m * ls + j];   // conj(W(m, i)) T(m, j)
+      gr += w.x * t.x + w.y * t.y;
+      gi += w.x * t.y - w.y * t.x;
+    }
+    G[i * ls + j] = make_double2(gr, gi);
+  }
+  const int s64 = jacobi2<double, double2>(G, W, l, ls, 1e-14, 2e-15 * gmax, max_sweeps, rot, pq,
+                                           &rotated);
+  if ((s32 >= max_sweeps || s64 >= max_sweeps) && threadIdx.x == 0 && status)
+    atomicOr(status, TP_DEV_NOCONV);
+  __syncthreads();
   for (int j = threadIdx.x; j < l; j += blockDim.x) {
-    const double lj = G[j * l + j].x;
+    const double lj = G[j * ls + j].x;
     int rank = 0;
     for (int m = 0; m < l; ++m) {
-      const double lm = G[m * l + m].x;
+      const double lm = G[m * ls + m].x;
       rank += (lm > lj) || (lm == lj && m < j);
     }
     order[rank] = j;
@@ -446,13 +543,13 @@ __global__ void __launch_bounds__(QR_THREADS) core_eig_kernel(
   __syncthreads();
   for (int e = threadIdx.x; e < l * k; e += blockDim.x) {
     const int i = e % l, c = e / l;
-    const double2 w = W[i * l + order[c]];
+    const double2 w = W[i * ls + order[c]];
     wkr[f * l * k + e] = float(w.x);
     wki[f * l * k + e] = float(w.y);
   }
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
     const int i = e % k, c = e / k;
-    const double lam = G[order[c] * l + order[c]].x;
+    const double lam = G[order[c] * ls + order[c]].x;
     sr_out[f * k * k + e] = (i == c) ? float(sqrt(fmax(lam, 0.0))) : 0.f;
     si_out[f * k * k + e] = 0.f;
   }
@@ -460,13 +557,12 @@ __global__ void __launch_bounds__(QR_THREADS) core_eig_kernel(
   for (int64_t e = threadIdx.x; e < int64_t(p) * k; e += blockDim.x) {
     const int r = int(e % p), c = int(e / p);
     const int j = order[c];
-    const double lam = G[j * l + j].x;
-    const double sg = sqrt(fmax(lam, 0.0));
+    const double sg = sqrt(fmax(G[j * ls + j].x, 0.0));
     float vr = 0.f, vi = 0.f;
     if (sg > 0.0) {
       for (int m = 0; m < l; ++m) {
-        const float2 b = Bs[m * p + r];
-        const double2 w = W[m * l + j];
+        const float2 b = Bs[m * ps + r];
+        const double2 w = W[m * ls + j];
         vr = fmaf(b.x, float(w.x), fmaf(-b.y, float(w.y), vr));
         vi = fmaf(b.x, float(w.y), fmaf(b.y, float(w.x), vi));
       }
@@ -614,7 +710,7 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
   cudaFuncSetAttribute(cholqr2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(qr_smem));
   constexpr size_t kSmemCap = 200 * 1024;
   auto orth = [&](float* yr, float* yi, int64_t rows) {
-    const size_t fast_smem = size_t(l) * l * (16 + 8) + size_t(rows) * l * 8;
+    const size_t fast_smem = size_t(l) * l * (16 + 8) + size_t(rows + 1) * l * 8;
     if (fast_smem <= kSmemCap) {
       cudaFuncSetAttribute(cholqr2_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            int(fast_smem));
@@ -639,13 +735,13 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
   }
   if ((rc = gemm(Hr, Hi, n2, n1, Yr, Yi, l, Zr, Zi))) return rc;     // B^H = X_hat^H Q
   const int sweeps = (opts && opts->max_sweeps > 0) ? opts->max_sweeps : 30;
-  const size_t eig_smem = size_t(l) * l * 32 + size_t(n2) * l * 8 + size_t((l + 1) / 2) * 40;
+  const size_t eig_smem = size_t(l) * (l | 1) * 48 + size_t(n2 + 1) * l * 8 + size_t((l + 1) / 2) * 40;
   if (eig_smem <= kSmemCap && l <= 128) {
     cudaFuncSetAttribute(core_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          int(eig_smem));
     {
       KernelScope ks("core_eig", st);
-      core_eig_kernel<<<unsigned(h), QR_THREADS, eig_smem, st>>>(
+      core_eig_kernel<<<unsigned(h), EIG_THREADS, eig_smem, st>>>(
           Zr, Zi, int(n2), int(l), k, sweeps, Wkr, Wki, Vr, Vi, Sr, Si, status);
     }
     if ((rc = launch_status("core_eig_kernel"))) return rc;
