@@ -14,7 +14,8 @@
 // output times) per chunk; the KC columns of the transform matrix a chunk
 // needs are built once per block in shared memory from the n3-entry twiddle
 // table exp(-2 pi i m / n3), m = k t mod n3.  KC is chosen per call to
-// minimise padding.
+// minimise padding.  The (Re, Im) and (P, Q) accumulator pairs are updated
+// with Blackwell's packed two-lane float32 FMA.
 #include "tp_internal.cuh"
 
 namespace tp {
@@ -133,11 +134,11 @@ __global__ void __launch_bounds__(RB) rdft_kernel(DftGather g, int stage) {
       __syncthreads();
       build_fwd_cols<KC>(Wc, tw, n3, nh, nhp, k0);
       __syncthreads();
-      float ar[TPT][KC], ai[TPT][KC];
+      float2 acc[TPT][KC];   // (Re, Im), updated by packed two-lane FMAs
 #pragma unroll
       for (int j = 0; j < TPT; ++j)
 #pragma unroll
-        for (int q = 0; q < KC; ++q) { ar[j][q] = 0.f; ai[j][q] = 0.f; }
+        for (int q = 0; q < KC; ++q) acc[j][q] = make_float2(0.f, 0.f);
       for (int t0 = 0; t0 <= nh; t0 += TU) {
         float ev[TPT][TU], ov[TPT][TU];
 #pragma unroll
@@ -164,10 +165,8 @@ __global__ void __launch_bounds__(RB) rdft_kernel(DftGather g, int stage) {
           for (int q = 0; q < KC; ++q) {
             const float2 w = Wc[(t0 + u) * KC + q];   // zero rows past nh
 #pragma unroll
-            for (int j = 0; j < TPT; ++j) {
-              ar[j][q] = fmaf(ev[j][u], w.x, ar[j][q]);
-              ai[j][q] = fmaf(-ov[j][u], w.y, ai[j][q]);
-            }
+            for (int j = 0; j < TPT; ++j)
+              acc[j][q] = __ffma2_rn(make_float2(ev[j][u], -ov[j][u]), w, acc[j][q]);
           }
       }
 #pragma unroll
@@ -178,15 +177,16 @@ __global__ void __launch_bounds__(RB) rdft_kernel(DftGather g, int stage) {
         for (int q = 0; q < KC; ++q) {
           if (k0 + q < h) {
             const int64_t oo = o + int64_t(k0 + q) * g.out_slice;
+            const float ar = acc[j][q].x, ai = acc[j][q].y;
             if (g.out_re_lo) {
-              const float hr = tf32_rna(ar[j][q]), hi = tf32_rna(ai[j][q]);
+              const float hr = tf32_rna(ar), hi = tf32_rna(ai);
               g.out_re[oo] = hr;
-              g.out_re_lo[oo] = ar[j][q] - hr;
+              g.out_re_lo[oo] = ar - hr;
               g.out_im[oo] = hi;
-              g.out_im_lo[oo] = ai[j][q] - hi;
+              g.out_im_lo[oo] = ai - hi;
             } else {
-              g.out_re[oo] = ar[j][q];
-              g.out_im[oo] = ai[j][q];
+              g.out_re[oo] = ar;
+              g.out_im[oo] = ai;
             }
           }
         }
@@ -235,11 +235,11 @@ __global__ void __launch_bounds__(RB) rdft_t_kernel(DftGather g) {
         Wc[e] = t < n3 ? tw[int((int64_t(k0 + q) * t) % n3)] : make_float2(0.f, 0.f);
       }
       __syncthreads();
-      float ar[TPTT][KC], ai[TPTT][KC];
+      float2 acc[TPTT][KC];   // (Re, Im), updated by packed two-lane FMAs
 #pragma unroll
       for (int j = 0; j < TPTT; ++j)
 #pragma unroll
-        for (int q = 0; q < KC; ++q) { ar[j][q] = 0.f; ai[j][q] = 0.f; }
+        for (int q = 0; q < KC; ++q) acc[j][q] = make_float2(0.f, 0.f);
       for (int t0 = 0; t0 < n3; t0 += TU) {
         float x[TPTT][TU];
 #pragma unroll
@@ -254,10 +254,8 @@ __global__ void __launch_bounds__(RB) rdft_t_kernel(DftGather g) {
           for (int q = 0; q < KC; ++q) {
             const float2 w = Wc[(t0 + u) * KC + q];
 #pragma unroll
-            for (int j = 0; j < TPTT; ++j) {
-              ar[j][q] = fmaf(x[j][u], w.x, ar[j][q]);
-              ai[j][q] = fmaf(-x[j][u], w.y, ai[j][q]);
-            }
+            for (int j = 0; j < TPTT; ++j)
+              acc[j][q] = __ffma2_rn(make_float2(x[j][u], -x[j][u]), w, acc[j][q]);
           }
       }
       // planes: 0 re (hi), 1 im (hi), 2 re lo, 3 im lo
@@ -268,7 +266,7 @@ __global__ void __launch_bounds__(RB) rdft_t_kernel(DftGather g) {
         for (int j = 0; j < TPTT; ++j)
 #pragma unroll
           for (int q = 0; q < KC; ++q) {
-            const float v = (pl & 1) ? ai[j][q] : ar[j][q];
+            const float v = (pl & 1) ? acc[j][q].y : acc[j][q].x;
             float o;
             if (!g.out_re_lo) o = v;
             else if (pl < 2) o = tf32_rna(v);
@@ -330,11 +328,11 @@ __global__ void __launch_bounds__(RB) irdft_kernel(const float* __restrict__ in_
         }
       }
       __syncthreads();
-      float P[TPT][KC], Q[TPT][KC];
+      float2 PQ[TPT][KC];   // (P, Q), updated by packed two-lane FMAs
 #pragma unroll
       for (int j = 0; j < TPT; ++j)
 #pragma unroll
-        for (int q = 0; q < KC; ++q) { P[j][q] = 0.f; Q[j][q] = 0.f; }
+        for (int q = 0; q < KC; ++q) PQ[j][q] = make_float2(0.f, 0.f);
       for (int k0 = 0; k0 < h; k0 += TU) {
         float re[TPT][TU], im[TPT][TU];
 #pragma unroll
@@ -354,10 +352,8 @@ __global__ void __launch_bounds__(RB) irdft_kernel(const float* __restrict__ in_
           for (int q = 0; q < KC; ++q) {
             const float2 v = Vc[(k0 + u) * KC + q];
 #pragma unroll
-            for (int j = 0; j < TPT; ++j) {
-              P[j][q] = fmaf(re[j][u], v.x, P[j][q]);
-              Q[j][q] = fmaf(im[j][u], v.y, Q[j][q]);
-            }
+            for (int j = 0; j < TPT; ++j)
+              PQ[j][q] = __ffma2_rn(make_float2(re[j][u], im[j][u]), v, PQ[j][q]);
           }
       }
 #pragma unroll
@@ -367,8 +363,8 @@ __global__ void __launch_bounds__(RB) irdft_kernel(const float* __restrict__ in_
         for (int q = 0; q < KC; ++q) {
           const int t = t0 + q;
           if (t <= nh) {
-            out[r[j] + rows * int64_t(t)] = P[j][q] - Q[j][q];
-            if (t > 0 && n3 - t > nh) out[r[j] + rows * int64_t(n3 - t)] = P[j][q] + Q[j][q];
+            out[r[j] + rows * int64_t(t)] = PQ[j][q].x - PQ[j][q].y;
+            if (t > 0 && n3 - t > nh) out[r[j] + rows * int64_t(n3 - t)] = PQ[j][q].x + PQ[j][q].y;
           }
         }
       }
