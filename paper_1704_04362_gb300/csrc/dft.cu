@@ -36,11 +36,16 @@ __device__ __forceinline__ float tf32_rna(float x) {
   return __uint_as_float(r);
 }
 
+// (cos, sin)(2 pi m / n3) for m < n3.  float sincospi (about 1 ulp; exact at
+// quarter turns, m/n3 in {0, 1/4, 1/2, 3/4}) keeps the tables off the slow
+// float64 pipe.  The argument 2m/n3 is formed exactly enough: 2m and n3 are
+// small integers, and the quotient's rounding (2^-24 relative) moves the angle
+// by less than the float result's own rounding.
 __device__ __forceinline__ void build_twiddles(float2* tw, int n3) {
   for (int m = threadIdx.x; m < n3; m += blockDim.x) {
-    double s, c;
-    sincospi(2.0 * double(m) / double(n3), &s, &c);   // exact at quarter turns
-    tw[m] = make_float2(float(c), float(s));
+    float s, c;
+    sincospif(float(2 * m) / float(n3), &s, &c);
+    tw[m] = make_float2(c, s);
   }
 }
 

@@ -124,11 +124,12 @@ __device__ float2* stockham(const FftPlan& plan, const float2* __restrict__ tw, 
   return src;
 }
 
+// exp(-2 pi i m / n) for m < n, by float sincospi (off the float64 pipe).
 __device__ __forceinline__ void build_tw(float2* tw, int n) {
   for (int m = threadIdx.x; m < n; m += blockDim.x) {
-    double s, c;
-    sincospi(-2.0 * double(m) / double(n), &s, &c);   // exp(-2 pi i m / n)
-    tw[m] = make_float2(float(c), float(s));
+    float s, c;
+    sincospif(-float(2 * m) / float(n), &s, &c);
+    tw[m] = make_float2(c, s);
   }
 }
 
