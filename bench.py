@@ -189,6 +189,12 @@ def gpu_uuid(torch, dev):
         return str(dev)
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# single-pass ncu capture of the full-size workload; valid only for the kernel
+# version it was taken on (profiles/cgemm_tc_2000x4000x1500x64_traffic.md).
+MEASURED_TRAFFIC = {"cgemm_tc": 864519680 + 755867392}
+
+
 def roofline_for(name, ms_avg, cprime, peaks, sm_mhz):
     """Algorithmic work per launch of the named kernel and its roofline."""
     h = N3 // 2 + 1
@@ -203,8 +209,14 @@ def roofline_for(name, ms_avg, cprime, peaks, sm_mhz):
     if name == "cgemm_tc":
         peak = peaks["bf16_tflops"] / 2.0   # tf32 dense = bf16 / 2 (nominal ratio)
         ach = 3 * fl / (ms_avg * 1e-3) / 1e12
+        h = N3 // 2 + 1
+        kp = (cprime + 15) // 16 * 16
+        alg = 16.0 * (N1 + N4) * kp * h + 8.0 * N1 * N4 * h
         return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None, "peak_src": peaks["src"]}
+                "frac": ach / peak, "traffic": MEASURED_TRAFFIC.get("cgemm_tc"),
+                "algorithmic_bytes": alg,
+                "peak_src": peaks["src"] + " bf16 x 1/2 (tf32 nominal ratio)",
+                "work": "3 tf32 products per real product of the 8 n1 c' n4 nominal flops"}
     bytes_per = {
         "norms_lateral": 4.0 * N1 * N2 * N3,
         "norms_horizontal": 4.0 * N2 * N4 * N3,
