@@ -136,6 +136,76 @@ def run_oracle_sample(A, B, seed):
 RSVD_K, RSVD_P, RSVD_Q = 40, 10, 2
 
 
+def reduce_max(value, dist, device):
+    """Largest value over the ranks (the job's time is its slowest rank)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_gpu(fn, reps, torch):
+    """Mean milliseconds of fn() over reps calls, CUDA events on the current stream."""
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def bench_rows(tp, torch, with_cpu):
+    """The other rows of the hot path, each timed on the GPU through the C ABI
+    with the float64 oracle timed beside it on the host cores:
+      tsvd   t-SVD (Theorem 2.6) of the 64 x 48 x 16 iid N(0,1) tensor
+      tcx    t-CX (Algorithm 4), 256 x 512 x 32 tubal rank 10 + 1% noise, c = 64
+      svt    completion ADMM (Algorithm 7), one 144 x 256 x 80 video (tubal rank
+             10, sigma 0.01, 50% observed; the paper's video shape), 10 iterations"""
+    from paper_1704_04362_gb300 import synth
+    rows = {}
+    X = synth.iid_normal((64, 48, 16), seed=0)
+    Xd = tp.as_tprod_layout(X)
+    ms = time_gpu(lambda: tp.tsvd(Xd), 20, torch)
+    rows["tsvd"] = {"workload": "64x48x16 iid N(0,1)", "gpu_ms": ms}
+    A = synth.lowrank_np(256, 512, 32, 10, seed=3, noise=0.01)
+    Ad = tp.as_tprod_layout(A)
+    ms = time_gpu(lambda: tp.tcx(Ad, 64, seed=0), 10, torch)
+    rows["tcx"] = {"workload": "256x512x32 tubal rank 10 + 1% noise, c = 64", "gpu_ms": ms}
+    truth, noisy, mask = synth.video_np(144, 256, 80, r=10, seed=0)
+    Xv = tp.as_tprod_layout(noisy)
+    Mv = tp.as_tprod_layout(mask, torch.uint8)
+    iters = 10
+
+    def run_svt():
+        tp.tcomplete_svt(Xv, Mv, iters)
+    ms = time_gpu(run_svt, 2, torch)
+    rows["svt"] = {"workload": "144x256x80 video, tubal rank 10, 50% observed", "iterations": iters,
+                   "gpu_ms": ms, "gpu_iterations_per_s": iters / (ms * 1e-3)}
+    if with_cpu:
+        from oracle import completion_ref, decomp_ref
+        t0 = time.perf_counter()
+        decomp_ref.tsvd(X.astype(np.float64))
+        rows["tsvd"]["oracle_ms"] = (time.perf_counter() - t0) * 1e3
+        t0 = time.perf_counter()
+        decomp_ref.tcx(A.astype(np.float64), 64, 0)
+        rows["tcx"]["oracle_ms"] = (time.perf_counter() - t0) * 1e3
+        t0 = time.perf_counter()
+        completion_ref.tcomplete_svt(noisy.astype(np.float64), mask.astype(bool), 2)
+        per_iter = (time.perf_counter() - t0) / 2
+        rows["svt"]["oracle_ms"] = per_iter * iters * 1e3
+        rows["svt"]["oracle_sample"] = "2 oracle iterations timed, scaled to 10"
+    for r in rows.values():
+        if "oracle_ms" in r:
+            r["speedup_vs_oracle"] = r["oracle_ms"] / r["gpu_ms"]
+    return rows
+
+
 def bench_rsvd(args, tp, torch, with_cpu):
     """Randomized low-tubal-rank t-SVD on the mass-spectrometry-shaped
     workload (128 x 128 pixels x 2000 channels, Gamma factors at tubal rank
@@ -242,6 +312,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--small", action="store_true", help="profiling case, not a bench number")
     ap.add_argument("--no-rsvd", action="store_true", help="skip the randomized t-SVD line")
+    ap.add_argument("--no-rows", action="store_true", help="skip the t-SVD / t-CX / ADMM rows")
     args = ap.parse_args()
     if args.small:
         use_small_case()
@@ -293,11 +364,7 @@ def main():
         nl = tp.launch_count() - n0
         if dist:
             dist.barrier()
-        t_ms = ev0.elapsed_time(ev1) / args.steps
-        if dist:
-            t = torch.tensor([t_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_ms = float(t.item())
+        t_ms = reduce_max(ev0.elapsed_time(ev1) / args.steps, dist, "cuda")
         return t_ms, pf, nl
 
     compare = None
@@ -357,11 +424,7 @@ def main():
             e2e_step()
         ev1.record(stream)
         torch.cuda.synchronize()
-        ems = ev0.elapsed_time(ev1) / args.e2e_steps
-        if dist:
-            t = torch.tensor([ems], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = reduce_max(ev0.elapsed_time(ev1) / args.e2e_steps, dist, "cuda")
         e2e = {"value": world * flops / (ems * 1e-3) / 1e12, "unit": "TFLOP/s",
                "ms_per_step": ems,
                "h2d_bytes_per_step": int(Ah.numel() * 4 + Bh.numel() * 4),
@@ -388,6 +451,9 @@ def main():
         rsvd = bench_rsvd(args, tp, torch, with_cpu=(rank == 0 and world == 1
                                                       and not args.no_cpu_baseline))
         rsvd["value"] *= world
+    rows = None
+    if not args.no_rows and not args.small:
+        rows = bench_rows(tp, torch, with_cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
 
     if rank == 0:
         line = {
@@ -407,6 +473,7 @@ def main():
             "kernels": kernels, "cpu_baseline": cpu, "clocks": clocks,
             "compare": compare,
             "secondary": rsvd,
+            "rows": rows,
         }
         print(json.dumps(line))
     if dist:

@@ -6,20 +6,22 @@
 // four real products (Re = ArBr - AiBi, Im = ArBi + AiBr); the minus sign is
 // the instruction descriptor's negate-A bit.
 //
-// One CTA computes a 128 x 128 output tile of one frequency slice:
-//   warp 0 lane 0   TMA producer: 8 operand planes per K block into a
+// Persistent kernel: one CTA per SM walks the list of 128 x 128 output tiles
+// (frequency slowest, so the CTAs in flight share a slice's operands in L2).
+//   warp 0 lane 0   TMA producer: 8 operand planes per 16-deep K block into a
 //                   3-stage shared-memory ring (mbarrier complete_tx)
 //   warp 1 lane 0   MMA issuer: 12 tcgen05.mma (K = 8) per 8-deep K step into
-//                   three TMEM accumulators: Re(A)Re(B) at columns 0..127,
-//                   Im(A)Im(B) at 128..255, Im at 256..383; tcgen05.commit
-//                   frees a stage and finally signals the epilogue
-//   warps 0-3       epilogue: tcgen05.ld 32x32b, Re = first - second,
-//                   bounds-checked coalesced stores
+//                   one of two TMEM accumulator sets (Re at +0, Im at +128
+//                   columns; sets at columns 0 and 256); tcgen05.commit frees a
+//                   stage, and after a tile's last K block marks its set full
+//   warps 2-5       epilogue: wait for a full set, tcgen05.ld 32x32b,
+//                   bounds-checked coalesced stores, mark the set empty; the
+//                   next tile's MMAs run into the other set meanwhile
 // Both operands are K-major (kind::tf32 takes no transposed operand): A
 // planes hold element (m, kk) at kk + lda*m, B planes (kk, n) at kk + ldb*n,
 // read as 64-byte-swizzled 128 x 16 tiles.  Every mbarrier wait is bounded:
-// on timeout the CTA records TP_DEV_TIMEOUT, waits (bounded) for its own
-// copies in flight, frees its tensor memory and exits.
+// on timeout the CTA records TP_DEV_TIMEOUT, stops issuing, waits (bounded)
+// for its own copies in flight, frees its tensor memory and exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -28,11 +30,11 @@
 namespace tp {
 namespace {
 
-constexpr int TM = 128, TN = 128, TBK = 16, STAGES = 3, NTHR = 128;
+constexpr int TM = 128, TN = 128, TBK = 16, STAGES = 3, NTHR = 192;
 constexpr uint32_t A_PLANE_BYTES = TM * TBK * 4;        // 8 KB
 constexpr uint32_t B_PLANE_BYTES = TN * TBK * 4;        // 8 KB
 constexpr uint32_t STAGE_BYTES = 4 * A_PLANE_BYTES + 4 * B_PLANE_BYTES;   // 64 KB
-constexpr uint32_t TMEM_COLS = 4 * TN;   // three accumulators used, allocation is a power of 2
+constexpr uint32_t TMEM_COLS = 4 * TN;   // two accumulator sets of (Re, Im)
 constexpr size_t SMEM_BYTES = size_t(STAGES) * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 constexpr long long WAIT_LIMIT = 4000000000LL;           // clock64 ticks (~2 s)
 
@@ -46,6 +48,7 @@ struct TcParams {
   int64_t K;
   int64_t h, n3;
   int32_t* status;
+  int mt, nt;   // output tiles along M and N
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -105,9 +108,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 constexpr uint32_t LAYOUT_SW64 = 4;
 
 // Instruction descriptor, kind::tf32: F32 accumulate, TF32 A and B, both
-// K-major, N = TN, M = TM.
+// K-major, N = TN, M = TM; bit 13 negates A.
 constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(TN >> 3) << 17) |
                            (uint32_t(TM >> 4) << 24);
+constexpr uint32_t IDESC_NEG = IDESC | (1u << 13);
 
 __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t accum) {
@@ -138,29 +142,39 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 __global__ void __launch_bounds__(NTHR, 1) cgemm_tc_kernel(const __grid_constant__ TcParams p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + size_t(STAGES) * STAGE_BYTES);
-  // bars[0..S-1] full, bars[S..2S-1] empty, bars[2S] accumulator ready; then TMEM slot
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  // full[S], empty[S], acc_full[2], acc_empty[2], then the TMEM slot
+  uint64_t* full = bars;
+  uint64_t* empty = bars + STAGES;
+  uint64_t* acc_full = bars + 2 * STAGES;
+  uint64_t* acc_empty = bars + 2 * STAGES + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
   __shared__ int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t f = blockIdx.z;
-  const int64_t m0 = int64_t(blockIdx.x) * TM, n0 = int64_t(blockIdx.y) * TN;
   const int64_t K = p.dynK ? *p.dynK : p.K;
   const int nkb = int((K + TBK - 1) / TBK);
-  const bool real_slice = (f == 0) || ((p.n3 % 2 == 0) && f == p.h - 1);
+  const int tiles_per_f = p.mt * p.nt;
+  const int64_t ntiles = int64_t(tiles_per_f) * p.h;
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(smem_u32(&bars[s]), 1);
-      mbar_init(smem_u32(&bars[STAGES + s]), 1);
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
     }
-    mbar_init(smem_u32(&bars[2 * STAGES]), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&acc_full[b]), 1);
+      mbar_init(smem_u32(&acc_empty[b]), 4);   // one arrival per epilogue warp
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     for (int i = 0; i < 4; ++i) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&p.a[i])) : "memory");
@@ -180,119 +194,140 @@ __global__ void __launch_bounds__(NTHR, 1) cgemm_tc_kernel(const __grid_constant
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0 && nkb > 0) {
-    // ---------------- TMA producer
-    int issued = 0;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES, r = kb / STAGES;
-      if (r > 0 && !mbar_wait(smem_u32(&bars[STAGES + s]), uint32_t((r - 1) & 1))) {
-        atomicExch(&abort_flag, 1);
-        break;
+    // ---------------- TMA producer: stage ring continues across tiles
+    int64_t it = 0;   // global K-block counter of this CTA
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const int f = int(t / tiles_per_f);
+      const int rem = int(t - int64_t(f) * tiles_per_f);
+      const int m0 = (rem / p.nt) * TM, n0 = (rem % p.nt) * TN;
+      for (int kb = 0; kb < nkb; ++kb, ++it) {
+        const int s = int(it % STAGES);
+        const int64_t r = it / STAGES;
+        if (r > 0 && !mbar_wait(smem_u32(&empty[s]), uint32_t((r - 1) & 1))) {
+          atomicExch(&abort_flag, 1);
+          ok = false;
+          break;
+        }
+        if (*(volatile int*)&abort_flag) { ok = false; break; }
+        const uint32_t fb = smem_u32(&full[s]);
+        const uint32_t st = smem_u32(smem + size_t(s) * STAGE_BYTES);
+        mbar_expect_tx(fb, STAGE_BYTES);
+        const int k0 = kb * TBK;
+        for (int pl = 0; pl < 4; ++pl) {
+          tma_load_3d(st + pl * A_PLANE_BYTES, &p.a[pl], k0, m0, f, fb);
+          tma_load_3d(st + 4 * A_PLANE_BYTES + pl * B_PLANE_BYTES, &p.b[pl], k0, n0, f, fb);
+        }
       }
-      if (*(volatile int*)&abort_flag) break;
-      const uint32_t full = smem_u32(&bars[s]);
-      const uint32_t st = smem_u32(smem + size_t(s) * STAGE_BYTES);
-      mbar_expect_tx(full, STAGE_BYTES);
-      const int k0 = kb * TBK;
-      for (int pl = 0; pl < 4; ++pl) {
-        tma_load_3d(st + pl * A_PLANE_BYTES, &p.a[pl], k0, int(m0), int(f), full);
-        tma_load_3d(st + 4 * A_PLANE_BYTES + pl * B_PLANE_BYTES, &p.b[pl], k0, int(n0), int(f),
-                    full);
-      }
-      issued = kb + 1;
     }
-    // drain: every issued stage's copies must have landed before the CTA may exit
-    for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb) {
-      const int s = kb % STAGES, r = kb / STAGES;
-      if (!mbar_wait(smem_u32(&bars[s]), uint32_t(r & 1))) break;
+    // drain: the last issued stages must land before the CTA may exit
+    const int64_t last = it;
+    for (int64_t q = (last > STAGES ? last - STAGES : 0); q < last; ++q) {
+      if (!mbar_wait(smem_u32(&full[int(q % STAGES)]), uint32_t((q / STAGES) & 1))) break;
     }
   } else if (warp == 1 && lane == 0 && nkb > 0) {
     // ---------------- MMA issuer
-    const uint32_t dp = tmem, dn = tmem + TN, di = tmem + 2 * TN;
+    int64_t it = 0;
+    int64_t local = 0;   // tiles processed by this CTA
     bool ok = true;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES, r = kb / STAGES;
-      if (!mbar_wait(smem_u32(&bars[s]), uint32_t(r & 1))) {
-        ok = false;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++local) {
+      const int f = int(t / tiles_per_f);
+      const bool real_slice = (f == 0) || ((p.n3 % 2 == 0) && f == p.h - 1);
+      const int b = int(local & 1);
+      const int64_t use = local >> 1;
+      if (use > 0 && !mbar_wait(smem_u32(&acc_empty[b]), uint32_t((use - 1) & 1))) {
+        atomicExch(&abort_flag, 1);
         break;
       }
-      if (*(volatile int*)&abort_flag) { ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t st = smem_u32(smem + size_t(s) * STAGE_BYTES);
-#pragma unroll
-      for (int sub = 0; sub < TBK / 8; ++sub) {
-        uint64_t a[4], b[4];
-#pragma unroll
-        for (int pl = 0; pl < 4; ++pl) {
-          a[pl] = smem_desc(st + pl * A_PLANE_BYTES + sub * 32, 16, 512, LAYOUT_SW64);
-          b[pl] = smem_desc(st + 4 * A_PLANE_BYTES + pl * B_PLANE_BYTES + sub * 32, 16, 512,
-                            LAYOUT_SW64);
+      const uint32_t dre = tmem + uint32_t(b) * (2 * TN), dim = dre + TN;
+      for (int kb = 0; kb < nkb; ++kb, ++it) {
+        const int s = int(it % STAGES);
+        if (!mbar_wait(smem_u32(&full[s]), uint32_t((it / STAGES) & 1))) {
+          ok = false;
+          break;
         }
-        const uint32_t first = (kb == 0 && sub == 0) ? 0u : 1u;
-        // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
-        mma_tf32(dp, a[0], b[0], IDESC, first);
-        mma_tf32(dp, a[0], b[1], IDESC, 1);
-        mma_tf32(dp, a[1], b[0], IDESC, 1);
-        if (!real_slice) {
-          mma_tf32(dn, a[2], b[2], IDESC, first);
-          mma_tf32(dn, a[2], b[3], IDESC, 1);
-          mma_tf32(dn, a[3], b[2], IDESC, 1);
-          mma_tf32(di, a[0], b[2], IDESC, first);
-          mma_tf32(di, a[0], b[3], IDESC, 1);
-          mma_tf32(di, a[1], b[2], IDESC, 1);
-          mma_tf32(di, a[2], b[0], IDESC, 1);
-          mma_tf32(di, a[2], b[1], IDESC, 1);
-          mma_tf32(di, a[3], b[0], IDESC, 1);
+        if (*(volatile int*)&abort_flag) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st = smem_u32(smem + size_t(s) * STAGE_BYTES);
+#pragma unroll
+        for (int sub = 0; sub < TBK / 8; ++sub) {
+          uint64_t a[4], bb[4];
+#pragma unroll
+          for (int pl = 0; pl < 4; ++pl) {
+            a[pl] = smem_desc(st + pl * A_PLANE_BYTES + sub * 32, 16, 512, LAYOUT_SW64);
+            bb[pl] = smem_desc(st + 4 * A_PLANE_BYTES + pl * B_PLANE_BYTES + sub * 32, 16, 512,
+                               LAYOUT_SW64);
+          }
+          const uint32_t first = (kb == 0 && sub == 0) ? 0u : 1u;
+          // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
+          mma_tf32(dre, a[0], bb[0], IDESC, first);
+          mma_tf32(dre, a[0], bb[1], IDESC, 1);
+          mma_tf32(dre, a[1], bb[0], IDESC, 1);
+          if (!real_slice) {
+            mma_tf32(dre, a[2], bb[2], IDESC_NEG, 1);
+            mma_tf32(dre, a[2], bb[3], IDESC_NEG, 1);
+            mma_tf32(dre, a[3], bb[2], IDESC_NEG, 1);
+            mma_tf32(dim, a[0], bb[2], IDESC, first);
+            mma_tf32(dim, a[0], bb[3], IDESC, 1);
+            mma_tf32(dim, a[1], bb[2], IDESC, 1);
+            mma_tf32(dim, a[2], bb[0], IDESC, 1);
+            mma_tf32(dim, a[2], bb[1], IDESC, 1);
+            mma_tf32(dim, a[3], bb[0], IDESC, 1);
+          }
         }
+        mma_commit(smem_u32(&empty[s]));   // stage s free once these MMAs finish
       }
-      mma_commit(smem_u32(&bars[STAGES + s]));   // stage s free once these MMAs finish
+      mma_commit(smem_u32(&acc_full[b]));  // accumulator set b final (or abandoned)
     }
     if (!ok) atomicExch(&abort_flag, 1);
-    mma_commit(smem_u32(&bars[2 * STAGES]));      // accumulators final (or abandoned)
-  }
-  __syncwarp();
-
-  // ---------------- epilogue (all four warps)
-  bool have = nkb > 0;
-  if (have) {
-    if (!mbar_wait(smem_u32(&bars[2 * STAGES]), 0u)) {
-      atomicExch(&abort_flag, 1);
-      have = false;
-    }
-  }
-  have = __all_sync(0xffffffffu, have);   // tcgen05.ld below is warp-collective
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const int64_t m = m0 + warp * 32 + lane;
-  float* zr = p.zr + f * p.sZ;
-  float* zi = p.zi + f * p.sZ;
-  for (int c0 = 0; c0 < TN; c0 += 32) {
-    uint32_t vp[32], vn[32], vi[32];
-    if (have) {
-      const uint32_t lane_base = uint32_t(warp * 32) << 16;
-      tmem_ld32(tmem + lane_base + uint32_t(c0), vp);
-      if (!real_slice) {
-        tmem_ld32(tmem + lane_base + uint32_t(TN + c0), vn);
-        tmem_ld32(tmem + lane_base + uint32_t(2 * TN + c0), vi);
+  } else if (warp >= 2) {
+    // ---------------- epilogue warps: TMEM lane quarter = warp % 4
+    const int q = warp & 3;
+    int64_t local = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++local) {
+      const int f = int(t / tiles_per_f);
+      const int rem = int(t - int64_t(f) * tiles_per_f);
+      const int64_t m0 = int64_t(rem / p.nt) * TM, n0 = int64_t(rem % p.nt) * TN;
+      const bool real_slice = (f == 0) || ((p.n3 % 2 == 0) && f == p.h - 1);
+      const int b = int(local & 1);
+      const int64_t use = local >> 1;
+      bool have = nkb > 0;
+      if (have && !mbar_wait(smem_u32(&acc_full[b]), uint32_t(use & 1))) {
+        atomicExch(&abort_flag, 1);
+        have = false;
       }
-    }
-    if (m < p.M) {
+      have = __all_sync(0xffffffffu, have);   // tcgen05.ld below is warp-collective
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int64_t m = m0 + q * 32 + lane;
+      float* zr = p.zr + int64_t(f) * p.sZ;
+      float* zi = p.zi + int64_t(f) * p.sZ;
+      const uint32_t base = tmem + (uint32_t(q * 32) << 16) + uint32_t(b) * (2 * TN);
+      for (int c0 = 0; c0 < TN; c0 += 32) {
+        uint32_t vr[32], vi[32];
+        if (have) {
+          tmem_ld32(base + uint32_t(c0), vr);
+          if (!real_slice) tmem_ld32(base + uint32_t(TN + c0), vi);
+        }
+        if (m < p.M) {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int64_t n = n0 + c0 + j;
-        if (n < p.N) {
-          float re = 0.f, im = 0.f;
-          if (have) {
-            re = __uint_as_float(vp[j]);
-            if (!real_slice) {
-              re -= __uint_as_float(vn[j]);
-              im = __uint_as_float(vi[j]);
+          for (int j = 0; j < 32; ++j) {
+            const int64_t n = n0 + c0 + j;
+            if (n < p.N) {
+              zr[m + p.ldz * n] = have ? __uint_as_float(vr[j]) : 0.f;
+              zi[m + p.ldz * n] = (have && !real_slice) ? __uint_as_float(vi[j]) : 0.f;
             }
           }
-          zr[m + p.ldz * n] = re;
-          zi[m + p.ldz * n] = im;
         }
       }
+      // hand set b back to the MMA warp
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0 && nkb > 0) mbar_arrive(smem_u32(&acc_empty[b]));
+      if (*(volatile int*)&abort_flag) break;
     }
   }
+  __syncwarp();
 
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -361,7 +396,8 @@ int launch_cgemm_tc(const CGemm& g, cudaStream_t st) {
     set_error("cgemm_tc: leading dimensions must be multiples of 4 floats");
     return TP_EALIGN;
   }
-  if (g.M > 0x7fffffff || g.N > 0x7fffffff || g.kcap > 0x7fffffff || g.h > 65535) {
+  if (g.M > 0x7fffffff || g.N > 0x7fffffff || g.kcap > 0x7fffffff || g.h > 65535 ||
+      (g.M + TM - 1) / TM * ((g.N + TN - 1) / TN) > 0x7fffffff / 65536) {
     set_error("cgemm_tc: sizes too large for one launch");
     return TP_EUNSUPPORTED;
   }
@@ -392,9 +428,15 @@ int launch_cgemm_tc(const CGemm& g, cudaStream_t st) {
   p.h = g.h;
   p.n3 = g.n3;
   p.status = g.status;
+  p.mt = int((g.M + TM - 1) / TM);
+  p.nt = int((g.N + TN - 1) / TN);
   cudaFuncSetAttribute(cgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        int(SMEM_BYTES));
-  const dim3 grid(unsigned((g.M + TM - 1) / TM), unsigned((g.N + TN - 1) / TN), unsigned(g.h));
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t ntiles = int64_t(p.mt) * p.nt * g.h;
+  const dim3 grid(unsigned(ntiles < sms ? ntiles : sms));
   {
     KernelScope ks("cgemm_tc", st);
     cgemm_tc_kernel<<<grid, NTHR, SMEM_BYTES, st>>>(p);
