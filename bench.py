@@ -262,7 +262,7 @@ def gpu_uuid(torch, dev):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # single-pass ncu capture of the full-size workload; valid only for the kernel
 # version it was taken on (profiles/cgemm_tc_2000x4000x1500x64_traffic.md).
-MEASURED_TRAFFIC = {"cgemm_tc": 864519680 + 755867392}
+MEASURED_TRAFFIC = {"cgemm_tc": 862899712 + 750405888}
 
 
 def roofline_for(name, ms_avg, cprime, peaks, sm_mhz):
