@@ -16,10 +16,11 @@
 // table exp(-2 pi i m / n3), m = k t mod n3.  KC is chosen per call to
 // minimise padding.  The (Re, Im) and (P, Q) accumulator pairs are updated
 // with Blackwell's packed two-lane float32 FMA.
-#include "tp_internal.cuh"
+#include "dft_common.cuh"
 
 namespace tp {
 namespace {
+using namespace dftc;
 
 #ifndef TP_DFT_TPT
 #define TP_DFT_TPT 2
@@ -28,13 +29,6 @@ constexpr int TPT = TP_DFT_TPT;  // tubes per thread
 constexpr int RB = 128;          // threads per block
 constexpr int TU = 8;            // samples (forward) or frequencies (inverse) loaded ahead
 constexpr int STAGE_BYTES_MAX = 64 * 1024;
-
-// Nearest tf32 value of x (10 explicit mantissa bits), as a float.
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
 
 // (cos, sin)(2 pi m / n3) for m < n3.  float sincospi (about 1 ulp; exact at
 // quarter turns, m/n3 in {0, 1/4, 1/2, 3/4}) keeps the tables off the slow
@@ -58,38 +52,6 @@ __device__ __forceinline__ void fold(float x0, float x1, int t, int n3, float& e
     e = x0 + x1;
     o = x0 - x1;
   }
-}
-
-struct Extent {
-  int64_t rows_eff, cols_eff, rows_pad, cols_pad;
-};
-__device__ __forceinline__ Extent extent_of(const DftGather& g) {
-  const int64_t count = g.dyn_count ? *g.dyn_count : (g.gather_dim == 1 ? g.rows : g.cols);
-  Extent x{g.rows, g.cols, g.rows, g.cols};
-  if (g.gather_dim == 1) {
-    x.rows_eff = count;
-    x.rows_pad = min(g.rows, (count + 31) / 32 * 32);   // zero tail for tiled consumers
-  } else if (g.gather_dim == 2) {
-    x.cols_eff = count;
-    x.cols_pad = min(g.cols, (count + 31) / 32 * 32);
-  }
-  return x;
-}
-
-__device__ __forceinline__ const float* tube_ptr(const DftGather& g, const Extent& x, int64_t r,
-                                                 int64_t c, float& s) {
-  s = 0.f;
-  if (r >= x.rows_eff || c >= x.cols_eff) return nullptr;
-  int64_t ro = r, co = c;
-  s = 1.0f;
-  if (g.gather_dim == 1) {
-    ro = g.idx[r];
-    if (g.scale) s = g.scale[r];
-  } else if (g.gather_dim == 2) {
-    co = g.idx[c];
-    if (g.scale) s = g.scale[c];
-  }
-  return g.src + ro * g.row_stride + co * g.col_stride;
 }
 
 // Wc[t*KC + q] = (cos, sin)(2 pi (k0+q) t / n3) for t <= nh, zero above.
@@ -445,6 +407,10 @@ int launch_irdft_kc(const float* in_re, const float* in_im, int64_t rows, int64_
 }  // namespace
 
 bool fft_supported(int64_t n3);
+bool rfft_reg_supported(int64_t n3);
+int launch_rfft_reg(const DftGather& g, cudaStream_t st);
+int launch_irfft_reg(const float* in_re, const float* in_im, int64_t rows, int64_t in_slice,
+                     int64_t n3, float* out, cudaStream_t st);
 int launch_fft_fwd(const float* X, int64_t rows, int64_t n3, float* ore, float* oim,
                    int64_t out_slice, cudaStream_t st);
 int launch_fft_inv(const float* ire, const float* iim, int64_t rows, int64_t in_slice, int64_t n3,
@@ -456,6 +422,12 @@ int launch_fft_inv(const float* ire, const float* iim, int64_t rows, int64_t in_
 #define TP_FFT_THRESHOLD 256
 #endif
 constexpr int64_t kFftThreshold = TP_FFT_THRESHOLD;
+// Power-of-two tubes up to 128 go through the register FFT (rfft_reg.cu);
+// building with -DTP_REG_FFT=0 keeps them on the direct contraction.
+#ifndef TP_REG_FFT
+#define TP_REG_FFT 1
+#endif
+constexpr bool kRegFft = TP_REG_FFT != 0;
 
 int launch_rdft(const DftGather& g, cudaStream_t st) {
   const bool plain = g.gather_dim == 0 && !g.out_transposed && !g.out_re_lo &&
@@ -470,6 +442,7 @@ int launch_rdft(const DftGather& g, cudaStream_t st) {
     return TP_EUNSUPPORTED;
   }
   if (g.rows == 0 || g.cols == 0) return TP_OK;
+  if (kRegFft && rfft_reg_supported(g.n3)) return launch_rfft_reg(g, st);
   switch (pick_kc(g.n3 / 2 + 1)) {
     case 8: return launch_rdft_kc<8>(g, st);
     case 12: return launch_rdft_kc<12>(g, st);
@@ -486,6 +459,8 @@ int launch_irdft(const float* in_re, const float* in_im, int64_t rows, int64_t i
     return TP_EUNSUPPORTED;
   }
   if (rows == 0) return TP_OK;
+  if (kRegFft && rfft_reg_supported(n3))
+    return launch_irfft_reg(in_re, in_im, rows, in_slice, n3, out, st);
   switch (pick_kc(n3 / 2 + 1)) {
     case 8: return launch_irdft_kc<8>(in_re, in_im, rows, in_slice, n3, out, st);
     case 12: return launch_irdft_kc<12>(in_re, in_im, rows, in_slice, n3, out, st);

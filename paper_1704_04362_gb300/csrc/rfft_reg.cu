@@ -1,0 +1,366 @@
+// Mode-3 DFT of real tubes (half spectrum) and its inverse for power-of-two
+// tube lengths N = 2 .. 128, one tube per thread, held in registers
+// (Section 2, "Operators": fft(X,[],3) / ifft(X,[],3); Algorithm 1 steps 2-3
+// and the final inverse).
+//
+// Forward.  The N real samples are packed as M = N/2 complex values
+// z_n = x_{2n} + i x_{2n+1}.  An M-point complex FFT (radix-2 decimation in
+// frequency, fully unrolled, output in bit-reversed order) gives Z_k, and the
+// spectra of the even and of the odd samples are
+//     E_k = (Z_k + conj Z_{M-k}) / 2,   O_k = (Z_k - conj Z_{M-k}) / (2i),
+// so that with w = exp(-2 pi i / N)
+//     X_k = E_k + w^k O_k,   X_{M-k} = conj(E_k - w^k O_k),
+//     X_0 = Re Z_0 + Im Z_0,  X_M = Re Z_0 - Im Z_0.
+// Inverse.  The same relations read backwards give, from the half spectrum,
+//     E_k = (X_k + conj X_{M-k}) / 2,   O_k = (X_k - conj X_{M-k}) conj(w^k) / 2,
+//     Z_k = E_k + i O_k,
+// and z = IFFT_M(Z) = conj(FFT_M(conj Z)) / M returns x_{2n} = Re z_n,
+// x_{2n+1} = Im z_n.  The imaginary parts of the real slices X_0 and X_M
+// are ignored, as the Hermitian completion requires.
+//
+// Each tube costs O(N log N) register arithmetic, so these kernels are bound
+// by their HBM traffic (the direct contraction costs O(N^2) and is bound by
+// instruction issue).  Twiddles are compile-time constants: a 128-entry
+// table exp(-2 pi i m / 128) evaluated by the compiler (Taylor series in
+// double, rounded once to float) and placed in constant memory, read at
+// indices known after unrolling.
+#include "dft_common.cuh"
+
+namespace tp {
+namespace {
+using namespace dftc;
+
+constexpr int kTw = 128;
+constexpr int kThreads = 256;
+
+constexpr double series_sin(double x) {   // |x| <= pi/4
+  double term = x, sum = x;
+  for (int n = 1; n <= 12; ++n) {
+    term *= -(x * x) / double((2 * n) * (2 * n + 1));
+    sum += term;
+  }
+  return sum;
+}
+constexpr double series_cos(double x) {   // |x| <= pi/4
+  double term = 1.0, sum = 1.0;
+  for (int n = 1; n <= 12; ++n) {
+    term *= -(x * x) / double((2 * n - 1) * (2 * n));
+    sum += term;
+  }
+  return sum;
+}
+
+struct TwTable {
+  float c[kTw];   // cos(2 pi m / 128)
+  float s[kTw];   // sin(2 pi m / 128)
+};
+
+// Angle 2 pi m / 128 = q (pi/2) + b with quadrant q and b = (pi/2) r / 128;
+// b above pi/4 is taken as the complement so that the series stay on [0, pi/4].
+constexpr TwTable make_twiddles() {
+  TwTable t{};
+  const double half_pi = 1.57079632679489661923;
+  for (int m = 0; m < kTw; ++m) {
+    const int q = (4 * m) / kTw;
+    const int r = 4 * m - q * kTw;
+    double cb = 0.0, sb = 0.0;
+    if (2 * r <= kTw) {
+      const double b = half_pi * double(r) / double(kTw);
+      cb = series_cos(b);
+      sb = series_sin(b);
+    } else {
+      const double b = half_pi * double(kTw - r) / double(kTw);
+      cb = series_sin(b);
+      sb = series_cos(b);
+    }
+    double c = cb, s = sb;
+    if (q == 1) {
+      c = -sb;
+      s = cb;
+    } else if (q == 2) {
+      c = -cb;
+      s = -sb;
+    } else if (q == 3) {
+      c = sb;
+      s = -cb;
+    }
+    t.c[m] = float(c);
+    t.s[m] = float(s);
+  }
+  return t;
+}
+
+__constant__ TwTable kTwd = make_twiddles();
+
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+
+__device__ __forceinline__ constexpr int bitrev(int k, int bits) {
+  int r = 0;
+  for (int b = 0; b < bits; ++b) r |= ((k >> b) & 1) << (bits - 1 - b);
+  return r;
+}
+
+// In-place M-point FFT (exp(-2 pi i nk / M)), natural order in, bit-reversed out.
+template <int M>
+__device__ __forceinline__ void fft_dif(float2 (&a)[M]) {
+  constexpr int S = ilog2(M);
+#pragma unroll
+  for (int st = 0; st < S; ++st) {
+    const int L = M >> (st + 1);   // butterfly half-span
+#pragma unroll
+    for (int b = 0; b < M; b += 2 * L) {
+#pragma unroll
+      for (int j = 0; j < L; ++j) {
+        const float2 u = a[b + j], v = a[b + j + L];
+        a[b + j] = make_float2(u.x + v.x, u.y + v.y);
+        const float dx = u.x - v.x, dy = u.y - v.y;
+        if (j == 0) {
+          a[b + j + L] = make_float2(dx, dy);
+        } else if (2 * j == L) {   // times exp(-i pi / 2) = -i
+          a[b + j + L] = make_float2(dy, -dx);
+        } else {                   // times exp(-2 pi i j / (2L)) = c - i s
+          const int m = j * (kTw / (2 * L));
+          const float c = kTwd.c[m], s = kTwd.s[m];
+          a[b + j + L] = make_float2(fmaf(dx, c, dy * s), fmaf(dy, c, -(dx * s)));
+        }
+      }
+    }
+  }
+}
+
+// Half spectrum X_0 .. X_M of the packed tube z (destroyed); put(k, re, im).
+template <int N, class Put>
+__device__ __forceinline__ void forward_tube(float2 (&z)[N / 2], Put&& put) {
+  constexpr int M = N / 2, B = ilog2(N / 2);
+  fft_dif<M>(z);
+  const float2 z0 = z[0];
+  put(0, z0.x + z0.y, 0.f);
+  put(M, z0.x - z0.y, 0.f);
+#pragma unroll
+  for (int k = 1; 2 * k <= M; ++k) {
+    const float2 A = z[bitrev(k, B)], Bv = z[bitrev(M - k, B)];
+    const float ex = 0.5f * (A.x + Bv.x), ey = 0.5f * (A.y - Bv.y);
+    const float ox = 0.5f * (A.y + Bv.y), oy = -0.5f * (A.x - Bv.x);   // (Z_k - conj Z_{M-k}) / 2i
+    const int m = k * (kTw / N);
+    const float c = kTwd.c[m], s = kTwd.s[m];                            // w^k = c - i s
+    const float tx = fmaf(ox, c, oy * s), ty = fmaf(oy, c, -(ox * s));
+    put(k, ex + tx, ey + ty);
+    if (2 * k != M) put(M - k, ex - tx, ty - ey);
+  }
+}
+
+// Samples of one tube from its half spectrum X[0 .. M]: x_{2n} = z[n].x,
+// x_{2n+1} = z[n].y on return (z in natural order).
+template <int N>
+__device__ __forceinline__ void inverse_tube(const float2 (&X)[N / 2 + 1], float2 (&z)[N / 2]) {
+  constexpr int M = N / 2, B = ilog2(N / 2);
+  float2 a[M];
+  a[0] = make_float2(0.5f * (X[0].x + X[M].x), -0.5f * (X[0].x - X[M].x));   // conj Z_0
+#pragma unroll
+  for (int k = 1; 2 * k <= M; ++k) {
+    const float2 P = X[k], Q = X[M - k];
+    const float ex = 0.5f * (P.x + Q.x), ey = 0.5f * (P.y - Q.y);
+    const float dx = P.x - Q.x, dy = P.y + Q.y;                        // X_k - conj X_{M-k}
+    const int m = k * (kTw / N);
+    const float c = kTwd.c[m], s = kTwd.s[m];                          // conj(w^k) = c + i s
+    const float ox = 0.5f * fmaf(dx, c, -(dy * s)), oy = 0.5f * fmaf(dx, s, dy * c);
+    a[k] = make_float2(ex - oy, -(ey + ox));                           // conj(E + i O)
+    if (2 * k != M) a[M - k] = make_float2(ex + oy, ey - ox);          // conj(conj E + i conj O)
+  }
+  fft_dif<M>(a);
+  constexpr float inv = 1.0f / float(M);
+#pragma unroll
+  for (int n = 0; n < M; ++n) {
+    const float2 v = a[bitrev(n, B)];
+    z[n] = make_float2(v.x * inv, -v.y * inv);
+  }
+}
+
+// The value of v, hidden from the optimiser so that the per-frequency output
+// offsets are formed inside each tube's iteration instead of being hoisted
+// out of the grid-stride loop (which would hold them all in registers).
+__device__ __forceinline__ int64_t opaque(int64_t v) {
+  asm volatile("" : "+l"(v));
+  return v;
+}
+
+__device__ __forceinline__ void put_value(const DftGather& g, int64_t o, float re, float im) {
+  if (g.out_re_lo) {
+    const float hr = tf32_rna(re), hi = tf32_rna(im);
+    g.out_re[o] = hr;
+    g.out_im[o] = hi;
+    g.out_re_lo[o] = re - hr;
+    g.out_im_lo[o] = im - hi;
+  } else {
+    g.out_re[o] = re;
+    g.out_im[o] = im;
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void load_tube(const float* p, float s, int64_t ss, float2 (&z)[N / 2]) {
+  if (p) {
+#pragma unroll
+    for (int n = 0; n < N / 2; ++n)
+      z[n] = make_float2(s * __ldg(p + int64_t(2 * n) * ss), s * __ldg(p + int64_t(2 * n + 1) * ss));
+  } else {
+#pragma unroll
+    for (int n = 0; n < N / 2; ++n) z[n] = make_float2(0.f, 0.f);
+  }
+}
+
+// Output element (r, c) of slice k at k*out_slice + r + out_ld*c.  Threads
+// walk the rows fastest, so reads and writes are coalesced along r (for a row
+// gather the reads are sector-granular gathers of the picked rows).
+template <int N>
+__global__ void __launch_bounds__(kThreads) rfft_reg_kernel(const DftGather g) {
+  const Extent ex = extent_of(g);
+  const int64_t total = ex.rows_pad * ex.cols_pad;
+#pragma unroll 1
+  for (int64_t e = int64_t(blockIdx.x) * kThreads + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * kThreads) {
+    const int64_t c = e / ex.rows_pad, r = e - c * ex.rows_pad;
+    float s;
+    const float* p = tube_ptr(g, ex, r, c, s);
+    float2 z[N / 2];
+    load_tube<N>(p, s, g.slice_stride, z);
+    const int64_t o = r + g.out_ld * c;
+    const int64_t os = opaque(g.out_slice);
+    forward_tube<N>(z, [&](int k, float re, float im) { put_value(g, o + int64_t(k) * os, re, im); });
+  }
+}
+
+// Output element (r, c) of slice k at k*out_slice + c + out_ld*r.  A block
+// owns tiles of 32 rows x 8 columns; a warp covers 4 rows x 8 columns, so a
+// load reads 8 runs of 4 consecutive rows and a store writes 4 runs of 8
+// consecutive columns (32 bytes each).
+template <int N>
+__global__ void __launch_bounds__(kThreads) rfft_reg_t_kernel(const DftGather g) {
+  const Extent ex = extent_of(g);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lr = warp * 4 + (lane >> 3), lc = lane & 7;
+  const int64_t tr = (ex.rows_pad + 31) / 32, tcn = (ex.cols_pad + 7) / 8;
+#pragma unroll 1
+  for (int64_t t = blockIdx.x; t < tr * tcn; t += gridDim.x) {
+    const int64_t tj = t / tr, ti = t - tj * tr;
+    const int64_t r = ti * 32 + lr, c = tj * 8 + lc;
+    if (r >= ex.rows_pad || c >= ex.cols_pad) continue;
+    float s;
+    const float* p = tube_ptr(g, ex, r, c, s);
+    float2 z[N / 2];
+    load_tube<N>(p, s, g.slice_stride, z);
+    const int64_t o = c + g.out_ld * r;
+    const int64_t os = opaque(g.out_slice);
+    forward_tube<N>(z, [&](int k, float re, float im) { put_value(g, o + int64_t(k) * os, re, im); });
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads) irfft_reg_kernel(const float* __restrict__ in_re,
+                                                             const float* __restrict__ in_im,
+                                                             int64_t rows, int64_t in_slice,
+                                                             float* __restrict__ out) {
+  constexpr int M = N / 2;
+#pragma unroll 1
+  for (int64_t r = int64_t(blockIdx.x) * kThreads + threadIdx.x; r < rows;
+       r += int64_t(gridDim.x) * kThreads) {
+    float2 X[M + 1];
+#pragma unroll
+    for (int k = 0; k <= M; ++k) {
+      const float re = __ldg(in_re + int64_t(k) * in_slice + r);
+      const float im = (k == 0 || k == M) ? 0.f : __ldg(in_im + int64_t(k) * in_slice + r);
+      X[k] = make_float2(re, im);
+    }
+    float2 z[M];
+    inverse_tube<N>(X, z);
+#pragma unroll
+    for (int n = 0; n < M; ++n) {
+      out[r + rows * int64_t(2 * n)] = z[n].x;
+      out[r + rows * int64_t(2 * n + 1)] = z[n].y;
+    }
+  }
+}
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    sms = 152;
+  return sms;
+}
+
+unsigned grid_for(int64_t work_blocks, int per_sm) {
+  const int64_t cap = int64_t(sm_count()) * per_sm;
+  int64_t b = work_blocks < cap ? work_blocks : cap;
+  return unsigned(b < 1 ? 1 : b);
+}
+
+constexpr int blocks_per_sm(int N) { return N <= 64 ? 4 : 2; }
+
+template <int N>
+int launch_fwd(const DftGather& g, cudaStream_t st) {
+  if (g.out_transposed) {
+    const int64_t tiles = (g.rows + 31) / 32 * ((g.cols + 7) / 8);
+    {
+      KernelScope ks("rdft_t", st);
+      rfft_reg_t_kernel<N><<<grid_for(tiles, blocks_per_sm(N)), kThreads, 0, st>>>(g);
+    }
+    return launch_status("rfft_reg_t_kernel");
+  }
+  {
+    KernelScope ks("rdft", st);
+    rfft_reg_kernel<N><<<grid_for((g.rows * g.cols + kThreads - 1) / kThreads, blocks_per_sm(N)),
+                         kThreads, 0, st>>>(g);
+  }
+  return launch_status("rfft_reg_kernel");
+}
+
+template <int N>
+int launch_inv(const float* in_re, const float* in_im, int64_t rows, int64_t in_slice, float* out,
+               cudaStream_t st) {
+  {
+    KernelScope ks("irdft", st);
+    irfft_reg_kernel<N><<<grid_for((rows + kThreads - 1) / kThreads, blocks_per_sm(N)), kThreads, 0,
+                          st>>>(in_re, in_im, rows, in_slice, out);
+  }
+  return launch_status("irfft_reg_kernel");
+}
+
+}  // namespace
+
+bool rfft_reg_supported(int64_t n3) {
+  return n3 >= 2 && n3 <= kTw && (n3 & (n3 - 1)) == 0;
+}
+
+int launch_rfft_reg(const DftGather& g, cudaStream_t st) {
+  switch (g.n3) {
+    case 2: return launch_fwd<2>(g, st);
+    case 4: return launch_fwd<4>(g, st);
+    case 8: return launch_fwd<8>(g, st);
+    case 16: return launch_fwd<16>(g, st);
+    case 32: return launch_fwd<32>(g, st);
+    case 64: return launch_fwd<64>(g, st);
+    case 128: return launch_fwd<128>(g, st);
+    default:
+      set_error("register FFT: n3 = %lld is not a power of two in [2, 128]", (long long)g.n3);
+      return TP_EUNSUPPORTED;
+  }
+}
+
+int launch_irfft_reg(const float* in_re, const float* in_im, int64_t rows, int64_t in_slice,
+                     int64_t n3, float* out, cudaStream_t st) {
+  switch (n3) {
+    case 2: return launch_inv<2>(in_re, in_im, rows, in_slice, out, st);
+    case 4: return launch_inv<4>(in_re, in_im, rows, in_slice, out, st);
+    case 8: return launch_inv<8>(in_re, in_im, rows, in_slice, out, st);
+    case 16: return launch_inv<16>(in_re, in_im, rows, in_slice, out, st);
+    case 32: return launch_inv<32>(in_re, in_im, rows, in_slice, out, st);
+    case 64: return launch_inv<64>(in_re, in_im, rows, in_slice, out, st);
+    case 128: return launch_inv<128>(in_re, in_im, rows, in_slice, out, st);
+    default:
+      set_error("register FFT: n3 = %lld is not a power of two in [2, 128]", (long long)n3);
+      return TP_EUNSUPPORTED;
+  }
+}
+
+}  // namespace tp

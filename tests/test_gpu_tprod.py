@@ -15,8 +15,8 @@ def dev(x):
     return tp.as_tprod_layout(x)
 
 
-@pytest.mark.parametrize("n3", [1, 2, 3, 5, 16, 17, 64, 120, 257, 260, 512, 600, 1001, 2000,
-                                4096])
+@pytest.mark.parametrize("n3", [1, 2, 3, 4, 5, 8, 16, 17, 32, 64, 120, 128, 256, 257, 260, 512,
+                                600, 1001, 2000, 4096])
 def test_rdft_irdft_match_oracle(n3):
     X = synth.iid_normal((37, 5, n3), seed=n3)
     Xr, Xi = tp.rdft3(dev(X))
@@ -45,6 +45,10 @@ SHAPES = [
     (130, 70, 67, 17),    # ragged against the 128 x 64 x 16 tiles
     (257, 33, 129, 2),
     (40, 200, 30, 64),
+    (33, 20, 40, 128),    # power-of-two tube lengths: the register FFT
+    (70, 37, 41, 32),
+    (9, 8, 7, 4),
+    (5, 6, 3, 8),
 ]
 
 
@@ -122,7 +126,8 @@ def test_draw_edge_cases():
 @pytest.mark.parametrize("mode", [tp.TP_PROB_AB, tp.TP_PROB_A2])
 @pytest.mark.parametrize("n1,n2,n4,n3,c", [(64, 48, 32, 16, 12), (50, 300, 41, 7, 60),
                                            (33, 130, 20, 64, 400), (20, 9, 5, 4, 1),
-                                           (260, 500, 300, 8, 100)])
+                                           (260, 500, 300, 8, 100), (70, 90, 45, 128, 30),
+                                           (40, 64, 30, 32, 20), (17, 25, 9, 2, 10)])
 def test_tprod_sampled_matches_oracle(mode, n1, n2, n4, n3, c, prec):
     A = synth.lowrank_np(n1, n2, n3, 4, seed=6, noise=0.01)
     B = synth.lowrank_np(n2, n4, n3, 4, seed=7, noise=0.01)
