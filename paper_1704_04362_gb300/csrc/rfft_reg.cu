@@ -230,20 +230,26 @@ __global__ void __launch_bounds__(kThreads) rfft_reg_kernel(const DftGather g) {
   }
 }
 
-// Output element (r, c) of slice k at k*out_slice + c + out_ld*r.  A block
-// owns tiles of 32 rows x 8 columns; a warp covers 4 rows x 8 columns, so a
-// load reads 8 runs of 4 consecutive rows and a store writes 4 runs of 8
-// consecutive columns (32 bytes each).
+// Output element (r, c) of slice k at k*out_slice + c + out_ld*r.  A warp
+// covers (32 / LC) rows x LC columns, so a load reads LC runs of 32 / LC
+// consecutive rows and a store writes 32 / LC runs of LC consecutive columns;
+// a block's 8 warps stack along the rows.
+#ifndef TP_RFFT_T_LC
+#define TP_RFFT_T_LC 16
+#endif
+constexpr int LC = TP_RFFT_T_LC;
+constexpr int TROWS = (kThreads / 32) * (32 / LC);   // rows of a block tile
+
 template <int N>
 __global__ void __launch_bounds__(kThreads) rfft_reg_t_kernel(const DftGather g) {
   const Extent ex = extent_of(g);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int lr = warp * 4 + (lane >> 3), lc = lane & 7;
-  const int64_t tr = (ex.rows_pad + 31) / 32, tcn = (ex.cols_pad + 7) / 8;
+  const int lr = warp * (32 / LC) + lane / LC, lc = lane % LC;
+  const int64_t tr = (ex.rows_pad + TROWS - 1) / TROWS, tcn = (ex.cols_pad + LC - 1) / LC;
 #pragma unroll 1
   for (int64_t t = blockIdx.x; t < tr * tcn; t += gridDim.x) {
     const int64_t tj = t / tr, ti = t - tj * tr;
-    const int64_t r = ti * 32 + lr, c = tj * 8 + lc;
+    const int64_t r = ti * TROWS + lr, c = tj * LC + lc;
     if (r >= ex.rows_pad || c >= ex.cols_pad) continue;
     float s;
     const float* p = tube_ptr(g, ex, r, c, s);
@@ -252,6 +258,77 @@ __global__ void __launch_bounds__(kThreads) rfft_reg_t_kernel(const DftGather g)
     const int64_t o = c + g.out_ld * r;
     const int64_t os = opaque(g.out_slice);
     forward_tube<N>(z, [&](int k, float re, float im) { put_value(g, o + int64_t(k) * os, re, im); });
+  }
+}
+
+// Staged form of the transposed transform (unit row stride, no row gather,
+// N <= 64).  A block owns tiles of 8 rows x 32 columns.  The tile's samples
+// are first copied to shared memory as 32-byte runs (8 consecutive rows of
+// one column and one sample), then each thread transforms the tube (r, c)
+// from shared memory and a warp stores 128-byte runs along the columns.
+// Shared layout xs[t][row][col] with a row pitch of 36 floats: the copy
+// (8 rows x 4 columns per warp access) and the reads (32 columns of one row)
+// are both free of bank conflicts.
+constexpr int SROWS = 8, SCOLS = 32, SPITCH = 36;
+static_assert(SROWS * SCOLS == kThreads, "one tube per thread");
+
+template <int N>
+__global__ void __launch_bounds__(kThreads) rfft_reg_ts_kernel(const DftGather g) {
+  extern __shared__ float xs[];   // [N][SROWS][SPITCH]
+  __shared__ const float* cbase[SCOLS];
+  __shared__ float cscale[SCOLS];
+  const Extent ex = extent_of(g);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t tr = (ex.rows_pad + SROWS - 1) / SROWS, tcn = (ex.cols_pad + SCOLS - 1) / SCOLS;
+#pragma unroll 1
+  for (int64_t t = blockIdx.x; t < tr * tcn; t += gridDim.x) {
+    const int64_t tj = t / tr, ti = t - tj * tr;
+    const int64_t r0 = ti * SROWS, c0 = tj * SCOLS;
+    if (tid < SCOLS) {
+      float sc;
+      const float* p = tube_ptr(g, ex, 0, c0 + tid, sc);   // column base (row 0)
+      cbase[tid] = p;
+      cscale[tid] = sc;
+    }
+    __syncthreads();
+    // copy: run q = (column, sample); a warp access covers 4 runs x 8 rows.
+    // Asynchronous 4-byte copies keep every sample of the tile in flight;
+    // padding (rows or columns past the data) is zero-filled.
+    {
+      const int row = lane & 7, col = warp * 4 + (lane >> 3);
+      const float* p = cbase[col];
+      const bool ok = p != nullptr && r0 + row < ex.rows_eff;
+      const float* src = ok ? p + (r0 + row) : g.src;
+      const int64_t ss = ok ? opaque(g.slice_stride) : 0;
+      const int nbytes = ok ? 4 : 0;
+      uint32_t dst = uint32_t(__cvta_generic_to_shared(&xs[row * SPITCH + col]));
+#pragma unroll
+      for (int it = 0; it < N; ++it) {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src),
+                     "r"(nbytes)
+                     : "memory");
+        src += ss;
+        dst += SROWS * SPITCH * sizeof(float);
+      }
+      asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+    __syncthreads();
+    {
+      const int row = tid / SCOLS, col = tid % SCOLS;
+      const int64_t r = r0 + row, c = c0 + col;
+      const float s = cscale[col];
+      float2 z[N / 2];
+#pragma unroll
+      for (int n = 0; n < N / 2; ++n)
+        z[n] = make_float2(s * xs[(2 * n * SROWS + row) * SPITCH + col],
+                           s * xs[((2 * n + 1) * SROWS + row) * SPITCH + col]);
+      if (r < ex.rows_pad && c < ex.cols_pad) {
+        const int64_t o = c + g.out_ld * r;
+        const int64_t os = opaque(g.out_slice);
+        forward_tube<N>(z, [&](int k, float re, float im) { put_value(g, o + int64_t(k) * os, re, im); });
+      }
+    }
+    __syncthreads();   // xs and cbase are rewritten by the next tile
   }
 }
 
@@ -289,27 +366,52 @@ int sm_count() {
   return sms;
 }
 
-unsigned grid_for(int64_t work_blocks, int per_sm) {
-  const int64_t cap = int64_t(sm_count()) * per_sm;
-  int64_t b = work_blocks < cap ? work_blocks : cap;
+// TP_RFFT_OVERSUB waves of resident blocks (the kernels stride over their
+// work), or fewer blocks when the work is smaller.
+#ifndef TP_RFFT_OVERSUB
+#define TP_RFFT_OVERSUB 4
+#endif
+template <class Kernel>
+unsigned grid_for(Kernel kernel, int64_t work_blocks, size_t smem = 0) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const int64_t cap = int64_t(sm_count()) * per_sm * TP_RFFT_OVERSUB;
+  const int64_t b = work_blocks < cap ? work_blocks : cap;
   return unsigned(b < 1 ? 1 : b);
 }
 
-constexpr int blocks_per_sm(int N) { return N <= 64 ? 4 : 2; }
+#ifndef TP_RFFT_T_STAGE
+#define TP_RFFT_T_STAGE 1
+#endif
 
 template <int N>
 int launch_fwd(const DftGather& g, cudaStream_t st) {
+  if constexpr (N <= 64) {
+    if (TP_RFFT_T_STAGE && g.out_transposed && g.gather_dim != 1 && g.row_stride == 1) {
+      const size_t smem = size_t(N) * SROWS * SPITCH * sizeof(float);
+      cudaFuncSetAttribute(rfft_reg_ts_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(smem));
+      const int64_t tiles = (g.rows + SROWS - 1) / SROWS * ((g.cols + SCOLS - 1) / SCOLS);
+      {
+        KernelScope ks("rdft_t", st);
+        rfft_reg_ts_kernel<N><<<grid_for(rfft_reg_ts_kernel<N>, tiles, smem), kThreads, smem, st>>>(g);
+      }
+      return launch_status("rfft_reg_ts_kernel");
+    }
+  }
   if (g.out_transposed) {
-    const int64_t tiles = (g.rows + 31) / 32 * ((g.cols + 7) / 8);
+    const int64_t tiles = (g.rows + TROWS - 1) / TROWS * ((g.cols + LC - 1) / LC);
     {
       KernelScope ks("rdft_t", st);
-      rfft_reg_t_kernel<N><<<grid_for(tiles, blocks_per_sm(N)), kThreads, 0, st>>>(g);
+      rfft_reg_t_kernel<N><<<grid_for(rfft_reg_t_kernel<N>, tiles), kThreads, 0, st>>>(g);
     }
     return launch_status("rfft_reg_t_kernel");
   }
   {
     KernelScope ks("rdft", st);
-    rfft_reg_kernel<N><<<grid_for((g.rows * g.cols + kThreads - 1) / kThreads, blocks_per_sm(N)),
+    rfft_reg_kernel<N><<<grid_for(rfft_reg_kernel<N>, (g.rows * g.cols + kThreads - 1) / kThreads),
                          kThreads, 0, st>>>(g);
   }
   return launch_status("rfft_reg_kernel");
@@ -320,8 +422,8 @@ int launch_inv(const float* in_re, const float* in_im, int64_t rows, int64_t in_
                cudaStream_t st) {
   {
     KernelScope ks("irdft", st);
-    irfft_reg_kernel<N><<<grid_for((rows + kThreads - 1) / kThreads, blocks_per_sm(N)), kThreads, 0,
-                          st>>>(in_re, in_im, rows, in_slice, out);
+    irfft_reg_kernel<N><<<grid_for(irfft_reg_kernel<N>, (rows + kThreads - 1) / kThreads),
+                          kThreads, 0, st>>>(in_re, in_im, rows, in_slice, out);
   }
   return launch_status("irfft_reg_kernel");
 }
