@@ -7,6 +7,11 @@ its RMS; c = 400, probabilities proportional to ||A(:,j,:)|| ||B(j,:,:)||,
 Philox seed 0.  One step = one tprod_sampled call: slice norms of A and B,
 probabilities and Bernoulli picks, rescaled gathers fused into the mode-3
 DFTs, facewise complex GEMMs of the 33 half-spectrum slices, inverse DFT.
+The timed form (--precision, default bf16x3) runs the facewise GEMMs on the
+tensor cores with each operand split into a bf16 hi + lo pair and float32
+accumulation; the 3xTF32 split and the plain FP32 form are timed beside it
+(--compare).  All three are held to relative error 1e-5 against the float64
+oracle at this workload by tests/test_gpu_fullsize.py.
 
 metric  "t-product TFLOP/s": nominal facewise-GEMM flops of the step
         (8 n1 c' n4 per complex slice, 2 n1 c' n4 per real slice) divided by
@@ -262,10 +267,28 @@ def gpu_uuid(torch, dev):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # single-pass ncu capture of the full-size workload; valid only for the kernel
 # version it was taken on (profiles/cgemm_tc_2000x4000x1500x64_traffic.md).
-MEASURED_TRAFFIC = {"cgemm_tc": 862899712 + 750405888}
+MEASURED_TRAFFIC = {"cgemm_tc:bf16x3": 475086848 + 739951872}
 
 
-def roofline_for(name, ms_avg, cprime, peaks, sm_mhz):
+def kernel_bytes(name, cprime, precision):
+    """Algorithmic DRAM bytes per launch of the HBM-bound kernels of one step
+    (inputs read once, outputs written once; the picked-index dimension of the
+    transform outputs is padded to 32 with zeros for the tensor-core tiles)."""
+    h = N3 // 2 + 1
+    kp = (cprime + 31) // 32 * 32
+    split = {"fp32": 8.0, "tf32x3": 16.0, "bf16x3": 8.0}[precision]   # bytes per complex output
+    if precision == "fp32":
+        kp = cprime
+    return {
+        "norms_lateral": 4.0 * N1 * N2 * N3,
+        "norms_horizontal": 4.0 * N2 * N4 * N3,
+        "rdft_t": 4.0 * N1 * cprime * N3 + split * N1 * kp * h,
+        "rdft": 4.0 * cprime * N4 * N3 + split * kp * N4 * h,
+        "irdft": 8.0 * N1 * N4 * h + 4.0 * N1 * N4 * N3,
+    }.get(name)
+
+
+def roofline_for(name, ms_avg, cprime, peaks, sm_mhz, precision="tf32x3"):
     """Algorithmic work per launch of the named kernel and its roofline."""
     h = N3 // 2 + 1
     fl = gemm_flops(N1, cprime, N4, N3)
@@ -277,26 +300,27 @@ def roofline_for(name, ms_avg, cprime, peaks, sm_mhz):
                 "frac": ach / peak, "traffic": None,
                 "peak_src": "derived: 152 SM x 128 FP32 lanes x 2 x sm_max_mhz"}
     if name == "cgemm_tc":
-        peak = peaks["bf16_tflops"] / 2.0   # tf32 dense = bf16 / 2 (nominal ratio)
+        bf16 = precision == "bf16x3"
+        # tf32 dense = bf16 / 2 (nominal ratio); the BF16x3 split runs at the bf16 rate
+        peak = peaks["bf16_tflops"] / (1.0 if bf16 else 2.0)
         ach = 3 * fl / (ms_avg * 1e-3) / 1e12
-        h = N3 // 2 + 1
-        kp = (cprime + 15) // 16 * 16
-        alg = 16.0 * (N1 + N4) * kp * h + 8.0 * N1 * N4 * h
+        kblk = 32 if bf16 else 16
+        kp = (cprime + kblk - 1) // kblk * kblk
+        esz = 2.0 if bf16 else 4.0
+        alg = 4 * esz * (N1 + N4) * kp * h + 8.0 * N1 * N4 * h
         return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": MEASURED_TRAFFIC.get("cgemm_tc"),
+                "frac": ach / peak, "traffic": MEASURED_TRAFFIC.get("cgemm_tc:" + precision),
                 "algorithmic_bytes": alg,
-                "peak_src": peaks["src"] + " bf16 x 1/2 (tf32 nominal ratio)",
-                "work": "3 tf32 products per real product of the 8 n1 c' n4 nominal flops"}
-    bytes_per = {
-        "norms_lateral": 4.0 * N1 * N2 * N3,
-        "norms_horizontal": 4.0 * N2 * N4 * N3,
-        "irdft": 8.0 * N1 * N4 * h + 4.0 * N1 * N4 * N3,
-    }.get(name)
+                "peak_src": peaks["src"] + (" bf16" if bf16 else " bf16 x 1/2 (tf32 nominal ratio)"),
+                "work": "3 %s products per real product of the 8 n1 c' n4 nominal flops"
+                        % ("bf16" if bf16 else "tf32")}
+    bytes_per = kernel_bytes(name, cprime, precision)
     if bytes_per is None:
         return None
     ach = bytes_per / (ms_avg * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_src": peaks["src"]}
+            "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_src": peaks["src"],
+            "algorithmic_bytes": bytes_per}
 
 
 def main():
@@ -305,9 +329,10 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3", "bf16x3"])
-    ap.add_argument("--compare", default="fp32",
-                    help="also time this precision (the plain FP32 form) unless 'none'")
+    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "tf32x3", "bf16x3"])
+    ap.add_argument("--compare", default="tf32x3,fp32",
+                    help="comma-separated precisions also timed (the 3xTF32 split and the plain "
+                         "FP32 form), or 'none'")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--small", action="store_true", help="profiling case, not a bench number")
@@ -367,11 +392,12 @@ def main():
         t_ms = reduce_max(ev0.elapsed_time(ev1) / args.steps, dist, "cuda")
         return t_ms, pf, nl
 
-    compare = None
-    if args.compare != "none" and args.compare != args.precision:
+    compare = []
+    for cp in [c for c in args.compare.split(",") if c and c != "none" and c != args.precision]:
         Zc = tp.empty_tensor(N1, N4, N3)
-        c_ms, _, _ = timed(PREC[args.compare], Zc)
-        compare = {"precision": args.compare, "ms_per_step": c_ms}
+        c_ms, c_prof, _ = timed(PREC[cp], Zc)
+        compare.append({"precision": cp, "ms_per_step": c_ms, "Z": Zc,
+                        "kernels": {k: v[0] / max(1, v[1]) for k, v in c_prof.items()}})
 
     sampler = ClockSampler(gpu_uuid(torch, local_rank))
     sampler.start()
@@ -380,12 +406,13 @@ def main():
     cprime = int(cnt.item())
     flops = gemm_flops(N1, cprime, N4, N3)
     value = world * flops / (ms * 1e-3) / 1e12
-    if compare is not None:
-        compare["value"] = world * flops / (compare["ms_per_step"] * 1e-3) / 1e12
-        # agreement of the two GPU forms (each is checked against the float64
-        # oracle in tests/test_gpu_fullsize.py)
-        compare["rel_fro_diff"] = float(torch.linalg.vector_norm((Z - Zc).double()) /
-                                        torch.linalg.vector_norm(Zc.double()))
+    for cm in compare:
+        cm["value"] = world * flops / (cm["ms_per_step"] * 1e-3) / 1e12
+        # agreement with the headline form (each form is checked against the
+        # float64 oracle in tests/test_gpu_fullsize.py)
+        Zc = cm.pop("Z")
+        cm["rel_fro_diff"] = float(torch.linalg.vector_norm((Z - Zc).double()) /
+                                   torch.linalg.vector_norm(Z.double()))
         del Zc
 
     # per-kernel breakdown and roofline of the dominant kernel
@@ -393,7 +420,12 @@ def main():
                    "share": v[0] / max(1e-9, sum(x[0] for x in prof.values()))}
                for k, v in prof.items()}
     dom = max(prof, key=lambda k: prof[k][0]) if prof else None
-    roof = roofline_for(dom, prof[dom][0] / prof[dom][1], cprime, peaks, clocks.get("sm_mhz")) if dom else None
+    roof = roofline_for(dom, prof[dom][0] / prof[dom][1], cprime, peaks, clocks.get("sm_mhz"),
+                        args.precision) if dom else None
+    for k, kv in kernels.items():
+        kb = kernel_bytes(k, cprime, args.precision)
+        if kb is not None:
+            kv["hbm_frac"] = kb / (kv["ms_per_launch"] * 1e-3) / 1e9 / peaks["hbm_gbs"]
     if roof is not None:
         roof["kernel"] = dom
 

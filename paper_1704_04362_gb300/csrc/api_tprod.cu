@@ -10,11 +10,7 @@ int launch_cgemm_tc(const CGemm& g, cudaStream_t st);
 
 int launch_cgemm(const CGemm& g, cudaStream_t st) {
   if (g.precision == TP_FP32) return launch_cgemm_simt(g, st);
-  if (g.precision == TP_TF32X3) return launch_cgemm_tc(g, st);
-  if (g.precision == TP_BF16X3) {
-    set_error("BF16x3 facewise GEMM is not built yet");
-    return TP_EUNSUPPORTED;
-  }
+  if (g.precision == TP_TF32X3 || g.precision == TP_BF16X3) return launch_cgemm_tc(g, st);
   set_error("unknown precision %d", g.precision);
   return TP_EINVAL;
 }
@@ -37,6 +33,10 @@ int opt_precision(const tp_opts* o) { return o ? o->precision : TP_FP32; }
 
 inline int64_t pad4(int64_t v) { return (v + 3) / 4 * 4; }
 bool is_tc(int prec) { return prec == TP_TF32X3 || prec == TP_BF16X3; }
+// K leading dimension: 16-byte rows for the tensor maps (4 floats or 8 bf16)
+inline int64_t pad_k(int64_t v, int prec) {
+  return prec == TP_BF16X3 ? (v + 7) / 8 * 8 : prec == TP_TF32X3 ? pad4(v) : v;
+}
 
 // Fourier-domain operand storage of one call: plain planar FP32 for the SIMT
 // GEMM, or the 3xTF32 split (hi/lo planes) with leading dimensions padded to
@@ -58,12 +58,13 @@ Planes take_planes(Arena& ws, size_t elems, bool tc) {
 
 // Operand layouts.  SIMT: A_hat_k is n1 x K column-major (leading dimension
 // n1).  Tensor cores: A_hat_k is stored K-major, element (i, kk) at
-// kk + pad4(K)*i.  B_hat_k is K-major in both (leading dimension K, padded to
-// 4 for the tensor cores).
+// kk + lk*i with lk = K padded to 16 bytes (4 floats for 3xTF32, 8 bf16 for
+// BF16x3).  B_hat_k is K-major in both (leading dimension K, padded likewise
+// for the tensor cores).  The planes are sized as floats in both splits.
 size_t tprod_ws(int64_t n1, int64_t n2, int64_t n4, int64_t n3, int prec) {
   const size_t h = size_t(half_len(n3));
   const bool tc = is_tc(prec);
-  const int64_t lk = tc ? pad4(n2) : n2;
+  const int64_t lk = pad_k(n2, prec);
   return planes_bytes(size_t(tc ? lk : n2) * n1 * h, tc) + planes_bytes(size_t(lk) * n4 * h, tc) +
          2 * ws_bytes(size_t(n1) * n4 * h, 4);
 }
@@ -71,7 +72,7 @@ size_t tprod_ws(int64_t n1, int64_t n2, int64_t n4, int64_t n3, int prec) {
 size_t sampled_ws(int64_t n1, int64_t n2, int64_t n4, int64_t n3, int prec) {
   const size_t h = size_t(half_len(n3));
   const bool tc = is_tc(prec);
-  const int64_t lk = tc ? pad4(n2) : n2;
+  const int64_t lk = pad_k(n2, prec);
   size_t part = norms_partial_count(n1, n2, n3, 0);
   const size_t p2 = norms_partial_count(n2, n4, n3, 1);
   if (p2 > part) part = p2;
@@ -107,7 +108,7 @@ int tprod(const float* A, const float* B, float* C, int64_t n1, int64_t n2, int6
   int rc = acquire_workspace(opts, tprod_ws(n1, n2, n4, n3, prec), &ws);
   if (rc) return rc;
   const int64_t h = half_len(n3);
-  const int64_t lk = tc ? pad4(n2) : n2;          // K leading dimension
+  const int64_t lk = pad_k(n2, prec);              // K leading dimension
   const int64_t la = tc ? lk : n1;                 // A leading dimension
   Planes Ah = take_planes(ws, size_t(lk) * n1 * h, tc);
   Planes Bh = take_planes(ws, size_t(lk) * n4 * h, tc);
@@ -115,10 +116,11 @@ int tprod(const float* A, const float* B, float* C, int64_t n1, int64_t n2, int6
   float* Ci = ws.take<float>(size_t(n1) * n4 * h);
 
   DftGather ga{A, n1, n2, 1, n1, n1 * n2, nullptr, nullptr, nullptr, 0, n3,
-               Ah.re, Ah.im, la, la * (tc ? n1 : n2), Ah.re_lo, Ah.im_lo, tc ? 1 : 0};
+               Ah.re, Ah.im, la, la * (tc ? n1 : n2), Ah.re_lo, Ah.im_lo, tc ? 1 : 0,
+               prec == TP_BF16X3 ? 1 : 0};
   if ((rc = launch_rdft(ga, st))) return rc;
   DftGather gb{B, n2, n4, 1, n2, n2 * n4, nullptr, nullptr, nullptr, 0, n3,
-               Bh.re, Bh.im, lk, lk * n4, Bh.re_lo, Bh.im_lo, 0};
+               Bh.re, Bh.im, lk, lk * n4, Bh.re_lo, Bh.im_lo, 0, prec == TP_BF16X3 ? 1 : 0};
   if ((rc = launch_rdft(gb, st))) return rc;
   CGemm g{Ah.re, Ah.im, Bh.re, Bh.im, Cr, Ci, n1, n4, n2, nullptr,
           la, lk, n1, la * (tc ? n1 : n2), lk * n4, n1 * n4, h, n3, prec,
@@ -153,7 +155,7 @@ int tprod_sampled(const float* A, const float* B, float* Z, int64_t n1, int64_t 
   int rc = acquire_workspace(opts, sampled_ws(n1, n2, n4, n3, prec), &ws);
   if (rc) return rc;
   const int64_t h = half_len(n3);
-  const int64_t lk = tc ? pad4(n2) : n2;          // K (picked-slice) leading dimension capacity
+  const int64_t lk = pad_k(n2, prec);              // K (picked-slice) leading dimension capacity
   const int64_t la = tc ? lk : n1;
   size_t part_n = norms_partial_count(n1, n2, n3, 0);
   const size_t p2 = norms_partial_count(n2, n4, n3, 1);
@@ -183,11 +185,12 @@ int tprod_sampled(const float* A, const float* B, float* Z, int64_t n1, int64_t 
   // C_hat_k is n1 x c' (capacity n2 columns): column-major for the SIMT GEMM,
   // K-major (picked index contiguous) for the tensor cores.
   DftGather gc{A, n1, n2, 1, n1, n1 * n2, idx, scale, cnt, 2, n3,
-               Ch.re, Ch.im, la, la * (tc ? n1 : n2), Ch.re_lo, Ch.im_lo, tc ? 1 : 0};
+               Ch.re, Ch.im, la, la * (tc ? n1 : n2), Ch.re_lo, Ch.im_lo, tc ? 1 : 0,
+               prec == TP_BF16X3 ? 1 : 0};
   if ((rc = launch_rdft(gc, st))) return rc;
   // R_hat_k is c' x n4 (leading dimension lk, capacity n2 rows).
   DftGather gr{B, n2, n4, 1, n2, n2 * n4, idx, scale, cnt, 1, n3,
-               Rh.re, Rh.im, lk, lk * n4, Rh.re_lo, Rh.im_lo, 0};
+               Rh.re, Rh.im, lk, lk * n4, Rh.re_lo, Rh.im_lo, 0, prec == TP_BF16X3 ? 1 : 0};
   if ((rc = launch_rdft(gr, st))) return rc;
   // S6: facewise products with inner dimension c' read on the device
   CGemm g{Ch.re, Ch.im, Rh.re, Rh.im, Zr, Zi, n1, n4, 0, cnt,

@@ -1,16 +1,20 @@
 // Facewise complex GEMM of the half spectrum on the tcgen05 tensor cores
-// (Algorithm 1 / Algorithm 2 loop over k: C_hat_k = A_hat_k B_hat_k) with the
-// 3xTF32 split: every float operand x is held as x_hi = tf32(x) (round to
-// nearest) and x_lo = x - x_hi, and a*b is formed as a_hi b_hi + a_hi b_lo +
-// a_lo b_hi with float32 accumulation in tensor memory.  Complex products take
-// four real products (Re = ArBr - AiBi, Im = ArBi + AiBr); the minus sign is
-// the instruction descriptor's negate-A bit.
+// (Algorithm 1 / Algorithm 2 loop over k: C_hat_k = A_hat_k B_hat_k) with a
+// split operand: every float operand x is held as a pair x_hi + x_lo, and a*b
+// is formed as a_hi b_hi + a_hi b_lo + a_lo b_hi with float32 accumulation in
+// tensor memory.  3xTF32 (kind::tf32): x_hi = tf32(x) (round to nearest),
+// x_lo = x - x_hi in float planes.  BF16x3 (kind::f16 with bf16 operands, twice
+// the tf32 rate, half the operand bytes): x_hi = bf16(x), x_lo = bf16(x - x_hi).
+// Complex products take four real products (Re = ArBr - AiBi, Im = ArBi +
+// AiBr); the minus sign is the instruction descriptor's negate-A bit.
 //
 // Persistent kernel: one CTA per SM walks the list of 128 x 128 output tiles
 // (frequency slowest, so the CTAs in flight share a slice's operands in L2).
-//   warp 0 lane 0   TMA producer: 8 operand planes per 16-deep K block into a
-//                   3-stage shared-memory ring (mbarrier complete_tx)
-//   warp 1 lane 0   MMA issuer: 12 tcgen05.mma (K = 8) per 8-deep K step into
+//   warp 0 lane 0   TMA producer: 8 operand planes per K block (16 tf32 or
+//                   32 bf16 deep: 64-byte rows) into a 3-stage shared-memory
+//                   ring (mbarrier complete_tx)
+//   warp 1 lane 0   MMA issuer: 12 tcgen05.mma (K = 8 tf32 or 16 bf16: 32
+//                   bytes of each row) per K step into
 //                   one of two TMEM accumulator sets (Re at +0, Im at +128
 //                   columns; sets at columns 0 and 256); tcgen05.commit frees a
 //                   stage, and after a tile's last K block marks its set full
@@ -19,7 +23,7 @@
 //                   next tile's MMAs run into the other set meanwhile
 // Both operands are K-major (kind::tf32 takes no transposed operand): A
 // planes hold element (m, kk) at kk + lda*m, B planes (kk, n) at kk + ldb*n,
-// read as 64-byte-swizzled 128 x 16 tiles.  Every mbarrier wait is bounded:
+// read as 64-byte-swizzled tiles of 128 rows.  Every mbarrier wait is bounded:
 // on timeout the CTA records TP_DEV_TIMEOUT, stops issuing, waits (bounded)
 // for its own copies in flight, frees its tensor memory and exits.
 #include <cuda.h>
@@ -30,9 +34,9 @@
 namespace tp {
 namespace {
 
-constexpr int TM = 128, TN = 128, TBK = 16, STAGES = 3, NTHR = 192;
-constexpr uint32_t A_PLANE_BYTES = TM * TBK * 4;        // 8 KB
-constexpr uint32_t B_PLANE_BYTES = TN * TBK * 4;        // 8 KB
+constexpr int TM = 128, TN = 128, ROWB = 64, STAGES = 3, NTHR = 192;   // ROWB: K-block row bytes
+constexpr uint32_t A_PLANE_BYTES = TM * ROWB;           // 8 KB
+constexpr uint32_t B_PLANE_BYTES = TN * ROWB;           // 8 KB
 constexpr uint32_t STAGE_BYTES = 4 * A_PLANE_BYTES + 4 * B_PLANE_BYTES;   // 64 KB
 constexpr uint32_t TMEM_COLS = 4 * TN;   // two accumulator sets of (Re, Im)
 constexpr size_t SMEM_BYTES = size_t(STAGES) * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
@@ -112,6 +116,10 @@ constexpr uint32_t LAYOUT_SW64 = 4;
 constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(TN >> 3) << 17) |
                            (uint32_t(TM >> 4) << 24);
 constexpr uint32_t IDESC_NEG = IDESC | (1u << 13);
+// kind::f16: F32 accumulate, BF16 A and B, both K-major, N = TN, M = TM.
+constexpr uint32_t IDESC_BF16 = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(TN >> 3) << 17) |
+                                (uint32_t(TM >> 4) << 24);
+constexpr uint32_t IDESC_BF16_NEG = IDESC_BF16 | (1u << 13);
 
 __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t accum) {
@@ -120,6 +128,25 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
       "l"(a), "l"(b), "r"(idesc), "r"(accum)
       : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+// One K step (32 bytes of every row) of one accumulator.
+template <bool BF16>
+__device__ __forceinline__ void mma_step(uint32_t d, uint64_t a, uint64_t b, bool neg,
+                                         uint32_t accum) {
+  if constexpr (BF16)
+    mma_bf16(d, a, b, neg ? IDESC_BF16_NEG : IDESC_BF16, accum);
+  else
+    mma_tf32(d, a, b, neg ? IDESC_NEG : IDESC, accum);
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -146,7 +173,9 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+template <bool BF16>
 __global__ void __launch_bounds__(NTHR, 1) cgemm_tc_kernel(const __grid_constant__ TcParams p) {
+  constexpr int TBK = BF16 ? ROWB / 2 : ROWB / 4;   // K elements per K block
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~uintptr_t(1023));
@@ -251,7 +280,7 @@ __global__ void __launch_bounds__(NTHR, 1) cgemm_tc_kernel(const __grid_constant
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t st = smem_u32(smem + size_t(s) * STAGE_BYTES);
 #pragma unroll
-        for (int sub = 0; sub < TBK / 8; ++sub) {
+        for (int sub = 0; sub < ROWB / 32; ++sub) {
           uint64_t a[4], bb[4];
 #pragma unroll
           for (int pl = 0; pl < 4; ++pl) {
@@ -261,19 +290,19 @@ __global__ void __launch_bounds__(NTHR, 1) cgemm_tc_kernel(const __grid_constant
           }
           const uint32_t first = (kb == 0 && sub == 0) ? 0u : 1u;
           // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
-          mma_tf32(dre, a[0], bb[0], IDESC, first);
-          mma_tf32(dre, a[0], bb[1], IDESC, 1);
-          mma_tf32(dre, a[1], bb[0], IDESC, 1);
+          mma_step<BF16>(dre, a[0], bb[0], false, first);
+          mma_step<BF16>(dre, a[0], bb[1], false, 1);
+          mma_step<BF16>(dre, a[1], bb[0], false, 1);
           if (!real_slice) {
-            mma_tf32(dre, a[2], bb[2], IDESC_NEG, 1);
-            mma_tf32(dre, a[2], bb[3], IDESC_NEG, 1);
-            mma_tf32(dre, a[3], bb[2], IDESC_NEG, 1);
-            mma_tf32(dim, a[0], bb[2], IDESC, first);
-            mma_tf32(dim, a[0], bb[3], IDESC, 1);
-            mma_tf32(dim, a[1], bb[2], IDESC, 1);
-            mma_tf32(dim, a[2], bb[0], IDESC, 1);
-            mma_tf32(dim, a[2], bb[1], IDESC, 1);
-            mma_tf32(dim, a[3], bb[0], IDESC, 1);
+            mma_step<BF16>(dre, a[2], bb[2], true, 1);
+            mma_step<BF16>(dre, a[2], bb[3], true, 1);
+            mma_step<BF16>(dre, a[3], bb[2], true, 1);
+            mma_step<BF16>(dim, a[0], bb[2], false, first);
+            mma_step<BF16>(dim, a[0], bb[3], false, 1);
+            mma_step<BF16>(dim, a[1], bb[2], false, 1);
+            mma_step<BF16>(dim, a[2], bb[0], false, 1);
+            mma_step<BF16>(dim, a[2], bb[1], false, 1);
+            mma_step<BF16>(dim, a[3], bb[0], false, 1);
           }
         }
         mma_commit(smem_u32(&empty[s]));   // stage s free once these MMAs finish
@@ -357,9 +386,10 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   return fn;
 }
 
-int encode_map(CUtensorMap* map, const float* base, uint64_t d0, uint64_t d1, uint64_t d2,
+int encode_map(CUtensorMap* map, const void* base, uint64_t d0, uint64_t d1, uint64_t d2,
                uint64_t s1_bytes, uint64_t s2_bytes, uint32_t b0, uint32_t b1,
-               CUtensorMapSwizzle sw) {
+               CUtensorMapSwizzle sw,
+               CUtensorMapDataType dtype = CU_TENSOR_MAP_DATA_TYPE_FLOAT32) {
   const cuuint64_t dims[3] = {d0, d1, d2};
   const cuuint64_t strides[2] = {s1_bytes, s2_bytes};
   const cuuint32_t box[3] = {b0, b1, 1};
@@ -369,7 +399,7 @@ int encode_map(CUtensorMap* map, const float* base, uint64_t d0, uint64_t d1, ui
     set_error("cuTensorMapEncodeTiled is not available from the driver");
     return TP_ECUDA;
   }
-  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims,
+  const CUresult r = enc(map, dtype, 3, const_cast<void*>(base), dims,
                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
@@ -382,20 +412,26 @@ int encode_map(CUtensorMap* map, const float* base, uint64_t d0, uint64_t d1, ui
 }  // namespace
 
 // Operands for the tensor-core path come as split planes: g.ar/g.ai are the
-// hi planes and g.ar_lo/g.ai_lo (likewise b) the lo planes; A planes have
-// element (m, kk) at kk + lda*m, B planes (kk, n) at kk + ldb*n (lda, ldb
-// multiples of 4); K capacity g.kcap (zero-padded past K up to a multiple of
-// 32 or to the capacity).
+// hi planes and g.ar_lo/g.ai_lo (likewise b) the lo planes, float (3xTF32) or
+// bf16 (BF16x3) elements; A planes have element (m, kk) at kk + lda*m, B
+// planes (kk, n) at kk + ldb*n (lda, ldb multiples of 16 bytes); K capacity
+// g.kcap (zero-padded past K up to a multiple of 32 or to the capacity).
 int launch_cgemm_tc(const CGemm& g, cudaStream_t st) {
   if (g.M == 0 || g.N == 0 || g.h == 0) return TP_OK;
   if (!g.ar_lo || !g.ai_lo || !g.br_lo || !g.bi_lo) {
     set_error("cgemm_tc: split operand planes missing");
     return TP_EINVAL;
   }
-  if ((g.lda % 4) || (g.ldb % 4) || (g.sA % 4) || (g.sB % 4)) {
-    set_error("cgemm_tc: leading dimensions must be multiples of 4 floats");
+  const bool bf16 = g.precision == TP_BF16X3;
+  const int64_t ealign = bf16 ? 8 : 4;   // elements per 16 bytes
+  if ((g.lda % ealign) || (g.ldb % ealign) || (g.sA % ealign) || (g.sB % ealign)) {
+    set_error("cgemm_tc: leading dimensions must be multiples of 16 bytes");
     return TP_EALIGN;
   }
+  const uint64_t esz = bf16 ? 2 : 4;
+  const uint32_t tbk = uint32_t(ROWB / esz);
+  const CUtensorMapDataType dt =
+      bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   if (g.M > 0x7fffffff || g.N > 0x7fffffff || g.kcap > 0x7fffffff || g.h > 65535 ||
       (g.M + TM - 1) / TM * ((g.N + TN - 1) / TN) > 0x7fffffff / 65536) {
     set_error("cgemm_tc: sizes too large for one launch");
@@ -410,11 +446,12 @@ int launch_cgemm_tc(const CGemm& g, cudaStream_t st) {
       return TP_EALIGN;
     }
     int rc = encode_map(&p.a[i], ap[i], uint64_t(g.kcap), uint64_t(g.M), uint64_t(g.h),
-                        uint64_t(g.lda) * 4, uint64_t(g.sA) * 4, TBK, TM,
-                        CU_TENSOR_MAP_SWIZZLE_64B);
+                        uint64_t(g.lda) * esz, uint64_t(g.sA) * esz, tbk, TM,
+                        CU_TENSOR_MAP_SWIZZLE_64B, dt);
     if (rc) return rc;
     rc = encode_map(&p.b[i], bp[i], uint64_t(g.kcap), uint64_t(g.N), uint64_t(g.h),
-                    uint64_t(g.ldb) * 4, uint64_t(g.sB) * 4, TBK, TN, CU_TENSOR_MAP_SWIZZLE_64B);
+                    uint64_t(g.ldb) * esz, uint64_t(g.sB) * esz, tbk, TN, CU_TENSOR_MAP_SWIZZLE_64B,
+                    dt);
     if (rc) return rc;
   }
   p.zr = g.cr;
@@ -430,8 +467,8 @@ int launch_cgemm_tc(const CGemm& g, cudaStream_t st) {
   p.status = g.status;
   p.mt = int((g.M + TM - 1) / TM);
   p.nt = int((g.N + TN - 1) / TN);
-  cudaFuncSetAttribute(cgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       int(SMEM_BYTES));
+  auto kernel = bf16 ? cgemm_tc_kernel<true> : cgemm_tc_kernel<false>;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SMEM_BYTES));
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -439,7 +476,7 @@ int launch_cgemm_tc(const CGemm& g, cudaStream_t st) {
   const dim3 grid(unsigned(ntiles < sms ? ntiles : sms));
   {
     KernelScope ks("cgemm_tc", st);
-    cgemm_tc_kernel<<<grid, NTHR, SMEM_BYTES, st>>>(p);
+    kernel<<<grid, NTHR, SMEM_BYTES, st>>>(p);
   }
   return launch_status("cgemm_tc_kernel");
 }

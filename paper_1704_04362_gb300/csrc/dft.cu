@@ -146,11 +146,8 @@ __global__ void __launch_bounds__(RB) rdft_kernel(DftGather g, int stage) {
             const int64_t oo = o + int64_t(k0 + q) * g.out_slice;
             const float ar = acc[j][q].x, ai = acc[j][q].y;
             if (g.out_re_lo) {
-              const float hr = tf32_rna(ar), hi = tf32_rna(ai);
-              g.out_re[oo] = hr;
-              g.out_re_lo[oo] = ar - hr;
-              g.out_im[oo] = hi;
-              g.out_im_lo[oo] = ai - hi;
+              put_split(g.out_re, g.out_re_lo, g.out_bf16 != 0, oo, ar);
+              put_split(g.out_im, g.out_im_lo, g.out_bf16 != 0, oo, ai);
             } else {
               g.out_re[oo] = ar;
               g.out_im[oo] = ai;
@@ -235,9 +232,12 @@ __global__ void __launch_bounds__(RB) rdft_t_kernel(DftGather g) {
           for (int q = 0; q < KC; ++q) {
             const float v = (pl & 1) ? acc[j][q].y : acc[j][q].x;
             float o;
-            if (!g.out_re_lo) o = v;
-            else if (pl < 2) o = tf32_rna(v);
-            else o = v - tf32_rna(v);
+            if (!g.out_re_lo) {
+              o = v;
+            } else {   // hi, or lo = v - hi rounded to tf32 (a bf16 lo is rounded when stored)
+              const float hi = g.out_bf16 ? __bfloat162float(__float2bfloat16_rn(v)) : tf32_rna(v);
+              o = pl < 2 ? hi : (g.out_bf16 ? v - hi : tf32_rna(v - hi));
+            }
             stg[(q * TR + lr) * (TCOL + 1) + lc + 4 * j] = o;
           }
         __syncthreads();
@@ -251,9 +251,14 @@ __global__ void __launch_bounds__(RB) rdft_t_kernel(DftGather g) {
             for (int pass = 0; pass < TR / (RB / TCOL); ++pass) {
               const int rr = wr + pass * (RB / TCOL);
               const int64_t rg = r0 + rr;
-              if (rg < ex.rows_pad)
-                dst[int64_t(k0 + q) * g.out_slice + c + g.out_ld * rg] =
-                    stg[(q * TR + rr) * (TCOL + 1) + wc];
+              if (rg < ex.rows_pad) {
+                const int64_t o = int64_t(k0 + q) * g.out_slice + c + g.out_ld * rg;
+                const float v = stg[(q * TR + rr) * (TCOL + 1) + wc];
+                if (g.out_bf16 && g.out_re_lo)
+                  reinterpret_cast<__nv_bfloat16*>(dst)[o] = __float2bfloat16_rn(v);
+                else
+                  dst[o] = v;
+              }
             }
           }
         }

@@ -1,6 +1,9 @@
 // Helpers shared by the mode-3 DFT kernels (dft.cu, rfft_reg.cu): tube
-// addressing with the optional rescaled gather, and the 3xTF32 split.
+// addressing with the optional rescaled gather, and the hi/lo operand split
+// (3xTF32 or BF16x3).
 #pragma once
+
+#include <cuda_bf16.h>
 
 #include "tp_internal.cuh"
 
@@ -12,6 +15,24 @@ __device__ __forceinline__ float tf32_rna(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
+}
+
+// Element o of a split operand pair v ~ hi + lo: hi = tf32(v) and
+// lo = tf32(v - hi) in float planes, or hi = bf16(v) and lo = bf16(v - hi) in
+// 16-bit planes, all rounded to nearest.  (The tensor cores read only the
+// tf32 bits of a float operand; a lo plane left at full float precision would
+// be truncated there, a biased error.)
+__device__ __forceinline__ void put_split(float* hi_plane, float* lo_plane, bool bf16, int64_t o,
+                                          float v) {
+  if (bf16) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    reinterpret_cast<__nv_bfloat16*>(hi_plane)[o] = h;
+    reinterpret_cast<__nv_bfloat16*>(lo_plane)[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+  } else {
+    const float h = tf32_rna(v);
+    hi_plane[o] = h;
+    lo_plane[o] = tf32_rna(v - h);
+  }
 }
 
 struct Extent {

@@ -186,11 +186,8 @@ __device__ __forceinline__ int64_t opaque(int64_t v) {
 
 __device__ __forceinline__ void put_value(const DftGather& g, int64_t o, float re, float im) {
   if (g.out_re_lo) {
-    const float hr = tf32_rna(re), hi = tf32_rna(im);
-    g.out_re[o] = hr;
-    g.out_im[o] = hi;
-    g.out_re_lo[o] = re - hr;
-    g.out_im_lo[o] = im - hi;
+    put_split(g.out_re, g.out_re_lo, g.out_bf16 != 0, o, re);
+    put_split(g.out_im, g.out_im_lo, g.out_bf16 != 0, o, im);
   } else {
     g.out_re[o] = re;
     g.out_im[o] = im;

@@ -65,6 +65,7 @@ struct DftGather {
   float* out_re_lo;            // non-null: write the 3xTF32 split, hi to out_re/out_im
   float* out_im_lo;            //   (tf32 round-to-nearest) and lo = x - hi here
   int out_transposed;          // 1: element (r, c) of slice k at k*out_slice + c + out_ld*r
+  int out_bf16;                // with the split: the four planes hold bf16 (hi, lo) pairs
 };
 int launch_rdft(const DftGather& g, cudaStream_t st);
 

@@ -2,7 +2,9 @@
 rt-product of A 2000 x 4000 x 64 and B 4000 x 1500 x 64 (tubal rank 20 plus 1%
 noise), c = 400.  The oracle recomputes the slice norms and the draw from the
 same inputs (indices must agree exactly) and then a sample of output tubes one
-by one; FP32 and TF32x3 outputs must match them within 1e-5."""
+by one; the outputs of all three precisions (FP32, 3xTF32, BF16x3) must match
+them within 1e-5 (the split forms' accumulation error grows with the number of
+picked slices, c' = 426 here; see test_gpu_precision.py)."""
 import numpy as np
 import pytest
 
@@ -31,7 +33,7 @@ def test_fullsize_sampled_product_tubes(workload):
     import torch
     A, B = workload
     outs = {}
-    for prec in (tp.TP_FP32, tp.TP_TF32X3):
+    for prec in (tp.TP_FP32, tp.TP_TF32X3, tp.TP_BF16X3):
         st = torch.zeros(1, dtype=torch.int32, device="cuda")
         Z, idx, cnt = tp.tprod_sampled(A, B, C, seed=0, precision=prec, status=st)
         assert int(st.item()) == 0
@@ -58,6 +60,7 @@ def test_fullsize_sampled_product_tubes(workload):
         for prec, (Z, _) in outs.items():
             g = Z[i, l, :].double().cpu().numpy()
             num[prec] += float(np.sum((g - tube) ** 2))
-    for prec in outs:
-        err = np.sqrt(num[prec] / den)
+    errs = {prec: np.sqrt(num[prec] / den) for prec in outs}
+    print("relative error on sampled tubes by precision:", {k: f"{v:.2e}" for k, v in errs.items()})
+    for prec, err in errs.items():
         assert err < TOL_FP32, f"precision {prec}: relative error {err:.2e} on sampled tubes"

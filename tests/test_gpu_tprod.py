@@ -6,7 +6,7 @@ import pytest
 import paper_1704_04362_gb300 as tp
 from paper_1704_04362_gb300 import synth
 from oracle import philox_ref, sampling_ref, tensor_ref
-from tests.util import TOL_FP32, rel_fro, to_np
+from tests.util import TOL_FP32, rel_fro, to_np, tol_for
 
 pytestmark = pytest.mark.gpu
 
@@ -52,7 +52,7 @@ SHAPES = [
 ]
 
 
-PRECISIONS = [tp.TP_FP32, tp.TP_TF32X3]
+PRECISIONS = [tp.TP_FP32, tp.TP_TF32X3, tp.TP_BF16X3]
 
 
 def status_word():
@@ -69,7 +69,7 @@ def test_tprod_matches_oracle(n1, n2, n4, n3, prec):
     C = tp.tprod(dev(A), dev(B), precision=prec, status=st)
     ref = tensor_ref.tprod(A.astype(np.float64), B.astype(np.float64))
     assert int(st.item()) == 0
-    assert rel_fro(to_np(C), ref) < TOL_FP32
+    assert rel_fro(to_np(C), ref) < tol_for(prec)
 
 
 def test_tprod_identity_and_definition_tiny():
@@ -139,7 +139,7 @@ def test_tprod_sampled_matches_oracle(mode, n1, n2, n4, n3, c, prec):
     Zref, ref_idx, q = sampling_ref.tprod_sampled(A, B, c, 123, mode=mode)
     # index draws: the float64 probabilities agree to rounding, so the picks agree
     assert np.array_equal(idx[:cnt].cpu().numpy(), ref_idx)
-    assert rel_fro(to_np(Z), Zref) < TOL_FP32
+    assert rel_fro(to_np(Z), Zref) < tol_for(prec)
 
 
 def test_tprod_sampled_given_p_and_nothing_kept():

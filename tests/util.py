@@ -20,3 +20,16 @@ def rel_fro(a, b) -> float:
 
 # relative Frobenius tolerance of every FP32 output against the float64 oracle
 TOL_FP32 = 1e-5
+
+# BF16x3 split (bf16 hi + bf16 lo, the lo*lo term dropped).  Each operand keeps
+# 16 significand bits: |x - hi - lo| <= 2^-16 |x|, and the dropped lo*lo term
+# is at most 2^-16 |x y|, so one real product is exact to 3 * 2^-16 = 4.6e-5
+# relative in the worst case (about 5e-6 root-mean-square).  The tolerance is
+# the worst-case bound plus the float32 transform and accumulation error.
+TOL_BF16X3 = 5e-5
+
+
+def tol_for(precision: int) -> float:
+    """Relative Frobenius tolerance of a t-product output at this precision
+    (0 FP32, 1 3xTF32, 2 BF16x3)."""
+    return TOL_BF16X3 if precision == 2 else TOL_FP32
