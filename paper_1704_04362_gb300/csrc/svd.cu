@@ -1,7 +1,5 @@
 // Facewise SVD of the half spectrum for the t-SVD (Theorem 2.6 computed as in
-// Eq. circ1): every Fourier slice X_hat_k = U_k diag(s_k) V_k^H.  The float32
-// slice is copied into a float64 work matrix so that the accumulated
-// rotations keep the factors orthogonal to float32 accuracy.
+// Eq. circ1): every Fourier slice X_hat_k = U_k diag(s_k) V_k^H.
 //
 // One CTA per slice runs the one-sided (Hestenes) Jacobi method on the
 // columns of a p x q work matrix G (p >= q): pairs of columns (a, b) are
@@ -13,13 +11,26 @@
 // makes the pair real; zeta = (||b||^2 - ||a||^2) / (2|gamma|),
 // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t,
 // a' = c a - s b~, b' = s a + c b~.  Sweeps are capped (opts->max_sweeps); a
-// slice that reaches the cap sets TP_DEV_NOCONV.
+// slice that reaches the cap sets TP_DEV_NOCONV.  G and V live in shared
+// memory when they fit, else in global memory.
+//
+// GB300 runs float64 at 1/64 of the float32 rate, so the t-SVD takes the
+// sweeps in float32 and finishes in float64:
+//   1. float32 Jacobi on G = X (or X^H) from V = I, to float32 convergence;
+//   2. V <- V (3 I - V^H V) / 2 in float64 (one Newton-Schulz step: the
+//      accumulated float32 rotations are orthonormal to ~1e-6, after it to
+//      ~1e-12);
+//   3. G = X V in float64;
+//   4. float64 Jacobi on that G, starting from V: the columns are already
+//      orthogonal to float32 accuracy, so one or two sweeps (quadratic
+//      convergence) reach float64 accuracy.
+// Steps 2-3 are batched float64 GEMMs spread over all SMs.
 #include "tp_internal.cuh"
 
 namespace tp {
 namespace {
 
-constexpr int SVD_THREADS = 256;
+constexpr int SVD_THREADS = 512;
 
 template <class T>
 __device__ __forceinline__ T warp_sum_t(T v) {
@@ -35,27 +46,57 @@ template <> struct Eps<double> { static constexpr double v = 1.12e-16; };
 // Batched one-sided Jacobi.  Item b: G (p x q, column-major, ld p) at
 // g_re/g_im + b*sG, V (q x q) at v_re/v_im + b*sV.  On exit G holds U
 // (unit columns, unsorted), sig[b*q + j] the singular values (unsorted).
+// Flags of jacobi_kernel.
+constexpr int JAC_INIT_V = 1;      // start from V = I (else from the given V)
+constexpr int JAC_NORMALIZE = 2;   // on exit scale G's columns to unit length
+constexpr int JAC_SMEM = 4;        // work on shared-memory copies of G and V
+
 template <class T>
 __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(T* g_re, T* g_im, int64_t sG, T* v_re,
                                                              T* v_im, int64_t sV, T* sig, int p,
                                                              int q, int max_sweeps,
                                                              const int* real_flags,
-                                                             int32_t* status) {
+                                                             int32_t* status, int flags) {
+  extern __shared__ __align__(16) unsigned char jac_smem[];
   const int64_t b = blockIdx.x;
-  T* Gr = g_re + b * sG;
-  T* Gi = g_im + b * sG;
-  T* Vr = v_re + b * sV;
-  T* Vi = v_im + b * sV;
+  T* const gGr = g_re + b * sG;
+  T* const gGi = g_im + b * sG;
+  T* const gVr = v_re + b * sV;
+  T* const gVi = v_im + b * sV;
+  T* Gr = gGr;
+  T* Gi = gGi;
+  T* Vr = gVr;
+  T* Vi = gVi;
   const bool real = real_flags ? real_flags[b] != 0 : false;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = SVD_THREADS / 32;
+  const int64_t pq = int64_t(p) * q;
   __shared__ int rotated;
 
-  for (int e = tid; e < q * q; e += SVD_THREADS) {
-    Vr[e] = (e % (q + 1) == 0) ? T(1) : T(0);
-    Vi[e] = T(0);
+  if (flags & JAC_SMEM) {
+    T* sm = reinterpret_cast<T*>(jac_smem);
+    Gr = sm;
+    Gi = sm + pq;
+    Vr = sm + 2 * pq;
+    Vi = sm + 2 * pq + q * q;
+    for (int64_t e = tid; e < pq; e += SVD_THREADS) {
+      Gr[e] = gGr[e];
+      Gi[e] = gGi[e];
+    }
+    if (!(flags & JAC_INIT_V))
+      for (int e = tid; e < q * q; e += SVD_THREADS) {
+        Vr[e] = gVr[e];
+        Vi[e] = gVi[e];
+      }
   }
-  if (real)
-    for (int64_t e = tid; e < int64_t(p) * q; e += SVD_THREADS) Gi[e] = T(0);
+  if (flags & JAC_INIT_V)
+    for (int e = tid; e < q * q; e += SVD_THREADS) {
+      Vr[e] = (e % (q + 1) == 0) ? T(1) : T(0);
+      Vi[e] = T(0);
+    }
+  if (real) {
+    for (int64_t e = tid; e < pq; e += SVD_THREADS) Gi[e] = T(0);
+    for (int e = tid; e < q * q; e += SVD_THREADS) Vi[e] = T(0);
+  }
   __syncthreads();
 
   T tol = T(8) * Eps<T>::v * sqrt(T(p));
@@ -129,7 +170,7 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(T* g_re, T* g_im, i
     if (!any) break;
   }
   if (sweep >= max_sweeps && tid == 0 && status) atomicOr(status, TP_DEV_NOCONV);
-  // singular values and unit left vectors
+  // singular values and (optionally) unit left vectors
   for (int j = warp; j < q; j += nw) {
     T* xr = Gr + int64_t(j) * p;
     T* xi = Gi + int64_t(j) * p;
@@ -137,19 +178,33 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(T* g_re, T* g_im, i
     for (int r = lane; r < p; r += 32) nrm += xr[r] * xr[r] + xi[r] * xi[r];
     nrm = sqrt(warp_sum_t(nrm));
     if (lane == 0) sig[b * q + j] = nrm;
-    const T inv = nrm > T(0) ? T(1) / nrm : T(0);
-    for (int r = lane; r < p; r += 32) {
-      xr[r] *= inv;
-      xi[r] *= inv;
+    if (flags & JAC_NORMALIZE) {
+      const T inv = nrm > T(0) ? T(1) / nrm : T(0);
+      for (int r = lane; r < p; r += 32) {
+        xr[r] *= inv;
+        xi[r] *= inv;
+      }
+    }
+  }
+  if (flags & JAC_SMEM) {
+    __syncthreads();
+    for (int64_t e = tid; e < pq; e += SVD_THREADS) {
+      gGr[e] = Gr[e];
+      gGi[e] = Gi[e];
+    }
+    for (int e = tid; e < q * q; e += SVD_THREADS) {
+      gVr[e] = Vr[e];
+      gVi[e] = Vi[e];
     }
   }
 }
 
-// Gathers slice b of the half spectrum into the (float64) work matrix:
+// Gathers slice b of the half spectrum into the work matrix:
 // G = X_hat_k (n1 x n2) when n1 >= n2, else G = X_hat_k^H (n2 x n1).
+template <class T>
 __global__ void load_work_kernel(const float* __restrict__ xr, const float* __restrict__ xi,
                                  int64_t n1, int64_t n2, int64_t h, bool transpose,
-                                 double* __restrict__ gr, double* __restrict__ gi) {
+                                 T* __restrict__ gr, T* __restrict__ gi) {
   const int64_t per = n1 * n2;
   const int64_t total = per * h;
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
@@ -158,12 +213,12 @@ __global__ void load_work_kernel(const float* __restrict__ xr, const float* __re
     const int64_t i = r % n1, j = r / n1;
     const float vr = xr[e], vi = xi[e];
     if (!transpose) {
-      gr[e] = vr;
-      gi[e] = vi;
+      gr[e] = T(vr);
+      gi[e] = T(vi);
     } else {   // G(j, i) = conj(X(i, j)), G is n2 x n1
       const int64_t o = k * per + j + n2 * i;
-      gr[o] = vr;
-      gi[o] = -vi;
+      gr[o] = T(vr);
+      gi[o] = -T(vi);
     }
   }
 }
@@ -221,18 +276,150 @@ __global__ void real_flags_kernel(int* flags, int64_t h, int64_t n3) {
   if (k < h) flags[k] = (k == 0 || (n3 % 2 == 0 && k == h - 1)) ? 1 : 0;
 }
 
+// Batched complex GEMM in float64 (inputs float or double, planar):
+// C_b (M x N) = op(A_b) B_b with op(A) = A (M x K, element (m, k) at m + lda k)
+// or A^H (A stored K x M, element (k, m) at k + lda m); B (K x N) at k + ldb n;
+// C at m + ldc n.  16 x 16 output tiles, one element per thread, K staged
+// through shared memory in chunks of 16.
+constexpr int ZT = 16;
+template <class TA, class TB>
+__global__ void __launch_bounds__(ZT * ZT) zgemm64_kernel(
+    const TA* __restrict__ ar, const TA* __restrict__ ai, int64_t sA, int64_t lda, int conj_a,
+    const TB* __restrict__ br, const TB* __restrict__ bi, int64_t sB, int64_t ldb,
+    double* __restrict__ cr, double* __restrict__ ci, int64_t sC, int64_t ldc, int M, int N,
+    int K) {
+  __shared__ double As_r[ZT][ZT + 1], As_i[ZT][ZT + 1], Bs_r[ZT][ZT + 1], Bs_i[ZT][ZT + 1];
+  const int64_t b = blockIdx.z;
+  const int tx = threadIdx.x % ZT, ty = threadIdx.x / ZT;   // tx: row m, ty: column n
+  const int m0 = blockIdx.x * ZT, n0 = blockIdx.y * ZT;
+  ar += b * sA;
+  ai += b * sA;
+  br += b * sB;
+  bi += b * sB;
+  double accr = 0.0, acci = 0.0;
+  for (int k0 = 0; k0 < K; k0 += ZT) {
+    {   // A tile: As[m][k] = op(A)(m0 + m, k0 + k); thread (tx, ty) loads m = tx, k = ty
+      const int m = m0 + tx, k = k0 + ty;
+      double vr = 0.0, vi = 0.0;
+      if (m < M && k < K) {
+        if (conj_a) {
+          vr = double(ar[k + lda * m]);
+          vi = -double(ai[k + lda * m]);
+        } else {
+          vr = double(ar[m + lda * k]);
+          vi = double(ai[m + lda * k]);
+        }
+      }
+      As_r[tx][ty] = vr;
+      As_i[tx][ty] = vi;
+    }
+    {   // B tile: Bs[k][n]; thread loads k = tx, n = ty
+      const int k = k0 + tx, n = n0 + ty;
+      double vr = 0.0, vi = 0.0;
+      if (k < K && n < N) {
+        vr = double(br[k + ldb * n]);
+        vi = double(bi[k + ldb * n]);
+      }
+      Bs_r[tx][ty] = vr;
+      Bs_i[tx][ty] = vi;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < ZT; ++k) {
+      const double xr = As_r[tx][k], xi = As_i[tx][k], yr = Bs_r[k][ty], yi = Bs_i[k][ty];
+      accr = fma(xr, yr, fma(-xi, yi, accr));
+      acci = fma(xr, yi, fma(xi, yr, acci));
+    }
+    __syncthreads();
+  }
+  const int m = m0 + tx, n = n0 + ty;
+  if (m < M && n < N) {
+    cr[b * sC + m + ldc * n] = accr;
+    ci[b * sC + m + ldc * n] = acci;
+  }
+}
+
+template <class TA, class TB>
+void zgemm64(const TA* ar, const TA* ai, int64_t sA, int64_t lda, bool conj_a, const TB* br,
+             const TB* bi, int64_t sB, int64_t ldb, double* cr, double* ci, int64_t sC,
+             int64_t ldc, int M, int N, int K, int batch, cudaStream_t st) {
+  const dim3 grid(unsigned((M + ZT - 1) / ZT), unsigned((N + ZT - 1) / ZT), unsigned(batch));
+  zgemm64_kernel<TA, TB><<<grid, ZT * ZT, 0, st>>>(ar, ai, sA, lda, conj_a ? 1 : 0, br, bi, sB,
+                                                   ldb, cr, ci, sC, ldc, M, N, K);
+}
+
+// T <- (3 I - T) / 2 for q x q matrices (the Newton-Schulz factor).
+__global__ void ns_factor_kernel(double* tr, double* ti, int q, int64_t total) {
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = e % (int64_t(q) * q);
+    const bool diag = (r % q) == (r / q);
+    tr[e] = (diag ? 1.5 : 0.0) - 0.5 * tr[e];
+    ti[e] = -0.5 * ti[e];
+  }
+}
+
+unsigned grid_of(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  return unsigned(b);
+}
+
+// Shared memory a Jacobi CTA needs to hold G and V, or 0 when they do not fit.
+template <class T>
+size_t jacobi_smem(int p, int q) {
+  const size_t bytes = (2 * size_t(p) * q + 2 * size_t(q) * q) * sizeof(T);
+  return bytes <= size_t(200) * 1024 ? bytes : 0;
+}
+
+template <class T>
+int jacobi_launch(T* gr, T* gi, int64_t sG, T* vr, T* vi, int64_t sV, T* sig, int p, int q,
+                  int batch, int max_sweeps, const int* real_flags, int32_t* status, int flags,
+                  cudaStream_t st) {
+  if (batch <= 0 || q <= 0) return TP_OK;
+  const size_t smem = jacobi_smem<T>(p, q);
+  if (smem) {
+    flags |= JAC_SMEM;
+    cudaFuncSetAttribute(jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  }
+  {
+    KernelScope ks(sizeof(T) == 4 ? "jacobi_f32" : "jacobi_svd", st);
+    jacobi_kernel<T><<<unsigned(batch), SVD_THREADS, smem, st>>>(
+        gr, gi, sG, vr, vi, sV, sig, p, q, max_sweeps, real_flags, status, flags);
+  }
+  return launch_status("jacobi_kernel");
+}
+
 }  // namespace
+
+// float32 one-sided Jacobi from V = I; G is left rotated (not normalised).
+int jacobi_float_launch(float* gr, float* gi, int64_t sG, float* vr, float* vi, int64_t sV,
+                        float* sig, int p, int q, int batch, int max_sweeps,
+                        const int* real_flags, int32_t* status, cudaStream_t st) {
+  return jacobi_launch<float>(gr, gi, sG, vr, vi, sV, sig, p, q, batch, max_sweeps, real_flags,
+                              status, JAC_INIT_V, st);
+}
+
+// C_b = op(A_b) B_b in float64 from float32 planes (see zgemm64_kernel).
+int zgemm64_from_float(const float* ar, const float* ai, int64_t sA, int64_t lda, bool conj_a,
+                       const float* br, const float* bi, int64_t sB, int64_t ldb, double* cr,
+                       double* ci, int64_t sC, int64_t ldc, int M, int N, int K, int batch,
+                       cudaStream_t st) {
+  if (batch <= 0 || M <= 0 || N <= 0) return TP_OK;
+  {
+    KernelScope ks("zgemm64", st);
+    zgemm64<float, float>(ar, ai, sA, lda, conj_a, br, bi, sB, ldb, cr, ci, sC, ldc, M, N, K,
+                          batch, st);
+  }
+  return launch_status("zgemm64_kernel");
+}
 
 int jacobi_double_launch(double* gr, double* gi, int64_t sG, double* vr, double* vi, int64_t sV,
                          double* sig, int p, int q, int batch, int max_sweeps,
                          const int* real_flags, int32_t* status, cudaStream_t st) {
-  if (batch <= 0) return TP_OK;
-  {
-    KernelScope ks("jacobi_svd", st);
-    jacobi_kernel<double><<<unsigned(batch), SVD_THREADS, 0, st>>>(
-        gr, gi, sG, vr, vi, sV, sig, p, q, max_sweeps, real_flags, status);
-  }
-  return launch_status("jacobi_kernel");
+  return jacobi_launch<double>(gr, gi, sG, vr, vi, sV, sig, p, q, batch, max_sweeps, real_flags,
+                               status, JAC_INIT_V | JAC_NORMALIZE, st);
 }
 
 size_t tsvd_ws(int64_t n1, int64_t n2, int64_t n3) {
@@ -240,6 +427,10 @@ size_t tsvd_ws(int64_t n1, int64_t n2, int64_t n3) {
   const size_t m = size_t(n1 < n2 ? n1 : n2);
   const size_t p = size_t(n1 < n2 ? n2 : n1);
   return 2 * ws_bytes(size_t(n1) * n2 * h, 4)      // X_hat
+         + 2 * ws_bytes(p * m * h, 4)              // float32 work matrix
+         + 2 * ws_bytes(m * m * h, 4)              // float32 rotations
+         + ws_bytes(m * h, 4)                      // float32 column norms
+         + 2 * ws_bytes(m * m * h, 8)              // Newton-Schulz factor
          + 2 * ws_bytes(p * m * h, 8)              // G (float64)
          + 2 * ws_bytes(m * m * h, 8)              // V of the Jacobi (float64)
          + ws_bytes(m * h, 8)                      // singular values
@@ -258,8 +449,16 @@ int tsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, float* U, float
   Arena ws;
   int rc = acquire_workspace(opts, tsvd_ws(n1, n2, n3), &ws);
   if (rc) return rc;
+  int32_t* status = opts ? opts->status : nullptr;
   float* Xr = ws.take<float>(size_t(n1) * n2 * h);
   float* Xi = ws.take<float>(size_t(n1) * n2 * h);
+  float* Fr = ws.take<float>(size_t(p) * m * h);
+  float* Fi = ws.take<float>(size_t(p) * m * h);
+  float* Qr = ws.take<float>(size_t(m) * m * h);
+  float* Qi = ws.take<float>(size_t(m) * m * h);
+  float* fsig = ws.take<float>(size_t(m) * h);
+  double* Tr = ws.take<double>(size_t(m) * m * h);
+  double* Ti = ws.take<double>(size_t(m) * m * h);
   double* Gr = ws.take<double>(size_t(p) * m * h);
   double* Gi = ws.take<double>(size_t(p) * m * h);
   double* Wr = ws.take<double>(size_t(m) * m * h);
@@ -278,21 +477,36 @@ int tsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, float* U, float
   if ((rc = launch_rdft(gx, st))) return rc;
   {
     KernelScope ks("svd_prep", st);
-    int64_t blocks = (n1 * n2 * h + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    load_work_kernel<<<unsigned(blocks), 256, 0, st>>>(Xr, Xi, n1, n2, h, transpose, Gr, Gi);
+    load_work_kernel<float><<<grid_of(n1 * n2 * h), 256, 0, st>>>(Xr, Xi, n1, n2, h, transpose,
+                                                                  Fr, Fi);
     real_flags_kernel<<<unsigned((h + 255) / 256), 256, 0, st>>>(flags, h, n3);
   }
   note_launches(1);
   if ((rc = launch_status("svd_prep"))) return rc;
   const int sweeps = (opts && opts->max_sweeps > 0) ? opts->max_sweeps : 30;
+  // 1. float32 sweeps: rotations Q with X Q nearly column-orthogonal (a
+  //    float32 stall at the rounding floor is not an error: step 4 decides)
+  if ((rc = jacobi_launch<float>(Fr, Fi, p * m, Qr, Qi, m * m, fsig, int(p), int(m), int(h), sweeps,
+                                 flags, nullptr, JAC_INIT_V, st)))
+    return rc;
   {
-    KernelScope ks("jacobi_svd", st);
-    jacobi_kernel<double><<<unsigned(h), SVD_THREADS, 0, st>>>(
-        Gr, Gi, p * m, Wr, Wi, m * m, sig, int(p), int(m), sweeps, flags,
-        opts ? opts->status : nullptr);
+    KernelScope ks("svd_refine", st);
+    // 2. W = Q (3 I - Q^H Q) / 2
+    zgemm64<float, float>(Qr, Qi, m * m, m, true, Qr, Qi, m * m, m, Tr, Ti, m * m, m, int(m),
+                          int(m), int(m), int(h), st);
+    ns_factor_kernel<<<grid_of(m * m * h), 256, 0, st>>>(Tr, Ti, int(m), m * m * h);
+    zgemm64<float, double>(Qr, Qi, m * m, m, false, Tr, Ti, m * m, m, Wr, Wi, m * m, m, int(m),
+                           int(m), int(m), int(h), st);
+    // 3. G = X W (X^H W when the work matrix is the conjugate transpose)
+    zgemm64<float, double>(Xr, Xi, n1 * n2, n1, transpose, Wr, Wi, m * m, m, Gr, Gi, p * m, p,
+                           int(p), int(m), int(m), int(h), st);
   }
-  if ((rc = launch_status("jacobi_kernel"))) return rc;
+  note_launches(3);
+  if ((rc = launch_status("svd_refine"))) return rc;
+  // 4. float64 sweeps from W: one or two to float64 convergence
+  if ((rc = jacobi_launch<double>(Gr, Gi, p * m, Wr, Wi, m * m, sig, int(p), int(m), int(h), sweeps,
+                                  flags, status, JAC_NORMALIZE, st)))
+    return rc;
   {
     KernelScope ks("svd_factors", st);
     // n1 >= n2: G holds U (n1 x m), Jacobi V holds V (n2 x m).  n1 < n2: the

@@ -6,17 +6,26 @@
 //   E = (X_obs - L - Y/mu) off the mask, 0 on it
 //   Y = Y + mu (L + E - X_obs)                    (admm_post_kernel)
 //   mu = min(rho mu, mu_max)                      (admm_mu_kernel)
-// X_obs is X where the mask is set and 0 elsewhere.  The slice SVT uses the
-// float64 one-sided Jacobi of svd.cu on a copy of M_hat_k (or its conjugate
-// transpose when n1 < n2): G = M_hat_k V, s_j = ||G_j||; the shrunk slice is
-// sum_j max(s_j - tau, 0) u_j v_j^H = (G diag(max(1 - tau/s_j, 0))) V^H.
+// X_obs is X where the mask is set and 0 elsewhere.  The slice SVT takes the
+// right singular vectors V from the float32 one-sided Jacobi of svd.cu on a
+// copy of M_hat_k (or its conjugate transpose when n1 < n2), then forms
+// H = M_hat_k V in float64 and the singular values as Rayleigh quotients
+// s_j = ||h_j|| / ||v_j||: their error is second order in the error of v_j,
+// which matters because max(s_j - tau, 0) amplifies the error of any s_j
+// close to tau.  The shrunk slice is
+// sum_j max(s_j - tau, 0) u_j v_j^H = sum_j c_j h_j v_j^H,
+// c_j = max(s_j - tau, 0) / (s_j ||v_j||^2).
 #include "tp_internal.cuh"
 
 namespace tp {
 
-int jacobi_double_launch(double* gr, double* gi, int64_t sG, double* vr, double* vi, int64_t sV,
-                         double* sig, int p, int q, int batch, int max_sweeps,
-                         const int* real_flags, int32_t* status, cudaStream_t st);
+int jacobi_float_launch(float* gr, float* gi, int64_t sG, float* vr, float* vi, int64_t sV,
+                        float* sig, int p, int q, int batch, int max_sweeps,
+                        const int* real_flags, int32_t* status, cudaStream_t st);
+int zgemm64_from_float(const float* ar, const float* ai, int64_t sA, int64_t lda, bool conj_a,
+                       const float* br, const float* bi, int64_t sB, int64_t ldb, double* cr,
+                       double* ci, int64_t sC, int64_t ldc, int M, int N, int K, int batch,
+                       cudaStream_t st);
 
 namespace {
 
@@ -52,11 +61,11 @@ __global__ void admm_mu_kernel(double* mu, double rho, double mu_max) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *mu = fmin(rho * *mu, mu_max);
 }
 
-// Work matrix of every slice in float64: G = M_hat_k (n1 x n2) or, when
-// transposed, G = M_hat_k^H (n2 x n1).
+// Work matrix of every slice: G = M_hat_k (n1 x n2) or, when transposed,
+// G = M_hat_k^H (n2 x n1).
 __global__ void to_work_kernel(const float* __restrict__ xr, const float* __restrict__ xi,
                                int64_t n1, int64_t n2, int64_t h, bool transpose,
-                               double* __restrict__ gr, double* __restrict__ gi) {
+                               float* __restrict__ gr, float* __restrict__ gi) {
   const int64_t per = n1 * n2, total = per * h;
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
        e += int64_t(gridDim.x) * blockDim.x) {
@@ -67,52 +76,59 @@ __global__ void to_work_kernel(const float* __restrict__ xr, const float* __rest
       gi[e] = xi[e];
     } else {
       gr[k * per + j + n2 * i] = xr[e];
-      gi[k * per + j + n2 * i] = -double(xi[e]);
+      gi[k * per + j + n2 * i] = -xi[e];
     }
   }
 }
 
-// Shrinks and rebuilds every slice: after the Jacobi, G holds unit columns
-// u_j and sig the s_j of the p x q work matrix; W (q x q) the right factor.
-// Out (n1 x n2 half-spectrum slice) = sum_j max(s_j - tau, 0) u_j w_j^H, or
-// its conjugate transpose when the work matrix was M_hat^H.
-__global__ void svt_rebuild_kernel(const double* __restrict__ gr, const double* __restrict__ gi,
-                                   int64_t sG, const double* __restrict__ wr,
-                                   const double* __restrict__ wi, int64_t sW,
-                                   const double* __restrict__ sig, int p, int q,
+// Shrinks and rebuilds every slice from V (q x q, float32) and H = W V
+// (p x q, float64; W the work matrix): the p x q work-shaped result
+// R = sum_j c_j h_j v_j^H, written as the n1 x n2 slice itself, or as its
+// conjugate transpose when the work matrix was M_hat^H.
+__global__ void svt_rebuild_kernel(const double* __restrict__ hr, const double* __restrict__ hi,
+                                   int64_t sH, const float* __restrict__ wr,
+                                   const float* __restrict__ wi, int64_t sW, int p, int q,
                                    const double* __restrict__ mu, bool transpose, int64_t n1,
                                    float* __restrict__ outr, float* __restrict__ outi) {
-  extern __shared__ double shrink[];   // q factors max(s_j - tau, 0)
+  extern __shared__ float coef[];   // q factors c_j
   const int64_t f = blockIdx.x;
   const double tau = 1.0 / *mu;
+  const double* Hr = hr + f * sH;
+  const double* Hi = hi + f * sH;
+  const float* Wr = wr + f * sW;
+  const float* Wi = wi + f * sW;
   for (int j = threadIdx.x; j < q; j += blockDim.x) {
-    const double s = sig[f * q + j];
-    shrink[j] = s > tau ? s - tau : 0.0;
+    double nv = 0.0, nh = 0.0;
+    for (int b = 0; b < q; ++b) {
+      const double x = Wr[b + int64_t(q) * j], y = Wi[b + int64_t(q) * j];
+      nv += x * x + y * y;
+    }
+    for (int a = 0; a < p; ++a) {
+      const double x = Hr[a + int64_t(p) * j], y = Hi[a + int64_t(p) * j];
+      nh += x * x + y * y;
+    }
+    const double s = nv > 0.0 ? sqrt(nh / nv) : 0.0;
+    coef[j] = s > tau ? float((s - tau) / (s * nv)) : 0.f;
   }
   __syncthreads();
-  const double* Gr = gr + f * sG;
-  const double* Gi = gi + f * sG;
-  const double* Wr = wr + f * sW;
-  const double* Wi = wi + f * sW;
   const int64_t per = int64_t(p) * q;
   for (int64_t e = threadIdx.x; e < per; e += blockDim.x) {
-    // entry (a, b) of the p x q work-shaped result R = U diag(shrink) W^H
     const int64_t a = e % p, b = e / p;
-    double sr = 0.0, si = 0.0;
+    float sr = 0.f, si = 0.f;
     for (int j = 0; j < q; ++j) {
-      const double c = shrink[j];
-      if (c == 0.0) continue;
-      const double ur = Gr[a + int64_t(p) * j], ui = Gi[a + int64_t(p) * j];
-      const double vr = Wr[b + int64_t(q) * j], vi = -Wi[b + int64_t(q) * j];   // conj(W(b, j))
-      sr += c * (ur * vr - ui * vi);
-      si += c * (ur * vi + ui * vr);
+      const float c = coef[j];
+      if (c == 0.f) continue;
+      const float ur = float(Hr[a + int64_t(p) * j]), ui = float(Hi[a + int64_t(p) * j]);
+      const float vr = Wr[b + int64_t(q) * j], vi = -Wi[b + int64_t(q) * j];   // conj(V(b, j))
+      sr = fmaf(c, ur * vr - ui * vi, sr);
+      si = fmaf(c, ur * vi + ui * vr, si);
     }
     if (!transpose) {            // R is the n1 x n2 slice itself
-      outr[f * per + a + int64_t(p) * b] = float(sr);
-      outi[f * per + a + int64_t(p) * b] = float(si);
+      outr[f * per + a + int64_t(p) * b] = sr;
+      outi[f * per + a + int64_t(p) * b] = si;
     } else {                     // R = slice^H: slice(b, a) = conj(R(a, b)), slice is n1 x n2, n1 = q
-      outr[f * per + b + n1 * a] = float(sr);
-      outi[f * per + b + n1 * a] = float(-si);
+      outr[f * per + b + n1 * a] = sr;
+      outi[f * per + b + n1 * a] = -si;
     }
   }
 }
@@ -137,9 +153,10 @@ size_t svt_ws(int64_t n1, int64_t n2, int64_t n3) {
   const size_t n = size_t(n1) * n2;
   return ws_bytes(n * n3, 4)                  // M (and L, reused)
          + 2 * ws_bytes(n * h, 4)             // M_hat / L_hat
-         + 2 * ws_bytes(p * q * h, 8)         // G
-         + 2 * ws_bytes(q * q * h, 8)         // W
-         + ws_bytes(q * h, 8) + ws_bytes(h, 4);
+         + 2 * ws_bytes(p * q * h, 4)         // G
+         + 2 * ws_bytes(q * q * h, 4)         // V
+         + 2 * ws_bytes(p * q * h, 8)         // H = W V (float64)
+         + ws_bytes(q * h, 4) + ws_bytes(h, 4);
 }
 
 int svt_run(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t n3, int iters,
@@ -156,11 +173,13 @@ int svt_run(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t
   float* M = ws.take<float>(size_t(n));
   float* Mr = ws.take<float>(size_t(n1) * n2 * h);
   float* Mi = ws.take<float>(size_t(n1) * n2 * h);
-  double* Gr = ws.take<double>(size_t(p) * q * h);
-  double* Gi = ws.take<double>(size_t(p) * q * h);
-  double* Wr = ws.take<double>(size_t(q) * q * h);
-  double* Wi = ws.take<double>(size_t(q) * q * h);
-  double* sig = ws.take<double>(size_t(q) * h);
+  float* Gr = ws.take<float>(size_t(p) * q * h);
+  float* Gi = ws.take<float>(size_t(p) * q * h);
+  float* Wr = ws.take<float>(size_t(q) * q * h);
+  float* Wi = ws.take<float>(size_t(q) * q * h);
+  double* Hr = ws.take<double>(size_t(p) * q * h);
+  double* Hi = ws.take<double>(size_t(p) * q * h);
+  float* sig = ws.take<float>(size_t(q) * h);
   int* flags = ws.take<int>(size_t(h));
   {
     KernelScope ks("svt_flags", st);
@@ -179,13 +198,17 @@ int svt_run(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t
       KernelScope ks("svt_work", st);
       to_work_kernel<<<grid_n(n1 * n2 * h), 256, 0, st>>>(Mr, Mi, n1, n2, h, transpose, Gr, Gi);
     }
-    if ((rc = jacobi_double_launch(Gr, Gi, p * q, Wr, Wi, q * q, sig, int(p), int(q), int(h),
-                                   sweeps, flags, status, st)))
+    if ((rc = jacobi_float_launch(Gr, Gi, p * q, Wr, Wi, q * q, sig, int(p), int(q), int(h),
+                                  sweeps, flags, status, st)))
+      return rc;
+    // H = W V in float64 from the untouched half spectrum (W = M_hat or M_hat^H)
+    if ((rc = zgemm64_from_float(Mr, Mi, n1 * n2, n1, transpose, Wr, Wi, q * q, q, Hr, Hi, p * q,
+                                 p, int(p), int(q), int(q), int(h), st)))
       return rc;
     {
       KernelScope ks("svt_rebuild", st);
-      svt_rebuild_kernel<<<unsigned(h), 256, size_t(q) * sizeof(double), st>>>(
-          Gr, Gi, p * q, Wr, Wi, q * q, sig, int(p), int(q), mu, transpose, n1, Mr, Mi);
+      svt_rebuild_kernel<<<unsigned(h), 256, size_t(q) * sizeof(float), st>>>(
+          Hr, Hi, p * q, Wr, Wi, q * q, int(p), int(q), mu, transpose, n1, Mr, Mi);
     }
     if ((rc = launch_irdft(Mr, Mi, n1 * n2, n1 * n2, n3, L, st))) return rc;
     {
