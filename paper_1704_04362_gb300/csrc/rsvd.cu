@@ -14,7 +14,7 @@
 // complex GEMM because X_hat^H is formed once.
 #include <cmath>
 
-#include "tp_internal.cuh"
+#include "jacobi_rot.cuh"
 
 namespace tp {
 
@@ -393,14 +393,9 @@ __device__ int jacobi2(C2* G, C2* W, int l, int ls, T tol, T floor_abs, int max_
         if (b < l) {
           const T al = G[a * ls + a].x, be = G[b * ls + b].x;
           const C2 ga = G[a * ls + b];
-          const T g = sqrt(ga.x * ga.x + ga.y * ga.y);
-          if (g > tol * sqrt(fabs(al * be)) && g > floor_abs && g > T(0)) {
-            const T zeta = (be - al) / (T(2) * g);
-            const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-            cs = T(1) / sqrt(T(1) + t * t);
-            sn = cs * t;
-            er = ga.x / g;
-            ei = -ga.y / g;   // e^{-i phi}
+          const T g2 = ga.x * ga.x + ga.y * ga.y;
+          if (g2 > tol * tol * fabs(al * be) && g2 > floor_abs * floor_abs && g2 > T(0)) {
+            jrot::rotation(al, be, ga.x, ga.y, g2, cs, sn, er, ei);   // er, ei: e^{-i phi}
             *rotated = 1;
           }
         }

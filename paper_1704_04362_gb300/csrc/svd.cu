@@ -21,16 +21,22 @@
 //      accumulated float32 rotations are orthonormal to ~1e-6, after it to
 //      ~1e-12);
 //   3. G = X V in float64;
-//   4. float64 Jacobi on that G, starting from V: the columns are already
-//      orthogonal to float32 accuracy, so one or two sweeps (quadratic
-//      convergence) reach float64 accuracy.
+//   4. float64 Jacobi on that G, starting from V, to float64 convergence:
+//      the columns are already orthogonal to float32 accuracy, so two or
+//      three sweeps (quadratic convergence) suffice, more only for a cluster
+//      of singular values at the float32 rounding floor (rank-deficient
+//      input), which float32 cannot resolve.
 // Steps 2-3 are batched float64 GEMMs spread over all SMs.
-#include "tp_internal.cuh"
+#include "jacobi_rot.cuh"
 
 namespace tp {
 namespace {
+using jrot::rotation;
 
-constexpr int SVD_THREADS = 512;
+#ifndef TP_SVD_THREADS
+#define TP_SVD_THREADS 1024
+#endif
+constexpr int SVD_THREADS = TP_SVD_THREADS;
 
 template <class T>
 __device__ __forceinline__ T warp_sum_t(T v) {
@@ -134,14 +140,11 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(T* g_re, T* g_im, i
         beta = warp_sum_t(beta);
         gr = warp_sum_t(gr);
         gi = warp_sum_t(gi);
-        const T g = sqrt(gr * gr + gi * gi);
-        if (!(g > tol * sqrt(alpha * beta)) || g == T(0)) continue;
+        const T g2 = gr * gr + gi * gi;
+        if (!(g2 > tol * tol * alpha * beta) || g2 == T(0)) continue;
         if (lane == 0) rotated = 1;
-        const T zeta = (beta - alpha) / (T(2) * g);
-        const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-        const T cs = T(1) / sqrt(T(1) + t * t);
-        const T sn = cs * t;
-        const T er = gr / g, ei = -gi / g;   // e^{-i phi}
+        T cs, sn, er, ei;   // cos, sin and e^{-i phi}
+        rotation(alpha, beta, gr, gi, g2, cs, sn, er, ei);
         for (int r = lane; r < p; r += 32) {
           const T xr = ar[r], xi = ai[r];
           const T yr = br[r] * er - bi[r] * ei, yi = br[r] * ei + bi[r] * er;   // b~
@@ -393,12 +396,13 @@ int jacobi_launch(T* gr, T* gi, int64_t sG, T* vr, T* vi, int64_t sV, T* sig, in
 
 }  // namespace
 
-// float32 one-sided Jacobi from V = I; G is left rotated (not normalised).
+// float32 one-sided Jacobi from V = I (init_v) or from the given V (then G
+// must be the work matrix times that V); G is left rotated, not normalised.
 int jacobi_float_launch(float* gr, float* gi, int64_t sG, float* vr, float* vi, int64_t sV,
                         float* sig, int p, int q, int batch, int max_sweeps,
-                        const int* real_flags, int32_t* status, cudaStream_t st) {
+                        const int* real_flags, int32_t* status, bool init_v, cudaStream_t st) {
   return jacobi_launch<float>(gr, gi, sG, vr, vi, sV, sig, p, q, batch, max_sweeps, real_flags,
-                              status, JAC_INIT_V, st);
+                              status, init_v ? JAC_INIT_V : 0, st);
 }
 
 // C_b = op(A_b) B_b in float64 from float32 planes (see zgemm64_kernel).
@@ -420,6 +424,45 @@ int jacobi_double_launch(double* gr, double* gi, int64_t sG, double* vr, double*
                          const int* real_flags, int32_t* status, cudaStream_t st) {
   return jacobi_launch<double>(gr, gi, sG, vr, vi, sV, sig, p, q, batch, max_sweeps, real_flags,
                                status, JAC_INIT_V | JAC_NORMALIZE, st);
+}
+
+
+// Float64-quality SVD of every p x q work matrix op(X_b) (op = identity or
+// the conjugate transpose of the float32 slice X_b, leading dimension ldx,
+// slice stride sX): steps 1-4 of the header.  F (p x q float32) must hold the
+// work matrix on entry and is overwritten.  On exit G (p x q) holds the unit
+// left singular vectors, W (q x q) the right ones, sig the singular values
+// (unsorted).  Q (q x q float32), qsig (q float32) and T (q x q float64) are
+// scratch.
+int hybrid_svd(const float* xr, const float* xi, int64_t sX, int64_t ldx, bool conj, int p, int q,
+               int batch, float* fr, float* fi, float* qr, float* qi, float* qsig, double* tr,
+               double* ti, double* gr, double* gi, double* wr, double* wi, double* sig,
+               const int* real_flags, int max_sweeps, int32_t* status, cudaStream_t st) {
+  int rc;
+  const int64_t pq = int64_t(p) * q, qq = int64_t(q) * q;
+  // 1. float32 sweeps (a cluster of singular values at the float32 rounding
+  //    floor may stall here; step 4 decides convergence)
+  if ((rc = jacobi_launch<float>(fr, fi, pq, qr, qi, qq, qsig, p, q, batch, max_sweeps, real_flags,
+                                 nullptr, JAC_INIT_V, st)))
+    return rc;
+  {
+    KernelScope ks("svd_refine", st);
+    // 2. W = Q (3 I - Q^H Q) / 2
+    zgemm64<float, float>(qr, qi, qq, q, true, qr, qi, qq, q, tr, ti, qq, q, q, q, q, batch, st);
+    ns_factor_kernel<<<grid_of(qq * batch), 256, 0, st>>>(tr, ti, q, qq * batch);
+    zgemm64<float, double>(qr, qi, qq, q, false, tr, ti, qq, q, wr, wi, qq, q, q, q, q, batch, st);
+    // 3. G = op(X) W
+    zgemm64<float, double>(xr, xi, sX, ldx, conj, wr, wi, qq, q, gr, gi, pq, p, p, q, q, batch, st);
+  }
+  note_launches(3);
+  if ((rc = launch_status("svd_refine"))) return rc;
+  // 4. float64 sweeps from W to float64 convergence: from columns already
+  //    orthogonal to float32 accuracy each sweep squares the residual, so two
+  //    or three sweeps suffice, more only for clusters of singular values at
+  //    the float32 rounding floor (rank-deficient input); the sweep cap and
+  //    TP_DEV_NOCONV apply here
+  return jacobi_launch<double>(gr, gi, pq, wr, wi, qq, sig, p, q, batch, max_sweeps, real_flags,
+                               status, JAC_NORMALIZE, st);
 }
 
 size_t tsvd_ws(int64_t n1, int64_t n2, int64_t n3) {
@@ -484,28 +527,8 @@ int tsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, float* U, float
   note_launches(1);
   if ((rc = launch_status("svd_prep"))) return rc;
   const int sweeps = (opts && opts->max_sweeps > 0) ? opts->max_sweeps : 30;
-  // 1. float32 sweeps: rotations Q with X Q nearly column-orthogonal (a
-  //    float32 stall at the rounding floor is not an error: step 4 decides)
-  if ((rc = jacobi_launch<float>(Fr, Fi, p * m, Qr, Qi, m * m, fsig, int(p), int(m), int(h), sweeps,
-                                 flags, nullptr, JAC_INIT_V, st)))
-    return rc;
-  {
-    KernelScope ks("svd_refine", st);
-    // 2. W = Q (3 I - Q^H Q) / 2
-    zgemm64<float, float>(Qr, Qi, m * m, m, true, Qr, Qi, m * m, m, Tr, Ti, m * m, m, int(m),
-                          int(m), int(m), int(h), st);
-    ns_factor_kernel<<<grid_of(m * m * h), 256, 0, st>>>(Tr, Ti, int(m), m * m * h);
-    zgemm64<float, double>(Qr, Qi, m * m, m, false, Tr, Ti, m * m, m, Wr, Wi, m * m, m, int(m),
-                           int(m), int(m), int(h), st);
-    // 3. G = X W (X^H W when the work matrix is the conjugate transpose)
-    zgemm64<float, double>(Xr, Xi, n1 * n2, n1, transpose, Wr, Wi, m * m, m, Gr, Gi, p * m, p,
-                           int(p), int(m), int(m), int(h), st);
-  }
-  note_launches(3);
-  if ((rc = launch_status("svd_refine"))) return rc;
-  // 4. float64 sweeps from W: one or two to float64 convergence
-  if ((rc = jacobi_launch<double>(Gr, Gi, p * m, Wr, Wi, m * m, sig, int(p), int(m), int(h), sweeps,
-                                  flags, status, JAC_NORMALIZE, st)))
+  if ((rc = hybrid_svd(Xr, Xi, n1 * n2, n1, transpose, int(p), int(m), int(h), Fr, Fi, Qr, Qi, fsig,
+                       Tr, Ti, Gr, Gi, Wr, Wi, sig, flags, sweeps, status, st)))
     return rc;
   {
     KernelScope ks("svd_factors", st);

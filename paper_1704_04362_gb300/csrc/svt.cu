@@ -8,7 +8,9 @@
 //   mu = min(rho mu, mu_max)                      (admm_mu_kernel)
 // X_obs is X where the mask is set and 0 elsewhere.  The slice SVT takes the
 // right singular vectors V from the float32 one-sided Jacobi of svd.cu on a
-// copy of M_hat_k (or its conjugate transpose when n1 < n2), then forms
+// copy of M_hat_k (or its conjugate transpose when n1 < n2), warm-started
+// from the previous iteration's V (the ADMM iterate moves little between
+// iterations, so a sweep or two re-converges), then forms
 // H = M_hat_k V in float64 and the singular values as Rayleigh quotients
 // s_j = ||h_j|| / ||v_j||: their error is second order in the error of v_j,
 // which matters because max(s_j - tau, 0) amplifies the error of any s_j
@@ -21,7 +23,8 @@ namespace tp {
 
 int jacobi_float_launch(float* gr, float* gi, int64_t sG, float* vr, float* vi, int64_t sV,
                         float* sig, int p, int q, int batch, int max_sweeps,
-                        const int* real_flags, int32_t* status, cudaStream_t st);
+                        const int* real_flags, int32_t* status, bool init_v, cudaStream_t st);
+int launch_cgemm(const CGemm& g, cudaStream_t st);
 int zgemm64_from_float(const float* ar, const float* ai, int64_t sA, int64_t lda, bool conj_a,
                        const float* br, const float* bi, int64_t sB, int64_t ldb, double* cr,
                        double* ci, int64_t sC, int64_t ldc, int M, int N, int K, int batch,
@@ -155,6 +158,7 @@ size_t svt_ws(int64_t n1, int64_t n2, int64_t n3) {
          + 2 * ws_bytes(n * h, 4)             // M_hat / L_hat
          + 2 * ws_bytes(p * q * h, 4)         // G
          + 2 * ws_bytes(q * q * h, 4)         // V
+         + 2 * ws_bytes(p * q * h, 4)         // work matrix (warm start: G = work V)
          + 2 * ws_bytes(p * q * h, 8)         // H = W V (float64)
          + ws_bytes(q * h, 4) + ws_bytes(h, 4);
 }
@@ -177,6 +181,8 @@ int svt_run(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t
   float* Gi = ws.take<float>(size_t(p) * q * h);
   float* Wr = ws.take<float>(size_t(q) * q * h);
   float* Wi = ws.take<float>(size_t(q) * q * h);
+  float* Kr = ws.take<float>(size_t(p) * q * h);
+  float* Ki = ws.take<float>(size_t(p) * q * h);
   double* Hr = ws.take<double>(size_t(p) * q * h);
   double* Hi = ws.take<double>(size_t(p) * q * h);
   float* sig = ws.take<float>(size_t(q) * h);
@@ -194,12 +200,19 @@ int svt_run(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t
     DftGather gm{M, n1 * n2, 1, 1, 0, n1 * n2, nullptr, nullptr, nullptr, 0, n3, Mr, Mi,
                  n1 * n2, n1 * n2, nullptr, nullptr, 0};
     if ((rc = launch_rdft(gm, st))) return rc;
+    const bool warm = it > 0;
     {
       KernelScope ks("svt_work", st);
-      to_work_kernel<<<grid_n(n1 * n2 * h), 256, 0, st>>>(Mr, Mi, n1, n2, h, transpose, Gr, Gi);
+      to_work_kernel<<<grid_n(n1 * n2 * h), 256, 0, st>>>(Mr, Mi, n1, n2, h, transpose,
+                                                         warm ? Kr : Gr, warm ? Ki : Gi);
+    }
+    if (warm) {   // G = work V_prev
+      CGemm gw{Kr, Ki, Wr, Wi, Gr, Gi, p, q, q, nullptr, p, q, p, p * q, q * q, p * q, h, n3,
+               TP_FP32, nullptr, nullptr, nullptr, nullptr, q, status};
+      if ((rc = launch_cgemm(gw, st))) return rc;
     }
     if ((rc = jacobi_float_launch(Gr, Gi, p * q, Wr, Wi, q * q, sig, int(p), int(q), int(h),
-                                  sweeps, flags, status, st)))
+                                  sweeps, flags, status, !warm, st)))
       return rc;
     // H = W V in float64 from the untouched half spectrum (W = M_hat or M_hat^H)
     if ((rc = zgemm64_from_float(Mr, Mi, n1 * n2, n1, transpose, Wr, Wi, q * q, q, Hr, Hi, p * q,

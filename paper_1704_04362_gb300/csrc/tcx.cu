@@ -5,8 +5,9 @@
 // Z_hat_k = P_k A_hat_k with P_k = C_hat_k C_hat_k^dagger the orthogonal
 // projector onto range(C_hat_k).  P_k = U_r U_r^H where U_r are the left
 // singular vectors of C_hat_k (float64 one-sided Jacobi) whose singular values
-// exceed MATLAB's pinv cut-off max(n1, c') eps(s_max).  The number of picks
-// is read back to the host once (the Jacobi is sized by it).
+// exceed MATLAB's pinv cut-off max(n1, c') eps(s_max).  The SVD is the
+// float32-sweeps + float64-refinement one of svd.cu (float64 accuracy).  The
+// number of picks is read back to the host once (the SVD is sized by it).
 #include <cmath>
 
 #include "tp_internal.cuh"
@@ -14,15 +15,16 @@
 namespace tp {
 
 int launch_cgemm(const CGemm& g, cudaStream_t st);
-int jacobi_double_launch(double* gr, double* gi, int64_t sG, double* vr, double* vi, int64_t sV,
-                         double* sig, int p, int q, int batch, int max_sweeps,
-                         const int* real_flags, int32_t* status, cudaStream_t st);
+int hybrid_svd(const float* xr, const float* xi, int64_t sX, int64_t ldx, bool conj, int p, int q,
+               int batch, float* fr, float* fi, float* qr, float* qi, float* qsig, double* tr,
+               double* ti, double* gr, double* gi, double* wr, double* wi, double* sig,
+               const int* real_flags, int max_sweeps, int32_t* status, cudaStream_t st);
 
 namespace {
 
 __global__ void work_kernel(const float* __restrict__ xr, const float* __restrict__ xi,
                             int64_t n1, int64_t c, int64_t ld, int64_t slice, int64_t h,
-                            bool transpose, double* __restrict__ gr, double* __restrict__ gi) {
+                            bool transpose, float* __restrict__ gr, float* __restrict__ gi) {
   const int64_t per = n1 * c, total = per * h;
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
        e += int64_t(gridDim.x) * blockDim.x) {
@@ -34,7 +36,7 @@ __global__ void work_kernel(const float* __restrict__ xr, const float* __restric
       gi[e] = vi;
     } else {
       gr[k * per + j + c * i] = vr;
-      gi[k * per + j + c * i] = -double(vi);
+      gi[k * per + j + c * i] = -vi;
     }
   }
 }
@@ -93,8 +95,12 @@ size_t tcx_ws(int64_t n1, int64_t n2, int64_t n3) {
          ws_bytes(size_t(n2), 4) + ws_bytes(1, 8) +
          2 * ws_bytes(size_t(n1) * n2 * h, 4)      // C_hat (capacity n2 columns)
          + 2 * ws_bytes(size_t(n1) * n2 * h, 4)    // A_hat
-         + 2 * ws_bytes(P * m * h, 8)              // Jacobi G
-         + 2 * ws_bytes(size_t(n2) * n2 * h, 8)    // Jacobi W (q <= n2)
+         + 2 * ws_bytes(P * m * h, 8)              // SVD: G
+         + 2 * ws_bytes(size_t(n2) * n2 * h, 8)    // SVD: W (q <= n2)
+         + 2 * ws_bytes(P * m * h, 4)              // SVD: float32 work matrix
+         + 2 * ws_bytes(m * m * h, 4)              // SVD: float32 rotations
+         + ws_bytes(m * h, 4)                      // SVD: float32 norms
+         + 2 * ws_bytes(m * m * h, 8)              // SVD: Newton-Schulz factor
          + ws_bytes(size_t(n2) * h, 8) + ws_bytes(h, 4)
          + 4 * ws_bytes(size_t(n1) * m * h, 4)     // U_r and U_r^H
          + 2 * ws_bytes(m * n2 * h, 4)             // U_r^H A_hat
@@ -124,6 +130,13 @@ int tcx_run(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, uint6
   double* Gi = ws.take<double>(size_t(P_cap) * m_cap * h);
   double* Wr = ws.take<double>(size_t(n2) * n2 * h);
   double* Wi = ws.take<double>(size_t(n2) * n2 * h);
+  float* Fr = ws.take<float>(size_t(P_cap) * m_cap * h);
+  float* Fi = ws.take<float>(size_t(P_cap) * m_cap * h);
+  float* Qr = ws.take<float>(size_t(m_cap) * m_cap * h);
+  float* Qi = ws.take<float>(size_t(m_cap) * m_cap * h);
+  float* qsig = ws.take<float>(size_t(m_cap) * h);
+  double* NSr = ws.take<double>(size_t(m_cap) * m_cap * h);
+  double* NSi = ws.take<double>(size_t(m_cap) * m_cap * h);
   double* sig = ws.take<double>(size_t(n2) * h);
   int* flags = ws.take<int>(size_t(h));
   float* Br = ws.take<float>(size_t(n1) * m_cap * h);
@@ -169,13 +182,13 @@ int tcx_run(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, uint6
   {
     KernelScope ks("tcx_work", st);
     work_kernel<<<grid_n(n1 * cprime * h), 256, 0, st>>>(Cr, Ci, n1, cprime, n1, n1 * n2, h,
-                                                         transpose, Gr, Gi);
+                                                         transpose, Fr, Fi);
     flags_kernel<<<unsigned((h + 255) / 256), 256, 0, st>>>(flags, h, n3);
   }
   note_launches(1);
   const int sweeps = (opts && opts->max_sweeps > 0) ? opts->max_sweeps : 30;
-  if ((rc = jacobi_double_launch(Gr, Gi, p * q, Wr, Wi, q * q, sig, int(p), int(q), int(h), sweeps,
-                                 flags, status, st)))
+  if ((rc = hybrid_svd(Cr, Ci, n1 * n2, n1, transpose, int(p), int(q), int(h), Fr, Fi, Qr, Qi, qsig,
+                       NSr, NSi, Gr, Gi, Wr, Wi, sig, flags, sweeps, status, st)))
     return rc;
   {
     KernelScope ks("tcx_basis", st);
