@@ -92,7 +92,8 @@ typedef enum {
   TP_OP_TSVD_RANDOMIZED = 4, /* dims: n1, n2, n3, k, p */
   TP_OP_TCOMPLETE_SVT = 5,   /* dims: n1, n2, n3 */
   TP_OP_SLICE_NORMS = 6,     /* dims: n1, n2, n3 */
-  TP_OP_TCX = 7              /* dims: n1, n2, n3 */
+  TP_OP_TCX = 7,             /* dims: n1, n2, n3 */
+  TP_OP_TCOMPLETE_SVT_BATCHED = 8  /* dims: n1, n2, n3 of every tensor (nd = 3 ntens) */
 } tp_op;
 
 /* ---------------------------------------------------------------- t-product
@@ -180,12 +181,45 @@ int tcx(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, uint64_t 
  *            previous outputs resumes it)
  *   mu    device float64 scalar, read and updated in place
  * Paper constants: mu0 = 1e-3, rho = 1.1, mu_max = 1e10.  The slice SVT
- * runs the float64 one-sided Jacobi.  Limits as tsvd.                      */
+ * takes V from a float32 one-sided Jacobi (warm-started from the previous
+ * iteration's V within a call) and the singular values as Rayleigh quotients
+ * ||W v_j|| / ||v_j||.  Resuming from the returned state agrees with one
+ * longer call to float32 rounding (the Jacobi's starting rotations are not
+ * part of the state).  Limits as tsvd.                                      */
 int tcomplete_svt(const float* X, const uint8_t* mask,
                   int64_t n1, int64_t n2, int64_t n3, int iters,
                   double rho, double mu_max,
                   float* L, float* E, float* Y, double* mu,
                   const tp_opts* opts, void* stream);
+
+/* One tensor of a batched completion: X and mask are read; L, E, Y and *mu
+ * (device float64) are the state, read and updated as in tcomplete_svt.  All
+ * pointers are device pointers owned by the caller.                        */
+typedef struct {
+  const float* X;
+  const uint8_t* mask;
+  float* L;
+  float* E;
+  float* Y;
+  double* mu;
+  int64_t n1, n2, n3;
+} tp_tensor_desc;
+
+/* tcomplete_svt_batched: tcomplete_svt over ntens independent tensors of
+ * possibly different sizes (the batched form of the completion workload,
+ * e.g. many videos), `iters` iterations each.
+ *   descs  HOST array of ntens descriptors
+ * The tensors run concurrently on side streams forked from `stream`; the
+ * first iteration is launched directly and the remaining iters - 1 replay
+ * one captured CUDA graph of an iteration over all tensors.  Results are
+ * identical to ntens separate tcomplete_svt calls with the same arguments.
+ * Workspace: tp_workspace_query(TP_OP_TCOMPLETE_SVT_BATCHED, {n1, n2, n3 of
+ * each tensor}, 3 ntens) (the sum of the tensors' own).  Synchronises
+ * `stream` before returning (the graph and side streams are released).
+ * Errors: TP_ENULL for a NULL descs or tensor pointer, TP_EINVAL for
+ * ntens < 1 or invalid sizes; limits as tcomplete_svt.                      */
+int tcomplete_svt_batched(int ntens, const tp_tensor_desc* descs, int iters,
+                          double rho, double mu_max, const tp_opts* opts, void* stream);
 
 /* ---------------------------------------------------------------- stages
  * The steps of the paths above, exposed for callers that compose their own.

@@ -21,13 +21,13 @@ __all__ = [
     "TprodError", "lib", "lib_path", "empty_tensor", "as_tprod_layout",
     "tprod", "tprod_sampled", "tsvd", "tsvd_randomized", "tcomplete_svt", "tcx",
     "rdft3", "irdft3", "slice_norms", "sample_draw", "launch_count", "exported_symbols",
-    "profile_start", "profile_stop", "slice_norms_noalloc",
+    "profile_start", "profile_stop", "slice_norms_noalloc", "tcomplete_svt_batched",
 ]
 
 TP_FP32, TP_TF32X3, TP_BF16X3 = 0, 1, 2
 TP_PROB_AB, TP_PROB_A2, TP_PROB_GIVEN = 0, 1, 2
 TP_OP_TPROD, TP_OP_TPROD_SAMPLED, TP_OP_TSVD, TP_OP_TSVD_RANDOMIZED, TP_OP_TCOMPLETE_SVT, \
-    TP_OP_SLICE_NORMS, TP_OP_TCX = 1, 2, 3, 4, 5, 6, 7
+    TP_OP_SLICE_NORMS, TP_OP_TCX, TP_OP_TCOMPLETE_SVT_BATCHED = 1, 2, 3, 4, 5, 6, 7, 8
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _c_i64, _c_u64, _c_int, _c_u32 = ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32
@@ -44,6 +44,12 @@ class TpOpts(ctypes.Structure):
                 ("status", ctypes.c_void_p)]
 
 
+class TpTensorDesc(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("mask", ctypes.c_void_p), ("L", ctypes.c_void_p),
+                ("E", ctypes.c_void_p), ("Y", ctypes.c_void_p), ("mu", ctypes.c_void_p),
+                ("n1", ctypes.c_int64), ("n2", ctypes.c_int64), ("n3", ctypes.c_int64)]
+
+
 # Every symbol include/tprod.h declares, with its ctypes signature.
 _SIGS = {
     "tprod": (_c_int, [_vp, _vp, _vp, _c_i64, _c_i64, _c_i64, _c_i64, _vp, _vp]),
@@ -56,6 +62,7 @@ _SIGS = {
                                _vp, _vp, _vp, _vp, _vp, _vp]),
     "tcx": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_i64, _c_u64, _c_int, _vp, _vp, _vp, _vp,
                      _vp, _vp]),
+    "tcomplete_svt_batched": (_c_int, [_c_int, _vp, _c_int, _dbl, _dbl, _vp, _vp]),
     "tp_rdft3": (_c_int, [_vp, _c_i64, _c_i64, _vp, _vp, _vp]),
     "tp_irdft3": (_c_int, [_vp, _vp, _c_i64, _c_i64, _vp, _vp]),
     "tp_slice_norms": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_int, _vp, _vp, _vp]),
@@ -318,6 +325,29 @@ def tcomplete_svt(X, mask, iters, L=None, E=None, Y=None, mu=None, mu0=1e-3, rho
                              _tensor_arg(mu, "mu", torch.float64), ctypes.byref(o), _stream())
     _check(rc, "tcomplete_svt")
     return L, E, Y, mu
+
+
+def tcomplete_svt_batched(tensors, iters, rho=1.1, mu_max=1e10, status=None, max_sweeps=0):
+    """tcomplete_svt over a list of independent tensors of possibly different
+    sizes: each item is a tuple (X, mask, L, E, Y, mu) of device tensors
+    (column-major layout, mask uint8, mu a float64 1-element tensor), updated
+    in place.  Returns the list."""
+    torch = _torch()
+    descs = (TpTensorDesc * len(tensors))()
+    dims = []
+    for i, (X, mask, L, E, Y, mu) in enumerate(tensors):
+        n1, n2, n3 = X.shape
+        descs[i] = TpTensorDesc(_tensor_arg(X, "X").value,
+                                _tensor_arg(mask, "mask", torch.uint8).value,
+                                _tensor_arg(L, "L").value, _tensor_arg(E, "E").value,
+                                _tensor_arg(Y, "Y").value,
+                                _tensor_arg(mu, "mu", torch.float64).value, n1, n2, n3)
+        dims += [n1, n2, n3]
+    o = _opts(TP_OP_TCOMPLETE_SVT_BATCHED, dims, TP_FP32, status, max_sweeps)
+    rc = lib().tcomplete_svt_batched(len(tensors), ctypes.cast(descs, ctypes.c_void_p), int(iters),
+                                     float(rho), float(mu_max), ctypes.byref(o), _stream())
+    _check(rc, "tcomplete_svt_batched")
+    return tensors
 
 
 def tcx(A, c, seed=0, prob_mode=TP_PROB_A2, p_given=None, status=None):

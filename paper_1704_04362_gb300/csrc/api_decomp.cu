@@ -6,6 +6,9 @@ size_t tsvd_ws(int64_t n1, int64_t n2, int64_t n3);
 bool fft_supported(int64_t n3);
 size_t rsvd_ws(int64_t n1, int64_t n2, int64_t n3, int64_t k, int64_t p);
 size_t svt_ws(int64_t n1, int64_t n2, int64_t n3);
+size_t svt_batched_ws_dims(const int64_t* dims, int nd);
+int svt_batched_run(int ntens, const tp_tensor_desc* d, int iters, double rho, double mu_max,
+                    const tp_opts* opts, cudaStream_t st);
 int svt_run(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t n3, int iters,
             double rho, double mu_max, float* L, float* E, float* Y, double* mu,
             const tp_opts* opts, cudaStream_t st);
@@ -23,6 +26,7 @@ size_t workspace_for(int op, const int64_t* d, int nd) {
     case TP_OP_TSVD: return nd >= 3 ? tsvd_ws(d[0], d[1], d[2]) : 0;
     case TP_OP_TSVD_RANDOMIZED: return nd >= 5 ? rsvd_ws(d[0], d[1], d[2], d[3], d[4]) : 0;
     case TP_OP_TCOMPLETE_SVT: return nd >= 3 ? svt_ws(d[0], d[1], d[2]) : 0;
+    case TP_OP_TCOMPLETE_SVT_BATCHED: return nd >= 3 ? svt_batched_ws_dims(d, nd) : 0;
     case TP_OP_TCX: return nd >= 3 ? tcx_ws(d[0], d[1], d[2]) : 0;
     default: return 0;
   }
@@ -82,6 +86,35 @@ int tcomplete_svt(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, i
     return TP_EUNSUPPORTED;
   }
   return svt_run(X, mask, n1, n2, n3, iters, rho, mu_max, L, E, Y, mu, opts, as_stream(stream));
+}
+
+int tcomplete_svt_batched(int ntens, const tp_tensor_desc* descs, int iters, double rho,
+                          double mu_max, const tp_opts* opts, void* stream) {
+  if (!descs) { set_error("tcomplete_svt_batched: NULL descs"); return TP_ENULL; }
+  if (ntens < 1 || iters < 0 || !(rho > 0.0) || !(mu_max > 0.0)) {
+    set_error("tcomplete_svt_batched: invalid count or constants");
+    return TP_EINVAL;
+  }
+  for (int i = 0; i < ntens; ++i) {
+    const tp_tensor_desc& t = descs[i];
+    if (!t.X || !t.mask || !t.L || !t.E || !t.Y || !t.mu) {
+      set_error("tcomplete_svt_batched: tensor %d has a NULL pointer", i);
+      return TP_ENULL;
+    }
+    if (!dims3_ok(t.n1, t.n2, t.n3)) {
+      set_error("tcomplete_svt_batched: tensor %d has invalid sizes", i);
+      return TP_EINVAL;
+    }
+    if ((t.n1 < t.n2 ? t.n1 : t.n2) > 512) {
+      set_error("tcomplete_svt_batched: tensor %d has min(n1, n2) > 512", i);
+      return TP_EUNSUPPORTED;
+    }
+    if (t.n3 > 512 && !fft_supported(t.n3)) {
+      set_error("tcomplete_svt_batched: tensor %d: n3 > 512 must factor into radices 2..13", i);
+      return TP_EUNSUPPORTED;
+    }
+  }
+  return svt_batched_run(ntens, descs, iters, rho, mu_max, opts, as_stream(stream));
 }
 
 int tcx(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, uint64_t seed,

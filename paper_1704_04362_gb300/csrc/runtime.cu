@@ -61,6 +61,11 @@ constexpr size_t kMaxProfRecs = 1 << 16;
 
 KernelScope::KernelScope(const char* n, cudaStream_t s) : name(n), st(s), slot(-1) {
   if (!g_prof_on) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return;   // launches inside a graph capture are not timed one by one
+  }
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (!g_prof_on || g_prof_recs.size() >= kMaxProfRecs) return;
   ProfRec r{n, nullptr, nullptr};

@@ -10,13 +10,16 @@
 // right singular vectors V from the float32 one-sided Jacobi of svd.cu on a
 // copy of M_hat_k (or its conjugate transpose when n1 < n2), warm-started
 // from the previous iteration's V (the ADMM iterate moves little between
-// iterations, so a sweep or two re-converges), then forms
-// H = M_hat_k V in float64 and the singular values as Rayleigh quotients
-// s_j = ||h_j|| / ||v_j||: their error is second order in the error of v_j,
-// which matters because max(s_j - tau, 0) amplifies the error of any s_j
-// close to tau.  The shrunk slice is
+// iterations, so a sweep or two re-converges), then forms H = W V from the
+// unrotated work matrix W and the singular values as Rayleigh quotients
+// s_j = ||h_j|| / ||v_j||: their error is second order in the error of v_j
+// (the Jacobi's own column norms carry the rounding of every rotation), which
+// matters because max(s_j - tau, 0) amplifies the error of any s_j close to
+// tau.  The shrunk slice is
 // sum_j max(s_j - tau, 0) u_j v_j^H = sum_j c_j h_j v_j^H,
 // c_j = max(s_j - tau, 0) / (s_j ||v_j||^2).
+#include <vector>
+
 #include "tp_internal.cuh"
 
 namespace tp {
@@ -25,10 +28,6 @@ int jacobi_float_launch(float* gr, float* gi, int64_t sG, float* vr, float* vi, 
                         float* sig, int p, int q, int batch, int max_sweeps,
                         const int* real_flags, int32_t* status, bool init_v, cudaStream_t st);
 int launch_cgemm(const CGemm& g, cudaStream_t st);
-int zgemm64_from_float(const float* ar, const float* ai, int64_t sA, int64_t lda, bool conj_a,
-                       const float* br, const float* bi, int64_t sB, int64_t ldb, double* cr,
-                       double* ci, int64_t sC, int64_t ldc, int M, int N, int K, int batch,
-                       cudaStream_t st);
 
 namespace {
 
@@ -68,27 +67,30 @@ __global__ void admm_mu_kernel(double* mu, double rho, double mu_max) {
 // G = M_hat_k^H (n2 x n1).
 __global__ void to_work_kernel(const float* __restrict__ xr, const float* __restrict__ xi,
                                int64_t n1, int64_t n2, int64_t h, bool transpose,
-                               float* __restrict__ gr, float* __restrict__ gi) {
+                               float* __restrict__ gr, float* __restrict__ gi,
+                               float* __restrict__ g2r, float* __restrict__ g2i) {
   const int64_t per = n1 * n2, total = per * h;
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
        e += int64_t(gridDim.x) * blockDim.x) {
     const int64_t k = e / per, r = e - k * per;
     const int64_t i = r % n1, j = r / n1;
-    if (!transpose) {
-      gr[e] = xr[e];
-      gi[e] = xi[e];
-    } else {
-      gr[k * per + j + n2 * i] = xr[e];
-      gi[k * per + j + n2 * i] = -xi[e];
+    const int64_t o = transpose ? k * per + j + n2 * i : e;
+    const float vr = xr[e], vi = transpose ? -xi[e] : xi[e];
+    gr[o] = vr;
+    gi[o] = vi;
+    if (g2r) {   // second copy (the Jacobi rotates the first in place)
+      g2r[o] = vr;
+      g2i[o] = vi;
     }
   }
 }
 
-// Shrinks and rebuilds every slice from V (q x q, float32) and H = W V
-// (p x q, float64; W the work matrix): the p x q work-shaped result
-// R = sum_j c_j h_j v_j^H, written as the n1 x n2 slice itself, or as its
-// conjugate transpose when the work matrix was M_hat^H.
-__global__ void svt_rebuild_kernel(const double* __restrict__ hr, const double* __restrict__ hi,
+// Shrinks and rebuilds every slice from V (q x q) and H = W V (p x q; W the
+// work matrix): with n_j = ||v_j|| and s_j = ||h_j|| / n_j (norms accumulated
+// in float64), the p x q work-shaped result R = sum_j c_j h_j v_j^H,
+// c_j = max(s_j - tau, 0) / (s_j n_j^2), written as the n1 x n2 slice itself,
+// or as its conjugate transpose when the work matrix was M_hat^H.
+__global__ void svt_rebuild_kernel(const float* __restrict__ hr, const float* __restrict__ hi,
                                    int64_t sH, const float* __restrict__ wr,
                                    const float* __restrict__ wi, int64_t sW, int p, int q,
                                    const double* __restrict__ mu, bool transpose, int64_t n1,
@@ -96,8 +98,8 @@ __global__ void svt_rebuild_kernel(const double* __restrict__ hr, const double* 
   extern __shared__ float coef[];   // q factors c_j
   const int64_t f = blockIdx.x;
   const double tau = 1.0 / *mu;
-  const double* Hr = hr + f * sH;
-  const double* Hi = hi + f * sH;
+  const float* Hr = hr + f * sH;
+  const float* Hi = hi + f * sH;
   const float* Wr = wr + f * sW;
   const float* Wi = wi + f * sW;
   for (int j = threadIdx.x; j < q; j += blockDim.x) {
@@ -121,7 +123,7 @@ __global__ void svt_rebuild_kernel(const double* __restrict__ hr, const double* 
     for (int j = 0; j < q; ++j) {
       const float c = coef[j];
       if (c == 0.f) continue;
-      const float ur = float(Hr[a + int64_t(p) * j]), ui = float(Hi[a + int64_t(p) * j]);
+      const float ur = Hr[a + int64_t(p) * j], ui = Hi[a + int64_t(p) * j];
       const float vr = Wr[b + int64_t(q) * j], vi = -Wi[b + int64_t(q) * j];   // conj(V(b, j))
       sr = fmaf(c, ur * vr - ui * vi, sr);
       si = fmaf(c, ur * vi + ui * vr, si);
@@ -156,85 +158,247 @@ size_t svt_ws(int64_t n1, int64_t n2, int64_t n3) {
   const size_t n = size_t(n1) * n2;
   return ws_bytes(n * n3, 4)                  // M (and L, reused)
          + 2 * ws_bytes(n * h, 4)             // M_hat / L_hat
-         + 2 * ws_bytes(p * q * h, 4)         // G
+         + 2 * ws_bytes(p * q * h, 4)         // G (rotated by the Jacobi)
          + 2 * ws_bytes(q * q * h, 4)         // V
-         + 2 * ws_bytes(p * q * h, 4)         // work matrix (warm start: G = work V)
-         + 2 * ws_bytes(p * q * h, 8)         // H = W V (float64)
+         + 2 * ws_bytes(p * q * h, 4)         // work matrix W
+         + 2 * ws_bytes(p * q * h, 4)         // H = W V
          + ws_bytes(q * h, 4) + ws_bytes(h, 4);
+}
+
+// One tensor of a completion run: its ADMM state (caller's buffers) and its
+// workspace.
+struct SvtTensor {
+  const float* X;
+  const uint8_t* mask;
+  float *L, *E, *Y;
+  double* mu;
+  int64_t n1, n2, n3, h, p, q;
+  bool transpose;
+  float *M, *Mr, *Mi, *Gr, *Gi, *Vr, *Vi, *Kr, *Ki, *Hr, *Hi, *sig;
+  int* flags;
+};
+
+SvtTensor svt_carve(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t n3,
+                    float* L, float* E, float* Y, double* mu, Arena& ws) {
+  SvtTensor t{};
+  t.X = X;
+  t.mask = mask;
+  t.L = L;
+  t.E = E;
+  t.Y = Y;
+  t.mu = mu;
+  t.n1 = n1;
+  t.n2 = n2;
+  t.n3 = n3;
+  t.h = half_len(n3);
+  t.transpose = n1 < n2;
+  t.p = t.transpose ? n2 : n1;
+  t.q = t.transpose ? n1 : n2;
+  const size_t h = size_t(t.h), pq = size_t(t.p) * t.q, qq = size_t(t.q) * t.q;
+  t.M = ws.take<float>(size_t(n1) * n2 * n3);
+  t.Mr = ws.take<float>(size_t(n1) * n2 * h);
+  t.Mi = ws.take<float>(size_t(n1) * n2 * h);
+  t.Gr = ws.take<float>(pq * h);
+  t.Gi = ws.take<float>(pq * h);
+  t.Vr = ws.take<float>(qq * h);
+  t.Vi = ws.take<float>(qq * h);
+  t.Kr = ws.take<float>(pq * h);
+  t.Ki = ws.take<float>(pq * h);
+  t.Hr = ws.take<float>(pq * h);
+  t.Hi = ws.take<float>(pq * h);
+  t.sig = ws.take<float>(size_t(t.q) * h);
+  t.flags = ws.take<int>(h);
+  return t;
+}
+
+int svt_init(const SvtTensor& t, cudaStream_t st) {
+  {
+    KernelScope ks("svt_flags", st);
+    flags_kernel<<<unsigned((t.h + 255) / 256), 256, 0, st>>>(t.flags, t.h, t.n3);
+  }
+  return launch_status("svt_flags");
+}
+
+// One ADMM iteration of one tensor on stream st.  warm: start the Jacobi from
+// the V left by the previous iteration of this tensor.
+int svt_iteration(const SvtTensor& t, bool warm, double rho, double mu_max, int sweeps,
+                  int32_t* status, cudaStream_t st) {
+  int rc;
+  const int64_t n = t.n1 * t.n2 * t.n3, n12 = t.n1 * t.n2;
+  const int64_t p = t.p, q = t.q, h = t.h;
+  {
+    KernelScope ks("admm_pre", st);
+    admm_pre_kernel<<<grid_n(n), 256, 0, st>>>(t.X, t.mask, t.E, t.Y, t.mu, n, t.M);
+  }
+  DftGather gm{t.M, n12, 1, 1, 0, n12, nullptr, nullptr, nullptr, 0, t.n3, t.Mr, t.Mi,
+               n12, n12, nullptr, nullptr, 0};
+  if ((rc = launch_rdft(gm, st))) return rc;
+  {   // work matrix W (kept in K), and G = W for a cold start
+    KernelScope ks("svt_work", st);
+    to_work_kernel<<<grid_n(n12 * h), 256, 0, st>>>(t.Mr, t.Mi, t.n1, t.n2, h, t.transpose, t.Kr,
+                                                    t.Ki, warm ? nullptr : t.Gr,
+                                                    warm ? nullptr : t.Gi);
+  }
+  if (warm) {   // G = W V_prev
+    CGemm gw{t.Kr, t.Ki, t.Vr, t.Vi, t.Gr, t.Gi, p, q, q, nullptr, p, q, p, p * q, q * q, p * q,
+             h, t.n3, TP_FP32, nullptr, nullptr, nullptr, nullptr, q, status};
+    if ((rc = launch_cgemm(gw, st))) return rc;
+  }
+  if ((rc = jacobi_float_launch(t.Gr, t.Gi, p * q, t.Vr, t.Vi, q * q, t.sig, int(p), int(q),
+                                int(h), sweeps, t.flags, status, !warm, st)))
+    return rc;
+  {   // H = W V from the unrotated work matrix
+    CGemm gh{t.Kr, t.Ki, t.Vr, t.Vi, t.Hr, t.Hi, p, q, q, nullptr, p, q, p, p * q, q * q, p * q,
+             h, t.n3, TP_FP32, nullptr, nullptr, nullptr, nullptr, q, status};
+    if ((rc = launch_cgemm(gh, st))) return rc;
+  }
+  {
+    KernelScope ks("svt_rebuild", st);
+    svt_rebuild_kernel<<<unsigned(h), 256, size_t(q) * sizeof(float), st>>>(
+        t.Hr, t.Hi, p * q, t.Vr, t.Vi, q * q, int(p), int(q), t.mu, t.transpose, t.n1, t.Mr,
+        t.Mi);
+  }
+  if ((rc = launch_irdft(t.Mr, t.Mi, n12, n12, t.n3, t.L, st))) return rc;
+  {
+    KernelScope ks("admm_post", st);
+    admm_post_kernel<<<grid_n(n), 256, 0, st>>>(t.X, t.mask, t.L, t.E, t.Y, t.mu, n);
+  }
+  {
+    KernelScope ks("admm_mu", st);
+    admm_mu_kernel<<<1, 32, 0, st>>>(t.mu, rho, mu_max);
+  }
+  return launch_status("admm iteration");
 }
 
 int svt_run(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t n3, int iters,
             double rho, double mu_max, float* L, float* E, float* Y, double* mu,
             const tp_opts* opts, cudaStream_t st) {
-  const int64_t h = half_len(n3);
-  const bool transpose = n1 < n2;
-  const int64_t p = transpose ? n2 : n1, q = transpose ? n1 : n2;
-  const int64_t n = n1 * n2 * n3;
   Arena ws;
   int rc = acquire_workspace(opts, svt_ws(n1, n2, n3), &ws);
   if (rc) return rc;
   int32_t* status = opts ? opts->status : nullptr;
-  float* M = ws.take<float>(size_t(n));
-  float* Mr = ws.take<float>(size_t(n1) * n2 * h);
-  float* Mi = ws.take<float>(size_t(n1) * n2 * h);
-  float* Gr = ws.take<float>(size_t(p) * q * h);
-  float* Gi = ws.take<float>(size_t(p) * q * h);
-  float* Wr = ws.take<float>(size_t(q) * q * h);
-  float* Wi = ws.take<float>(size_t(q) * q * h);
-  float* Kr = ws.take<float>(size_t(p) * q * h);
-  float* Ki = ws.take<float>(size_t(p) * q * h);
-  double* Hr = ws.take<double>(size_t(p) * q * h);
-  double* Hi = ws.take<double>(size_t(p) * q * h);
-  float* sig = ws.take<float>(size_t(q) * h);
-  int* flags = ws.take<int>(size_t(h));
-  {
-    KernelScope ks("svt_flags", st);
-    flags_kernel<<<unsigned((h + 255) / 256), 256, 0, st>>>(flags, h, n3);
-  }
   const int sweeps = (opts && opts->max_sweeps > 0) ? opts->max_sweeps : 30;
-  for (int it = 0; it < iters; ++it) {
-    {
-      KernelScope ks("admm_pre", st);
-      admm_pre_kernel<<<grid_n(n), 256, 0, st>>>(X, mask, E, Y, mu, n, M);
-    }
-    DftGather gm{M, n1 * n2, 1, 1, 0, n1 * n2, nullptr, nullptr, nullptr, 0, n3, Mr, Mi,
-                 n1 * n2, n1 * n2, nullptr, nullptr, 0};
-    if ((rc = launch_rdft(gm, st))) return rc;
-    const bool warm = it > 0;
-    {
-      KernelScope ks("svt_work", st);
-      to_work_kernel<<<grid_n(n1 * n2 * h), 256, 0, st>>>(Mr, Mi, n1, n2, h, transpose,
-                                                         warm ? Kr : Gr, warm ? Ki : Gi);
-    }
-    if (warm) {   // G = work V_prev
-      CGemm gw{Kr, Ki, Wr, Wi, Gr, Gi, p, q, q, nullptr, p, q, p, p * q, q * q, p * q, h, n3,
-               TP_FP32, nullptr, nullptr, nullptr, nullptr, q, status};
-      if ((rc = launch_cgemm(gw, st))) return rc;
-    }
-    if ((rc = jacobi_float_launch(Gr, Gi, p * q, Wr, Wi, q * q, sig, int(p), int(q), int(h),
-                                  sweeps, flags, status, !warm, st)))
-      return rc;
-    // H = W V in float64 from the untouched half spectrum (W = M_hat or M_hat^H)
-    if ((rc = zgemm64_from_float(Mr, Mi, n1 * n2, n1, transpose, Wr, Wi, q * q, q, Hr, Hi, p * q,
-                                 p, int(p), int(q), int(q), int(h), st)))
-      return rc;
-    {
-      KernelScope ks("svt_rebuild", st);
-      svt_rebuild_kernel<<<unsigned(h), 256, size_t(q) * sizeof(float), st>>>(
-          Hr, Hi, p * q, Wr, Wi, q * q, int(p), int(q), mu, transpose, n1, Mr, Mi);
-    }
-    if ((rc = launch_irdft(Mr, Mi, n1 * n2, n1 * n2, n3, L, st))) return rc;
-    {
-      KernelScope ks("admm_post", st);
-      admm_post_kernel<<<grid_n(n), 256, 0, st>>>(X, mask, L, E, Y, mu, n);
-    }
-    {
-      KernelScope ks("admm_mu", st);
-      admm_mu_kernel<<<1, 32, 0, st>>>(mu, rho, mu_max);
-    }
-    if ((rc = launch_status("admm iteration"))) return rc;
-  }
+  const SvtTensor t = svt_carve(X, mask, n1, n2, n3, L, E, Y, mu, ws);
+  if ((rc = svt_init(t, st))) return rc;
+  for (int it = 0; it < iters; ++it)
+    if ((rc = svt_iteration(t, it > 0, rho, mu_max, sweeps, status, st))) return rc;
   return TP_OK;
+}
+
+size_t svt_batched_ws(int ntens, const tp_tensor_desc* d) {
+  size_t total = 0;
+  for (int i = 0; i < ntens; ++i) total += svt_ws(d[i].n1, d[i].n2, d[i].n3);
+  return total;
+}
+
+size_t svt_batched_ws_dims(const int64_t* dims, int nd) {
+  size_t total = 0;
+  for (int i = 0; i + 2 < nd; i += 3) total += svt_ws(dims[i], dims[i + 1], dims[i + 2]);
+  return total;
+}
+
+namespace {
+constexpr int kSideStreams = 8;
+
+// Forks the tensors of one iteration over the side streams and joins them
+// back into st (event record / wait pairs: valid eagerly and under capture).
+// The captured iteration is recorded on a private non-blocking stream (the
+// legacy default stream cannot be captured) and its graph launched on the
+// caller's stream.
+int svt_fork_join(std::vector<SvtTensor>& T, bool warm, bool init, double rho, double mu_max,
+                  int sweeps, int32_t* status, cudaStream_t st, cudaStream_t* side,
+                  cudaEvent_t fork, cudaEvent_t* join, int ns) {
+  int rc = TP_OK;
+  if (cudaEventRecord(fork, st) != cudaSuccess) return TP_ECUDA;
+  for (int s = 0; s < ns; ++s)
+    if (cudaStreamWaitEvent(side[s], fork, 0) != cudaSuccess) return TP_ECUDA;
+  for (size_t i = 0; i < T.size() && rc == TP_OK; ++i) {
+    cudaStream_t ss = side[i % size_t(ns)];
+    if (init) rc = svt_init(T[i], ss);
+    if (rc == TP_OK) rc = svt_iteration(T[i], warm, rho, mu_max, sweeps, status, ss);
+  }
+  for (int s = 0; s < ns; ++s) {
+    if (cudaEventRecord(join[s], side[s]) != cudaSuccess ||
+        cudaStreamWaitEvent(st, join[s], 0) != cudaSuccess)
+      return TP_ECUDA;
+  }
+  return rc;
+}
+}  // namespace
+
+int svt_batched_run(int ntens, const tp_tensor_desc* d, int iters, double rho, double mu_max,
+                    const tp_opts* opts, cudaStream_t st) {
+  Arena ws;
+  int rc = acquire_workspace(opts, svt_batched_ws(ntens, d), &ws);
+  if (rc) return rc;
+  if (iters <= 0) return TP_OK;
+  int32_t* status = opts ? opts->status : nullptr;
+  const int sweeps = (opts && opts->max_sweeps > 0) ? opts->max_sweeps : 30;
+  std::vector<SvtTensor> T;
+  T.reserve(size_t(ntens));
+  for (int i = 0; i < ntens; ++i)
+    T.push_back(svt_carve(d[i].X, d[i].mask, d[i].n1, d[i].n2, d[i].n3, d[i].L, d[i].E, d[i].Y,
+                          d[i].mu, ws));
+  const int ns = ntens < kSideStreams ? ntens : kSideStreams;
+  cudaStream_t side[kSideStreams] = {};
+  cudaEvent_t join[kSideStreams] = {};
+  cudaEvent_t fork = nullptr;
+  cudaStream_t cap = nullptr;   // capture stream (the caller's may be the legacy stream)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool ok = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess;
+  for (int s = 0; s < ns && ok; ++s)
+    ok = cudaStreamCreateWithFlags(&side[s], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&join[s], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    set_error("tcomplete_svt_batched: creating streams or events failed");
+    rc = TP_ECUDA;
+  }
+  // iteration 1: cold Jacobi start, launched directly
+  if (rc == TP_OK)
+    rc = svt_fork_join(T, false, true, rho, mu_max, sweeps, status, st, side, fork, join, ns);
+  // iterations 2..iters: one captured iteration, replayed
+  if (rc == TP_OK && iters > 1) {
+    const uint64_t before = tp_launch_count();
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      set_error("tcomplete_svt_batched: stream capture could not begin");
+      rc = TP_ECUDA;
+    } else {
+      rc = svt_fork_join(T, true, false, rho, mu_max, sweeps, status, cap, side, fork, join, ns);
+      const cudaError_t e = cudaStreamEndCapture(cap, &graph);
+      if (rc == TP_OK && e != cudaSuccess) {
+        set_error("tcomplete_svt_batched: stream capture failed (%s)", cudaGetErrorString(e));
+        rc = TP_ECUDA;
+      }
+    }
+    const uint64_t per_iter = tp_launch_count() - before;   // counted once at capture
+    if (rc == TP_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+      set_error("tcomplete_svt_batched: graph instantiation failed");
+      rc = TP_ECUDA;
+    }
+    for (int it = 1; it < iters && rc == TP_OK; ++it)
+      if (cudaGraphLaunch(exec, st) != cudaSuccess) {
+        set_error("tcomplete_svt_batched: graph launch failed");
+        rc = TP_ECUDA;
+      }
+    if (rc == TP_OK && iters > 2) note_launches(per_iter * uint64_t(iters - 2));
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess && rc == TP_OK) {
+    set_error("tcomplete_svt_batched: %s", cudaGetErrorString(cudaGetLastError()));
+    rc = TP_ECUDA;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  for (int s = 0; s < ns; ++s) {
+    if (join[s]) cudaEventDestroy(join[s]);
+    if (side[s]) cudaStreamDestroy(side[s]);
+  }
+  if (fork) cudaEventDestroy(fork);
+  if (cap) cudaStreamDestroy(cap);
+  cudaGetLastError();
+  return rc;
 }
 
 }  // namespace tp

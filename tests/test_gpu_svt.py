@@ -89,3 +89,38 @@ def test_recovers_low_rank_video():
     tp.tcomplete_svt(Xd, Md, 150, L=Ld, E=Ed, Y=Yd, mu=mud)
     rse = rel_fro(to_np(Ld), truth.astype(np.float64))
     assert rse < 0.05
+
+
+def test_batched_equals_separate_calls_and_oracle():
+    """tcomplete_svt_batched over tensors of uneven sizes (one per side
+    stream and a shared side stream for the rest, graph replay after the
+    first iteration) gives exactly the results of separate tcomplete_svt
+    calls; the smallest tensor also tracks the oracle."""
+    import torch
+    sizes = [(20, 16, 6), (12, 30, 5), (33, 17, 8), (24, 24, 1), (16, 40, 7), (9, 11, 4),
+             (30, 22, 3), (18, 18, 9), (40, 12, 6), (14, 26, 5)]
+    iters = 12
+    batch, single = [], []
+    for i, (n1, n2, n3) in enumerate(sizes):
+        X = synth.lowrank_np(n1, n2, n3, 3, seed=70 + i, noise=0.01)
+        X = X / np.sqrt(np.mean(X.astype(np.float64) ** 2))
+        mask = np.random.default_rng(80 + i).random(X.shape) < 0.6
+        Z = np.zeros_like(X)
+        batch.append(state_on_device(X, mask, Z, Z, Z, 1e-3))
+        single.append(state_on_device(X, mask, Z, Z, Z, 1e-3))
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    tp.tcomplete_svt_batched(batch, iters, status=st)
+    assert int(st.item()) == 0
+    for (Xd, Md, L, E, Y, mu) in single:
+        tp.tcomplete_svt(Xd, Md, iters, L=L, E=E, Y=Y, mu=mu)
+    for b, s in zip(batch, single):
+        for x, y in zip(b[2:], s[2:]):
+            assert torch.equal(x, y)
+    # the oracle on the first tensor
+    n1, n2, n3 = sizes[0]
+    X = synth.lowrank_np(n1, n2, n3, 3, seed=70, noise=0.01)
+    X = X / np.sqrt(np.mean(X.astype(np.float64) ** 2))
+    mask = np.random.default_rng(80).random(X.shape) < 0.6
+    Lr, _, _, mur = completion_ref.tcomplete_svt(X.astype(np.float64), mask, iters)
+    assert rel_fro(to_np(batch[0][2]), Lr) < 1e-4
+    assert abs(float(batch[0][5].item()) / mur - 1) < 1e-12
