@@ -17,9 +17,9 @@ metric  "t-product TFLOP/s": nominal facewise-GEMM flops of the step
         (8 n1 c' n4 per complex slice, 2 n1 c' n4 per real slice) divided by
         the step time; inputs (3.6 GB) are larger than L2 and are streamed
         every step.
-e2e     the same metric through the C entry point with host buffers: the
-        step's A and B copied from pinned host memory and Z copied back inside
-        the timed region.
+e2e     the same metric through the C entry point with host buffers: every
+        step's A and B copied from pinned host memory and its Z copied back
+        inside the timed region (steps pipelined over two device buffer sets).
 Multi-GPU: every rank runs its own replica (weak scaling, no collective).
 --impl reference times the float64 oracle on the host cores instead.
 """
@@ -396,7 +396,7 @@ def main():
                     help="comma-separated precisions also timed (the 3xTF32 split and the plain "
                          "FP32 form), or 'none'")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--small", action="store_true", help="profiling case, not a bench number")
     ap.add_argument("--no-rsvd", action="store_true", help="skip the randomized t-SVD line")
     ap.add_argument("--no-rows", action="store_true", help="skip the t-SVD / t-CX / ADMM rows")
@@ -491,39 +491,66 @@ def main():
     if roof is not None:
         roof["kernel"] = dom
 
-    # end to end through the C entry point with host buffers
+    # end to end through the C entry point with host buffers: every step
+    # copies its A and B from pinned host memory and its Z back.  Steps are
+    # pipelined over two device buffer sets: step k+1's upload (copy stream)
+    # overlaps step k's compute (launch stream) and download (second copy
+    # stream); the host link (about 210 GB/s each way on these boxes) bounds it.
     e2e = None
     if args.e2e_steps > 0:
         Ah = torch.empty((N3, N2, N1), dtype=torch.float32, pin_memory=True)
         Bh = torch.empty((N3, N4, N2), dtype=torch.float32, pin_memory=True)
-        Zh = torch.empty((N3, N4, N1), dtype=torch.float32, pin_memory=True)
+        Zh = [torch.empty((N3, N4, N1), dtype=torch.float32, pin_memory=True) for _ in range(2)]
         Ah.copy_(A.permute(2, 1, 0))
         Bh.copy_(B.permute(2, 1, 0))
-        Ad = tp.empty_tensor(N1, N2, N3)
-        Bd = tp.empty_tensor(N2, N4, N3)
+        Ad = [tp.empty_tensor(N1, N2, N3) for _ in range(2)]
+        Bd = [tp.empty_tensor(N2, N4, N3) for _ in range(2)]
+        Zd = [tp.empty_tensor(N1, N4, N3) for _ in range(2)]
+        up, down = torch.cuda.Stream(), torch.cuda.Stream()
+        uploaded = [torch.cuda.Event() for _ in range(2)]
+        computed = [torch.cuda.Event() for _ in range(2)]
+        downloaded = [torch.cuda.Event() for _ in range(2)]
+        for b in range(2):
+            computed[b].record(stream)
+            downloaded[b].record(stream)
         torch.cuda.synchronize()
 
-        def e2e_step():
-            Ad.permute(2, 1, 0).copy_(Ah, non_blocking=True)
-            Bd.permute(2, 1, 0).copy_(Bh, non_blocking=True)
-            tp.tprod_sampled(Ad, Bd, C_SAMPLES, seed=SEED, precision=prec, Z=Z, idx=idx, count=cnt)
-            Zh.copy_(Z.permute(2, 1, 0), non_blocking=True)
+        def e2e_steps(n):
+            for k in range(n):
+                b = k % 2
+                with torch.cuda.stream(up):
+                    up.wait_event(computed[b])           # set b's inputs free again
+                    Ad[b].permute(2, 1, 0).copy_(Ah, non_blocking=True)
+                    Bd[b].permute(2, 1, 0).copy_(Bh, non_blocking=True)
+                    uploaded[b].record(up)
+                stream.wait_event(uploaded[b])
+                stream.wait_event(downloaded[b])         # set b's Z read back
+                tp.tprod_sampled(Ad[b], Bd[b], C_SAMPLES, seed=SEED, precision=prec, Z=Zd[b],
+                                 idx=idx, count=cnt)
+                computed[b].record(stream)
+                with torch.cuda.stream(down):
+                    down.wait_event(computed[b])
+                    Zh[b].copy_(Zd[b].permute(2, 1, 0), non_blocking=True)
+                    downloaded[b].record(down)
+            stream.wait_event(downloaded[(n - 1) % 2])
+            stream.wait_event(downloaded[n % 2])
 
-        e2e_step()
+        e2e_steps(2)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         ev0.record(stream)
-        for _ in range(args.e2e_steps):
-            e2e_step()
+        e2e_steps(args.e2e_steps)
         ev1.record(stream)
         torch.cuda.synchronize()
         ems = reduce_max(ev0.elapsed_time(ev1) / args.e2e_steps, dist, "cuda")
         e2e = {"value": world * flops / (ems * 1e-3) / 1e12, "unit": "TFLOP/s",
                "ms_per_step": ems,
                "h2d_bytes_per_step": int(Ah.numel() * 4 + Bh.numel() * 4),
-               "d2h_bytes_per_step": int(Zh.numel() * 4)}
-        del Ah, Bh, Zh, Ad, Bd
+               "d2h_bytes_per_step": int(Zh[0].numel() * 4),
+               "pipeline": "two buffer sets; upload of step k+1 overlaps compute and "
+                           "download of step k"}
+        del Ah, Bh, Zh, Ad, Bd, Zd
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
