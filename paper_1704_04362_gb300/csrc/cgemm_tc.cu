@@ -141,12 +141,12 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b
 
 // One K step (32 bytes of every row) of one accumulator.
 template <bool BF16>
-__device__ __forceinline__ void mma_step(uint32_t d, uint64_t a, uint64_t b, bool neg,
+__device__ __forceinline__ void mma_step(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t accum) {
   if constexpr (BF16)
-    mma_bf16(d, a, b, neg ? IDESC_BF16_NEG : IDESC_BF16, accum);
+    mma_bf16(d, a, b, idesc, accum);
   else
-    mma_tf32(d, a, b, neg ? IDESC_NEG : IDESC, accum);
+    mma_tf32(d, a, b, idesc, accum);
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -191,6 +191,9 @@ __global__ void __launch_bounds__(NTHR, 1) cgemm_tc_kernel(const __grid_constant
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t K = p.dynK ? *p.dynK : p.K;
   const int nkb = int((K + TBK - 1) / TBK);
+  constexpr int SUBK = BF16 ? 16 : 8;   // K elements per 32-byte MMA step
+  const int klast = int(K - int64_t(nkb - 1) * TBK);
+  const int nsub_last = (klast + SUBK - 1) / SUBK;
   const int tiles_per_f = p.mt * p.nt;
   const int64_t ntiles = int64_t(tiles_per_f) * p.h;
 
@@ -270,6 +273,9 @@ __global__ void __launch_bounds__(NTHR, 1) cgemm_tc_kernel(const __grid_constant
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t dre = tmem + uint32_t(b) * (2 * TN), dim = dre + TN;
+      // full-width MMAs on every tile (a narrower MMA for the ragged last
+      // column of tiles measured slower than multiplying its zero padding)
+      const uint32_t id = BF16 ? IDESC_BF16 : IDESC, idn = BF16 ? IDESC_BF16_NEG : IDESC_NEG;
       for (int kb = 0; kb < nkb; ++kb, ++it) {
         const int s = int(it % STAGES);
         if (!mbar_wait(smem_u32(&full[s]), uint32_t((it / STAGES) & 1))) {
@@ -279,8 +285,11 @@ __global__ void __launch_bounds__(NTHR, 1) cgemm_tc_kernel(const __grid_constant
         if (*(volatile int*)&abort_flag) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t st = smem_u32(smem + size_t(s) * STAGE_BYTES);
+        // the last K block runs only the 32-byte steps that hold data
+        const int nsub = kb == nkb - 1 ? nsub_last : ROWB / 32;
 #pragma unroll
         for (int sub = 0; sub < ROWB / 32; ++sub) {
+          if (sub >= nsub) break;
           uint64_t a[4], bb[4];
 #pragma unroll
           for (int pl = 0; pl < 4; ++pl) {
@@ -290,19 +299,19 @@ __global__ void __launch_bounds__(NTHR, 1) cgemm_tc_kernel(const __grid_constant
           }
           const uint32_t first = (kb == 0 && sub == 0) ? 0u : 1u;
           // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
-          mma_step<BF16>(dre, a[0], bb[0], false, first);
-          mma_step<BF16>(dre, a[0], bb[1], false, 1);
-          mma_step<BF16>(dre, a[1], bb[0], false, 1);
+          mma_step<BF16>(dre, a[0], bb[0], id, first);
+          mma_step<BF16>(dre, a[0], bb[1], id, 1);
+          mma_step<BF16>(dre, a[1], bb[0], id, 1);
           if (!real_slice) {
-            mma_step<BF16>(dre, a[2], bb[2], true, 1);
-            mma_step<BF16>(dre, a[2], bb[3], true, 1);
-            mma_step<BF16>(dre, a[3], bb[2], true, 1);
-            mma_step<BF16>(dim, a[0], bb[2], false, first);
-            mma_step<BF16>(dim, a[0], bb[3], false, 1);
-            mma_step<BF16>(dim, a[1], bb[2], false, 1);
-            mma_step<BF16>(dim, a[2], bb[0], false, 1);
-            mma_step<BF16>(dim, a[2], bb[1], false, 1);
-            mma_step<BF16>(dim, a[3], bb[0], false, 1);
+            mma_step<BF16>(dre, a[2], bb[2], idn, 1);
+            mma_step<BF16>(dre, a[2], bb[3], idn, 1);
+            mma_step<BF16>(dre, a[3], bb[2], idn, 1);
+            mma_step<BF16>(dim, a[0], bb[2], id, first);
+            mma_step<BF16>(dim, a[0], bb[3], id, 1);
+            mma_step<BF16>(dim, a[1], bb[2], id, 1);
+            mma_step<BF16>(dim, a[2], bb[0], id, 1);
+            mma_step<BF16>(dim, a[2], bb[1], id, 1);
+            mma_step<BF16>(dim, a[3], bb[0], id, 1);
           }
         }
         mma_commit(smem_u32(&empty[s]));   // stage s free once these MMAs finish
