@@ -18,6 +18,10 @@ philox_ref      Philox4x32-10 counter-based generator (Salmon et al., SC'11)
 sampling_ref    Section 3.1: slice norms, sampling probabilities (eqs. for the
                 "nearly optimal" and "A-only" choices), Algorithm 2
                 (rt-product).
+learned_ref     Per-frequency adaptive rank rule for the randomized t-SVD and
+                the rank/oversampling predictor network (features, forward,
+                back-propagation, Adam): not in the paper; it fixes what the
+                predictor kernels compute.
 decomp_ref      Theorem 2.6 (t-SVD by facewise SVD), randomized low-tubal-rank
                 t-SVD (Halko-Martinsson-Tropp range finder per frequency),
                 Algorithm 3/4 (t-project, t-CX).
