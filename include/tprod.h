@@ -93,7 +93,9 @@ typedef enum {
   TP_OP_TCOMPLETE_SVT = 5,   /* dims: n1, n2, n3 */
   TP_OP_SLICE_NORMS = 6,     /* dims: n1, n2, n3 */
   TP_OP_TCX = 7,             /* dims: n1, n2, n3 */
-  TP_OP_TCOMPLETE_SVT_BATCHED = 8  /* dims: n1, n2, n3 of every tensor (nd = 3 ntens) */
+  TP_OP_TCOMPLETE_SVT_BATCHED = 8, /* dims: n1, n2, n3 of every tensor (nd = 3 ntens) */
+  TP_OP_SKETCH_SPECTRUM = 9,        /* dims: n1, n2, n3, l */
+  TP_OP_MLP_TRAIN = 10              /* dims: batch */
 } tp_op;
 
 /* ---------------------------------------------------------------- t-product
@@ -220,6 +222,50 @@ typedef struct {
  * ntens < 1 or invalid sizes; limits as tcomplete_svt.                      */
 int tcomplete_svt_batched(int ntens, const tp_tensor_desc* descs, int iters,
                           double rho, double mu_max, const tp_opts* opts, void* stream);
+
+/* ---------------------------------------------------------------- truncation ranks
+ * Per-frequency truncation ranks for the randomized t-SVD.  The paper sets
+ * no rank rule (its multi-rank, Section 2, r_i = rank of the i-th Fourier
+ * frontal slice, is the rule's tol -> 0 limit) and has no learned part; these
+ * calls are the plain adaptive rule and a small learned predictor of the
+ * rank and of the oversampling a sketch needs to resolve it.
+ *
+ * tp_sketch_spectrum: the randomized range finder of tsvd_randomized with l
+ *   columns and q power iterations (same seed use), then the singular values
+ *   of Q^H X_hat_k at every half-spectrum frequency, descending:
+ *   sig_out[k*l + i], device float32, h x l (h = n3/2 + 1).  Limits
+ *   l <= min(n1, n2, 96); workspace TP_OP_SKETCH_SPECTRUM {n1, n2, n3, l}.
+ * tp_rank_rule: rank_out[k] (device int32, h) = the smallest r in [1, cap]
+ *   with sum_{i>r} sig[k,i]^2 <= tol^2 sum_i sig[k,i]^2 (cap if none; 0 for
+ *   an all-zero row); sig is h x l device float32, rows descending.  Sums
+ *   are float64, accumulated from the smallest value, unfused.
+ * tp_rank_features: the predictor's inputs, feat_out[k*16 + i] (device
+ *   float16) = max(log10(sig[k,i+1] / sig[k,0]), -8) / 8, i = 0..15; l >= 17.
+ * tp_mlp_*: the predictor, a 16 -> 128 -> 128 -> 2 perceptron with ReLU.
+ *   theta: tp_mlp_param_count() float32 master parameters, packed W1 (128 x
+ *   16), b1, W2 (128 x 128), b2, W3 (2 x 128), b3, matrices row-major (output
+ *   index slowest); w16: the same as float16 (the values every kernel uses;
+ *   tp_mlp_round sets it from theta).
+ *   tp_mlp_forward: y[b*2 + o] (device float32) for float16 inputs x (batch
+ *   x 16), float32 accumulation.
+ *   tp_mlp_train_step: with loss (1/2B) sum (y - target)^2 over the batch
+ *   (target batch x 2, float32), writes grad_out[0 .. P-1] = the gradient
+ *   at w16 and grad_out[P] = the loss (P = tp_mlp_param_count(), device
+ *   float32), then, if lr > 0, one Adam step (beta 0.9, 0.999, eps 1e-8;
+ *   step >= 1 counts updates) on theta with moments adam_m, adam_v (zero
+ *   before the first step) and re-rounds w16.  Gradient sums are reduced in
+ *   a fixed order (deterministic).  Workspace TP_OP_MLP_TRAIN {batch}.     */
+int tp_sketch_spectrum(const float* X, int64_t n1, int64_t n2, int64_t n3, int l, int q,
+                       uint64_t seed, float* sig_out, const tp_opts* opts, void* stream);
+int tp_rank_rule(const float* sig, int64_t h, int l, int cap, double tol, int32_t* rank_out,
+                 void* stream);
+int tp_rank_features(const float* sig, int64_t h, int l, void* feat_out, void* stream);
+int tp_mlp_param_count(void);
+int tp_mlp_round(const float* theta, void* w16, void* stream);
+int tp_mlp_forward(const void* w16, const void* x16, int64_t batch, float* y, void* stream);
+int tp_mlp_train_step(float* theta, void* w16, float* adam_m, float* adam_v, int step, float lr,
+                      const void* x16, const float* target, int64_t batch, float* grad_out,
+                      const tp_opts* opts, void* stream);
 
 /* ---------------------------------------------------------------- stages
  * The steps of the paths above, exposed for callers that compose their own.

@@ -22,12 +22,15 @@ __all__ = [
     "tprod", "tprod_sampled", "tsvd", "tsvd_randomized", "tcomplete_svt", "tcx",
     "rdft3", "irdft3", "slice_norms", "sample_draw", "launch_count", "exported_symbols",
     "profile_start", "profile_stop", "slice_norms_noalloc", "tcomplete_svt_batched",
+    "sketch_spectrum", "rank_rule", "rank_features", "mlp_param_count", "mlp_round",
+    "mlp_forward", "mlp_train_step",
 ]
 
 TP_FP32, TP_TF32X3, TP_BF16X3 = 0, 1, 2
 TP_PROB_AB, TP_PROB_A2, TP_PROB_GIVEN = 0, 1, 2
 TP_OP_TPROD, TP_OP_TPROD_SAMPLED, TP_OP_TSVD, TP_OP_TSVD_RANDOMIZED, TP_OP_TCOMPLETE_SVT, \
-    TP_OP_SLICE_NORMS, TP_OP_TCX, TP_OP_TCOMPLETE_SVT_BATCHED = 1, 2, 3, 4, 5, 6, 7, 8
+    TP_OP_SLICE_NORMS, TP_OP_TCX, TP_OP_TCOMPLETE_SVT_BATCHED, TP_OP_SKETCH_SPECTRUM, \
+    TP_OP_MLP_TRAIN = 1, 2, 3, 4, 5, 6, 7, 8, 9, 10
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _c_i64, _c_u64, _c_int, _c_u32 = ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32
@@ -63,6 +66,15 @@ _SIGS = {
     "tcx": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_i64, _c_u64, _c_int, _vp, _vp, _vp, _vp,
                      _vp, _vp]),
     "tcomplete_svt_batched": (_c_int, [_c_int, _vp, _c_int, _dbl, _dbl, _vp, _vp]),
+    "tp_sketch_spectrum": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_int, _c_int, _c_u64, _vp,
+                                    _vp, _vp]),
+    "tp_rank_rule": (_c_int, [_vp, _c_i64, _c_int, _c_int, _dbl, _vp, _vp]),
+    "tp_rank_features": (_c_int, [_vp, _c_i64, _c_int, _vp, _vp]),
+    "tp_mlp_param_count": (_c_int, []),
+    "tp_mlp_round": (_c_int, [_vp, _vp, _vp]),
+    "tp_mlp_forward": (_c_int, [_vp, _vp, _c_i64, _vp, _vp]),
+    "tp_mlp_train_step": (_c_int, [_vp, _vp, _vp, _vp, _c_int, ctypes.c_float, _vp, _vp, _c_i64,
+                                   _vp, _vp, _vp]),
     "tp_rdft3": (_c_int, [_vp, _c_i64, _c_i64, _vp, _vp, _vp]),
     "tp_irdft3": (_c_int, [_vp, _vp, _c_i64, _c_i64, _vp, _vp]),
     "tp_slice_norms": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_int, _vp, _vp, _vp]),
@@ -348,6 +360,83 @@ def tcomplete_svt_batched(tensors, iters, rho=1.1, mu_max=1e10, status=None, max
                                      float(rho), float(mu_max), ctypes.byref(o), _stream())
     _check(rc, "tcomplete_svt_batched")
     return tensors
+
+
+def sketch_spectrum(X, l, q=2, seed=0, status=None):
+    """Singular values of the randomized sketch of every half-spectrum
+    frequency: (h, l) float32 device tensor, rows descending."""
+    torch = _torch()
+    n1, n2, n3 = X.shape
+    sig = torch.empty((n3 // 2 + 1, l), dtype=torch.float32, device=X.device)
+    o = _opts(TP_OP_SKETCH_SPECTRUM, (n1, n2, n3, l), TP_FP32, status)
+    rc = lib().tp_sketch_spectrum(_tensor_arg(X, "X"), n1, n2, n3, int(l), int(q), int(seed),
+                                  _tensor_arg(sig, "sig"), ctypes.byref(o), _stream())
+    _check(rc, "tp_sketch_spectrum")
+    return sig
+
+
+def rank_rule(sig, cap, tol=1e-2):
+    """Per-frequency ranks (int32 device tensor) from (h, l) spectra."""
+    torch = _torch()
+    h, l = sig.shape
+    out = torch.empty(h, dtype=torch.int32, device=sig.device)
+    rc = lib().tp_rank_rule(_tensor_arg(sig, "sig"), h, l, int(cap), float(tol),
+                            _tensor_arg(out, "rank", torch.int32), _stream())
+    _check(rc, "tp_rank_rule")
+    return out
+
+
+def rank_features(sig):
+    """(h, 16) float16 predictor features from (h, >= 17) spectra."""
+    torch = _torch()
+    h, l = sig.shape
+    out = torch.empty((h, 16), dtype=torch.float16, device=sig.device)
+    rc = lib().tp_rank_features(_tensor_arg(sig, "sig"), h, l,
+                                _tensor_arg(out, "features", torch.float16), _stream())
+    _check(rc, "tp_rank_features")
+    return out
+
+
+def mlp_param_count():
+    return int(lib().tp_mlp_param_count())
+
+
+def mlp_round(theta, w16=None):
+    """float16 copy of the float32 master parameters."""
+    torch = _torch()
+    if w16 is None:
+        w16 = torch.empty(theta.shape, dtype=torch.float16, device=theta.device)
+    rc = lib().tp_mlp_round(_tensor_arg(theta, "theta"), _tensor_arg(w16, "w16", torch.float16),
+                            _stream())
+    _check(rc, "tp_mlp_round")
+    return w16
+
+
+def mlp_forward(w16, x16):
+    torch = _torch()
+    B = x16.shape[0]
+    y = torch.empty((B, 2), dtype=torch.float32, device=x16.device)
+    rc = lib().tp_mlp_forward(_tensor_arg(w16, "w16", torch.float16),
+                              _tensor_arg(x16, "x", torch.float16), B, _tensor_arg(y, "y"),
+                              _stream())
+    _check(rc, "tp_mlp_forward")
+    return y
+
+
+def mlp_train_step(theta, w16, m, v, step, lr, x16, target, grad=None):
+    """Gradient and loss at w16 on the batch (returned: float32 tensor of
+    param_count + 1, the last the loss), then one Adam step if lr > 0."""
+    torch = _torch()
+    B = x16.shape[0]
+    if grad is None:
+        grad = torch.empty(mlp_param_count() + 1, dtype=torch.float32, device=x16.device)
+    o = _opts(TP_OP_MLP_TRAIN, (B,))
+    rc = lib().tp_mlp_train_step(_tensor_arg(theta, "theta"), _tensor_arg(w16, "w16", torch.float16),
+                                 _tensor_arg(m, "m"), _tensor_arg(v, "v"), int(step), float(lr),
+                                 _tensor_arg(x16, "x", torch.float16), _tensor_arg(target, "target"),
+                                 B, _tensor_arg(grad, "grad"), ctypes.byref(o), _stream())
+    _check(rc, "tp_mlp_train_step")
+    return grad
 
 
 def tcx(A, c, seed=0, prob_mode=TP_PROB_A2, p_given=None, status=None):

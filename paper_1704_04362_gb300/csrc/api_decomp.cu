@@ -7,6 +7,7 @@ bool fft_supported(int64_t n3);
 size_t rsvd_ws(int64_t n1, int64_t n2, int64_t n3, int64_t k, int64_t p);
 size_t svt_ws(int64_t n1, int64_t n2, int64_t n3);
 size_t svt_batched_ws_dims(const int64_t* dims, int nd);
+size_t mlp_ws(int64_t B);
 int svt_batched_run(int ntens, const tp_tensor_desc* d, int iters, double rho, double mu_max,
                     const tp_opts* opts, cudaStream_t st);
 int svt_run(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t n3, int iters,
@@ -17,7 +18,8 @@ int tcx_run(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, uint6
             int prob_mode, const double* p_given, float* Z, int32_t* idx_out, int64_t* count_out,
             const tp_opts* opts, cudaStream_t st);
 int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, int q,
-             uint64_t seed, float* U, float* S, float* V, const tp_opts* opts, cudaStream_t st);
+             uint64_t seed, float* U, float* S, float* V, const tp_opts* opts, cudaStream_t st,
+             float* sig_out);
 int tsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, float* U, float* S, float* V,
              const tp_opts* opts, cudaStream_t st);
 
@@ -27,6 +29,8 @@ size_t workspace_for(int op, const int64_t* d, int nd) {
     case TP_OP_TSVD_RANDOMIZED: return nd >= 5 ? rsvd_ws(d[0], d[1], d[2], d[3], d[4]) : 0;
     case TP_OP_TCOMPLETE_SVT: return nd >= 3 ? svt_ws(d[0], d[1], d[2]) : 0;
     case TP_OP_TCOMPLETE_SVT_BATCHED: return nd >= 3 ? svt_batched_ws_dims(d, nd) : 0;
+    case TP_OP_SKETCH_SPECTRUM: return nd >= 4 ? rsvd_ws(d[0], d[1], d[2], d[3], 0) : 0;
+    case TP_OP_MLP_TRAIN: return nd >= 1 ? mlp_ws(d[0]) : 0;
     case TP_OP_TCX: return nd >= 3 ? tcx_ws(d[0], d[1], d[2]) : 0;
     default: return 0;
   }
@@ -69,7 +73,7 @@ int tsvd_randomized(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, i
     set_error("tsvd_randomized: n3 = %lld > 512 must factor into radices 2..13", (long long)n3);
     return TP_EUNSUPPORTED;
   }
-  return rsvd_run(X, n1, n2, n3, k, p, q, seed, U, S, V, opts, as_stream(stream));
+  return rsvd_run(X, n1, n2, n3, k, p, q, seed, U, S, V, opts, as_stream(stream), nullptr);
 }
 int tcomplete_svt(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t n3,
                   int iters, double rho, double mu_max, float* L, float* E, float* Y, double* mu,

@@ -647,8 +647,22 @@ size_t rsvd_ws(int64_t n1, int64_t n2, int64_t n3, int64_t k, int64_t p) {
          + 2 * ws_bytes(size_t(n2) * k * h, 4); // V_hat
 }
 
+namespace {
+// Diagonal of every k x k half-spectrum slice of S: sig[f * k + j] = S_f(j, j).
+__global__ void diag_kernel(const float* __restrict__ sr, int k, int64_t h, float* __restrict__ sig) {
+  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= h * k) return;
+  const int64_t f = e / k;
+  const int j = int(e - f * k);
+  sig[e] = sr[f * k * k + j * (k + 1)];
+}
+}  // namespace
+
+// sig_out non-null: only the core singular values of every frequency are
+// wanted (descending, h x k, float32); U, S, V are not formed.
 int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, int q,
-             uint64_t seed, float* U, float* S, float* V, const tp_opts* opts, cudaStream_t st) {
+             uint64_t seed, float* U, float* S, float* V, const tp_opts* opts, cudaStream_t st,
+             float* sig_out) {
   const int64_t h = half_len(n3);
   const int64_t l = k + p;
   Arena ws;
@@ -758,6 +772,13 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
         Gr, Gi, n2 * l, Wr, Wi, l * l, sig, int(n2), int(l), k, Wkr, Wki, Vr, Vi, Sr, Si);
   }
   if ((rc = launch_status("pick_topk_kernel"))) return rc;
+  }
+  if (sig_out) {
+    {
+      KernelScope ks("sketch_spectrum", st);
+      diag_kernel<<<unsigned((h * k + 255) / 256), 256, 0, st>>>(Sr, k, h, sig_out);
+    }
+    return launch_status("diag_kernel");
   }
   if ((rc = gemm(Yr, Yi, n1, l, Wkr, Wki, k, Ur, Ui))) return rc;    // U_hat = Q W_k
   if ((rc = launch_irdft(Ur, Ui, n1 * k, n1 * k, n3, U, st))) return rc;
