@@ -130,3 +130,36 @@ def lowrank_torch(n1, n2, n3, r, seed, noise=0.0, device="cuda", chunk=8):
         out.add_(z, alpha=noise * rms)
         del z
     return out
+
+
+def spectral_torch(n1, n2, n3, alpha, jitter, seed, device="cuda"):
+    """Tensor with a prescribed spectrum at every Fourier frequency (the
+    rank-predictor workload): X_hat_k = U_k diag(s_k) V_k^H with Haar-like
+    unitary factors (QR of complex Gaussians; real orthogonal at the real
+    frequencies k = 0 and, n3 even, k = n3/2) and s_{k,i} = i^(-a_k),
+    a_k = alpha + jitter * u_k, u_k uniform in [-1, 1].  The transform back
+    is torch.fft.irfft (the conjugate half is implied).  Returns the
+    column-major real tensor and the exact spectra (h x min(n1, n2),
+    float64, of X_hat_k as formed by the unnormalised forward transform)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    h, m = n3 // 2 + 1, min(n1, n2)
+    a = alpha + jitter * (2.0 * torch.rand(h, generator=g, device=device, dtype=torch.float64) - 1.0)
+    i = torch.arange(1, m + 1, device=device, dtype=torch.float64)
+    s = i[None, :] ** (-a[:, None])                                     # h x m
+    def factor(rows):
+        re = torch.randn((h, rows, m), generator=g, device=device, dtype=torch.float64)
+        im = torch.randn((h, rows, m), generator=g, device=device, dtype=torch.float64)
+        im[0] = 0.0
+        if n3 % 2 == 0:
+            im[h - 1] = 0.0
+        q, r = torch.linalg.qr(torch.complex(re, im))
+        d = torch.diagonal(r, dim1=-2, dim2=-1)
+        return q * (d / d.abs().clamp_min(1e-300)).conj()[:, None, :]   # unique phases
+    U, V = factor(n1), factor(n2)
+    Xh = (U * s[:, None, :].to(U.dtype)) @ V.conj().transpose(-1, -2)   # h x n1 x n2
+    X = torch.fft.irfft(Xh, n=n3, dim=0)                                # n3 x n1 x n2, real
+    out = fortran_empty_torch(n1, n2, n3, device=device)
+    out.copy_(X.permute(1, 2, 0))
+    return out, s
