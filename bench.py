@@ -273,6 +273,51 @@ def bench_svt_batched(tp, torch, count=256, warm_iters=3):
                     "tensors (8 side streams)"}
 
 
+def bench_learned(torch, train_count=192, eval_shape=(1024, 1024, 64),
+                  alphas=(1.5, 2.0, 2.5, 3.0, 3.5, 4.0)):
+    """The learned sketch-size predictor against the plain adaptive method
+    (rank rule on a 50-column sketch, q = 2) on tensors shaped like the
+    1024 x 1024 x n3 rank-predictor workload with per-frequency spectra
+    i^(-a_k) (a_k = alpha +- 0.3).  Both methods' per-frequency ranks come
+    from a sketch's spectrum and the plain rule; the learned one chooses the
+    sketch size from a 17-column sketch, is judged by the rule and falls
+    back to 50 columns when a rank reaches its cap.  Times cover the whole
+    rank pipeline of each (the learned one includes its cheap pass, the
+    network and any fallback); errors are the exact relative truncation
+    errors from the known spectra."""
+    from paper_1704_04362_gb300 import predictor as P
+    from paper_1704_04362_gb300 import synth
+    t0 = time.perf_counter()
+    x, t = P.training_set(train_count, seed0=100)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, w16, losses = P.train(x, t, steps=3000, lr=2e-3, seed=1)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    n1, n2, n3 = eval_shape
+    cases = []
+    for i, a in enumerate(alphas):
+        X, spec = synth.spectral_torch(n1, n2, n3, a, 0.3, 77000 + i)
+        r_p, _, _ = P.decompose(X, None, seed=i)
+        r_l, l, fb = P.decompose(X, w16, seed=i)
+        ms_p = P.time_call(lambda: P.decompose(X, None, seed=i))
+        ms_l = P.time_call(lambda: P.decompose(X, w16, seed=i))
+        cases.append({"alpha": a, "sketch_columns": l, "fell_back": bool(fb),
+                      "plain_ms": ms_p, "learned_ms": ms_l, "speedup": ms_p / ms_l,
+                      "plain_error": P.truncation_error(spec, r_p, n3),
+                      "learned_error": P.truncation_error(spec, r_l, n3),
+                      "ranks_equal_fraction": float((r_p == r_l).float().mean().item())})
+        del X, spec
+    return {"workload": f"{n1}x{n2}x{n3} tensors, per-frequency spectra i^-a, a = alpha +- 0.3; "
+                        f"trained on {train_count} tensors of 128..160 x 96..128 x 16..32",
+            "training_samples": int(x.shape[0]), "data_s": t_data, "train_s": t_train,
+            "loss_first_last": [losses[0][1], losses[-1][1]],
+            "total_plain_ms": sum(c["plain_ms"] for c in cases),
+            "total_learned_ms": sum(c["learned_ms"] for c in cases),
+            "cases": cases}
+
+
 def bench_rsvd(args, tp, torch, with_cpu):
     """Randomized low-tubal-rank t-SVD on the mass-spectrometry-shaped
     workload (128 x 128 pixels x 2000 channels, Gamma factors at tubal rank
@@ -576,6 +621,7 @@ def main():
     if not args.no_rows and not args.small:
         rows = bench_rows(tp, torch, with_cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
         rows["completion_batched"] = bench_svt_batched(tp, torch)
+        rows["learned_rank"] = bench_learned(torch)
 
     if rank == 0:
         line = {
