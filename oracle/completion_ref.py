@@ -73,3 +73,43 @@ def tcomplete_svt(X, mask, iters: int, mu0=1e-3, rho=1.1, mu_max=1e10,
     for _ in range(iters):
         L, E, Y, mu = admm_step(Xo, obs, L, E, Y, mu, rho, mu_max)
     return L, E, Y, mu
+
+
+# ---------------------------------------------------------------- robust form
+# Algorithm 7 as printed, for problem (tlow7): minimise ||L||_TNN + lambda ||E||_1
+# subject to X = L + E.  The E-step's closed form is the entrywise soft
+# threshold of X - L - Y/mu at lambda/mu (the proximal map of lambda ||.||_1
+# with weight 1/mu).  The paper leaves lambda open; the default is Lu et al.'s
+# 1 / sqrt(max(n1, n2) n3).
+
+def default_lambda(n1: int, n2: int, n3: int) -> float:
+    return 1.0 / np.sqrt(max(n1, n2) * n3)
+
+
+def soft_threshold(V: np.ndarray, t: float) -> np.ndarray:
+    return np.sign(V) * np.maximum(np.abs(V) - t, 0.0)
+
+
+def admm_robust_step(X, L, E, Y, mu, lam, rho=1.1, mu_max=1e10):
+    """One iteration of Algorithm 7 (tlow7).  Returns (L, E, Y, mu_next)."""
+    L = svt_tensor(X - E - Y / mu, 1.0 / mu)
+    E = soft_threshold(X - L - Y / mu, lam / mu)
+    Y = Y + mu * (L + E - X)
+    return L, E, Y, min(rho * mu, mu_max)
+
+
+def trpca(X, iters: int, lam=None, mu0=1e-3, rho=1.1, mu_max=1e10, state=None):
+    """Run ``iters`` iterations of Algorithm 7 from (L, E, Y, mu) = state or
+    zeros/mu0.  Returns (L, E, Y, mu)."""
+    X = np.asarray(X, dtype=np.float64)
+    n1, n2, n3 = X.shape
+    lam = default_lambda(n1, n2, n3) if lam is None else float(lam)
+    if state is None:
+        L, E, Y = np.zeros_like(X), np.zeros_like(X), np.zeros_like(X)
+        mu = float(mu0)
+    else:
+        L, E, Y = (np.array(s, dtype=np.float64) for s in state[:3])
+        mu = float(state[3])
+    for _ in range(iters):
+        L, E, Y, mu = admm_robust_step(X, L, E, Y, mu, lam, rho, mu_max)
+    return L, E, Y, mu

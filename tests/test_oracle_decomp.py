@@ -185,3 +185,38 @@ def test_admm_resume_equals_continuous_run():
     b = Cm.tcomplete_svt(X, mask, iters=6, state=b)
     for x, y in zip(a[:3], b[:3]):
         np.testing.assert_allclose(x, y, atol=1e-12)
+
+
+def test_soft_threshold_is_prox_of_l1():
+    # argmin_E lam |E|_1 + 1/2 |E - V|^2: no perturbation does better
+    from oracle import completion_ref as C
+    g = np.random.default_rng(31)
+    V = g.standard_normal((4, 5, 3))
+    lam = 0.4
+    E = C.soft_threshold(V, lam)
+    f = lambda Z: lam * np.abs(Z).sum() + 0.5 * np.sum((Z - V) ** 2)
+    for s in range(20):
+        assert f(E) <= f(E + 1e-3 * g.standard_normal(V.shape)) + 1e-12
+    np.testing.assert_array_equal(C.soft_threshold(np.array([-2.0, -0.3, 0.0, 0.5, 1.5]), 0.5),
+                                  [-1.5, 0.0, 0.0, 0.0, 1.0])
+
+
+def test_robust_admm_recovers_low_rank_plus_sparse():
+    # Algorithm 7 on X = L0 + S0, S0 5% large spikes: L is recovered
+    from oracle import completion_ref as C
+    from paper_1704_04362_gb300 import synth
+    L0 = synth.lowrank_np(30, 30, 6, 2, seed=41).astype(np.float64)
+    L0 /= np.sqrt(np.mean(L0 ** 2))
+    g = np.random.default_rng(42)
+    S0 = np.where(g.random(L0.shape) < 0.05, 10.0 * g.standard_normal(L0.shape), 0.0)
+    L, E, Y, mu = C.trpca(L0 + S0, 120)
+    assert np.linalg.norm(L - L0) / np.linalg.norm(L0) < 1e-3
+    assert np.linalg.norm(E - S0) / np.linalg.norm(S0) < 1e-3
+
+
+def test_robust_admm_with_huge_lambda_keeps_e_zero():
+    # lambda large: the soft threshold kills E, the iteration is SVT of X - Y/mu
+    from oracle import completion_ref as C
+    X = np.random.default_rng(43).standard_normal((6, 5, 4))
+    L, E, Y, mu = C.trpca(X, 5, lam=1e12)
+    assert np.all(E == 0.0)
