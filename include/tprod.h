@@ -95,7 +95,8 @@ typedef enum {
   TP_OP_TCX = 7,             /* dims: n1, n2, n3 */
   TP_OP_TCOMPLETE_SVT_BATCHED = 8, /* dims: n1, n2, n3 of every tensor (nd = 3 ntens) */
   TP_OP_SKETCH_SPECTRUM = 9,        /* dims: n1, n2, n3, l */
-  TP_OP_MLP_TRAIN = 10              /* dims: batch */
+  TP_OP_MLP_TRAIN = 10,             /* dims: batch */
+  TP_OP_TRPCA = 11                  /* dims: n1, n2, n3 */
 } tp_op;
 
 /* ---------------------------------------------------------------- t-product
@@ -193,6 +194,19 @@ int tcomplete_svt(const float* X, const uint8_t* mask,
                   double rho, double mu_max,
                   float* L, float* E, float* Y, double* mu,
                   const tp_opts* opts, void* stream);
+
+/* trpca_admm: `iters` iterations of Algorithm 7 as printed, for the robust
+ * problem (tlow7): minimise ||L||_TNN + lambda ||E||_1 subject to X = L + E.
+ * Per iteration, with tau = 1/mu:
+ *   L <- SVT_tau(X - E - Y/mu)
+ *   E <- soft(X - L - Y/mu, lambda/mu)   (sign(v) max(|v| - lambda/mu, 0))
+ *   Y <- Y + mu (L + E - X);    mu <- min(rho mu, mu_max)
+ * lambda <= 0 takes 1/sqrt(max(n1, n2) n3) (the paper leaves it open; Lu et
+ * al.'s choice).  State (L, E, Y, *mu) as tcomplete_svt; same SVT, limits
+ * and workspace (TP_OP_TRPCA).                                              */
+int trpca_admm(const float* X, int64_t n1, int64_t n2, int64_t n3, int iters, double lambda,
+               double rho, double mu_max, float* L, float* E, float* Y, double* mu,
+               const tp_opts* opts, void* stream);
 
 /* One tensor of a batched completion: X and mask are read; L, E, Y and *mu
  * (device float64) are the state, read and updated as in tcomplete_svt.  All

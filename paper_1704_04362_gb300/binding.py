@@ -23,14 +23,14 @@ __all__ = [
     "rdft3", "irdft3", "slice_norms", "sample_draw", "launch_count", "exported_symbols",
     "profile_start", "profile_stop", "slice_norms_noalloc", "tcomplete_svt_batched",
     "sketch_spectrum", "rank_rule", "rank_features", "mlp_param_count", "mlp_round",
-    "mlp_forward", "mlp_train_step",
+    "mlp_forward", "mlp_train_step", "trpca_admm",
 ]
 
 TP_FP32, TP_TF32X3, TP_BF16X3 = 0, 1, 2
 TP_PROB_AB, TP_PROB_A2, TP_PROB_GIVEN = 0, 1, 2
 TP_OP_TPROD, TP_OP_TPROD_SAMPLED, TP_OP_TSVD, TP_OP_TSVD_RANDOMIZED, TP_OP_TCOMPLETE_SVT, \
     TP_OP_SLICE_NORMS, TP_OP_TCX, TP_OP_TCOMPLETE_SVT_BATCHED, TP_OP_SKETCH_SPECTRUM, \
-    TP_OP_MLP_TRAIN = 1, 2, 3, 4, 5, 6, 7, 8, 9, 10
+    TP_OP_MLP_TRAIN, TP_OP_TRPCA = 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _c_i64, _c_u64, _c_int, _c_u32 = ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32
@@ -66,6 +66,8 @@ _SIGS = {
     "tcx": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_i64, _c_u64, _c_int, _vp, _vp, _vp, _vp,
                      _vp, _vp]),
     "tcomplete_svt_batched": (_c_int, [_c_int, _vp, _c_int, _dbl, _dbl, _vp, _vp]),
+    "trpca_admm": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_int, _dbl, _dbl, _dbl, _vp, _vp, _vp,
+                            _vp, _vp, _vp]),
     "tp_sketch_spectrum": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_int, _c_int, _c_u64, _vp,
                                     _vp, _vp]),
     "tp_rank_rule": (_c_int, [_vp, _c_i64, _c_int, _c_int, _dbl, _vp, _vp]),
@@ -336,6 +338,27 @@ def tcomplete_svt(X, mask, iters, L=None, E=None, Y=None, mu=None, mu0=1e-3, rho
                              _tensor_arg(L, "L"), _tensor_arg(E, "E"), _tensor_arg(Y, "Y"),
                              _tensor_arg(mu, "mu", torch.float64), ctypes.byref(o), _stream())
     _check(rc, "tcomplete_svt")
+    return L, E, Y, mu
+
+
+def trpca_admm(X, iters, lam=0.0, L=None, E=None, Y=None, mu=None, mu0=1e-3, rho=1.1,
+               mu_max=1e10, status=None, max_sweeps=0):
+    """Robust TNN (Algorithm 7, problem tlow7); lam <= 0 takes the default
+    1/sqrt(max(n1, n2) n3).  State (L, E, Y, mu) updated in place and returned."""
+    torch = _torch()
+    n1, n2, n3 = X.shape
+    if L is None:
+        L = torch.zeros_like(X)
+        E = torch.zeros_like(X)
+        Y = torch.zeros_like(X)
+    if mu is None:
+        mu = torch.full((1,), float(mu0), dtype=torch.float64, device=X.device)
+    o = _opts(TP_OP_TRPCA, (n1, n2, n3), TP_FP32, status, max_sweeps)
+    rc = lib().trpca_admm(_tensor_arg(X, "X"), n1, n2, n3, int(iters), float(lam), float(rho),
+                          float(mu_max), _tensor_arg(L, "L"), _tensor_arg(E, "E"),
+                          _tensor_arg(Y, "Y"), _tensor_arg(mu, "mu", torch.float64),
+                          ctypes.byref(o), _stream())
+    _check(rc, "trpca_admm")
     return L, E, Y, mu
 
 

@@ -1,4 +1,6 @@
 // C entry points of the decomposition paths (filled in by later kernels).
+#include <cmath>
+
 #include "tp_internal.cuh"
 
 namespace tp {
@@ -12,7 +14,7 @@ int svt_batched_run(int ntens, const tp_tensor_desc* d, int iters, double rho, d
                     const tp_opts* opts, cudaStream_t st);
 int svt_run(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t n3, int iters,
             double rho, double mu_max, float* L, float* E, float* Y, double* mu,
-            const tp_opts* opts, cudaStream_t st);
+            const tp_opts* opts, cudaStream_t st, double lam);
 size_t tcx_ws(int64_t n1, int64_t n2, int64_t n3);
 int tcx_run(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, uint64_t seed,
             int prob_mode, const double* p_given, float* Z, int32_t* idx_out, int64_t* count_out,
@@ -27,7 +29,8 @@ size_t workspace_for(int op, const int64_t* d, int nd) {
   switch (op) {
     case TP_OP_TSVD: return nd >= 3 ? tsvd_ws(d[0], d[1], d[2]) : 0;
     case TP_OP_TSVD_RANDOMIZED: return nd >= 5 ? rsvd_ws(d[0], d[1], d[2], d[3], d[4]) : 0;
-    case TP_OP_TCOMPLETE_SVT: return nd >= 3 ? svt_ws(d[0], d[1], d[2]) : 0;
+    case TP_OP_TCOMPLETE_SVT:
+    case TP_OP_TRPCA: return nd >= 3 ? svt_ws(d[0], d[1], d[2]) : 0;
     case TP_OP_TCOMPLETE_SVT_BATCHED: return nd >= 3 ? svt_batched_ws_dims(d, nd) : 0;
     case TP_OP_SKETCH_SPECTRUM: return nd >= 4 ? rsvd_ws(d[0], d[1], d[2], d[3], 0) : 0;
     case TP_OP_MLP_TRAIN: return nd >= 1 ? mlp_ws(d[0]) : 0;
@@ -89,7 +92,26 @@ int tcomplete_svt(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, i
     set_error("tcomplete_svt: n3 > 512 must factor into radices 2..13");
     return TP_EUNSUPPORTED;
   }
-  return svt_run(X, mask, n1, n2, n3, iters, rho, mu_max, L, E, Y, mu, opts, as_stream(stream));
+  return svt_run(X, mask, n1, n2, n3, iters, rho, mu_max, L, E, Y, mu, opts, as_stream(stream),
+                 0.0);
+}
+
+int trpca_admm(const float* X, int64_t n1, int64_t n2, int64_t n3, int iters, double lambda,
+               double rho, double mu_max, float* L, float* E, float* Y, double* mu,
+               const tp_opts* opts, void* stream) {
+  if (!X || !L || !E || !Y || !mu) { set_error("trpca_admm: NULL pointer"); return TP_ENULL; }
+  if (!dims3_ok(n1, n2, n3) || iters < 0 || !(rho > 0.0) || !(mu_max > 0.0) || lambda < 0.0) {
+    set_error("trpca_admm: invalid sizes or constants");
+    return TP_EINVAL;
+  }
+  if ((n1 < n2 ? n1 : n2) > 512) { set_error("trpca_admm: min(n1, n2) > 512 not supported"); return TP_EUNSUPPORTED; }
+  if (n3 > 512 && !fft_supported(n3)) {
+    set_error("trpca_admm: n3 > 512 must factor into radices 2..13");
+    return TP_EUNSUPPORTED;
+  }
+  const double lam = lambda > 0.0 ? lambda : 1.0 / sqrt(double(n1 > n2 ? n1 : n2) * double(n3));
+  return svt_run(X, nullptr, n1, n2, n3, iters, rho, mu_max, L, E, Y, mu, opts, as_stream(stream),
+                 lam);
 }
 
 int tcomplete_svt_batched(int ntens, const tp_tensor_desc* descs, int iters, double rho,

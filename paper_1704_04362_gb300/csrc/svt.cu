@@ -1,5 +1,7 @@
-// Tensor completion by ADMM with tensor singular-value thresholding
-// (Algorithm 7 in the completion form of problem (tlow6)).  Per iteration,
+// ADMM with tensor singular-value thresholding: Algorithm 7 as printed
+// (robust TNN, problem tlow7: E-step = entrywise soft threshold of
+// X - L - Y/mu at lambda/mu, every entry observed) and its completion form
+// (problem tlow6, below).  Per iteration of the completion form,
 // with tau = 1/mu (mu held on the device):
 //   M = X_obs - E - Y/mu                         (admm_pre_kernel)
 //   L = ifft(SVT_tau(fft(M)))                     (half spectrum, per slice)
@@ -37,23 +39,34 @@ __global__ void admm_pre_kernel(const float* __restrict__ X, const uint8_t* __re
   const float inv_mu = float(1.0 / *mu);
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n;
        e += int64_t(gridDim.x) * blockDim.x) {
-    const float x = mask[e] ? X[e] : 0.f;
+    const float x = (mask == nullptr || mask[e]) ? X[e] : 0.f;   // robust form: no mask
     M[e] = x - E[e] - Y[e] * inv_mu;
   }
 }
 
+// E and Y updates.  lam > 0: robust form, E = soft(X - L - Y/mu, lam/mu) on
+// every entry; else completion form, E = X_obs - L - Y/mu off the mask, 0 on it.
 __global__ void admm_post_kernel(const float* __restrict__ X, const uint8_t* __restrict__ mask,
                                  const float* __restrict__ L, float* __restrict__ E,
-                                 float* __restrict__ Y, const double* __restrict__ mu, int64_t n) {
+                                 float* __restrict__ Y, const double* __restrict__ mu, int64_t n,
+                                 double lam) {
   const float m = float(*mu);
   const float inv_mu = float(1.0 / *mu);
+  const float thr = float(lam / *mu);
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n;
        e += int64_t(gridDim.x) * blockDim.x) {
-    const bool obs = mask[e] != 0;
-    const float x = obs ? X[e] : 0.f;
     const float y = Y[e];
     const float l = L[e];
-    const float enew = obs ? 0.f : (x - l - y * inv_mu);
+    float x, enew;
+    if (lam > 0.0) {
+      x = X[e];
+      const float v = x - l - y * inv_mu;
+      enew = copysignf(fmaxf(fabsf(v) - thr, 0.f), v);
+    } else {
+      const bool obs = mask[e] != 0;
+      x = obs ? X[e] : 0.f;
+      enew = obs ? 0.f : (x - l - y * inv_mu);
+    }
     E[e] = enew;
     Y[e] = y + m * (l + enew - x);
   }
@@ -172,6 +185,7 @@ struct SvtTensor {
   const uint8_t* mask;
   float *L, *E, *Y;
   double* mu;
+  double lam;   // > 0: robust form (no mask), else completion form
   int64_t n1, n2, n3, h, p, q;
   bool transpose;
   float *M, *Mr, *Mi, *Gr, *Gi, *Vr, *Vi, *Kr, *Ki, *Hr, *Hi, *sig;
@@ -261,7 +275,7 @@ int svt_iteration(const SvtTensor& t, bool warm, double rho, double mu_max, int 
   if ((rc = launch_irdft(t.Mr, t.Mi, n12, n12, t.n3, t.L, st))) return rc;
   {
     KernelScope ks("admm_post", st);
-    admm_post_kernel<<<grid_n(n), 256, 0, st>>>(t.X, t.mask, t.L, t.E, t.Y, t.mu, n);
+    admm_post_kernel<<<grid_n(n), 256, 0, st>>>(t.X, t.mask, t.L, t.E, t.Y, t.mu, n, t.lam);
   }
   {
     KernelScope ks("admm_mu", st);
@@ -270,15 +284,17 @@ int svt_iteration(const SvtTensor& t, bool warm, double rho, double mu_max, int 
   return launch_status("admm iteration");
 }
 
+// mask null and lam > 0: the robust form; else the completion form.
 int svt_run(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t n3, int iters,
             double rho, double mu_max, float* L, float* E, float* Y, double* mu,
-            const tp_opts* opts, cudaStream_t st) {
+            const tp_opts* opts, cudaStream_t st, double lam) {
   Arena ws;
   int rc = acquire_workspace(opts, svt_ws(n1, n2, n3), &ws);
   if (rc) return rc;
   int32_t* status = opts ? opts->status : nullptr;
   const int sweeps = (opts && opts->max_sweeps > 0) ? opts->max_sweeps : 30;
-  const SvtTensor t = svt_carve(X, mask, n1, n2, n3, L, E, Y, mu, ws);
+  SvtTensor t = svt_carve(X, mask, n1, n2, n3, L, E, Y, mu, ws);
+  t.lam = lam;
   if ((rc = svt_init(t, st))) return rc;
   for (int it = 0; it < iters; ++it)
     if ((rc = svt_iteration(t, it > 0, rho, mu_max, sweeps, status, st))) return rc;

@@ -124,3 +124,40 @@ def test_batched_equals_separate_calls_and_oracle():
     Lr, _, _, mur = completion_ref.tcomplete_svt(X.astype(np.float64), mask, iters)
     assert rel_fro(to_np(batch[0][2]), Lr) < 1e-4
     assert abs(float(batch[0][5].item()) / mur - 1) < 1e-12
+
+
+def test_robust_form_one_iteration_matches_oracle():
+    """Algorithm 7 as printed (problem tlow7): the E-step soft-thresholds every
+    entry at lambda/mu."""
+    import torch
+    g = np.random.default_rng(50)
+    X = synth.lowrank_np(22, 18, 6, 3, seed=51, noise=0.01)
+    X = (X / np.sqrt(np.mean(X.astype(np.float64) ** 2))).astype(np.float32)
+    E = (0.3 * g.standard_normal(X.shape)).astype(np.float32)
+    Y = (0.1 * g.standard_normal(X.shape)).astype(np.float32)
+    mu, lam = 0.08, 0.15
+    Ld, Ed, Yd = dev(np.zeros_like(X)), dev(E), dev(Y)
+    mud = torch.tensor([mu], dtype=torch.float64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    tp.trpca_admm(dev(X), 1, lam=lam, L=Ld, E=Ed, Y=Yd, mu=mud, status=st)
+    assert int(st.item()) == 0
+    Lr, Er, Yr, mur = completion_ref.admm_robust_step(X.astype(np.float64), 0.0, E.astype(np.float64),
+                                                      Y.astype(np.float64), mu, lam)
+    assert rel_fro(to_np(Ld), Lr) < TOL_FP32
+    assert rel_fro(to_np(Ed), Er) < TOL_FP32
+    assert rel_fro(to_np(Yd), Yr) < TOL_FP32
+    assert abs(float(mud.item()) - mur) <= 1e-15 * mur
+
+
+def test_robust_form_recovers_low_rank_plus_sparse_and_tracks_oracle():
+    L0 = synth.lowrank_np(30, 30, 6, 2, seed=41).astype(np.float64)
+    L0 /= np.sqrt(np.mean(L0 ** 2))
+    g = np.random.default_rng(42)
+    S0 = np.where(g.random(L0.shape) < 0.05, 10.0 * g.standard_normal(L0.shape), 0.0)
+    X = (L0 + S0).astype(np.float32)
+    L, E, Y, mu = tp.trpca_admm(dev(X), 60)
+    Lr, Er, Yr, mur = completion_ref.trpca(X.astype(np.float64), 60)
+    assert rel_fro(to_np(L), Lr) < 1e-4                 # float32 state over 60 iterations
+    assert abs(float(mu.item()) / mur - 1) < 1e-12
+    L2, E2, _, _ = tp.trpca_admm(dev(X), 120)
+    assert rel_fro(to_np(L2), L0) < 1e-3 and rel_fro(to_np(E2), S0) < 1e-3
