@@ -10,6 +10,8 @@ tsvd_randomized Randomized low-tubal-rank t-SVD: per Fourier slice the
                 passed in.  The paper names randomized approximations
                 (Section 5.2) without fixing one; this is the reading used.
 tproject, tcx   Algorithm 3 (t-project) and Algorithm 4 (t-CX).
+tcur            Algorithm 5 (t-CUR) with the row leverage probabilities of
+                eq. (colprob_rows_exact).
 """
 from __future__ import annotations
 
@@ -155,3 +157,56 @@ def tcx(A: np.ndarray, c: int, seed: int, mode: int = sampling_ref.PROB_A2,
         return np.zeros_like(A), idx, q
     C = A[:, idx, :] / np.sqrt(q[idx])[None, :, None]
     return tproject(A, C), idx, q
+
+
+def row_leverage(C: np.ndarray) -> np.ndarray:
+    """Horizontal-slice probabilities of Algorithm 5 (eq. colprob_rows_exact,
+    beta = 1): p_i proportional to ||U_hat_{i::}||_F^2, U_hat_k the left
+    singular vectors of every Fourier slice C_hat_k (all n3 frequencies) whose
+    singular values pass MATLAB's pinv cut-off max(n1, c) eps(s_max);
+    normalised to sum 1."""
+    C = np.asarray(C, dtype=np.float64)
+    n1, c, n3 = C.shape
+    Ch = fft3(C)
+    lev = np.zeros(n1)
+    for f in range(n3):
+        u, sv, _ = np.linalg.svd(Ch[:, :, f], full_matrices=False)
+        if sv.size == 0 or sv[0] == 0:
+            continue
+        keep = sv > max(n1, c) * np.spacing(sv[0])
+        lev += np.sum(np.abs(u[:, keep]) ** 2, axis=1)
+    tot = lev.sum()
+    return lev / tot if tot > 0 else lev
+
+
+def tcur(A: np.ndarray, c: int, l: int, seed: int, mode: int = sampling_ref.PROB_A2,
+         p_cols: np.ndarray | None = None, p_rows: np.ndarray | None = None):
+    """t-CUR, Algorithm 5: lateral slices as t-CX (Philox stream 0), horizontal
+    slices with probability min{1, l p_i} (stream 1; p_i the row leverage of
+    C unless given), R_hat_k = D S^T A_hat_k, U_hat_k = (D S^T C_hat_k)^dagger,
+    Z_hat_k = C_hat_k U_hat_k R_hat_k.  Returns (Z, col_idx, row_idx, p_rows)."""
+    from .philox_ref import STREAM_HORIZONTAL
+    A = np.asarray(A, dtype=np.float64)
+    n1, n2, n3 = A.shape
+    if mode == sampling_ref.PROB_GIVEN:
+        p = np.asarray(p_cols, dtype=np.float64)
+    else:
+        p = sampling_ref.probabilities(sampling_ref.lateral_norms_sq(A), None,
+                                       sampling_ref.PROB_A2)
+    cidx, qc = sampling_ref.draw(p, c, seed)
+    if len(cidx) == 0:
+        return np.zeros_like(A), cidx, np.zeros(0, dtype=cidx.dtype), np.zeros(n1)
+    C = A[:, cidx, :] / np.sqrt(qc[cidx])[None, :, None]
+    pr = row_leverage(C) if p_rows is None else np.asarray(p_rows, dtype=np.float64)
+    ridx, qr = sampling_ref.draw(pr, l, seed, STREAM_HORIZONTAL)
+    if len(ridx) == 0:
+        return np.zeros_like(A), cidx, ridx, pr
+    d = 1.0 / np.sqrt(qr[ridx])
+    Ah = fft3(A)
+    Ch = fft3(C)
+    Zh = np.empty_like(Ah)
+    for f in range(n3):
+        R = d[:, None] * Ah[ridx, :, f]
+        W = d[:, None] * Ch[ridx, :, f]
+        Zh[:, :, f] = Ch[:, :, f] @ (pinv_matlab(W) @ R)
+    return ifft3(Zh).real, cidx, ridx, pr

@@ -220,3 +220,55 @@ def test_robust_admm_with_huge_lambda_keeps_e_zero():
     X = np.random.default_rng(43).standard_normal((6, 5, 4))
     L, E, Y, mu = C.trpca(X, 5, lam=1e12)
     assert np.all(E == 0.0)
+
+
+def test_tcur_keeps_everything_when_every_slice_is_picked():
+    from oracle import decomp_ref as D
+    A = np.random.default_rng(61).standard_normal((8, 6, 4))
+    Z, ci, ri, _ = D.tcur(A, 10 ** 6, 10 ** 6, 3)
+    assert len(ci) == 6 and len(ri) == 8
+    np.testing.assert_allclose(Z, A, atol=1e-10)
+
+
+def test_tcur_reconstructs_low_tubal_rank_exactly():
+    from oracle import decomp_ref as D
+    from paper_1704_04362_gb300 import synth
+    A = synth.lowrank_np(20, 16, 5, 2, seed=62, dtype=np.float64)
+    Z, ci, ri, _ = D.tcur(A, 12, 14, 7)
+    assert len(ci) >= 2 and len(ri) >= 2
+    assert np.linalg.norm(Z - A) / np.linalg.norm(A) < 1e-9
+
+
+def test_tcur_with_n3_one_is_matrix_cur():
+    # Drineas et al.'s CUR: Z = C pinv(W) R with W the picked rows of C
+    from oracle import decomp_ref as D, sampling_ref as S, philox_ref as P
+    A = np.random.default_rng(63).standard_normal((12, 10, 1))
+    Z, ci, ri, pr = D.tcur(A, 6, 7, 11)
+    M = A[:, :, 0]
+    _, qc = S.draw(S.probabilities(S.lateral_norms_sq(A), None, S.PROB_A2), 6, 11)
+    C = M[:, ci] / np.sqrt(qc[ci])
+    qr = S.keep_probabilities(pr, 7)
+    W = C[ri, :] / np.sqrt(qr[ri])[:, None]
+    R = M[ri, :] / np.sqrt(qr[ri])[:, None]
+    np.testing.assert_allclose(Z[:, :, 0], C @ np.linalg.pinv(W) @ R, atol=1e-10)
+
+
+def test_row_leverage_of_an_orthonormal_basis_is_uniform():
+    from oracle import decomp_ref as D
+    Q, _ = np.linalg.qr(np.random.default_rng(64).standard_normal((9, 9)))
+    p = D.row_leverage(Q[:, :, None])                  # n3 = 1, full rank: U U^H = I
+    np.testing.assert_allclose(p, np.full(9, 1 / 9), atol=1e-12)
+
+
+def test_row_leverage_is_the_projector_diagonal_summed_over_frequencies():
+    # for C of full column rank in every slice, ||U_hat_k(i, :)||^2 is the
+    # i-th diagonal entry of the projector C_k (C_k^H C_k)^{-1} C_k^H: no SVD
+    from oracle import decomp_ref as D
+    C = np.random.default_rng(65).standard_normal((11, 4, 5))
+    Ch = np.fft.fft(C, axis=2)
+    lev = np.zeros(11)
+    for f in range(5):
+        M = Ch[:, :, f]
+        lev += np.real(np.diag(M @ np.linalg.solve(M.conj().T @ M, M.conj().T)))
+    np.testing.assert_allclose(D.row_leverage(C), lev / lev.sum(), atol=1e-12)
+    assert abs(lev.sum() - 4 * 5) < 1e-9                 # trace of a rank-4 projector, 5 times
