@@ -170,6 +170,7 @@ def bench_rows(tp, torch, with_cpu):
     with the float64 oracle timed beside it on the host cores:
       tsvd   t-SVD (Theorem 2.6) of the 64 x 48 x 16 iid N(0,1) tensor
       tcx    t-CX (Algorithm 4), 256 x 512 x 32 tubal rank 10 + 1% noise, c = 64
+      tcur   t-CUR (Algorithm 5), the same tensor, c = 64, l = 64, leverage rows
       svt    completion ADMM (Algorithm 7), one 144 x 256 x 80 video (tubal rank
              10, sigma 0.01, 50% observed; the paper's video shape), 10 iterations
       trpca  robust ADMM (Algorithm 7 as printed), 192 x 168 x 64, 30 iterations"""
@@ -183,6 +184,12 @@ def bench_rows(tp, torch, with_cpu):
     Ad = tp.as_tprod_layout(A)
     ms = time_gpu(lambda: tp.tcx(Ad, 64, seed=0), 10, torch)
     rows["tcx"] = {"workload": "256x512x32 tubal rank 10 + 1% noise, c = 64", "gpu_ms": ms}
+    ms = time_gpu(lambda: tp.tcur(Ad, 64, 64, seed=0), 10, torch)
+    Zc = tp.tcur(Ad, 64, 64, seed=0)[0]
+    Adn = torch.linalg.vector_norm(Ad)
+    rows["tcur"] = {"workload": "256x512x32 tubal rank 10 + 1% noise, c = 64, l = 64",
+                    "gpu_ms": ms,
+                    "relative_error": float(torch.linalg.vector_norm(Zc - Ad) / Adn)}
     truth, noisy, mask = synth.video_np(144, 256, 80, r=10, seed=0)
     Xv = tp.as_tprod_layout(noisy)
     Mv = tp.as_tprod_layout(mask, torch.uint8)
@@ -221,6 +228,9 @@ def bench_rows(tp, torch, with_cpu):
         t0 = time.perf_counter()
         decomp_ref.tcx(A.astype(np.float64), 64, 0)
         rows["tcx"]["oracle_ms"] = (time.perf_counter() - t0) * 1e3
+        t0 = time.perf_counter()
+        decomp_ref.tcur(A.astype(np.float64), 64, 64, 0)
+        rows["tcur"]["oracle_ms"] = (time.perf_counter() - t0) * 1e3
         t0 = time.perf_counter()
         completion_ref.tcomplete_svt(noisy.astype(np.float64), mask.astype(bool), 2)
         per_iter = (time.perf_counter() - t0) / 2

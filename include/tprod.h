@@ -96,7 +96,8 @@ typedef enum {
   TP_OP_TCOMPLETE_SVT_BATCHED = 8, /* dims: n1, n2, n3 of every tensor (nd = 3 ntens) */
   TP_OP_SKETCH_SPECTRUM = 9,        /* dims: n1, n2, n3, l */
   TP_OP_MLP_TRAIN = 10,             /* dims: batch */
-  TP_OP_TRPCA = 11                  /* dims: n1, n2, n3 */
+  TP_OP_TRPCA = 11,                 /* dims: n1, n2, n3 */
+  TP_OP_TCUR = 12                   /* dims: n1, n2, n3 */
 } tp_op;
 
 /* ---------------------------------------------------------------- t-product
@@ -168,6 +169,32 @@ int tsvd_randomized(const float* X, int64_t n1, int64_t n2, int64_t n3,
 int tcx(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, uint64_t seed,
         int prob_mode, const double* p_given, float* Z, int32_t* idx_out, int64_t* count_out,
         const tp_opts* opts, void* stream);
+
+/* tcur: t-CUR of Algorithm 5.  Lateral slices C as in tcx (probability
+ * min{1, c p_j}, p from prob_mode / p_cols, Philox stream 0, rescaled by
+ * 1/sqrt(q_j)).  Horizontal slice i is picked with probability
+ * min{1, l p_i} by the Philox coins of stream 1 and rescaled by 1/sqrt(q_i)
+ * (D); p_i is p_rows[i] when p_rows (device float64[n1]) is given, else the
+ * row leverage of C (eq. colprob_rows_exact with beta = 1): the squared row
+ * norms of the left singular vectors of every Fourier slice C_hat_k above
+ * the pinv cut-off max(n1, c') eps(s_max), summed over all n3 frequencies
+ * and normalised to sum 1.  Per half-spectrum slice
+ *   Z_hat_k = C_hat_k (D S^T C_hat_k)^dagger (D S^T A_hat_k),
+ * the pseudo-inverse with MATLAB's cut-off max(l', c') eps(s_max).
+ *   A        n1 x n2 x n3 input (device);  Z  n1 x n2 x n3 output (device).
+ *   col_idx / col_count: int32[n2] / int64[1] (device, may be NULL): the
+ *            picked lateral slices, as tcx.
+ *   row_idx / row_count: int32[n1] / int64[1] (device, may be NULL): the
+ *            picked horizontal slices, ascending.
+ *   row_prob float64[n1] (device, may be NULL): the row probabilities used
+ *            (zeros when no lateral slice was picked).
+ * No pick in either draw gives Z = 0.  Reads both pick counts back to the
+ * host (synchronises `stream` twice).  Workspace: TP_OP_TCUR {n1, n2, n3}.
+ * Limits: min(n1, n2) <= 512, max(n1, n2) <= 4096, n3 <= 512.               */
+int tcur(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, int64_t l, uint64_t seed,
+         int prob_mode, const double* p_cols, const double* p_rows, float* Z, int32_t* col_idx,
+         int64_t* col_count, int32_t* row_idx, int64_t* row_count, double* row_prob,
+         const tp_opts* opts, void* stream);
 
 /* ---------------------------------------------------------------- completion
  * tcomplete_svt: `iters` iterations of the ADMM of Algorithm 7 in the

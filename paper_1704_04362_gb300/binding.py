@@ -23,14 +23,14 @@ __all__ = [
     "rdft3", "irdft3", "slice_norms", "sample_draw", "launch_count", "exported_symbols",
     "profile_start", "profile_stop", "slice_norms_noalloc", "tcomplete_svt_batched",
     "sketch_spectrum", "rank_rule", "rank_features", "mlp_param_count", "mlp_round",
-    "mlp_forward", "mlp_train_step", "trpca_admm",
+    "mlp_forward", "mlp_train_step", "trpca_admm", "tcur",
 ]
 
 TP_FP32, TP_TF32X3, TP_BF16X3 = 0, 1, 2
 TP_PROB_AB, TP_PROB_A2, TP_PROB_GIVEN = 0, 1, 2
 TP_OP_TPROD, TP_OP_TPROD_SAMPLED, TP_OP_TSVD, TP_OP_TSVD_RANDOMIZED, TP_OP_TCOMPLETE_SVT, \
     TP_OP_SLICE_NORMS, TP_OP_TCX, TP_OP_TCOMPLETE_SVT_BATCHED, TP_OP_SKETCH_SPECTRUM, \
-    TP_OP_MLP_TRAIN, TP_OP_TRPCA = 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11
+    TP_OP_MLP_TRAIN, TP_OP_TRPCA, TP_OP_TCUR = 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _c_i64, _c_u64, _c_int, _c_u32 = ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32
@@ -65,6 +65,8 @@ _SIGS = {
                                _vp, _vp, _vp, _vp, _vp, _vp]),
     "tcx": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_i64, _c_u64, _c_int, _vp, _vp, _vp, _vp,
                      _vp, _vp]),
+    "tcur": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_i64, _c_i64, _c_u64, _c_int, _vp, _vp, _vp,
+                      _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "tcomplete_svt_batched": (_c_int, [_c_int, _vp, _c_int, _dbl, _dbl, _vp, _vp]),
     "trpca_admm": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_int, _dbl, _dbl, _dbl, _vp, _vp, _vp,
                             _vp, _vp, _vp]),
@@ -476,6 +478,31 @@ def tcx(A, c, seed=0, prob_mode=TP_PROB_A2, p_given=None, status=None):
                    _tensor_arg(count, "count", torch.int64), ctypes.byref(o), _stream())
     _check(rc, "tcx")
     return Z, idx, count
+
+
+def tcur(A, c, l, seed=0, prob_mode=TP_PROB_A2, p_cols=None, p_rows=None, status=None):
+    """t-CUR (Algorithm 5): returns (Z, col_idx, col_count, row_idx, row_count,
+    row_prob); row_prob is the row leverage of C unless p_rows is given."""
+    torch = _torch()
+    n1, n2, n3 = A.shape
+    Z = empty_tensor(n1, n2, n3, device=A.device)
+    cidx = torch.empty(n2, dtype=torch.int32, device=A.device)
+    ccnt = torch.empty(1, dtype=torch.int64, device=A.device)
+    ridx = torch.empty(n1, dtype=torch.int32, device=A.device)
+    rcnt = torch.empty(1, dtype=torch.int64, device=A.device)
+    prob = torch.empty(n1, dtype=torch.float64, device=A.device)
+    pc = _tensor_arg(p_cols, "p_cols", torch.float64) if prob_mode == TP_PROB_GIVEN else None
+    pr = _tensor_arg(p_rows, "p_rows", torch.float64) if p_rows is not None else None
+    o = _opts(TP_OP_TCUR, (n1, n2, n3), TP_FP32, status)
+    rc = lib().tcur(_tensor_arg(A, "A"), n1, n2, n3, int(c), int(l), int(seed) & ((1 << 64) - 1),
+                    int(prob_mode), pc, pr, _tensor_arg(Z, "Z"),
+                    _tensor_arg(cidx, "col_idx", torch.int32),
+                    _tensor_arg(ccnt, "col_count", torch.int64),
+                    _tensor_arg(ridx, "row_idx", torch.int32),
+                    _tensor_arg(rcnt, "row_count", torch.int64),
+                    _tensor_arg(prob, "row_prob", torch.float64), ctypes.byref(o), _stream())
+    _check(rc, "tcur")
+    return Z, cidx, ccnt, ridx, rcnt, prob
 
 
 def rdft3(X):

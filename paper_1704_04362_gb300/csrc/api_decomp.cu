@@ -19,6 +19,11 @@ size_t tcx_ws(int64_t n1, int64_t n2, int64_t n3);
 int tcx_run(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, uint64_t seed,
             int prob_mode, const double* p_given, float* Z, int32_t* idx_out, int64_t* count_out,
             const tp_opts* opts, cudaStream_t st);
+size_t tcur_ws(int64_t n1, int64_t n2, int64_t n3);
+int tcur_run(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, int64_t l,
+             uint64_t seed, int prob_mode, const double* p_cols, const double* p_rows, float* Z,
+             int32_t* col_idx, int64_t* col_count, int32_t* row_idx, int64_t* row_count,
+             double* row_prob, const tp_opts* opts, cudaStream_t st);
 int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, int q,
              uint64_t seed, float* U, float* S, float* V, const tp_opts* opts, cudaStream_t st,
              float* sig_out);
@@ -35,6 +40,7 @@ size_t workspace_for(int op, const int64_t* d, int nd) {
     case TP_OP_SKETCH_SPECTRUM: return nd >= 4 ? rsvd_ws(d[0], d[1], d[2], d[3], 0) : 0;
     case TP_OP_MLP_TRAIN: return nd >= 1 ? mlp_ws(d[0]) : 0;
     case TP_OP_TCX: return nd >= 3 ? tcx_ws(d[0], d[1], d[2]) : 0;
+    case TP_OP_TCUR: return nd >= 3 ? tcur_ws(d[0], d[1], d[2]) : 0;
     default: return 0;
   }
 }
@@ -160,5 +166,25 @@ int tcx(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, uint64_t 
   if (n3 > 512) { set_error("tcx: n3 > 512 not supported (the gathered transform is direct)"); return TP_EUNSUPPORTED; }
   return tcx_run(A, n1, n2, n3, c, seed, prob_mode, p_given, Z, idx_out, count_out, opts,
                  as_stream(stream));
+}
+
+int tcur(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, int64_t l, uint64_t seed,
+         int prob_mode, const double* p_cols, const double* p_rows, float* Z, int32_t* col_idx,
+         int64_t* col_count, int32_t* row_idx, int64_t* row_count, double* row_prob,
+         const tp_opts* opts, void* stream) {
+  if (!A || !Z) { set_error("tcur: NULL tensor"); return TP_ENULL; }
+  if (!dims3_ok(n1, n2, n3) || c < 1 || l < 1) { set_error("tcur: invalid sizes"); return TP_EINVAL; }
+  if (prob_mode != TP_PROB_A2 && prob_mode != TP_PROB_GIVEN) {
+    set_error("tcur: prob_mode must be TP_PROB_A2 or TP_PROB_GIVEN");
+    return TP_EINVAL;
+  }
+  if (prob_mode == TP_PROB_GIVEN && !p_cols) { set_error("tcur: TP_PROB_GIVEN needs p_cols"); return TP_ENULL; }
+  if ((n1 < n2 ? n1 : n2) > 512 || (n1 > n2 ? n1 : n2) > 4096) {
+    set_error("tcur: needs min(n1, n2) <= 512 and max(n1, n2) <= 4096");
+    return TP_EUNSUPPORTED;
+  }
+  if (n3 > 512) { set_error("tcur: n3 > 512 not supported (the gathered transform is direct)"); return TP_EUNSUPPORTED; }
+  return tcur_run(A, n1, n2, n3, c, l, seed, prob_mode, p_cols, p_rows, Z, col_idx, col_count,
+                  row_idx, row_count, row_prob, opts, as_stream(stream));
 }
 }

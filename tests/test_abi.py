@@ -52,6 +52,12 @@ def test_null_and_size_errors_need_no_gpu(L):
     assert L.tprod_sampled(p, p, p, 2, 2, 2, 2, 1, 0, 2, nul, nul, nul, nul, nul) == -2  # p_given
     assert L.tp_sample_draw(nul, nul, 4, 1, 0, 0, 0, nul, nul, nul, nul, nul) == -2
     assert L.tp_slice_norms(p, 2, 2, 2, 5, p, nul, nul) == -1
+    t = [nul] * 8
+    assert L.tcur(nul, 2, 2, 2, 1, 1, 0, 1, nul, nul, p, *t) == -2         # A
+    assert L.tcur(p, 2, 2, 2, 1, 0, 0, 1, nul, nul, p, *t) == -1           # l = 0
+    assert L.tcur(p, 2, 2, 2, 1, 1, 0, 0, nul, nul, p, *t) == -1           # mode AB
+    assert L.tcur(p, 2, 2, 2, 1, 1, 0, 2, nul, nul, p, *t) == -2           # p_cols
+    assert L.tcur(p, 600, 600, 2, 1, 1, 0, 1, nul, nul, p, *t) == -10      # min(n1, n2) > 512
 
 
 def test_workspace_query_is_monotone(L):
