@@ -12,6 +12,8 @@ tsvd_randomized Randomized low-tubal-rank t-SVD: per Fourier slice the
 tproject, tcx   Algorithm 3 (t-project) and Algorithm 4 (t-CX).
 tcur            Algorithm 5 (t-CUR) with the row leverage probabilities of
                 eq. (colprob_rows_exact).
+cur_tnn         Algorithm 6 (CUR t-NN): ADMM on the picked lateral and
+                horizontal slices, then C~ * W~^dagger * R~.
 """
 from __future__ import annotations
 
@@ -159,12 +161,13 @@ def tcx(A: np.ndarray, c: int, seed: int, mode: int = sampling_ref.PROB_A2,
     return tproject(A, C), idx, q
 
 
-def row_leverage(C: np.ndarray) -> np.ndarray:
+def row_leverage(C: np.ndarray, r: int = 0) -> np.ndarray:
     """Horizontal-slice probabilities of Algorithm 5 (eq. colprob_rows_exact,
     beta = 1): p_i proportional to ||U_hat_{i::}||_F^2, U_hat_k the left
     singular vectors of every Fourier slice C_hat_k (all n3 frequencies) whose
-    singular values pass MATLAB's pinv cut-off max(n1, c) eps(s_max);
-    normalised to sum 1."""
+    singular values pass MATLAB's pinv cut-off max(n1, c) eps(s_max), and with
+    r > 0 only the top r of them (the rank parameter of Algorithm 5; the
+    top-r estimate of the remark after Corollary 3.7); normalised to sum 1."""
     C = np.asarray(C, dtype=np.float64)
     n1, c, n3 = C.shape
     Ch = fft3(C)
@@ -174,13 +177,15 @@ def row_leverage(C: np.ndarray) -> np.ndarray:
         if sv.size == 0 or sv[0] == 0:
             continue
         keep = sv > max(n1, c) * np.spacing(sv[0])
+        if r > 0:
+            keep[r:] = False                   # sv is descending
         lev += np.sum(np.abs(u[:, keep]) ** 2, axis=1)
     tot = lev.sum()
     return lev / tot if tot > 0 else lev
 
 
 def tcur(A: np.ndarray, c: int, l: int, seed: int, mode: int = sampling_ref.PROB_A2,
-         p_cols: np.ndarray | None = None, p_rows: np.ndarray | None = None):
+         p_cols: np.ndarray | None = None, p_rows: np.ndarray | None = None, r: int = 0):
     """t-CUR, Algorithm 5: lateral slices as t-CX (Philox stream 0), horizontal
     slices with probability min{1, l p_i} (stream 1; p_i the row leverage of
     C unless given), R_hat_k = D S^T A_hat_k, U_hat_k = (D S^T C_hat_k)^dagger,
@@ -197,7 +202,7 @@ def tcur(A: np.ndarray, c: int, l: int, seed: int, mode: int = sampling_ref.PROB
     if len(cidx) == 0:
         return np.zeros_like(A), cidx, np.zeros(0, dtype=cidx.dtype), np.zeros(n1)
     C = A[:, cidx, :] / np.sqrt(qc[cidx])[None, :, None]
-    pr = row_leverage(C) if p_rows is None else np.asarray(p_rows, dtype=np.float64)
+    pr = row_leverage(C, r) if p_rows is None else np.asarray(p_rows, dtype=np.float64)
     ridx, qr = sampling_ref.draw(pr, l, seed, STREAM_HORIZONTAL)
     if len(ridx) == 0:
         return np.zeros_like(A), cidx, ridx, pr
@@ -210,3 +215,71 @@ def tcur(A: np.ndarray, c: int, l: int, seed: int, mode: int = sampling_ref.PROB
         W = d[:, None] * Ch[ridx, :, f]
         Zh[:, :, f] = Ch[:, :, f] @ (pinv_matlab(W) @ R)
     return ifft3(Zh).real, cidx, ridx, pr
+
+
+def pinv_rtol(M: np.ndarray, rtol: float) -> np.ndarray:
+    """Pseudo-inverse over the singular values above rtol * sigma_max (MATLAB's
+    pinv(M, tol) with tol = rtol sigma_max); rtol <= 0 gives pinv_matlab."""
+    if rtol <= 0:
+        return pinv_matlab(M)
+    u, sv, vt = np.linalg.svd(M, full_matrices=False)
+    if sv.size == 0:
+        return np.zeros((M.shape[1], M.shape[0]), dtype=M.dtype)
+    keep = sv > rtol * sv[0]
+    inv = np.where(keep, 1.0 / np.where(keep, sv, 1.0), 0.0)
+    return (np.conj(vt).T * inv) @ np.conj(u).T
+
+
+def cur_combine(Ct: np.ndarray, Rt: np.ndarray, ridx: np.ndarray, rtol: float) -> np.ndarray:
+    """Steps 6-7 of Algorithm 6: W~ = the horizontal slices ridx of C~,
+    U~ = W~^dagger and L~ = C~ * U~ * R~, per Fourier slice."""
+    Ch = fft3(Ct)
+    Rh = fft3(Rt)
+    n1, n3 = Ct.shape[0], Ct.shape[2]
+    Lh = np.empty((n1, Rt.shape[1], n3), dtype=complex)
+    for f in range(n3):
+        Lh[:, :, f] = Ch[:, :, f] @ (pinv_rtol(Ch[ridx, :, f], rtol) @ Rh[:, :, f])
+    return ifft3(Lh).real
+
+
+def cur_tnn(X: np.ndarray, c: int, l: int, seed: int, iters: int, r: int = 0, mask=None,
+            lam=None, mode: int = sampling_ref.PROB_A2, p_cols=None, p_rows=None,
+            rtol: float = 1e-4, mu0: float = 1e-3, rho: float = 1.1, mu_max: float = 1e10):
+    """CUR t-NN, Algorithm 6.  Lateral slices C of X are picked with
+    probability min{1, c p_j} (Philox stream 0; p from the lateral norms of
+    the observed data, or given), horizontal slices R with probability
+    min{1, l p_i} (stream 1; p_i the top-r row leverage of C, or given); the
+    picked slices are not rescaled.  C~ and R~ are the ADMM solutions of
+    problem tlow7 (mask None; lambda per sub-tensor from its own sizes unless
+    given) or of problem tlow6 (the mask's observed entries).  Returns
+    (L~, C~, R~, col_idx, row_idx, p_rows)."""
+    from . import completion_ref
+    from .philox_ref import STREAM_HORIZONTAL
+    X = np.asarray(X, dtype=np.float64)
+    n1, n2, n3 = X.shape
+    obs = None if mask is None else np.asarray(mask).astype(bool)
+    Xo = X if obs is None else np.where(obs, X, 0.0)
+    if mode == sampling_ref.PROB_GIVEN:
+        p = np.asarray(p_cols, dtype=np.float64)
+    else:
+        p = sampling_ref.probabilities(sampling_ref.lateral_norms_sq(Xo), None,
+                                       sampling_ref.PROB_A2)
+    cidx, _ = sampling_ref.draw(p, c, seed)
+    empty = np.zeros(0, dtype=cidx.dtype)
+    if len(cidx) == 0:
+        return (np.zeros_like(X), np.zeros((n1, 0, n3)), np.zeros((0, n2, n3)), cidx, empty,
+                np.zeros(n1))
+    C = Xo[:, cidx, :]
+    pr = row_leverage(C, r) if p_rows is None else np.asarray(p_rows, dtype=np.float64)
+    ridx, _ = sampling_ref.draw(pr, l, seed, STREAM_HORIZONTAL)
+    if len(ridx) == 0:
+        return np.zeros_like(X), np.zeros((n1, 0, n3)), np.zeros((0, n2, n3)), cidx, ridx, pr
+    R = Xo[ridx, :, :]
+
+    def admm(T, M):
+        if M is None:
+            return completion_ref.trpca(T, iters, lam, mu0, rho, mu_max)[0]
+        return completion_ref.tcomplete_svt(T, M, iters, mu0, rho, mu_max)[0]
+    Ct = admm(C, None if obs is None else obs[:, cidx, :])
+    Rt = admm(R, None if obs is None else obs[ridx, :, :])
+    return cur_combine(Ct, Rt, ridx, rtol), Ct, Rt, cidx, ridx, pr

@@ -272,3 +272,63 @@ def test_row_leverage_is_the_projector_diagonal_summed_over_frequencies():
         lev += np.real(np.diag(M @ np.linalg.solve(M.conj().T @ M, M.conj().T)))
     np.testing.assert_allclose(D.row_leverage(C), lev / lev.sum(), atol=1e-12)
     assert abs(lev.sum() - 4 * 5) < 1e-9                 # trace of a rank-4 projector, 5 times
+
+
+def test_top_r_row_leverage_is_the_top_eigenspace_of_c_ct():
+    # n3 = 1: ||U_r(i, :)||^2 is the i-th diagonal entry of the projector on
+    # the top-r eigenvectors of C C^T (a symmetric eigensolver, not an SVD)
+    from oracle import decomp_ref as D
+    C = np.random.default_rng(66).standard_normal((14, 6)) @ np.diag([9, 7, 5, 1, 0.5, 0.2])
+    w, V = np.linalg.eigh(C @ C.T)
+    top = V[:, np.argsort(w)[::-1][:3]]
+    lev = np.sum(top ** 2, axis=1)
+    np.testing.assert_allclose(D.row_leverage(C[:, :, None], 3), lev / 3, atol=1e-12)
+
+
+def test_top_r_row_leverage_of_exact_rank_r_equals_the_cut_off_leverage():
+    from oracle import decomp_ref as D
+    from paper_1704_04362_gb300 import synth
+    C = synth.lowrank_np(20, 9, 6, 3, seed=67, dtype=np.float64)
+    np.testing.assert_allclose(D.row_leverage(C, 3), D.row_leverage(C, 0), atol=1e-10)
+    assert abs(D.row_leverage(C, 5).sum() - 1) < 1e-12
+    assert np.max(np.abs(D.row_leverage(C, 2) - D.row_leverage(C, 0))) > 1e-3
+
+
+def test_cur_combine_with_n3_one_is_a_library_pinv():
+    from oracle import decomp_ref as D
+    g = np.random.default_rng(68)
+    Ct = g.standard_normal((12, 5, 1))
+    Rt = g.standard_normal((7, 9, 1))
+    ridx = np.array([0, 2, 3, 5, 8, 10, 11])
+    got = D.cur_combine(Ct, Rt, ridx, 1e-4)[:, :, 0]
+    want = Ct[:, :, 0] @ np.linalg.pinv(Ct[ridx, :, 0], rcond=1e-4) @ Rt[:, :, 0]
+    np.testing.assert_allclose(got, want, atol=1e-10)
+
+
+def test_cur_tnn_with_every_slice_is_the_full_admm():
+    # W~ = C~ = R~ = ADMM(X): L~ = C~ C~^dagger C~ = C~
+    from oracle import completion_ref, decomp_ref as D
+    from paper_1704_04362_gb300 import synth
+    X = synth.lowrank_np(14, 12, 4, 2, seed=69, noise=0.05, dtype=np.float64)
+    L, Ct, Rt, ci, ri, _ = D.cur_tnn(X, 10 ** 6, 10 ** 6, 1, 15, rtol=0.0)
+    assert len(ci) == 12 and len(ri) == 14
+    full = completion_ref.trpca(X, 15)[0]
+    np.testing.assert_allclose(Ct, full, atol=1e-12)
+    np.testing.assert_allclose(L, full, atol=1e-9 * np.abs(full).max())
+    mask = np.random.default_rng(70).random(X.shape) < 0.6
+    L, *_ = D.cur_tnn(X, 10 ** 6, 10 ** 6, 1, 15, mask=mask, rtol=0.0)
+    full = completion_ref.tcomplete_svt(X, mask, 15)[0]
+    np.testing.assert_allclose(L, full, atol=1e-9 * np.abs(full).max())
+
+
+def test_cur_tnn_recovers_low_rank_plus_sparse_from_sampled_slices():
+    from oracle import decomp_ref as D
+    from paper_1704_04362_gb300 import synth
+    L0 = synth.lowrank_np(60, 50, 4, 2, seed=71, dtype=np.float64)
+    L0 /= np.sqrt(np.mean(L0 ** 2))
+    g = np.random.default_rng(72)
+    S0 = np.where(g.random(L0.shape) < 0.05, 10.0 * g.standard_normal(L0.shape), 0.0)
+    L, Ct, Rt, ci, ri, _ = D.cur_tnn(L0 + S0, 25, 30, 3, 80, r=2)
+    assert len(ci) < 50 and len(ri) < 60
+    err = np.linalg.norm(L - L0) / np.linalg.norm(L0)
+    assert err < 1e-3, err
