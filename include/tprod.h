@@ -97,7 +97,8 @@ typedef enum {
   TP_OP_SKETCH_SPECTRUM = 9,        /* dims: n1, n2, n3, l */
   TP_OP_MLP_TRAIN = 10,             /* dims: batch */
   TP_OP_TRPCA = 11,                 /* dims: n1, n2, n3 */
-  TP_OP_TCUR = 12                   /* dims: n1, n2, n3 */
+  TP_OP_TCUR = 12,                  /* dims: n1, n2, n3 */
+  TP_OP_CUR_TNN = 13                /* dims: n1, n2, n3 */
 } tp_op;
 
 /* ---------------------------------------------------------------- t-product
@@ -177,8 +178,9 @@ int tcx(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, uint64_t 
  * (D); p_i is p_rows[i] when p_rows (device float64[n1]) is given, else the
  * row leverage of C (eq. colprob_rows_exact with beta = 1): the squared row
  * norms of the left singular vectors of every Fourier slice C_hat_k above
- * the pinv cut-off max(n1, c') eps(s_max), summed over all n3 frequencies
- * and normalised to sum 1.  Per half-spectrum slice
+ * the pinv cut-off max(n1, c') eps(s_max) -- with rank > 0 (Algorithm 5's
+ * rank parameter) only the `rank` largest of each slice -- summed over all
+ * n3 frequencies and normalised to sum 1.  Per half-spectrum slice
  *   Z_hat_k = C_hat_k (D S^T C_hat_k)^dagger (D S^T A_hat_k),
  * the pseudo-inverse with MATLAB's cut-off max(l', c') eps(s_max).
  *   A        n1 x n2 x n3 input (device);  Z  n1 x n2 x n3 output (device).
@@ -191,10 +193,41 @@ int tcx(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, uint64_t 
  * No pick in either draw gives Z = 0.  Reads both pick counts back to the
  * host (synchronises `stream` twice).  Workspace: TP_OP_TCUR {n1, n2, n3}.
  * Limits: min(n1, n2) <= 512, max(n1, n2) <= 4096, n3 <= 512.               */
-int tcur(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, int64_t l, uint64_t seed,
-         int prob_mode, const double* p_cols, const double* p_rows, float* Z, int32_t* col_idx,
-         int64_t* col_count, int32_t* row_idx, int64_t* row_count, double* row_prob,
-         const tp_opts* opts, void* stream);
+int tcur(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, int64_t l, int rank,
+         uint64_t seed, int prob_mode, const double* p_cols, const double* p_rows, float* Z,
+         int32_t* col_idx, int64_t* col_count, int32_t* row_idx, int64_t* row_count,
+         double* row_prob, const tp_opts* opts, void* stream);
+
+/* cur_tnn: CUR t-NN of Algorithm 6.  Lateral slices C of X are picked with
+ * probability min{1, c p_j} (Philox stream 0; p from the lateral norms of
+ * the observed data P_Omega(X), TP_PROB_A2, or p_cols, TP_PROB_GIVEN) and
+ * horizontal slices R with probability min{1, l p_i} (stream 1; p_i from
+ * p_rows, else the top-`rank` row leverage of C as in tcur); the picks are
+ * not rescaled.  C~ and R~ are the results of `iters` iterations of the ADMM
+ * of Algorithm 7 from (L, E, Y) = 0, mu = mu0: with mask == NULL the robust
+ * form of problem tlow7 (lambda > 0, or 0 for 1/sqrt(max(rows, cols) n3) of
+ * each sub-tensor), with a mask the completion form of problem tlow6 on the
+ * observed entries (lambda unused).  The two ADMM runs go concurrently on
+ * side streams.  Then per half-spectrum slice
+ *   L~_hat_k = C~_hat_k (S^T C~_hat_k)^dagger R~_hat_k,
+ * the pseudo-inverse over the singular values above pinv_rtol * s_max
+ * (MATLAB's pinv(W, tol); pinv_rtol = 0 takes the default cut-off
+ * max(l', c') eps(s_max)).
+ *   X, L      n1 x n2 x n3 input / output (device);  mask  uint8 n1 x n2 x n3
+ *             (device, 1 = observed) or NULL.
+ *   Ct, Rt    device float32[n1 n2 n3] or NULL: receive C~ (n1 x c' x n3)
+ *             and R~ (l' x n2 x n3), column-major, compact.
+ *   col_idx, col_count, row_idx, row_count, row_prob: as tcur.
+ * No pick in either draw gives L = 0.  Synchronises `stream` (pick counts,
+ * the concurrent ADMM runs).  Workspace: TP_OP_CUR_TNN {n1, n2, n3}.
+ * Limits: min(n1, n2) <= 512, max(n1, n2) <= 4096; n3 <= 512 or a product of
+ * the radices 2..13.                                                         */
+int cur_tnn(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t n3, int64_t c,
+            int64_t l, int rank, uint64_t seed, int prob_mode, const double* p_cols,
+            const double* p_rows, int iters, double lambda, double mu0, double rho, double mu_max,
+            double pinv_rtol, float* L, float* Ct, float* Rt, int32_t* col_idx,
+            int64_t* col_count, int32_t* row_idx, int64_t* row_count, double* row_prob,
+            const tp_opts* opts, void* stream);
 
 /* ---------------------------------------------------------------- completion
  * tcomplete_svt: `iters` iterations of the ADMM of Algorithm 7 in the

@@ -23,14 +23,15 @@ __all__ = [
     "rdft3", "irdft3", "slice_norms", "sample_draw", "launch_count", "exported_symbols",
     "profile_start", "profile_stop", "slice_norms_noalloc", "tcomplete_svt_batched",
     "sketch_spectrum", "rank_rule", "rank_features", "mlp_param_count", "mlp_round",
-    "mlp_forward", "mlp_train_step", "trpca_admm", "tcur",
+    "mlp_forward", "mlp_train_step", "trpca_admm", "tcur", "cur_tnn",
 ]
 
 TP_FP32, TP_TF32X3, TP_BF16X3 = 0, 1, 2
 TP_PROB_AB, TP_PROB_A2, TP_PROB_GIVEN = 0, 1, 2
 TP_OP_TPROD, TP_OP_TPROD_SAMPLED, TP_OP_TSVD, TP_OP_TSVD_RANDOMIZED, TP_OP_TCOMPLETE_SVT, \
     TP_OP_SLICE_NORMS, TP_OP_TCX, TP_OP_TCOMPLETE_SVT_BATCHED, TP_OP_SKETCH_SPECTRUM, \
-    TP_OP_MLP_TRAIN, TP_OP_TRPCA, TP_OP_TCUR = 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12
+    TP_OP_MLP_TRAIN, TP_OP_TRPCA, TP_OP_TCUR, TP_OP_CUR_TNN = \
+    1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _c_i64, _c_u64, _c_int, _c_u32 = ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32
@@ -65,8 +66,11 @@ _SIGS = {
                                _vp, _vp, _vp, _vp, _vp, _vp]),
     "tcx": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_i64, _c_u64, _c_int, _vp, _vp, _vp, _vp,
                      _vp, _vp]),
-    "tcur": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_i64, _c_i64, _c_u64, _c_int, _vp, _vp, _vp,
-                      _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "tcur": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_i64, _c_i64, _c_int, _c_u64, _c_int, _vp,
+                      _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "cur_tnn": (_c_int, [_vp, _vp, _c_i64, _c_i64, _c_i64, _c_i64, _c_i64, _c_int, _c_u64, _c_int,
+                         _vp, _vp, _c_int, _dbl, _dbl, _dbl, _dbl, _dbl, _vp, _vp, _vp, _vp, _vp,
+                         _vp, _vp, _vp, _vp, _vp]),
     "tcomplete_svt_batched": (_c_int, [_c_int, _vp, _c_int, _dbl, _dbl, _vp, _vp]),
     "trpca_admm": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_int, _dbl, _dbl, _dbl, _vp, _vp, _vp,
                             _vp, _vp, _vp]),
@@ -480,9 +484,10 @@ def tcx(A, c, seed=0, prob_mode=TP_PROB_A2, p_given=None, status=None):
     return Z, idx, count
 
 
-def tcur(A, c, l, seed=0, prob_mode=TP_PROB_A2, p_cols=None, p_rows=None, status=None):
+def tcur(A, c, l, seed=0, prob_mode=TP_PROB_A2, p_cols=None, p_rows=None, rank=0, status=None):
     """t-CUR (Algorithm 5): returns (Z, col_idx, col_count, row_idx, row_count,
-    row_prob); row_prob is the row leverage of C unless p_rows is given."""
+    row_prob); row_prob is the (top-rank) row leverage of C unless p_rows is
+    given."""
     torch = _torch()
     n1, n2, n3 = A.shape
     Z = empty_tensor(n1, n2, n3, device=A.device)
@@ -494,7 +499,8 @@ def tcur(A, c, l, seed=0, prob_mode=TP_PROB_A2, p_cols=None, p_rows=None, status
     pc = _tensor_arg(p_cols, "p_cols", torch.float64) if prob_mode == TP_PROB_GIVEN else None
     pr = _tensor_arg(p_rows, "p_rows", torch.float64) if p_rows is not None else None
     o = _opts(TP_OP_TCUR, (n1, n2, n3), TP_FP32, status)
-    rc = lib().tcur(_tensor_arg(A, "A"), n1, n2, n3, int(c), int(l), int(seed) & ((1 << 64) - 1),
+    rc = lib().tcur(_tensor_arg(A, "A"), n1, n2, n3, int(c), int(l), int(rank),
+                    int(seed) & ((1 << 64) - 1),
                     int(prob_mode), pc, pr, _tensor_arg(Z, "Z"),
                     _tensor_arg(cidx, "col_idx", torch.int32),
                     _tensor_arg(ccnt, "col_count", torch.int64),
@@ -503,6 +509,44 @@ def tcur(A, c, l, seed=0, prob_mode=TP_PROB_A2, p_cols=None, p_rows=None, status
                     _tensor_arg(prob, "row_prob", torch.float64), ctypes.byref(o), _stream())
     _check(rc, "tcur")
     return Z, cidx, ccnt, ridx, rcnt, prob
+
+
+def cur_tnn(X, c, l, iters, seed=0, rank=0, mask=None, lam=0.0, prob_mode=TP_PROB_A2,
+            p_cols=None, p_rows=None, pinv_rtol=1e-4, mu0=1e-3, rho=1.1, mu_max=1e10,
+            status=None, max_sweeps=0):
+    """CUR t-NN (Algorithm 6): returns (L, Ct, Rt, col_idx, col_count, row_idx,
+    row_count, row_prob); Ct and Rt are the ADMM solutions on the picked
+    lateral (n1 x c' x n3) and horizontal (l' x n2 x n3) slices, as
+    column-major tensors."""
+    torch = _torch()
+    n1, n2, n3 = X.shape
+    dev = X.device
+    L = empty_tensor(n1, n2, n3, device=dev)
+    ct = torch.empty(n1 * n2 * n3, dtype=torch.float32, device=dev)
+    rt = torch.empty(n1 * n2 * n3, dtype=torch.float32, device=dev)
+    cidx = torch.empty(n2, dtype=torch.int32, device=dev)
+    ccnt = torch.empty(1, dtype=torch.int64, device=dev)
+    ridx = torch.empty(n1, dtype=torch.int32, device=dev)
+    rcnt = torch.empty(1, dtype=torch.int64, device=dev)
+    prob = torch.empty(n1, dtype=torch.float64, device=dev)
+    mk = _tensor_arg(mask, "mask", torch.uint8) if mask is not None else None
+    pc = _tensor_arg(p_cols, "p_cols", torch.float64) if prob_mode == TP_PROB_GIVEN else None
+    pr = _tensor_arg(p_rows, "p_rows", torch.float64) if p_rows is not None else None
+    o = _opts(TP_OP_CUR_TNN, (n1, n2, n3), TP_FP32, status, max_sweeps)
+    rc = lib().cur_tnn(_tensor_arg(X, "X"), mk, n1, n2, n3, int(c), int(l), int(rank),
+                       int(seed) & ((1 << 64) - 1), int(prob_mode), pc, pr, int(iters),
+                       float(lam), float(mu0), float(rho), float(mu_max), float(pinv_rtol),
+                       _tensor_arg(L, "L"), _tensor_arg(ct, "Ct"), _tensor_arg(rt, "Rt"),
+                       _tensor_arg(cidx, "col_idx", torch.int32),
+                       _tensor_arg(ccnt, "col_count", torch.int64),
+                       _tensor_arg(ridx, "row_idx", torch.int32),
+                       _tensor_arg(rcnt, "row_count", torch.int64),
+                       _tensor_arg(prob, "row_prob", torch.float64), ctypes.byref(o), _stream())
+    _check(rc, "cur_tnn")
+    cp, lp = int(ccnt.item()), int(rcnt.item())
+    Ct = ct[: n1 * cp * n3].view(n3, cp, n1).permute(2, 1, 0)
+    Rt = rt[: lp * n2 * n3].view(n3, n2, lp).permute(2, 1, 0)
+    return L, Ct, Rt, cidx, ccnt, ridx, rcnt, prob
 
 
 def rdft3(X):

@@ -11,7 +11,7 @@ size_t svt_ws(int64_t n1, int64_t n2, int64_t n3);
 size_t svt_batched_ws_dims(const int64_t* dims, int nd);
 size_t mlp_ws(int64_t B);
 int svt_batched_run(int ntens, const tp_tensor_desc* d, int iters, double rho, double mu_max,
-                    const tp_opts* opts, cudaStream_t st);
+                    const tp_opts* opts, cudaStream_t st, const double* lams = nullptr);
 int svt_run(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t n3, int iters,
             double rho, double mu_max, float* L, float* E, float* Y, double* mu,
             const tp_opts* opts, cudaStream_t st, double lam);
@@ -20,10 +20,17 @@ int tcx_run(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, uint6
             int prob_mode, const double* p_given, float* Z, int32_t* idx_out, int64_t* count_out,
             const tp_opts* opts, cudaStream_t st);
 size_t tcur_ws(int64_t n1, int64_t n2, int64_t n3);
-int tcur_run(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, int64_t l,
+int tcur_run(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, int64_t l, int rank,
              uint64_t seed, int prob_mode, const double* p_cols, const double* p_rows, float* Z,
              int32_t* col_idx, int64_t* col_count, int32_t* row_idx, int64_t* row_count,
              double* row_prob, const tp_opts* opts, cudaStream_t st);
+size_t cur_tnn_ws(int64_t n1, int64_t n2, int64_t n3);
+int cur_tnn_run(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t n3,
+                int64_t c, int64_t l, int rank, uint64_t seed, int prob_mode, const double* p_cols,
+                const double* p_rows, int iters, double lambda, double mu0, double rho,
+                double mu_max, double rtol, float* Lout, float* Ct_out, float* Rt_out,
+                int32_t* col_idx, int64_t* col_count, int32_t* row_idx, int64_t* row_count,
+                double* row_prob, const tp_opts* opts, cudaStream_t st);
 int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, int q,
              uint64_t seed, float* U, float* S, float* V, const tp_opts* opts, cudaStream_t st,
              float* sig_out);
@@ -41,6 +48,7 @@ size_t workspace_for(int op, const int64_t* d, int nd) {
     case TP_OP_MLP_TRAIN: return nd >= 1 ? mlp_ws(d[0]) : 0;
     case TP_OP_TCX: return nd >= 3 ? tcx_ws(d[0], d[1], d[2]) : 0;
     case TP_OP_TCUR: return nd >= 3 ? tcur_ws(d[0], d[1], d[2]) : 0;
+    case TP_OP_CUR_TNN: return nd >= 3 ? cur_tnn_ws(d[0], d[1], d[2]) : 0;
     default: return 0;
   }
 }
@@ -168,12 +176,12 @@ int tcx(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, uint64_t 
                  as_stream(stream));
 }
 
-int tcur(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, int64_t l, uint64_t seed,
-         int prob_mode, const double* p_cols, const double* p_rows, float* Z, int32_t* col_idx,
+int tcur(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, int64_t l, int rank,
+         uint64_t seed, int prob_mode, const double* p_cols, const double* p_rows, float* Z, int32_t* col_idx,
          int64_t* col_count, int32_t* row_idx, int64_t* row_count, double* row_prob,
          const tp_opts* opts, void* stream) {
   if (!A || !Z) { set_error("tcur: NULL tensor"); return TP_ENULL; }
-  if (!dims3_ok(n1, n2, n3) || c < 1 || l < 1) { set_error("tcur: invalid sizes"); return TP_EINVAL; }
+  if (!dims3_ok(n1, n2, n3) || c < 1 || l < 1 || rank < 0) { set_error("tcur: invalid sizes"); return TP_EINVAL; }
   if (prob_mode != TP_PROB_A2 && prob_mode != TP_PROB_GIVEN) {
     set_error("tcur: prob_mode must be TP_PROB_A2 or TP_PROB_GIVEN");
     return TP_EINVAL;
@@ -184,7 +192,37 @@ int tcur(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, int64_t 
     return TP_EUNSUPPORTED;
   }
   if (n3 > 512) { set_error("tcur: n3 > 512 not supported (the gathered transform is direct)"); return TP_EUNSUPPORTED; }
-  return tcur_run(A, n1, n2, n3, c, l, seed, prob_mode, p_cols, p_rows, Z, col_idx, col_count,
+  return tcur_run(A, n1, n2, n3, c, l, rank, seed, prob_mode, p_cols, p_rows, Z, col_idx, col_count,
                   row_idx, row_count, row_prob, opts, as_stream(stream));
+}
+
+int cur_tnn(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t n3, int64_t c,
+            int64_t l, int rank, uint64_t seed, int prob_mode, const double* p_cols,
+            const double* p_rows, int iters, double lambda, double mu0, double rho, double mu_max,
+            double pinv_rtol, float* L, float* Ct, float* Rt, int32_t* col_idx,
+            int64_t* col_count, int32_t* row_idx, int64_t* row_count, double* row_prob,
+            const tp_opts* opts, void* stream) {
+  if (!X || !L) { set_error("cur_tnn: NULL tensor"); return TP_ENULL; }
+  if (!dims3_ok(n1, n2, n3) || c < 1 || l < 1 || rank < 0 || iters < 0 || !(mu0 > 0.0) ||
+      !(rho > 0.0) || !(mu_max > 0.0) || lambda < 0.0 || pinv_rtol < 0.0) {
+    set_error("cur_tnn: invalid sizes or constants");
+    return TP_EINVAL;
+  }
+  if (prob_mode != TP_PROB_A2 && prob_mode != TP_PROB_GIVEN) {
+    set_error("cur_tnn: prob_mode must be TP_PROB_A2 or TP_PROB_GIVEN");
+    return TP_EINVAL;
+  }
+  if (prob_mode == TP_PROB_GIVEN && !p_cols) { set_error("cur_tnn: TP_PROB_GIVEN needs p_cols"); return TP_ENULL; }
+  if ((n1 < n2 ? n1 : n2) > 512 || (n1 > n2 ? n1 : n2) > 4096) {
+    set_error("cur_tnn: needs min(n1, n2) <= 512 and max(n1, n2) <= 4096");
+    return TP_EUNSUPPORTED;
+  }
+  if (n3 > 512 && !fft_supported(n3)) {
+    set_error("cur_tnn: n3 > 512 must factor into radices 2..13");
+    return TP_EUNSUPPORTED;
+  }
+  return cur_tnn_run(X, mask, n1, n2, n3, c, l, rank, seed, prob_mode, p_cols, p_rows, iters,
+                     lambda, mu0, rho, mu_max, pinv_rtol, L, Ct, Rt, col_idx, col_count, row_idx,
+                     row_count, row_prob, opts, as_stream(stream));
 }
 }

@@ -343,7 +343,7 @@ int svt_fork_join(std::vector<SvtTensor>& T, bool warm, bool init, double rho, d
 }  // namespace
 
 int svt_batched_run(int ntens, const tp_tensor_desc* d, int iters, double rho, double mu_max,
-                    const tp_opts* opts, cudaStream_t st) {
+                    const tp_opts* opts, cudaStream_t st, const double* lams) {
   Arena ws;
   int rc = acquire_workspace(opts, svt_batched_ws(ntens, d), &ws);
   if (rc) return rc;
@@ -352,9 +352,11 @@ int svt_batched_run(int ntens, const tp_tensor_desc* d, int iters, double rho, d
   const int sweeps = (opts && opts->max_sweeps > 0) ? opts->max_sweeps : 30;
   std::vector<SvtTensor> T;
   T.reserve(size_t(ntens));
-  for (int i = 0; i < ntens; ++i)
+  for (int i = 0; i < ntens; ++i) {
     T.push_back(svt_carve(d[i].X, d[i].mask, d[i].n1, d[i].n2, d[i].n3, d[i].L, d[i].E, d[i].Y,
                           d[i].mu, ws));
+    if (lams) T.back().lam = lams[i];   // > 0: robust form of problem tlow7
+  }
   const int ns = ntens < kSideStreams ? ntens : kSideStreams;
   cudaStream_t side[kSideStreams] = {};
   cudaEvent_t join[kSideStreams] = {};

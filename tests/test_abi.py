@@ -53,11 +53,20 @@ def test_null_and_size_errors_need_no_gpu(L):
     assert L.tp_sample_draw(nul, nul, 4, 1, 0, 0, 0, nul, nul, nul, nul, nul) == -2
     assert L.tp_slice_norms(p, 2, 2, 2, 5, p, nul, nul) == -1
     t = [nul] * 8
-    assert L.tcur(nul, 2, 2, 2, 1, 1, 0, 1, nul, nul, p, *t) == -2         # A
-    assert L.tcur(p, 2, 2, 2, 1, 0, 0, 1, nul, nul, p, *t) == -1           # l = 0
-    assert L.tcur(p, 2, 2, 2, 1, 1, 0, 0, nul, nul, p, *t) == -1           # mode AB
-    assert L.tcur(p, 2, 2, 2, 1, 1, 0, 2, nul, nul, p, *t) == -2           # p_cols
-    assert L.tcur(p, 600, 600, 2, 1, 1, 0, 1, nul, nul, p, *t) == -10      # min(n1, n2) > 512
+    assert L.tcur(nul, 2, 2, 2, 1, 1, 0, 0, 1, nul, nul, p, *t) == -2      # A
+    assert L.tcur(p, 2, 2, 2, 1, 0, 0, 0, 1, nul, nul, p, *t) == -1        # l = 0
+    assert L.tcur(p, 2, 2, 2, 1, 1, -1, 0, 1, nul, nul, p, *t) == -1       # rank < 0
+    assert L.tcur(p, 2, 2, 2, 1, 1, 0, 0, 0, nul, nul, p, *t) == -1        # mode AB
+    assert L.tcur(p, 2, 2, 2, 1, 1, 0, 0, 2, nul, nul, p, *t) == -2        # p_cols
+    assert L.tcur(p, 600, 600, 2, 1, 1, 0, 0, 1, nul, nul, p, *t) == -10   # min(n1, n2) > 512
+    d = ctypes.c_double
+    k = [d(1e-3), d(1.1), d(1e10), d(1e-4), p, nul, nul] + [nul] * 7
+    assert L.cur_tnn(nul, nul, 2, 2, 2, 1, 1, 0, 0, 1, nul, nul, 5, d(0), *k) == -2   # X
+    assert L.cur_tnn(p, nul, 2, 2, 2, 1, 1, 0, 0, 1, nul, nul, -1, d(0), *k) == -1    # iters
+    assert L.cur_tnn(p, nul, 2, 2, 2, 1, 1, 0, 0, 1, nul, nul, 5, d(-1), *k) == -1    # lambda
+    assert L.cur_tnn(p, nul, 2, 2, 2, 1, 1, 0, 0, 2, nul, nul, 5, d(0), *k) == -2     # p_cols
+    k[0] = d(0.0)
+    assert L.cur_tnn(p, nul, 2, 2, 2, 1, 1, 0, 0, 1, nul, nul, 5, d(0), *k) == -1     # mu0
 
 
 def test_workspace_query_is_monotone(L):

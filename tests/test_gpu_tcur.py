@@ -91,3 +91,21 @@ def test_tcur_special_cases():
     Z, ci, cc, ri, rc, pr = tp.tcur(dev(C), 4, 4, seed=1, p_rows=zr)
     assert int(cc.item()) > 0 and int(rc.item()) == 0
     assert float(torch.abs(Z).max().item()) == 0.0
+
+
+@pytest.mark.parametrize("n1,n2,n3,c,l,r", [(40, 30, 6, 12, 24, 3), (20, 40, 7, 30, 16, 2)])
+def test_tcur_top_r_leverage_matches_oracle(n1, n2, n3, c, l, r):
+    # low tubal rank r plus noise: the top r directions are well separated
+    A = synth.lowrank_np(n1, n2, n3, r, seed=n1 * r, noise=0.05)
+    import torch
+    Z, ci, cc, ri, rc, pr = tp.tcur(dev(A), c, l, seed=4, rank=r)
+    cidx = ci[: int(cc.item())].cpu().numpy()
+    ridx = ri[: int(rc.item())].cpu().numpy()
+    p_dev = pr.cpu().numpy()
+    _, cref, _, pref = decomp_ref.tcur(A, c, l, 4, r=r)
+    assert np.array_equal(cidx, cref)
+    assert rel_fro(p_dev, pref) < TOL_FP32
+    want, _ = sampling_ref.draw(p_dev, l, 4, philox_ref.STREAM_HORIZONTAL)
+    assert np.array_equal(ridx, want)
+    Zr, *_ = decomp_ref.tcur(A, c, l, 4, p_rows=p_dev)
+    assert rel_fro(to_np(Z), Zr) < TOL_FP32
