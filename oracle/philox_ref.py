@@ -65,6 +65,16 @@ def uniform53(index, stream: int, seed: int) -> np.ndarray:
     return ((x0 >> np.uint64(5)) << np.uint64(26)) | (x1 >> np.uint64(6))
 
 
+def uniform53_iid(t, stream: int, seed: int) -> np.ndarray:
+    """53-bit integers of the i.i.d. draws t: counter (t mod 2^32, t >> 32,
+    stream, 1) (the fourth word 1 keeps them apart from the Bernoulli coins)."""
+    t = np.asarray(t, dtype=np.uint64)
+    seed = int(seed) & ((1 << 64) - 1)
+    x0, x1, _, _ = philox4x32_10(t & _MASK, t >> np.uint64(32), stream, 1,
+                                 seed & 0xFFFFFFFF, seed >> 32)
+    return ((x0 >> np.uint64(5)) << np.uint64(26)) | (x1 >> np.uint64(6))
+
+
 def threshold53(q: np.ndarray) -> np.ndarray:
     """Q_j = floor(q_j * 2^53) for 0 <= q_j <= 1 (exact: scaling by 2^53 is exact)."""
     q = np.asarray(q, dtype=np.float64)

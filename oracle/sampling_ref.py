@@ -17,6 +17,9 @@ PROB_AB = 0     # p_j proportional to ||A_{:j:}||_F ||B_{j::}||_F   (choice i)
 PROB_A2 = 1     # p_j proportional to ||A_{:j:}||_F^2                (choice ii)
 PROB_GIVEN = 2  # caller-supplied p
 
+SAMPLE_BERNOULLI = 0   # Algorithm 2: slice j kept with probability min{1, c p_j}
+SAMPLE_IID = 1         # c independent draws with replacement (Drineas et al. 2006)
+
 
 def lateral_norms_sq(A: np.ndarray) -> np.ndarray:
     """||A_{:j:}||_F^2 for every lateral slice j, summed in float64."""
@@ -64,6 +67,39 @@ def draw(p: np.ndarray, c: int, seed: int, stream: int = philox_ref.STREAM_LATER
     return idx, q
 
 
+def draw_iid(p: np.ndarray, c: int, seed: int, stream: int = philox_ref.STREAM_LATERAL):
+    """c independent draws with replacement, index j with probability p_j (the
+    sampling Algorithm 2 reduces to at n3 = 1 in Drineas, Kannan and Mahoney
+    2006).  Integer form, so that any implementation given the same float64 p
+    draws the same indices: W_j = floor(p_j 2^53), cdf_j = W_0 + ... + W_j
+    (exact in integers), draw t takes the 53-bit U_t of counter
+    (t, stream, 1), target_t = floor(U_t cdf_last / 2^53) and the first j with
+    cdf_j > target_t.  Returns (idx in draw order, s) with s_t = c p_{j_t},
+    the rescale of draw t being 1/sqrt(s_t).  No draws when sum W = 0."""
+    p = np.asarray(p, dtype=np.float64)
+    W = [int(w) for w in philox_ref.threshold53(np.clip(p, 0.0, 1.0))]
+    cdf, acc = [], 0
+    for w in W:
+        acc += w
+        cdf.append(acc)
+    if acc == 0 or c <= 0:
+        return np.zeros(0, dtype=np.int64), np.zeros(0)
+    U = philox_ref.uniform53_iid(np.arange(c, dtype=np.uint64), stream, seed)
+    idx = []
+    for t in range(c):
+        target = (int(U[t]) * acc) >> 53
+        lo, hi = 0, len(cdf) - 1                 # first j with cdf_j > target
+        while lo < hi:
+            mid = (lo + hi) // 2
+            if cdf[mid] > target:
+                hi = mid
+            else:
+                lo = mid + 1
+        idx.append(lo)
+    idx = np.array(idx, dtype=np.int64)
+    return idx, c * p[idx]
+
+
 def sample_CR(A: np.ndarray, B: np.ndarray, idx: np.ndarray, q: np.ndarray):
     """C = A*S*D and R = D*S^T*B of Algorithm 2, without forming S or D:
     the picked lateral slices of A and horizontal slices of B, each divided by
@@ -75,11 +111,14 @@ def sample_CR(A: np.ndarray, B: np.ndarray, idx: np.ndarray, q: np.ndarray):
 
 
 def tprod_sampled(A: np.ndarray, B: np.ndarray, c: int, seed: int,
-                  mode: int = PROB_AB, p_given: np.ndarray | None = None):
+                  mode: int = PROB_AB, p_given: np.ndarray | None = None,
+                  sample: int = SAMPLE_BERNOULLI):
     """rt-product, Algorithm 2: Z = C * R.  Returns (Z, idx, q).
 
     Probabilities come from the slice norms (mode PROB_AB / PROB_A2) or from
-    ``p_given`` (mode PROB_GIVEN).  With no slice picked, Z is zero.
+    ``p_given`` (mode PROB_GIVEN).  With no slice picked, Z is zero.  With
+    ``sample`` = SAMPLE_IID the c draws are independent with replacement
+    (draw_iid); q then holds c p_j at the drawn positions (in draw order).
     """
     A = np.asarray(A, dtype=np.float64)
     B = np.asarray(B, dtype=np.float64)
@@ -89,9 +128,17 @@ def tprod_sampled(A: np.ndarray, B: np.ndarray, c: int, seed: int,
         a2 = lateral_norms_sq(A)
         b2 = horizontal_norms_sq(B) if mode == PROB_AB else None
         p = probabilities(a2, b2, mode)
-    idx, q = draw(p, c, seed)
     n1, _, n3 = A.shape
     n4 = B.shape[1]
+    if sample == SAMPLE_IID:
+        idx, s = draw_iid(p, c, seed)
+        if len(idx) == 0:
+            return np.zeros((n1, n4, n3)), idx, s
+        d = 1.0 / np.sqrt(s)
+        C = A[:, idx, :] * d[None, :, None]
+        R = B[idx, :, :] * d[:, None, None]
+        return tprod(C, R), idx, s
+    idx, q = draw(p, c, seed)
     if len(idx) == 0:
         return np.zeros((n1, n4, n3)), idx, q
     C, R = sample_CR(A, B, idx, q)

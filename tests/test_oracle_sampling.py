@@ -144,3 +144,61 @@ def test_monte_carlo_error_matches_expectation():
         errs.append(np.sum((Z - exact) ** 2))
     expect = S.sampled_error_sq_expectation(A, B, q)
     assert abs(np.mean(errs) / expect - 1) < 0.2
+
+
+def test_iid_draw_brute_force_expectation_is_the_exact_product():
+    # all n^c ordered draw sequences with their probabilities prod p_{j_t}
+    import itertools
+    from oracle import sampling_ref as S, tensor_ref as T
+    g = np.random.default_rng(90)
+    A = g.standard_normal((3, 4, 3))
+    B = g.standard_normal((4, 2, 3))
+    p = np.array([0.1, 0.4, 0.2, 0.3])
+    c = 3
+    exact = T.tprod(A, B)
+    mean = np.zeros_like(exact)
+    var = 0.0
+    for seq in itertools.product(range(4), repeat=c):
+        w = np.prod(p[list(seq)])
+        d = 1.0 / np.sqrt(c * p[list(seq)])
+        Z = T.tprod(A[:, seq, :] * d[None, :, None], B[seq, :, :] * d[:, None, None])
+        mean += w * Z
+        var += w * np.sum((Z - exact) ** 2)
+    np.testing.assert_allclose(mean, exact, atol=1e-12)
+    # Drineas et al.: E||AB - CR||^2 = (sum_j ||A_j B_j||^2 / p_j - ||AB||^2) / c
+    terms = sum(np.sum(T.tprod(A[:, j:j + 1, :], B[j:j + 1, :, :]) ** 2) / p[j] for j in range(4))
+    assert abs(var - (terms - np.sum(exact ** 2)) / c) < 1e-10
+
+
+def test_iid_draw_frequencies_and_degenerate_weights():
+    from oracle import sampling_ref as S
+    p = np.array([0.5, 0.0, 0.25, 0.125, 0.125])
+    idx, s = S.draw_iid(p, 20000, 7)
+    assert len(idx) == 20000 and not np.any(idx == 1)            # zero weight never drawn
+    counts = np.bincount(idx, minlength=5)
+    exp = 20000 * p
+    chi2 = sum((counts[j] - exp[j]) ** 2 / exp[j] for j in (0, 2, 3, 4))
+    assert chi2 < 20.0                                            # 3 dof, p ~ 2e-4
+    np.testing.assert_allclose(s, 20000 * p[idx])
+    one = np.zeros(6)
+    one[4] = 1.0
+    assert np.array_equal(S.draw_iid(one, 9, 3)[0], np.full(9, 4))
+    assert len(S.draw_iid(np.zeros(6), 9, 3)[0]) == 0
+    # the integer search by hand: cdf = (2^52, 2^52 + 2^51, ...), target below
+    # 2^52 takes index 0
+    a, _ = S.draw_iid(np.array([0.5, 0.25, 0.25]), 64, 11)
+    from oracle import philox_ref as P
+    U = P.uniform53_iid(np.arange(64, dtype=np.uint64), 0, 11)
+    want = np.where(U < 2 ** 52, 0, np.where(U < 2 ** 52 + 2 ** 51, 1, 2))
+    assert np.array_equal(a, want)
+
+
+def test_iid_sampled_product_with_n3_one_is_drineas_kannan_mahoney():
+    from oracle import sampling_ref as S
+    g = np.random.default_rng(91)
+    A = g.standard_normal((5, 8, 1))
+    B = g.standard_normal((8, 4, 1))
+    Z, idx, s = S.tprod_sampled(A, B, 6, 13, sample=S.SAMPLE_IID)
+    p = S.probabilities(S.lateral_norms_sq(A), S.horizontal_norms_sq(B), S.PROB_AB)
+    want = sum(np.outer(A[:, j, 0], B[j, :, 0]) / (6 * p[j]) for j in idx)
+    np.testing.assert_allclose(Z[:, :, 0], want, atol=1e-12)
