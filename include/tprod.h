@@ -76,6 +76,14 @@ typedef enum {
   TP_PROB_GIVEN = 2  /* p_j supplied by the caller (device float64[n2]) */
 } tp_prob_mode;
 
+/* How slices are drawn. */
+typedef enum {
+  TP_SAMPLE_BERNOULLI = 0, /* Algorithm 2: slice j kept with probability min{1, c p_j} */
+  TP_SAMPLE_IID = 1        /* c independent draws with replacement, j with probability
+                              p_j (the matrix case Algorithm 2 reduces to at n3 = 1,
+                              Drineas, Kannan and Mahoney 2006), rescale 1/sqrt(c p_j) */
+} tp_sample_mode;
+
 typedef struct {
   int precision;          /* tp_precision of the facewise GEMMs (default TP_FP32) */
   int max_sweeps;         /* Jacobi sweep cap, 0 = default (30) */
@@ -120,14 +128,21 @@ int tprod(const float* A, const float* B, float* C,
  * formed.  The coin for slice j is Philox4x32-10 (Salmon et al., SC'11) with
  * counter (j mod 2^32, j >> 32, 0, 0) and key (seed mod 2^32, seed >> 32):
  * j is kept iff ((x0 >> 5) * 2^26 + (x1 >> 6)) < floor(q_j * 2^53).
- *   idx_out    device int32[n2] or NULL: kept indices, ascending, first c' valid
+ * sample_mode TP_SAMPLE_IID instead draws c indices independently with
+ * replacement (1 <= c <= n2): with W_j = floor(p_j 2^53) and U_t the 53-bit
+ * integer of counter (t mod 2^32, t >> 32, 0, 1), draw t is the first j whose
+ * prefix sum W_0 + ... + W_j exceeds floor(U_t sum(W) / 2^53); each drawn
+ * slice pair is scaled by 1/sqrt(c p_j) and the c' = c draws (duplicates
+ * allowed) are multiplied in draw order.
+ *   idx_out    device int32[n2] or NULL: kept indices, ascending (Bernoulli)
+ *              or in draw order (i.i.d.), first c' valid
  *   count_out  device int64 or NULL: c', the number kept
  *   Z          n1 x n4 x n3 output (zero when nothing is kept)
  * c >= 1.  The count stays on the device: no host synchronisation.          */
 int tprod_sampled(const float* A, const float* B, float* Z,
                   int64_t n1, int64_t n2, int64_t n4, int64_t n3,
-                  int64_t c, uint64_t seed, int prob_mode, const double* p_given,
-                  int32_t* idx_out, int64_t* count_out,
+                  int64_t c, uint64_t seed, int prob_mode, int sample_mode,
+                  const double* p_given, int32_t* idx_out, int64_t* count_out,
                   const tp_opts* opts, void* stream);
 
 /* ---------------------------------------------------------------- t-SVD
@@ -149,11 +164,15 @@ int tsvd(const float* X, int64_t n1, int64_t n2, int64_t n3,
  * q power iterations Q <- orth(X_hat^H Q), Q <- orth(X_hat Q), each orth a
  * CholeskyQR2 with float64 Gram and Cholesky, then B = Q^H X_hat, a float64
  * SVD of B and U = Q U_B truncated to k.
+ *   rank_per_freq  device int32[n3/2 + 1] or NULL: per-frequency ranks (the
+ *                  multi-rank of Section 2): half-spectrum slice f keeps its
+ *                  top min(max(r_f, 0), k) triplets and zeroes the rest (its
+ *                  conjugate slice alike); NULL keeps k everywhere.
  *   U  n1 x k x n3,  S  k x k x n3,  V  n2 x k x n3 (outputs).
  * Requires 1 <= k, p >= 0, q >= 0, k + p <= min(n1, n2, 96); n3 <= 512 or
  * n3 a product of the radices 2, 3, 5, 7, 11, 13.                           */
 int tsvd_randomized(const float* X, int64_t n1, int64_t n2, int64_t n3,
-                    int k, int p, int q, uint64_t seed,
+                    int k, int p, int q, uint64_t seed, const int32_t* rank_per_freq,
                     float* U, float* S, float* V, const tp_opts* opts, void* stream);
 
 /* tcx: t-CX of Algorithm 4 with the t-project of Algorithm 3.  Lateral
@@ -390,9 +409,12 @@ size_t tp_slice_norms_noalloc_capacity(void);
  * p = w) computes q_j = min{1, c p_j}, draws with Philox as in tprod_sampled
  * (counter word 2 = `stream_id`), and writes the kept indices ascending to
  * idx (int32[n]), 1/sqrt(q) of each kept index to scale (float32[n]) and
- * the count to count (int64).  q_out (float64[n]) receives q when non-NULL. */
+ * the count to count (int64).  q_out (float64[n]) receives q when non-NULL.
+ * sample_mode TP_SAMPLE_IID: the c (<= n) i.i.d. draws of tprod_sampled
+ * (counter word 2 = `stream_id`, word 3 = 1) in draw order, scale
+ * 1/sqrt(c p_j), count = c (0 when every weight is zero), q_out = c p.    */
 int tp_sample_draw(const double* w, const double* w2, int64_t n, int64_t c,
-                   uint64_t seed, int prob_mode, uint32_t stream_id,
+                   uint64_t seed, int prob_mode, int sample_mode, uint32_t stream_id,
                    int32_t* idx, float* scale, int64_t* count, double* q_out,
                    void* stream);
 

@@ -110,10 +110,18 @@ def tsvd_randomized_hat(X: np.ndarray, k: int, p: int, q: int, Omega: np.ndarray
     return Uh, s, Vh
 
 
-def tsvd_randomized(X: np.ndarray, k: int, p: int, q: int, Omega: np.ndarray):
-    """Randomized tubal-rank-k t-SVD; same output form as ``tsvd`` with m = k."""
+def tsvd_randomized(X: np.ndarray, k: int, p: int, q: int, Omega: np.ndarray, ranks=None):
+    """Randomized tubal-rank-k t-SVD; same output form as ``tsvd`` with m = k.
+    ranks (h integers): half-spectrum slice f keeps only its top
+    min(max(r_f, 0), k) triplets (the multi-rank of Section 2)."""
     n3 = X.shape[2]
     Uh, s, Vh = tsvd_randomized_hat(X, k, p, q, Omega)
+    if ranks is not None:
+        for f in range(s.shape[1]):
+            r = min(max(int(ranks[f]), 0), k)
+            Uh[:, r:, f] = 0.0
+            Vh[:, r:, f] = 0.0
+            s[r:, f] = 0.0
     Sh = np.zeros((k, k, s.shape[1]), dtype=np.complex128)
     for f in range(s.shape[1]):
         Sh[:, :, f] = np.diag(s[:, f])

@@ -18,6 +18,7 @@ import numpy as np
 
 __all__ = [
     "TP_FP32", "TP_TF32X3", "TP_BF16X3", "TP_PROB_AB", "TP_PROB_A2", "TP_PROB_GIVEN",
+    "TP_SAMPLE_BERNOULLI", "TP_SAMPLE_IID",
     "TprodError", "lib", "lib_path", "empty_tensor", "as_tprod_layout",
     "tprod", "tprod_sampled", "tsvd", "tsvd_randomized", "tcomplete_svt", "tcx",
     "rdft3", "irdft3", "slice_norms", "sample_draw", "launch_count", "exported_symbols",
@@ -28,6 +29,7 @@ __all__ = [
 
 TP_FP32, TP_TF32X3, TP_BF16X3 = 0, 1, 2
 TP_PROB_AB, TP_PROB_A2, TP_PROB_GIVEN = 0, 1, 2
+TP_SAMPLE_BERNOULLI, TP_SAMPLE_IID = 0, 1
 TP_OP_TPROD, TP_OP_TPROD_SAMPLED, TP_OP_TSVD, TP_OP_TSVD_RANDOMIZED, TP_OP_TCOMPLETE_SVT, \
     TP_OP_SLICE_NORMS, TP_OP_TCX, TP_OP_TCOMPLETE_SVT_BATCHED, TP_OP_SKETCH_SPECTRUM, \
     TP_OP_MLP_TRAIN, TP_OP_TRPCA, TP_OP_TCUR, TP_OP_CUR_TNN = \
@@ -58,10 +60,10 @@ class TpTensorDesc(ctypes.Structure):
 _SIGS = {
     "tprod": (_c_int, [_vp, _vp, _vp, _c_i64, _c_i64, _c_i64, _c_i64, _vp, _vp]),
     "tprod_sampled": (_c_int, [_vp, _vp, _vp, _c_i64, _c_i64, _c_i64, _c_i64, _c_i64, _c_u64,
-                               _c_int, _vp, _vp, _vp, _vp, _vp]),
+                               _c_int, _c_int, _vp, _vp, _vp, _vp, _vp]),
     "tsvd": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _vp, _vp, _vp, _vp, _vp]),
     "tsvd_randomized": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_int, _c_int, _c_int, _c_u64,
-                                 _vp, _vp, _vp, _vp, _vp]),
+                                 _vp, _vp, _vp, _vp, _vp, _vp]),
     "tcomplete_svt": (_c_int, [_vp, _vp, _c_i64, _c_i64, _c_i64, _c_int, _dbl, _dbl,
                                _vp, _vp, _vp, _vp, _vp, _vp]),
     "tcx": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_i64, _c_u64, _c_int, _vp, _vp, _vp, _vp,
@@ -86,8 +88,8 @@ _SIGS = {
     "tp_rdft3": (_c_int, [_vp, _c_i64, _c_i64, _vp, _vp, _vp]),
     "tp_irdft3": (_c_int, [_vp, _vp, _c_i64, _c_i64, _vp, _vp]),
     "tp_slice_norms": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_int, _vp, _vp, _vp]),
-    "tp_sample_draw": (_c_int, [_vp, _vp, _c_i64, _c_i64, _c_u64, _c_int, _c_u32, _vp, _vp,
-                                _vp, _vp, _vp]),
+    "tp_sample_draw": (_c_int, [_vp, _vp, _c_i64, _c_i64, _c_u64, _c_int, _c_int, _c_u32, _vp,
+                                _vp, _vp, _vp, _vp]),
     "tp_workspace_query": (ctypes.c_size_t, [_c_int, _vp, _c_int, _vp]),
     "tp_status_string": (ctypes.c_char_p, [_c_int]),
     "tp_last_error": (ctypes.c_char_p, []),
@@ -269,9 +271,10 @@ def tprod(A, B, C=None, precision=TP_FP32, status=None):
 
 
 def tprod_sampled(A, B, c, seed=0, prob_mode=TP_PROB_AB, p_given=None, precision=TP_FP32,
-                  Z=None, idx=None, count=None, status=None):
+                  Z=None, idx=None, count=None, status=None, sample_mode=TP_SAMPLE_BERNOULLI):
     """rt-product (Algorithm 2).  Returns (Z, idx int32[n2], count int64[1]);
-    idx[:count] are the kept slice indices, ascending."""
+    idx[:count] are the kept slice indices, ascending (Bernoulli) or in draw
+    order (TP_SAMPLE_IID)."""
     torch = _torch()
     n1, n2, n3 = A.shape
     n2b, n4, n3b = B.shape
@@ -291,7 +294,7 @@ def tprod_sampled(A, B, c, seed=0, prob_mode=TP_PROB_AB, p_given=None, precision
     o = _opts(TP_OP_TPROD_SAMPLED, (n1, n2, n4, n3), precision, status)
     rc = lib().tprod_sampled(_tensor_arg(A, "A"), _tensor_arg(B, "B"), _tensor_arg(Z, "Z"),
                              n1, n2, n4, n3, int(c), int(seed) & ((1 << 64) - 1), int(prob_mode),
-                             pg, _tensor_arg(idx, "idx", torch.int32),
+                             int(sample_mode), pg, _tensor_arg(idx, "idx", torch.int32),
                              _tensor_arg(count, "count", torch.int64), ctypes.byref(o), _stream())
     _check(rc, "tprod_sampled")
     return Z, idx, count
@@ -311,15 +314,22 @@ def tsvd(X, max_sweeps=0, status=None):
     return U, S, V
 
 
-def tsvd_randomized(X, k, p=10, q=2, seed=0, status=None, max_sweeps=0):
-    """Randomized tubal-rank-k t-SVD: returns (U, S, V)."""
+def tsvd_randomized(X, k, p=10, q=2, seed=0, status=None, max_sweeps=0, ranks=None):
+    """Randomized tubal-rank-k t-SVD: returns (U, S, V).  ranks: optional
+    device int32[n3 // 2 + 1] per-frequency ranks (each at most k)."""
+    torch = _torch()
     n1, n2, n3 = X.shape
+    rk = None
+    if ranks is not None:
+        if ranks.numel() != n3 // 2 + 1:
+            raise TprodError("tsvd_randomized: ranks needs n3 // 2 + 1 entries")
+        rk = _tensor_arg(ranks, "ranks", torch.int32)
     U = empty_tensor(n1, k, n3, device=X.device)
     S = empty_tensor(k, k, n3, device=X.device)
     V = empty_tensor(n2, k, n3, device=X.device)
     o = _opts(TP_OP_TSVD_RANDOMIZED, (n1, n2, n3, k, p), TP_FP32, status, max_sweeps)
     rc = lib().tsvd_randomized(_tensor_arg(X, "X"), n1, n2, n3, int(k), int(p), int(q),
-                               int(seed) & ((1 << 64) - 1), _tensor_arg(U, "U"),
+                               int(seed) & ((1 << 64) - 1), rk, _tensor_arg(U, "U"),
                                _tensor_arg(S, "S"), _tensor_arg(V, "V"), ctypes.byref(o),
                                _stream())
     _check(rc, "tsvd_randomized")
@@ -599,7 +609,7 @@ def slice_norms_noalloc(X, which, out=None):
     return out
 
 
-def sample_draw(w, w2, c, seed, prob_mode, stream_id=0):
+def sample_draw(w, w2, c, seed, prob_mode, stream_id=0, sample_mode=TP_SAMPLE_BERNOULLI):
     """Picking loop of Algorithm 2.  Returns (idx, scale, count, q)."""
     torch = _torch()
     n = w.numel()
@@ -610,7 +620,8 @@ def sample_draw(w, w2, c, seed, prob_mode, stream_id=0):
     rc = lib().tp_sample_draw(_tensor_arg(w, "w", torch.float64),
                               _tensor_arg(w2, "w2", torch.float64) if w2 is not None else None,
                               n, int(c), int(seed) & ((1 << 64) - 1), int(prob_mode),
-                              int(stream_id), _tensor_arg(idx, "idx", torch.int32),
+                              int(sample_mode), int(stream_id),
+                              _tensor_arg(idx, "idx", torch.int32),
                               _tensor_arg(scale, "scale", torch.float32),
                               _tensor_arg(count, "count", torch.int64),
                               _tensor_arg(q, "q", torch.float64), _stream())

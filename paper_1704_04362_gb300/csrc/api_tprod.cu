@@ -130,8 +130,9 @@ int tprod(const float* A, const float* B, float* C, int64_t n1, int64_t n2, int6
 }
 
 int tprod_sampled(const float* A, const float* B, float* Z, int64_t n1, int64_t n2, int64_t n4,
-                  int64_t n3, int64_t c, uint64_t seed, int prob_mode, const double* p_given,
-                  int32_t* idx_out, int64_t* count_out, const tp_opts* opts, void* stream) {
+                  int64_t n3, int64_t c, uint64_t seed, int prob_mode, int sample_mode,
+                  const double* p_given, int32_t* idx_out, int64_t* count_out,
+                  const tp_opts* opts, void* stream) {
   if (!A || !B || !Z) { set_error("tprod_sampled: NULL tensor"); return TP_ENULL; }
   if (!dims_ok({n1, n2, n3}) || !dims_ok({n2, n4, n3}) || !dims_ok({n1, n4, n3})) {
     set_error("tprod_sampled: invalid sizes");
@@ -140,6 +141,14 @@ int tprod_sampled(const float* A, const float* B, float* Z, int64_t n1, int64_t 
   if (c < 1) { set_error("tprod_sampled: c must be >= 1"); return TP_EINVAL; }
   if (prob_mode < TP_PROB_AB || prob_mode > TP_PROB_GIVEN) {
     set_error("tprod_sampled: unknown prob_mode %d", prob_mode);
+    return TP_EINVAL;
+  }
+  if (sample_mode != TP_SAMPLE_BERNOULLI && sample_mode != TP_SAMPLE_IID) {
+    set_error("tprod_sampled: unknown sample_mode %d", sample_mode);
+    return TP_EINVAL;
+  }
+  if (sample_mode == TP_SAMPLE_IID && c > n2) {
+    set_error("tprod_sampled: TP_SAMPLE_IID needs c <= n2");
     return TP_EINVAL;
   }
   if (prob_mode == TP_PROB_GIVEN && !p_given) {
@@ -180,7 +189,9 @@ int tprod_sampled(const float* A, const float* B, float* Z, int64_t n1, int64_t 
       if ((rc = launch_slice_norms(B, n2, n4, n3, 1, b2, part, st))) return rc;
   }
   const double* w = prob_mode == TP_PROB_GIVEN ? p_given : a2;
-  if ((rc = launch_draw(w, b2, n2, c, seed, prob_mode, 0u, idx, scale, cnt, nullptr, st))) return rc;
+  if ((rc = launch_draw(w, b2, n2, c, seed, prob_mode, 0u, idx, scale, cnt, nullptr, st,
+                        sample_mode)))
+    return rc;
   // S5 + S1: rescaled gathers fused into the forward transforms.
   // C_hat_k is n1 x c' (capacity n2 columns): column-major for the SIMT GEMM,
   // K-major (picked index contiguous) for the tensor cores.
@@ -229,14 +240,16 @@ int tp_slice_norms(const float* X, int64_t n1, int64_t n2, int64_t n3, int which
 }
 
 int tp_sample_draw(const double* w, const double* w2, int64_t n, int64_t c, uint64_t seed,
-                   int prob_mode, uint32_t stream_id, int32_t* idx, float* scale, int64_t* count,
-                   double* q_out, void* stream) {
+                   int prob_mode, int sample_mode, uint32_t stream_id, int32_t* idx, float* scale,
+                   int64_t* count, double* q_out, void* stream) {
   if (!w || !idx || !count) { set_error("tp_sample_draw: NULL pointer"); return TP_ENULL; }
   if (prob_mode == TP_PROB_AB && !w2) { set_error("tp_sample_draw: TP_PROB_AB needs w2"); return TP_ENULL; }
   if (prob_mode < TP_PROB_AB || prob_mode > TP_PROB_GIVEN) { set_error("tp_sample_draw: bad mode"); return TP_EINVAL; }
   if (n < 1 || n > (int64_t(1) << 31) - 1 || c < 1) { set_error("tp_sample_draw: invalid sizes"); return TP_EINVAL; }
+  if (sample_mode != TP_SAMPLE_BERNOULLI && sample_mode != TP_SAMPLE_IID) { set_error("tp_sample_draw: bad sample_mode"); return TP_EINVAL; }
+  if (sample_mode == TP_SAMPLE_IID && c > n) { set_error("tp_sample_draw: TP_SAMPLE_IID needs c <= n"); return TP_EINVAL; }
   return launch_draw(w, w2, n, c, seed, prob_mode, stream_id, idx, scale, count, q_out,
-                     as_stream(stream));
+                     as_stream(stream), sample_mode);
 }
 
 size_t tp_workspace_query(int op, const int64_t* d, int nd, const tp_opts* opts) {

@@ -610,6 +610,29 @@ __global__ void pick_topk_kernel(const double* __restrict__ gr, const double* __
   }
 }
 
+// Per-frequency truncation: columns c >= r_f of W_k (l x k), V (p x k) and the
+// diagonal of S (k x k) of frequency f are zeroed.  One block per frequency.
+__global__ void rank_mask_kernel(const int32_t* __restrict__ rank, int l, int p, int k,
+                                 float* __restrict__ wkr, float* __restrict__ wki,
+                                 float* __restrict__ vkr, float* __restrict__ vki,
+                                 float* __restrict__ sr, float* __restrict__ si) {
+  const int64_t f = blockIdx.x;
+  const int r = min(max(rank[f], 0), k);
+  if (r == k) return;
+  for (int e = threadIdx.x + l * r; e < l * k; e += blockDim.x) {
+    wkr[f * l * k + e] = 0.f;
+    wki[f * l * k + e] = 0.f;
+  }
+  for (int64_t e = threadIdx.x + int64_t(p) * r; e < int64_t(p) * k; e += blockDim.x) {
+    vkr[f * p * k + e] = 0.f;
+    vki[f * p * k + e] = 0.f;
+  }
+  for (int c = threadIdx.x + r; c < k; c += blockDim.x) {
+    sr[f * k * k + c + int64_t(k) * c] = 0.f;
+    si[f * k * k + c + int64_t(k) * c] = 0.f;
+  }
+}
+
 __global__ void to_double_kernel(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n;
        e += int64_t(gridDim.x) * blockDim.x)
@@ -659,10 +682,12 @@ __global__ void diag_kernel(const float* __restrict__ sr, int k, int64_t h, floa
 }  // namespace
 
 // sig_out non-null: only the core singular values of every frequency are
-// wanted (descending, h x k, float32); U, S, V are not formed.
+// wanted (descending, h x k, float32); U, S, V are not formed.  rank_per_freq
+// non-null (device int32[h]): frequency f keeps its top min(max(r_f, 0), k)
+// triplets, the others are zero.
 int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, int q,
              uint64_t seed, float* U, float* S, float* V, const tp_opts* opts, cudaStream_t st,
-             float* sig_out) {
+             float* sig_out, const int32_t* rank_per_freq) {
   const int64_t h = half_len(n3);
   const int64_t l = k + p;
   Arena ws;
@@ -779,6 +804,14 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
       diag_kernel<<<unsigned((h * k + 255) / 256), 256, 0, st>>>(Sr, k, h, sig_out);
     }
     return launch_status("diag_kernel");
+  }
+  if (rank_per_freq) {
+    {
+      KernelScope ks("rank_mask", st);
+      rank_mask_kernel<<<unsigned(h), 256, 0, st>>>(rank_per_freq, int(l), int(n2), k, Wkr, Wki,
+                                                    Vr, Vi, Sr, Si);
+    }
+    if ((rc = launch_status("rank_mask_kernel"))) return rc;
   }
   if ((rc = gemm(Yr, Yi, n1, l, Wkr, Wki, k, Ur, Ui))) return rc;    // U_hat = Q W_k
   if ((rc = launch_irdft(Ur, Ui, n1 * k, n1 * k, n3, U, st))) return rc;

@@ -202,6 +202,105 @@ __global__ void __launch_bounds__(1024) draw_kernel(const double* __restrict__ w
   if (tid == 0) *count = base_s;
 }
 
+__device__ __forceinline__ uint64_t uniform53_iid(uint64_t t, uint32_t stream_id, uint64_t seed) {
+  uint32_t c[4] = {uint32_t(t), uint32_t(t >> 32), stream_id, 1u};
+  philox4x32_10(c, uint32_t(seed), uint32_t(seed >> 32));
+  return (uint64_t(c[0] >> 5) << 26) | uint64_t(c[1] >> 6);
+}
+
+// p_j of the i.i.d. draws and its integer weight floor(p_j 2^53) (p clipped to
+// [0, 1], NaN to 0).  One out-of-line function so that every use rounds alike.
+__device__ __noinline__ double iid_p(const double* w, const double* w2, int mode, double total,
+                                    int64_t j) {
+  double p;
+  if (mode == TP_PROB_GIVEN) p = w[j];
+  else p = (total > 0.0) ? weight(w, w2, mode, j) / total : 0.0;
+  if (!(p > 0.0)) p = 0.0;
+  return p < 1.0 ? p : 1.0;
+}
+
+// c independent draws with replacement (the with-replacement sampling that
+// Algorithm 2 reduces to at n3 = 1, Drineas, Kannan and Mahoney 2006), in
+// integers so that the oracle given the same float64 p draws the same
+// indices: W_j = floor(p_j 2^53), draw t takes the 53-bit U_t of counter
+// (t, stream, 1) and the first j whose inclusive prefix sum of W exceeds
+// floor(U_t sum(W) / 2^53).  Thread i owns the contiguous chunk
+// [i L, (i + 1) L) of the indices; the exact uint64 chunk sums are scanned in
+// shared memory, a draw binary-searches the chunk and walks it.  One block of
+// 1024 threads; no workspace.  scale_t = 1/sqrt(c p_j); q_out[j] = c p_j.
+__global__ void __launch_bounds__(1024) draw_iid_kernel(const double* __restrict__ w,
+                                                        const double* __restrict__ w2, int64_t n,
+                                                        int64_t c, uint64_t seed, int mode,
+                                                        uint32_t stream_id,
+                                                        int32_t* __restrict__ idx,
+                                                        float* __restrict__ scale,
+                                                        int64_t* __restrict__ count,
+                                                        double* __restrict__ q_out) {
+  __shared__ double red[1024];
+  __shared__ uint64_t csum[1024];
+  const int tid = threadIdx.x;
+  double total = 1.0;
+  if (mode != TP_PROB_GIVEN) {
+    double a = 0.0;
+    for (int64_t j = tid; j < n; j += 1024) a += weight(w, w2, mode, j);
+    red[tid] = a;
+    __syncthreads();
+    for (int s = 512; s > 0; s >>= 1) {
+      if (tid < s) red[tid] += red[tid + s];
+      __syncthreads();
+    }
+    total = red[0];
+  }
+  const int64_t L = (n + 1023) / 1024;
+  const int64_t j0 = int64_t(tid) * L, j1 = j0 + L < n ? j0 + L : n;
+  uint64_t own = 0;
+  for (int64_t j = j0; j < j1; ++j) {
+    const double p = iid_p(w, w2, mode, total, j);
+    own += uint64_t(p * 9007199254740992.0);
+    if (q_out) q_out[j] = double(c) * p;
+  }
+  csum[tid] = own;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {   // inclusive scan (exact in uint64)
+    const uint64_t v = tid >= o ? csum[tid - o] : 0;
+    __syncthreads();
+    csum[tid] += v;
+    __syncthreads();
+  }
+  const uint64_t W = csum[1023];
+  if (W == 0) {
+    if (tid == 0) *count = 0;
+    return;
+  }
+  for (int64_t t = tid; t < c; t += 1024) {
+    const uint64_t U = uniform53_iid(uint64_t(t), stream_id, seed);
+    const uint64_t lo = U * W, hi = __umul64hi(U, W);
+    const uint64_t target = (hi << 11) | (lo >> 53);   // floor(U W / 2^53) < W
+    int a = 0, b = 1023;                                 // first chunk with csum > target
+    while (a < b) {
+      const int m = (a + b) >> 1;
+      if (csum[m] > target) b = m;
+      else a = m + 1;
+    }
+    uint64_t run = a > 0 ? csum[a - 1] : 0;
+    const int64_t k0 = int64_t(a) * L, k1 = k0 + L < n ? k0 + L : n;
+    int64_t j = k1 - 1;
+    double pj = 0.0;
+    for (int64_t k = k0; k < k1; ++k) {
+      const double p = iid_p(w, w2, mode, total, k);
+      run += uint64_t(p * 9007199254740992.0);
+      if (run > target) {
+        j = k;
+        pj = p;
+        break;
+      }
+    }
+    idx[t] = int32_t(j);
+    if (scale) scale[t] = float(1.0 / sqrt(double(c) * pj));
+  }
+  if (tid == 0) *count = c;
+}
+
 }  // namespace
 
 size_t norms_partial_count(int64_t n1, int64_t n2, int64_t n3, int which) {
@@ -248,7 +347,15 @@ int launch_slice_norms(const float* X, int64_t n1, int64_t n2, int64_t n3, int w
 
 int launch_draw(const double* w, const double* w2, int64_t n, int64_t c, uint64_t seed,
                 int mode, uint32_t stream_id, int32_t* idx, float* scale, int64_t* count,
-                double* q_out, cudaStream_t st) {
+                double* q_out, cudaStream_t st, int sample_mode) {
+  if (sample_mode == TP_SAMPLE_IID) {
+    {
+      KernelScope ks("draw_iid", st);
+      draw_iid_kernel<<<1, 1024, 0, st>>>(w, w2, n, c, seed, mode, stream_id, idx, scale, count,
+                                          q_out);
+    }
+    return launch_status("draw_iid_kernel");
+  }
   {
     KernelScope ks("draw", st);
     draw_kernel<<<1, 1024, 0, st>>>(w, w2, n, c, seed, mode, stream_id, idx, scale, count, q_out);

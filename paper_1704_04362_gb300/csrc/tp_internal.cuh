@@ -103,8 +103,9 @@ int launch_slice_norms(const float* X, int64_t n1, int64_t n2, int64_t n3, int w
                        double* out, double* partial, cudaStream_t st);
 
 // Picking loop of Algorithm 2 (see tp_sample_draw in tprod.h).
+// sample_mode TP_SAMPLE_IID: c independent draws with replacement instead.
 int launch_draw(const double* w, const double* w2, int64_t n, int64_t c, uint64_t seed,
                 int mode, uint32_t stream_id, int32_t* idx, float* scale, int64_t* count,
-                double* q_out, cudaStream_t st);
+                double* q_out, cudaStream_t st, int sample_mode = TP_SAMPLE_BERNOULLI);
 
 }  // namespace tp

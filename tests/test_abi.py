@@ -47,10 +47,13 @@ def test_null_and_size_errors_need_no_gpu(L):
     p = ctypes.c_void_p(16)  # never dereferenced: validation fails first
     assert L.tprod(p, p, p, 0, 2, 2, 2, nul, nul) == -1
     assert L.tprod(p, p, p, 2, -1, 2, 2, nul, nul) == -1
-    assert L.tprod_sampled(p, p, p, 2, 2, 2, 2, 0, 0, 0, nul, nul, nul, nul, nul) == -1  # c = 0
-    assert L.tprod_sampled(p, p, p, 2, 2, 2, 2, 1, 0, 7, nul, nul, nul, nul, nul) == -1  # mode
-    assert L.tprod_sampled(p, p, p, 2, 2, 2, 2, 1, 0, 2, nul, nul, nul, nul, nul) == -2  # p_given
-    assert L.tp_sample_draw(nul, nul, 4, 1, 0, 0, 0, nul, nul, nul, nul, nul) == -2
+    assert L.tprod_sampled(p, p, p, 2, 2, 2, 2, 0, 0, 0, 0, nul, nul, nul, nul, nul) == -1  # c = 0
+    assert L.tprod_sampled(p, p, p, 2, 2, 2, 2, 1, 0, 7, 0, nul, nul, nul, nul, nul) == -1  # mode
+    assert L.tprod_sampled(p, p, p, 2, 2, 2, 2, 1, 0, 2, 0, nul, nul, nul, nul, nul) == -2  # p_given
+    assert L.tprod_sampled(p, p, p, 2, 2, 2, 2, 1, 0, 0, 5, nul, nul, nul, nul, nul) == -1  # sample
+    assert L.tprod_sampled(p, p, p, 2, 2, 2, 2, 3, 0, 0, 1, nul, nul, nul, nul, nul) == -1  # c > n2
+    assert L.tp_sample_draw(nul, nul, 4, 1, 0, 0, 0, 0, nul, nul, nul, nul, nul) == -2
+    assert L.tp_sample_draw(p, nul, 4, 1, 0, 1, 2, 0, p, nul, p, nul, nul) == -1     # sample
     assert L.tp_slice_norms(p, 2, 2, 2, 5, p, nul, nul) == -1
     t = [nul] * 8
     assert L.tcur(nul, 2, 2, 2, 1, 1, 0, 0, 1, nul, nul, p, *t) == -2      # A

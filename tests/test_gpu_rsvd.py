@@ -95,3 +95,31 @@ def test_breakdown_is_flagged_not_hung():
     tp.tsvd_randomized(dev(X), 3, 2, 1, seed=0, status=st)
     torch.cuda.synchronize()
     assert int(st.item()) & 0x2
+
+
+def test_per_frequency_ranks_match_oracle():
+    # a spectrum with clear gaps at every rank used (tubal rank 6 with
+    # decaying factors): each frequency keeps its own r_f <= 6
+    import torch
+    n1, n2, n3, k, p, q = 48, 40, 10, 6, 4, 1
+    X = synth.lowrank_np(n1, n2, n3, 6, seed=21)
+    h = n3 // 2 + 1
+    ranks = np.array([6, 2, 0, 4, 1, 3], dtype=np.int32)
+    rk = torch.from_numpy(ranks).cuda()
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    U, S, V = tp.tsvd_randomized(dev(X), k, p, q, seed=5, status=st, ranks=rk)
+    assert int(st.item()) == 0
+    Om = philox_ref.sketch_signs(n2, k + p, h, n3, 5)
+    Ur, Sr, Vr = decomp_ref.tsvd_randomized(X.astype(np.float64), k, p, q, Om, ranks=ranks)
+    s, sr = sing_vals(to_np(S)), sing_vals(Sr)
+    for f in range(h):            # zero in the Fourier domain up to the round trip of S
+        assert np.all(np.abs(s[ranks[f]:, f]) < 1e-6 * s.max())
+    assert rel_fro(s, sr) < TOL_FP32
+    # the truncated approximations agree (each frequency's top r_f subspace is
+    # separated from the rest)
+    assert rel_fro(approx(to_np(U), to_np(S), to_np(V)), approx(Ur, Sr, Vr)) < TOL_FP32
+    # ranks = k everywhere is the plain call
+    U2, S2, V2 = tp.tsvd_randomized(dev(X), k, p, q, seed=5,
+                                    ranks=torch.full((h,), k, dtype=torch.int32, device="cuda"))
+    U0, S0, V0 = tp.tsvd_randomized(dev(X), k, p, q, seed=5)
+    assert torch.equal(U2, U0) and torch.equal(S2, S0) and torch.equal(V2, V0)

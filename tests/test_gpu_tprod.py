@@ -154,3 +154,59 @@ def test_tprod_sampled_given_p_and_nothing_kept():
     assert rel_fro(to_np(Z), Zref) < TOL_FP32
     Z0, _, c0 = tp.tprod_sampled(dev(np.zeros_like(A)), dev(B), 3, seed=5)
     assert int(c0.item()) == 0 and float(Z0.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("n,c,seed", [(1, 1, 0), (7, 5, 1), (1000, 300, 2), (5000, 4096, 3),
+                                      (70000, 1000, 4)])
+def test_iid_draw_bit_exact_given_p(n, c, seed):
+    import torch
+    g = np.random.default_rng(seed)
+    w = g.gamma(0.5, 1.0, n)
+    w[g.random(n) < 0.2] = 0.0                     # zero weights are never drawn
+    if w.sum() == 0:
+        w[0] = 1.0
+    p = w / w.sum()
+    pt = torch.from_numpy(p).cuda()
+    idx, scale, count, q = tp.sample_draw(pt, None, c, seed, tp.TP_PROB_GIVEN,
+                                          sample_mode=tp.TP_SAMPLE_IID)
+    ref_idx, ref_s = sampling_ref.draw_iid(p, c, seed)
+    assert int(count.item()) == c == len(ref_idx)
+    assert np.array_equal(idx[:c].cpu().numpy(), ref_idx)
+    np.testing.assert_allclose(scale[:c].cpu().numpy(), 1 / np.sqrt(ref_s), rtol=1e-7)
+    np.testing.assert_allclose(q.cpu().numpy(), c * p, rtol=1e-15)
+    # the norm modes draw the oracle's indices from the same weights
+    wt = torch.from_numpy(w).cuda()
+    idx2, _, count2, _ = tp.sample_draw(wt, None, c, seed, tp.TP_PROB_A2,
+                                        sample_mode=tp.TP_SAMPLE_IID)
+    ref2, _ = sampling_ref.draw_iid(sampling_ref.probabilities(w, None, sampling_ref.PROB_A2), c, seed)
+    assert np.array_equal(idx2[:c].cpu().numpy(), ref2)
+
+
+def test_iid_draw_edge_cases():
+    import torch
+    z = torch.zeros(10, dtype=torch.float64, device="cuda")
+    idx, scale, count, q = tp.sample_draw(z, z, 3, 0, tp.TP_PROB_AB, sample_mode=tp.TP_SAMPLE_IID)
+    assert int(count.item()) == 0
+    one = torch.zeros(10, dtype=torch.float64, device="cuda")
+    one[6] = 1.0
+    idx, scale, count, q = tp.sample_draw(one, None, 10, 5, tp.TP_PROB_GIVEN,
+                                          sample_mode=tp.TP_SAMPLE_IID)
+    assert int(count.item()) == 10 and idx.tolist() == [6] * 10
+    assert torch.allclose(scale, torch.full_like(scale, 10 ** -0.5))
+    with pytest.raises(tp.TprodError):
+        tp.sample_draw(one, None, 11, 5, tp.TP_PROB_GIVEN, sample_mode=tp.TP_SAMPLE_IID)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+@pytest.mark.parametrize("n1,n2,n4,n3,c", [(64, 48, 32, 16, 12), (50, 300, 41, 7, 60),
+                                           (33, 130, 20, 64, 130), (260, 500, 300, 8, 100)])
+def test_tprod_sampled_iid_matches_oracle(n1, n2, n4, n3, c, prec):
+    A = synth.lowrank_np(n1, n2, n3, 4, seed=16, noise=0.01)
+    B = synth.lowrank_np(n2, n4, n3, 4, seed=17, noise=0.01)
+    st = status_word()
+    Z, idx, count = tp.tprod_sampled(dev(A), dev(B), c, seed=321, precision=prec, status=st,
+                                     sample_mode=tp.TP_SAMPLE_IID)
+    assert int(st.item()) == 0 and int(count.item()) == c
+    Zref, ref_idx, _ = sampling_ref.tprod_sampled(A, B, c, 321, sample=sampling_ref.SAMPLE_IID)
+    assert np.array_equal(idx[:c].cpu().numpy(), ref_idx)
+    assert rel_fro(to_np(Z), Zref) < tol_for(prec)

@@ -332,3 +332,25 @@ def test_cur_tnn_recovers_low_rank_plus_sparse_from_sampled_slices():
     assert len(ci) < 50 and len(ri) < 60
     err = np.linalg.norm(L - L0) / np.linalg.norm(L0)
     assert err < 1e-3, err
+
+
+def test_per_frequency_ranks_give_the_multi_rank_truncation():
+    # with l = n2 the sketch is exact: frequency f truncated to r_f leaves
+    # exactly the per-slice Eckart-Young error sum_{i > r_f} s_i^2 (counted
+    # twice for the conjugate slices), against the exact t-SVD
+    from oracle import decomp_ref as D, philox_ref as P
+    g = np.random.default_rng(73)
+    X = g.standard_normal((10, 8, 6))
+    h = 4
+    Om = P.sketch_signs(8, 8, h, 6, 2)
+    ranks = np.array([3, 1, 0, 5])
+    U, S, V = D.tsvd_randomized(X, 6, 2, 1, Om, ranks=ranks)
+    from oracle.tensor_ref import tprod, ttranspose
+    R = tprod(tprod(U, S), ttranspose(V))
+    s_exact = [np.linalg.svd(np.fft.fft(X, axis=2)[:, :, f], compute_uv=False) for f in range(h)]
+    w = [1, 2, 2, 1]
+    err = sum(w[f] * np.sum(s_exact[f][ranks[f]:] ** 2) for f in range(h)) / 6
+    assert abs(np.linalg.norm(X - R) ** 2 - err) < 1e-9 * np.linalg.norm(X) ** 2
+    U0, S0, V0 = D.tsvd_randomized(X, 6, 2, 1, Om)
+    Uf, Sf, Vf = D.tsvd_randomized(X, 6, 2, 1, Om, ranks=np.full(h, 6))
+    assert np.array_equal(U0, Uf) and np.array_equal(S0, Sf)
