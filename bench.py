@@ -347,6 +347,78 @@ def bench_svt_batched(tp, torch, count=256, warm_iters=3):
                     "tensors (8 side streams)"}
 
 
+def orthonormal_tube_tensor(torch, n1, r, n3, seed):
+    """U (n1 x r x n3, float32) with U^T * U = I, distributed as the top-r
+    left singular tensor of a dense N(0, 1) tensor: per Fourier slice the Q
+    factor of a Gaussian matrix (a uniformly random r-dimensional subspace),
+    real at the real slices, conjugate-symmetric elsewhere."""
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    h = n3 // 2 + 1
+    Uh = torch.zeros(n3, n1, r, dtype=torch.complex128, device="cuda")
+    for f in range(h):
+        real = f == 0 or (n3 % 2 == 0 and f == n3 // 2)
+        G = torch.randn(n1, r, device="cuda", generator=g, dtype=torch.float64)
+        if not real:
+            G = torch.complex(G, torch.randn(n1, r, device="cuda", generator=g,
+                                             dtype=torch.float64))
+        Q, _ = torch.linalg.qr(G)
+        Uh[f] = Q.to(torch.complex128)
+        if 0 < f < n3 - f:
+            Uh[n3 - f] = Q.conj()
+    U = torch.fft.ifft(Uh, dim=0).real                       # fft(U) slice f = Q_f
+    return U.permute(1, 2, 0).float()                        # logical (n1, r, n3)
+
+
+def bench_table1(tp, torch, configs=((100, 460), (200, 1000), (300, 1700), (400, 2500),
+                                      (500, 3100)), n1=100000, n3=5):
+    """The shape of the paper's tensor-multiplication experiment (its Table
+    1): U_r^T * U_r for an orthonormal n1 x r x n3 tensor U_r (n1 = 10^5,
+    n3 = 5; the left singular tensor of dense N(0, 1) data), exactly (tprod)
+    and by the rt-product with l picked slices under the norm probabilities
+    of Section 3.1 (the leverage of U_r's rows) and uniform ones.
+    RFE = ||I - U~^T U~||_F / ||U_r||_F^2 and RSE = ||I - U~^T U~||_2 /
+    ||U_r||_2^2 (the spectral norm of a tensor is the largest over its
+    Fourier slices; the slices of U~^T U~ are Hermitian, so it is the largest
+    eigenvalue modulus, taken on the host), averaged over 10 seeds."""
+    out = []
+    for (r, l) in configs:
+        t_setup = time.perf_counter()
+        U = orthonormal_tube_tensor(torch, n1, r, n3, seed=r)
+        Ut = U.permute(1, 0, 2)                                     # slices transposed
+        Ut = torch.roll(torch.flip(Ut, dims=[2]), 1, dims=2)        # slices 2..n3 reversed
+        Ut = tp.as_tprod_layout(Ut.contiguous())
+        Ud = tp.as_tprod_layout(U)
+        I = torch.zeros(r, r, n3, device="cuda")
+        I[:, :, 0] = torch.eye(r, device="cuda")
+        unif = torch.full((n1,), 1.0 / n1, dtype=torch.float64, device="cuda")
+
+        def errs(Z):
+            D = (Z - I).permute(2, 0, 1).double()
+            Dh = torch.fft.fft(D, dim=0)[: n3 // 2 + 1].cpu().numpy()
+            rfe = float(torch.linalg.vector_norm(D)) / r
+            rse = max(float(np.abs(np.linalg.eigvalsh(0.5 * (M + M.conj().T))).max()) for M in Dh)
+            return rfe, rse
+        setup_s = time.perf_counter() - t_setup
+        t_exact = time_gpu(lambda: tp.tprod(Ut, Ud, precision=tp.TP_BF16X3), 3, torch)
+        exact_err = errs(tp.tprod(Ut, Ud, precision=tp.TP_BF16X3))
+        row = {"r": r, "l": l, "tprod_ms": t_exact, "tprod_rfe": exact_err[0], "setup_s": setup_s}
+        for name, kw in (("nonuniform", {"prob_mode": tp.TP_PROB_AB}),
+                         ("uniform", {"prob_mode": tp.TP_PROB_GIVEN, "p_given": unif})):
+            t = time_gpu(lambda: tp.tprod_sampled(Ut, Ud, l, seed=0, precision=tp.TP_BF16X3,
+                                                  **kw), 3, torch)
+            e = [errs(tp.tprod_sampled(Ut, Ud, l, seed=s, precision=tp.TP_BF16X3, **kw)[0])
+                 for s in range(10)]
+            row[name] = {"ms": t, "rfe": float(np.mean([x[0] for x in e])),
+                         "rse": float(np.mean([x[1] for x in e]))}
+        out.append(row)
+        del U, Ut, Ud
+        torch.cuda.empty_cache()
+    return {"workload": f"U_r^T * U_r, U_r {n1} x r x {n3} orthonormal (heavy-tailed row "
+                        "leverage), BF16x3, errors averaged over 10 seeds",
+            "cases": out}
+
+
 def bench_learned(torch, train_count=192, eval_shape=(1024, 1024, 64),
                   alphas=(1.5, 2.0, 2.5, 3.0, 3.5, 4.0)):
     """The learned sketch-size predictor against the plain adaptive method
@@ -696,6 +768,7 @@ def main():
         rows = bench_rows(tp, torch, with_cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
         rows["completion_batched"] = bench_svt_batched(tp, torch)
         rows["learned_rank"] = bench_learned(torch)
+        rows["table1_shape"] = bench_table1(tp, torch)
 
     if rank == 0:
         line = {

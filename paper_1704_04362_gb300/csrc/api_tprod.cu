@@ -78,7 +78,8 @@ size_t sampled_ws(int64_t n1, int64_t n2, int64_t n4, int64_t n3, int prec) {
   if (p2 > part) part = p2;
   return 2 * ws_bytes(size_t(n2), 8) + ws_bytes(part, 8) + ws_bytes(size_t(n2), 4) +
          ws_bytes(size_t(n2), 4) + ws_bytes(1, 8) + planes_bytes(size_t(lk) * n1 * h, tc) +
-         planes_bytes(size_t(lk) * n4 * h, tc) + 2 * ws_bytes(size_t(n1) * n4 * h, 4);
+         planes_bytes(size_t(lk) * n4 * h, tc) + 2 * ws_bytes(size_t(n1) * n4 * h, 4) +
+         draw_scratch_bytes(n2);
 }
 
 }  // namespace
@@ -179,6 +180,7 @@ int tprod_sampled(const float* A, const float* B, float* Z, int64_t n1, int64_t 
   Planes Rh = take_planes(ws, size_t(lk) * n4 * h, tc);
   float* Zr = ws.take<float>(size_t(n1) * n4 * h);
   float* Zi = ws.take<float>(size_t(n1) * n4 * h);
+  char* dscr = ws.take<char>(draw_scratch_bytes(n2));
   int32_t* idx = idx_out ? idx_out : idx_ws;
   int64_t* cnt = count_out ? count_out : cnt_ws;
 
@@ -189,7 +191,7 @@ int tprod_sampled(const float* A, const float* B, float* Z, int64_t n1, int64_t 
       if ((rc = launch_slice_norms(B, n2, n4, n3, 1, b2, part, st))) return rc;
   }
   const double* w = prob_mode == TP_PROB_GIVEN ? p_given : a2;
-  if ((rc = launch_draw(w, b2, n2, c, seed, prob_mode, 0u, idx, scale, cnt, nullptr, st,
+  if ((rc = launch_draw(w, b2, n2, c, seed, prob_mode, 0u, idx, scale, cnt, nullptr, dscr, st,
                         sample_mode)))
     return rc;
   // S5 + S1: rescaled gathers fused into the forward transforms.
@@ -248,7 +250,10 @@ int tp_sample_draw(const double* w, const double* w2, int64_t n, int64_t c, uint
   if (n < 1 || n > (int64_t(1) << 31) - 1 || c < 1) { set_error("tp_sample_draw: invalid sizes"); return TP_EINVAL; }
   if (sample_mode != TP_SAMPLE_BERNOULLI && sample_mode != TP_SAMPLE_IID) { set_error("tp_sample_draw: bad sample_mode"); return TP_EINVAL; }
   if (sample_mode == TP_SAMPLE_IID && c > n) { set_error("tp_sample_draw: TP_SAMPLE_IID needs c <= n"); return TP_EINVAL; }
-  return launch_draw(w, w2, n, c, seed, prob_mode, stream_id, idx, scale, count, q_out,
+  Arena ws;
+  int rc = acquire_workspace(nullptr, draw_scratch_bytes(n), &ws);
+  if (rc) return rc;
+  return launch_draw(w, w2, n, c, seed, prob_mode, stream_id, idx, scale, count, q_out, ws.base,
                      as_stream(stream), sample_mode);
 }
 

@@ -131,52 +131,102 @@ __device__ __forceinline__ double weight(const double* w, const double* w2, int 
   return w[j];
 }
 
-// One block of 1024 threads.  Deterministic float64 normaliser: each thread
-// sums a strided subsequence in order, then a fixed tree over threads.
-__global__ void __launch_bounds__(1024) draw_kernel(const double* __restrict__ w,
-                                                    const double* __restrict__ w2, int64_t n,
-                                                    int64_t c, uint64_t seed, int mode,
-                                                    uint32_t stream_id, int32_t* __restrict__ idx,
-                                                    float* __restrict__ scale,
-                                                    int64_t* __restrict__ count,
-                                                    double* __restrict__ q_out) {
-  __shared__ double red[1024];
+// The picking loop runs in three launches so that the float64 work (square
+// roots, divisions; GB300's float64 rate is a small fraction of its float32
+// rate) is spread over every SM and only integer compaction stays in one
+// block:
+//   1. draw_sum_kernel: per-block sums of the weights (fixed order);
+//   2. draw_decide_kernel: every block adds the block sums in block order
+//      (the same total everywhere), then per index j the probability p_j,
+//      q_j = min{1, c p_j} and the Philox coin; the decision is parked in
+//      idx[j] (1 picked, 0 not) and 1/sqrt(q_j) in scale[j];
+//   3. draw_compact_kernel (one block): the picked j, ascending, packed to
+//      the front of idx and scale in place (a chunk is read completely
+//      before any of its positions is written, and positions never pass j).
+// The i.i.d. mode replaces 2-3 by iid_weights_kernel (W_j = floor(p_j 2^53)
+// and 1/sqrt(c p_j) per j, in parallel) and iid_draw_kernel (one block,
+// integer chunk sums, scan and searches).
+constexpr int kDrawBlocks = 608;
+
+int draw_blocks(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  if (g > kDrawBlocks) g = kDrawBlocks;
+  return g < 1 ? 1 : int(g);
+}
+
+__device__ __forceinline__ double block_sum256(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (int(threadIdx.x) < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  return red[0];
+}
+
+__global__ void __launch_bounds__(256) draw_sum_kernel(const double* __restrict__ w,
+                                                       const double* __restrict__ w2, int64_t n,
+                                                       int mode, double* __restrict__ bpart) {
+  __shared__ double red[256];
+  double a = 0.0;
+  for (int64_t j = int64_t(blockIdx.x) * 256 + threadIdx.x; j < n; j += int64_t(gridDim.x) * 256)
+    a += weight(w, w2, mode, j);
+  const double t = block_sum256(a, red);
+  if (threadIdx.x == 0) bpart[blockIdx.x] = t;
+}
+
+__device__ __forceinline__ double draw_total(const double* bpart, int G, int mode) {
+  __shared__ double tot;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    if (mode != TP_PROB_GIVEN)
+      for (int b = 0; b < G; ++b) s += bpart[b];
+    tot = s;
+  }
+  __syncthreads();
+  return tot;
+}
+
+// p_j from the weights (mode) and the total.
+__device__ __forceinline__ double draw_p(const double* w, const double* w2, int mode,
+                                         double total, int64_t j) {
+  if (mode == TP_PROB_GIVEN) return w[j];
+  return (total > 0.0) ? weight(w, w2, mode, j) / total : 0.0;
+}
+
+__global__ void __launch_bounds__(256) draw_decide_kernel(
+    const double* __restrict__ w, const double* __restrict__ w2, int64_t n, int64_t c,
+    uint64_t seed, int mode, uint32_t stream_id, const double* __restrict__ bpart, int G,
+    int32_t* __restrict__ idx, float* __restrict__ scale, double* __restrict__ q_out) {
+  const double total = draw_total(bpart, G, mode);
+  const double cd = double(c);
+  for (int64_t j = int64_t(blockIdx.x) * 256 + threadIdx.x; j < n; j += int64_t(gridDim.x) * 256) {
+    double q = fmin(1.0, cd * draw_p(w, w2, mode, total, j));
+    if (!(q > 0.0)) q = 0.0;   // also maps NaN to 0
+    const uint64_t Q = uint64_t(q * 9007199254740992.0);   // floor(q 2^53), q in [0,1]
+    const bool pick = uniform53(uint64_t(j), stream_id, seed) < Q;
+    idx[j] = pick ? 1 : 0;
+    if (scale) scale[j] = pick ? float(1.0 / sqrt(q)) : 0.f;
+    if (q_out) q_out[j] = q;
+  }
+}
+
+__global__ void __launch_bounds__(1024) draw_compact_kernel(int64_t n, int32_t* __restrict__ idx,
+                                                            float* __restrict__ scale,
+                                                            int64_t* __restrict__ count) {
   __shared__ int wsum[32];
   __shared__ int64_t base_s;
   const int tid = threadIdx.x;
-  double total = 1.0;
-  if (mode != TP_PROB_GIVEN) {
-    double a = 0.0;
-    for (int64_t j = tid; j < n; j += 1024) a += weight(w, w2, mode, j);
-    red[tid] = a;
-    __syncthreads();
-    for (int s = 512; s > 0; s >>= 1) {
-      if (tid < s) red[tid] += red[tid + s];
-      __syncthreads();
-    }
-    total = red[0];
-  }
+  const int lane = tid & 31, wid = tid >> 5;
   if (tid == 0) base_s = 0;
   __syncthreads();
-  const double cd = double(c);
-  const int lane = tid & 31, wid = tid >> 5;
   for (int64_t j0 = 0; j0 < n; j0 += 1024) {
     const int64_t j = j0 + tid;
-    bool pick = false;
-    double q = 0.0;
-    if (j < n) {
-      double p;
-      if (mode == TP_PROB_GIVEN) p = w[j];
-      else p = (total > 0.0) ? weight(w, w2, mode, j) / total : 0.0;
-      q = fmin(1.0, cd * p);
-      if (!(q > 0.0)) q = 0.0;   // also maps NaN to 0
-      const uint64_t Q = uint64_t(q * 9007199254740992.0);   // floor(q 2^53), q in [0,1]
-      pick = uniform53(uint64_t(j), stream_id, seed) < Q;
-      if (q_out) q_out[j] = q;
-    }
+    const bool pick = j < n && idx[j] != 0;
+    const float sv = (pick && scale) ? scale[j] : 0.f;
     const unsigned ball = __ballot_sync(0xffffffffu, pick);
     if (lane == 0) wsum[wid] = __popc(ball);
-    __syncthreads();
+    __syncthreads();   // also: the whole chunk has been read
     if (wid == 0) {
       int v = wsum[lane];
       int incl = v;
@@ -192,10 +242,9 @@ __global__ void __launch_bounds__(1024) draw_kernel(const double* __restrict__ w
     if (pick) {
       const int64_t pos = base + wsum[wid] + __popc(ball & ((1u << lane) - 1u));
       idx[pos] = int32_t(j);
-      if (scale) scale[pos] = float(1.0 / sqrt(q));
+      if (scale) scale[pos] = sv;
     }
     __syncthreads();   // every thread has used base_s and wsum
-    // running total = prefix before warp 31 plus warp 31's own picks
     if (wid == 31 && lane == 0) base_s = base + wsum[31] + __popc(ball);
     __syncthreads();
   }
@@ -208,57 +257,44 @@ __device__ __forceinline__ uint64_t uniform53_iid(uint64_t t, uint32_t stream_id
   return (uint64_t(c[0] >> 5) << 26) | uint64_t(c[1] >> 6);
 }
 
-// p_j of the i.i.d. draws and its integer weight floor(p_j 2^53) (p clipped to
-// [0, 1], NaN to 0).  One out-of-line function so that every use rounds alike.
-__device__ __noinline__ double iid_p(const double* w, const double* w2, int mode, double total,
-                                    int64_t j) {
-  double p;
-  if (mode == TP_PROB_GIVEN) p = w[j];
-  else p = (total > 0.0) ? weight(w, w2, mode, j) / total : 0.0;
-  if (!(p > 0.0)) p = 0.0;
-  return p < 1.0 ? p : 1.0;
+// i.i.d. draws, pass 2: p_j clipped to [0, 1] (NaN to 0), its integer weight
+// W_j = floor(p_j 2^53), the rescale 1/sqrt(c p_j) and q_out[j] = c p_j.
+__global__ void __launch_bounds__(256) iid_weights_kernel(
+    const double* __restrict__ w, const double* __restrict__ w2, int64_t n, int64_t c, int mode,
+    const double* __restrict__ bpart, int G, uint64_t* __restrict__ W, float* __restrict__ sval,
+    double* __restrict__ q_out) {
+  const double total = draw_total(bpart, G, mode);
+  for (int64_t j = int64_t(blockIdx.x) * 256 + threadIdx.x; j < n; j += int64_t(gridDim.x) * 256) {
+    double p = draw_p(w, w2, mode, total, j);
+    if (!(p > 0.0)) p = 0.0;
+    if (p > 1.0) p = 1.0;
+    W[j] = uint64_t(p * 9007199254740992.0);
+    sval[j] = p > 0.0 ? float(1.0 / sqrt(double(c) * p)) : 0.f;
+    if (q_out) q_out[j] = double(c) * p;
+  }
 }
 
-// c independent draws with replacement (the with-replacement sampling that
-// Algorithm 2 reduces to at n3 = 1, Drineas, Kannan and Mahoney 2006), in
-// integers so that the oracle given the same float64 p draws the same
-// indices: W_j = floor(p_j 2^53), draw t takes the 53-bit U_t of counter
-// (t, stream, 1) and the first j whose inclusive prefix sum of W exceeds
-// floor(U_t sum(W) / 2^53).  Thread i owns the contiguous chunk
+// i.i.d. draws, pass 3 (one block of 1024): c independent draws with
+// replacement (the with-replacement sampling Algorithm 2 reduces to at
+// n3 = 1, Drineas, Kannan and Mahoney 2006) in integers, so that the oracle
+// given the same float64 p draws the same indices: draw t takes the 53-bit
+// U_t of counter (t, stream, 1) and the first j whose inclusive prefix sum of
+// W exceeds floor(U_t sum(W) / 2^53).  Thread i owns the contiguous chunk
 // [i L, (i + 1) L) of the indices; the exact uint64 chunk sums are scanned in
-// shared memory, a draw binary-searches the chunk and walks it.  One block of
-// 1024 threads; no workspace.  scale_t = 1/sqrt(c p_j); q_out[j] = c p_j.
-__global__ void __launch_bounds__(1024) draw_iid_kernel(const double* __restrict__ w,
-                                                        const double* __restrict__ w2, int64_t n,
-                                                        int64_t c, uint64_t seed, int mode,
+// shared memory, a draw binary-searches the chunks and walks one.
+__global__ void __launch_bounds__(1024) iid_draw_kernel(int64_t n, int64_t c, uint64_t seed,
                                                         uint32_t stream_id,
+                                                        const uint64_t* __restrict__ W,
+                                                        const float* __restrict__ sval,
                                                         int32_t* __restrict__ idx,
                                                         float* __restrict__ scale,
-                                                        int64_t* __restrict__ count,
-                                                        double* __restrict__ q_out) {
-  __shared__ double red[1024];
+                                                        int64_t* __restrict__ count) {
   __shared__ uint64_t csum[1024];
   const int tid = threadIdx.x;
-  double total = 1.0;
-  if (mode != TP_PROB_GIVEN) {
-    double a = 0.0;
-    for (int64_t j = tid; j < n; j += 1024) a += weight(w, w2, mode, j);
-    red[tid] = a;
-    __syncthreads();
-    for (int s = 512; s > 0; s >>= 1) {
-      if (tid < s) red[tid] += red[tid + s];
-      __syncthreads();
-    }
-    total = red[0];
-  }
   const int64_t L = (n + 1023) / 1024;
   const int64_t j0 = int64_t(tid) * L, j1 = j0 + L < n ? j0 + L : n;
   uint64_t own = 0;
-  for (int64_t j = j0; j < j1; ++j) {
-    const double p = iid_p(w, w2, mode, total, j);
-    own += uint64_t(p * 9007199254740992.0);
-    if (q_out) q_out[j] = double(c) * p;
-  }
+  for (int64_t j = j0; j < j1; ++j) own += W[j];
   csum[tid] = own;
   __syncthreads();
   for (int o = 1; o < 1024; o <<= 1) {   // inclusive scan (exact in uint64)
@@ -267,15 +303,15 @@ __global__ void __launch_bounds__(1024) draw_iid_kernel(const double* __restrict
     csum[tid] += v;
     __syncthreads();
   }
-  const uint64_t W = csum[1023];
-  if (W == 0) {
+  const uint64_t tot = csum[1023];
+  if (tot == 0) {
     if (tid == 0) *count = 0;
     return;
   }
   for (int64_t t = tid; t < c; t += 1024) {
     const uint64_t U = uniform53_iid(uint64_t(t), stream_id, seed);
-    const uint64_t lo = U * W, hi = __umul64hi(U, W);
-    const uint64_t target = (hi << 11) | (lo >> 53);   // floor(U W / 2^53) < W
+    const uint64_t lo = U * tot, hi = __umul64hi(U, tot);
+    const uint64_t target = (hi << 11) | (lo >> 53);   // floor(U tot / 2^53) < tot
     int a = 0, b = 1023;                                 // first chunk with csum > target
     while (a < b) {
       const int m = (a + b) >> 1;
@@ -285,18 +321,15 @@ __global__ void __launch_bounds__(1024) draw_iid_kernel(const double* __restrict
     uint64_t run = a > 0 ? csum[a - 1] : 0;
     const int64_t k0 = int64_t(a) * L, k1 = k0 + L < n ? k0 + L : n;
     int64_t j = k1 - 1;
-    double pj = 0.0;
     for (int64_t k = k0; k < k1; ++k) {
-      const double p = iid_p(w, w2, mode, total, k);
-      run += uint64_t(p * 9007199254740992.0);
+      run += W[k];
       if (run > target) {
         j = k;
-        pj = p;
         break;
       }
     }
     idx[t] = int32_t(j);
-    if (scale) scale[t] = float(1.0 / sqrt(double(c) * pj));
+    if (scale) scale[t] = sval[j];
   }
   if (tid == 0) *count = c;
 }
@@ -345,22 +378,33 @@ int launch_slice_norms(const float* X, int64_t n1, int64_t n2, int64_t n3, int w
   return launch_status("slice_norms");
 }
 
+size_t draw_scratch_bytes(int64_t n) {
+  return ws_bytes(kDrawBlocks, 8) + ws_bytes(size_t(n), 8) + ws_bytes(size_t(n), 4);
+}
+
 int launch_draw(const double* w, const double* w2, int64_t n, int64_t c, uint64_t seed,
                 int mode, uint32_t stream_id, int32_t* idx, float* scale, int64_t* count,
-                double* q_out, cudaStream_t st, int sample_mode) {
-  if (sample_mode == TP_SAMPLE_IID) {
-    {
-      KernelScope ks("draw_iid", st);
-      draw_iid_kernel<<<1, 1024, 0, st>>>(w, w2, n, c, seed, mode, stream_id, idx, scale, count,
-                                          q_out);
-    }
-    return launch_status("draw_iid_kernel");
-  }
+                double* q_out, void* scratch, cudaStream_t st, int sample_mode) {
+  const int G = draw_blocks(n);
+  char* sp = static_cast<char*>(scratch);
+  double* bpart = reinterpret_cast<double*>(sp);
+  const bool iid = sample_mode == TP_SAMPLE_IID;
   {
-    KernelScope ks("draw", st);
-    draw_kernel<<<1, 1024, 0, st>>>(w, w2, n, c, seed, mode, stream_id, idx, scale, count, q_out);
+    KernelScope ks(iid ? "draw_iid" : "draw", st);
+    if (mode != TP_PROB_GIVEN) draw_sum_kernel<<<G, 256, 0, st>>>(w, w2, n, mode, bpart);
+    if (iid) {
+      uint64_t* W = reinterpret_cast<uint64_t*>(sp + ws_bytes(kDrawBlocks, 8));
+      float* sval = reinterpret_cast<float*>(sp + ws_bytes(kDrawBlocks, 8) + ws_bytes(size_t(n), 8));
+      iid_weights_kernel<<<G, 256, 0, st>>>(w, w2, n, c, mode, bpart, G, W, sval, q_out);
+      iid_draw_kernel<<<1, 1024, 0, st>>>(n, c, seed, stream_id, W, sval, idx, scale, count);
+    } else {
+      draw_decide_kernel<<<G, 256, 0, st>>>(w, w2, n, c, seed, mode, stream_id, bpart, G, idx,
+                                            scale, q_out);
+      draw_compact_kernel<<<1, 1024, 0, st>>>(n, idx, scale, count);
+    }
   }
-  return launch_status("draw_kernel");
+  note_launches(mode != TP_PROB_GIVEN ? 2 : 1);
+  return launch_status(iid ? "draw_iid" : "draw");
 }
 
 }  // namespace tp

@@ -429,6 +429,7 @@ size_t tcur_ws(int64_t n1, int64_t n2, int64_t n3) {
          + ws_bytes(N1, 8)                                     // row probabilities
          + 2 * ws_bytes(N1 * N2 * h, 4)                        // C_hat (c' <= n2)
          + 2 * ws_bytes(N1 * N2 * h, 4)                        // R_hat (l' <= n1)
+         + draw_scratch_bytes(n1 > n2 ? n1 : n2)
          + cur_bufs_ws(n1, n2, n3);
 }
 
@@ -454,6 +455,7 @@ int tcur_run(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, int6
   float* Ci = ws.take<float>(size_t(n1) * n2 * h);
   float* Rr = ws.take<float>(size_t(n1) * n2 * h);
   float* Ri = ws.take<float>(size_t(n1) * n2 * h);
+  char* dscr = ws.take<char>(draw_scratch_bytes(n1 > n2 ? n1 : n2));
   const CurBufs b = cur_carve(ws, n1, n2, n3);
   int32_t* cidx = col_idx ? col_idx : cidx_ws;
   int64_t* ccnt = col_count ? col_count : ccnt_ws;
@@ -467,7 +469,8 @@ int tcur_run(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, int6
   if (prob_mode == TP_PROB_A2)
     if ((rc = launch_slice_norms(A, n1, n2, n3, 0, a2, part, st))) return rc;
   const double* w = prob_mode == TP_PROB_GIVEN ? p_cols : a2;
-  if ((rc = launch_draw(w, nullptr, n2, c, seed, prob_mode, 0u, cidx, cscale, ccnt, nullptr, st)))
+  if ((rc = launch_draw(w, nullptr, n2, c, seed, prob_mode, 0u, cidx, cscale, ccnt, nullptr, dscr,
+                        st)))
     return rc;
   int64_t cp = 0;
   if ((rc = read_count(ccnt, &cp, "tcur: reading the number of picked lateral slices failed", st)))
@@ -496,7 +499,7 @@ int tcur_run(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, int6
   }
   // 4. horizontal picks (stream 1)
   if ((rc = launch_draw(prow, nullptr, n1, l, seed, TP_PROB_GIVEN, 1u, ridx, rscale, rcnt, nullptr,
-                        st)))
+                        dscr, st)))
     return rc;
   int64_t lp = 0;
   if ((rc = read_count(rcnt, &lp, "tcur: reading the number of picked horizontal slices failed",
@@ -526,6 +529,7 @@ size_t cur_tnn_ws(int64_t n1, int64_t n2, int64_t n3) {
          + 2 * svt_ws(n1, n2, n3)                        // the two ADMM workspaces
          + 2 * ws_bytes(N1 * N2 * h, 4)                        // C~_hat
          + 2 * ws_bytes(N1 * N2 * h, 4)                        // R~_hat
+         + draw_scratch_bytes(n1 > n2 ? n1 : n2)
          + cur_bufs_ws(n1, n2, n3);
 }
 
@@ -563,6 +567,7 @@ int cur_tnn_run(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int
   float* Chi = ws.take<float>(size_t(n1) * n2 * h);
   float* Rhr = ws.take<float>(size_t(n1) * n2 * h);
   float* Rhi = ws.take<float>(size_t(n1) * n2 * h);
+  char* dscr = ws.take<char>(draw_scratch_bytes(n1 > n2 ? n1 : n2));
   const CurBufs b = cur_carve(ws, n1, n2, n3);
   int32_t* cidx = col_idx ? col_idx : cidx_ws;
   int64_t* ccnt = col_count ? col_count : ccnt_ws;
@@ -587,7 +592,8 @@ int cur_tnn_run(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int
   if (prob_mode == TP_PROB_A2)
     if ((rc = launch_slice_norms(Xd, n1, n2, n3, 0, a2, part, st))) return rc;
   const double* w = prob_mode == TP_PROB_GIVEN ? p_cols : a2;
-  if ((rc = launch_draw(w, nullptr, n2, c, seed, prob_mode, 0u, cidx, cscale, ccnt, nullptr, st)))
+  if ((rc = launch_draw(w, nullptr, n2, c, seed, prob_mode, 0u, cidx, cscale, ccnt, nullptr, dscr,
+                        st)))
     return rc;
   int64_t cp = 0;
   if ((rc = read_count(ccnt, &cp, "cur_tnn: reading the number of picked lateral slices failed",
@@ -623,7 +629,7 @@ int cur_tnn_run(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int
   }
   // 4. horizontal picks (stream 1), R = the picked rows (not rescaled)
   if ((rc = launch_draw(prow, nullptr, n1, l, seed, TP_PROB_GIVEN, 1u, ridx, rscale, rcnt, nullptr,
-                        st)))
+                        dscr, st)))
     return rc;
   int64_t lp = 0;
   if ((rc = read_count(rcnt, &lp,

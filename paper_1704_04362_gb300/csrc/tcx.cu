@@ -104,7 +104,8 @@ size_t tcx_ws(int64_t n1, int64_t n2, int64_t n3) {
          + ws_bytes(size_t(n2) * h, 8) + ws_bytes(h, 4)
          + 4 * ws_bytes(size_t(n1) * m * h, 4)     // U_r and U_r^H
          + 2 * ws_bytes(m * n2 * h, 4)             // U_r^H A_hat
-         + 2 * ws_bytes(size_t(n1) * n2 * h, 4);   // Z_hat
+         + 2 * ws_bytes(size_t(n1) * n2 * h, 4)    // Z_hat
+         + draw_scratch_bytes(n2);
 }
 
 int tcx_run(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, uint64_t seed,
@@ -147,13 +148,15 @@ int tcx_run(const float* A, int64_t n1, int64_t n2, int64_t n3, int64_t c, uint6
   float* Ti = ws.take<float>(size_t(m_cap) * n2 * h);
   float* Zr = ws.take<float>(size_t(n1) * n2 * h);
   float* Zi = ws.take<float>(size_t(n1) * n2 * h);
+  char* dscr = ws.take<char>(draw_scratch_bytes(n2));
   int32_t* idx = idx_out ? idx_out : idx_ws;
   int64_t* cnt = count_out ? count_out : cnt_ws;
 
   if (prob_mode == TP_PROB_A2)
     if ((rc = launch_slice_norms(A, n1, n2, n3, 0, a2, part, st))) return rc;
   const double* w = prob_mode == TP_PROB_GIVEN ? p_given : a2;
-  if ((rc = launch_draw(w, nullptr, n2, c, seed, prob_mode, 0u, idx, scale, cnt, nullptr, st)))
+  if ((rc = launch_draw(w, nullptr, n2, c, seed, prob_mode, 0u, idx, scale, cnt, nullptr, dscr,
+                        st)))
     return rc;
   int64_t cprime = 0;
   if (cudaMemcpyAsync(&cprime, cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||

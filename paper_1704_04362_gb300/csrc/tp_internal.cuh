@@ -104,8 +104,12 @@ int launch_slice_norms(const float* X, int64_t n1, int64_t n2, int64_t n3, int w
 
 // Picking loop of Algorithm 2 (see tp_sample_draw in tprod.h).
 // sample_mode TP_SAMPLE_IID: c independent draws with replacement instead.
+// idx must hold n entries (the decisions are parked there before packing);
+// scratch: draw_scratch_bytes(n) bytes of device memory, 256-byte aligned.
+size_t draw_scratch_bytes(int64_t n);
 int launch_draw(const double* w, const double* w2, int64_t n, int64_t c, uint64_t seed,
                 int mode, uint32_t stream_id, int32_t* idx, float* scale, int64_t* count,
-                double* q_out, cudaStream_t st, int sample_mode = TP_SAMPLE_BERNOULLI);
+                double* q_out, void* scratch, cudaStream_t st,
+                int sample_mode = TP_SAMPLE_BERNOULLI);
 
 }  // namespace tp

@@ -136,6 +136,17 @@ def decompose(X, w16=None, seed=0):
     return r, L_PLAIN, True
 
 
+def factorize(X, w16=None, seed=0):
+    """The multi-rank factorisation X ~ U * S * V^T: per-frequency ranks from
+    decompose(), then the randomized t-SVD with the same sketch size (k the
+    largest rank, p the rest of the sketch, q = 2) truncating every
+    frequency to its own rank.  Returns (U, S, V, ranks, sketch size)."""
+    r, l, _ = decompose(X, w16, seed)
+    k = max(1, int(r.max().item()))
+    U, S, V = tp.tsvd_randomized(X, k, l - k, Q_PLAIN, seed=seed, ranks=r.int().contiguous())
+    return U, S, V, r, l
+
+
 def truncation_error(s, ranks, n3):
     """Relative error of the per-frequency best rank-r_k approximation, from
     the exact spectra s (h x m): frequencies other than 0 and n3/2 count

@@ -7,6 +7,7 @@ than the plain method's 50 columns where the spectra decay fast."""
 import numpy as np
 import pytest
 
+import paper_1704_04362_gb300 as tp
 from paper_1704_04362_gb300 import predictor as P
 from paper_1704_04362_gb300 import synth
 
@@ -45,3 +46,22 @@ def test_learned_matches_plain_error_with_smaller_sketches(trained, alpha):
         assert e_learn <= 1.05 * e_plain + 2e-3, (alpha, s, e_learn, e_plain, l, fell_back)
     if alpha >= 2.5:
         assert np.mean(sizes) < 40, sizes       # fast decay: smaller sketches than 50
+
+
+def test_multi_rank_factorisation_reaches_the_rule_error(trained):
+    # U * S * V^T with every frequency truncated to the predicted-and-judged
+    # rank: its error is the per-frequency truncation error of those ranks
+    # (up to the sketch's resolution of the tail)
+    import torch
+    w16 = trained[0]
+    X, spec = synth.spectral_torch(144, 128, 16, 3.0, 0.3, 9100)
+    U, S, V, r, l = P.factorize(X, w16, seed=1)
+    assert U.shape[1] == int(r.max().item()) and l <= 50
+    # t-product U * S * V^T through the library's own exact t-product
+    Vt = torch.flip(V.permute(1, 0, 2), dims=[2])
+    Vt = torch.roll(Vt, 1, dims=2)                     # (V^T): transpose slices, reverse 2..n3
+    US = tp.tprod(tp.as_tprod_layout(U), tp.as_tprod_layout(S))
+    R = tp.tprod(US, tp.as_tprod_layout(Vt.contiguous()))
+    err = float(torch.linalg.vector_norm(R - X) / torch.linalg.vector_norm(X))
+    want = P.truncation_error(spec, r, 16)
+    assert want * (1 - 1e-4) <= err <= 1.05 * want + 2e-3, (err, want)
