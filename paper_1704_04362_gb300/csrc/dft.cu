@@ -370,7 +370,12 @@ int launch_rdft_kc(const DftGather& g, cudaStream_t st) {
     cudaFuncSetAttribute(rdft_t_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     const int64_t bx = (g.rows + TR - 1) / TR;
     if (bx > 0x7fffffff) { set_error("rdft: too many rows"); return TP_EINVAL; }
+    // the column tiles are walked grid-stride: with all rows live (no row
+    // gather) about 16 blocks per SM suffice, and a column gather's capacity
+    // can far exceed the picked count
     int64_t by = (g.cols + TCOL - 1) / TCOL;
+    const int64_t by_cap = bx >= 152 * 16 ? 1 : 152 * 16 / bx;
+    if (g.gather_dim != 1 && by > by_cap) by = by_cap;
     if (by > 65535) by = 65535;
     {
       KernelScope ks("rdft_t", st);
@@ -385,7 +390,9 @@ int launch_rdft_kc(const DftGather& g, cudaStream_t st) {
   cudaFuncSetAttribute(rdft_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   const int64_t bx = (g.rows + RB * TPT - 1) / (RB * TPT);
   if (bx > 0x7fffffff) { set_error("rdft: too many rows"); return TP_EINVAL; }
-  const int64_t by = g.cols < 65535 ? g.cols : 65535;
+  int64_t by = g.cols < 65535 ? g.cols : 65535;   // columns walked grid-stride
+  const int64_t by_cap = bx >= 152 * 16 ? 1 : 152 * 16 / bx;
+  if (g.gather_dim == 2 && by > by_cap) by = by_cap;   // see the transposed form
   {
     KernelScope ks("rdft", st);
     rdft_kernel<KC><<<dim3(unsigned(bx), unsigned(by)), RB, smem, st>>>(g, stage);

@@ -5,9 +5,9 @@
 // Norms stream the tensor once with coalesced loads.  Each lane keeps its
 // running sum of squares as an unevaluated float pair (hi + lo, Dekker's
 // two-sum with the exact FMA square residual), so that the result carries
-// about 44 significant bits at float32 speed; lanes, warps and partial blocks
-// are then combined in float64 in a fixed order, making every norm
-// deterministic run to run.
+// about 44 significant bits at float32 speed; the lanes of a column are
+// combined as float pairs, partial sums in float64, all in a fixed order,
+// making every norm deterministic run to run.
 #include "tp_internal.cuh"
 
 namespace tp {
@@ -23,34 +23,53 @@ __device__ __forceinline__ void acc_sq(float& hi, float& lo, float x) {
   lo += err + e;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+// (h, l) += (h2, l2) for unevaluated float pairs: Knuth's two-sum of the
+// high parts, the low parts added to its error, then renormalised so that
+// |l| <= ulp(h) / 2.
+__device__ __forceinline__ void pair_add(float& h, float& l, float h2, float l2) {
+  const float s = h + h2;
+  const float bp = s - h;
+  const float e = ((h - (s - bp)) + (h2 - bp)) + (l + l2);
+  h = s + e;
+  l = e - (h - s);
 }
 
-// Lateral: one warp per column s of the n1 x (n2*n3) matrix; column s is the
-// contiguous segment (j, t) with s = j + n2*t.  partial[s] = sum_i X(i,s)^2.
+// Lateral: a group of LC lanes per column s of the n1 x (n2*n3) matrix
+// (32 / LC columns per warp, so that short columns still keep every lane
+// loading); column s is the contiguous segment (j, t) with s = j + n2*t.
+// partial[s] = sum_i X(i,s)^2.  Every lane of a warp runs the same number of
+// iterations (the shuffles need them all).
+template <int LC>
 __global__ void lateral_partial_kernel(const float* __restrict__ X, int64_t n1, int64_t ncols,
                                        bool vec4, double* __restrict__ partial) {
+  constexpr int G = 32 / LC;
   const int lane = threadIdx.x & 31;
+  const int sub = lane & (LC - 1), grp = lane / LC;
   const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t s = warp; s < ncols; s += nwarps) {
-    const float* col = X + s * n1;
+  for (int64_t s0 = warp * G; s0 < ncols; s0 += nwarps * G) {
+    const int64_t s = s0 + grp;
     float hi = 0.f, lo = 0.f;
-    if (vec4) {
-      const float4* c4 = reinterpret_cast<const float4*>(col);
-      const int64_t n4 = n1 >> 2;
-      for (int64_t i = lane; i < n4; i += 32) {
-        const float4 v = __ldg(c4 + i);
-        acc_sq(hi, lo, v.x); acc_sq(hi, lo, v.y); acc_sq(hi, lo, v.z); acc_sq(hi, lo, v.w);
+    if (s < ncols) {
+      const float* col = X + s * n1;
+      if (vec4) {
+        const float4* c4 = reinterpret_cast<const float4*>(col);
+        const int64_t n4 = n1 >> 2;
+#pragma unroll 4
+        for (int64_t i = sub; i < n4; i += LC) {
+          const float4 v = __ldg(c4 + i);
+          acc_sq(hi, lo, v.x); acc_sq(hi, lo, v.y); acc_sq(hi, lo, v.z); acc_sq(hi, lo, v.w);
+        }
+      } else {
+        for (int64_t i = sub; i < n1; i += LC) acc_sq(hi, lo, __ldg(col + i));
       }
-    } else {
-      for (int64_t i = lane; i < n1; i += 32) acc_sq(hi, lo, __ldg(col + i));
     }
-    const double v = warp_sum(double(hi) + double(lo));
-    if (lane == 0) partial[s] = v;
+    // combine the lanes' float pairs in float32 (float64 arithmetic runs at a
+    // small fraction of the float32 rate on this part); one conversion per column
+#pragma unroll
+    for (int o = LC / 2; o > 0; o >>= 1)
+      pair_add(hi, lo, __shfl_xor_sync(0xffffffffu, hi, o), __shfl_xor_sync(0xffffffffu, lo, o));
+    if (sub == 0 && s < ncols) partial[s] = double(hi) + double(lo);
   }
 }
 
@@ -60,7 +79,8 @@ __global__ void lateral_reduce_kernel(const double* __restrict__ partial, int64_
   for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n2;
        j += int64_t(gridDim.x) * blockDim.x) {
     double a = 0.0;
-    for (int64_t t = 0; t < n3; ++t) a += partial[j + n2 * t];
+#pragma unroll 8
+    for (int64_t t = 0; t < n3; ++t) a += partial[j + n2 * t];   // loads batched, adds in order
     out[j] = a;
   }
 }
@@ -76,12 +96,12 @@ __global__ void horizontal_partial_kernel(const float* __restrict__ X, int64_t n
   const int64_t s1 = min(ncols, s0 + chunk);
   float hi = 0.f, lo = 0.f;
   int64_t s = s0;
-  for (; s + 4 <= s1; s += 4) {
-    const float a = __ldg(X + i + n1 * s);
-    const float b = __ldg(X + i + n1 * (s + 1));
-    const float c = __ldg(X + i + n1 * (s + 2));
-    const float d = __ldg(X + i + n1 * (s + 3));
-    acc_sq(hi, lo, a); acc_sq(hi, lo, b); acc_sq(hi, lo, c); acc_sq(hi, lo, d);
+  for (; s + 8 <= s1; s += 8) {   // eight loads in flight per thread
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = __ldg(X + i + n1 * (s + u));
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc_sq(hi, lo, v[u]);
   }
   for (; s < s1; ++s) acc_sq(hi, lo, __ldg(X + i + n1 * s));
   partial[g * n1 + i] = double(hi) + double(lo);
@@ -92,14 +112,21 @@ __global__ void horizontal_reduce_kernel(const double* __restrict__ partial, int
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n1;
        i += int64_t(gridDim.x) * blockDim.x) {
     double a = 0.0;
-    for (int64_t g = 0; g < G; ++g) a += partial[g * n1 + i];
+#pragma unroll 8
+    for (int64_t g = 0; g < G; ++g) a += partial[g * n1 + i];   // loads batched, adds in order
     out[i] = a;
   }
 }
 
 int64_t horizontal_chunks(int64_t n1, int64_t ncols) {
+  // about four waves of 8 blocks per SM, so that the last wave's tail is
+  // short, while the G n1 partial sums stay within 2^20 doubles (8 MiB) unless
+  // one wave alone needs more
   const int64_t bx = (n1 + 255) / 256;
-  int64_t G = (152 * 8 + bx - 1) / bx;
+  const int64_t one_wave = (152 * 8 + bx - 1) / bx;
+  int64_t G = (152 * 8 * 4 + bx - 1) / bx;
+  const int64_t fit = (int64_t(1) << 20) / n1;
+  if (G > fit) G = fit > one_wave ? fit : one_wave;
   if (G > ncols) G = ncols;
   if (G < 1) G = 1;
   if (G > 65535) G = 65535;
@@ -346,12 +373,25 @@ int launch_slice_norms(const float* X, int64_t n1, int64_t n2, int64_t n3, int w
   const int64_t ncols = n2 * n3;
   if (which == 0) {
     const bool vec4 = (n1 % 4 == 0) && aligned16(X);
-    int64_t blocks = (ncols * 32 + 255) / 256;
+    // lanes per column: about three loads each, a power of two up to 32
+    const int64_t loads = vec4 ? n1 / 4 : n1;
+    int lc = 32;
+    while (lc > 1 && int64_t(lc) * 3 > loads) lc >>= 1;
+    const int64_t warps = (ncols + (32 / lc) - 1) / (32 / lc);
+    int64_t blocks = (warps * 32 + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
     {
       KernelScope ks("norms_lateral", st);
-      lateral_partial_kernel<<<unsigned(blocks), 256, 0, st>>>(X, n1, ncols, vec4, partial);
+      const unsigned b = unsigned(blocks);
+      switch (lc) {
+        case 32: lateral_partial_kernel<32><<<b, 256, 0, st>>>(X, n1, ncols, vec4, partial); break;
+        case 16: lateral_partial_kernel<16><<<b, 256, 0, st>>>(X, n1, ncols, vec4, partial); break;
+        case 8: lateral_partial_kernel<8><<<b, 256, 0, st>>>(X, n1, ncols, vec4, partial); break;
+        case 4: lateral_partial_kernel<4><<<b, 256, 0, st>>>(X, n1, ncols, vec4, partial); break;
+        case 2: lateral_partial_kernel<2><<<b, 256, 0, st>>>(X, n1, ncols, vec4, partial); break;
+        default: lateral_partial_kernel<1><<<b, 256, 0, st>>>(X, n1, ncols, vec4, partial); break;
+      }
     }
     int64_t rb = (n2 + 255) / 256;
     if (rb > 152 * 8) rb = 152 * 8;
