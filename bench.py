@@ -789,6 +789,8 @@ def main():
             "compare": compare,
             "secondary": rsvd,
             "rows": rows,
+            "autotune": [{"key": k, "choice": c, "candidates": n, "ms": b, "default_ms": d}
+                         for (k, c, n, b, d) in tp.autotune_table()],
         }
         print(json.dumps(line))
     if dist:

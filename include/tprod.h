@@ -428,6 +428,36 @@ int tp_release(void);
 uint64_t tp_launch_count(void);
 int tp_version(void);
 
+/* Launch-shape autotuner.  Tunable launches (the tile width of the direct
+ * DFT contractions, the blocks per SM of the register FFTs and of the
+ * lateral norm pass) offer candidate shapes that compute bit-identical
+ * results.  With tuning on (the default; environment variable TP_AUTOTUNE=0
+ * at load switches it off) the first call with a given problem shape times
+ * every candidate on the caller's stream (CUDA events; the call synchronises
+ * that stream once) and keeps the fastest; later calls reuse it.  A stream
+ * being captured into a CUDA graph is never timed (cached choice or the
+ * default).
+ *   tp_autotune_mode     TP_TUNE_OFF / TP_TUNE_ON; any other value only
+ *                        queries.  Returns the previous mode.
+ *   tp_autotune_force    every tunable launch takes candidate `candidate`
+ *                        (clamped to its count); -1 ends forcing.  For tests.
+ *                        Returns the previous setting.
+ *   tp_autotune_count / tp_autotune_entry  list the table: key text
+ *                        ("op:dims"), chosen and candidate count, its time
+ *                        and the default's (ms per launch; -1 if loaded).
+ *   tp_autotune_save / tp_autotune_load  one "key choice" line per entry.
+ *   tp_autotune_reset    empties the table.                                  */
+#define TP_TUNE_OFF 0
+#define TP_TUNE_ON 1
+int tp_autotune_mode(int mode);
+int tp_autotune_force(int candidate);
+int tp_autotune_count(void);
+int tp_autotune_entry(int i, char* key, int key_len, int* choice, int* ncand, double* best_ms,
+                      double* default_ms);
+int tp_autotune_save(const char* path);
+int tp_autotune_load(const char* path);
+int tp_autotune_reset(void);
+
 /* Per-kernel timing.  Between tp_profile_start() and tp_profile_stop() every
  * kernel launch of this library is bracketed by a CUDA event pair recorded on
  * the launch stream.  tp_profile_stop() synchronises the device and adds the

@@ -25,6 +25,8 @@ __all__ = [
     "profile_start", "profile_stop", "slice_norms_noalloc", "tcomplete_svt_batched",
     "sketch_spectrum", "rank_rule", "rank_features", "mlp_param_count", "mlp_round",
     "mlp_forward", "mlp_train_step", "trpca_admm", "tcur", "cur_tnn",
+    "TP_TUNE_OFF", "TP_TUNE_ON", "autotune_mode", "autotune_force", "autotune_table",
+    "autotune_save", "autotune_load", "autotune_reset",
 ]
 
 TP_FP32, TP_TF32X3, TP_BF16X3 = 0, 1, 2
@@ -94,6 +96,13 @@ _SIGS = {
     "tp_status_string": (ctypes.c_char_p, [_c_int]),
     "tp_last_error": (ctypes.c_char_p, []),
     "tp_release": (_c_int, []),
+    "tp_autotune_mode": (_c_int, [_c_int]),
+    "tp_autotune_force": (_c_int, [_c_int]),
+    "tp_autotune_count": (_c_int, []),
+    "tp_autotune_entry": (_c_int, [_c_int, _vp, _c_int, _vp, _vp, _vp, _vp]),
+    "tp_autotune_save": (_c_int, [ctypes.c_char_p]),
+    "tp_autotune_load": (_c_int, [ctypes.c_char_p]),
+    "tp_autotune_reset": (_c_int, []),
     "tp_launch_count": (_c_u64, []),
     "tp_version": (_c_int, []),
     "tp_profile_start": (_c_int, []),
@@ -134,6 +143,50 @@ def lib():
 
 def exported_symbols():
     return list(_SIGS)
+
+
+TP_TUNE_OFF, TP_TUNE_ON = 0, 1
+
+
+def autotune_mode(mode=-1) -> int:
+    """Sets the autotuner mode (TP_TUNE_OFF / TP_TUNE_ON); returns the previous
+    one (any other value only queries)."""
+    return int(lib().tp_autotune_mode(int(mode)))
+
+
+def autotune_force(candidate=-1) -> int:
+    """Forces every tunable launch to one candidate (-1: stop forcing)."""
+    return int(lib().tp_autotune_force(int(candidate)))
+
+
+def autotune_table() -> list:
+    """[(key, choice, candidates, best ms, default ms)] of the tuned launches."""
+    L = lib()
+    out = []
+    buf = ctypes.create_string_buffer(512)
+    for i in range(int(L.tp_autotune_count())):
+        ch, nc = ctypes.c_int(), ctypes.c_int()
+        best, dflt = ctypes.c_double(), ctypes.c_double()
+        rc = L.tp_autotune_entry(i, ctypes.cast(buf, ctypes.c_void_p), 512,
+                                 ctypes.cast(ctypes.byref(ch), ctypes.c_void_p),
+                                 ctypes.cast(ctypes.byref(nc), ctypes.c_void_p),
+                                 ctypes.cast(ctypes.byref(best), ctypes.c_void_p),
+                                 ctypes.cast(ctypes.byref(dflt), ctypes.c_void_p))
+        _check(rc, "tp_autotune_entry")
+        out.append((buf.value.decode(), ch.value, nc.value, best.value, dflt.value))
+    return out
+
+
+def autotune_save(path):
+    _check(lib().tp_autotune_save(str(path).encode()), "tp_autotune_save")
+
+
+def autotune_load(path):
+    _check(lib().tp_autotune_load(str(path).encode()), "tp_autotune_load")
+
+
+def autotune_reset():
+    _check(lib().tp_autotune_reset(), "tp_autotune_reset")
 
 
 def launch_count() -> int:

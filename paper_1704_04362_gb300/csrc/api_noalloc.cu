@@ -85,7 +85,8 @@ int tp_slice_norms_noalloc(const float* X, int64_t n1, int64_t n2, int64_t n3, i
   if (rc) return rc;
   // Every partial slot the kernels read is written first in the same call,
   // so nothing in the array has to start at zero.
-  return launch_slice_norms(X, n1, n2, n3, which, out, scratch, as_stream(stream));
+  // the default launch shape: no autotuning (it would time and synchronise)
+  return launch_slice_norms(X, n1, n2, n3, which, out, scratch, as_stream(stream), false);
 }
 
 }  // extern "C"

@@ -455,11 +455,21 @@ int launch_rdft(const DftGather& g, cudaStream_t st) {
   }
   if (g.rows == 0 || g.cols == 0) return TP_OK;
   if (kRegFft && rfft_reg_supported(g.n3)) return launch_rfft_reg(g, st);
-  switch (pick_kc(g.n3 / 2 + 1)) {
-    case 8: return launch_rdft_kc<8>(g, st);
-    case 12: return launch_rdft_kc<12>(g, st);
-    default: return launch_rdft_kc<16>(g, st);
-  }
+  // tile width KC among {8, 12, 16} (each frequency sums its samples in the
+  // same order whatever the width): autotuned, default the least padding
+  const auto run = [&](int c) {
+    switch (c) {
+      case 0: return launch_rdft_kc<8>(g, st);
+      case 1: return launch_rdft_kc<12>(g, st);
+      default: return launch_rdft_kc<16>(g, st);
+    }
+  };
+  const int kc = pick_kc(g.n3 / 2 + 1);
+  const int64_t key[7] = {g.n3, g.rows, g.cols, g.gather_dim, g.out_transposed,
+                          g.out_re_lo ? 1 : 0, g.out_bf16};
+  int c = 0;
+  const int rc = autotune_pick("rdft", key, 7, 3, kc == 8 ? 0 : kc == 12 ? 1 : 2, run, st, &c);
+  return rc ? rc : run(c);
 }
 
 int launch_irdft(const float* in_re, const float* in_im, int64_t rows, int64_t in_slice,
@@ -473,11 +483,18 @@ int launch_irdft(const float* in_re, const float* in_im, int64_t rows, int64_t i
   if (rows == 0) return TP_OK;
   if (kRegFft && rfft_reg_supported(n3))
     return launch_irfft_reg(in_re, in_im, rows, in_slice, n3, out, st);
-  switch (pick_kc(n3 / 2 + 1)) {
-    case 8: return launch_irdft_kc<8>(in_re, in_im, rows, in_slice, n3, out, st);
-    case 12: return launch_irdft_kc<12>(in_re, in_im, rows, in_slice, n3, out, st);
-    default: return launch_irdft_kc<16>(in_re, in_im, rows, in_slice, n3, out, st);
-  }
+  const auto run = [&](int c) {
+    switch (c) {
+      case 0: return launch_irdft_kc<8>(in_re, in_im, rows, in_slice, n3, out, st);
+      case 1: return launch_irdft_kc<12>(in_re, in_im, rows, in_slice, n3, out, st);
+      default: return launch_irdft_kc<16>(in_re, in_im, rows, in_slice, n3, out, st);
+    }
+  };
+  const int kc = pick_kc(n3 / 2 + 1);
+  const int64_t key[2] = {n3, rows};
+  int c = 0;
+  const int rc = autotune_pick("irdft", key, 2, 3, kc == 8 ? 0 : kc == 12 ? 1 : 2, run, st, &c);
+  return rc ? rc : run(c);
 }
 
 }  // namespace tp

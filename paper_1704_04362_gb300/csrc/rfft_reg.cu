@@ -369,12 +369,13 @@ int sm_count() {
 #define TP_RFFT_OVERSUB 4
 #endif
 template <class Kernel>
-unsigned grid_for(Kernel kernel, int64_t work_blocks, size_t smem = 0) {
+unsigned grid_for(Kernel kernel, int64_t work_blocks, size_t smem = 0,
+                  int oversub = TP_RFFT_OVERSUB) {
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
-  const int64_t cap = int64_t(sm_count()) * per_sm * TP_RFFT_OVERSUB;
+  const int64_t cap = int64_t(sm_count()) * per_sm * oversub;
   const int64_t b = work_blocks < cap ? work_blocks : cap;
   return unsigned(b < 1 ? 1 : b);
 }
@@ -384,7 +385,7 @@ unsigned grid_for(Kernel kernel, int64_t work_blocks, size_t smem = 0) {
 #endif
 
 template <int N>
-int launch_fwd(const DftGather& g, cudaStream_t st) {
+int launch_fwd(const DftGather& g, cudaStream_t st, int oversub) {
   if constexpr (N <= 64) {
     if (TP_RFFT_T_STAGE && g.out_transposed && g.gather_dim != 1 && g.row_stride == 1) {
       const size_t smem = size_t(N) * SROWS * SPITCH * sizeof(float);
@@ -393,7 +394,8 @@ int launch_fwd(const DftGather& g, cudaStream_t st) {
       const int64_t tiles = (g.rows + SROWS - 1) / SROWS * ((g.cols + SCOLS - 1) / SCOLS);
       {
         KernelScope ks("rdft_t", st);
-        rfft_reg_ts_kernel<N><<<grid_for(rfft_reg_ts_kernel<N>, tiles, smem), kThreads, smem, st>>>(g);
+        rfft_reg_ts_kernel<N>
+            <<<grid_for(rfft_reg_ts_kernel<N>, tiles, smem, oversub), kThreads, smem, st>>>(g);
       }
       return launch_status("rfft_reg_ts_kernel");
     }
@@ -402,13 +404,14 @@ int launch_fwd(const DftGather& g, cudaStream_t st) {
     const int64_t tiles = (g.rows + TROWS - 1) / TROWS * ((g.cols + LC - 1) / LC);
     {
       KernelScope ks("rdft_t", st);
-      rfft_reg_t_kernel<N><<<grid_for(rfft_reg_t_kernel<N>, tiles), kThreads, 0, st>>>(g);
+      rfft_reg_t_kernel<N><<<grid_for(rfft_reg_t_kernel<N>, tiles, 0, oversub), kThreads, 0, st>>>(g);
     }
     return launch_status("rfft_reg_t_kernel");
   }
   {
     KernelScope ks("rdft", st);
-    rfft_reg_kernel<N><<<grid_for(rfft_reg_kernel<N>, (g.rows * g.cols + kThreads - 1) / kThreads),
+    rfft_reg_kernel<N><<<grid_for(rfft_reg_kernel<N>, (g.rows * g.cols + kThreads - 1) / kThreads,
+                                  0, oversub),
                          kThreads, 0, st>>>(g);
   }
   return launch_status("rfft_reg_kernel");
@@ -416,10 +419,11 @@ int launch_fwd(const DftGather& g, cudaStream_t st) {
 
 template <int N>
 int launch_inv(const float* in_re, const float* in_im, int64_t rows, int64_t in_slice, float* out,
-               cudaStream_t st) {
+               cudaStream_t st, int oversub) {
   {
     KernelScope ks("irdft", st);
-    irfft_reg_kernel<N><<<grid_for(irfft_reg_kernel<N>, (rows + kThreads - 1) / kThreads),
+    irfft_reg_kernel<N><<<grid_for(irfft_reg_kernel<N>, (rows + kThreads - 1) / kThreads, 0,
+                                   oversub),
                           kThreads, 0, st>>>(in_re, in_im, rows, in_slice, out);
   }
   return launch_status("irfft_reg_kernel");
@@ -431,35 +435,57 @@ bool rfft_reg_supported(int64_t n3) {
   return n3 >= 2 && n3 <= kTw && (n3 & (n3 - 1)) == 0;
 }
 
+// Waves of resident blocks per launch, the autotuned choice (every tube is
+// transformed alone, so the grid does not change any result).
+constexpr int kOversub[4] = {1, 2, 4, 8};
+constexpr int kOversubDefault = 2;   // TP_RFFT_OVERSUB = 4
+
 int launch_rfft_reg(const DftGather& g, cudaStream_t st) {
-  switch (g.n3) {
-    case 2: return launch_fwd<2>(g, st);
-    case 4: return launch_fwd<4>(g, st);
-    case 8: return launch_fwd<8>(g, st);
-    case 16: return launch_fwd<16>(g, st);
-    case 32: return launch_fwd<32>(g, st);
-    case 64: return launch_fwd<64>(g, st);
-    case 128: return launch_fwd<128>(g, st);
-    default:
-      set_error("register FFT: n3 = %lld is not a power of two in [2, 128]", (long long)g.n3);
-      return TP_EUNSUPPORTED;
-  }
+  const auto run = [&](int c) {
+    const int os = kOversub[c];
+    switch (g.n3) {
+      case 2: return launch_fwd<2>(g, st, os);
+      case 4: return launch_fwd<4>(g, st, os);
+      case 8: return launch_fwd<8>(g, st, os);
+      case 16: return launch_fwd<16>(g, st, os);
+      case 32: return launch_fwd<32>(g, st, os);
+      case 64: return launch_fwd<64>(g, st, os);
+      case 128: return launch_fwd<128>(g, st, os);
+      default:
+        set_error("register FFT: n3 = %lld is not a power of two in [2, 128]", (long long)g.n3);
+        return int(TP_EUNSUPPORTED);
+    }
+  };
+  if (!rfft_reg_supported(g.n3)) return run(0);
+  const int64_t key[7] = {g.n3, g.rows, g.cols, g.gather_dim, g.out_transposed,
+                          g.out_re_lo ? 1 : 0, g.out_bf16};
+  int c = kOversubDefault;
+  const int rc = autotune_pick("rfft_reg", key, 7, 4, kOversubDefault, run, st, &c);
+  return rc ? rc : run(c);
 }
 
 int launch_irfft_reg(const float* in_re, const float* in_im, int64_t rows, int64_t in_slice,
                      int64_t n3, float* out, cudaStream_t st) {
-  switch (n3) {
-    case 2: return launch_inv<2>(in_re, in_im, rows, in_slice, out, st);
-    case 4: return launch_inv<4>(in_re, in_im, rows, in_slice, out, st);
-    case 8: return launch_inv<8>(in_re, in_im, rows, in_slice, out, st);
-    case 16: return launch_inv<16>(in_re, in_im, rows, in_slice, out, st);
-    case 32: return launch_inv<32>(in_re, in_im, rows, in_slice, out, st);
-    case 64: return launch_inv<64>(in_re, in_im, rows, in_slice, out, st);
-    case 128: return launch_inv<128>(in_re, in_im, rows, in_slice, out, st);
-    default:
-      set_error("register FFT: n3 = %lld is not a power of two in [2, 128]", (long long)n3);
-      return TP_EUNSUPPORTED;
-  }
+  const auto run = [&](int c) {
+    const int os = kOversub[c];
+    switch (n3) {
+      case 2: return launch_inv<2>(in_re, in_im, rows, in_slice, out, st, os);
+      case 4: return launch_inv<4>(in_re, in_im, rows, in_slice, out, st, os);
+      case 8: return launch_inv<8>(in_re, in_im, rows, in_slice, out, st, os);
+      case 16: return launch_inv<16>(in_re, in_im, rows, in_slice, out, st, os);
+      case 32: return launch_inv<32>(in_re, in_im, rows, in_slice, out, st, os);
+      case 64: return launch_inv<64>(in_re, in_im, rows, in_slice, out, st, os);
+      case 128: return launch_inv<128>(in_re, in_im, rows, in_slice, out, st, os);
+      default:
+        set_error("register FFT: n3 = %lld is not a power of two in [2, 128]", (long long)n3);
+        return int(TP_EUNSUPPORTED);
+    }
+  };
+  if (!rfft_reg_supported(n3)) return run(0);
+  const int64_t key[3] = {n3, rows, in_slice};
+  int c = kOversubDefault;
+  const int rc = autotune_pick("irfft_reg", key, 3, 4, kOversubDefault, run, st, &c);
+  return rc ? rc : run(c);
 }
 
 }  // namespace tp

@@ -369,7 +369,8 @@ size_t norms_partial_count(int64_t n1, int64_t n2, int64_t n3, int which) {
 }
 
 int launch_slice_norms(const float* X, int64_t n1, int64_t n2, int64_t n3, int which,
-                       double* out, double* partial, cudaStream_t st) {
+                       double* out, double* partial, cudaStream_t st,
+                       bool tunable) {
   const int64_t ncols = n2 * n3;
   if (which == 0) {
     const bool vec4 = (n1 % 4 == 0) && aligned16(X);
@@ -378,21 +379,32 @@ int launch_slice_norms(const float* X, int64_t n1, int64_t n2, int64_t n3, int w
     int lc = 32;
     while (lc > 1 && int64_t(lc) * 3 > loads) lc >>= 1;
     const int64_t warps = (ncols + (32 / lc) - 1) / (32 / lc);
-    int64_t blocks = (warps * 32 + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    if (blocks < 1) blocks = 1;
-    {
-      KernelScope ks("norms_lateral", st);
-      const unsigned b = unsigned(blocks);
-      switch (lc) {
-        case 32: lateral_partial_kernel<32><<<b, 256, 0, st>>>(X, n1, ncols, vec4, partial); break;
-        case 16: lateral_partial_kernel<16><<<b, 256, 0, st>>>(X, n1, ncols, vec4, partial); break;
-        case 8: lateral_partial_kernel<8><<<b, 256, 0, st>>>(X, n1, ncols, vec4, partial); break;
-        case 4: lateral_partial_kernel<4><<<b, 256, 0, st>>>(X, n1, ncols, vec4, partial); break;
-        case 2: lateral_partial_kernel<2><<<b, 256, 0, st>>>(X, n1, ncols, vec4, partial); break;
-        default: lateral_partial_kernel<1><<<b, 256, 0, st>>>(X, n1, ncols, vec4, partial); break;
+    // blocks per SM (the grid-stride walk does not change any column's sum):
+    // autotuned among 4, 8, 16 and 32, default 16
+    const auto run = [&](int c) {
+      int64_t blocks = (warps * 32 + 255) / 256;
+      const int64_t cap = int64_t(152) * (int64_t(4) << c);
+      if (blocks > cap) blocks = cap;
+      if (blocks < 1) blocks = 1;
+      {
+        KernelScope ks("norms_lateral", st);
+        const unsigned b = unsigned(blocks);
+        switch (lc) {
+          case 32: lateral_partial_kernel<32><<<b, 256, 0, st>>>(X, n1, ncols, vec4, partial); break;
+          case 16: lateral_partial_kernel<16><<<b, 256, 0, st>>>(X, n1, ncols, vec4, partial); break;
+          case 8: lateral_partial_kernel<8><<<b, 256, 0, st>>>(X, n1, ncols, vec4, partial); break;
+          case 4: lateral_partial_kernel<4><<<b, 256, 0, st>>>(X, n1, ncols, vec4, partial); break;
+          case 2: lateral_partial_kernel<2><<<b, 256, 0, st>>>(X, n1, ncols, vec4, partial); break;
+          default: lateral_partial_kernel<1><<<b, 256, 0, st>>>(X, n1, ncols, vec4, partial); break;
+        }
       }
-    }
+      return launch_status("lateral_partial_kernel");
+    };
+    const int64_t key[3] = {n1, ncols, vec4 ? 1 : 0};
+    int c = 2;
+    int rc = tunable ? autotune_pick("norms_lateral", key, 3, 4, 2, run, st, &c) : TP_OK;
+    if (!rc) rc = run(c);
+    if (rc) return rc;
     int64_t rb = (n2 + 255) / 256;
     if (rb > 152 * 8) rb = 152 * 8;
     {

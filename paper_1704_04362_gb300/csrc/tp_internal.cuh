@@ -5,6 +5,8 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <functional>
+
 #include "../../include/tprod.h"
 
 namespace tp {
@@ -97,10 +99,12 @@ int launch_cgemm(const CGemm& g, cudaStream_t st);
 
 // Slice norms (squared, float64).  Lateral: out[j] = sum over (i,t) of X(i,j,t)^2.
 // Horizontal: out[i] = sum over (j,t) of X(i,j,t)^2.  `partial` is scratch of
-// norms_partial_count() doubles.
+// norms_partial_count() doubles.  tunable = false keeps the launch shape at
+// its default (no autotuning: no timing, no stream synchronisation).
 size_t norms_partial_count(int64_t n1, int64_t n2, int64_t n3, int which);
 int launch_slice_norms(const float* X, int64_t n1, int64_t n2, int64_t n3, int which,
-                       double* out, double* partial, cudaStream_t st);
+                       double* out, double* partial, cudaStream_t st,
+                       bool tunable = true);
 
 // Picking loop of Algorithm 2 (see tp_sample_draw in tprod.h).
 // sample_mode TP_SAMPLE_IID: c independent draws with replacement instead.
@@ -111,5 +115,12 @@ int launch_draw(const double* w, const double* w2, int64_t n, int64_t c, uint64_
                 int mode, uint32_t stream_id, int32_t* idx, float* scale, int64_t* count,
                 double* q_out, void* scratch, cudaStream_t st,
                 int sample_mode = TP_SAMPLE_BERNOULLI);
+
+// Launch-shape autotuner (autotune.cu): `launch(c)` enqueues candidate c of a
+// tunable launch on st (every candidate computes bit-identical results); the
+// chosen candidate for this op and key is returned in *choice (timed on the
+// first call, cached after; `dflt` when tuning is off or st is capturing).
+int autotune_pick(const char* op, const int64_t* key, int nkey, int ncand, int dflt,
+                  const std::function<int(int)>& launch, cudaStream_t st, int* choice);
 
 }  // namespace tp

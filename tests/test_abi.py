@@ -90,3 +90,27 @@ def test_no_cpu_fallback_without_cuda():
         pytest.skip("a GPU is present")
     with pytest.raises(tp.TprodError):
         tp.empty_tensor(2, 2, 2)
+
+
+def test_autotune_table_round_trip_needs_no_gpu(L, tmp_path):
+    prev = L.tp_autotune_mode(-1)
+    assert prev in (0, 1)
+    assert L.tp_autotune_mode(0) == prev and L.tp_autotune_mode(-1) == 0
+    L.tp_autotune_mode(prev)
+    tp.autotune_reset()
+    f = tmp_path / "tune.txt"
+    f.write_text("rdft:64,2000,4000,2,1,1,1 2\nnorms_lateral:2000,256000,1 1\n")
+    tp.autotune_load(f)
+    table = tp.autotune_table()
+    assert [(k, c) for k, c, *_ in table] == [("norms_lateral:2000,256000,1", 1),
+                                               ("rdft:64,2000,4000,2,1,1,1", 2)]
+    assert all(best == -1.0 and d == -1.0 for *_, best, d in table)   # loaded, not timed
+    g = tmp_path / "again.txt"
+    tp.autotune_save(g)
+    assert sorted(g.read_text().splitlines()) == sorted(f.read_text().splitlines())
+    (tmp_path / "bad.txt").write_text("rdft:1 x\n")
+    with pytest.raises(tp.TprodError):
+        tp.autotune_load(tmp_path / "bad.txt")
+    tp.autotune_reset()
+    assert tp.autotune_table() == []
+    assert tp.autotune_force(3) == -1 and tp.autotune_force(-1) == 3
