@@ -591,6 +591,10 @@ def main():
     ap.add_argument("--small", action="store_true", help="profiling case, not a bench number")
     ap.add_argument("--no-rsvd", action="store_true", help="skip the randomized t-SVD line")
     ap.add_argument("--no-rows", action="store_true", help="skip the t-SVD / t-CX / ADMM rows")
+    ap.add_argument("--tune-file", default=None,
+                    help="autotuner table: loaded before the run when the file exists, "
+                         "written after it (so that a profiled run reuses the plain run's "
+                         "launch shapes instead of timing them under the profiler)")
     args = ap.parse_args()
     if args.small:
         use_small_case()
@@ -612,6 +616,8 @@ def main():
     PREC = {"fp32": tp.TP_FP32, "tf32x3": tp.TP_TF32X3, "bf16x3": tp.TP_BF16X3}
     prec = PREC[args.precision]
     peaks = load_peaks()
+    if args.tune_file and os.path.exists(args.tune_file):
+        tp.autotune_load(args.tune_file)
 
     A, B = make_inputs("cuda")
     Z = tp.empty_tensor(N1, N4, N3)
@@ -793,6 +799,8 @@ def main():
                          for (k, c, n, b, d) in tp.autotune_table()],
         }
         print(json.dumps(line))
+        if args.tune_file:
+            tp.autotune_save(args.tune_file)
     if dist:
         dist.destroy_process_group()
 

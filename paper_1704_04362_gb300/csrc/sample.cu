@@ -107,14 +107,33 @@ __global__ void horizontal_partial_kernel(const float* __restrict__ X, int64_t n
   partial[g * n1 + i] = double(hi) + double(lo);
 }
 
-__global__ void horizontal_reduce_kernel(const double* __restrict__ partial, int64_t n1, int64_t G,
-                                         double* __restrict__ out) {
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n1;
-       i += int64_t(gridDim.x) * blockDim.x) {
+// out[i] = sum over the G chunk partials of row i: a block takes 32 rows,
+// its 8 warps each sum a contiguous eighth of the chunks (loads batched,
+// adds in chunk order), then warp 0 adds the eight eighths in order; the
+// same partition for a given G, so every norm is deterministic.
+__global__ void __launch_bounds__(256) horizontal_reduce_kernel(const double* __restrict__ partial,
+                                                                int64_t n1, int64_t G,
+                                                                double* __restrict__ out) {
+  __shared__ double seg_sum[8][33];
+  const int lr = threadIdx.x & 31, seg = threadIdx.x >> 5;
+  const int64_t S = (G + 7) / 8;
+  for (int64_t r0 = int64_t(blockIdx.x) * 32; r0 < n1; r0 += int64_t(gridDim.x) * 32) {
+    const int64_t i = r0 + lr;
     double a = 0.0;
+    if (i < n1) {
+      const int64_t g1 = (seg + 1) * S < G ? (seg + 1) * S : G;
 #pragma unroll 8
-    for (int64_t g = 0; g < G; ++g) a += partial[g * n1 + i];   // loads batched, adds in order
-    out[i] = a;
+      for (int64_t g = seg * S; g < g1; ++g) a += partial[g * n1 + i];
+    }
+    seg_sum[seg][lr] = a;
+    __syncthreads();
+    if (seg == 0 && i < n1) {
+      double t = 0.0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) t += seg_sum[k][lr];
+      out[i] = t;
+    }
+    __syncthreads();
   }
 }
 
@@ -420,7 +439,7 @@ int launch_slice_norms(const float* X, int64_t n1, int64_t n2, int64_t n3, int w
       horizontal_partial_kernel<<<dim3(unsigned(bx), unsigned(G)), 256, 0, st>>>(X, n1, ncols,
                                                                                 chunk, partial);
     }
-    int64_t rb = (n1 + 255) / 256;
+    int64_t rb = (n1 + 31) / 32;
     if (rb > 152 * 8) rb = 152 * 8;
     {
       KernelScope ks("norms_reduce", st);
