@@ -261,7 +261,9 @@ __global__ void __launch_bounds__(kThreads) rfft_reg_t_kernel(const DftGather g)
 // Staged form of the transposed transform (unit row stride, no row gather,
 // N <= 64).  A block owns tiles of 8 rows x 32 columns.  The tile's samples
 // are first copied to shared memory as 32-byte runs (8 consecutive rows of
-// one column and one sample), then each thread transforms the tube (r, c)
+// one column and one sample; by 16-byte loads staged through registers when
+// the columns are 16-byte aligned (VEC), else by 4-byte asynchronous
+// copies), then each thread transforms the tube (r, c)
 // from shared memory and a warp stores 128-byte runs along the columns.
 // Shared layout xs[t][row][col] with a row pitch of 36 floats: the copy
 // (8 rows x 4 columns per warp access) and the reads (32 columns of one row)
@@ -269,7 +271,7 @@ __global__ void __launch_bounds__(kThreads) rfft_reg_t_kernel(const DftGather g)
 constexpr int SROWS = 8, SCOLS = 32, SPITCH = 36;
 static_assert(SROWS * SCOLS == kThreads, "one tube per thread");
 
-template <int N>
+template <int N, bool VEC>
 __global__ void __launch_bounds__(kThreads) rfft_reg_ts_kernel(const DftGather g) {
   extern __shared__ float xs[];   // [N][SROWS][SPITCH]
   __shared__ const float* cbase[SCOLS];
@@ -288,10 +290,51 @@ __global__ void __launch_bounds__(kThreads) rfft_reg_ts_kernel(const DftGather g
       cscale[tid] = sc;
     }
     __syncthreads();
+    if constexpr (VEC) {
+      // copy by 16-byte loads (4 rows of one column and sample; columns and
+      // samples 16-byte aligned): chunk q = (sample s, column c, half hh), a
+      // warp covers 16 columns x both halves of one sample (32-byte runs);
+      // eight loads of a thread are issued before they are stored to shared
+      // memory.  Stores: row pitch 36 puts the two halves on disjoint banks.
+      constexpr int PER = N * SCOLS * 2 / kThreads;
+      constexpr int BATCH = PER < 8 ? PER : 8;   // loads in flight per thread (registers)
+#pragma unroll 1
+      for (int m0 = 0; m0 < PER; m0 += BATCH) {
+      float4 v[BATCH];
+#pragma unroll
+      for (int m = 0; m < BATCH; ++m) {
+        const int q = tid + kThreads * (m0 + m);
+        const int hh = q & 1, c = (q >> 1) & (SCOLS - 1), smp = q >> 6;
+        const float* p = cbase[c];
+        const int64_t r = r0 + 4 * hh;
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (p != nullptr) {
+          const float* a = p + r + int64_t(smp) * g.slice_stride;
+          if (r + 3 < ex.rows_eff) {
+            x = __ldg(reinterpret_cast<const float4*>(a));
+          } else {   // ragged last rows
+            if (r < ex.rows_eff) x.x = __ldg(a);
+            if (r + 1 < ex.rows_eff) x.y = __ldg(a + 1);
+            if (r + 2 < ex.rows_eff) x.z = __ldg(a + 2);
+          }
+        }
+        v[m] = x;
+      }
+#pragma unroll
+      for (int m = 0; m < BATCH; ++m) {
+        const int q = tid + kThreads * (m0 + m);
+        const int hh = q & 1, c = (q >> 1) & (SCOLS - 1), smp = q >> 6;
+        float* d = &xs[(smp * SROWS + 4 * hh) * SPITCH + c];
+        d[0] = v[m].x;
+        d[SPITCH] = v[m].y;
+        d[2 * SPITCH] = v[m].z;
+        d[3 * SPITCH] = v[m].w;
+      }
+      }
+    } else {
     // copy: run q = (column, sample); a warp access covers 4 runs x 8 rows.
     // Asynchronous 4-byte copies keep every sample of the tile in flight;
     // padding (rows or columns past the data) is zero-filled.
-    {
       const int row = lane & 7, col = warp * 4 + (lane >> 3);
       const float* p = cbase[col];
       const bool ok = p != nullptr && r0 + row < ex.rows_eff;
@@ -389,13 +432,21 @@ int launch_fwd(const DftGather& g, cudaStream_t st, int oversub) {
   if constexpr (N <= 64) {
     if (TP_RFFT_T_STAGE && g.out_transposed && g.gather_dim != 1 && g.row_stride == 1) {
       const size_t smem = size_t(N) * SROWS * SPITCH * sizeof(float);
-      cudaFuncSetAttribute(rfft_reg_ts_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           int(smem));
       const int64_t tiles = (g.rows + SROWS - 1) / SROWS * ((g.cols + SCOLS - 1) / SCOLS);
+      // 16-byte loads when every column and sample starts 16-byte aligned
+      const bool vec = N >= 4 && g.col_stride % 4 == 0 && g.slice_stride % 4 == 0 &&
+                       aligned16(g.src);
       {
         KernelScope ks("rdft_t", st);
-        rfft_reg_ts_kernel<N>
-            <<<grid_for(rfft_reg_ts_kernel<N>, tiles, smem, oversub), kThreads, smem, st>>>(g);
+        if (vec) {
+          auto k = rfft_reg_ts_kernel<N, (N >= 4)>;
+          cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+          k<<<grid_for(k, tiles, smem, oversub), kThreads, smem, st>>>(g);
+        } else {
+          auto k = rfft_reg_ts_kernel<N, false>;
+          cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+          k<<<grid_for(k, tiles, smem, oversub), kThreads, smem, st>>>(g);
+        }
       }
       return launch_status("rfft_reg_ts_kernel");
     }
