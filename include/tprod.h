@@ -157,10 +157,18 @@ int tprod_sampled(const float* A, const float* B, float* Z,
 int tsvd(const float* X, int64_t n1, int64_t n2, int64_t n3,
          float* U, float* S, float* V, const tp_opts* opts, void* stream);
 
+/* Test matrix of the randomized t-SVD. */
+#define TP_SKETCH_SIGNS 0   /* random signs (below) */
+#define TP_SKETCH_SLICES 1  /* picked lateral slices of X (t-CX sketch) */
+
 /* tsvd_randomized: rank-k approximation X ~ U * S * V^T of tubal rank k.
- * Per half-spectrum slice: Y = X_hat Omega with an n2 x (k+p) random-sign
- * test matrix from Philox stream 2 (entries (s0 + i s1)/sqrt(2), real
- * signs on the real slices; entry (r,c,f) uses counter r + n2*(c + (k+p)*f)),
+ * Per half-spectrum slice: Y = X_hat Omega with an n2 x (k+p) test matrix:
+ * TP_SKETCH_SIGNS, random signs from Philox stream 2 (entries
+ * (s0 + i s1)/sqrt(2), real signs on the real slices; entry (r,c,f) uses
+ * counter r + n2*(c + (k+p)*f)); TP_SKETCH_SLICES, the k + p lateral slices
+ * of X drawn with replacement as tprod_sampled's TP_SAMPLE_IID does (p_j =
+ * ||X(:,j,:)||_F^2 / ||X||_F^2, Philox stream 2), each rescaled by
+ * 1/sqrt((k+p) p_j), so that Y holds picked columns of X_hat;
  * q power iterations Q <- orth(X_hat^H Q), Q <- orth(X_hat Q), each orth a
  * CholeskyQR2 with float64 Gram and Cholesky, then B = Q^H X_hat, a float64
  * SVD of B and U = Q U_B truncated to k.
@@ -172,7 +180,8 @@ int tsvd(const float* X, int64_t n1, int64_t n2, int64_t n3,
  * Requires 1 <= k, p >= 0, q >= 0, k + p <= min(n1, n2, 96); n3 <= 512 or
  * n3 a product of the radices 2, 3, 5, 7, 11, 13.                           */
 int tsvd_randomized(const float* X, int64_t n1, int64_t n2, int64_t n3,
-                    int k, int p, int q, uint64_t seed, const int32_t* rank_per_freq,
+                    int k, int p, int q, uint64_t seed, int sketch_mode,
+                    const int32_t* rank_per_freq,
                     float* U, float* S, float* V, const tp_opts* opts, void* stream);
 
 /* tcx: t-CX of Algorithm 4 with the t-project of Algorithm 3.  Lateral

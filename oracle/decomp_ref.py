@@ -110,6 +110,24 @@ def tsvd_randomized_hat(X: np.ndarray, k: int, p: int, q: int, Omega: np.ndarray
     return Uh, s, Vh
 
 
+def slice_sketch(X: np.ndarray, ell: int, seed: int) -> np.ndarray:
+    """Test matrix of the slice (t-CX) sketch: ell lateral slices drawn i.i.d.
+    with probability p_j = ||X(:,j,:)||_F^2 / ||X||_F^2 (Philox stream 2,
+    with-replacement draws), Omega(j_c, c, f) = 1/sqrt(ell p_{j_c}) at every
+    half-spectrum frequency f, so that X_hat_f Omega_f is the rescaled picked
+    columns.  Returns Omega (n2 x ell x h, real)."""
+    from .philox_ref import STREAM_SKETCH
+    X = np.asarray(X, dtype=np.float64)
+    n2, n3 = X.shape[1], X.shape[2]
+    h = n3 // 2 + 1
+    p = sampling_ref.probabilities(sampling_ref.lateral_norms_sq(X), None, sampling_ref.PROB_A2)
+    idx, s = sampling_ref.draw_iid(p, ell, seed, STREAM_SKETCH)
+    Om = np.zeros((n2, ell, h))
+    for c, j in enumerate(idx):
+        Om[j, c, :] = 1.0 / np.sqrt(s[c])
+    return Om
+
+
 def tsvd_randomized(X: np.ndarray, k: int, p: int, q: int, Omega: np.ndarray, ranks=None):
     """Randomized tubal-rank-k t-SVD; same output form as ``tsvd`` with m = k.
     ranks (h integers): half-spectrum slice f keeps only its top

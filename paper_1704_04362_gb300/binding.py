@@ -18,7 +18,7 @@ import numpy as np
 
 __all__ = [
     "TP_FP32", "TP_TF32X3", "TP_BF16X3", "TP_PROB_AB", "TP_PROB_A2", "TP_PROB_GIVEN",
-    "TP_SAMPLE_BERNOULLI", "TP_SAMPLE_IID",
+    "TP_SAMPLE_BERNOULLI", "TP_SAMPLE_IID", "TP_SKETCH_SIGNS", "TP_SKETCH_SLICES",
     "TprodError", "lib", "lib_path", "empty_tensor", "as_tprod_layout",
     "tprod", "tprod_sampled", "tsvd", "tsvd_randomized", "tcomplete_svt", "tcx",
     "rdft3", "irdft3", "slice_norms", "sample_draw", "launch_count", "exported_symbols",
@@ -32,6 +32,7 @@ __all__ = [
 TP_FP32, TP_TF32X3, TP_BF16X3 = 0, 1, 2
 TP_PROB_AB, TP_PROB_A2, TP_PROB_GIVEN = 0, 1, 2
 TP_SAMPLE_BERNOULLI, TP_SAMPLE_IID = 0, 1
+TP_SKETCH_SIGNS, TP_SKETCH_SLICES = 0, 1
 TP_OP_TPROD, TP_OP_TPROD_SAMPLED, TP_OP_TSVD, TP_OP_TSVD_RANDOMIZED, TP_OP_TCOMPLETE_SVT, \
     TP_OP_SLICE_NORMS, TP_OP_TCX, TP_OP_TCOMPLETE_SVT_BATCHED, TP_OP_SKETCH_SPECTRUM, \
     TP_OP_MLP_TRAIN, TP_OP_TRPCA, TP_OP_TCUR, TP_OP_CUR_TNN = \
@@ -65,7 +66,7 @@ _SIGS = {
                                _c_int, _c_int, _vp, _vp, _vp, _vp, _vp]),
     "tsvd": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _vp, _vp, _vp, _vp, _vp]),
     "tsvd_randomized": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_int, _c_int, _c_int, _c_u64,
-                                 _vp, _vp, _vp, _vp, _vp, _vp]),
+                                 _c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
     "tcomplete_svt": (_c_int, [_vp, _vp, _c_i64, _c_i64, _c_i64, _c_int, _dbl, _dbl,
                                _vp, _vp, _vp, _vp, _vp, _vp]),
     "tcx": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_i64, _c_u64, _c_int, _vp, _vp, _vp, _vp,
@@ -367,9 +368,11 @@ def tsvd(X, max_sweeps=0, status=None):
     return U, S, V
 
 
-def tsvd_randomized(X, k, p=10, q=2, seed=0, status=None, max_sweeps=0, ranks=None):
+def tsvd_randomized(X, k, p=10, q=2, seed=0, status=None, max_sweeps=0, ranks=None,
+                    sketch=0):
     """Randomized tubal-rank-k t-SVD: returns (U, S, V).  ranks: optional
-    device int32[n3 // 2 + 1] per-frequency ranks (each at most k)."""
+    device int32[n3 // 2 + 1] per-frequency ranks (each at most k); sketch:
+    TP_SKETCH_SIGNS (0) or TP_SKETCH_SLICES (1, picked lateral slices)."""
     torch = _torch()
     n1, n2, n3 = X.shape
     rk = None
@@ -382,7 +385,8 @@ def tsvd_randomized(X, k, p=10, q=2, seed=0, status=None, max_sweeps=0, ranks=No
     V = empty_tensor(n2, k, n3, device=X.device)
     o = _opts(TP_OP_TSVD_RANDOMIZED, (n1, n2, n3, k, p), TP_FP32, status, max_sweeps)
     rc = lib().tsvd_randomized(_tensor_arg(X, "X"), n1, n2, n3, int(k), int(p), int(q),
-                               int(seed) & ((1 << 64) - 1), rk, _tensor_arg(U, "U"),
+                               int(seed) & ((1 << 64) - 1), int(sketch), rk,
+                               _tensor_arg(U, "U"),
                                _tensor_arg(S, "S"), _tensor_arg(V, "V"), ctypes.byref(o),
                                _stream())
     _check(rc, "tsvd_randomized")

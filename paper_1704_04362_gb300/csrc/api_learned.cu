@@ -6,7 +6,7 @@
 namespace tp {
 int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, int q,
              uint64_t seed, float* U, float* S, float* V, const tp_opts* opts, cudaStream_t st,
-             float* sig_out, const int32_t* rank_per_freq);
+             float* sig_out, const int32_t* rank_per_freq, int sketch_mode);
 size_t rsvd_ws(int64_t n1, int64_t n2, int64_t n3, int64_t k, int64_t p);
 bool fft_supported(int64_t n3);
 size_t mlp_partial_count(int64_t B);
@@ -45,7 +45,7 @@ int tp_sketch_spectrum(const float* X, int64_t n1, int64_t n2, int64_t n3, int l
     return TP_EUNSUPPORTED;
   }
   return rsvd_run(X, n1, n2, n3, l, 0, q, seed, nullptr, nullptr, nullptr, opts,
-                  as_stream(stream), sig_out, nullptr);
+                  as_stream(stream), sig_out, nullptr, TP_SKETCH_SIGNS);
 }
 
 int tp_rank_rule(const float* sig, int64_t h, int l, int cap, double tol, int32_t* rank_out,

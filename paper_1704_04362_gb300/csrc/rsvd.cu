@@ -667,10 +667,30 @@ size_t rsvd_ws(int64_t n1, int64_t n2, int64_t n3, int64_t k, int64_t p) {
          + 2 * ws_bytes(l * size_t(k) * h, 4)   // W_k
          + 2 * ws_bytes(size_t(n1) * k * h, 4)  // U_hat
          + 2 * ws_bytes(size_t(k) * k * h, 4)   // S_hat
-         + 2 * ws_bytes(size_t(n2) * k * h, 4); // V_hat
+         + 2 * ws_bytes(size_t(n2) * k * h, 4)  // V_hat
+         // slice sketch: lateral norms, picks, draw scratch
+         + ws_bytes(size_t(n2), 8) + ws_bytes(norms_partial_count(n1, n2, n3, 0), 8) +
+         ws_bytes(l, 4) + ws_bytes(l, 4) + ws_bytes(1, 8) + draw_scratch_bytes(n2);
 }
 
 namespace {
+// Test matrix of the slice (t-CX) sketch: Omega_f(j_c, c) = scale_c for the
+// c-th of the `count` with-replacement picks at every frequency f, zero
+// elsewhere (X_hat_f Omega_f is the rescaled picked columns).
+__global__ void slice_sketch_kernel(float* __restrict__ om_r, float* __restrict__ om_i, int64_t n2,
+                                    int64_t l, int64_t h, const int32_t* __restrict__ idx,
+                                    const float* __restrict__ scale,
+                                    const int64_t* __restrict__ count) {
+  const int64_t cnt = *count;
+  const int64_t total = n2 * l * h;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = e % n2, c = (e / n2) % l;
+    om_r[e] = (c < cnt && idx[c] == r) ? scale[c] : 0.f;
+    om_i[e] = 0.f;
+  }
+}
+
 // Diagonal of every k x k half-spectrum slice of S: sig[f * k + j] = S_f(j, j).
 __global__ void diag_kernel(const float* __restrict__ sr, int k, int64_t h, float* __restrict__ sig) {
   const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -687,7 +707,7 @@ __global__ void diag_kernel(const float* __restrict__ sr, int k, int64_t h, floa
 // triplets, the others are zero.
 int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, int q,
              uint64_t seed, float* U, float* S, float* V, const tp_opts* opts, cudaStream_t st,
-             float* sig_out, const int32_t* rank_per_freq) {
+             float* sig_out, const int32_t* rank_per_freq, int sketch_mode) {
   const int64_t h = half_len(n3);
   const int64_t l = k + p;
   Arena ws;
@@ -718,6 +738,12 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
   float* Si = ws.take<float>(size_t(k) * k * h);
   float* Vr = ws.take<float>(size_t(n2) * k * h);
   float* Vi = ws.take<float>(size_t(n2) * k * h);
+  double* a2 = ws.take<double>(size_t(n2));
+  double* part = ws.take<double>(norms_partial_count(n1, n2, n3, 0));
+  int32_t* pidx = ws.take<int32_t>(size_t(l));
+  float* pscale = ws.take<float>(size_t(l));
+  int64_t* pcnt = ws.take<int64_t>(1);
+  char* dscr = ws.take<char>(draw_scratch_bytes(n2));
 
   // X_hat and X_hat^H
   DftGather gx{X, n1 * n2, 1, 1, 0, n1 * n2, nullptr, nullptr, nullptr, 0, n3, Xr, Xi,
@@ -728,7 +754,19 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
     conj_transpose_kernel<<<dim3(unsigned((n1 + 31) / 32), unsigned((n2 + 31) / 32), unsigned(h)),
                             dim3(32, 8), 0, st>>>(Xr, Xi, n1, n2, Hr, Hi);
   }
-  {
+  if (sketch_mode == TP_SKETCH_SLICES) {
+    // l lateral slices drawn with replacement, p_j ~ ||X(:,j,:)||_F^2
+    // (Philox stream 2, word 3 = 1), rescaled by 1/sqrt(l p_j)
+    if ((rc = launch_slice_norms(X, n1, n2, n3, 0, a2, part, st))) return rc;
+    if ((rc = launch_draw(a2, nullptr, n2, l, seed, TP_PROB_A2, 2u, pidx, pscale, pcnt, nullptr,
+                          dscr, st, TP_SAMPLE_IID)))
+      return rc;
+    {
+      KernelScope ks("sketch", st);
+      slice_sketch_kernel<<<grid_for(n2 * l * h), 256, 0, st>>>(Or, Oi, n2, l, h, pidx, pscale,
+                                                                 pcnt);
+    }
+  } else {
     KernelScope ks("sketch", st);
     sketch_kernel<<<grid_for(n2 * l * h), 256, 0, st>>>(Or, Oi, n2, l, h, n3, seed);
   }

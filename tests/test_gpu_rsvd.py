@@ -123,3 +123,24 @@ def test_per_frequency_ranks_match_oracle():
                                     ranks=torch.full((h,), k, dtype=torch.int32, device="cuda"))
     U0, S0, V0 = tp.tsvd_randomized(dev(X), k, p, q, seed=5)
     assert torch.equal(U2, U0) and torch.equal(S2, S0) and torch.equal(V2, V0)
+
+
+@pytest.mark.parametrize("n1,n2,n3,r,k,p,q", [(48, 40, 8, 4, 4, 6, 1), (30, 64, 7, 3, 3, 5, 0),
+                                              (64, 48, 16, 5, 6, 4, 2)])
+def test_slice_sketch_matches_oracle(n1, n2, n3, r, k, p, q):
+    # t-CX sketch: Y = rescaled picked columns of X_hat (i.i.d. picks)
+    import torch
+    X = synth.lowrank_np(n1, n2, n3, r, seed=n1 + r)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    U, S, V = tp.tsvd_randomized(dev(X), k, p, q, seed=7, status=st, sketch=tp.TP_SKETCH_SLICES)
+    assert int(st.item()) == 0
+    Om = decomp_ref.slice_sketch(X, k + p, 7)
+    Ur, Sr, Vr = decomp_ref.tsvd_randomized(X.astype(np.float64), k, p, q, Om)
+    A = approx(to_np(U), to_np(S), to_np(V))
+    assert rel_fro(A, X.astype(np.float64)) < TOL_FP32          # exact tubal rank recovered
+    assert rel_fro(A, approx(Ur, Sr, Vr)) < TOL_FP32
+    s, sr = sing_vals(to_np(S)), sing_vals(Sr)
+    assert rel_fro(s[:r], sr[:r]) < TOL_FP32
+    # the sign sketch is a different test matrix but the same exact result
+    U2, S2, V2 = tp.tsvd_randomized(dev(X), k, p, q, seed=7)
+    assert rel_fro(approx(to_np(U2), to_np(S2), to_np(V2)), A) < TOL_FP32

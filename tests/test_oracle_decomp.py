@@ -354,3 +354,22 @@ def test_per_frequency_ranks_give_the_multi_rank_truncation():
     U0, S0, V0 = D.tsvd_randomized(X, 6, 2, 1, Om)
     Uf, Sf, Vf = D.tsvd_randomized(X, 6, 2, 1, Om, ranks=np.full(h, 6))
     assert np.array_equal(U0, Uf) and np.array_equal(S0, Sf)
+
+
+def test_slice_sketch_recovers_exact_low_tubal_rank():
+    # the sketch is rescaled picked columns of X_hat: with tubal rank r <= l
+    # and generic picks their span is X's range, so the rank-r result is X
+    from oracle import decomp_ref as D
+    from oracle.tensor_ref import tprod, ttranspose
+    from paper_1704_04362_gb300 import synth
+    X = synth.lowrank_np(24, 30, 6, 3, seed=76, dtype=np.float64)
+    Om = D.slice_sketch(X, 8, 4)
+    assert Om.shape == (30, 8, 4) and np.count_nonzero(Om[:, :, 0]) == 8
+    assert np.array_equal(Om[:, :, 0] != 0, Om[:, :, 3] != 0)         # same picks at every f
+    U, S, V = D.tsvd_randomized(X, 3, 5, 0, Om)
+    R = tprod(tprod(U, S), ttranspose(V))
+    assert np.linalg.norm(R - X) / np.linalg.norm(X) < 1e-10
+    # the columns of Omega select and rescale: X_hat Omega = picked columns / sqrt(l p)
+    Xh = np.fft.fft(X, axis=2)
+    j, c = np.nonzero(Om[:, :, 0])
+    np.testing.assert_allclose((Xh[:, :, 1] @ Om[:, :, 1])[:, c], Xh[:, j, 1] * Om[j, c, 1], atol=1e-12)
