@@ -433,6 +433,12 @@ const char* tp_status_string(int status);
 const char* tp_last_error(void);
 /* Frees the library-managed workspace of the current device (synchronises it). */
 int tp_release(void);
+/* tp_sync_status: waits for `stream`, then reports what went wrong on the
+ * device since: TP_ECUDA (message in tp_last_error) for a CUDA error raised
+ * by an earlier asynchronous launch, else TP_OK.  With status_dev (a device
+ * int32 the calls' tp_opts.status pointed at) non-NULL its TP_DEV_* bits are
+ * copied to *status_host (and the device word is left as it is).            */
+int tp_sync_status(void* stream, const int32_t* status_dev, int32_t* status_host);
 /* Number of kernels this library has launched in this process. */
 uint64_t tp_launch_count(void);
 int tp_version(void);

@@ -26,7 +26,7 @@ __all__ = [
     "sketch_spectrum", "rank_rule", "rank_features", "mlp_param_count", "mlp_round",
     "mlp_forward", "mlp_train_step", "trpca_admm", "tcur", "cur_tnn",
     "TP_TUNE_OFF", "TP_TUNE_ON", "autotune_mode", "autotune_force", "autotune_table",
-    "autotune_save", "autotune_load", "autotune_reset",
+    "autotune_save", "autotune_load", "autotune_reset", "sync_status",
 ]
 
 TP_FP32, TP_TF32X3, TP_BF16X3 = 0, 1, 2
@@ -97,6 +97,7 @@ _SIGS = {
     "tp_status_string": (ctypes.c_char_p, [_c_int]),
     "tp_last_error": (ctypes.c_char_p, []),
     "tp_release": (_c_int, []),
+    "tp_sync_status": (_c_int, [_vp, _vp, _vp]),
     "tp_autotune_mode": (_c_int, [_c_int]),
     "tp_autotune_force": (_c_int, [_c_int]),
     "tp_autotune_count": (_c_int, []),
@@ -188,6 +189,18 @@ def autotune_load(path):
 
 def autotune_reset():
     _check(lib().tp_autotune_reset(), "tp_autotune_reset")
+
+
+def sync_status(status=None) -> int:
+    """Waits for the current stream; raises on an asynchronous CUDA error and
+    returns the TP_DEV_* bits of the device status word `status` (0 without)."""
+    torch = _torch()
+    out = ctypes.c_int32(0)
+    sd = _tensor_arg(status, "status", torch.int32) if status is not None else None
+    rc = lib().tp_sync_status(_stream(), sd, ctypes.cast(ctypes.byref(out), ctypes.c_void_p)
+                              if status is not None else None)
+    _check(rc, "tp_sync_status")
+    return int(out.value)
 
 
 def launch_count() -> int:

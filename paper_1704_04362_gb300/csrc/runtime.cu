@@ -151,6 +151,25 @@ const char* tp_status_string(int s) {
 
 const char* tp_last_error(void) { return tp::g_err; }
 
+int tp_sync_status(void* stream, const int32_t* status_dev, int32_t* status_host) {
+  if (status_dev && !status_host) { tp::set_error("tp_sync_status: NULL status_host"); return TP_ENULL; }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    tp::set_error("asynchronous CUDA error: %s", cudaGetErrorString(e));
+    return TP_ECUDA;
+  }
+  if (status_dev) {
+    if (cudaMemcpy(status_host, status_dev, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      tp::set_error("tp_sync_status: reading the status word failed");
+      return TP_ECUDA;
+    }
+  }
+  return TP_OK;
+}
+
 int tp_release(void) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= tp::kMaxDev) return TP_ECUDA;

@@ -81,3 +81,13 @@ def test_tsvd_low_rank_and_zero():
     Z = np.zeros((4, 3, 2), dtype=np.float32)
     U, S, V = tp.tsvd(dev(Z))
     assert float(S.abs().max()) == 0.0
+
+
+def test_sync_status_reports_the_device_status_word():
+    import torch
+    X = synth.iid_normal((40, 30, 6), seed=8)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    tp.tsvd(dev(X), status=st)
+    assert tp.sync_status(st) == 0 and tp.sync_status() == 0
+    tp.tsvd(dev(X), status=st, max_sweeps=1)
+    assert tp.sync_status(st) & 0x1          # TP_DEV_NOCONV
