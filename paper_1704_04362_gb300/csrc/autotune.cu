@@ -1,8 +1,10 @@
 // Launch-shape autotuner.  A tunable launch offers a few candidate shapes
 // (tile widths, blocks per SM) that all compute bit-identical results; the
-// first call with a given problem key times each candidate on the caller's
-// stream with CUDA events (one warm-up and three timed launches each), keeps
-// the fastest, and every later call with that key launches it directly.  A
+// first call with a given problem key (sizes taken by their size class, the
+// bit length, so that problems within a factor of two share a choice) times
+// each candidate on the caller's stream with CUDA events (one warm-up and
+// three timed launches each), keeps the fastest, and every later call with
+// that key launches it directly.  A
 // stream being captured into a CUDA graph is never timed: the call takes the
 // cached choice or the default.  The table can be listed, saved to and
 // loaded from a text file (one "key choice" line per entry), and tuning can

@@ -465,8 +465,8 @@ int launch_rdft(const DftGather& g, cudaStream_t st) {
     }
   };
   const int kc = pick_kc(g.n3 / 2 + 1);
-  const int64_t key[7] = {g.n3, g.rows, g.cols, g.gather_dim, g.out_transposed,
-                          g.out_re_lo ? 1 : 0, g.out_bf16};
+  const int64_t key[7] = {g.n3, size_class(g.rows), size_class(g.cols), g.gather_dim,
+                          g.out_transposed, g.out_re_lo ? 1 : 0, g.out_bf16};
   int c = 0;
   const int rc = autotune_pick("rdft", key, 7, 3, kc == 8 ? 0 : kc == 12 ? 1 : 2, run, st, &c);
   return rc ? rc : run(c);
@@ -491,7 +491,7 @@ int launch_irdft(const float* in_re, const float* in_im, int64_t rows, int64_t i
     }
   };
   const int kc = pick_kc(n3 / 2 + 1);
-  const int64_t key[2] = {n3, rows};
+  const int64_t key[2] = {n3, size_class(rows)};
   int c = 0;
   const int rc = autotune_pick("irdft", key, 2, 3, kc == 8 ? 0 : kc == 12 ? 1 : 2, run, st, &c);
   return rc ? rc : run(c);

@@ -508,8 +508,8 @@ int launch_rfft_reg(const DftGather& g, cudaStream_t st) {
     }
   };
   if (!rfft_reg_supported(g.n3)) return run(0);
-  const int64_t key[7] = {g.n3, g.rows, g.cols, g.gather_dim, g.out_transposed,
-                          g.out_re_lo ? 1 : 0, g.out_bf16};
+  const int64_t key[7] = {g.n3, size_class(g.rows), size_class(g.cols), g.gather_dim,
+                          g.out_transposed, g.out_re_lo ? 1 : 0, g.out_bf16};
   int c = kOversubDefault;
   const int rc = autotune_pick("rfft_reg", key, 7, 4, kOversubDefault, run, st, &c);
   return rc ? rc : run(c);
@@ -533,7 +533,7 @@ int launch_irfft_reg(const float* in_re, const float* in_im, int64_t rows, int64
     }
   };
   if (!rfft_reg_supported(n3)) return run(0);
-  const int64_t key[3] = {n3, rows, in_slice};
+  const int64_t key[3] = {n3, size_class(rows), size_class(in_slice)};
   int c = kOversubDefault;
   const int rc = autotune_pick("irfft_reg", key, 3, 4, kOversubDefault, run, st, &c);
   return rc ? rc : run(c);

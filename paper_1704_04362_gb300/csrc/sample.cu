@@ -419,9 +419,9 @@ int launch_slice_norms(const float* X, int64_t n1, int64_t n2, int64_t n3, int w
       }
       return launch_status("lateral_partial_kernel");
     };
-    const int64_t key[3] = {n1, ncols, vec4 ? 1 : 0};
+    const int64_t key[4] = {n1, size_class(ncols), vec4 ? 1 : 0, lc};
     int c = 2;
-    int rc = tunable ? autotune_pick("norms_lateral", key, 3, 4, 2, run, st, &c) : TP_OK;
+    int rc = tunable ? autotune_pick("norms_lateral", key, 4, 4, 2, run, st, &c) : TP_OK;
     if (!rc) rc = run(c);
     if (rc) return rc;
     int64_t rb = (n2 + 255) / 256;

@@ -116,6 +116,17 @@ int launch_draw(const double* w, const double* w2, int64_t n, int64_t c, uint64_
                 double* q_out, void* scratch, cudaStream_t st,
                 int sample_mode = TP_SAMPLE_BERNOULLI);
 
+// Bit length of v (0 for v <= 0): the size class of a tuning key, so that
+// problems within a factor of two share one tuned choice.
+inline int64_t size_class(int64_t v) {
+  int64_t b = 0;
+  while (v > 0) {
+    ++b;
+    v >>= 1;
+  }
+  return b;
+}
+
 // Launch-shape autotuner (autotune.cu): `launch(c)` enqueues candidate c of a
 // tunable launch on st (every candidate computes bit-identical results); the
 // chosen candidate for this op and key is returned in *choice (timed on the
