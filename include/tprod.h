@@ -53,7 +53,7 @@ typedef enum {
   TP_ENOMEM = -4,        /* the library could not allocate its workspace */
   TP_ECUDA = -5,         /* a CUDA runtime call or kernel launch failed */
   TP_EWORKSPACE = -9,    /* opts->workspace is smaller than tp_workspace_query() */
-  TP_EUNSUPPORTED = -10  /* valid but not supported by this build (see message) */
+  TP_EUNSUPPORTED = -10  /* valid but not supported by this library (see message) */
 } tp_status;
 
 /* Device status bits OR-ed into opts->status. */

@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(NTHR, 1) cgemm_tc_kernel(const __grid_constant
 }
 
 // ---------------------------------------------------------------- host side
-// The driver's tensor-map encoder, looked up through the runtime so that the
+// The CUDA driver API's tensor-map encoder, looked up through the runtime so that the
 // library has no link-time dependency on libcuda (it loads on GPU-less hosts).
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;

@@ -144,7 +144,7 @@ const char* tp_status_string(int s) {
     case TP_ENOMEM: return "TP_ENOMEM: workspace allocation failed";
     case TP_ECUDA: return "TP_ECUDA: CUDA error";
     case TP_EWORKSPACE: return "TP_EWORKSPACE: workspace too small";
-    case TP_EUNSUPPORTED: return "TP_EUNSUPPORTED: not supported by this build";
+    case TP_EUNSUPPORTED: return "TP_EUNSUPPORTED: not supported by this library";
     default: return "unknown tp_status";
   }
 }

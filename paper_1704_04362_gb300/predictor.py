@@ -7,7 +7,7 @@ rule's r_k (tol 1e-2, cap k = 40).  Many tensors need far fewer columns: the
 predictor looks at a cheap sketch (17 columns, no power iteration), predicts
 each frequency's rank r_k and the oversampling p_k a sketch needs to resolve
 it, and the decomposition runs with l* = max_k (r_k + p_k) columns.  The
-plain rule stays the judge: it re-derives the ranks from the l*-column
+plain rule stays the arbiter: it re-derives the ranks from the l*-column
 sketch, and if any frequency reaches its cap (l* - 2) the sketch was too
 small and the method falls back to l = 50.
 

@@ -41,7 +41,7 @@ def test_learned_matches_plain_error_with_smaller_sketches(trained, alpha):
         sizes.append(l)
         errs_p.append(e_plain)
         errs_l.append(e_learn)
-        # the judge: never a worse truncation than the plain method (beyond the
+        # the rule as arbiter: never a worse truncation than the plain method (beyond the
         # sketch's own resolution of the tail)
         assert e_learn <= 1.05 * e_plain + 2e-3, (alpha, s, e_learn, e_plain, l, fell_back)
     if alpha >= 2.5:
