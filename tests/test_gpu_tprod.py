@@ -210,3 +210,18 @@ def test_tprod_sampled_iid_matches_oracle(n1, n2, n4, n3, c, prec):
     Zref, ref_idx, _ = sampling_ref.tprod_sampled(A, B, c, 321, sample=sampling_ref.SAMPLE_IID)
     assert np.array_equal(idx[:c].cpu().numpy(), ref_idx)
     assert rel_fro(to_np(Z), Zref) < tol_for(prec)
+
+
+def test_hand_worked_fixtures_on_the_device():
+    # tests/golden: the t-product of Def. 2.1 worked by hand (2 x 2 x 2 and
+    # the tube (1,2,3) * (4,5,6) = (31,31,28)), through the C ABI
+    from tests.util import golden, golden_tensor
+    g = golden("tprod_2x2x2_by_hand.txt")
+    A, B, C = (golden_tensor(g[k], 2, 2, 2).astype(np.float32) for k in ("A", "B", "C"))
+    for prec in PRECISIONS:
+        Z = tp.tprod(dev(A), dev(B), precision=prec)
+        np.testing.assert_allclose(to_np(Z), C, atol=1e-5)
+    t = golden("tube_1x1x3_by_hand.txt")
+    a = np.array([1, 2, 3], dtype=np.float32).reshape(1, 1, 3)
+    b = np.array([4, 5, 6], dtype=np.float32).reshape(1, 1, 3)
+    np.testing.assert_allclose(to_np(tp.tprod(dev(a), dev(b))).ravel(), t["prod"][0], rtol=1e-6)

@@ -91,3 +91,12 @@ def test_sync_status_reports_the_device_status_word():
     assert tp.sync_status(st) == 0 and tp.sync_status() == 0
     tp.tsvd(dev(X), status=st, max_sweeps=1)
     assert tp.sync_status(st) & 0x1          # TP_DEV_NOCONV
+
+
+def test_hand_worked_singular_tube():
+    # tests/golden/tube_1x1x3_by_hand.txt: the singular tube of (1, 2, 3)
+    from tests.util import golden
+    t = golden("tube_1x1x3_by_hand.txt")
+    a = np.array([1, 2, 3], dtype=np.float32).reshape(1, 1, 3)
+    U, S, V = tp.tsvd(dev(a))
+    np.testing.assert_allclose(to_np(S).ravel(), t["svd_s"][0], rtol=1e-6)

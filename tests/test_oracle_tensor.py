@@ -125,3 +125,21 @@ def test_conjugate_symmetry_of_half_spectrum():
         X = rng(n3).standard_normal((2, 3, n3))
         Xh = T.fft3(X)
         np.testing.assert_allclose(T.hermitian_fill(T.half_spectrum(Xh), n3), Xh, atol=1e-12)
+
+
+def test_hand_worked_fixtures():
+    # tests/golden: values worked by hand from Def. 2.1, the t-transpose of
+    # Section 2 and Theorem 2.6 (derivations in the files)
+    from oracle import decomp_ref, tensor_ref
+    from tests.util import golden, golden_tensor
+    g = golden("tprod_2x2x2_by_hand.txt")
+    A, B, C, AT = (golden_tensor(g[k], 2, 2, 2) for k in ("A", "B", "C", "AT"))
+    np.testing.assert_allclose(tensor_ref.tprod(A, B), C, atol=1e-12)
+    np.testing.assert_allclose(tensor_ref.ttranspose(A), AT, atol=0)
+    t = golden("tube_1x1x3_by_hand.txt")
+    a = np.array([1.0, 2.0, 3.0]).reshape(1, 1, 3)
+    b = np.array([4.0, 5.0, 6.0]).reshape(1, 1, 3)
+    np.testing.assert_allclose(tensor_ref.tprod(a, b).ravel(), t["prod"][0], atol=1e-12)
+    U, S, V = decomp_ref.tsvd(a)
+    np.testing.assert_allclose(S.ravel(), t["svd_s"][0], atol=1e-12)
+    assert abs(tensor_ref.tnn(a) - t["tnn"][0][0]) < 1e-12

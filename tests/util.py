@@ -33,3 +33,26 @@ def tol_for(precision: int) -> float:
     """Relative Frobenius tolerance of a t-product output at this precision
     (0 FP32, 1 3xTF32, 2 BF16x3)."""
     return TOL_BF16X3 if precision == 2 else TOL_FP32
+
+
+def golden(name):
+    """Entries of a hand-worked fixture under tests/golden/: {key: [rows of
+    numbers]} (lines "key numbers..."; '#' starts a comment line)."""
+    import os
+    out = {}
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, *vals = line.split()
+            out.setdefault(key, []).append([float(v) for v in vals])
+    return out
+
+
+def golden_tensor(rows, n1, n2, n3):
+    """Tensor from fixture rows "slice row values..." (1-based slice and row)."""
+    X = np.zeros((n1, n2, n3))
+    for r in rows:
+        X[int(r[1]) - 1, :, int(r[0]) - 1] = r[2:]
+    return X
