@@ -4,12 +4,12 @@
 // bit length, so that problems within a factor of two share a choice) times
 // each candidate on the caller's stream with CUDA events (one warm-up and
 // three timed launches each), keeps the fastest, and every later call with
-// that key launches it directly.  A
-// stream being captured into a CUDA graph is never timed: the call takes the
-// cached choice or the default.  The table can be listed, saved to and
-// loaded from a text file (one "key choice" line per entry), and tuning can
-// be switched off (the default candidate everywhere; environment variable
-// TP_AUTOTUNE=0 at load) or forced to one candidate (for tests).
+// that key launches it directly.  A stream being captured into a CUDA graph
+// is never timed: the call takes the cached choice or the default.  The
+// table can be listed, saved to and loaded from a text file (one "key
+// choice" line per entry), and tuning can be switched off (the default
+// candidate everywhere; environment variable TP_AUTOTUNE=0 at load) or
+// forced to one candidate (for tests).
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
