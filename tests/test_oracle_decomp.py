@@ -220,6 +220,11 @@ def test_robust_admm_with_huge_lambda_keeps_e_zero():
     X = np.random.default_rng(43).standard_normal((6, 5, 4))
     L, E, Y, mu = C.trpca(X, 5, lam=1e12)
     assert np.all(E == 0.0)
+    # ... and the iteration is the completion form with every entry observed
+    Lc, Ec, Yc, muc = C.tcomplete_svt(X, np.ones(X.shape, dtype=bool), 5)
+    np.testing.assert_allclose(L, Lc, atol=1e-12)
+    np.testing.assert_allclose(Y, Yc, atol=1e-12)
+    assert mu == muc
 
 
 def test_tcur_keeps_everything_when_every_slice_is_picked():
