@@ -1,0 +1,254 @@
+// Blocked one-sided Jacobi (float32) for the singular-value thresholding of
+// the completion ADMM (Algorithm 7) on slices too large for the
+// shared-memory form of svd.cu.
+//
+// The columns of the p x q work matrix G are cut into blocks of B = 16.  For
+// every pair of blocks (I, J) the CTA copies the (at most 32) columns of both
+// blocks into shared memory, runs one cyclic sweep of column-pair rotations
+// among them there (round-robin order, one pair per warp per round; the same
+// rotation formula as svd.cu), accumulates those rotations in a small
+// 32 x 32 matrix Q, writes the columns back and applies Q to the matching 32
+// columns of V (V_blk <- V_blk Q, staged through the same shared memory).
+// Visiting every block pair is one sweep of a cyclic Jacobi ordering (pairs
+// inside a block are revisited with every partner block); sweeps repeat until
+// one makes no rotation (or the sweep cap, TP_DEV_NOCONV).  Each column pair
+// thereby costs shared-memory traffic; global memory sees each column once
+// per block pair instead of twice per rotation.  The convergence threshold
+// is the one of svd.cu, so the result is an SVD to the same tolerance (the
+// rotation order differs).
+#include "jacobi_rot.cuh"
+
+namespace tp {
+namespace {
+using jrot::rotation;
+
+constexpr int JB_THREADS = 512;   // 16 warps: one column pair each per round
+constexpr int JB_B = 16;          // columns per block; a block pair holds <= 32
+constexpr int JB_C = 2 * JB_B;
+constexpr size_t JB_SMEM_MAX = size_t(220) * 1024;
+
+__device__ __forceinline__ float jb_warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Global column of local column c of the block pair (I, J): the bI columns
+// of block I first, then those of block J.
+__device__ __forceinline__ int jb_col(int c, int I, int J, int bI) {
+  return c < bI ? I * JB_B + c : J * JB_B + (c - bI);
+}
+
+
+// One CTA per slice b: G (p x q, ld p) at g_re/g_im + b*sG, V (q x q) at
+// v_re/v_im + b*sV, q <= p.  On exit G is rotated (not normalised), V holds
+// the accumulated rotations and sig[b*q + j] = ||G_j||.
+__global__ void __launch_bounds__(JB_THREADS) jacobi_blocked_kernel(
+    float* __restrict__ g_re, float* __restrict__ g_im, int64_t sG, float* __restrict__ v_re,
+    float* __restrict__ v_im, int64_t sV, float* __restrict__ sig, int p, int q, int max_sweeps,
+    const int* __restrict__ real_flags, int32_t* __restrict__ status, int init_v) {
+  extern __shared__ __align__(16) float jb_smem[];
+  float* const Sr = jb_smem;                      // [JB_C][p]: columns of G, later of V
+  float* const Si = jb_smem + size_t(JB_C) * p;
+  float* const Qr = jb_smem + size_t(2) * JB_C * p;   // Q(r, c) at c * JB_C + r
+  float* const Qi = Qr + JB_C * JB_C;
+  __shared__ int any_rot, blk_rot;
+  const int64_t b = blockIdx.x;
+  float* const Gr = g_re + b * sG;
+  float* const Gi = g_im + b * sG;
+  float* const Vr = v_re + b * sV;
+  float* const Vi = v_im + b * sV;
+  const bool real = real_flags ? real_flags[b] != 0 : false;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = JB_THREADS / 32;
+  const int64_t pq = int64_t(p) * q, qq = int64_t(q) * q;
+  if (init_v)
+    for (int64_t e = tid; e < qq; e += JB_THREADS) {
+      Vr[e] = (e % (q + 1) == 0) ? 1.f : 0.f;
+      Vi[e] = 0.f;
+    }
+  if (real) {
+    for (int64_t e = tid; e < pq; e += JB_THREADS) Gi[e] = 0.f;
+    for (int64_t e = tid; e < qq; e += JB_THREADS) Vi[e] = 0.f;
+  }
+  __syncthreads();
+
+  float tol = 8.f * 5.96e-8f * sqrtf(float(p));
+  if (tol < 1e-6f) tol = 1e-6f;
+  const int nb = (q + JB_B - 1) / JB_B;
+  const int npair = nb == 1 ? 1 : nb * (nb - 1) / 2;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) any_rot = 0;
+    for (int bp = 0; bp < npair; ++bp) {
+      int I = 0, J = -1;   // block pair bp, I < J, row by row
+      if (nb > 1) {
+        int rem = bp;
+        while (rem >= nb - 1 - I) {
+          rem -= nb - 1 - I;
+          ++I;
+        }
+        J = I + 1 + rem;
+      }
+      const int bI = min(JB_B, q - I * JB_B);
+      const int bJ = J < 0 ? 0 : min(JB_B, q - J * JB_B);
+      const int nc = bI + bJ;
+      if (tid == 0) blk_rot = 0;
+      for (int e = tid; e < nc * p; e += JB_THREADS) {
+        const int c = e / p, r = e - c * p;
+        const int64_t src = int64_t(jb_col(c, I, J, bI)) * p + r;
+        Sr[e] = Gr[src];
+        Si[e] = Gi[src];
+      }
+      for (int e = tid; e < JB_C * JB_C; e += JB_THREADS) {
+        Qr[e] = (e % (JB_C + 1) == 0) ? 1.f : 0.f;
+        Qi[e] = 0.f;
+      }
+      __syncthreads();
+      // one cyclic sweep over the nc columns: round-robin rounds of disjoint
+      // pairs, one pair per warp
+      const int ncc = nc + (nc & 1);
+      for (int step = 0; step < ncc - 1; ++step) {
+        for (int i = warp; i < ncc / 2; i += NW) {
+          int a, c2;
+          if (i == 0) {
+            a = ncc - 1;
+            c2 = step;
+          } else {
+            a = (step + i) % (ncc - 1);
+            c2 = (step - i + (ncc - 1)) % (ncc - 1);
+          }
+          if (a >= nc || c2 >= nc) continue;
+          if (a > c2) {
+            const int t = a;
+            a = c2;
+            c2 = t;
+          }
+          float* const ar = Sr + size_t(a) * p;
+          float* const ai = Si + size_t(a) * p;
+          float* const br = Sr + size_t(c2) * p;
+          float* const bi = Si + size_t(c2) * p;
+          float alpha = 0.f, beta = 0.f, gr = 0.f, gi = 0.f;
+          for (int r = lane; r < p; r += 32) {
+            const float xr = ar[r], xi = ai[r], yr = br[r], yi = bi[r];
+            alpha += xr * xr + xi * xi;
+            beta += yr * yr + yi * yi;
+            gr += xr * yr + xi * yi;   // Re(conj(x) y)
+            gi += xr * yi - xi * yr;   // Im(conj(x) y)
+          }
+          alpha = jb_warp_sum(alpha);
+          beta = jb_warp_sum(beta);
+          gr = jb_warp_sum(gr);
+          gi = jb_warp_sum(gi);
+          const float g2 = gr * gr + gi * gi;
+          if (!(g2 > tol * tol * alpha * beta) || g2 == 0.f) continue;
+          if (lane == 0) blk_rot = 1;
+          float cs, sn, er, ei;   // cos, sin and e^{-i phi}
+          rotation(alpha, beta, gr, gi, g2, cs, sn, er, ei);
+          for (int r = lane; r < p; r += 32) {
+            const float xr = ar[r], xi = ai[r];
+            const float yr = br[r] * er - bi[r] * ei, yi = br[r] * ei + bi[r] * er;
+            ar[r] = cs * xr - sn * yr;
+            ai[r] = cs * xi - sn * yi;
+            br[r] = sn * xr + cs * yr;
+            bi[r] = sn * xi + cs * yi;
+          }
+          // the same column operation on Q (rows 0 .. nc-1; lane r < 32)
+          {
+            float* const qa_r = Qr + a * JB_C;
+            float* const qa_i = Qi + a * JB_C;
+            float* const qb_r = Qr + c2 * JB_C;
+            float* const qb_i = Qi + c2 * JB_C;
+            const int r = lane;
+            if (r < nc) {
+              const float xr = qa_r[r], xi = qa_i[r];
+              const float yr = qb_r[r] * er - qb_i[r] * ei, yi = qb_r[r] * ei + qb_i[r] * er;
+              qa_r[r] = cs * xr - sn * yr;
+              qa_i[r] = cs * xi - sn * yi;
+              qb_r[r] = sn * xr + cs * yr;
+              qb_i[r] = sn * xi + cs * yi;
+            }
+          }
+        }
+        __syncthreads();
+      }
+      if (blk_rot) {   // uniform: every write of it precedes the last barrier
+        for (int e = tid; e < nc * p; e += JB_THREADS) {
+          const int c = e / p, r = e - c * p;
+          const int64_t dst = int64_t(jb_col(c, I, J, bI)) * p + r;
+          Gr[dst] = Sr[e];
+          Gi[dst] = Si[e];
+        }
+        __syncthreads();   // the staging area now takes V's columns
+        for (int e = tid; e < nc * q; e += JB_THREADS) {
+          const int c = e / q, r = e - c * q;
+          const int64_t src = int64_t(jb_col(c, I, J, bI)) * q + r;
+          Sr[e] = Vr[src];
+          Si[e] = Vi[src];
+        }
+        __syncthreads();
+        // V_blk <- V_blk Q
+        for (int e = tid; e < nc * q; e += JB_THREADS) {
+          const int j = e / q, r = e - j * q;
+          float accr = 0.f, acci = 0.f;
+          for (int k = 0; k < nc; ++k) {
+            const float xr = Sr[k * q + r], xi = Si[k * q + r];
+            const float yr = Qr[j * JB_C + k], yi = Qi[j * JB_C + k];
+            accr += xr * yr - xi * yi;
+            acci += xr * yi + xi * yr;
+          }
+          const int64_t dst = int64_t(jb_col(j, I, J, bI)) * q + r;
+          Vr[dst] = accr;
+          Vi[dst] = acci;
+        }
+        if (tid == 0) any_rot = 1;
+      }
+      __syncthreads();   // the staging area and blk_rot are reused by the next pair
+    }
+    const int any = any_rot;
+    __syncthreads();
+    if (!any) break;
+  }
+  if (sweep >= max_sweeps && tid == 0 && status) atomicOr(status, TP_DEV_NOCONV);
+  for (int j = warp; j < q; j += NW) {
+    const float* xr = Gr + int64_t(j) * p;
+    const float* xi = Gi + int64_t(j) * p;
+    float nrm = 0.f;
+    for (int r = lane; r < p; r += 32) nrm += xr[r] * xr[r] + xi[r] * xi[r];
+    nrm = sqrtf(jb_warp_sum(nrm));
+    if (lane == 0) sig[b * q + j] = nrm;
+  }
+}
+
+size_t jb_smem_bytes(int p) {
+  return (size_t(2) * JB_C * p + size_t(2) * JB_C * JB_C) * sizeof(float);
+}
+
+}  // namespace
+
+// The blocked form serves slices whose G and V do not fit the shared-memory
+// form of svd.cu (200 KB) while 32 of G's columns do.
+bool jacobi_blocked_applies(int p, int q) {
+  const size_t whole = (size_t(2) * p * q + size_t(2) * q * q) * sizeof(float);
+  return q <= p && whole > size_t(200) * 1024 && jb_smem_bytes(p) <= JB_SMEM_MAX;
+}
+
+// float32 blocked one-sided Jacobi from V = I (init_v) or from the given V
+// (then G must be the work matrix times that V); G is left rotated.
+int jacobi_float_blocked_launch(float* gr, float* gi, int64_t sG, float* vr, float* vi,
+                                int64_t sV, float* sig, int p, int q, int batch, int max_sweeps,
+                                const int* real_flags, int32_t* status, bool init_v,
+                                cudaStream_t st) {
+  if (batch <= 0 || q <= 0) return TP_OK;
+  const size_t smem = jb_smem_bytes(p);
+  cudaFuncSetAttribute(jacobi_blocked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       int(smem));
+  {
+    KernelScope ks("jacobi_blocked", st);
+    jacobi_blocked_kernel<<<unsigned(batch), JB_THREADS, smem, st>>>(
+        gr, gi, sG, vr, vi, sV, sig, p, q, max_sweeps, real_flags, status, init_v ? 1 : 0);
+  }
+  return launch_status("jacobi_blocked_kernel");
+}
+
+}  // namespace tp

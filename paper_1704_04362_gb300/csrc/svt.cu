@@ -29,6 +29,16 @@ namespace tp {
 int jacobi_float_launch(float* gr, float* gi, int64_t sG, float* vr, float* vi, int64_t sV,
                         float* sig, int p, int q, int batch, int max_sweeps,
                         const int* real_flags, int32_t* status, bool init_v, cudaStream_t st);
+bool jacobi_blocked_applies(int p, int q);
+int jacobi_float_blocked_launch(float* gr, float* gi, int64_t sG, float* vr, float* vi,
+                                int64_t sV, float* sig, int p, int q, int batch, int max_sweeps,
+                                const int* real_flags, int32_t* status, bool init_v,
+                                cudaStream_t st);
+// Slices too large for the shared-memory Jacobi take the blocked one
+// (jacobi_blocked.cu); -DTP_SVT_BLOCKED=0 keeps them on the global-memory form.
+#ifndef TP_SVT_BLOCKED
+#define TP_SVT_BLOCKED 1
+#endif
 int launch_cgemm(const CGemm& g, cudaStream_t st);
 
 namespace {
@@ -258,9 +268,13 @@ int svt_iteration(const SvtTensor& t, bool warm, double rho, double mu_max, int 
              h, t.n3, TP_FP32, nullptr, nullptr, nullptr, nullptr, q, status};
     if ((rc = launch_cgemm(gw, st))) return rc;
   }
-  if ((rc = jacobi_float_launch(t.Gr, t.Gi, p * q, t.Vr, t.Vi, q * q, t.sig, int(p), int(q),
-                                int(h), sweeps, t.flags, status, !warm, st)))
-    return rc;
+  if (TP_SVT_BLOCKED && jacobi_blocked_applies(int(p), int(q)))
+    rc = jacobi_float_blocked_launch(t.Gr, t.Gi, p * q, t.Vr, t.Vi, q * q, t.sig, int(p), int(q),
+                                     int(h), sweeps, t.flags, status, !warm, st);
+  else
+    rc = jacobi_float_launch(t.Gr, t.Gi, p * q, t.Vr, t.Vi, q * q, t.sig, int(p), int(q),
+                             int(h), sweeps, t.flags, status, !warm, st);
+  if (rc) return rc;
   {   // H = W V from the unrotated work matrix
     CGemm gh{t.Kr, t.Ki, t.Vr, t.Vi, t.Hr, t.Hi, p, q, q, nullptr, p, q, p, p * q, q * q, p * q,
              h, t.n3, TP_FP32, nullptr, nullptr, nullptr, nullptr, q, status};

@@ -22,7 +22,10 @@ def state_on_device(X, mask, L, E, Y, mu):
             torch.tensor([mu], dtype=torch.float64, device="cuda"))
 
 
-@pytest.mark.parametrize("n1,n2,n3", [(20, 16, 6), (12, 30, 5), (24, 24, 1), (33, 17, 8)])
+# the last two slices exceed the shared-memory Jacobi and take the blocked
+# one (128 columns in 8 blocks; 150 columns, transposed, with a ragged block)
+@pytest.mark.parametrize("n1,n2,n3", [(20, 16, 6), (12, 30, 5), (24, 24, 1), (33, 17, 8),
+                                      (160, 128, 4), (150, 200, 5)])
 def test_one_iteration_matches_oracle(n1, n2, n3):
     import torch
     g = np.random.default_rng(n1 * n2 + n3)
@@ -44,7 +47,10 @@ def test_one_iteration_matches_oracle(n1, n2, n3):
     assert np.linalg.norm(Lr) > 0          # the threshold keeps part of the spectrum
     assert rel_fro(to_np(Ld), Lr) < TOL_FP32
     assert rel_fro(to_np(Ed), Er) < TOL_FP32
-    assert rel_fro(to_np(Yd), Yr) < TOL_FP32
+    # Y <- Y + mu (L + E - X) (Algorithm 7) inherits mu times L's error: Y is
+    # held to the float32 bound on the scale of that update
+    dY = np.linalg.norm(to_np(Yd) - Yr)
+    assert dY < TOL_FP32 * (np.linalg.norm(Yr) + mu * np.linalg.norm(Lr))
     assert abs(float(mud.item()) - mur) <= 1e-15 * mur
     assert np.all(to_np(Ed)[mask] == 0)
 
@@ -161,3 +167,19 @@ def test_robust_form_recovers_low_rank_plus_sparse_and_tracks_oracle():
     assert abs(float(mu.item()) / mur - 1) < 1e-12
     L2, E2, _, _ = tp.trpca_admm(dev(X), 120)
     assert rel_fro(to_np(L2), L0) < 1e-3 and rel_fro(to_np(E2), S0) < 1e-3
+
+
+def test_blocked_jacobi_slices_track_oracle_over_iterations():
+    # 160 x 128 slices take the blocked Jacobi, warm-started every iteration
+    import torch
+    X = synth.lowrank_np(160, 128, 4, 3, seed=62, noise=0.01)
+    X = X / np.sqrt(np.mean(X.astype(np.float64) ** 2))
+    mask = np.random.default_rng(63).random(X.shape) < 0.6
+    Z = np.zeros_like(X)
+    Xd, Md, Ld, Ed, Yd, mud = state_on_device(X, mask, Z, Z, Z, 1e-3)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    tp.tcomplete_svt(Xd, Md, 30, L=Ld, E=Ed, Y=Yd, mu=mud, status=st)
+    assert int(st.item()) == 0
+    Lr, Er, Yr, mur = completion_ref.tcomplete_svt(X.astype(np.float64), mask, 30)
+    assert rel_fro(to_np(Ld), Lr) < 1e-4                 # float32 state over 30 iterations
+    assert abs(float(mud.item()) / mur - 1) < 1e-12
