@@ -428,6 +428,20 @@ int tp_sample_draw(const double* w, const double* w2, int64_t n, int64_t c,
                    void* stream);
 
 /* ---------------------------------------------------------------- runtime */
+/* tp_philox4x32_10: the library's counter-based generator, exposed so that
+ * its words can be checked against the published known-answer vectors of
+ * Philox4x32-10 (Salmon et al., SC'11).  Every random choice of the library
+ * (Algorithm 2's coins, the with-replacement draws, Algorithm 4-5's picks,
+ * the randomized t-SVD's test matrix) is a function of these words; the
+ * paper does not say how its draws are made (see tprod_sampled).
+ *   counters  device uint32[4 n]: counter e is words 4e .. 4e+3 (word 0 first)
+ *   k0, k1    the key (k0 = the low key word)
+ *   out       device uint32[4 n]: the four output words of counter e
+ * n = 0 enqueues nothing.  Returns TP_EINVAL for n < 0, TP_ENULL for a NULL
+ * buffer with n > 0.                                                       */
+int tp_philox4x32_10(const uint32_t* counters, uint32_t k0, uint32_t k1, int64_t n,
+                     uint32_t* out, void* stream);
+
 size_t tp_workspace_query(int op, const int64_t* dims, int ndims, const tp_opts* opts);
 const char* tp_status_string(int status);
 const char* tp_last_error(void);

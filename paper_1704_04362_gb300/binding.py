@@ -26,7 +26,7 @@ __all__ = [
     "sketch_spectrum", "rank_rule", "rank_features", "mlp_param_count", "mlp_round",
     "mlp_forward", "mlp_train_step", "trpca_admm", "tcur", "cur_tnn",
     "TP_TUNE_OFF", "TP_TUNE_ON", "autotune_mode", "autotune_force", "autotune_table",
-    "autotune_save", "autotune_load", "autotune_reset", "sync_status",
+    "autotune_save", "autotune_load", "autotune_reset", "sync_status", "philox4x32_10",
 ]
 
 TP_FP32, TP_TF32X3, TP_BF16X3 = 0, 1, 2
@@ -113,6 +113,7 @@ _SIGS = {
     "tp_profile_reset": (_c_int, []),
     "tp_slice_norms_noalloc": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_int, _vp, _vp]),
     "tp_slice_norms_noalloc_capacity": (ctypes.c_size_t, []),
+    "tp_philox4x32_10": (_c_int, [_vp, _c_u32, _c_u32, _c_i64, _vp, _vp]),
 }
 
 _LIB = None
@@ -677,6 +678,19 @@ def slice_norms_noalloc(X, which, out=None):
                                       _tensor_arg(out, "out", torch.float64), _stream())
     _check(rc, "tp_slice_norms_noalloc")
     return out
+
+
+def philox4x32_10(counters, k0, k1):
+    """Philox4x32-10 words of the counters (an (n, 4) array of uint32 values,
+    word 0 first) under key (k0, k1); returns an (n, 4) numpy uint32 array."""
+    torch = _torch()
+    ctr = np.ascontiguousarray(np.asarray(counters, dtype=np.uint32).reshape(-1, 4))
+    n = ctr.shape[0]
+    c_dev = torch.from_numpy(ctr.view(np.int32)).to("cuda")
+    out = torch.empty((n, 4), dtype=torch.int32, device="cuda")
+    _check(lib().tp_philox4x32_10(c_dev.data_ptr(), int(k0) & 0xFFFFFFFF, int(k1) & 0xFFFFFFFF,
+                                  n, out.data_ptr(), _stream()), "tp_philox4x32_10")
+    return out.cpu().numpy().view(np.uint32)
 
 
 def sample_draw(w, w2, c, seed, prob_mode, stream_id=0, sample_mode=TP_SAMPLE_BERNOULLI):

@@ -11,8 +11,13 @@
 // library holds its kNoAllocScratch doubles (8 MiB) until the process exits.
 // Host code cannot use the array's name as a device address (on the host it
 // names a stand-in object), so its device address is looked up with
-// cudaGetSymbolAddress once per device, on the first call made with that
-// device current, and cached.
+// cudaGetSymbolAddress on the first call made with a device current, and
+// cached for that device and its CUDA context.  A call under a different
+// context (after cudaDeviceReset, or with another context made current
+// through the driver API) sees the context change and looks the address up
+// again, since the module may then live at a new address.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "tp_internal.cuh"
@@ -25,10 +30,34 @@ constexpr size_t kNoAllocScratch = size_t(1) << 20;   // doubles (8 MiB)
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratch];
 
 constexpr int kMaxDevices = 64;
-double* g_scratch_addr[kMaxDevices] = {};
+struct ScratchSlot {
+  CUcontext ctx = nullptr;
+  double* addr = nullptr;
+};
+ScratchSlot g_scratch[kMaxDevices];
 std::mutex g_scratch_mu;
 
-// Device address of the scratch array on the current device (looked up once).
+typedef CUresult (*PFN_ctx_get_current)(CUcontext*);
+
+// The current CUDA context (driver API, reached through the runtime so that
+// the library needs no link against libcuda); null if it cannot be read.
+CUcontext current_context() {
+  static PFN_ctx_get_current fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_ctx_get_current>(p);
+    cudaGetLastError();
+  });
+  CUcontext c = nullptr;
+  if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
+
+// Device address of the scratch array on the current device and context.
 int scratch_address(double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -36,8 +65,12 @@ int scratch_address(double** out) {
     set_error("tp_slice_norms_noalloc: no usable current CUDA device");
     return TP_ECUDA;
   }
+  // null before the runtime has made a context current: the lookup below
+  // then runs (and creates the primary context), and the next call caches
+  const CUcontext ctx = current_context();
   std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
+  ScratchSlot& slot = g_scratch[dev];
+  if (!slot.addr || !ctx || slot.ctx != ctx) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
@@ -46,9 +79,10 @@ int scratch_address(double** out) {
                 cudaGetErrorString(e));
       return TP_ECUDA;
     }
-    g_scratch_addr[dev] = static_cast<double*>(p);
+    slot.addr = static_cast<double*>(p);
+    slot.ctx = ctx;
   }
-  *out = g_scratch_addr[dev];
+  *out = slot.addr;
   return TP_OK;
 }
 

@@ -257,6 +257,13 @@ int tp_sample_draw(const double* w, const double* w2, int64_t n, int64_t c, uint
                      as_stream(stream), sample_mode);
 }
 
+int tp_philox4x32_10(const uint32_t* counters, uint32_t k0, uint32_t k1, int64_t n,
+                     uint32_t* out, void* stream) {
+  if (n < 0 || n > (int64_t(1) << 40)) { set_error("tp_philox4x32_10: invalid n"); return TP_EINVAL; }
+  if (n > 0 && (!counters || !out)) { set_error("tp_philox4x32_10: NULL pointer"); return TP_ENULL; }
+  return launch_philox_words(counters, k0, k1, n, out, as_stream(stream));
+}
+
 size_t tp_workspace_query(int op, const int64_t* d, int nd, const tp_opts* opts) {
   if (!d) return 0;
   switch (op) {

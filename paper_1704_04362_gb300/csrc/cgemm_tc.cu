@@ -477,10 +477,8 @@ int launch_cgemm_tc(const CGemm& g, cudaStream_t st) {
   p.mt = int((g.M + TM - 1) / TM);
   p.nt = int((g.N + TN - 1) / TN);
   auto kernel = bf16 ? cgemm_tc_kernel<true> : cgemm_tc_kernel<false>;
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SMEM_BYTES));
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  TP_SET_SMEM(kernel, SMEM_BYTES);
+  const int sms = sm_count();
   const int64_t ntiles = int64_t(p.mt) * p.nt * g.h;
   const dim3 grid(unsigned(ntiles < sms ? ntiles : sms));
   {

@@ -367,14 +367,14 @@ int launch_rdft_kc(const DftGather& g, cudaStream_t st) {
     const int64_t n3p = (g.n3 + TU - 1) / TU * TU;
     const size_t smem = size_t(g.n3 + n3p * KC) * sizeof(float2) +
                         size_t(KC) * TR * (TCOL + 1) * sizeof(float);
-    cudaFuncSetAttribute(rdft_t_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    TP_SET_SMEM(rdft_t_kernel<KC>, smem);
     const int64_t bx = (g.rows + TR - 1) / TR;
     if (bx > 0x7fffffff) { set_error("rdft: too many rows"); return TP_EINVAL; }
     // the column tiles are walked grid-stride: with all rows live (no row
     // gather) about 16 blocks per SM suffice, and a column gather's capacity
     // can far exceed the picked count
     int64_t by = (g.cols + TCOL - 1) / TCOL;
-    const int64_t by_cap = bx >= 152 * 16 ? 1 : 152 * 16 / bx;
+    const int64_t by_cap = bx >= int64_t(sm_count()) * 16 ? 1 : int64_t(sm_count()) * 16 / bx;
     if (g.gather_dim != 1 && by > by_cap) by = by_cap;
     if (by > 65535) by = 65535;
     {
@@ -387,11 +387,11 @@ int launch_rdft_kc(const DftGather& g, cudaStream_t st) {
   const size_t stage_bytes = size_t(g.n3) * RB * TPT * sizeof(float);
   const int stage = (g.gather_dim == 1 && stage_bytes <= size_t(STAGE_BYTES_MAX)) ? 1 : 0;
   const size_t smem = size_t(g.n3 + nhp * KC) * sizeof(float2) + (stage ? stage_bytes : 0);
-  cudaFuncSetAttribute(rdft_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  TP_SET_SMEM(rdft_kernel<KC>, smem);
   const int64_t bx = (g.rows + RB * TPT - 1) / (RB * TPT);
   if (bx > 0x7fffffff) { set_error("rdft: too many rows"); return TP_EINVAL; }
   int64_t by = g.cols < 65535 ? g.cols : 65535;   // columns walked grid-stride
-  const int64_t by_cap = bx >= 152 * 16 ? 1 : 152 * 16 / bx;
+  const int64_t by_cap = bx >= int64_t(sm_count()) * 16 ? 1 : int64_t(sm_count()) * 16 / bx;
   if (g.gather_dim == 2 && by > by_cap) by = by_cap;   // see the transposed form
   {
     KernelScope ks("rdft", st);
@@ -406,9 +406,9 @@ int launch_irdft_kc(const float* in_re, const float* in_im, int64_t rows, int64_
   const int64_t h = n3 / 2 + 1;
   const int64_t hp = (h + TU - 1) / TU * TU;
   const size_t smem = size_t(n3 + hp * KC) * sizeof(float2);
-  cudaFuncSetAttribute(irdft_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  TP_SET_SMEM(irdft_kernel<KC>, smem);
   int64_t blocks = (rows + RB * TPT - 1) / (RB * TPT);
-  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks > int64_t(sm_count()) * 64) blocks = int64_t(sm_count()) * 64;
   {
     KernelScope ks("irdft", st);
     irdft_kernel<KC><<<unsigned(blocks), RB, smem, st>>>(in_re, in_im, rows, in_slice, int(n3), out);

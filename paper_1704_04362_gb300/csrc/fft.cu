@@ -287,9 +287,9 @@ int launch_fft_fwd(const float* X, int64_t rows, int64_t n3, float* ore, float* 
   }
   if (rows == 0) return TP_OK;
   const size_t smem = fft_smem(n3, nw);
-  cudaFuncSetAttribute(fft_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  TP_SET_SMEM(fft_fwd_kernel, smem);
   int64_t blocks = (rows + 2 * nw - 1) / (2 * nw);
-  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks > int64_t(sm_count()) * 64) blocks = int64_t(sm_count()) * 64;
   {
     KernelScope ks("fft_fwd", st);
     fft_fwd_kernel<<<unsigned(blocks), nw * 32, smem, st>>>(X, rows, plan, ore, oim, out_slice);
@@ -308,9 +308,9 @@ int launch_fft_inv(const float* ire, const float* iim, int64_t rows, int64_t in_
   }
   if (rows == 0) return TP_OK;
   const size_t smem = fft_smem(n3, nw);
-  cudaFuncSetAttribute(fft_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  TP_SET_SMEM(fft_inv_kernel, smem);
   int64_t blocks = (rows + 2 * nw - 1) / (2 * nw);
-  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks > int64_t(sm_count()) * 64) blocks = int64_t(sm_count()) * 64;
   {
     KernelScope ks("fft_inv", st);
     fft_inv_kernel<<<unsigned(blocks), nw * 32, smem, st>>>(ire, iim, rows, in_slice, plan, out);

@@ -241,8 +241,7 @@ int jacobi_float_blocked_launch(float* gr, float* gi, int64_t sG, float* vr, flo
                                 cudaStream_t st) {
   if (batch <= 0 || q <= 0) return TP_OK;
   const size_t smem = jb_smem_bytes(p);
-  cudaFuncSetAttribute(jacobi_blocked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       int(smem));
+  TP_SET_SMEM(jacobi_blocked_kernel, smem);
   {
     KernelScope ks("jacobi_blocked", st);
     jacobi_blocked_kernel<<<unsigned(batch), JB_THREADS, smem, st>>>(

@@ -314,7 +314,7 @@ int launch_rank_features(const float* sig, int64_t h, int l, void* feat, cudaStr
 int launch_mlp_forward(const void* w16, const void* x16, int64_t B, float* y, cudaStream_t st) {
   if (B == 0) return TP_OK;
   const size_t smem = sizeof(MlpSmem);
-  cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  TP_SET_SMEM(mlp_forward_kernel, smem);
   {
     KernelScope ks("mlp_forward", st);
     mlp_forward_kernel<<<unsigned((B + MLP_S - 1) / MLP_S), MLP_THREADS, smem, st>>>(
@@ -338,7 +338,7 @@ int launch_mlp_grad(const void* w16, const void* x16, const float* tgt, int64_t 
                     float* grad, cudaStream_t st) {
   const int64_t nb = (B + MLP_S - 1) / MLP_S;
   const size_t smem = sizeof(MlpSmem);
-  cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  TP_SET_SMEM(mlp_grad_kernel, smem);
   {
     KernelScope ks("mlp_grad", st);
     mlp_grad_kernel<<<unsigned(nb), MLP_THREADS, smem, st>>>(

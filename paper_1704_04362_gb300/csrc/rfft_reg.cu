@@ -398,14 +398,6 @@ __global__ void __launch_bounds__(kThreads) irfft_reg_kernel(const float* __rest
   }
 }
 
-int sm_count() {
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
-    sms = 152;
-  return sms;
-}
-
 // TP_RFFT_OVERSUB waves of resident blocks (the kernels stride over their
 // work), or fewer blocks when the work is smaller.
 #ifndef TP_RFFT_OVERSUB
@@ -440,11 +432,11 @@ int launch_fwd(const DftGather& g, cudaStream_t st, int oversub) {
         KernelScope ks("rdft_t", st);
         if (vec) {
           auto k = rfft_reg_ts_kernel<N, (N >= 4)>;
-          cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+          TP_SET_SMEM(k, smem);
           k<<<grid_for(k, tiles, smem, oversub), kThreads, smem, st>>>(g);
         } else {
           auto k = rfft_reg_ts_kernel<N, false>;
-          cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+          TP_SET_SMEM(k, smem);
           k<<<grid_for(k, tiles, smem, oversub), kThreads, smem, st>>>(g);
         }
       }

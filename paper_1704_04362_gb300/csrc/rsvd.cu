@@ -15,6 +15,7 @@
 #include <cmath>
 
 #include "jacobi_rot.cuh"
+#include "philox.cuh"
 
 namespace tp {
 
@@ -55,18 +56,6 @@ __global__ void conj_transpose_kernel(const float* __restrict__ ir, const float*
   }
 }
 
-__device__ __forceinline__ void philox(uint32_t c[4], uint32_t k0, uint32_t k1) {
-  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    if (r) { k0 += W0; k1 += W1; }
-    const uint32_t hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
-    const uint32_t hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
-    const uint32_t y0 = hi1 ^ c[1] ^ k0, y2 = hi0 ^ c[3] ^ k1;
-    c[0] = y0; c[1] = lo1; c[2] = y2; c[3] = lo0;
-  }
-}
-
 // Omega(r, c, f) at e = r + n2*(c + l*f): (s0 + i s1)/sqrt(2) from the top bits
 // of Philox(e, stream 2); the real slices take s0.
 __global__ void sketch_kernel(float* __restrict__ om_r, float* __restrict__ om_i, int64_t n2,
@@ -76,7 +65,7 @@ __global__ void sketch_kernel(float* __restrict__ om_r, float* __restrict__ om_i
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
        e += int64_t(gridDim.x) * blockDim.x) {
     uint32_t c[4] = {uint32_t(e), uint32_t(uint64_t(e) >> 32), 2u, 0u};
-    philox(c, uint32_t(seed), uint32_t(seed >> 32));
+    philox4x32_10(c, uint32_t(seed), uint32_t(seed >> 32));
     const float s0 = (c[0] >> 31) ? -1.f : 1.f;
     const float s1 = (c[1] >> 31) ? -1.f : 1.f;
     const int64_t f = e / (n2 * l);
@@ -646,7 +635,7 @@ __global__ void real_flags2_kernel(int* flags, int64_t h, int64_t n3) {
 
 unsigned grid_for(int64_t n) {
   int64_t b = (n + 255) / 256;
-  if (b > 152 * 16) b = 152 * 16;
+  if (b > int64_t(sm_count()) * 16) b = int64_t(sm_count()) * 16;
   if (b < 1) b = 1;
   return unsigned(b);
 }
@@ -779,13 +768,12 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
     return launch_cgemm(g, st);
   };
   const size_t qr_smem = size_t(2) * l * l * sizeof(double);
-  cudaFuncSetAttribute(cholqr2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(qr_smem));
+  TP_SET_SMEM(cholqr2_kernel, qr_smem);
   constexpr size_t kSmemCap = 200 * 1024;
   auto orth = [&](float* yr, float* yi, int64_t rows) {
     const size_t fast_smem = size_t(l) * l * (16 + 8) + size_t(rows + 1) * l * 8;
     if (fast_smem <= kSmemCap) {
-      cudaFuncSetAttribute(cholqr2_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           int(fast_smem));
+      TP_SET_SMEM(cholqr2_smem_kernel, fast_smem);
       KernelScope ks("cholqr2", st);
       cholqr2_smem_kernel<<<unsigned(h), QR_THREADS, fast_smem, st>>>(yr, yi, rows * l, int(rows),
                                                                      int(l), status);
@@ -809,8 +797,7 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
   const int sweeps = (opts && opts->max_sweeps > 0) ? opts->max_sweeps : 30;
   const size_t eig_smem = size_t(l) * (l | 1) * 48 + size_t(n2 + 1) * l * 8 + size_t((l + 1) / 2) * 40;
   if (eig_smem <= kSmemCap && l <= 128) {
-    cudaFuncSetAttribute(core_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(eig_smem));
+    TP_SET_SMEM(core_eig_kernel, eig_smem);
     {
       KernelScope ks("core_eig", st);
       core_eig_kernel<<<unsigned(h), EIG_THREADS, eig_smem, st>>>(

@@ -42,6 +42,37 @@ int launch_status(const char* what) {
 
 void note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+int set_smem_attr(const void* func, size_t bytes, const char* name) {
+  const cudaError_t e =
+      cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("%s: cannot allow %zu bytes of dynamic shared memory: %s", name, bytes,
+              cudaGetErrorString(e));
+    return TP_ECUDA;
+  }
+  return TP_OK;
+}
+
+int sm_count() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cache[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+    cudaGetLastError();
+    return 152;
+  }
+  int sms = cache[dev].load(std::memory_order_relaxed);
+  if (sms > 0) return sms;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms < 1) {
+    cudaGetLastError();
+    sms = 152;
+  }
+  cache[dev].store(sms, std::memory_order_relaxed);
+  return sms;
+}
+
 namespace {
 struct ProfRec {
   const char* name;

@@ -8,6 +8,7 @@
 // about 44 significant bits at float32 speed; the lanes of a column are
 // combined as float pairs, partial sums in float64, all in a fixed order,
 // making every norm deterministic run to run.
+#include "philox.cuh"
 #include "tp_internal.cuh"
 
 namespace tp {
@@ -140,7 +141,10 @@ __global__ void __launch_bounds__(256) horizontal_reduce_kernel(const double* __
 int64_t horizontal_chunks(int64_t n1, int64_t ncols) {
   // about four waves of 8 blocks per SM, so that the last wave's tail is
   // short, while the G n1 partial sums stay within 2^20 doubles (8 MiB) unless
-  // one wave alone needs more
+  // one wave alone needs more.  The SM count is fixed at GB300's 152 here, not
+  // queried: G is the partition of each row's sum, so a fixed G keeps the
+  // horizontal norms bit-identical on every device, and the no-allocation
+  // entry point's capacity check depends on it.
   const int64_t bx = (n1 + 255) / 256;
   const int64_t one_wave = (152 * 8 + bx - 1) / bx;
   int64_t G = (152 * 8 * 4 + bx - 1) / bx;
@@ -153,19 +157,6 @@ int64_t horizontal_chunks(int64_t n1, int64_t ncols) {
 }
 
 // ---------------------------------------------------------------- Philox
-__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
-  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
-  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    if (r) { k0 += W0; k1 += W1; }
-    const uint32_t hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
-    const uint32_t hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
-    const uint32_t y0 = hi1 ^ c[1] ^ k0, y2 = hi0 ^ c[3] ^ k1;
-    c[0] = y0; c[1] = lo1; c[2] = y2; c[3] = lo0;
-  }
-}
-
 __device__ __forceinline__ uint64_t uniform53(uint64_t j, uint32_t stream_id, uint64_t seed) {
   uint32_t c[4] = {uint32_t(j), uint32_t(j >> 32), stream_id, 0u};
   philox4x32_10(c, uint32_t(seed), uint32_t(seed >> 32));
@@ -380,7 +371,33 @@ __global__ void __launch_bounds__(1024) iid_draw_kernel(int64_t n, int64_t c, ui
   if (tid == 0) *count = c;
 }
 
+// Raw Philox4x32-10 words of n caller-given counters (tp_philox4x32_10).
+__global__ void philox_words_kernel(const uint32_t* __restrict__ ctr, uint32_t k0, uint32_t k1,
+                                    int64_t n, uint32_t* __restrict__ out) {
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    uint32_t c[4] = {ctr[4 * e], ctr[4 * e + 1], ctr[4 * e + 2], ctr[4 * e + 3]};
+    philox4x32_10(c, k0, k1);
+    out[4 * e] = c[0];
+    out[4 * e + 1] = c[1];
+    out[4 * e + 2] = c[2];
+    out[4 * e + 3] = c[3];
+  }
+}
+
 }  // namespace
+
+int launch_philox_words(const uint32_t* ctr, uint32_t k0, uint32_t k1, int64_t n, uint32_t* out,
+                        cudaStream_t st) {
+  if (n == 0) return TP_OK;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > int64_t(sm_count()) * 8) blocks = int64_t(sm_count()) * 8;
+  {
+    KernelScope ks("philox_words", st);
+    philox_words_kernel<<<unsigned(blocks), 256, 0, st>>>(ctr, k0, k1, n, out);
+  }
+  return launch_status("philox_words_kernel");
+}
 
 size_t norms_partial_count(int64_t n1, int64_t n2, int64_t n3, int which) {
   if (which == 0) return size_t(n2) * size_t(n3);
@@ -402,7 +419,7 @@ int launch_slice_norms(const float* X, int64_t n1, int64_t n2, int64_t n3, int w
     // autotuned among 4, 8, 16 and 32, default 16
     const auto run = [&](int c) {
       int64_t blocks = (warps * 32 + 255) / 256;
-      const int64_t cap = int64_t(152) * (int64_t(4) << c);
+      const int64_t cap = int64_t(sm_count()) * (int64_t(4) << c);
       if (blocks > cap) blocks = cap;
       if (blocks < 1) blocks = 1;
       {
@@ -425,7 +442,7 @@ int launch_slice_norms(const float* X, int64_t n1, int64_t n2, int64_t n3, int w
     if (!rc) rc = run(c);
     if (rc) return rc;
     int64_t rb = (n2 + 255) / 256;
-    if (rb > 152 * 8) rb = 152 * 8;
+    if (rb > int64_t(sm_count()) * 8) rb = int64_t(sm_count()) * 8;
     {
       KernelScope ks("norms_reduce", st);
       lateral_reduce_kernel<<<unsigned(rb), 256, 0, st>>>(partial, n2, n3, out);
@@ -440,7 +457,7 @@ int launch_slice_norms(const float* X, int64_t n1, int64_t n2, int64_t n3, int w
                                                                                 chunk, partial);
     }
     int64_t rb = (n1 + 31) / 32;
-    if (rb > 152 * 8) rb = 152 * 8;
+    if (rb > int64_t(sm_count()) * 8) rb = int64_t(sm_count()) * 8;
     {
       KernelScope ks("norms_reduce", st);
       horizontal_reduce_kernel<<<unsigned(rb), 256, 0, st>>>(partial, n1, G, out);

@@ -364,7 +364,7 @@ __global__ void ns_factor_kernel(double* tr, double* ti, int q, int64_t total) {
 
 unsigned grid_of(int64_t n) {
   int64_t b = (n + 255) / 256;
-  if (b > 152 * 16) b = 152 * 16;
+  if (b > int64_t(sm_count()) * 16) b = int64_t(sm_count()) * 16;
   if (b < 1) b = 1;
   return unsigned(b);
 }
@@ -384,7 +384,7 @@ int jacobi_launch(T* gr, T* gi, int64_t sG, T* vr, T* vi, int64_t sV, T* sig, in
   const size_t smem = jacobi_smem<T>(p, q);
   if (smem) {
     flags |= JAC_SMEM;
-    cudaFuncSetAttribute(jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    TP_SET_SMEM(jacobi_kernel<T>, smem);
   }
   {
     KernelScope ks(sizeof(T) == 4 ? "jacobi_f32" : "jacobi_svd", st);

@@ -15,6 +15,7 @@ namespace tp {
 void set_error(const char* fmt, ...);
 int launch_status(const char* what);      // cudaGetLastError -> TP_OK / TP_ECUDA
 void note_launches(uint64_t n);           // kernel launch counter
+int sm_count();                           // SMs of the current device (cached per device)
 
 // Brackets one kernel launch: counts it and, while tp_profile_start() is in
 // effect, records a CUDA event pair around it on the launch stream.
@@ -25,6 +26,16 @@ struct KernelScope {
   cudaStream_t st;
   int slot;
 };
+// Raises a kernel's dynamic shared memory limit to `bytes`; a failure is
+// reported (TP_ECUDA with the kernel's name and the size) instead of
+// surfacing later as a launch error under another name.
+int set_smem_attr(const void* func, size_t bytes, const char* name);
+#define TP_SET_SMEM(kernel, bytes)                                                   \
+  do {                                                                             \
+    if (int rc_smem_ = ::tp::set_smem_attr((const void*)(kernel), (bytes), #kernel)) \
+      return rc_smem_;                                                             \
+  } while (0)
+
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 // Bump allocator over a workspace buffer; every block 256-byte aligned.
@@ -115,6 +126,10 @@ int launch_draw(const double* w, const double* w2, int64_t n, int64_t c, uint64_
                 int mode, uint32_t stream_id, int32_t* idx, float* scale, int64_t* count,
                 double* q_out, void* scratch, cudaStream_t st,
                 int sample_mode = TP_SAMPLE_BERNOULLI);
+
+// Raw Philox4x32-10 words: out[4e..4e+3] = philox(ctr[4e..4e+3], key (k0, k1)).
+int launch_philox_words(const uint32_t* ctr, uint32_t k0, uint32_t k1, int64_t n, uint32_t* out,
+                        cudaStream_t st);
 
 // Bit length of v (0 for v <= 0): the size class of a tuning key, so that
 // problems within a factor of two share one tuned choice.

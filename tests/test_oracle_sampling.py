@@ -31,6 +31,25 @@ def test_philox_uniformity_and_avalanche():
     assert np.count_nonzero(a == b) == 0 and np.count_nonzero(a == c) == 0
 
 
+# Known-answer vectors of Philox4x32-10 published with the generator's
+# reference implementation (Salmon et al., SC'11, the Random123 distribution):
+# (counter words 0..3, key words 0..1) -> output words 0..3.
+PHILOX_KAT = [
+    ((0x00000000, 0x00000000, 0x00000000, 0x00000000), (0x00000000, 0x00000000),
+     (0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8)),
+    ((0xffffffff, 0xffffffff, 0xffffffff, 0xffffffff), (0xffffffff, 0xffffffff),
+     (0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd)),
+    ((0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344), (0xa4093822, 0x299f31d0),
+     (0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1)),
+]
+
+
+@pytest.mark.parametrize("ctr,key,want", PHILOX_KAT)
+def test_philox_known_answer_vectors(ctr, key, want):
+    got = tuple(int(x) for x in P.philox4x32_10(*ctr, *key))
+    assert got == want, [hex(x) for x in got]
+
+
 def test_threshold_exact_edges():
     Q = P.threshold53(np.array([0.0, 1.0, 0.5, 2.0 ** -53, 1 - 2.0 ** -53]))
     assert list(Q) == [0, 2 ** 53, 2 ** 52, 1, 2 ** 53 - 1]

@@ -8,9 +8,13 @@ def to_np(x) -> np.ndarray:
 
 
 def rel_fro(a, b) -> float:
-    """||a - b||_F / ||b||_F (0/0 -> 0)."""
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
+    """||a - b||_F / ||b||_F (0/0 -> 0); complex arguments keep their
+    imaginary parts."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    dt = np.complex128 if (np.iscomplexobj(a) or np.iscomplexobj(b)) else np.float64
+    a = a.astype(dt)
+    b = b.astype(dt)
     nb = np.linalg.norm(b)
     na = np.linalg.norm(a - b)
     if nb == 0:
