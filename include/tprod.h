@@ -90,6 +90,13 @@ typedef struct {
   void* workspace;        /* device scratch or NULL (library-managed) */
   size_t workspace_bytes; /* size of `workspace` */
   int32_t* status;        /* device int32 receiving TP_DEV_* bits, or NULL */
+  int64_t pipeline_wait_limit; /* failure-detection test hook: bound, in clock64 ticks, of the
+                              tensor-core GEMM's wait for a loaded operand stage (0 = the
+                              default, about two seconds).  A tiny value makes that wait
+                              run out: the kernel then sets TP_DEV_TIMEOUT, stops, waits
+                              for the copies and products it already issued and returns;
+                              the outputs of that call are invalid, the context stays
+                              usable. */
 } tp_opts;
 
 /* Operation codes for tp_workspace_query(). */

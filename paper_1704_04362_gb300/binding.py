@@ -50,7 +50,7 @@ class TprodError(RuntimeError):
 class TpOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_sweeps", ctypes.c_int),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
-                ("status", ctypes.c_void_p)]
+                ("status", ctypes.c_void_p), ("pipeline_wait_limit", ctypes.c_int64)]
 
 
 class TpTensorDesc(ctypes.Structure):
@@ -301,12 +301,12 @@ def _stream():
 _WS = {}
 
 
-def _opts(op, dims, precision=TP_FP32, status=None, max_sweeps=0):
+def _opts(op, dims, precision=TP_FP32, status=None, max_sweeps=0, wait_limit=0):
     """tp_opts with a torch-allocated workspace large enough for this call."""
     torch = _torch()
     L = lib()
     d = (ctypes.c_int64 * len(dims))(*[int(v) for v in dims])
-    o = TpOpts(int(precision), int(max_sweeps), None, 0, None)
+    o = TpOpts(int(precision), int(max_sweeps), None, 0, None, int(wait_limit))
     need = int(L.tp_workspace_query(op, ctypes.cast(d, ctypes.c_void_p), len(dims), ctypes.byref(o)))
     dev = torch.cuda.current_device()
     buf = _WS.get(dev)
@@ -322,16 +322,17 @@ def _opts(op, dims, precision=TP_FP32, status=None, max_sweeps=0):
 
 # ---------------------------------------------------------------- entry points
 
-def tprod(A, B, C=None, precision=TP_FP32, status=None):
+def tprod(A, B, C=None, precision=TP_FP32, status=None, wait_limit=0):
     """C = A * B (Def. 2.1 / Algorithm 1).  ``status``: optional device int32
-    tensor that receives TP_DEV_* bits."""
+    tensor that receives TP_DEV_* bits.  ``wait_limit``: tp_opts'
+    pipeline_wait_limit (a failure-detection test hook; 0 = default)."""
     n1, n2, n3 = A.shape
     n2b, n4, n3b = B.shape
     if n2b != n2 or n3b != n3:
         raise TprodError(f"tprod: shapes {tuple(A.shape)} and {tuple(B.shape)} do not chain")
     if C is None:
         C = empty_tensor(n1, n4, n3, device=A.device)
-    o = _opts(TP_OP_TPROD, (n1, n2, n4, n3), precision, status)
+    o = _opts(TP_OP_TPROD, (n1, n2, n4, n3), precision, status, wait_limit=wait_limit)
     rc = lib().tprod(_tensor_arg(A, "A"), _tensor_arg(B, "B"), _tensor_arg(C, "C"),
                      n1, n2, n4, n3, ctypes.byref(o), _stream())
     _check(rc, "tprod")

@@ -125,7 +125,8 @@ int tprod(const float* A, const float* B, float* C, int64_t n1, int64_t n2, int6
   if ((rc = launch_rdft(gb, st))) return rc;
   CGemm g{Ah.re, Ah.im, Bh.re, Bh.im, Cr, Ci, n1, n4, n2, nullptr,
           la, lk, n1, la * (tc ? n1 : n2), lk * n4, n1 * n4, h, n3, prec,
-          Ah.re_lo, Ah.im_lo, Bh.re_lo, Bh.im_lo, n2, opts ? opts->status : nullptr};
+          Ah.re_lo, Ah.im_lo, Bh.re_lo, Bh.im_lo, n2, opts ? opts->status : nullptr,
+          opts ? opts->pipeline_wait_limit : 0};
   if ((rc = launch_cgemm(g, st))) return rc;
   return launch_irdft(Cr, Ci, n1 * n4, n1 * n4, n3, C, st);
 }
@@ -208,7 +209,8 @@ int tprod_sampled(const float* A, const float* B, float* Z, int64_t n1, int64_t 
   // S6: facewise products with inner dimension c' read on the device
   CGemm g{Ch.re, Ch.im, Rh.re, Rh.im, Zr, Zi, n1, n4, 0, cnt,
           la, lk, n1, la * (tc ? n1 : n2), lk * n4, n1 * n4, h, n3, prec,
-          Ch.re_lo, Ch.im_lo, Rh.re_lo, Rh.im_lo, n2, opts ? opts->status : nullptr};
+          Ch.re_lo, Ch.im_lo, Rh.re_lo, Rh.im_lo, n2, opts ? opts->status : nullptr,
+          opts ? opts->pipeline_wait_limit : 0};
   if ((rc = launch_cgemm(g, st))) return rc;
   // S7: inverse transform
   return launch_irdft(Zr, Zi, n1 * n4, n1 * n4, n3, Z, st);

@@ -18,9 +18,18 @@
 //                   one of two TMEM accumulator sets (Re at +0, Im at +128
 //                   columns; sets at columns 0 and 256); tcgen05.commit frees a
 //                   stage, and after a tile's last K block marks its set full
-//   warps 2-5       epilogue: wait for a full set, tcgen05.ld 32x32b,
-//                   bounds-checked coalesced stores, mark the set empty; the
-//                   next tile's MMAs run into the other set meanwhile
+//   warps 2-9       epilogue: two warps per TMEM lane quarter, each owning
+//                   64 of the tile's 128 columns; wait for a full set,
+//                   tcgen05.ld 32x32b, add into float32 registers, mark the
+//                   set empty; after a tile's last chunk, bounds-checked
+//                   coalesced stores
+// K is cut into chunks of KCB K blocks (256 bf16 or 128 tf32 elements): every
+// chunk accumulates into a fresh TMEM set (the sets alternate, so the next
+// chunk's MMAs run while the epilogue drains the previous one) and the
+// epilogue adds the chunk sums in float32 registers with round-to-nearest.
+// The tensor cores' own float32 accumulation error grows with the number of
+// updates it absorbs; draining every chunk bounds that growth by the chunk
+// length, so the split forms keep float32-level error at any K.
 // Both operands are K-major (kind::tf32 takes no transposed operand): A
 // planes hold element (m, kk) at kk + lda*m, B planes (kk, n) at kk + ldb*n,
 // read as 64-byte-swizzled tiles of 128 rows.  Every mbarrier wait is bounded:
@@ -34,7 +43,10 @@
 namespace tp {
 namespace {
 
-constexpr int TM = 128, TN = 128, ROWB = 64, STAGES = 3, NTHR = 192;   // ROWB: K-block row bytes
+constexpr int TM = 128, TN = 128, ROWB = 64, STAGES = 3;   // ROWB: K-block row bytes
+constexpr int EPI_WARPS = 8, NTHR = 32 * (2 + EPI_WARPS);
+constexpr int KCB = 8;                                   // K blocks per accumulation chunk
+constexpr int EPI_COLS = TN / 2;                         // columns per epilogue warp
 constexpr uint32_t A_PLANE_BYTES = TM * ROWB;           // 8 KB
 constexpr uint32_t B_PLANE_BYTES = TN * ROWB;           // 8 KB
 constexpr uint32_t STAGE_BYTES = 4 * A_PLANE_BYTES + 4 * B_PLANE_BYTES;   // 64 KB
@@ -53,6 +65,7 @@ struct TcParams {
   int64_t h, n3;
   int32_t* status;
   int mt, nt;   // output tiles along M and N
+  long long mma_wait_limit;   // the MMA warp's wait for loaded stages (clock64 ticks)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -80,13 +93,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 }
 
 // Bounded wait; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          long long limit = WAIT_LIMIT) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > WAIT_LIMIT) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
+}
+
+// Bounded wait that also gives up once another warp has raised the abort
+// flag: 0 = phase completed, 1 = timeout, 2 = aborted.
+__device__ __forceinline__ int mbar_wait_or_abort(uint32_t bar, uint32_t parity,
+                                                  const int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return 0;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*(const volatile int*)abort_flag) return 2;
+    if (clock64() - t0 > WAIT_LIMIT) return 1;
+  }
+  return 0;
 }
 
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
@@ -155,17 +182,18 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+// 16 consecutive TMEM columns of this warp's 32 lanes (no wait).
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
-      "%30, %31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
         "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
-        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
-        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        "=r"(v[14]), "=r"(v[15])
       : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
@@ -173,8 +201,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+// 200 registers: 10 warps x 32 x 200 fit the register file; under
+// __launch_bounds__(NTHR, 1) the compiler picked 168 and spilled the epilogue.
 template <bool BF16>
-__global__ void __launch_bounds__(NTHR, 1) cgemm_tc_kernel(const __grid_constant__ TcParams p) {
+__global__ void __maxnreg__(200) cgemm_tc_kernel(const __grid_constant__ TcParams p) {
   constexpr int TBK = BF16 ? ROWB / 2 : ROWB / 4;   // K elements per K block
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -196,6 +226,7 @@ __global__ void __launch_bounds__(NTHR, 1) cgemm_tc_kernel(const __grid_constant
   const int nsub_last = (klast + SUBK - 1) / SUBK;
   const int tiles_per_f = p.mt * p.nt;
   const int64_t ntiles = int64_t(tiles_per_f) * p.h;
+  const int nch = (nkb + KCB - 1) / KCB;   // accumulation chunks per tile
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
@@ -205,7 +236,7 @@ __global__ void __launch_bounds__(NTHR, 1) cgemm_tc_kernel(const __grid_constant
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&acc_full[b]), 1);
-      mbar_init(smem_u32(&acc_empty[b]), 4);   // one arrival per epilogue warp
+      mbar_init(smem_u32(&acc_empty[b]), EPI_WARPS);   // one arrival per epilogue warp
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     for (int i = 0; i < 4; ++i) {
@@ -236,10 +267,13 @@ __global__ void __launch_bounds__(NTHR, 1) cgemm_tc_kernel(const __grid_constant
       for (int kb = 0; kb < nkb; ++kb, ++it) {
         const int s = int(it % STAGES);
         const int64_t r = it / STAGES;
-        if (r > 0 && !mbar_wait(smem_u32(&empty[s]), uint32_t((r - 1) & 1))) {
-          atomicExch(&abort_flag, 1);
-          ok = false;
-          break;
+        if (r > 0) {
+          const int w = mbar_wait_or_abort(smem_u32(&empty[s]), uint32_t((r - 1) & 1), &abort_flag);
+          if (w) {
+            if (w == 1) atomicExch(&abort_flag, 1);
+            ok = false;
+            break;
+          }
         }
         if (*(volatile int*)&abort_flag) { ok = false; break; }
         const uint32_t fb = smem_u32(&full[s]);
@@ -259,110 +293,141 @@ __global__ void __launch_bounds__(NTHR, 1) cgemm_tc_kernel(const __grid_constant
     }
   } else if (warp == 1 && lane == 0 && nkb > 0) {
     // ---------------- MMA issuer
-    int64_t it = 0;
-    int64_t local = 0;   // tiles processed by this CTA
+    int64_t it = 0;   // global K-block counter (stage ring)
+    int64_t ch = 0;   // global chunk counter (accumulator sets alternate per chunk)
     bool ok = true;
-    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++local) {
+    const uint32_t id = BF16 ? IDESC_BF16 : IDESC, idn = BF16 ? IDESC_BF16_NEG : IDESC_NEG;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       const int f = int(t / tiles_per_f);
       const bool real_slice = (f == 0) || ((p.n3 % 2 == 0) && f == p.h - 1);
-      const int b = int(local & 1);
-      const int64_t use = local >> 1;
-      if (use > 0 && !mbar_wait(smem_u32(&acc_empty[b]), uint32_t((use - 1) & 1))) {
-        atomicExch(&abort_flag, 1);
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t dre = tmem + uint32_t(b) * (2 * TN), dim = dre + TN;
-      // full-width MMAs on every tile (a narrower MMA for the ragged last
-      // column of tiles measured slower than multiplying its zero padding)
-      const uint32_t id = BF16 ? IDESC_BF16 : IDESC, idn = BF16 ? IDESC_BF16_NEG : IDESC_NEG;
-      for (int kb = 0; kb < nkb; ++kb, ++it) {
-        const int s = int(it % STAGES);
-        if (!mbar_wait(smem_u32(&full[s]), uint32_t((it / STAGES) & 1))) {
+      for (int c = 0; c < nch && ok; ++c, ++ch) {
+        const int b = int(ch & 1);
+        const int64_t use = ch >> 1;
+        if (use > 0 && !mbar_wait(smem_u32(&acc_empty[b]), uint32_t((use - 1) & 1))) {
+          atomicExch(&abort_flag, 1);
           ok = false;
           break;
         }
-        if (*(volatile int*)&abort_flag) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t st = smem_u32(smem + size_t(s) * STAGE_BYTES);
-        // the last K block runs only the 32-byte steps that hold data
-        const int nsub = kb == nkb - 1 ? nsub_last : ROWB / 32;
-#pragma unroll
-        for (int sub = 0; sub < ROWB / 32; ++sub) {
-          if (sub >= nsub) break;
-          uint64_t a[4], bb[4];
-#pragma unroll
-          for (int pl = 0; pl < 4; ++pl) {
-            a[pl] = smem_desc(st + pl * A_PLANE_BYTES + sub * 32, 16, 512, LAYOUT_SW64);
-            bb[pl] = smem_desc(st + 4 * A_PLANE_BYTES + pl * B_PLANE_BYTES + sub * 32, 16, 512,
-                               LAYOUT_SW64);
+        const uint32_t dre = tmem + uint32_t(b) * (2 * TN), dim = dre + TN;
+        // full-width MMAs on every tile (a narrower MMA for the ragged last
+        // column of tiles measured slower than multiplying its zero padding)
+        const int kb0 = c * KCB, kb1 = min(nkb, kb0 + KCB);
+        for (int kb = kb0; kb < kb1; ++kb, ++it) {
+          const int s = int(it % STAGES);
+          if (!mbar_wait(smem_u32(&full[s]), uint32_t((it / STAGES) & 1), p.mma_wait_limit)) {
+            // raise the flag before the commit below, so that the epilogue
+            // sees it once this chunk's MMAs have completed
+            atomicExch(&abort_flag, 1);
+            ok = false;
+            break;
           }
-          const uint32_t first = (kb == 0 && sub == 0) ? 0u : 1u;
-          // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
-          mma_step<BF16>(dre, a[0], bb[0], id, first);
-          mma_step<BF16>(dre, a[0], bb[1], id, 1);
-          mma_step<BF16>(dre, a[1], bb[0], id, 1);
-          if (!real_slice) {
-            mma_step<BF16>(dre, a[2], bb[2], idn, 1);
-            mma_step<BF16>(dre, a[2], bb[3], idn, 1);
-            mma_step<BF16>(dre, a[3], bb[2], idn, 1);
-            mma_step<BF16>(dim, a[0], bb[2], id, first);
-            mma_step<BF16>(dim, a[0], bb[3], id, 1);
-            mma_step<BF16>(dim, a[1], bb[2], id, 1);
-            mma_step<BF16>(dim, a[2], bb[0], id, 1);
-            mma_step<BF16>(dim, a[2], bb[1], id, 1);
-            mma_step<BF16>(dim, a[3], bb[0], id, 1);
+          if (*(volatile int*)&abort_flag) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t st = smem_u32(smem + size_t(s) * STAGE_BYTES);
+          // the last K block runs only the 32-byte steps that hold data
+          const int nsub = kb == nkb - 1 ? nsub_last : ROWB / 32;
+#pragma unroll
+          for (int sub = 0; sub < ROWB / 32; ++sub) {
+            if (sub >= nsub) break;
+            uint64_t a[4], bb[4];
+#pragma unroll
+            for (int pl = 0; pl < 4; ++pl) {
+              a[pl] = smem_desc(st + pl * A_PLANE_BYTES + sub * 32, 16, 512, LAYOUT_SW64);
+              bb[pl] = smem_desc(st + 4 * A_PLANE_BYTES + pl * B_PLANE_BYTES + sub * 32, 16, 512,
+                                 LAYOUT_SW64);
+            }
+            const uint32_t first = (kb == kb0 && sub == 0) ? 0u : 1u;
+            // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
+            mma_step<BF16>(dre, a[0], bb[0], id, first);
+            mma_step<BF16>(dre, a[0], bb[1], id, 1);
+            mma_step<BF16>(dre, a[1], bb[0], id, 1);
+            if (!real_slice) {
+              mma_step<BF16>(dre, a[2], bb[2], idn, 1);
+              mma_step<BF16>(dre, a[2], bb[3], idn, 1);
+              mma_step<BF16>(dre, a[3], bb[2], idn, 1);
+              mma_step<BF16>(dim, a[0], bb[2], id, first);
+              mma_step<BF16>(dim, a[0], bb[3], id, 1);
+              mma_step<BF16>(dim, a[1], bb[2], id, 1);
+              mma_step<BF16>(dim, a[2], bb[0], id, 1);
+              mma_step<BF16>(dim, a[2], bb[1], id, 1);
+              mma_step<BF16>(dim, a[3], bb[0], id, 1);
+            }
           }
+          mma_commit(smem_u32(&empty[s]));   // stage s free once these MMAs finish
         }
-        mma_commit(smem_u32(&empty[s]));   // stage s free once these MMAs finish
+        mma_commit(smem_u32(&acc_full[b]));  // chunk's accumulator set final (or abandoned)
       }
-      mma_commit(smem_u32(&acc_full[b]));  // accumulator set b final (or abandoned)
     }
     if (!ok) atomicExch(&abort_flag, 1);
   } else if (warp >= 2) {
-    // ---------------- epilogue warps: TMEM lane quarter = warp % 4
+    // ---------------- epilogue warps: TMEM lane quarter = warp % 4, column
+    // half = which of the two warps of that quarter
     const int q = warp & 3;
-    int64_t local = 0;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++local) {
+    const int half = (warp - 2) >> 2;
+    int64_t ch = 0;
+    bool stop = false;
+    for (int64_t t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
       const int f = int(t / tiles_per_f);
       const int rem = int(t - int64_t(f) * tiles_per_f);
-      const int64_t m0 = int64_t(rem / p.nt) * TM, n0 = int64_t(rem % p.nt) * TN;
+      const int64_t m0 = int64_t(rem / p.nt) * TM;
+      const int64_t n0 = int64_t(rem % p.nt) * TN + half * EPI_COLS;
       const bool real_slice = (f == 0) || ((p.n3 % 2 == 0) && f == p.h - 1);
-      const int b = int(local & 1);
-      const int64_t use = local >> 1;
-      bool have = nkb > 0;
-      if (have && !mbar_wait(smem_u32(&acc_full[b]), uint32_t(use & 1))) {
-        atomicExch(&abort_flag, 1);
-        have = false;
-      }
-      have = __all_sync(0xffffffffu, have);   // tcgen05.ld below is warp-collective
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int64_t m = m0 + q * 32 + lane;
-      float* zr = p.zr + int64_t(f) * p.sZ;
-      float* zi = p.zi + int64_t(f) * p.sZ;
-      const uint32_t base = tmem + (uint32_t(q * 32) << 16) + uint32_t(b) * (2 * TN);
-      for (int c0 = 0; c0 < TN; c0 += 32) {
-        uint32_t vr[32], vi[32];
-        if (have) {
-          tmem_ld32(base + uint32_t(c0), vr);
-          if (!real_slice) tmem_ld32(base + uint32_t(TN + c0), vi);
-        }
-        if (m < p.M) {
+      float accr[EPI_COLS], acci[EPI_COLS];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int64_t n = n0 + c0 + j;
-            if (n < p.N) {
-              zr[m + p.ldz * n] = have ? __uint_as_float(vr[j]) : 0.f;
-              zi[m + p.ldz * n] = (have && !real_slice) ? __uint_as_float(vi[j]) : 0.f;
+      for (int j = 0; j < EPI_COLS; ++j) {
+        accr[j] = 0.f;
+        acci[j] = 0.f;
+      }
+      for (int c = 0; c < nch; ++c, ++ch) {
+        const int b = int(ch & 1);
+        const int64_t use = ch >> 1;
+        bool have = mbar_wait(smem_u32(&acc_full[b]), uint32_t(use & 1));
+        if (!have) atomicExch(&abort_flag, 1);
+        have = __all_sync(0xffffffffu, have);   // tcgen05.ld below is warp-collective
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (have) {
+          const uint32_t base = tmem + (uint32_t(q * 32) << 16) + uint32_t(b) * (2 * TN) +
+                                uint32_t(half * EPI_COLS);
+#pragma unroll
+          for (int c0 = 0; c0 < EPI_COLS; c0 += 16) {
+            uint32_t vr[16], vi[16];
+            tmem_ld16_nowait(base + uint32_t(c0), vr);
+            if (!real_slice) tmem_ld16_nowait(base + uint32_t(TN + c0), vi);
+            tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              // chunk sums added in float32, round to nearest
+              accr[c0 + j] = c == 0 ? __uint_as_float(vr[j]) : accr[c0 + j] + __uint_as_float(vr[j]);
+              if (!real_slice)
+                acci[c0 + j] =
+                    c == 0 ? __uint_as_float(vi[j]) : acci[c0 + j] + __uint_as_float(vi[j]);
             }
           }
         }
+        // hand set b back to the MMA warp
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
+        if (!have || *(volatile int*)&abort_flag) {
+          stop = true;
+          break;
+        }
       }
-      // hand set b back to the MMA warp
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0 && nkb > 0) mbar_arrive(smem_u32(&acc_empty[b]));
-      if (*(volatile int*)&abort_flag) break;
+      if (stop) break;
+      const int64_t m = m0 + q * 32 + lane;
+      if (m < p.M) {
+        float* zr = p.zr + int64_t(f) * p.sZ;
+        float* zi = p.zi + int64_t(f) * p.sZ;
+#pragma unroll
+        for (int j = 0; j < EPI_COLS; ++j) {
+          const int64_t n = n0 + j;
+          if (n < p.N) {
+            zr[m + p.ldz * n] = accr[j];
+            zi[m + p.ldz * n] = real_slice ? 0.f : acci[j];
+          }
+        }
+      }
     }
   }
   __syncwarp();
@@ -476,6 +541,7 @@ int launch_cgemm_tc(const CGemm& g, cudaStream_t st) {
   p.status = g.status;
   p.mt = int((g.M + TM - 1) / TM);
   p.nt = int((g.N + TN - 1) / TN);
+  p.mma_wait_limit = g.wait_limit > 0 ? g.wait_limit : WAIT_LIMIT;
   auto kernel = bf16 ? cgemm_tc_kernel<true> : cgemm_tc_kernel<false>;
   TP_SET_SMEM(kernel, SMEM_BYTES);
   const int sms = sm_count();

@@ -105,6 +105,9 @@ struct CGemm {
   const float *ar_lo, *ai_lo, *br_lo, *bi_lo;
   int64_t kcap;
   int32_t* status;
+  // tensor-core path: bound of the MMA warp's wait for a loaded stage, in
+  // clock64 ticks (0 = the default of about two seconds)
+  long long wait_limit = 0;
 };
 int launch_cgemm(const CGemm& g, cudaStream_t st);
 
