@@ -309,15 +309,18 @@ def bench_rows(tp, torch, with_cpu):
     return rows
 
 
-def bench_svt_batched(tp, torch, count=256, warm_iters=3):
+def bench_svt_batched(tp, torch, count=256, iters=100):
     """The batched completion workload: `count` videos of uneven size (H, W, T
     drawn uniformly from 64..480 x 64..360 x 16..120, PCG64 seed 0), each
     tubal rank 10 (N(0,1) factors) at unit RMS plus sigma = 0.01 noise, 50%
     observed uniformly at random; tcomplete_svt_batched from L = E = Y = 0,
-    mu0 = 1e-3.  After one untimed call, one call of 1 iteration (cold slice Jacobi) and one of
-    1 + warm_iters iterations (the later ones replay the captured graph with
-    warm-started Jacobi) are timed; warm iterations/s = warm_iters / the
-    difference."""
+    mu0 = 1e-3, `iters` iterations in one call.  The first iteration runs
+    directly (cold slice Jacobi), the later ones replay one captured CUDA
+    graph of an iteration over all tensors; the library's profiler times the
+    replays as one region on the launch stream (CUDA events), so the warm
+    iteration time is that region over iters - 1 and the first iteration is
+    the call's time minus it.  After one untimed 1-iteration call (the
+    autotuner times its candidate launch shapes on first use)."""
     from paper_1704_04362_gb300 import synth
     sizes = synth.video_sizes(count, seed=0)
     data, truths = [], []
@@ -337,7 +340,7 @@ def bench_svt_batched(tp, torch, count=256, warm_iters=3):
         truths.append(truth)
         del noise, keep
 
-    def run(iters):
+    def run(n):
         for d in data:
             d[2].zero_()
             d[3].zero_()
@@ -345,31 +348,37 @@ def bench_svt_batched(tp, torch, count=256, warm_iters=3):
             d[5].fill_(1e-3)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tp.profile_start()
         e0.record()
-        tp.tcomplete_svt_batched(data, iters)
+        tp.tcomplete_svt_batched(data, n)
         e1.record()
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1)
+        prof = tp.profile_stop()
+        return e0.elapsed_time(e1), prof
 
-    run(1)   # untimed: the autotuner times its candidate launch shapes on first use
+    run(1)
     n0 = tp.launch_count()
-    cold_ms = run(1)
-    full_ms = run(1 + warm_iters)
+    total_ms, prof = run(iters)
     launches = tp.launch_count() - n0
+    replay_ms = prof.get("svt_graph_replays", (0.0, 0))[0]
+    warm_ms = replay_ms / max(1, iters - 1)
     num = sum(float(torch.linalg.vector_norm((d[2] - t).double()) ** 2) for d, t in zip(data, truths))
     den = sum(float(torch.linalg.vector_norm(t.double()) ** 2) for t in truths)
     elems = sum(a * b * c for a, b, c in sizes)
     slices = sum(c // 2 + 1 for _, _, c in sizes)
+    first = {k: v[0] for k, v in prof.items() if k != "svt_graph_replays"}
     del data, truths
-    warm_ms = (full_ms - cold_ms) / warm_iters
     return {"workload": f"{count} videos of uneven size (64..480 x 64..360 x 16..120), "
                         f"{elems} elements, {slices} half-spectrum slices per iteration, "
                         "tubal rank 10 + sigma 0.01, 50% observed",
-            "first_iteration_ms": cold_ms, "warm_iteration_ms": warm_ms,
-            "warm_iterations_per_s": 1e3 / warm_ms, "iterations_timed": 1 + warm_iters,
+            "precision": "fp32",
+            "iterations": iters, "total_ms": total_ms,
+            "first_iteration_ms": total_ms - replay_ms, "warm_iteration_ms": warm_ms,
+            "warm_iterations_per_s": 1e3 / warm_ms if warm_ms > 0 else None,
             "relative_error_to_truth": (num / den) ** 0.5, "gpu_launches": launches,
+            "first_iteration_kernels_ms": first,
             "note": "iterations after the first replay one captured CUDA graph over all "
-                    "tensors (8 side streams)"}
+                    "tensors (8 side streams), timed as one profiled region"}
 
 
 def orthonormal_tube_tensor(torch, n1, r, n3, seed):
@@ -444,7 +453,7 @@ def bench_table1(tp, torch, configs=((100, 460), (200, 1000), (300, 1700), (400,
             "cases": out}
 
 
-def bench_learned(torch, train_count=192, eval_shape=(1024, 1024, 64),
+def bench_learned(torch, train_count=192, eval_n3=(64, 128, 256), eval_n12=(1024, 1024),
                   alphas=(1.5, 2.0, 2.5, 3.0, 3.5, 4.0)):
     """The learned sketch-size predictor against the plain adaptive method
     (rank rule on a 50-column sketch, q = 2) on tensors shaped like the
@@ -466,22 +475,25 @@ def bench_learned(torch, train_count=192, eval_shape=(1024, 1024, 64),
     _, w16, losses = P.train(x, t, steps=3000, lr=2e-3, seed=1)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    n1, n2, n3 = eval_shape
+    n1, n2 = eval_n12
     cases = []
-    for i, a in enumerate(alphas):
-        X, spec = synth.spectral_torch(n1, n2, n3, a, 0.3, 77000 + i)
-        r_p, _, _ = P.decompose(X, None, seed=i)
-        r_l, l, fb = P.decompose(X, w16, seed=i)
-        ms_p = P.time_call(lambda: P.decompose(X, None, seed=i))
-        ms_l = P.time_call(lambda: P.decompose(X, w16, seed=i))
-        cases.append({"alpha": a, "sketch_columns": l, "fell_back": bool(fb),
-                      "plain_ms": ms_p, "learned_ms": ms_l, "speedup": ms_p / ms_l,
-                      "plain_error": P.truncation_error(spec, r_p, n3),
-                      "learned_error": P.truncation_error(spec, r_l, n3),
-                      "ranks_equal_fraction": float((r_p == r_l).float().mean().item())})
-        del X, spec
-    return {"workload": f"{n1}x{n2}x{n3} tensors, per-frequency spectra i^-a, a = alpha +- 0.3; "
-                        f"trained on {train_count} tensors of 128..160 x 96..128 x 16..32",
+    for n3 in eval_n3:
+        for i, a in enumerate(alphas if n3 == eval_n3[0] else alphas[::2]):
+            X, spec = synth.spectral_torch(n1, n2, n3, a, 0.3, 77000 + i + 100 * n3)
+            r_p, _, _ = P.decompose(X, None, seed=i)
+            r_l, l, fb = P.decompose(X, w16, seed=i)
+            ms_p = P.time_call(lambda: P.decompose(X, None, seed=i), reps=2)
+            ms_l = P.time_call(lambda: P.decompose(X, w16, seed=i), reps=2)
+            cases.append({"n3": n3, "alpha": a, "sketch_columns": l, "fell_back": bool(fb),
+                          "plain_ms": ms_p, "learned_ms": ms_l, "speedup": ms_p / ms_l,
+                          "plain_error": P.truncation_error(spec, r_p, n3),
+                          "learned_error": P.truncation_error(spec, r_l, n3),
+                          "ranks_equal_fraction": float((r_p == r_l).float().mean().item())})
+            del X, spec
+            torch.cuda.empty_cache()
+    return {"workload": f"{n1}x{n2}x{{{','.join(str(v) for v in eval_n3)}}} tensors, "
+                        "per-frequency spectra i^-a, a = alpha +- 0.3; trained on "
+                        f"{train_count} tensors of 64..160 x 64..128 x 16..256",
             "training_samples": int(x.shape[0]), "data_s": t_data, "train_s": t_train,
             "loss_first_last": [losses[0][1], losses[-1][1]],
             "total_plain_ms": sum(c["plain_ms"] for c in cases),
@@ -489,42 +501,70 @@ def bench_learned(torch, train_count=192, eval_shape=(1024, 1024, 64),
             "cases": cases}
 
 
-def bench_rsvd(args, tp, torch, with_cpu):
+def bench_rsvd(args, tp, torch, with_cpu, forms=("bf16x3", "fp32", "tf32x3")):
     """Randomized low-tubal-rank t-SVD on the mass-spectrometry-shaped
     workload (128 x 128 pixels x 2000 channels, Gamma factors at tubal rank
-    15, spikes, 0.5% noise; k = 40, p = 10, q = 2): tensors per second."""
+    15, spikes, 0.5% noise; k = 40, p = 10, q = 2): tensors per second of the
+    split tensor-core form (first of `forms`) and of the plain FP32 form.
+    With the CPU baseline the float64 oracle decomposes the same tensor once
+    (same test matrix) and every form's top-k singular values (all 1001
+    frequencies) are compared with it (relative Frobenius error)."""
     from paper_1704_04362_gb300 import synth
+    PREC = {"fp32": tp.TP_FP32, "tf32x3": tp.TP_TF32X3, "bf16x3": tp.TP_BF16X3}
     X = synth.msi_like_np()
     Xd = tp.as_tprod_layout(X)
-    for _ in range(2):
-        tp.tsvd_randomized(Xd, RSVD_K, RSVD_P, RSVD_Q, seed=0)
-    torch.cuda.synchronize()
     steps = max(3, min(20, args.steps // 5))
     stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    tp.profile_start()
-    e0.record(stream)
-    for _ in range(steps):
-        tp.tsvd_randomized(Xd, RSVD_K, RSVD_P, RSVD_Q, seed=0)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    prof = tp.profile_stop()
-    ms = e0.elapsed_time(e1) / steps
+    res = {}
+    outs = {}
+    prof_main = None
+    for name in forms:
+        pr = PREC[name]
+        for _ in range(2):
+            outs[name] = tp.tsvd_randomized(Xd, RSVD_K, RSVD_P, RSVD_Q, seed=0, precision=pr)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tp.profile_start()
+        e0.record(stream)
+        for _ in range(steps):
+            tp.tsvd_randomized(Xd, RSVD_K, RSVD_P, RSVD_Q, seed=0, precision=pr)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = tp.profile_stop()
+        if prof_main is None:
+            prof_main = prof
+        res[name] = e0.elapsed_time(e1) / steps
+    main = forms[0]
+    ms = res[main]
     out = {"metric": "randomized t-SVD tensors/s", "value": 1e3 / ms, "unit": "tensors/s",
-           "ms_per_tensor": ms, "steps": steps, "dtype": "f32 data, f64 CholeskyQR2 and core SVD",
+           "ms_per_tensor": ms, "steps": steps, "precision": main,
+           "dtype": "f32 data; products %s; f64-accurate CholeskyQR first pass" % main,
            "workload": "128x128x2000 MSI-shaped, tubal rank 15 + spikes + 0.5% noise, "
                        "k=40 p=10 q=2",
+           "forms_ms": res,
            "kernels": {k: {"ms_per_launch": v[0] / max(1, v[1]), "launches": v[1]}
-                       for k, v in prof.items()}}
+                       for k, v in prof_main.items()}}
+    cmp = {"fp32_tensors_per_s": 1e3 / res["fp32"]} if "fp32" in res else {}
     if with_cpu:
         from oracle import decomp_ref, philox_ref
         X64 = X.astype(np.float64)
         Om = philox_ref.sketch_signs(128, RSVD_K + RSVD_P, 1001, 2000, 0)
         t0 = time.perf_counter()
-        decomp_ref.tsvd_randomized(X64, RSVD_K, RSVD_P, RSVD_Q, Om)
+        _, Sr, _ = decomp_ref.tsvd_randomized(X64, RSVD_K, RSVD_P, RSVD_Q, Om)
         dt = time.perf_counter() - t0
         out["cpu_baseline"] = {"value": 1.0 / dt, "unit": "tensors/s", "cores": os.cpu_count(),
                                "kind": "oracle", "sample": f"one full tensor, {dt:.1f} s"}
+        # singular values of every half-spectrum slice (diagonal of S_hat)
+        sr = np.stack([np.diag(M).real for M in np.moveaxis(
+            np.fft.fft(Sr, axis=2)[:, :, :1001], 2, 0)])
+        den = np.linalg.norm(sr)
+        for name, (_, S, _) in outs.items():
+            Sh = torch.fft.fft(S.permute(2, 0, 1).double(), dim=0)[:1001]
+            s = torch.diagonal(Sh, dim1=1, dim2=2).real.cpu().numpy()
+            e = float(np.linalg.norm(s - sr) / den)
+            out.setdefault("rel_err_singular_values", {})[name] = e
+            cmp[("" if name == main else name + "_") + "rel_err"] = sig(e, 3)
+    out["compare"] = {k: sig(v) for k, v in cmp.items()}
     return out
 
 
@@ -747,6 +787,11 @@ def main():
                          "are written (the stdout headline stays under 2 KB)")
     ap.add_argument("--no-rsvd", action="store_true", help="skip the randomized t-SVD line")
     ap.add_argument("--no-rows", action="store_true", help="skip the t-SVD / t-CX / ADMM rows")
+    ap.add_argument("--svt-iters", type=int, default=100,
+                    help="iterations of the batched completion row (256 videos)")
+    ap.add_argument("--only", default=None,
+                    help="comma-separated rows to run instead of the headline step "
+                         "(rsvd, svt_batched): profiling and tuning runs, no headline line")
     ap.add_argument("--tune-file", default=None,
                     help="autotuner table: loaded before the run when the file exists, "
                          "written after it (so that a profiled run reuses the plain run's "
@@ -774,6 +819,18 @@ def main():
     peaks = load_peaks()
     if args.tune_file and os.path.exists(args.tune_file):
         tp.autotune_load(args.tune_file)
+
+    if args.only:
+        # single rows for profiling and tuning: printed one per line, no headline
+        for name in args.only.split(","):
+            if name == "rsvd":
+                out = bench_rsvd(args, tp, torch, with_cpu=False)
+            elif name == "svt_batched":
+                out = bench_svt_batched(tp, torch, iters=args.svt_iters)
+            else:
+                raise SystemExit(f"bench: unknown row {name!r}")
+            print(json.dumps({"row": name, **out}, default=str))
+        return
 
     A, B = make_inputs("cuda")
     Z = tp.empty_tensor(N1, N4, N3)
@@ -933,7 +990,7 @@ def main():
     rows = None
     if not args.no_rows and not args.small:
         rows = bench_rows(tp, torch, with_cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
-        rows["completion_batched"] = bench_svt_batched(tp, torch)
+        rows["completion_batched"] = bench_svt_batched(tp, torch, iters=args.svt_iters)
         rows["learned_rank"] = bench_learned(torch)
         rows["table1_shape"] = bench_table1(tp, torch)
 

@@ -177,8 +177,15 @@ int tsvd(const float* X, int64_t n1, int64_t n2, int64_t n3,
  * ||X(:,j,:)||_F^2 / ||X||_F^2, Philox stream 2), each rescaled by
  * 1/sqrt((k+p) p_j), so that Y holds picked columns of X_hat;
  * q power iterations Q <- orth(X_hat^H Q), Q <- orth(X_hat Q), each orth a
- * CholeskyQR2 with float64 Gram and Cholesky, then B = Q^H X_hat, a float64
- * SVD of B and U = Q U_B truncated to k.
+ * CholeskyQR2 (first pass: float64-accurate Gram and float64 Cholesky;
+ * second pass, on a Gram within u32 cond(Y) of the identity, in float32),
+ * then B = Q^H X_hat, the SVD of B through its l x l Gram (float32
+ * two-sided Jacobi, singular values as the Rayleigh quotients ||B^H w_j||
+ * with float64 sums) and U = Q U_B truncated to k.
+ *   opts->precision  TP_FP32: the products with X_hat on the CUDA cores;
+ *                  TP_TF32X3 / TP_BF16X3: those products on the tcgen05
+ *                  tensor cores with split (hi + lo) operands, float32
+ *                  accumulation drained every K chunk (float32-level error).
  *   rank_per_freq  device int32[n3/2 + 1] or NULL: per-frequency ranks (the
  *                  multi-rank of Section 2): half-spectrum slice f keeps its
  *                  top min(max(r_f, 0), k) triplets and zeroes the rest (its

@@ -384,10 +384,12 @@ def tsvd(X, max_sweeps=0, status=None):
 
 
 def tsvd_randomized(X, k, p=10, q=2, seed=0, status=None, max_sweeps=0, ranks=None,
-                    sketch=0):
+                    sketch=0, precision=TP_FP32):
     """Randomized tubal-rank-k t-SVD: returns (U, S, V).  ranks: optional
     device int32[n3 // 2 + 1] per-frequency ranks (each at most k); sketch:
-    TP_SKETCH_SIGNS (0) or TP_SKETCH_SLICES (1, picked lateral slices)."""
+    TP_SKETCH_SIGNS (0) or TP_SKETCH_SLICES (1, picked lateral slices);
+    precision: TP_FP32 (products on the CUDA cores) or TP_TF32X3 / TP_BF16X3
+    (the products with X_hat on the tensor cores, split operands)."""
     torch = _torch()
     n1, n2, n3 = X.shape
     rk = None
@@ -398,7 +400,7 @@ def tsvd_randomized(X, k, p=10, q=2, seed=0, status=None, max_sweeps=0, ranks=No
     U = empty_tensor(n1, k, n3, device=X.device)
     S = empty_tensor(k, k, n3, device=X.device)
     V = empty_tensor(n2, k, n3, device=X.device)
-    o = _opts(TP_OP_TSVD_RANDOMIZED, (n1, n2, n3, k, p), TP_FP32, status, max_sweeps)
+    o = _opts(TP_OP_TSVD_RANDOMIZED, (n1, n2, n3, k, p), precision, status, max_sweeps)
     rc = lib().tsvd_randomized(_tensor_arg(X, "X"), n1, n2, n3, int(k), int(p), int(q),
                                int(seed) & ((1 << 64) - 1), int(sketch), rk,
                                _tensor_arg(U, "U"),

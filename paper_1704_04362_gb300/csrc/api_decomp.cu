@@ -6,7 +6,7 @@
 namespace tp {
 size_t tsvd_ws(int64_t n1, int64_t n2, int64_t n3);
 bool fft_supported(int64_t n3);
-size_t rsvd_ws(int64_t n1, int64_t n2, int64_t n3, int64_t k, int64_t p);
+size_t rsvd_ws(int64_t n1, int64_t n2, int64_t n3, int64_t k, int64_t p, int prec = TP_FP32);
 size_t svt_ws(int64_t n1, int64_t n2, int64_t n3);
 size_t svt_batched_ws_dims(const int64_t* dims, int nd);
 size_t mlp_ws(int64_t B);
@@ -37,10 +37,11 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
 int tsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, float* U, float* S, float* V,
              const tp_opts* opts, cudaStream_t st);
 
-size_t workspace_for(int op, const int64_t* d, int nd) {
+size_t workspace_for(int op, const int64_t* d, int nd, const tp_opts* opts) {
   switch (op) {
     case TP_OP_TSVD: return nd >= 3 ? tsvd_ws(d[0], d[1], d[2]) : 0;
-    case TP_OP_TSVD_RANDOMIZED: return nd >= 5 ? rsvd_ws(d[0], d[1], d[2], d[3], d[4]) : 0;
+    case TP_OP_TSVD_RANDOMIZED:
+      return nd >= 5 ? rsvd_ws(d[0], d[1], d[2], d[3], d[4], opts ? opts->precision : TP_FP32) : 0;
     case TP_OP_TCOMPLETE_SVT:
     case TP_OP_TRPCA: return nd >= 3 ? svt_ws(d[0], d[1], d[2]) : 0;
     case TP_OP_TCOMPLETE_SVT_BATCHED: return nd >= 3 ? svt_batched_ws_dims(d, nd) : 0;

@@ -7,7 +7,7 @@ namespace tp {
 int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, int q,
              uint64_t seed, float* U, float* S, float* V, const tp_opts* opts, cudaStream_t st,
              float* sig_out, const int32_t* rank_per_freq, int sketch_mode);
-size_t rsvd_ws(int64_t n1, int64_t n2, int64_t n3, int64_t k, int64_t p);
+size_t rsvd_ws(int64_t n1, int64_t n2, int64_t n3, int64_t k, int64_t p, int prec = TP_FP32);
 bool fft_supported(int64_t n3);
 size_t mlp_partial_count(int64_t B);
 int launch_rank_rule(const float* sig, int64_t h, int l, int cap, double tol, int32_t* out,

@@ -10,6 +10,10 @@ int launch_cgemm_tc(const CGemm& g, cudaStream_t st);
 
 int launch_cgemm(const CGemm& g, cudaStream_t st) {
   if (g.precision == TP_FP32) return launch_cgemm_simt(g, st);
+  if (g.b_conj_trans) {
+    set_error("cgemm: a conjugate-transposed B is supported by the FP32 path only");
+    return TP_EINVAL;
+  }
   if (g.precision == TP_TF32X3 || g.precision == TP_BF16X3) return launch_cgemm_tc(g, st);
   set_error("unknown precision %d", g.precision);
   return TP_EINVAL;
@@ -84,7 +88,7 @@ size_t sampled_ws(int64_t n1, int64_t n2, int64_t n4, int64_t n3, int prec) {
 
 }  // namespace
 
-size_t workspace_for(int op, const int64_t* d, int nd);
+size_t workspace_for(int op, const int64_t* d, int nd, const tp_opts* opts);
 
 }  // namespace tp
 
@@ -278,7 +282,7 @@ size_t tp_workspace_query(int op, const int64_t* d, int nd, const tp_opts* opts)
         size_t a = norms_partial_count(d[0], d[1], d[2], 0), b = norms_partial_count(d[0], d[1], d[2], 1);
         return ws_bytes(a > b ? a : b, 8);
       }
-    default: return tp::workspace_for(op, d, nd);
+    default: return tp::workspace_for(op, d, nd, opts);
   }
 }
 

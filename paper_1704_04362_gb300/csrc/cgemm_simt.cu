@@ -51,8 +51,12 @@ __device__ __forceinline__ void cgemm_tile(const CGemm& g, int64_t f, int64_t K,
       const int64_t n = n0 + b_n + 16 * u;
       const int64_t kk = kt + b_k;
       const bool ok = (n < g.N) && (kk < K);
-      rb[0][u] = ok ? __ldg(br + kk + g.ldb * n) : 0.f;
-      if (!REAL) rb[1][u] = ok ? __ldg(bi + kk + g.ldb * n) : 0.f;
+      const int64_t off = g.b_conj_trans ? n + g.ldb * kk : kk + g.ldb * n;
+      rb[0][u] = ok ? __ldg(br + off) : 0.f;
+      if (!REAL) {
+        const float v = ok ? __ldg(bi + off) : 0.f;
+        rb[1][u] = g.b_conj_trans ? -v : v;
+      }
     }
   };
   auto store = [&]() {

@@ -182,14 +182,12 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                : "memory");
 }
 
-// 16 consecutive TMEM columns of this warp's 32 lanes (no wait).
-__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&v)[16]) {
+// 8 consecutive TMEM columns of this warp's 32 lanes (no wait).
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&v)[8]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15}, [%16];"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-        "=r"(v[14]), "=r"(v[15])
+        "=r"(v[7])
       : "r"(taddr));
 }
 
@@ -201,10 +199,11 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// 200 registers: 10 warps x 32 x 200 fit the register file; under
-// __launch_bounds__(NTHR, 1) the compiler picked 168 and spilled the epilogue.
+// Ten warps: two of the four SM sub-partitions hold three of them, and a
+// sub-partition's 16K registers then allow 170 per thread; the epilogue's
+// 128 float32 accumulators fit with 8-column TMEM loads.
 template <bool BF16>
-__global__ void __maxnreg__(200) cgemm_tc_kernel(const __grid_constant__ TcParams p) {
+__global__ void __launch_bounds__(NTHR, 1) cgemm_tc_kernel(const __grid_constant__ TcParams p) {
   constexpr int TBK = BF16 ? ROWB / 2 : ROWB / 4;   // K elements per K block
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -390,13 +389,13 @@ __global__ void __maxnreg__(200) cgemm_tc_kernel(const __grid_constant__ TcParam
           const uint32_t base = tmem + (uint32_t(q * 32) << 16) + uint32_t(b) * (2 * TN) +
                                 uint32_t(half * EPI_COLS);
 #pragma unroll
-          for (int c0 = 0; c0 < EPI_COLS; c0 += 16) {
-            uint32_t vr[16], vi[16];
-            tmem_ld16_nowait(base + uint32_t(c0), vr);
-            if (!real_slice) tmem_ld16_nowait(base + uint32_t(TN + c0), vi);
+          for (int c0 = 0; c0 < EPI_COLS; c0 += 8) {
+            uint32_t vr[8], vi[8];
+            tmem_ld8_nowait(base + uint32_t(c0), vr);
+            if (!real_slice) tmem_ld8_nowait(base + uint32_t(TN + c0), vi);
             tmem_ld_wait();
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
+            for (int j = 0; j < 8; ++j) {
               // chunk sums added in float32, round to nearest
               accr[c0 + j] = c == 0 ? __uint_as_float(vr[j]) : accr[c0 + j] + __uint_as_float(vr[j]);
               if (!real_slice)

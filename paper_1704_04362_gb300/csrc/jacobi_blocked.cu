@@ -187,19 +187,59 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_blocked_kernel(
           Si[e] = Vi[src];
         }
         __syncthreads();
-        // V_blk <- V_blk Q
-        for (int e = tid; e < nc * q; e += JB_THREADS) {
-          const int j = e / q, r = e - j * q;
-          float accr = 0.f, acci = 0.f;
-          for (int k = 0; k < nc; ++k) {
-            const float xr = Sr[k * q + r], xi = Si[k * q + r];
-            const float yr = Qr[j * JB_C + k], yi = Qi[j * JB_C + k];
-            accr += xr * yr - xi * yi;
-            acci += xr * yi + xi * yr;
+        // V_blk <- V_blk Q, register-tiled: a warp task is 128 rows (4 per
+        // lane, 32 apart, so the lanes read consecutive words) by 4 columns;
+        // per k a lane loads 4 entries of V_blk and 4 of Q (the same for the
+        // whole warp) for 16 complex multiply-adds
+        {
+          const int rgroups = (q + 127) / 128, cgroups = (nc + 3) / 4;
+          for (int task = warp; task < rgroups * cgroups; task += NW) {
+            const int r0 = (task % rgroups) * 128 + lane, c0 = (task / rgroups) * 4;
+            float ar[4][4], ai[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                ar[i][j] = 0.f;
+                ai[i][j] = 0.f;
+              }
+            for (int k = 0; k < nc; ++k) {
+              float xr[4], xi[4], yr[4], yi[4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                const int r = r0 + 32 * i;
+                xr[i] = r < q ? Sr[k * q + r] : 0.f;
+                xi[i] = r < q ? Si[k * q + r] : 0.f;
+              }
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const int c = c0 + j;
+                yr[j] = c < nc ? Qr[c * JB_C + k] : 0.f;
+                yi[j] = c < nc ? Qi[c * JB_C + k] : 0.f;
+              }
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  ar[i][j] = fmaf(xr[i], yr[j], fmaf(-xi[i], yi[j], ar[i][j]));
+                  ai[i][j] = fmaf(xr[i], yi[j], fmaf(xi[i], yr[j], ai[i][j]));
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int c = c0 + j;
+              if (c >= nc) continue;
+              const int64_t col = int64_t(jb_col(c, I, J, bI)) * q;
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                const int r = r0 + 32 * i;
+                if (r < q) {
+                  Vr[col + r] = ar[i][j];
+                  Vi[col + r] = ai[i][j];
+                }
+              }
+            }
           }
-          const int64_t dst = int64_t(jb_col(j, I, J, bI)) * q + r;
-          Vr[dst] = accr;
-          Vi[dst] = acci;
         }
         if (tid == 0) any_rot = 1;
       }

@@ -14,6 +14,7 @@
 // complex GEMM because X_hat^H is formed once.
 #include <cmath>
 
+#include "dft_common.cuh"
 #include "jacobi_rot.cuh"
 #include "philox.cuh"
 
@@ -53,6 +54,33 @@ __global__ void conj_transpose_kernel(const float* __restrict__ ir, const float*
       dr[j + n2 * i] = tr[threadIdx.x][dy];
       di[j + n2 * i] = -ti[threadIdx.x][dy];
     }
+  }
+}
+
+// Split operand planes (tensor-core products) of a batch of column-major
+// complex matrices: element (r, c) of matrix f (rows x cols, at
+// f*s_src + r + ld_src*c) goes to f*s_dst + r + ld_dst*c of the hi/lo
+// planes (3xTF32 float or BF16x3 bf16 pairs), the imaginary part negated
+// when conj; rows [rows, ld_dst) are zero (the K padding of the tiles).
+__global__ void split_planes_kernel(const float* __restrict__ sr, const float* __restrict__ si,
+                                    int64_t rows, int64_t cols, int64_t ld_src, int64_t s_src,
+                                    int64_t h, int64_t ld_dst, int64_t s_dst, int conj, int bf16,
+                                    float* __restrict__ re_hi, float* __restrict__ re_lo,
+                                    float* __restrict__ im_hi, float* __restrict__ im_lo) {
+  const int64_t per = ld_dst * cols, total = per * h;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t f = e / per, rem = e - f * per;
+    const int64_t c = rem / ld_dst, r = rem - c * ld_dst;
+    float vr = 0.f, vi = 0.f;
+    if (r < rows) {
+      vr = sr[f * s_src + r + ld_src * c];
+      vi = si[f * s_src + r + ld_src * c];
+      if (conj) vi = -vi;
+    }
+    const int64_t o = f * s_dst + r + ld_dst * c;
+    dftc::put_split(re_hi, re_lo, bf16 != 0, o, vr);
+    dftc::put_split(im_hi, im_lo, bf16 != 0, o, vi);
   }
 }
 
@@ -237,46 +265,85 @@ __device__ void gram_smem(const float2* __restrict__ Ys, int ps, int p, int l, d
   }
 }
 
-// Right-looking Cholesky G = R^H R on the upper triangle of G (float64
-// interleaved, l x l): for each j the pivot, row j of R, then the trailing
-// update G(i, k) -= conj(R(j, i)) R(j, k), i <= k, spread over the block.
+// Right-looking Cholesky G = R^H R on the upper triangle of G (interleaved
+// re/im, l x l, element type T: float64 for a general Gram, float32 for the
+// near-identity Gram of CholeskyQR2's second pass), one barrier per step:
+// step j reads the pivot d_j = G(j, j) and row j as the earlier steps left
+// them and updates the trailing triangle G(i, k) -= conj(G(j, i)) G(j, k) / d_j
+// (i.e. conj(R(j, i)) R(j, k) with R(j, .) = G(j, .) / sqrt(d_j)), which no
+// thread of the step reads; the rows are scaled into R after the last step.
 // Returns false on a non-positive pivot (block-uniform).
-__device__ bool cholesky_rl(double* G, int l, int* fail) {
-  __shared__ double inv_d;
+template <class T>
+__device__ bool cholesky_rl(T* G, int l, int* fail) {
   for (int j = 0; j < l; ++j) {
     __syncthreads();
-    if (threadIdx.x == 0) {
-      const double d = G[2 * (j * l + j)];
-      if (!(d > 0.0) || !isfinite(d)) *fail = 1;
-      const double r = (d > 0.0 && isfinite(d)) ? sqrt(d) : 1.0;
-      G[2 * (j * l + j)] = r;
-      G[2 * (j * l + j) + 1] = 0.0;
-      inv_d = 1.0 / r;
-    }
-    __syncthreads();
-    for (int k = j + 1 + threadIdx.x; k < l; k += blockDim.x) {
-      G[2 * (j * l + k)] *= inv_d;
-      G[2 * (j * l + k) + 1] *= inv_d;
-    }
-    __syncthreads();
+    const T d = G[2 * (j * l + j)];
+    const bool good = d > T(0) && isfinite(d);
+    if (!good && threadIdx.x == 0) *fail = 1;
+    const T inv_d = good ? T(1) / d : T(1);
     const int m = l - j - 1;   // trailing size
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
       const int i = j + 1 + e / m, k = j + 1 + e % m;
       if (i > k) continue;
-      const double ar = G[2 * (j * l + i)], ai = G[2 * (j * l + i) + 1];   // R(j, i)
-      const double br = G[2 * (j * l + k)], bi = G[2 * (j * l + k) + 1];   // R(j, k)
-      G[2 * (i * l + k)] -= ar * br + ai * bi;
-      G[2 * (i * l + k) + 1] -= ar * bi - ai * br;
+      const T ar = G[2 * (j * l + i)], ai = G[2 * (j * l + i) + 1];   // G(j, i)
+      const T br = G[2 * (j * l + k)], bi = G[2 * (j * l + k) + 1];   // G(j, k)
+      G[2 * (i * l + k)] -= (ar * br + ai * bi) * inv_d;
+      G[2 * (i * l + k) + 1] -= (ar * bi - ai * br) * inv_d;
     }
+  }
+  __syncthreads();
+  // R(j, j) = sqrt(d_j), R(j, k) = G(j, k) / sqrt(d_j)
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int j = e / l, k = e % l;
+    if (k < j) continue;
+    const T d = G[2 * (j * l + j)];
+    const T r = (d > T(0) && isfinite(d)) ? sqrt(d) : T(1);
+    if (k > j) {
+      G[2 * e] /= r;
+      G[2 * e + 1] /= r;
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < l; j += blockDim.x) {
+    const T d = G[2 * (j * l + j)];
+    G[2 * (j * l + j)] = (d > T(0) && isfinite(d)) ? sqrt(d) : T(1);
+    G[2 * (j * l + j) + 1] = T(0);
   }
   __syncthreads();
   return *fail == 0;
 }
 
-// CholeskyQR2 with Y held in shared memory: compensated float32 Gram,
-// float64 Cholesky and triangular inverse, float32 Y R^{-1}.  The second pass
-// restores orthogonality to float32 accuracy (the first pass's float32
-// product leaves an error ~ eps_32 cond(Y)).  Shifted retry as cholqr2_kernel.
+// Plain float32 Gram G(a, b) = sum_r conj(Y(r, a)) Y(r, b) (Hermitian fill),
+// G float32 interleaved; for the second CholeskyQR pass, whose Y already has
+// orthonormal columns to about u32 cond(Y_0).
+__device__ void gram_smem_f32(const float2* __restrict__ Ys, int ps, int p, int l, float* G) {
+  const int npairs = l * (l + 1) / 2;
+  for (int e = threadIdx.x; e < npairs; e += blockDim.x) {
+    int a = 0, rem = e;
+    while (rem >= l - a) { rem -= l - a; ++a; }
+    const int b = a + rem;
+    const float2* xa = Ys + a * ps;
+    const float2* xb = Ys + b * ps;
+    float gr = 0.f, gi = 0.f;
+    for (int r = 0; r < p; ++r) {
+      const float2 u = xa[r], v = xb[r];
+      gr = fmaf(u.x, v.x, fmaf(u.y, v.y, gr));
+      gi = fmaf(u.x, v.y, fmaf(-u.y, v.x, gi));
+    }
+    G[2 * (a * l + b)] = gr;
+    G[2 * (a * l + b) + 1] = gi;
+    G[2 * (b * l + a)] = gr;
+    G[2 * (b * l + a) + 1] = -gi;
+  }
+}
+
+// CholeskyQR2 with Y held in shared memory.  First pass: compensated float32
+// Gram (float64-accurate), float64 Cholesky, float32 Y R^{-1}; its float32
+// product leaves Y with orthonormal columns to about u32 cond(Y), so the
+// second pass factors a Gram within u32 cond(Y) of the identity and runs in
+// float32 (Gram and Cholesky), restoring orthogonality to float32 accuracy.
+// Shifted retry as cholqr2_kernel (the passes after a shifted one stay in
+// float64 but the last).
 __global__ void __launch_bounds__(QR_THREADS) cholqr2_smem_kernel(float* y_re, float* y_im,
                                                                   int64_t sY, int p, int l,
                                                                   int32_t* status) {
@@ -293,35 +360,50 @@ __global__ void __launch_bounds__(QR_THREADS) cholqr2_smem_kernel(float* y_re, f
   __syncthreads();
   int passes_left = 2;
   bool shifted = false;
+  bool prev_shifted = false;
   bool ok_all = true;
-  for (int it = 0; it < 4 && passes_left > 0; ++it) {
+  for (int it = 0; it < 5 && passes_left > 0; ++it) {
     if (threadIdx.x == 0) fail = 0;
-    gram_smem(Ys, ps, p, l, G);
-    __syncthreads();
-    if (shifted) {
-      if (threadIdx.x == 0) {
-        double tr = 0.0;
-        for (int j = 0; j < l; ++j) tr += G[2 * (j * l + j)];
-        const double sft = 11.0 * (double(p) * l + double(l) * (l + 1)) * 1.1102230246251565e-16 * tr;
-        for (int j = 0; j < l; ++j) G[2 * (j * l + j)] += sft;
-      }
+    const bool f32 = passes_left == 1 && !shifted && !prev_shifted && it > 0;
+    if (f32) {
+      float* Gs = reinterpret_cast<float*>(G);
+      gram_smem_f32(Ys, ps, p, l, Gs);
       __syncthreads();
-    }
-    const bool ok = cholesky_rl(G, l, &fail);
-    if (!ok) {
-      if (shifted) {
-        ok_all = false;
-        break;
+      if (!cholesky_rl<float>(Gs, l, &fail)) {
+        // not expected after a successful float64 pass; redo it in float64
+        prev_shifted = true;
+        continue;
       }
-      shifted = true;
-      passes_left = 3;
-      continue;
+      for (int e = threadIdx.x; e < l * l; e += blockDim.x)
+        Ri[e] = make_float2(Gs[2 * e], Gs[2 * e + 1]);
+    } else {
+      gram_smem(Ys, ps, p, l, G);
+      __syncthreads();
+      if (shifted) {
+        if (threadIdx.x == 0) {
+          double tr = 0.0;
+          for (int j = 0; j < l; ++j) tr += G[2 * (j * l + j)];
+          const double sft =
+              11.0 * (double(p) * l + double(l) * (l + 1)) * 1.1102230246251565e-16 * tr;
+          for (int j = 0; j < l; ++j) G[2 * (j * l + j)] += sft;
+        }
+        __syncthreads();
+      }
+      if (!cholesky_rl<double>(G, l, &fail)) {
+        if (shifted) {
+          ok_all = false;
+          break;
+        }
+        shifted = true;
+        passes_left = 3;
+        continue;
+      }
+      // R in float32 (its float64 Gram made the factor accurate; the product
+      // below needs only float32)
+      for (int e = threadIdx.x; e < l * l; e += blockDim.x)
+        Ri[e] = make_float2(float(G[2 * e]), float(G[2 * e + 1]));
     }
-    // R in float32 (its float64 Gram made the factor accurate; the product
-    // below needs only float32), then Y <- Y R^{-1} row by row by forward
-    // substitution x R = y, in place
-    for (int e = threadIdx.x; e < l * l; e += blockDim.x)
-      Ri[e] = make_float2(float(G[2 * e]), float(G[2 * e + 1]));
+    // Y <- Y R^{-1} row by row by forward substitution x R = y, in place
     __syncthreads();
     for (int r = threadIdx.x; r < p; r += blockDim.x) {
       for (int j = 0; j < l; ++j) {
@@ -337,6 +419,7 @@ __global__ void __launch_bounds__(QR_THREADS) cholqr2_smem_kernel(float* y_re, f
       }
     }
     __syncthreads();
+    prev_shifted = shifted;
     shifted = false;
     --passes_left;
   }
@@ -349,80 +432,109 @@ __global__ void __launch_bounds__(QR_THREADS) cholqr2_smem_kernel(float* y_re, f
   }
 }
 
-// Cyclic two-sided Jacobi sweeps on the Hermitian l x l matrix G (row-major),
-// accumulating the rotations into W (W <- W K).  Each step takes ll/2
-// disjoint round-robin pairs: their parameters from the current G, then all
-// row rotations, then all column rotations (of G and W).  Pair (a, b) with
-// g = G(a,b) = |g| e^{i phi}: zeta = (G(b,b) - G(a,a)) / (2|g|),
-// t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t;
-// K = [[c, s], [-s e^{-i phi}, c e^{-i phi}]] zeroes G(a,b) in K^H G K.
-// Row stride ls (odd) keeps the column accesses free of bank conflicts.
-// A pair is rotated only while |G(a,b)| exceeds both tol sqrt(|G(a,a) G(b,b)|)
-// and the rounding floor `floor_abs` (entries below the working precision's
-// noise level of ||G|| cannot be resolved further).  Returns the number of
-// sweeps that rotated something (stops after a quiet sweep or at max_sweeps).
-template <class T, class C2>
-__device__ int jacobi2(C2* G, C2* W, int l, int ls, T tol, T floor_abs, int max_sweeps, T* rot,
-                       int* pq, int* rotated) {
+// Two-sided Jacobi on the Hermitian l x l matrix G (row stride ls) with the
+// rotations accumulated into W (W <- W K), float32.  Each step takes the
+// ll/2 disjoint round-robin pairs: first every pair's rotation from the
+// current G, then one pass that updates every 2 x 2 block (rows of pair i,
+// columns of pair j) with both rotations at once (K_i^H G K_j restricted to
+// the block; disjoint blocks, so no ordering within the pass) and W's
+// columns.  A pair is rotated while |G(a,b)| > tol sqrt(G(a,a) G(b,b)) (a
+// relative test: G is graded -- its diagonal spans the squared singular
+// values -- and a floor on the scale of the largest entry of G would leave
+// the small ones unresolved) and while |G(a,b)| exceeds the rounding floor of
+// the pair itself, a few ulp of max(G(a,a), G(b,b)).  Returns the number of sweeps that
+// rotated (stops after a quiet sweep or at max_sweeps).
+__device__ int jacobi2_fused(float2* G, float2* W, int l, int ls, float tol, int max_sweeps,
+                             float4* rot, int2* pq, int* rotated) {
   const int ll = l + (l & 1), npairs = ll / 2;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     __syncthreads();
     if (threadIdx.x == 0) *rotated = 0;
-    __syncthreads();
     for (int step = 0; step < ll - 1; ++step) {
+      __syncthreads();
       for (int i = threadIdx.x; i < npairs; i += blockDim.x) {
         int a, b;
         if (i == 0) { a = ll - 1; b = step; }
         else { a = (step + i) % (ll - 1); b = (step - i + (ll - 1)) % (ll - 1); }
         if (a > b) { const int t = a; a = b; b = t; }
-        pq[2 * i] = a;
-        pq[2 * i + 1] = b;
-        T cs = 1, sn = 0, er = 1, ei = 0;
+        pq[i] = make_int2(a, b);
+        float cs = 1.f, sn = 0.f, er = 1.f, ei = 0.f;
         if (b < l) {
-          const T al = G[a * ls + a].x, be = G[b * ls + b].x;
-          const C2 ga = G[a * ls + b];
-          const T g2 = ga.x * ga.x + ga.y * ga.y;
-          if (g2 > tol * tol * fabs(al * be) && g2 > floor_abs * floor_abs && g2 > T(0)) {
+          const float al = G[a * ls + a].x, be = G[b * ls + b].x;
+          const float2 ga = G[a * ls + b];
+          const float g2 = ga.x * ga.x + ga.y * ga.y;
+          // float32 rounding leaves |G(a,b)| at a few ulp of the larger
+          // diagonal term: pairs below that cannot be resolved further
+          const float fl = 5e-7f * fmaxf(fabsf(al), fabsf(be));
+          if (g2 > tol * tol * fabsf(al * be) && g2 > fl * fl && g2 > 0.f) {
             jrot::rotation(al, be, ga.x, ga.y, g2, cs, sn, er, ei);   // er, ei: e^{-i phi}
             *rotated = 1;
           }
         }
-        rot[4 * i] = cs;
-        rot[4 * i + 1] = sn;
-        rot[4 * i + 2] = er;
-        rot[4 * i + 3] = ei;
+        rot[i] = make_float4(cs, sn, er, ei);
       }
       __syncthreads();
-      for (int e = threadIdx.x; e < npairs * l; e += blockDim.x) {
-        const int i = e / l, j = e - i * l;
-        const int a = pq[2 * i], b = pq[2 * i + 1];
-        if (b >= l || rot[4 * i + 1] == T(0)) continue;
-        const T c = rot[4 * i], s = rot[4 * i + 1], er = rot[4 * i + 2], ei = -rot[4 * i + 3];
-        const C2 x = G[a * ls + j], y = G[b * ls + j];
-        const T yr = y.x * er - y.y * ei, yi = y.x * ei + y.y * er;   // e^{i phi} y
-        G[a * ls + j].x = c * x.x - s * yr;
-        G[a * ls + j].y = c * x.y - s * yi;
-        G[b * ls + j].x = s * x.x + c * yr;
-        G[b * ls + j].y = s * x.y + c * yi;
+      // G blocks: new rows (a, b) = [c x_a - s e^{i phi} x_b, s x_a + c e^{i phi} x_b]
+      // of pair i, then new columns (a, b) = [c y_a - s e^{-i phi} y_b,
+      // s y_a + c e^{-i phi} y_b] of pair j; W: the column rotation only
+      const int nblk = npairs * npairs;
+      for (int e = threadIdx.x; e < nblk + npairs * l; e += blockDim.x) {
+        if (e < nblk) {
+          const int i = e / npairs, j = e - i * npairs;
+          const int2 ri = pq[i], rj = pq[j];
+          // with odd l one pair holds the padding index l: its real index
+          // takes the other pair's rotation only
+          const bool ip = ri.y < l, jp = rj.y < l;
+          const float4 Ri = rot[i], Rj = rot[j];
+          const bool rowrot = ip && Ri.y != 0.f, colrot = jp && Rj.y != 0.f;
+          if (!rowrot && !colrot) continue;
+          const float2 zero = make_float2(0.f, 0.f);
+          float2 x00 = G[ri.x * ls + rj.x];
+          float2 x01 = jp ? G[ri.x * ls + rj.y] : zero;
+          float2 x10 = ip ? G[ri.y * ls + rj.x] : zero;
+          float2 x11 = (ip && jp) ? G[ri.y * ls + rj.y] : zero;
+          if (rowrot) {   // rows, with e^{i phi_i} = (er, -ei)
+            const float c = Ri.x, s = Ri.y, er = Ri.z, ei = -Ri.w;
+            const float2 y0 = make_float2(x10.x * er - x10.y * ei, x10.x * ei + x10.y * er);
+            const float2 y1 = make_float2(x11.x * er - x11.y * ei, x11.x * ei + x11.y * er);
+            const float2 n00 = make_float2(c * x00.x - s * y0.x, c * x00.y - s * y0.y);
+            const float2 n01 = make_float2(c * x01.x - s * y1.x, c * x01.y - s * y1.y);
+            x10 = make_float2(s * x00.x + c * y0.x, s * x00.y + c * y0.y);
+            x11 = make_float2(s * x01.x + c * y1.x, s * x01.y + c * y1.y);
+            x00 = n00;
+            x01 = n01;
+          }
+          if (colrot) {   // columns, with e^{-i phi_j} = (er, ei)
+            const float c = Rj.x, s = Rj.y, er = Rj.z, ei = Rj.w;
+            const float2 y0 = make_float2(x01.x * er - x01.y * ei, x01.x * ei + x01.y * er);
+            const float2 y1 = make_float2(x11.x * er - x11.y * ei, x11.x * ei + x11.y * er);
+            const float2 n00 = make_float2(c * x00.x - s * y0.x, c * x00.y - s * y0.y);
+            const float2 n10 = make_float2(c * x10.x - s * y1.x, c * x10.y - s * y1.y);
+            x01 = make_float2(s * x00.x + c * y0.x, s * x00.y + c * y0.y);
+            x11 = make_float2(s * x10.x + c * y1.x, s * x10.y + c * y1.y);
+            x00 = n00;
+            x10 = n10;
+          }
+          G[ri.x * ls + rj.x] = x00;
+          if (jp) G[ri.x * ls + rj.y] = x01;
+          if (ip) G[ri.y * ls + rj.x] = x10;
+          if (ip && jp) G[ri.y * ls + rj.y] = x11;
+        } else {
+          const int w = e - nblk;
+          const int j = w / l, r = w - j * l;
+          const int2 rj = pq[j];
+          const float4 Rj = rot[j];
+          if (rj.y >= l || Rj.y == 0.f) continue;
+          const float c = Rj.x, s = Rj.y, er = Rj.z, ei = Rj.w;
+          const float2 x = W[r * ls + rj.x], y = W[r * ls + rj.y];
+          const float2 yy = make_float2(y.x * er - y.y * ei, y.x * ei + y.y * er);
+          W[r * ls + rj.x] = make_float2(c * x.x - s * yy.x, c * x.y - s * yy.y);
+          W[r * ls + rj.y] = make_float2(s * x.x + c * yy.x, s * x.y + c * yy.y);
+        }
       }
-      __syncthreads();
-      for (int e = threadIdx.x; e < 2 * npairs * l; e += blockDim.x) {
-        const int which = e / (npairs * l), rest = e - which * npairs * l;
-        const int i = rest / l, j = rest - i * l;
-        const int a = pq[2 * i], b = pq[2 * i + 1];
-        if (b >= l || rot[4 * i + 1] == T(0)) continue;
-        const T c = rot[4 * i], s = rot[4 * i + 1], er = rot[4 * i + 2], ei = rot[4 * i + 3];
-        C2* M = which ? W : G;
-        const C2 x = M[j * ls + a], y = M[j * ls + b];
-        const T yr = y.x * er - y.y * ei, yi = y.x * ei + y.y * er;   // e^{-i phi} y
-        M[j * ls + a].x = c * x.x - s * yr;
-        M[j * ls + a].y = c * x.y - s * yi;
-        M[j * ls + b].x = s * x.x + c * yr;
-        M[j * ls + b].y = s * x.y + c * yi;
-      }
-      __syncthreads();
     }
+    __syncthreads();
     const int any = *rotated;
     __syncthreads();
     if (!any) break;
@@ -430,14 +542,18 @@ __device__ int jacobi2(C2* G, C2* W, int l, int ls, T tol, T floor_abs, int max_
   return sweep;
 }
 
-// Core SVD through the l x l Gram of B^H (n2 x l, held in shared memory):
-// G = B B^H = W diag(s^2) W^H.  A float32 two-sided Jacobi converges first;
-// then, in float64, the Rayleigh-Ritz projection G' = W^H G W of the float64
-// Gram (nearly diagonal) and float64 Jacobi sweeps on G' (updating W in
-// float64) finish the eigendecomposition to float64 accuracy.  The top k
-// eigenpairs give W_k (left singular vectors of B), S = sqrt(eigenvalues)
-// and V_k = B^H W_k S^{-1}.
-constexpr int EIG_THREADS = 512;
+// Core SVD through the l x l Gram of B^H (n2 x l, read from global memory,
+// which the previous product left in L2): G = B B^H = W diag(s^2) W^H by the
+// fused float32 two-sided Jacobi above (from W = I).  The singular values are
+// then the Rayleigh quotients s_j = ||B^H w_j|| (float32 products, float64
+// sums of squares), whose error is second order in the error of w_j -- the
+// square roots of G's float32 eigenvalues would carry an error u ||G|| /
+// (2 s_j) that grows as 1/s_j.  B^H itself is a float32 product of float32
+// data, so its singular values are only defined to about u32 s_1 (absolute);
+// a float64 polish of W would not change the result beyond that, at 1/64 of
+// the float32 rate.  The top k give W_k (left singular vectors of B),
+// S = diag(s) and V_k = B^H W_k S^{-1}.
+constexpr int EIG_THREADS = 256;
 
 __global__ void __launch_bounds__(EIG_THREADS) core_eig_kernel(
     const float* __restrict__ bh_re, const float* __restrict__ bh_im, int p, int l, int k,
@@ -447,79 +563,67 @@ __global__ void __launch_bounds__(EIG_THREADS) core_eig_kernel(
   extern __shared__ double dyn[];
   const int ls = l | 1;                                     // odd row stride
   const int L2 = l * ls;
-  double2* G = reinterpret_cast<double2*>(dyn);             // l x l float64 Gram, then G'
-  double2* W = G + L2;                                      // l x l float64 eigenvectors
-  double2* T = W + L2;                                      // l x l scratch; float32 phase: Gf, Wf
-  float2* Gf = reinterpret_cast<float2*>(T);
-  float2* Wf = Gf + L2;
-  float2* Bs = reinterpret_cast<float2*>(T + L2);           // p x l, column stride p + 1
-  const int ps = p + 1;
-  double* rot = reinterpret_cast<double*>(Bs + ps * l);     // per pair: c, s, er, ei
-  int* pq = reinterpret_cast<int*>(rot + 4 * ((l + 1) / 2));
-  float* rotf = reinterpret_cast<float*>(rot);
+  double* sig2 = dyn;                                       // l: ||B^H w_j||^2
+  float2* Gf = reinterpret_cast<float2*>(dyn + ((l + 1) & ~1));   // l x l Gram
+  float2* Wf = Gf + L2;                                     // l x l eigenvectors
+  float4* rot = reinterpret_cast<float4*>(Wf + L2);        // per pair: c, s, er, ei
+  int2* pq = reinterpret_cast<int2*>(rot + (l + 1) / 2);
   __shared__ int rotated;
   __shared__ int order[128];
   const int64_t f = blockIdx.x;
   const float* br = bh_re + f * int64_t(p) * l;
   const float* bi = bh_im + f * int64_t(p) * l;
-  for (int e = threadIdx.x; e < p * l; e += blockDim.x)
-    Bs[(e / p) * ps + e % p] = make_float2(br[e], bi[e]);
-  __syncthreads();
-  gram_smem(Bs, ps, p, l, reinterpret_cast<double*>(T));   // dense l x l into T first
-  __syncthreads();
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) G[(e / l) * ls + e % l] = T[e];
-  __syncthreads();
+  for (int j = threadIdx.x; j < l; j += blockDim.x) sig2[j] = 0.0;
+  // G(a, b) = sum_r conj(B^H(r, a)) B^H(r, b), a <= b, Hermitian fill; W = I
+  const int npairs = l * (l + 1) / 2;
+  for (int e = threadIdx.x; e < npairs; e += blockDim.x) {
+    int a = 0, rem = e;
+    while (rem >= l - a) { rem -= l - a; ++a; }
+    const int b = a + rem;
+    const float* xar = br + int64_t(a) * p;
+    const float* xai = bi + int64_t(a) * p;
+    const float* xbr = br + int64_t(b) * p;
+    const float* xbi = bi + int64_t(b) * p;
+    float gr = 0.f, gi = 0.f;
+    for (int r = 0; r < p; ++r) {
+      const float ur = __ldg(xar + r), ui = __ldg(xai + r), vr = __ldg(xbr + r),
+                  vi = __ldg(xbi + r);
+      gr = fmaf(ur, vr, fmaf(ui, vi, gr));
+      gi = fmaf(ur, vi, fmaf(-ui, vr, gi));
+    }
+    Gf[a * ls + b] = make_float2(gr, gi);
+    Gf[b * ls + a] = make_float2(gr, -gi);
+  }
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
     const int i = e / l, j = e % l;
-    Gf[i * ls + j] = make_float2(float(G[i * ls + j].x), float(G[i * ls + j].y));
     Wf[i * ls + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
   }
-  __shared__ double gmax;
-  if (threadIdx.x == 0) {
-    double m = 0.0;
-    for (int j = 0; j < l; ++j) m = fmax(m, G[j * ls + j].x);
-    gmax = m;
-  }
+  const int s32 = jacobi2_fused(Gf, Wf, l, ls, 1e-6f, max_sweeps, rot, pq, &rotated);
+  if (s32 >= max_sweeps && threadIdx.x == 0 && status) atomicOr(status, TP_DEV_NOCONV);
   __syncthreads();
-  const int s32 = jacobi2<float, float2>(Gf, Wf, l, ls, 1e-6f, float(4e-7 * gmax), max_sweeps,
-                                         rotf, pq, &rotated);
-  // float64 Rayleigh-Ritz: W = Wf, T = G W, G' = W^H T
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
-    const int i = e / l, j = e % l;
-    W[i * ls + j] = make_double2(Wf[i * ls + j].x, Wf[i * ls + j].y);
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
-    const int i = e / l, j = e % l;
-    double tr = 0.0, ti = 0.0;
-    for (int m = 0; m < l; ++m) {
-      const double2 g = G[i * ls + m], w = W[m * ls + j];
-      tr += g.x * w.x - g.y * w.y;
-      ti += g.x * w.y + g.y * w.x;
+  // s_j^2 = ||B^H w_j||^2: one warp per column at a time, lanes over rows
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (int j = warp; j < l; j += nwarp) {
+    double acc = 0.0;
+    for (int r = lane; r < p; r += 32) {
+      float pr = 0.f, pim = 0.f;
+      for (int m = 0; m < l; ++m) {
+        const float bre = __ldg(br + r + int64_t(p) * m), bim = __ldg(bi + r + int64_t(p) * m);
+        const float2 w = Wf[m * ls + j];
+        pr = fmaf(bre, w.x, fmaf(-bim, w.y, pr));
+        pim = fmaf(bre, w.y, fmaf(bim, w.x, pim));
+      }
+      acc += double(pr) * pr + double(pim) * pim;
     }
-    T[i * ls + j] = make_double2(tr, ti);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) sig2[j] = acc;
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
-    const int i = e / l, j = e % l;
-    double gr = 0.0, gi = 0.0;
-    for (int m = 0; m < l; ++m) {
-      const double2 w = W[m * ls + i], t = T[m * ls + j];   // conj(W(m, i)) T(m, j)
-      gr += w.x * t.x + w.y * t.y;
-      gi += w.x * t.y - w.y * t.x;
-    }
-    G[i * ls + j] = make_double2(gr, gi);
-  }
-  const int s64 = jacobi2<double, double2>(G, W, l, ls, 1e-14, 2e-15 * gmax, max_sweeps, rot, pq,
-                                           &rotated);
-  if ((s32 >= max_sweeps || s64 >= max_sweeps) && threadIdx.x == 0 && status)
-    atomicOr(status, TP_DEV_NOCONV);
   __syncthreads();
   for (int j = threadIdx.x; j < l; j += blockDim.x) {
-    const double lj = G[j * ls + j].x;
+    const double lj = sig2[j];
     int rank = 0;
     for (int m = 0; m < l; ++m) {
-      const double lm = G[m * ls + m].x;
+      const double lm = sig2[m];
       rank += (lm > lj) || (lm == lj && m < j);
     }
     order[rank] = j;
@@ -527,28 +631,27 @@ __global__ void __launch_bounds__(EIG_THREADS) core_eig_kernel(
   __syncthreads();
   for (int e = threadIdx.x; e < l * k; e += blockDim.x) {
     const int i = e % l, c = e / l;
-    const double2 w = W[i * ls + order[c]];
-    wkr[f * l * k + e] = float(w.x);
-    wki[f * l * k + e] = float(w.y);
+    const float2 w = Wf[i * ls + order[c]];
+    wkr[f * l * k + e] = w.x;
+    wki[f * l * k + e] = w.y;
   }
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
     const int i = e % k, c = e / k;
-    const double lam = G[order[c] * ls + order[c]].x;
-    sr_out[f * k * k + e] = (i == c) ? float(sqrt(fmax(lam, 0.0))) : 0.f;
+    sr_out[f * k * k + e] = (i == c) ? float(sqrt(sig2[order[c]])) : 0.f;
     si_out[f * k * k + e] = 0.f;
   }
   // V_k = B^H W_k S^{-1}
   for (int64_t e = threadIdx.x; e < int64_t(p) * k; e += blockDim.x) {
     const int r = int(e % p), c = int(e / p);
     const int j = order[c];
-    const double sg = sqrt(fmax(G[j * ls + j].x, 0.0));
+    const double sg = sqrt(sig2[j]);
     float vr = 0.f, vi = 0.f;
     if (sg > 0.0) {
       for (int m = 0; m < l; ++m) {
-        const float2 b = Bs[m * ps + r];
-        const double2 w = W[m * ls + j];
-        vr = fmaf(b.x, float(w.x), fmaf(-b.y, float(w.y), vr));
-        vi = fmaf(b.x, float(w.y), fmaf(b.y, float(w.x), vi));
+        const float bre = __ldg(br + r + int64_t(p) * m), bim = __ldg(bi + r + int64_t(p) * m);
+        const float2 w = Wf[m * ls + j];
+        vr = fmaf(bre, w.x, fmaf(-bim, w.y, vr));
+        vi = fmaf(bre, w.y, fmaf(bim, w.x, vi));
       }
       const float inv = float(1.0 / sg);
       vr *= inv;
@@ -557,6 +660,14 @@ __global__ void __launch_bounds__(EIG_THREADS) core_eig_kernel(
     vkr[f * int64_t(p) * k + e] = vr;
     vki[f * int64_t(p) * k + e] = vi;
   }
+}
+
+size_t core_eig_smem(int p, int l) {
+  (void)p;
+  const int ls = l | 1;
+  const size_t L2 = size_t(l) * ls;
+  return size_t((l + 1) & ~1) * 8 + 2 * L2 * 8 + size_t((l + 1) / 2) * 16 +
+         size_t((l + 1) / 2) * 8;
 }
 
 // Sorts the l Jacobi singular triplets of every slice, keeps the top k and
@@ -642,10 +753,22 @@ unsigned grid_for(int64_t n) {
 
 }  // namespace
 
-size_t rsvd_ws(int64_t n1, int64_t n2, int64_t n3, int64_t k, int64_t p) {
+// K leading dimension of the split operand planes (16-byte rows for TMA).
+int64_t split_ld(int64_t k, int prec) {
+  return prec == TP_BF16X3 ? (k + 7) / 8 * 8 : (k + 3) / 4 * 4;
+}
+
+size_t rsvd_ws(int64_t n1, int64_t n2, int64_t n3, int64_t k, int64_t p, int prec) {
   const size_t h = size_t(half_len(n3));
   const size_t l = size_t(k + p);
-  return 2 * ws_bytes(size_t(n1) * n2 * h, 4)   // X_hat
+  const bool tc = prec == TP_TF32X3 || prec == TP_BF16X3;
+  const size_t ln = size_t(split_ld(n1, prec)), lm = size_t(split_ld(n2, prec));
+  const size_t lb = ln > lm ? ln : lm;
+  const size_t split = tc ? 4 * ws_bytes(lm * n1 * h, 4)      // X_hat, K-major (for X_hat .)
+                                + 4 * ws_bytes(ln * n2 * h, 4)  // X_hat^H, K-major
+                                + 4 * ws_bytes(lb * l * h, 4)   // B operand (Omega, Q or Z)
+                          : 0;
+  return split + 2 * ws_bytes(size_t(n1) * n2 * h, 4)   // X_hat
          + 2 * ws_bytes(size_t(n1) * n2 * h, 4) // X_hat^H
          + 2 * ws_bytes(size_t(n2) * l * h, 4)  // Omega
          + 2 * ws_bytes(size_t(n1) * l * h, 4)  // Y / Q
@@ -699,10 +822,27 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
              float* sig_out, const int32_t* rank_per_freq, int sketch_mode) {
   const int64_t h = half_len(n3);
   const int64_t l = k + p;
+  const int prec = opts ? opts->precision : TP_FP32;
+  if (prec != TP_FP32 && prec != TP_TF32X3 && prec != TP_BF16X3) {
+    set_error("tsvd_randomized: unknown precision %d", prec);
+    return TP_EINVAL;
+  }
+  const bool tc = prec != TP_FP32;
   Arena ws;
-  int rc = acquire_workspace(opts, rsvd_ws(n1, n2, n3, k, p), &ws);
+  int rc = acquire_workspace(opts, rsvd_ws(n1, n2, n3, k, p, prec), &ws);
   if (rc) return rc;
   int32_t* status = opts ? opts->status : nullptr;
+  // tensor-core form: split planes of X_hat (K-major for X_hat Omega and
+  // X_hat Z), of X_hat^H (K-major for X_hat^H Q) and of the B operand
+  const int64_t ln = split_ld(n1, prec), lm = split_ld(n2, prec), lb = ln > lm ? ln : lm;
+  float* XA[4] = {};
+  float* XH[4] = {};
+  float* BP[4] = {};
+  if (tc) {
+    for (int i = 0; i < 4; ++i) XA[i] = ws.take<float>(size_t(lm) * n1 * h);
+    for (int i = 0; i < 4; ++i) XH[i] = ws.take<float>(size_t(ln) * n2 * h);
+    for (int i = 0; i < 4; ++i) BP[i] = ws.take<float>(size_t(lb) * l * h);
+  }
   float* Xr = ws.take<float>(size_t(n1) * n2 * h);
   float* Xi = ws.take<float>(size_t(n1) * n2 * h);
   float* Hr = ws.take<float>(size_t(n1) * n2 * h);
@@ -767,6 +907,40 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
             TP_FP32, nullptr, nullptr, nullptr, nullptr, K, status};
     return launch_cgemm(g, st);
   };
+  const int bf = prec == TP_BF16X3 ? 1 : 0;
+  // split planes of the column-major rows x cols matrices (src, ld rows) with
+  // K leading dimension ldk
+  auto split = [&](const float* sr, const float* si, int64_t rows, int64_t cols, int conj,
+                   int64_t ldk, float* const* P) {
+    {
+      KernelScope ks("rsvd_split", st);
+      split_planes_kernel<<<grid_for(ldk * cols * h), 256, 0, st>>>(
+          sr, si, rows, cols, rows, rows * cols, h, ldk, ldk * cols, conj, bf, P[0], P[1], P[2],
+          P[3]);
+    }
+    return launch_status("split_planes_kernel");
+  };
+  // C (M x N, column-major) = A B with A the split planes XA (M = n1, K = n2)
+  // or XH (M = n2, K = n1) and B the split planes BP (K x N, column-major)
+  auto gemm_tc = [&](bool hermitian, int64_t N, float* cr, float* ci) {
+    const int64_t M = hermitian ? n2 : n1, K = hermitian ? n1 : n2;
+    const int64_t lk = hermitian ? ln : lm;
+    float* const* A = hermitian ? XH : XA;
+    CGemm g{A[0], A[2], BP[0], BP[2], cr, ci, M, N, K, nullptr, lk, lk, M, lk * M, lk * N, M * N,
+            h, n3, prec, A[1], A[3], BP[1], BP[3], lk, status};
+    return launch_cgemm(g, st);
+  };
+  // Y = X_hat B (hermitian = false) or X_hat^H B on the selected path, with B
+  // given as float32 (br, bi: K x N column-major)
+  auto product = [&](bool hermitian, const float* br, const float* bi, int64_t N, float* cr,
+                     float* ci) {
+    const int64_t K = hermitian ? n1 : n2;
+    if (!tc) return hermitian ? gemm(Hr, Hi, n2, n1, br, bi, N, cr, ci)
+                              : gemm(Xr, Xi, n1, n2, br, bi, N, cr, ci);
+    int r2 = split(br, bi, K, N, 0, hermitian ? ln : lm, BP);
+    if (r2) return r2;
+    return gemm_tc(hermitian, N, cr, ci);
+  };
   const size_t qr_smem = size_t(2) * l * l * sizeof(double);
   TP_SET_SMEM(cholqr2_kernel, qr_smem);
   constexpr size_t kSmemCap = 200 * 1024;
@@ -785,17 +959,23 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
     return launch_status("cholqr2_kernel");
   };
 
-  if ((rc = gemm(Xr, Xi, n1, n2, Or, Oi, l, Yr, Yi))) return rc;     // Y = X_hat Omega
+  if (tc) {
+    // X_hat (element (i, j) at j + lm i: the transpose of X_hat^H without
+    // its conjugation) and conj(X_hat) (element (j, i) of X_hat^H at i + ln j)
+    if ((rc = split(Hr, Hi, n2, n1, 1, lm, XA))) return rc;
+    if ((rc = split(Xr, Xi, n1, n2, 1, ln, XH))) return rc;
+  }
+  if ((rc = product(false, Or, Oi, l, Yr, Yi))) return rc;     // Y = X_hat Omega
   if ((rc = orth(Yr, Yi, n1))) return rc;
   for (int it = 0; it < q; ++it) {
-    if ((rc = gemm(Hr, Hi, n2, n1, Yr, Yi, l, Zr, Zi))) return rc;   // Z = X_hat^H Q
+    if ((rc = product(true, Yr, Yi, l, Zr, Zi))) return rc;    // Z = X_hat^H Q
     if ((rc = orth(Zr, Zi, n2))) return rc;
-    if ((rc = gemm(Xr, Xi, n1, n2, Zr, Zi, l, Yr, Yi))) return rc;   // Y = X_hat Z
+    if ((rc = product(false, Zr, Zi, l, Yr, Yi))) return rc;   // Y = X_hat Z
     if ((rc = orth(Yr, Yi, n1))) return rc;
   }
-  if ((rc = gemm(Hr, Hi, n2, n1, Yr, Yi, l, Zr, Zi))) return rc;     // B^H = X_hat^H Q
+  if ((rc = product(true, Yr, Yi, l, Zr, Zi))) return rc;      // B^H = X_hat^H Q
   const int sweeps = (opts && opts->max_sweeps > 0) ? opts->max_sweeps : 30;
-  const size_t eig_smem = size_t(l) * (l | 1) * 48 + size_t(n2 + 1) * l * 8 + size_t((l + 1) / 2) * 40;
+  const size_t eig_smem = core_eig_smem(int(n2), int(l));
   if (eig_smem <= kSmemCap && l <= 128) {
     TP_SET_SMEM(core_eig_kernel, eig_smem);
     {

@@ -90,7 +90,8 @@ std::vector<ProfTotal> g_prof_tot;
 constexpr size_t kMaxProfRecs = 1 << 16;
 }  // namespace
 
-KernelScope::KernelScope(const char* n, cudaStream_t s) : name(n), st(s), slot(-1) {
+KernelScope::KernelScope(const char* n, cudaStream_t s, bool c)
+    : name(n), st(s), slot(-1), count(c) {
   if (!g_prof_on) return;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
@@ -110,7 +111,7 @@ KernelScope::KernelScope(const char* n, cudaStream_t s) : name(n), st(s), slot(-
 }
 
 KernelScope::~KernelScope() {
-  note_launches(1);
+  if (count) note_launches(1);
   if (slot < 0) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (slot < int(g_prof_recs.size())) cudaEventRecord(g_prof_recs[slot].b, st);

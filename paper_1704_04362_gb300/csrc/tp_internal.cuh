@@ -19,12 +19,15 @@ int sm_count();                           // SMs of the current device (cached p
 
 // Brackets one kernel launch: counts it and, while tp_profile_start() is in
 // effect, records a CUDA event pair around it on the launch stream.
+// count = false: a timed region that is not one kernel (e.g. a graph
+// replay), profiled under its name but not counted as a launch.
 struct KernelScope {
-  KernelScope(const char* name, cudaStream_t st);
+  KernelScope(const char* name, cudaStream_t st, bool count = true);
   ~KernelScope();
   const char* name;
   cudaStream_t st;
   int slot;
+  bool count;
 };
 // Raises a kernel's dynamic shared memory limit to `bytes`; a failure is
 // reported (TP_ECUDA with the kernel's name and the size) instead of
@@ -108,6 +111,9 @@ struct CGemm {
   // tensor-core path: bound of the MMA warp's wait for a loaded stage, in
   // clock64 ticks (0 = the default of about two seconds)
   long long wait_limit = 0;
+  // FP32 path only: B_k(kk, n) = conj(b[k*sB + n + ldb*kk]) (B given as its
+  // conjugate transpose)
+  int b_conj_trans = 0;
 };
 int launch_cgemm(const CGemm& g, cudaStream_t st);
 

@@ -63,10 +63,16 @@ def targets(X, seed=0):
     return r_star, need - r_star
 
 
-def training_set(count, seed0, sizes=((128, 128, 16), (128, 96, 32), (160, 128, 16))):
+TRAIN_SIZES = ((128, 128, 16), (128, 96, 32), (160, 128, 16), (96, 96, 64), (80, 64, 128),
+               (64, 64, 256))
+
+
+def training_set(count, seed0, sizes=TRAIN_SIZES):
     """Features (N x 16 float16) and scaled targets (N x 2 float32) from
     `count` tensors of the spectral family with decay exponents drawn in
-    [1.5, 4] (per tensor) and jittered +-0.3 per frequency."""
+    [1.5, 4] (per tensor) and jittered +-0.3 per frequency; the sizes cycle
+    through tube lengths n3 = 16 .. 256 (the network sees one frequency at a
+    time, so n3 sets how many samples a tensor gives)."""
     import torch
     g = np.random.default_rng(seed0)
     feats, tgts = [], []

@@ -31,11 +31,14 @@ def approx(U, S, V):
     return tensor_ref.tprod(tensor_ref.tprod(U, S), tensor_ref.ttranspose(V))
 
 
-def run_both(X, k, p, q, seed):
+PRECISIONS = [tp.TP_FP32, tp.TP_TF32X3, tp.TP_BF16X3]
+
+
+def run_both(X, k, p, q, seed, precision=tp.TP_FP32):
     import torch
     n1, n2, n3 = X.shape
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
-    U, S, V = tp.tsvd_randomized(dev(X), k, p, q, seed=seed, status=st)
+    U, S, V = tp.tsvd_randomized(dev(X), k, p, q, seed=seed, status=st, precision=precision)
     assert int(st.item()) == 0
     h = n3 // 2 + 1
     Om = philox_ref.sketch_signs(n2, k + p, h, n3, seed)
@@ -43,21 +46,23 @@ def run_both(X, k, p, q, seed):
     return (to_np(U), to_np(S), to_np(V)), ref
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("n1,n2,n3,r,k,p,q", [(40, 30, 6, 3, 4, 3, 1), (30, 40, 7, 2, 3, 2, 0),
                                               (64, 48, 16, 5, 6, 4, 2), (20, 20, 1, 4, 5, 5, 1)])
-def test_exact_low_rank_is_recovered(n1, n2, n3, r, k, p, q):
+def test_exact_low_rank_is_recovered(n1, n2, n3, r, k, p, q, precision):
     X = synth.lowrank_np(n1, n2, n3, r, seed=7)
-    (U, S, V), (Ur, Sr, Vr) = run_both(X, k, p, q, seed=3)
+    (U, S, V), (Ur, Sr, Vr) = run_both(X, k, p, q, seed=3, precision=precision)
     assert rel_fro(approx(U, S, V), X.astype(np.float64)) < TOL_FP32
     s, sr = sing_vals(S), sing_vals(Sr)
     assert rel_fro(s[:r], sr[:r]) < TOL_FP32
     assert np.all(s[r:] < 1e-4 * s[0])
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("n3", [16, 2000])
-def test_gap_case_matches_oracle(n3):
+def test_gap_case_matches_oracle(n3, precision):
     X = synth.lowrank_np(48, 36, n3, 5, seed=11, noise=1e-4)
-    (U, S, V), (Ur, Sr, Vr) = run_both(X, 5, 5, 2, seed=1)
+    (U, S, V), (Ur, Sr, Vr) = run_both(X, 5, 5, 2, seed=1, precision=precision)
     assert rel_fro(sing_vals(S), sing_vals(Sr)) < TOL_FP32
     assert rel_fro(approx(U, S, V), approx(Ur, Sr, Vr)) < TOL_FP32
     I = tensor_ref.identity(5, n3)
@@ -65,20 +70,37 @@ def test_gap_case_matches_oracle(n3):
     assert np.linalg.norm(tensor_ref.tprod(tensor_ref.ttranspose(V), V) - I) < 1e-4
 
 
-def test_msi_workload_full_size():
-    """128 x 128 pixels x 2000 channels, Gamma(2,1) factors at tubal rank 15,
-    sparse positive spikes and 0.5% noise; k = 40, oversampling 10, 2 power
-    iterations."""
+@pytest.fixture(scope="module")
+def msi_oracle():
     X = synth.msi_like_np()
     k, p, q = 40, 10, 2
-    (U, S, V), (Ur, Sr, Vr) = run_both(X, k, p, q, seed=0)
+    Om = philox_ref.sketch_signs(128, k + p, 1001, 2000, 0)
+    return X, decomp_ref.tsvd_randomized(X.astype(np.float64), k, p, q, Om)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_msi_workload_full_size(msi_oracle, precision):
+    """128 x 128 pixels x 2000 channels, Gamma(2,1) factors at tubal rank 15,
+    sparse positive spikes and 0.5% noise; k = 40, oversampling 10, 2 power
+    iterations; the plain FP32 form and both split tensor-core forms."""
+    import torch
+    X, (Ur, Sr, Vr) = msi_oracle
+    k, p, q = 40, 10, 2
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    U, S, V = tp.tsvd_randomized(dev(X), k, p, q, seed=0, status=st, precision=precision)
+    assert int(st.item()) == 0
+    U, S, V = to_np(U), to_np(S), to_np(V)
     s, sr = sing_vals(S), sing_vals(Sr)
-    # the rank-15 signal part of every slice
-    assert rel_fro(s[:15], sr[:15]) < 1e-4
+    # the rank-15 signal part of every slice, and the whole top-k spectrum
+    e15 = rel_fro(s[:15], sr[:15])
+    ek = rel_fro(s, sr)
     X64 = X.astype(np.float64)
     err = np.linalg.norm(X64 - approx(U, S, V))
     err_ref = np.linalg.norm(X64 - approx(Ur, Sr, Vr))
-    assert abs(err / err_ref - 1) < 1e-3
+    print(f"precision {precision}: signal singular values {e15:.2e}, top-{k} {ek:.2e}, "
+          f"approximation error ratio {err / err_ref - 1:.2e}")
+    assert e15 < TOL_FP32 and ek < TOL_FP32
+    assert abs(err / err_ref - 1) < 1e-4
     # factors orthonormal slice by slice
     Uh = tensor_ref.half_spectrum(tensor_ref.fft3(U))
     for f in (0, 1, 500, 1000):
