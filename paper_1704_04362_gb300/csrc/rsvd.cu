@@ -237,11 +237,50 @@ __device__ __forceinline__ void acc2(float& hi, float& lo, float a, float b) {
   lo += err + e;
 }
 
-// G(a, b) = sum_r conj(Y(r, a)) Y(r, b) for a <= b (Hermitian fill), Y in
-// shared memory as float2 column-major p x l with column stride ps (p + 1:
-// the odd stride spreads the threads' different columns over the banks);
-// G float64 interleaved.
-__device__ void gram_smem(const float2* __restrict__ Ys, int ps, int p, int l, double* G) {
+// ---------------------------------------------------------------- float pairs
+// Unevaluated sums hi + lo of two floats (about 44 significant bits) on the
+// float32 pipe: GB300 runs float64 at 1/64 of the float32 rate, and the
+// first CholeskyQR pass needs a float64-class Gram and Cholesky.  Sums by
+// Knuth's two-sum, products by the FMA residual (Dekker's product).
+struct dfloat {
+  float hi, lo;
+};
+__device__ __forceinline__ dfloat df_quick(float a, float b) {   // |a| >= |b|
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ dfloat df_add(dfloat x, dfloat y) {
+  const float s = x.hi + y.hi;
+  const float bb = s - x.hi;
+  const float e = (x.hi - (s - bb)) + (y.hi - bb) + x.lo + y.lo;
+  return df_quick(s, e);
+}
+__device__ __forceinline__ dfloat df_mul(dfloat x, dfloat y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  return df_quick(p, e);
+}
+__device__ __forceinline__ dfloat df_neg(dfloat x) { return {-x.hi, -x.lo}; }
+// sqrt(d) and 1/r by one Newton correction of the float32 estimate
+__device__ __forceinline__ dfloat df_sqrt(dfloat d) {
+  const float s = sqrtf(d.hi);
+  const float e = fmaf(-s, s, d.hi) + d.lo;
+  return df_quick(s, e / (2.f * s));
+}
+__device__ __forceinline__ dfloat df_recip(dfloat r) {
+  const float q = 1.f / r.hi;
+  const float e = fmaf(-r.hi, q, 1.f) - r.lo * q;
+  return df_quick(q, e * q);
+}
+
+// G(a, b) = sum_r conj(Y(r, a)) Y(r, b) for a <= b (Hermitian fill) by the
+// compensated products and sums of acc2, as float pairs: G[a l + b] = (re hi,
+// re lo, im hi, im lo).  Y is in shared memory as float2 column-major p x l
+// with column stride ps (p + 1: the odd stride spreads the threads'
+// different columns over the banks).
+__device__ void gram_smem_df(const float2* __restrict__ Ys, int ps, int p, int l, float4* G) {
   const int npairs = l * (l + 1) / 2;
   for (int e = threadIdx.x; e < npairs; e += blockDim.x) {
     int a = 0, rem = e;
@@ -257,12 +296,48 @@ __device__ void gram_smem(const float2* __restrict__ Ys, int ps, int p, int l, d
       acc2(ih, il, u.x, v.y);
       acc2(ih, il, -u.y, v.x);
     }
-    const double sr = double(rh) + double(rl), si = double(ih) + double(il);
-    G[2 * (a * l + b)] = sr;
-    G[2 * (a * l + b) + 1] = si;
-    G[2 * (b * l + a)] = sr;
-    G[2 * (b * l + a) + 1] = -si;
+    const dfloat gr = df_quick(rh, rl), gi = df_quick(ih, il);
+    G[a * l + b] = make_float4(gr.hi, gr.lo, gi.hi, gi.lo);
+    G[b * l + a] = make_float4(gr.hi, gr.lo, -gi.hi, -gi.lo);
   }
+}
+
+// Right-looking Cholesky G = R^H R on the upper triangle of G in float pairs
+// (float4 per complex entry as gram_smem_df writes it).  Step j: every
+// thread forms r = sqrt(d_j) and 1/r from the pivot (float32 operations
+// only), scales its share of row j into R(j, .), and after a barrier the
+// trailing triangle takes G(i, k) -= conj(R(j, i)) R(j, k).  Returns false on
+// a non-positive pivot (block-uniform).
+__device__ bool cholesky_df(float4* G, int l, int* fail) {
+  for (int j = 0; j < l; ++j) {
+    __syncthreads();
+    const float4 dj = G[j * l + j];
+    const bool good = dj.x > 0.f && isfinite(dj.x);
+    if (!good && threadIdx.x == 0) *fail = 1;
+    const dfloat r = good ? df_sqrt({dj.x, dj.y}) : dfloat{1.f, 0.f};
+    const dfloat inv = df_recip(r);
+    for (int k = j + 1 + threadIdx.x; k < l; k += blockDim.x) {
+      const float4 g = G[j * l + k];
+      const dfloat a = df_mul({g.x, g.y}, inv), b = df_mul({g.z, g.w}, inv);
+      G[j * l + k] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) G[j * l + j] = make_float4(r.hi, r.lo, 0.f, 0.f);
+    const int m = l - j - 1;   // trailing size
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = j + 1 + e / m, k = j + 1 + e % m;
+      if (i > k) continue;
+      const float4 A = G[j * l + i], B = G[j * l + k];   // R(j, i), R(j, k)
+      const dfloat ar = {A.x, A.y}, ai = {A.z, A.w}, br = {B.x, B.y}, bi = {B.z, B.w};
+      const dfloat pr = df_add(df_mul(ar, br), df_mul(ai, bi));
+      const dfloat pi = df_add(df_mul(ar, bi), df_neg(df_mul(ai, br)));
+      const float4 g = G[i * l + k];
+      const dfloat nr = df_add({g.x, g.y}, df_neg(pr)), ni = df_add({g.z, g.w}, df_neg(pi));
+      G[i * l + k] = make_float4(nr.hi, nr.lo, ni.hi, ni.lo);
+    }
+  }
+  __syncthreads();
+  return *fail == 0;
 }
 
 // Right-looking Cholesky G = R^H R on the upper triangle of G (interleaved
@@ -338,7 +413,8 @@ __device__ void gram_smem_f32(const float2* __restrict__ Ys, int ps, int p, int 
 }
 
 // CholeskyQR2 with Y held in shared memory.  First pass: compensated float32
-// Gram (float64-accurate), float64 Cholesky, float32 Y R^{-1}; its float32
+// Gram and Cholesky in float pairs (float64-class accuracy on the float32
+// pipe), float32 Y R^{-1}; its float32
 // product leaves Y with orthonormal columns to about u32 cond(Y), so the
 // second pass factors a Gram within u32 cond(Y) of the identity and runs in
 // float32 (Gram and Cholesky), restoring orthogonality to float32 accuracy.
@@ -377,19 +453,25 @@ __global__ void __launch_bounds__(QR_THREADS) cholqr2_smem_kernel(float* y_re, f
       for (int e = threadIdx.x; e < l * l; e += blockDim.x)
         Ri[e] = make_float2(Gs[2 * e], Gs[2 * e + 1]);
     } else {
-      gram_smem(Ys, ps, p, l, G);
+      float4* Gd = reinterpret_cast<float4*>(G);
+      gram_smem_df(Ys, ps, p, l, Gd);
       __syncthreads();
       if (shifted) {
         if (threadIdx.x == 0) {
           double tr = 0.0;
-          for (int j = 0; j < l; ++j) tr += G[2 * (j * l + j)];
+          for (int j = 0; j < l; ++j) tr += double(Gd[j * l + j].x) + double(Gd[j * l + j].y);
           const double sft =
               11.0 * (double(p) * l + double(l) * (l + 1)) * 1.1102230246251565e-16 * tr;
-          for (int j = 0; j < l; ++j) G[2 * (j * l + j)] += sft;
+          const float sh = float(sft), sl = float(sft - double(sh));
+          for (int j = 0; j < l; ++j) {
+            const float4 g = Gd[j * l + j];
+            const dfloat d = df_add({g.x, g.y}, {sh, sl});
+            Gd[j * l + j] = make_float4(d.hi, d.lo, g.z, g.w);
+          }
         }
         __syncthreads();
       }
-      if (!cholesky_rl<double>(G, l, &fail)) {
+      if (!cholesky_df(Gd, l, &fail)) {
         if (shifted) {
           ok_all = false;
           break;
@@ -398,10 +480,12 @@ __global__ void __launch_bounds__(QR_THREADS) cholqr2_smem_kernel(float* y_re, f
         passes_left = 3;
         continue;
       }
-      // R in float32 (its float64 Gram made the factor accurate; the product
-      // below needs only float32)
-      for (int e = threadIdx.x; e < l * l; e += blockDim.x)
-        Ri[e] = make_float2(float(G[2 * e]), float(G[2 * e + 1]));
+      // R in float32 (its float64-class Gram and factorisation made the
+      // factor accurate; the product below needs only float32)
+      for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+        const float4 g = Gd[e];
+        Ri[e] = make_float2(g.x + g.y, g.z + g.w);
+      }
     }
     // Y <- Y R^{-1} row by row by forward substitution x R = y, in place
     __syncthreads();
