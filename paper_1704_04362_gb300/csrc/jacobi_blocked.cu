@@ -4,14 +4,15 @@
 //
 // The columns of the p x q work matrix G are cut into blocks of B = 16.  For
 // every pair of blocks (I, J) the CTA copies the (at most 32) columns of both
-// blocks into shared memory, runs one cyclic sweep of column-pair rotations
-// among them there (round-robin order, one pair per warp per round; the same
-// rotation formula as svd.cu), accumulates those rotations in a small
-// 32 x 32 matrix Q, writes the columns back and applies Q to the matching 32
-// columns of V (V_blk <- V_blk Q, staged through the same shared memory).
-// Visiting every block pair is one sweep of a cyclic Jacobi ordering (pairs
-// inside a block are revisited with every partner block); sweeps repeat until
-// one makes no rotation (or the sweep cap, TP_DEV_NOCONV).  Each column pair
+// blocks into shared memory, rotates there the 16 x 16 pairs across the two
+// blocks (and, once per sweep, each block's internal pairs) in rounds of
+// disjoint pairs, one pair per warp per round (the same rotation formula as
+// svd.cu), accumulates those rotations in a small 32 x 32 matrix Q, writes
+// the columns back and applies Q to the matching 32 columns of V
+// (V_blk <- V_blk Q, staged through the same shared memory).  Visiting every
+// block pair rotates every column pair once: one sweep of a cyclic Jacobi
+// ordering by blocks; sweeps repeat until one makes no rotation (or the
+// sweep cap, TP_DEV_NOCONV).  Each column pair
 // thereby costs shared-memory traffic; global memory sees each column once
 // per block pair instead of twice per rotation.  The convergence threshold
 // is the one of svd.cu, so the result is an SVD to the same tolerance (the
@@ -105,24 +106,48 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_blocked_kernel(
         Qi[e] = 0.f;
       }
       __syncthreads();
-      // one cyclic sweep over the nc columns: round-robin rounds of disjoint
-      // pairs, one pair per warp
-      const int ncc = nc + (nc & 1);
-      for (int step = 0; step < ncc - 1; ++step) {
-        for (int i = warp; i < ncc / 2; i += NW) {
+      // The rotations of this block pair, in rounds of disjoint column pairs
+      // (one pair per warp): the bI x bJ cross pairs (round t pairs local
+      // column i of I with column (i + t) mod bI of J), and each block's
+      // internal pairs once per sweep -- block I's in the block pair
+      // (I, I + 1), the last block's also in (nb - 2, nb - 1) -- by the
+      // round-robin order; a lone block has internal pairs only.
+      const bool within_I = J < 0 || J == I + 1;
+      const bool within_J = J >= 0 && J == nb - 1 && I == nb - 2;
+      const int ncI = bI + (bI & 1), ncJ = bJ + (bJ & 1);
+      const int wrounds = max(within_I ? ncI - 1 : 0, within_J ? ncJ - 1 : 0);
+      const int crounds = J < 0 ? 0 : bI;
+      for (int round = 0; round < wrounds + crounds; ++round) {
+        const bool cross = round >= wrounds;
+        const int t = cross ? round - wrounds : round;
+        const int npr = cross ? bI : (within_I ? ncI / 2 : 0) + (within_J ? ncJ / 2 : 0);
+        for (int i = warp; i < npr; i += NW) {
           int a, c2;
-          if (i == 0) {
-            a = ncc - 1;
-            c2 = step;
+          if (cross) {
+            const int jj = (i + t) % bI;
+            if (jj >= bJ) continue;
+            a = i;
+            c2 = bI + jj;
           } else {
-            a = (step + i) % (ncc - 1);
-            c2 = (step - i + (ncc - 1)) % (ncc - 1);
-          }
-          if (a >= nc || c2 >= nc) continue;
-          if (a > c2) {
-            const int t = a;
-            a = c2;
-            c2 = t;
+            int base = 0, n = bI, nn = ncI, k = i;
+            if (!within_I || k >= ncI / 2) {
+              k -= within_I ? ncI / 2 : 0;
+              base = bI;
+              n = bJ;
+              nn = ncJ;
+            }
+            if (t >= nn - 1) continue;
+            int x, y;
+            if (k == 0) {
+              x = nn - 1;
+              y = t;
+            } else {
+              x = (t + k) % (nn - 1);
+              y = (t - k + (nn - 1)) % (nn - 1);
+            }
+            if (x >= n || y >= n) continue;
+            a = base + min(x, y);
+            c2 = base + max(x, y);
           }
           float* const ar = Sr + size_t(a) * p;
           float* const ai = Si + size_t(a) * p;
