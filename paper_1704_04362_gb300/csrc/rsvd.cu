@@ -565,7 +565,11 @@ __device__ int jacobi2_fused(float2* G, float2* W, int l, int ls, float tol, int
       const int nblk = npairs * npairs;
       for (int e = threadIdx.x; e < nblk + npairs * l; e += blockDim.x) {
         if (e < nblk) {
+          // upper blocks only (pair i <= pair j); a block above the diagonal
+          // also writes its mirror, conj(K_j^H G K_i) = (K_i^H G K_j)^H, so
+          // that G stays Hermitian with half of the block updates
           const int i = e / npairs, j = e - i * npairs;
+          if (i > j) continue;
           const int2 ri = pq[i], rj = pq[j];
           // with odd l one pair holds the padding index l: its real index
           // takes the other pair's rotation only
@@ -604,6 +608,12 @@ __device__ int jacobi2_fused(float2* G, float2* W, int l, int ls, float tol, int
           if (jp) G[ri.x * ls + rj.y] = x01;
           if (ip) G[ri.y * ls + rj.x] = x10;
           if (ip && jp) G[ri.y * ls + rj.y] = x11;
+          if (i != j) {
+            G[rj.x * ls + ri.x] = make_float2(x00.x, -x00.y);
+            if (jp) G[rj.y * ls + ri.x] = make_float2(x01.x, -x01.y);
+            if (ip) G[rj.x * ls + ri.y] = make_float2(x10.x, -x10.y);
+            if (ip && jp) G[rj.y * ls + ri.y] = make_float2(x11.x, -x11.y);
+          }
         } else {
           const int w = e - nblk;
           const int j = w / l, r = w - j * l;
