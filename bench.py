@@ -585,7 +585,7 @@ def gpu_uuid(torch, dev):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # single-pass ncu capture of the full-size workload; valid only for the kernel
 # version it was taken on (profiles/cgemm_tc_2000x4000x1500x64_traffic.md).
-MEASURED_TRAFFIC = {"cgemm_tc:bf16x3": 475604480 + 739154944}
+MEASURED_TRAFFIC = {"cgemm_tc:bf16x3": 475354624 + 739854080}
 
 
 def kernel_bytes(name, cprime, precision):
