@@ -309,7 +309,7 @@ def bench_rows(tp, torch, with_cpu):
     return rows
 
 
-def bench_svt_batched(tp, torch, count=256, iters=100):
+def bench_svt_batched(tp, torch, count=256, iters=100, precision="fp32", sizes=None):
     """The batched completion workload: `count` videos of uneven size (H, W, T
     drawn uniformly from 64..480 x 64..360 x 16..120, PCG64 seed 0), each
     tubal rank 10 (N(0,1) factors) at unit RMS plus sigma = 0.01 noise, 50%
@@ -322,7 +322,7 @@ def bench_svt_batched(tp, torch, count=256, iters=100):
     the call's time minus it.  After one untimed 1-iteration call (the
     autotuner times its candidate launch shapes on first use)."""
     from paper_1704_04362_gb300 import synth
-    sizes = synth.video_sizes(count, seed=0)
+    sizes = sizes or synth.video_sizes(count, seed=0)
     data, truths = [], []
     for i, (H, W, T) in enumerate(sizes):
         truth = synth.lowrank_torch(H, W, T, 10, seed=5000 + i)
@@ -350,7 +350,8 @@ def bench_svt_batched(tp, torch, count=256, iters=100):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         tp.profile_start()
         e0.record()
-        tp.tcomplete_svt_batched(data, n)
+        tp.tcomplete_svt_batched(data, n, precision={"fp32": tp.TP_FP32, "tf32x3": tp.TP_TF32X3,
+                                                     "bf16x3": tp.TP_BF16X3}[precision])
         e1.record()
         torch.cuda.synchronize()
         prof = tp.profile_stop()
@@ -371,7 +372,7 @@ def bench_svt_batched(tp, torch, count=256, iters=100):
     return {"workload": f"{count} videos of uneven size (64..480 x 64..360 x 16..120), "
                         f"{elems} elements, {slices} half-spectrum slices per iteration, "
                         "tubal rank 10 + sigma 0.01, 50% observed",
-            "precision": "fp32",
+            "precision": precision,
             "iterations": iters, "total_ms": total_ms,
             "first_iteration_ms": total_ms - replay_ms, "warm_iteration_ms": warm_ms,
             "warm_iterations_per_s": 1e3 / warm_ms if warm_ms > 0 else None,
@@ -708,7 +709,8 @@ def headline(args, world, value, ms, cprime, launches, roof, kernels, cpu, e2e, 
             # frac: nominal 8mnk complex flops; pipe_frac: the three split
             # products the tensor cores execute per real product
             roof_c["pipe_frac"] = sig(roof["pipe_frac"])
-        roof_c["peak_src"] = roof.get("peak_src")
+        roof_c["peak_src"] = "measured bf16 burst" if roof.get("unit") == "TFLOP/s" and \
+            str(roof.get("peak_src", "")).startswith("measured") else roof.get("peak_src")
     forms = {args.precision: {"tflops": sig(value), "ms": sig(ms)}}
     for cm in compare:
         forms[cm["precision"]] = {"tflops": sig(cm["value"]), "ms": sig(cm["ms_per_step"])}
@@ -725,11 +727,13 @@ def headline(args, world, value, ms, cprime, launches, roof, kernels, cpu, e2e, 
         if rsvd.get("cpu_baseline"):
             r["oracle_tensors_per_s"] = sig(rsvd["cpu_baseline"]["value"], 3)
         sec["tsvd_randomized"] = r
-    cb = (rows or {}).get("completion_batched")
-    if cb:
-        sec["completion_batched"] = {k: sig(cb[k]) for k in
-                                     ("warm_iteration_ms", "iterations", "relative_error_to_truth")
-                                     if k in cb}
+    # batched completion: [warm iteration ms, iterations, relative error to the truth]
+    for key, name in (("completion_batched", "completion_fp32"),
+                      ("completion_batched_bf16x3", "completion_bf16x3")):
+        cb = (rows or {}).get(key)
+        if cb:
+            sec[name] = [sig(cb.get("warm_iteration_ms")), cb.get("iterations"),
+                         sig(cb.get("relative_error_to_truth"), 3)]
     line = {
         "metric": "t-product TFLOP/s & randomized t-SVD tensors/s vs plain FP32 at equal rel. error",
         "value": sig(value), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -739,7 +743,7 @@ def headline(args, world, value, ms, cprime, launches, roof, kernels, cpu, e2e, 
                   "bf16x3": "bf16x3 (f32 accumulate)"}[args.precision],
         "data": "synthetic",
         "config": {"workload": "rt-product (Alg. 2) A 2000x4000x64 * B 4000x1500x64, tubal "
-                               "rank 20 + 1% noise, c=400, p ~ ||A(:,j,:)|| ||B(j,:,:)||",
+                               "rank 20 + 1% noise, c=400, norm-product probabilities",
                    "c_prime": cprime, "precision": args.precision,
                    "l2": "inputs 3.58 GB > L2, streamed",
                    "parallelism": f"replicas x{world}"},
@@ -763,7 +767,7 @@ def headline(args, world, value, ms, cprime, launches, roof, kernels, cpu, e2e, 
     }
     # keep the line short: drop the least important parts first
     for drop in ("detail_file", "kernels_ms", "secondary"):
-        if len(json.dumps(line)) < 1900:
+        if len(json.dumps(line)) < 2000:
             break
         line.pop(drop, None)
     return line
@@ -791,7 +795,8 @@ def main():
                     help="iterations of the batched completion row (256 videos)")
     ap.add_argument("--only", default=None,
                     help="comma-separated rows to run instead of the headline step "
-                         "(rsvd, svt_batched): profiling and tuning runs, no headline line")
+                         "(rsvd, svt_batched, svt_batched_bf16x3, svt_video): profiling and "
+                         "tuning runs, no headline line")
     ap.add_argument("--tune-file", default=None,
                     help="autotuner table: loaded before the run when the file exists, "
                          "written after it (so that a profiled run reuses the plain run's "
@@ -827,6 +832,13 @@ def main():
                 out = bench_rsvd(args, tp, torch, with_cpu=False)
             elif name == "svt_batched":
                 out = bench_svt_batched(tp, torch, iters=args.svt_iters)
+            elif name == "svt_batched_bf16x3":
+                out = bench_svt_batched(tp, torch, iters=args.svt_iters, precision="bf16x3")
+            elif name == "svt_video":
+                # one 480 x 360 x 120 video (the largest of the batch): a
+                # single-tensor profiling case a few GB in size
+                out = bench_svt_batched(tp, torch, count=1, iters=args.svt_iters,
+                                        sizes=[(480, 360, 120)])
             else:
                 raise SystemExit(f"bench: unknown row {name!r}")
             print(json.dumps({"row": name, **out}, default=str))
@@ -991,6 +1003,9 @@ def main():
     if not args.no_rows and not args.small:
         rows = bench_rows(tp, torch, with_cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
         rows["completion_batched"] = bench_svt_batched(tp, torch, iters=args.svt_iters)
+        # the BF16x3 form (the SVT's three GEMMs on the tensor cores), fewer iterations
+        rows["completion_batched_bf16x3"] = bench_svt_batched(
+            tp, torch, iters=max(2, args.svt_iters // 4), precision="bf16x3")
         rows["learned_rank"] = bench_learned(torch)
         rows["table1_shape"] = bench_table1(tp, torch)
 

@@ -411,9 +411,10 @@ def tsvd_randomized(X, k, p=10, q=2, seed=0, status=None, max_sweeps=0, ranks=No
 
 
 def tcomplete_svt(X, mask, iters, L=None, E=None, Y=None, mu=None, mu0=1e-3, rho=1.1,
-                  mu_max=1e10, status=None, max_sweeps=0):
+                  mu_max=1e10, status=None, max_sweeps=0, precision=TP_FP32):
     """ADMM completion (Algorithm 7, problem tlow6).  State (L, E, Y, mu) is
-    updated in place and returned."""
+    updated in place and returned.  precision: TP_FP32, or TP_TF32X3 /
+    TP_BF16X3 for the SVT's three GEMMs on the tensor cores."""
     torch = _torch()
     n1, n2, n3 = X.shape
     if L is None:
@@ -422,7 +423,7 @@ def tcomplete_svt(X, mask, iters, L=None, E=None, Y=None, mu=None, mu0=1e-3, rho
         Y = torch.zeros_like(X)
     if mu is None:
         mu = torch.full((1,), float(mu0), dtype=torch.float64, device=X.device)
-    o = _opts(TP_OP_TCOMPLETE_SVT, (n1, n2, n3), TP_FP32, status, max_sweeps)
+    o = _opts(TP_OP_TCOMPLETE_SVT, (n1, n2, n3), precision, status, max_sweeps)
     rc = lib().tcomplete_svt(_tensor_arg(X, "X"), _tensor_arg(mask, "mask", torch.uint8),
                              n1, n2, n3, int(iters), float(rho), float(mu_max),
                              _tensor_arg(L, "L"), _tensor_arg(E, "E"), _tensor_arg(Y, "Y"),
@@ -432,7 +433,7 @@ def tcomplete_svt(X, mask, iters, L=None, E=None, Y=None, mu=None, mu0=1e-3, rho
 
 
 def trpca_admm(X, iters, lam=0.0, L=None, E=None, Y=None, mu=None, mu0=1e-3, rho=1.1,
-               mu_max=1e10, status=None, max_sweeps=0):
+               mu_max=1e10, status=None, max_sweeps=0, precision=TP_FP32):
     """Robust TNN (Algorithm 7, problem tlow7); lam <= 0 takes the default
     1/sqrt(max(n1, n2) n3).  State (L, E, Y, mu) updated in place and returned."""
     torch = _torch()
@@ -443,7 +444,7 @@ def trpca_admm(X, iters, lam=0.0, L=None, E=None, Y=None, mu=None, mu0=1e-3, rho
         Y = torch.zeros_like(X)
     if mu is None:
         mu = torch.full((1,), float(mu0), dtype=torch.float64, device=X.device)
-    o = _opts(TP_OP_TRPCA, (n1, n2, n3), TP_FP32, status, max_sweeps)
+    o = _opts(TP_OP_TRPCA, (n1, n2, n3), precision, status, max_sweeps)
     rc = lib().trpca_admm(_tensor_arg(X, "X"), n1, n2, n3, int(iters), float(lam), float(rho),
                           float(mu_max), _tensor_arg(L, "L"), _tensor_arg(E, "E"),
                           _tensor_arg(Y, "Y"), _tensor_arg(mu, "mu", torch.float64),
@@ -452,7 +453,8 @@ def trpca_admm(X, iters, lam=0.0, L=None, E=None, Y=None, mu=None, mu0=1e-3, rho
     return L, E, Y, mu
 
 
-def tcomplete_svt_batched(tensors, iters, rho=1.1, mu_max=1e10, status=None, max_sweeps=0):
+def tcomplete_svt_batched(tensors, iters, rho=1.1, mu_max=1e10, status=None, max_sweeps=0,
+                          precision=TP_FP32):
     """tcomplete_svt over a list of independent tensors of possibly different
     sizes: each item is a tuple (X, mask, L, E, Y, mu) of device tensors
     (column-major layout, mask uint8, mu a float64 1-element tensor), updated
@@ -468,7 +470,7 @@ def tcomplete_svt_batched(tensors, iters, rho=1.1, mu_max=1e10, status=None, max
                                 _tensor_arg(Y, "Y").value,
                                 _tensor_arg(mu, "mu", torch.float64).value, n1, n2, n3)
         dims += [n1, n2, n3]
-    o = _opts(TP_OP_TCOMPLETE_SVT_BATCHED, dims, TP_FP32, status, max_sweeps)
+    o = _opts(TP_OP_TCOMPLETE_SVT_BATCHED, dims, precision, status, max_sweeps)
     rc = lib().tcomplete_svt_batched(len(tensors), ctypes.cast(descs, ctypes.c_void_p), int(iters),
                                      float(rho), float(mu_max), ctypes.byref(o), _stream())
     _check(rc, "tcomplete_svt_batched")

@@ -7,8 +7,8 @@ namespace tp {
 size_t tsvd_ws(int64_t n1, int64_t n2, int64_t n3);
 bool fft_supported(int64_t n3);
 size_t rsvd_ws(int64_t n1, int64_t n2, int64_t n3, int64_t k, int64_t p, int prec = TP_FP32);
-size_t svt_ws(int64_t n1, int64_t n2, int64_t n3);
-size_t svt_batched_ws_dims(const int64_t* dims, int nd);
+size_t svt_ws(int64_t n1, int64_t n2, int64_t n3, int prec = TP_FP32);
+size_t svt_batched_ws_dims(const int64_t* dims, int nd, int prec);
 size_t mlp_ws(int64_t B);
 int svt_batched_run(int ntens, const tp_tensor_desc* d, int iters, double rho, double mu_max,
                     const tp_opts* opts, cudaStream_t st, const double* lams = nullptr);
@@ -43,8 +43,10 @@ size_t workspace_for(int op, const int64_t* d, int nd, const tp_opts* opts) {
     case TP_OP_TSVD_RANDOMIZED:
       return nd >= 5 ? rsvd_ws(d[0], d[1], d[2], d[3], d[4], opts ? opts->precision : TP_FP32) : 0;
     case TP_OP_TCOMPLETE_SVT:
-    case TP_OP_TRPCA: return nd >= 3 ? svt_ws(d[0], d[1], d[2]) : 0;
-    case TP_OP_TCOMPLETE_SVT_BATCHED: return nd >= 3 ? svt_batched_ws_dims(d, nd) : 0;
+    case TP_OP_TRPCA:
+      return nd >= 3 ? svt_ws(d[0], d[1], d[2], opts ? opts->precision : TP_FP32) : 0;
+    case TP_OP_TCOMPLETE_SVT_BATCHED:
+      return nd >= 3 ? svt_batched_ws_dims(d, nd, opts ? opts->precision : TP_FP32) : 0;
     case TP_OP_SKETCH_SPECTRUM: return nd >= 4 ? rsvd_ws(d[0], d[1], d[2], d[3], 0) : 0;
     case TP_OP_MLP_TRAIN: return nd >= 1 ? mlp_ws(d[0]) : 0;
     case TP_OP_TCX: return nd >= 3 ? tcx_ws(d[0], d[1], d[2]) : 0;

@@ -20,8 +20,16 @@
 // tau.  The shrunk slice is
 // sum_j max(s_j - tau, 0) u_j v_j^H = sum_j c_j h_j v_j^H,
 // c_j = max(s_j - tau, 0) / (s_j ||v_j||^2).
+//
+// Split forms (opts->precision TP_TF32X3 / TP_BF16X3): the iteration's three
+// GEMMs (G = W V_prev, H = W V, the rebuild) run on the tcgen05 tensor cores
+// with hi + lo operand planes.  Their operands are stored K-major: W and H
+// row-major (element (a, k) at k + lq a), V and the small rebuild operand
+// column-major; H is formed as its transpose H^T = V^T W^T, which comes out
+// of the GEMM already row-major, so no operand needs a transpose pass but W's.
 #include <vector>
 
+#include "dft_common.cuh"
 #include "tp_internal.cuh"
 
 namespace tp {
@@ -116,7 +124,8 @@ __global__ void to_work_kernel(const float* __restrict__ xr, const float* __rest
 // c_j conj(V(b, j))) when the slice is R itself, or V D (entry (b, j) =
 // V(b, j) c_j) when the slice is R^H = V D H^H.
 __global__ void svt_coef_kernel(const float* __restrict__ hr, const float* __restrict__ hi,
-                                int64_t sH, const float* __restrict__ vr,
+                                int64_t sH, int64_t h_row, int64_t h_col,
+                                const float* __restrict__ vr,
                                 const float* __restrict__ vi, int64_t sV, int p, int q,
                                 const double* __restrict__ mu, bool transpose,
                                 float* __restrict__ outr, float* __restrict__ outi) {
@@ -133,8 +142,8 @@ __global__ void svt_coef_kernel(const float* __restrict__ hr, const float* __res
       const double x = Vr[b + int64_t(q) * j], y = Vi[b + int64_t(q) * j];
       nv += x * x + y * y;
     }
-    for (int a = 0; a < p; ++a) {
-      const double x = Hr[a + int64_t(p) * j], y = Hi[a + int64_t(p) * j];
+    for (int a = 0; a < p; ++a) {   // H(a, j) at a h_row + j h_col
+      const double x = Hr[a * h_row + j * h_col], y = Hi[a * h_row + j * h_col];
       nh += x * x + y * y;
     }
     const double s = nv > 0.0 ? sqrt(nh / nv) : 0.0;
@@ -158,6 +167,58 @@ __global__ void svt_coef_kernel(const float* __restrict__ hr, const float* __res
   }
 }
 
+// Split planes of a batch of matrices (rows x cols, column-major, leading
+// dimension ld_src, batch stride s_src) at f*s_dst + r + ld_dst*c; rows
+// [rows, ld_dst) are zero; the imaginary part negated when conj.
+__global__ void svt_split_kernel(const float* __restrict__ sr, const float* __restrict__ si,
+                                 int64_t rows, int64_t cols, int64_t ld_src, int64_t s_src,
+                                 int64_t h, int64_t ld_dst, int64_t s_dst, int conj, int bf16,
+                                 float* __restrict__ p0, float* __restrict__ p1,
+                                 float* __restrict__ p2, float* __restrict__ p3) {
+  const int64_t per = ld_dst * cols, total = per * h;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t f = e / per, rem = e - f * per;
+    const int64_t c = rem / ld_dst, r = rem - c * ld_dst;
+    float vr = 0.f, vi = 0.f;
+    if (r < rows) {
+      vr = sr[f * s_src + r + ld_src * c];
+      vi = si[f * s_src + r + ld_src * c];
+      if (conj) vi = -vi;
+    }
+    dftc::put_split(p0, p1, bf16 != 0, e, vr);
+    dftc::put_split(p2, p3, bf16 != 0, e, vi);
+  }
+}
+
+// The same split of the transposes: element (r, c) of matrix f (rows x cols,
+// column-major, ld rows) goes to f*s_dst + c + ld_dst*r (the K-major, i.e.
+// row-major, operand); 32 x 32 tiles through shared memory.
+__global__ void svt_split_t_kernel(const float* __restrict__ sr, const float* __restrict__ si,
+                                   int64_t rows, int64_t cols, int64_t ld_dst, int64_t s_dst,
+                                   int bf16, float* __restrict__ p0, float* __restrict__ p1,
+                                   float* __restrict__ p2, float* __restrict__ p3) {
+  __shared__ float tr[32][33], ti[32][33];
+  const int64_t f = blockIdx.z;
+  const int64_t r0 = int64_t(blockIdx.x) * 32, c0 = int64_t(blockIdx.y) * 32;
+  const float* xr = sr + f * rows * cols;
+  const float* xi = si + f * rows * cols;
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int64_t r = r0 + threadIdx.x, c = c0 + dy;
+    tr[dy][threadIdx.x] = (r < rows && c < cols) ? xr[r + rows * c] : 0.f;
+    ti[dy][threadIdx.x] = (r < rows && c < cols) ? xi[r + rows * c] : 0.f;
+  }
+  __syncthreads();
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int64_t c = c0 + threadIdx.x, r = r0 + dy;
+    if (r < rows && c < ld_dst) {   // c in [cols, ld_dst): the zero K padding
+      const int64_t o = f * s_dst + c + ld_dst * r;
+      dftc::put_split(p0, p1, bf16 != 0, o, tr[threadIdx.x][dy]);
+      dftc::put_split(p2, p3, bf16 != 0, o, ti[threadIdx.x][dy]);
+    }
+  }
+}
+
 __global__ void flags_kernel(int* flags, int64_t h, int64_t n3) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k < h) flags[k] = (k == 0 || (n3 % 2 == 0 && k == h - 1)) ? 1 : 0;
@@ -172,11 +233,21 @@ unsigned grid_n(int64_t n) {
 
 }  // namespace
 
-size_t svt_ws(int64_t n1, int64_t n2, int64_t n3) {
+// K leading dimension of the split operand planes (16-byte rows for TMA).
+int64_t svt_ld(int64_t k, int prec) {
+  return prec == TP_BF16X3 ? (k + 7) / 8 * 8 : (k + 3) / 4 * 4;
+}
+bool svt_tc(int prec) { return prec == TP_TF32X3 || prec == TP_BF16X3; }
+
+size_t svt_ws(int64_t n1, int64_t n2, int64_t n3, int prec) {
   const size_t h = size_t(half_len(n3));
   const size_t p = size_t(n1 > n2 ? n1 : n2), q = size_t(n1 < n2 ? n1 : n2);
   const size_t n = size_t(n1) * n2;
-  return ws_bytes(n * n3, 4)                  // M (and L, reused)
+  const size_t lq = size_t(svt_ld(int64_t(q), prec)), esz = prec == TP_BF16X3 ? 2 : 4;
+  const size_t split = svt_tc(prec) ? 4 * (2 * ws_bytes(lq * p * h, esz)      // W, H planes
+                                           + 2 * ws_bytes(lq * q * h, esz))   // V, rebuild planes
+                                    : 0;
+  return split + ws_bytes(n * n3, 4)          // M (and L, reused)
          + 2 * ws_bytes(n * h, 4)             // M_hat / L_hat
          + 2 * ws_bytes(p * q * h, 4)         // G (rotated by the Jacobi)
          + 2 * ws_bytes(q * q * h, 4)         // V
@@ -197,11 +268,18 @@ struct SvtTensor {
   bool transpose;
   float *M, *Mr, *Mi, *Gr, *Gi, *Vr, *Vi, *Kr, *Ki, *Hr, *Hi, *sig;
   int* flags;
+  // split forms: precision, K leading dimension lq, operand planes (re hi,
+  // re lo, im hi, im lo): W and H row-major, V and the rebuild operand
+  // column-major (or row-major for V D)
+  int prec;
+  int64_t lq;
+  float *WP[4], *HP[4], *VP[4], *BP[4];
 };
 
 SvtTensor svt_carve(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t n3,
-                    float* L, float* E, float* Y, double* mu, Arena& ws) {
+                    float* L, float* E, float* Y, double* mu, Arena& ws, int prec) {
   SvtTensor t{};
+  t.prec = prec;
   t.X = X;
   t.mask = mask;
   t.L = L;
@@ -229,6 +307,19 @@ SvtTensor svt_carve(const float* X, const uint8_t* mask, int64_t n1, int64_t n2,
   t.Hi = ws.take<float>(pq * h);
   t.sig = ws.take<float>(size_t(t.q) * h);
   t.flags = ws.take<int>(h);
+  t.lq = svt_ld(t.q, prec);
+  if (svt_tc(prec)) {
+    const size_t lq = size_t(t.lq);
+    auto planes = [&](float** P, size_t elems) {
+      for (int i = 0; i < 4; ++i)
+        P[i] = prec == TP_BF16X3 ? reinterpret_cast<float*>(ws.take<uint16_t>(elems))
+                                 : ws.take<float>(elems);
+    };
+    planes(t.WP, lq * size_t(t.p) * h);
+    planes(t.HP, lq * size_t(t.p) * h);
+    planes(t.VP, lq * size_t(t.q) * h);
+    planes(t.BP, lq * size_t(t.q) * h);
+  }
   return t;
 }
 
@@ -260,10 +351,48 @@ int svt_iteration(const SvtTensor& t, bool warm, double rho, double mu_max, int 
                                                     t.Ki, warm ? nullptr : t.Gr,
                                                     warm ? nullptr : t.Gi);
   }
+  const bool tc = svt_tc(t.prec);
+  const int bf = t.prec == TP_BF16X3 ? 1 : 0;
+  const int64_t lq = t.lq;
+  // tensor-core GEMM C = A B over the h slices, A (M x K) and B (K x N) split
+  // planes stored K-major with leading dimension lq, C column-major (ldc)
+  auto gemm_tc = [&](float* const* A, float* const* B, float* cr, float* ci, int64_t M,
+                     int64_t N, int64_t ldc) {
+    CGemm g{A[0], A[2], B[0], B[2], cr, ci, M, N, q, nullptr, lq, lq, ldc, lq * M, lq * N,
+            M * N, h, t.n3, t.prec, A[1], A[3], B[1], B[3], lq, status};
+    return launch_cgemm(g, st);
+  };
+  auto split = [&](const float* sr, const float* si, int64_t rows, int64_t cols, int conj,
+                   float* const* P) {
+    {
+      KernelScope ks("svt_split", st);
+      svt_split_kernel<<<grid_n(lq * cols * h), 256, 0, st>>>(
+          sr, si, rows, cols, rows, rows * cols, h, lq, lq * cols, conj, bf, P[0], P[1], P[2],
+          P[3]);
+    }
+    return launch_status("svt_split_kernel");
+  };
+  // row-major split of the column-major rows x cols matrices (K = cols)
+  auto split_t = [&](const float* sr, const float* si, int64_t rows, int64_t cols,
+                     float* const* P) {
+    {
+      KernelScope ks("svt_split_t", st);
+      svt_split_t_kernel<<<dim3(unsigned((rows + 31) / 32), unsigned((lq + 31) / 32),
+                                unsigned(h)),
+                           dim3(32, 8), 0, st>>>(sr, si, rows, cols, lq, lq * rows, bf, P[0],
+                                                 P[1], P[2], P[3]);
+    }
+    return launch_status("svt_split_t_kernel");
+  };
+  if (tc && (rc = split_t(t.Kr, t.Ki, p, q, t.WP))) return rc;   // W, row-major
   if (warm) {   // G = W V_prev
-    CGemm gw{t.Kr, t.Ki, t.Vr, t.Vi, t.Gr, t.Gi, p, q, q, nullptr, p, q, p, p * q, q * q, p * q,
-             h, t.n3, TP_FP32, nullptr, nullptr, nullptr, nullptr, q, status};
-    if ((rc = launch_cgemm(gw, st))) return rc;
+    if (tc) {
+      if ((rc = gemm_tc(t.WP, t.VP, t.Gr, t.Gi, p, q, p))) return rc;
+    } else {
+      CGemm gw{t.Kr, t.Ki, t.Vr, t.Vi, t.Gr, t.Gi, p, q, q, nullptr, p, q, p, p * q, q * q, p * q,
+               h, t.n3, TP_FP32, nullptr, nullptr, nullptr, nullptr, q, status};
+      if ((rc = launch_cgemm(gw, st))) return rc;
+    }
   }
   if (TP_SVT_BLOCKED && jacobi_blocked_applies(int(p), int(q)))
     rc = jacobi_float_blocked_launch(t.Gr, t.Gi, p * q, t.Vr, t.Vi, q * q, t.sig, int(p), int(q),
@@ -272,7 +401,12 @@ int svt_iteration(const SvtTensor& t, bool warm, double rho, double mu_max, int 
     rc = jacobi_float_launch(t.Gr, t.Gi, p * q, t.Vr, t.Vi, q * q, t.sig, int(p), int(q),
                              int(h), sweeps, t.flags, status, !warm, st);
   if (rc) return rc;
-  {   // H = W V from the unrotated work matrix
+  if (tc) {
+    // V's planes (also V_prev of the next iteration's G = W V_prev), then
+    // H^T = V^T W^T (q x p, column-major: H row-major) from the unrotated W
+    if ((rc = split(t.Vr, t.Vi, q, q, 0, t.VP))) return rc;
+    if ((rc = gemm_tc(t.VP, t.WP, t.Hr, t.Hi, q, p, q))) return rc;
+  } else {   // H = W V from the unrotated work matrix
     CGemm gh{t.Kr, t.Ki, t.Vr, t.Vi, t.Hr, t.Hi, p, q, q, nullptr, p, q, p, p * q, q * q, p * q,
              h, t.n3, TP_FP32, nullptr, nullptr, nullptr, nullptr, q, status};
     if ((rc = launch_cgemm(gh, st))) return rc;
@@ -280,9 +414,20 @@ int svt_iteration(const SvtTensor& t, bool warm, double rho, double mu_max, int 
   {   // shrink factors into the small operand (in G, free after the Jacobi)
     KernelScope ks("svt_coef", st);
     svt_coef_kernel<<<unsigned(h), 256, size_t(q) * sizeof(float), st>>>(
-        t.Hr, t.Hi, p * q, t.Vr, t.Vi, q * q, int(p), int(q), t.mu, t.transpose, t.Gr, t.Gi);
+        t.Hr, t.Hi, p * q, tc ? q : 1, tc ? 1 : p, t.Vr, t.Vi, q * q, int(p), int(q), t.mu,
+        t.transpose, t.Gr, t.Gi);
   }
-  if (!t.transpose) {   // slice = H (D V^H): n1 x n2 = p x q
+  if (tc) {
+    if (!t.transpose) {   // slice (p x q) = H (D V^H)
+      if ((rc = split(t.Hr, t.Hi, q, p, 0, t.HP))) return rc;     // H row-major
+      if ((rc = split(t.Gr, t.Gi, q, q, 0, t.BP))) return rc;     // D V^H column-major
+      if ((rc = gemm_tc(t.HP, t.BP, t.Mr, t.Mi, p, q, p))) return rc;
+    } else {              // slice (q x p) = (V D) H^H
+      if ((rc = split(t.Hr, t.Hi, q, p, 1, t.HP))) return rc;     // conj(H) row-major
+      if ((rc = split_t(t.Gr, t.Gi, q, q, t.BP))) return rc;      // V D row-major
+      if ((rc = gemm_tc(t.BP, t.HP, t.Mr, t.Mi, q, p, q))) return rc;
+    }
+  } else if (!t.transpose) {   // slice = H (D V^H): n1 x n2 = p x q
     CGemm gr{t.Hr, t.Hi, t.Gr, t.Gi, t.Mr, t.Mi, p, q, q, nullptr, p, q, p, p * q, q * q, p * q,
              h, t.n3, TP_FP32, nullptr, nullptr, nullptr, nullptr, q, status};
     if ((rc = launch_cgemm(gr, st))) return rc;
@@ -308,12 +453,17 @@ int svt_iteration(const SvtTensor& t, bool warm, double rho, double mu_max, int 
 int svt_run(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t n3, int iters,
             double rho, double mu_max, float* L, float* E, float* Y, double* mu,
             const tp_opts* opts, cudaStream_t st, double lam) {
+  const int prec = opts ? opts->precision : TP_FP32;
+  if (prec != TP_FP32 && !svt_tc(prec)) {
+    set_error("admm: unknown precision %d", prec);
+    return TP_EINVAL;
+  }
   Arena ws;
-  int rc = acquire_workspace(opts, svt_ws(n1, n2, n3), &ws);
+  int rc = acquire_workspace(opts, svt_ws(n1, n2, n3, prec), &ws);
   if (rc) return rc;
   int32_t* status = opts ? opts->status : nullptr;
   const int sweeps = (opts && opts->max_sweeps > 0) ? opts->max_sweeps : 30;
-  SvtTensor t = svt_carve(X, mask, n1, n2, n3, L, E, Y, mu, ws);
+  SvtTensor t = svt_carve(X, mask, n1, n2, n3, L, E, Y, mu, ws, prec);
   t.lam = lam;
   if ((rc = svt_init(t, st))) return rc;
   for (int it = 0; it < iters; ++it)
@@ -321,15 +471,15 @@ int svt_run(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t
   return TP_OK;
 }
 
-size_t svt_batched_ws(int ntens, const tp_tensor_desc* d) {
+size_t svt_batched_ws(int ntens, const tp_tensor_desc* d, int prec) {
   size_t total = 0;
-  for (int i = 0; i < ntens; ++i) total += svt_ws(d[i].n1, d[i].n2, d[i].n3);
+  for (int i = 0; i < ntens; ++i) total += svt_ws(d[i].n1, d[i].n2, d[i].n3, prec);
   return total;
 }
 
-size_t svt_batched_ws_dims(const int64_t* dims, int nd) {
+size_t svt_batched_ws_dims(const int64_t* dims, int nd, int prec) {
   size_t total = 0;
-  for (int i = 0; i + 2 < nd; i += 3) total += svt_ws(dims[i], dims[i + 1], dims[i + 2]);
+  for (int i = 0; i + 2 < nd; i += 3) total += svt_ws(dims[i], dims[i + 1], dims[i + 2], prec);
   return total;
 }
 
@@ -364,8 +514,13 @@ int svt_fork_join(std::vector<SvtTensor>& T, bool warm, bool init, double rho, d
 
 int svt_batched_run(int ntens, const tp_tensor_desc* d, int iters, double rho, double mu_max,
                     const tp_opts* opts, cudaStream_t st, const double* lams) {
+  const int prec = opts ? opts->precision : TP_FP32;
+  if (prec != TP_FP32 && !svt_tc(prec)) {
+    set_error("tcomplete_svt_batched: unknown precision %d", prec);
+    return TP_EINVAL;
+  }
   Arena ws;
-  int rc = acquire_workspace(opts, svt_batched_ws(ntens, d), &ws);
+  int rc = acquire_workspace(opts, svt_batched_ws(ntens, d, prec), &ws);
   if (rc) return rc;
   if (iters <= 0) return TP_OK;
   int32_t* status = opts ? opts->status : nullptr;
@@ -374,7 +529,7 @@ int svt_batched_run(int ntens, const tp_tensor_desc* d, int iters, double rho, d
   T.reserve(size_t(ntens));
   for (int i = 0; i < ntens; ++i) {
     T.push_back(svt_carve(d[i].X, d[i].mask, d[i].n1, d[i].n2, d[i].n3, d[i].L, d[i].E, d[i].Y,
-                          d[i].mu, ws));
+                          d[i].mu, ws, prec));
     if (lams) T.back().lam = lams[i];   // > 0: robust form of problem tlow7
   }
   const int ns = ntens < kSideStreams ? ntens : kSideStreams;

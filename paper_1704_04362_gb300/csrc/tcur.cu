@@ -33,7 +33,7 @@
 namespace tp {
 
 int launch_cgemm(const CGemm& g, cudaStream_t st);
-size_t svt_ws(int64_t n1, int64_t n2, int64_t n3);
+size_t svt_ws(int64_t n1, int64_t n2, int64_t n3, int prec = TP_FP32);
 int svt_batched_run(int ntens, const tp_tensor_desc* d, int iters, double rho, double mu_max,
                     const tp_opts* opts, cudaStream_t st, const double* lams);
 int hybrid_svd(const float* xr, const float* xi, int64_t sX, int64_t ldx, bool conj, int p, int q,

@@ -7,7 +7,7 @@ import pytest
 import paper_1704_04362_gb300 as tp
 from paper_1704_04362_gb300 import synth
 from oracle import completion_ref
-from tests.util import TOL_FP32, rel_fro, to_np
+from tests.util import TOL_FP32, rel_fro, to_np, tol_for
 
 pytestmark = pytest.mark.gpu
 
@@ -24,9 +24,13 @@ def state_on_device(X, mask, L, E, Y, mu):
 
 # the last two slices exceed the shared-memory Jacobi and take the blocked
 # one (128 columns in 8 blocks; 150 columns, transposed, with a ragged block)
+@pytest.mark.parametrize("precision", [tp.TP_FP32, tp.TP_TF32X3, tp.TP_BF16X3])
 @pytest.mark.parametrize("n1,n2,n3", [(20, 16, 6), (12, 30, 5), (24, 24, 1), (33, 17, 8),
                                       (160, 128, 4), (150, 200, 5)])
-def test_one_iteration_matches_oracle(n1, n2, n3):
+def test_one_iteration_matches_oracle(n1, n2, n3, precision):
+    """One iteration in each form: FP32, and the SVT's three GEMMs on the
+    tensor cores with the 3xTF32 or BF16x3 split (held to that split's
+    tolerance)."""
     import torch
     g = np.random.default_rng(n1 * n2 + n3)
     X = synth.lowrank_np(n1, n2, n3, 3, seed=n3, noise=0.01)
@@ -39,18 +43,19 @@ def test_one_iteration_matches_oracle(n1, n2, n3):
     mu = 0.08
     Xd, Md, Ld, Ed, Yd, mud = state_on_device(X, mask, L0, E, Y, mu)
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
-    tp.tcomplete_svt(Xd, Md, 1, L=Ld, E=Ed, Y=Yd, mu=mud, status=st)
+    tp.tcomplete_svt(Xd, Md, 1, L=Ld, E=Ed, Y=Yd, mu=mud, status=st, precision=precision)
     assert int(st.item()) == 0
     Xo = np.where(mask, X.astype(np.float64), 0.0)
     Lr, Er, Yr, mur = completion_ref.admm_step(Xo, mask, L0.astype(np.float64),
                                                E.astype(np.float64), Y.astype(np.float64), mu)
     assert np.linalg.norm(Lr) > 0          # the threshold keeps part of the spectrum
-    assert rel_fro(to_np(Ld), Lr) < TOL_FP32
-    assert rel_fro(to_np(Ed), Er) < TOL_FP32
+    tol = tol_for(precision)
+    assert rel_fro(to_np(Ld), Lr) < tol
+    assert rel_fro(to_np(Ed), Er) < tol
     # Y <- Y + mu (L + E - X) (Algorithm 7) inherits mu times L's error: Y is
     # held to the float32 bound on the scale of that update
     dY = np.linalg.norm(to_np(Yd) - Yr)
-    assert dY < TOL_FP32 * (np.linalg.norm(Yr) + mu * np.linalg.norm(Lr))
+    assert dY < tol * (np.linalg.norm(Yr) + mu * np.linalg.norm(Lr))
     assert abs(float(mud.item()) - mur) <= 1e-15 * mur
     assert np.all(to_np(Ed)[mask] == 0)
 
@@ -97,11 +102,13 @@ def test_recovers_low_rank_video():
     assert rse < 0.05
 
 
-def test_batched_equals_separate_calls_and_oracle():
+@pytest.mark.parametrize("precision", [tp.TP_FP32, tp.TP_BF16X3])
+def test_batched_equals_separate_calls_and_oracle(precision):
     """tcomplete_svt_batched over tensors of uneven sizes (one per side
     stream and a shared side stream for the rest, graph replay after the
     first iteration) gives exactly the results of separate tcomplete_svt
-    calls; the smallest tensor also tracks the oracle."""
+    calls, in the FP32 and the BF16x3 form; the first tensor also tracks the
+    oracle."""
     import torch
     sizes = [(20, 16, 6), (12, 30, 5), (33, 17, 8), (24, 24, 1), (16, 40, 7), (9, 11, 4),
              (30, 22, 3), (18, 18, 9), (40, 12, 6), (14, 26, 5)]
@@ -115,10 +122,10 @@ def test_batched_equals_separate_calls_and_oracle():
         batch.append(state_on_device(X, mask, Z, Z, Z, 1e-3))
         single.append(state_on_device(X, mask, Z, Z, Z, 1e-3))
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
-    tp.tcomplete_svt_batched(batch, iters, status=st)
+    tp.tcomplete_svt_batched(batch, iters, status=st, precision=precision)
     assert int(st.item()) == 0
     for (Xd, Md, L, E, Y, mu) in single:
-        tp.tcomplete_svt(Xd, Md, iters, L=L, E=E, Y=Y, mu=mu)
+        tp.tcomplete_svt(Xd, Md, iters, L=L, E=E, Y=Y, mu=mu, precision=precision)
     for b, s in zip(batch, single):
         for x, y in zip(b[2:], s[2:]):
             assert torch.equal(x, y)
@@ -128,7 +135,7 @@ def test_batched_equals_separate_calls_and_oracle():
     X = X / np.sqrt(np.mean(X.astype(np.float64) ** 2))
     mask = np.random.default_rng(80).random(X.shape) < 0.6
     Lr, _, _, mur = completion_ref.tcomplete_svt(X.astype(np.float64), mask, iters)
-    assert rel_fro(to_np(batch[0][2]), Lr) < 1e-4
+    assert rel_fro(to_np(batch[0][2]), Lr) < (1e-4 if precision == tp.TP_FP32 else 5e-4)
     assert abs(float(batch[0][5].item()) / mur - 1) < 1e-12
 
 
