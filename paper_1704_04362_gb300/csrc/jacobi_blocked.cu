@@ -54,6 +54,7 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_blocked_kernel(
   float* const Qr = jb_smem + size_t(2) * JB_C * p;   // Q(r, c) at c * JB_C + r
   float* const Qi = Qr + JB_C * JB_C;
   __shared__ int any_rot, blk_rot;
+  __shared__ float nrm[JB_C];   // squared norms of the staged columns
   const int64_t b = blockIdx.x;
   float* const Gr = g_re + b * sG;
   float* const Gi = g_im + b * sG;
@@ -95,11 +96,24 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_blocked_kernel(
       const int bJ = J < 0 ? 0 : min(JB_B, q - J * JB_B);
       const int nc = bI + bJ;
       if (tid == 0) blk_rot = 0;
-      for (int e = tid; e < nc * p; e += JB_THREADS) {
-        const int c = e / p, r = e - c * p;
-        const int64_t src = int64_t(jb_col(c, I, J, bI)) * p + r;
-        Sr[e] = Gr[src];
-        Si[e] = Gi[src];
+      // stage the nc columns (a warp per column, lanes along it) and their
+      // squared norms; the rotations below update the norms exactly
+      // (||a'||^2 = alpha - t |gamma|, ||b'||^2 = beta + t |gamma|), so each
+      // pair needs only its inner product
+      for (int c = warp; c < nc; c += NW) {
+        const float* gr_c = Gr + int64_t(jb_col(c, I, J, bI)) * p;
+        const float* gi_c = Gi + int64_t(jb_col(c, I, J, bI)) * p;
+        float* sr_c = Sr + size_t(c) * p;
+        float* si_c = Si + size_t(c) * p;
+        float acc = 0.f;
+        for (int r = lane; r < p; r += 32) {
+          const float xr = gr_c[r], xi = gi_c[r];
+          sr_c[r] = xr;
+          si_c[r] = xi;
+          acc = fmaf(xr, xr, fmaf(xi, xi, acc));
+        }
+        acc = jb_warp_sum(acc);
+        if (lane == 0) nrm[c] = acc;
       }
       for (int e = tid; e < JB_C * JB_C; e += JB_THREADS) {
         Qr[e] = (e % (JB_C + 1) == 0) ? 1.f : 0.f;
@@ -153,16 +167,13 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_blocked_kernel(
           float* const ai = Si + size_t(a) * p;
           float* const br = Sr + size_t(c2) * p;
           float* const bi = Si + size_t(c2) * p;
-          float alpha = 0.f, beta = 0.f, gr = 0.f, gi = 0.f;
+          const float alpha = nrm[a], beta = nrm[c2];
+          float gr = 0.f, gi = 0.f;
           for (int r = lane; r < p; r += 32) {
             const float xr = ar[r], xi = ai[r], yr = br[r], yi = bi[r];
-            alpha += xr * xr + xi * xi;
-            beta += yr * yr + yi * yi;
-            gr += xr * yr + xi * yi;   // Re(conj(x) y)
-            gi += xr * yi - xi * yr;   // Im(conj(x) y)
+            gr = fmaf(xr, yr, fmaf(xi, yi, gr));    // Re(conj(x) y)
+            gi = fmaf(xr, yi, fmaf(-xi, yr, gi));   // Im(conj(x) y)
           }
-          alpha = jb_warp_sum(alpha);
-          beta = jb_warp_sum(beta);
           gr = jb_warp_sum(gr);
           gi = jb_warp_sum(gi);
           const float g2 = gr * gr + gi * gi;
@@ -170,6 +181,11 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_blocked_kernel(
           if (lane == 0) blk_rot = 1;
           float cs, sn, er, ei;   // cos, sin and e^{-i phi}
           rotation(alpha, beta, gr, gi, g2, cs, sn, er, ei);
+          if (lane == 0) {
+            const float tg = (sn / cs) * sqrtf(g2);
+            nrm[a] = alpha - tg;
+            nrm[c2] = beta + tg;
+          }
           for (int r = lane; r < p; r += 32) {
             const float xr = ar[r], xi = ai[r];
             const float yr = br[r] * er - bi[r] * ei, yi = br[r] * ei + bi[r] * er;
@@ -198,18 +214,26 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_blocked_kernel(
         __syncthreads();
       }
       if (blk_rot) {   // uniform: every write of it precedes the last barrier
-        for (int e = tid; e < nc * p; e += JB_THREADS) {
-          const int c = e / p, r = e - c * p;
-          const int64_t dst = int64_t(jb_col(c, I, J, bI)) * p + r;
-          Gr[dst] = Sr[e];
-          Gi[dst] = Si[e];
+        for (int c = warp; c < nc; c += NW) {
+          float* gr_c = Gr + int64_t(jb_col(c, I, J, bI)) * p;
+          float* gi_c = Gi + int64_t(jb_col(c, I, J, bI)) * p;
+          const float* sr_c = Sr + size_t(c) * p;
+          const float* si_c = Si + size_t(c) * p;
+          for (int r = lane; r < p; r += 32) {
+            gr_c[r] = sr_c[r];
+            gi_c[r] = si_c[r];
+          }
         }
         __syncthreads();   // the staging area now takes V's columns
-        for (int e = tid; e < nc * q; e += JB_THREADS) {
-          const int c = e / q, r = e - c * q;
-          const int64_t src = int64_t(jb_col(c, I, J, bI)) * q + r;
-          Sr[e] = Vr[src];
-          Si[e] = Vi[src];
+        for (int c = warp; c < nc; c += NW) {
+          const float* vr_c = Vr + int64_t(jb_col(c, I, J, bI)) * q;
+          const float* vi_c = Vi + int64_t(jb_col(c, I, J, bI)) * q;
+          float* sr_c = Sr + size_t(c) * q;
+          float* si_c = Si + size_t(c) * q;
+          for (int r = lane; r < q; r += 32) {
+            sr_c[r] = vr_c[r];
+            si_c[r] = vi_c[r];
+          }
         }
         __syncthreads();
         // V_blk <- V_blk Q, register-tiled: a warp task is 128 rows (4 per
