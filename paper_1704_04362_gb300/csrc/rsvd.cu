@@ -517,7 +517,8 @@ __global__ void __launch_bounds__(QR_THREADS) cholqr2_smem_kernel(float* y_re, f
 }
 
 // Two-sided Jacobi on the Hermitian l x l matrix G (row stride ls) with the
-// rotations accumulated into W (W <- W K), float32.  Each step takes the
+// rotations accumulated into W (W <- W K; W column-major, column stride ls),
+// float32.  Each step takes the
 // ll/2 disjoint round-robin pairs: first every pair's rotation from the
 // current G, then one pass that updates every 2 x 2 block (rows of pair i,
 // columns of pair j) with both rotations at once (K_i^H G K_j restricted to
@@ -561,20 +562,23 @@ __device__ int jacobi2_fused(float2* G, float2* W, int l, int ls, float tol, int
       __syncthreads();
       // G blocks: new rows (a, b) = [c x_a - s e^{i phi} x_b, s x_a + c e^{i phi} x_b]
       // of pair i, then new columns (a, b) = [c y_a - s e^{-i phi} y_b,
-      // s y_a + c e^{-i phi} y_b] of pair j; W: the column rotation only
-      const int nblk = npairs * npairs;
-      for (int e = threadIdx.x; e < nblk + npairs * l; e += blockDim.x) {
-        if (e < nblk) {
+      // s y_a + c e^{-i phi} y_b] of pair j (a warp per block row i, its lanes
+      // over j); W (column-major) takes the column rotation only (a warp per
+      // pair, its lanes along the two columns)
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+      for (int i = warp; i < npairs; i += nw) {
+        const int2 ri = pq[i];
+        const float4 Ri = rot[i];
+        const bool ip = ri.y < l;
+        for (int j = i + lane; j < npairs; j += 32) {
           // upper blocks only (pair i <= pair j); a block above the diagonal
           // also writes its mirror, conj(K_j^H G K_i) = (K_i^H G K_j)^H, so
           // that G stays Hermitian with half of the block updates
-          const int i = e / npairs, j = e - i * npairs;
-          if (i > j) continue;
-          const int2 ri = pq[i], rj = pq[j];
+          const int2 rj = pq[j];
           // with odd l one pair holds the padding index l: its real index
           // takes the other pair's rotation only
-          const bool ip = ri.y < l, jp = rj.y < l;
-          const float4 Ri = rot[i], Rj = rot[j];
+          const bool jp = rj.y < l;
+          const float4 Rj = rot[j];
           const bool rowrot = ip && Ri.y != 0.f, colrot = jp && Rj.y != 0.f;
           if (!rowrot && !colrot) continue;
           const float2 zero = make_float2(0.f, 0.f);
@@ -614,17 +618,20 @@ __device__ int jacobi2_fused(float2* G, float2* W, int l, int ls, float tol, int
             if (ip) G[rj.x * ls + ri.y] = make_float2(x10.x, -x10.y);
             if (ip && jp) G[rj.y * ls + ri.y] = make_float2(x11.x, -x11.y);
           }
-        } else {
-          const int w = e - nblk;
-          const int j = w / l, r = w - j * l;
-          const int2 rj = pq[j];
-          const float4 Rj = rot[j];
-          if (rj.y >= l || Rj.y == 0.f) continue;
-          const float c = Rj.x, s = Rj.y, er = Rj.z, ei = Rj.w;
-          const float2 x = W[r * ls + rj.x], y = W[r * ls + rj.y];
+        }
+      }
+      for (int j = warp; j < npairs; j += nw) {
+        const int2 rj = pq[j];
+        const float4 Rj = rot[j];
+        if (rj.y >= l || Rj.y == 0.f) continue;
+        const float c = Rj.x, s = Rj.y, er = Rj.z, ei = Rj.w;
+        float2* wa = W + rj.x * ls;
+        float2* wb = W + rj.y * ls;
+        for (int r = lane; r < l; r += 32) {
+          const float2 x = wa[r], y = wb[r];
           const float2 yy = make_float2(y.x * er - y.y * ei, y.x * ei + y.y * er);
-          W[r * ls + rj.x] = make_float2(c * x.x - s * yy.x, c * x.y - s * yy.y);
-          W[r * ls + rj.y] = make_float2(s * x.x + c * yy.x, s * x.y + c * yy.y);
+          wa[r] = make_float2(c * x.x - s * yy.x, c * x.y - s * yy.y);
+          wb[r] = make_float2(s * x.x + c * yy.x, s * x.y + c * yy.y);
         }
       }
     }
@@ -648,65 +655,95 @@ __device__ int jacobi2_fused(float2* G, float2* W, int l, int ls, float tol, int
 // the float32 rate.  The top k give W_k (left singular vectors of B),
 // S = diag(s) and V_k = B^H W_k S^{-1}.
 constexpr int EIG_THREADS = 256;
+constexpr int EIG_CHUNK = 32;   // rows of B^H staged per step of the Gram
 
 __global__ void __launch_bounds__(EIG_THREADS) core_eig_kernel(
     const float* __restrict__ bh_re, const float* __restrict__ bh_im, int p, int l, int k,
     int max_sweeps, float* __restrict__ wkr, float* __restrict__ wki, float* __restrict__ vkr,
     float* __restrict__ vki, float* __restrict__ sr_out, float* __restrict__ si_out,
-    int32_t* status) {
+    float2* __restrict__ pscratch, int32_t* status) {
   extern __shared__ double dyn[];
-  const int ls = l | 1;                                     // odd row stride
+  const int ls = l | 1;                                     // odd stride
   const int L2 = l * ls;
   double* sig2 = dyn;                                       // l: ||B^H w_j||^2
-  float2* Gf = reinterpret_cast<float2*>(dyn + ((l + 1) & ~1));   // l x l Gram
-  float2* Wf = Gf + L2;                                     // l x l eigenvectors
-  float4* rot = reinterpret_cast<float4*>(Wf + L2);        // per pair: c, s, er, ei
+  float2* Gf = reinterpret_cast<float2*>(dyn + ((l + 1) & ~1));   // l x l Gram (row stride ls)
+  float2* Wf = Gf + L2;                                     // l x l eigenvectors (column stride ls)
+  float4* rot = reinterpret_cast<float4*>(Wf + L2);         // per pair: c, s, er, ei
   int2* pq = reinterpret_cast<int2*>(rot + (l + 1) / 2);
   __shared__ int rotated;
   __shared__ int order[128];
   const int64_t f = blockIdx.x;
   const float* br = bh_re + f * int64_t(p) * l;
   const float* bi = bh_im + f * int64_t(p) * l;
-  for (int j = threadIdx.x; j < l; j += blockDim.x) sig2[j] = 0.0;
-  // G(a, b) = sum_r conj(B^H(r, a)) B^H(r, b), a <= b, Hermitian fill; W = I
+  float2* P = pscratch + f * int64_t(p) * l;                // B^H W (p x l), column-major
+  // G(a, b) = sum_r conj(B^H(r, a)) B^H(r, b), a <= b, Hermitian fill: rows of
+  // B^H staged EIG_CHUNK at a time (in W's space, before W is set)
+  float2* chunk = Wf;                                       // EIG_CHUNK x l, row stride l
   const int npairs = l * (l + 1) / 2;
-  for (int e = threadIdx.x; e < npairs; e += blockDim.x) {
-    int a = 0, rem = e;
-    while (rem >= l - a) { rem -= l - a; ++a; }
-    const int b = a + rem;
-    const float* xar = br + int64_t(a) * p;
-    const float* xai = bi + int64_t(a) * p;
-    const float* xbr = br + int64_t(b) * p;
-    const float* xbi = bi + int64_t(b) * p;
-    float gr = 0.f, gi = 0.f;
-    for (int r = 0; r < p; ++r) {
-      const float ur = __ldg(xar + r), ui = __ldg(xai + r), vr = __ldg(xbr + r),
-                  vi = __ldg(xbi + r);
-      gr = fmaf(ur, vr, fmaf(ui, vi, gr));
-      gi = fmaf(ur, vi, fmaf(-ui, vr, gi));
+  constexpr int PPT = 8;                                    // pairs per thread and pass
+  for (int base = 0; base < npairs; base += PPT * EIG_THREADS) {
+    int pa[PPT], pb[PPT];
+    float gr[PPT], gi[PPT];
+#pragma unroll
+    for (int u = 0; u < PPT; ++u) {
+      const int e = base + u * EIG_THREADS + threadIdx.x;
+      int a = 0, rem = e;
+      while (a < l && rem >= l - a) { rem -= l - a; ++a; }
+      pa[u] = e < npairs ? a : -1;
+      pb[u] = a + rem;
+      gr[u] = 0.f;
+      gi[u] = 0.f;
     }
-    Gf[a * ls + b] = make_float2(gr, gi);
-    Gf[b * ls + a] = make_float2(gr, -gi);
+    const int ch = min(EIG_CHUNK, ls);   // the chunk (ch x l) fits in W's l x ls
+    for (int r0 = 0; r0 < p; r0 += ch) {
+      const int nr = min(ch, p - r0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < nr * l; e += EIG_THREADS) {
+        const int c = e / nr, r = e - c * nr;
+        chunk[r * l + c] = make_float2(__ldg(br + r0 + r + int64_t(p) * c),
+                                       __ldg(bi + r0 + r + int64_t(p) * c));
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < PPT; ++u) {
+        if (pa[u] < 0) continue;
+        for (int r = 0; r < nr; ++r) {
+          const float2 x = chunk[r * l + pa[u]], y = chunk[r * l + pb[u]];
+          gr[u] = fmaf(x.x, y.x, fmaf(x.y, y.y, gr[u]));
+          gi[u] = fmaf(x.x, y.y, fmaf(-x.y, y.x, gi[u]));
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < PPT; ++u) {
+      if (pa[u] < 0) continue;
+      Gf[pa[u] * ls + pb[u]] = make_float2(gr[u], gi[u]);
+      Gf[pb[u] * ls + pa[u]] = make_float2(gr[u], -gi[u]);
+    }
   }
+  __syncthreads();
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
     const int i = e / l, j = e % l;
     Wf[i * ls + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
   }
+  for (int j = threadIdx.x; j < l; j += blockDim.x) sig2[j] = 0.0;
   const int s32 = jacobi2_fused(Gf, Wf, l, ls, 1e-6f, max_sweeps, rot, pq, &rotated);
   if (s32 >= max_sweeps && threadIdx.x == 0 && status) atomicOr(status, TP_DEV_NOCONV);
   __syncthreads();
-  // s_j^2 = ||B^H w_j||^2: one warp per column at a time, lanes over rows
+  // P = B^H W and s_j^2 = ||P(:, j)||^2: a warp per column, lanes over rows
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   for (int j = warp; j < l; j += nwarp) {
+    const float2* wj = Wf + j * ls;
     double acc = 0.0;
     for (int r = lane; r < p; r += 32) {
       float pr = 0.f, pim = 0.f;
       for (int m = 0; m < l; ++m) {
         const float bre = __ldg(br + r + int64_t(p) * m), bim = __ldg(bi + r + int64_t(p) * m);
-        const float2 w = Wf[m * ls + j];
+        const float2 w = wj[m];
         pr = fmaf(bre, w.x, fmaf(-bim, w.y, pr));
         pim = fmaf(bre, w.y, fmaf(bim, w.x, pim));
       }
+      P[r + int64_t(p) * j] = make_float2(pr, pim);
       acc += double(pr) * pr + double(pim) * pim;
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -725,7 +762,7 @@ __global__ void __launch_bounds__(EIG_THREADS) core_eig_kernel(
   __syncthreads();
   for (int e = threadIdx.x; e < l * k; e += blockDim.x) {
     const int i = e % l, c = e / l;
-    const float2 w = Wf[i * ls + order[c]];
+    const float2 w = Wf[order[c] * ls + i];
     wkr[f * l * k + e] = w.x;
     wki[f * l * k + e] = w.y;
   }
@@ -734,25 +771,16 @@ __global__ void __launch_bounds__(EIG_THREADS) core_eig_kernel(
     sr_out[f * k * k + e] = (i == c) ? float(sqrt(sig2[order[c]])) : 0.f;
     si_out[f * k * k + e] = 0.f;
   }
-  // V_k = B^H W_k S^{-1}
-  for (int64_t e = threadIdx.x; e < int64_t(p) * k; e += blockDim.x) {
-    const int r = int(e % p), c = int(e / p);
+  // V_k = B^H W_k S^{-1}: the columns of P in order, scaled
+  for (int c = warp; c < k; c += nwarp) {
     const int j = order[c];
     const double sg = sqrt(sig2[j]);
-    float vr = 0.f, vi = 0.f;
-    if (sg > 0.0) {
-      for (int m = 0; m < l; ++m) {
-        const float bre = __ldg(br + r + int64_t(p) * m), bim = __ldg(bi + r + int64_t(p) * m);
-        const float2 w = Wf[m * ls + j];
-        vr = fmaf(bre, w.x, fmaf(-bim, w.y, vr));
-        vi = fmaf(bre, w.y, fmaf(bim, w.x, vi));
-      }
-      const float inv = float(1.0 / sg);
-      vr *= inv;
-      vi *= inv;
+    const float inv = sg > 0.0 ? float(1.0 / sg) : 0.f;
+    for (int r = lane; r < p; r += 32) {
+      const float2 v = P[r + int64_t(p) * j];
+      vkr[f * int64_t(p) * k + r + int64_t(p) * c] = v.x * inv;
+      vki[f * int64_t(p) * k + r + int64_t(p) * c] = v.y * inv;
     }
-    vkr[f * int64_t(p) * k + e] = vr;
-    vki[f * int64_t(p) * k + e] = vi;
   }
 }
 
@@ -1075,7 +1103,8 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
     {
       KernelScope ks("core_eig", st);
       core_eig_kernel<<<unsigned(h), EIG_THREADS, eig_smem, st>>>(
-          Zr, Zi, int(n2), int(l), k, sweeps, Wkr, Wki, Vr, Vi, Sr, Si, status);
+          Zr, Zi, int(n2), int(l), k, sweeps, Wkr, Wki, Vr, Vi, Sr, Si,
+          reinterpret_cast<float2*>(Gr), status);
     }
     if ((rc = launch_status("core_eig_kernel"))) return rc;
   } else {
