@@ -539,7 +539,7 @@ def bench_rsvd(args, tp, torch, with_cpu, forms=("bf16x3", "fp32", "tf32x3")):
     ms = res[main]
     out = {"metric": "randomized t-SVD tensors/s", "value": 1e3 / ms, "unit": "tensors/s",
            "ms_per_tensor": ms, "steps": steps, "precision": main,
-           "dtype": "f32 data; products %s; f64-accurate CholeskyQR first pass" % main,
+           "dtype": "f32 data; products %s; f32 Householder QR" % main,
            "workload": "128x128x2000 MSI-shaped, tubal rank 15 + spikes + 0.5% noise, "
                        "k=40 p=10 q=2",
            "forms_ms": res,

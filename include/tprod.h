@@ -58,7 +58,7 @@ typedef enum {
 
 /* Device status bits OR-ed into opts->status. */
 #define TP_DEV_NOCONV     0x1  /* Jacobi sweeps reached opts->max_sweeps */
-#define TP_DEV_BREAKDOWN  0x2  /* CholeskyQR: Gram matrix not positive definite after shift */
+#define TP_DEV_BREAKDOWN  0x2  /* CholeskyQR (slices > 256 rows): Gram not positive definite after shift */
 #define TP_DEV_TIMEOUT    0x4  /* a pipeline wait inside a kernel gave up (results invalid) */
 
 typedef enum {
@@ -177,9 +177,9 @@ int tsvd(const float* X, int64_t n1, int64_t n2, int64_t n3,
  * ||X(:,j,:)||_F^2 / ||X||_F^2, Philox stream 2), each rescaled by
  * 1/sqrt((k+p) p_j), so that Y holds picked columns of X_hat;
  * q power iterations Q <- orth(X_hat^H Q), Q <- orth(X_hat Q), each orth a
- * CholeskyQR2 (first pass: float64-accurate Gram and float64 Cholesky;
- * second pass, on a Gram within u32 cond(Y) of the identity, in float32),
- * then B = Q^H X_hat, the SVD of B through its l x l Gram (float32
+ * float32 Householder QR in shared memory (slices of at most 256 rows; it
+ * cannot break down) or, for taller slices, CholeskyQR2 with a float64 Gram
+ * (shifted CholeskyQR3 on failure, then TP_DEV_BREAKDOWN), then B = Q^H X_hat, the SVD of B through its l x l Gram (float32
  * two-sided Jacobi, singular values as the Rayleigh quotients ||B^H w_j||
  * with float64 sums) and U = Q U_B truncated to k.
  *   opts->precision  TP_FP32: the products with X_hat on the CUDA cores;

@@ -6,11 +6,12 @@
 //   U_f = Q W[:, :k],  V_f = V_B[:, :k],  S_f = diag(s[:k])
 // followed by the inverse DFT of U, S, V (Theorem 2.6's form, tubal rank k).
 // The test matrix has random-sign entries from Philox stream 2 (see
-// tsvd_randomized in tprod.h).  orth() is CholeskyQR2 (Fukaya et al. 2014):
-// G = Y^H Y and its Cholesky factor R in float64, Y <- Y R^{-1}, twice; if a
-// Cholesky fails, the Gram matrix is shifted (shifted CholeskyQR, Fukaya et
-// al. 2020) and one more pass is made; a failure after that sets
-// TP_DEV_BREAKDOWN.  Every product with X_hat is a plain column-major batched
+// tsvd_randomized in tprod.h).  orth() is a float32 Householder QR in shared
+// memory for slices of at most 256 rows; taller slices take CholeskyQR2
+// (Fukaya et al. 2014): G = Y^H Y and its Cholesky factor R in float64,
+// Y <- Y R^{-1}, twice; if a Cholesky fails, the Gram matrix is shifted
+// (shifted CholeskyQR, Fukaya et al. 2020) and one more pass is made; a
+// failure after that sets TP_DEV_BREAKDOWN.  Every product with X_hat is a plain column-major batched
 // complex GEMM because X_hat^H is formed once.
 #include <cmath>
 
@@ -223,296 +224,165 @@ __global__ void __launch_bounds__(QR_THREADS) cholqr2_kernel(float* y_re, float*
   }
 }
 
-// ---------------------------------------------------------------- shared-memory forms
-// a*b added to the unevaluated float pair (hi, lo): the product's rounding
-// error comes from the FMA residual, the sum's from Knuth's two-sum, so the
-// pair carries about 44 significant bits at float32 speed.
-__device__ __forceinline__ void acc2(float& hi, float& lo, float a, float b) {
-  const float p = a * b;
-  const float e = fmaf(a, b, -p);
-  const float s = hi + p;
-  const float bb = s - hi;
-  const float err = (hi - (s - bb)) + (p - bb);
-  hi = s;
-  lo += err + e;
+// ---------------------------------------------------------------- Householder QR in shared memory
+// orth() of one slice's Y (p x l, p >= l, float32) held in shared memory:
+// the Householder QR Y = Q R with reflectors H_j = I - tau_j v_j v_j^H
+// (v_j(j) = 1, zero above) chosen as LAPACK's zlarfg chooses them, so that
+// H_j^H maps rows j.. of column j onto beta_j e_j with beta_j real; then
+// Q = H_0 H_1 ... H_{l-1} [I_l; 0] formed in place by backward accumulation.
+// Householder QR is backward stable whatever the conditioning of Y: Q is
+// orthonormal to float32 rounding in one pass and cannot break down, and it
+// spans the columns of Y (completed by the reflectors where Y is rank
+// deficient), which is all the range finder uses.  A step's reflector sits
+// in registers (lane r % 32 holds rows r); each warp applies it to its
+// columns k = j + 1 + warp (mod warps), and the owner of column j + 1 forms
+// the next reflector at once (look-ahead), so a step costs one barrier.
+constexpr int HQR_THREADS = 256;
+constexpr int HQR_WARPS = HQR_THREADS / 32;
+constexpr int HQR_MAX_L = 96;
+
+__device__ __forceinline__ float hqr_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
-// ---------------------------------------------------------------- float pairs
-// Unevaluated sums hi + lo of two floats (about 44 significant bits) on the
-// float32 pipe: GB300 runs float64 at 1/64 of the float32 rate, and the
-// first CholeskyQR pass needs a float64-class Gram and Cholesky.  Sums by
-// Knuth's two-sum, products by the FMA residual (Dekker's product).
-struct dfloat {
-  float hi, lo;
-};
-__device__ __forceinline__ dfloat df_quick(float a, float b) {   // |a| >= |b|
-  const float s = a + b;
-  return {s, b - (s - a)};
-}
-__device__ __forceinline__ dfloat df_add(dfloat x, dfloat y) {
-  const float s = x.hi + y.hi;
-  const float bb = s - x.hi;
-  const float e = (x.hi - (s - bb)) + (y.hi - bb) + x.lo + y.lo;
-  return df_quick(s, e);
-}
-__device__ __forceinline__ dfloat df_mul(dfloat x, dfloat y) {
-  const float p = x.hi * y.hi;
-  float e = fmaf(x.hi, y.hi, -p);
-  e = fmaf(x.hi, y.lo, e);
-  e = fmaf(x.lo, y.hi, e);
-  return df_quick(p, e);
-}
-__device__ __forceinline__ dfloat df_neg(dfloat x) { return {-x.hi, -x.lo}; }
-// sqrt(d) and 1/r by one Newton correction of the float32 estimate
-__device__ __forceinline__ dfloat df_sqrt(dfloat d) {
-  const float s = sqrtf(d.hi);
-  const float e = fmaf(-s, s, d.hi) + d.lo;
-  return df_quick(s, e / (2.f * s));
-}
-__device__ __forceinline__ dfloat df_recip(dfloat r) {
-  const float q = 1.f / r.hi;
-  const float e = fmaf(-r.hi, q, 1.f) - r.lo * q;
-  return df_quick(q, e * q);
+// Reflector of column a (rows j .. p-1), one warp: rows j+1.. become v,
+// row j becomes beta; returns tau (0 when the column is already beta e_j with
+// beta real).
+__device__ float2 hqr_reflector(float2* a, int j, int p, int lane) {
+  const float2 al = a[j];
+  float s = 0.f;
+  for (int r = j + 1 + lane; r < p; r += 32) {
+    const float2 x = a[r];
+    s = fmaf(x.x, x.x, fmaf(x.y, x.y, s));
+  }
+  s = hqr_sum(s);
+  if (s == 0.f && al.y == 0.f) return make_float2(0.f, 0.f);
+  const float nrm = sqrtf(fmaf(al.x, al.x, fmaf(al.y, al.y, s)));
+  const float beta = al.x >= 0.f ? -nrm : nrm;
+  // v = x / (alpha - beta); |alpha - beta| >= nrm > 0 by the sign of beta
+  const float dr = al.x - beta, di = al.y;
+  const float den = fmaf(dr, dr, di * di);
+  const float sr = dr / den, si = -di / den;
+  for (int r = j + 1 + lane; r < p; r += 32) {
+    const float2 x = a[r];
+    a[r] = make_float2(x.x * sr - x.y * si, x.x * si + x.y * sr);
+  }
+  __syncwarp();
+  if (lane == 0) a[j] = make_float2(beta, 0.f);
+  return make_float2((beta - al.x) / beta, -al.y / beta);
 }
 
-// G(a, b) = sum_r conj(Y(r, a)) Y(r, b) for a <= b (Hermitian fill) by the
-// compensated products and sums of acc2, as float pairs: G[a l + b] = (re hi,
-// re lo, im hi, im lo).  Y is in shared memory as float2 column-major p x l
-// with column stride ps (p + 1: the odd stride spreads the threads'
-// different columns over the banks).
-__device__ void gram_smem_df(const float2* __restrict__ Ys, int ps, int p, int l, float4* G) {
-  const int npairs = l * (l + 1) / 2;
-  for (int e = threadIdx.x; e < npairs; e += blockDim.x) {
-    int a = 0, rem = e;
-    while (rem >= l - a) { rem -= l - a; ++a; }
-    const int b = a + rem;
-    const float2* xa = Ys + a * ps;
-    const float2* xb = Ys + b * ps;
-    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-    for (int r = 0; r < p; ++r) {
-      const float2 u = xa[r], v = xb[r];
-      acc2(rh, rl, u.x, v.x);
-      acc2(rh, rl, u.y, v.y);
-      acc2(ih, il, u.x, v.y);
-      acc2(ih, il, -u.y, v.x);
-    }
-    const dfloat gr = df_quick(rh, rl), gi = df_quick(ih, il);
-    G[a * l + b] = make_float4(gr.hi, gr.lo, gi.hi, gi.lo);
-    G[b * l + a] = make_float4(gr.hi, gr.lo, -gi.hi, -gi.lo);
+// v_j of column a into registers: row r = lane + 32 t, 1 at row j, 0 above.
+template <int RPL>
+__device__ __forceinline__ void hqr_load_v(const float2* a, int j, int p, int lane,
+                                           float2 (&v)[RPL]) {
+#pragma unroll
+  for (int t = 0; t < RPL; ++t) {
+    const int r = lane + 32 * t;
+    v[t] = (r <= j || r >= p) ? make_float2(r == j ? 1.f : 0.f, 0.f) : a[r];
   }
 }
 
-// Right-looking Cholesky G = R^H R on the upper triangle of G in float pairs
-// (float4 per complex entry as gram_smem_df writes it).  Step j: every
-// thread forms r = sqrt(d_j) and 1/r from the pivot (float32 operations
-// only), scales its share of row j into R(j, .), and after a barrier the
-// trailing triangle takes G(i, k) -= conj(R(j, i)) R(j, k).  Returns false on
-// a non-positive pivot (block-uniform).
-__device__ bool cholesky_df(float4* G, int l, int* fail) {
-  for (int j = 0; j < l; ++j) {
-    __syncthreads();
-    const float4 dj = G[j * l + j];
-    const bool good = dj.x > 0.f && isfinite(dj.x);
-    if (!good && threadIdx.x == 0) *fail = 1;
-    const dfloat r = good ? df_sqrt({dj.x, dj.y}) : dfloat{1.f, 0.f};
-    const dfloat inv = df_recip(r);
-    for (int k = j + 1 + threadIdx.x; k < l; k += blockDim.x) {
-      const float4 g = G[j * l + k];
-      const dfloat a = df_mul({g.x, g.y}, inv), b = df_mul({g.z, g.w}, inv);
-      G[j * l + k] = make_float4(a.hi, a.lo, b.hi, b.lo);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) G[j * l + j] = make_float4(r.hi, r.lo, 0.f, 0.f);
-    const int m = l - j - 1;   // trailing size
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      const int i = j + 1 + e / m, k = j + 1 + e % m;
-      if (i > k) continue;
-      const float4 A = G[j * l + i], B = G[j * l + k];   // R(j, i), R(j, k)
-      const dfloat ar = {A.x, A.y}, ai = {A.z, A.w}, br = {B.x, B.y}, bi = {B.z, B.w};
-      const dfloat pr = df_add(df_mul(ar, br), df_mul(ai, bi));
-      const dfloat pi = df_add(df_mul(ar, bi), df_neg(df_mul(ai, br)));
-      const float4 g = G[i * l + k];
-      const dfloat nr = df_add({g.x, g.y}, df_neg(pr)), ni = df_add({g.z, g.w}, df_neg(pi));
-      G[i * l + k] = make_float4(nr.hi, nr.lo, ni.hi, ni.lo);
-    }
+// c <- c - f v (v^H c) on rows j .. p-1 (f = conj(tau) applies H^H, f = tau H)
+template <int RPL>
+__device__ __forceinline__ void hqr_apply(const float2 (&v)[RPL], float2* c, int j, int p,
+                                          float2 f, int lane) {
+  float2 x[RPL];
+  float dr = 0.f, di = 0.f;
+#pragma unroll
+  for (int t = 0; t < RPL; ++t) {
+    const int r = lane + 32 * t;
+    x[t] = (r >= j && r < p) ? c[r] : make_float2(0.f, 0.f);
+    dr = fmaf(v[t].x, x[t].x, fmaf(v[t].y, x[t].y, dr));    // Re(conj(v) x)
+    di = fmaf(v[t].x, x[t].y, fmaf(-v[t].y, x[t].x, di));   // Im(conj(v) x)
   }
-  __syncthreads();
-  return *fail == 0;
-}
-
-// Right-looking Cholesky G = R^H R on the upper triangle of G (interleaved
-// re/im, l x l, element type T: float64 for a general Gram, float32 for the
-// near-identity Gram of CholeskyQR2's second pass), one barrier per step:
-// step j reads the pivot d_j = G(j, j) and row j as the earlier steps left
-// them and updates the trailing triangle G(i, k) -= conj(G(j, i)) G(j, k) / d_j
-// (i.e. conj(R(j, i)) R(j, k) with R(j, .) = G(j, .) / sqrt(d_j)), which no
-// thread of the step reads; the rows are scaled into R after the last step.
-// Returns false on a non-positive pivot (block-uniform).
-template <class T>
-__device__ bool cholesky_rl(T* G, int l, int* fail) {
-  for (int j = 0; j < l; ++j) {
-    __syncthreads();
-    const T d = G[2 * (j * l + j)];
-    const bool good = d > T(0) && isfinite(d);
-    if (!good && threadIdx.x == 0) *fail = 1;
-    const T inv_d = good ? T(1) / d : T(1);
-    const int m = l - j - 1;   // trailing size
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      const int i = j + 1 + e / m, k = j + 1 + e % m;
-      if (i > k) continue;
-      const T ar = G[2 * (j * l + i)], ai = G[2 * (j * l + i) + 1];   // G(j, i)
-      const T br = G[2 * (j * l + k)], bi = G[2 * (j * l + k) + 1];   // G(j, k)
-      G[2 * (i * l + k)] -= (ar * br + ai * bi) * inv_d;
-      G[2 * (i * l + k) + 1] -= (ar * bi - ai * br) * inv_d;
-    }
-  }
-  __syncthreads();
-  // R(j, j) = sqrt(d_j), R(j, k) = G(j, k) / sqrt(d_j)
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
-    const int j = e / l, k = e % l;
-    if (k < j) continue;
-    const T d = G[2 * (j * l + j)];
-    const T r = (d > T(0) && isfinite(d)) ? sqrt(d) : T(1);
-    if (k > j) {
-      G[2 * e] /= r;
-      G[2 * e + 1] /= r;
-    }
-  }
-  __syncthreads();
-  for (int j = threadIdx.x; j < l; j += blockDim.x) {
-    const T d = G[2 * (j * l + j)];
-    G[2 * (j * l + j)] = (d > T(0) && isfinite(d)) ? sqrt(d) : T(1);
-    G[2 * (j * l + j) + 1] = T(0);
-  }
-  __syncthreads();
-  return *fail == 0;
-}
-
-// Plain float32 Gram G(a, b) = sum_r conj(Y(r, a)) Y(r, b) (Hermitian fill),
-// G float32 interleaved; for the second CholeskyQR pass, whose Y already has
-// orthonormal columns to about u32 cond(Y_0).
-__device__ void gram_smem_f32(const float2* __restrict__ Ys, int ps, int p, int l, float* G) {
-  const int npairs = l * (l + 1) / 2;
-  for (int e = threadIdx.x; e < npairs; e += blockDim.x) {
-    int a = 0, rem = e;
-    while (rem >= l - a) { rem -= l - a; ++a; }
-    const int b = a + rem;
-    const float2* xa = Ys + a * ps;
-    const float2* xb = Ys + b * ps;
-    float gr = 0.f, gi = 0.f;
-    for (int r = 0; r < p; ++r) {
-      const float2 u = xa[r], v = xb[r];
-      gr = fmaf(u.x, v.x, fmaf(u.y, v.y, gr));
-      gi = fmaf(u.x, v.y, fmaf(-u.y, v.x, gi));
-    }
-    G[2 * (a * l + b)] = gr;
-    G[2 * (a * l + b) + 1] = gi;
-    G[2 * (b * l + a)] = gr;
-    G[2 * (b * l + a) + 1] = -gi;
+  dr = hqr_sum(dr);
+  di = hqr_sum(di);
+  const float gr = f.x * dr - f.y * di, gi = f.x * di + f.y * dr;
+#pragma unroll
+  for (int t = 0; t < RPL; ++t) {
+    const int r = lane + 32 * t;
+    if (r >= j && r < p)
+      c[r] = make_float2(x[t].x - (v[t].x * gr - v[t].y * gi),
+                         x[t].y - (v[t].x * gi + v[t].y * gr));
   }
 }
 
-// CholeskyQR2 with Y held in shared memory.  First pass: compensated float32
-// Gram and Cholesky in float pairs (float64-class accuracy on the float32
-// pipe), float32 Y R^{-1}; its float32
-// product leaves Y with orthonormal columns to about u32 cond(Y), so the
-// second pass factors a Gram within u32 cond(Y) of the identity and runs in
-// float32 (Gram and Cholesky), restoring orthogonality to float32 accuracy.
-// Shifted retry as cholqr2_kernel (the passes after a shifted one stay in
-// float64 but the last).
-__global__ void __launch_bounds__(QR_THREADS) cholqr2_smem_kernel(float* y_re, float* y_im,
-                                                                  int64_t sY, int p, int l,
-                                                                  int32_t* status) {
-  extern __shared__ double dyn[];
-  double* G = dyn;                                          // 2 l^2 doubles
-  float2* Ri = reinterpret_cast<float2*>(G + 2 * l * l);    // l^2 float2
-  float2* Ys = Ri + l * l;                                  // (p + 1) l float2
-  const int ps = p + 1;
-  __shared__ int fail;
+// Column k of Q from its reflector (stored in place): H_k e_k restricted to
+// rows k.. -- 1 - tau at row k, -tau v below -- and zeros above.
+__device__ __forceinline__ void hqr_materialize(float2* a, int k, int p, float2 tau, int lane) {
+  for (int r = lane; r < p; r += 32) {
+    float2 y;
+    if (r < k) {
+      y = make_float2(0.f, 0.f);
+    } else if (r == k) {
+      y = make_float2(1.f - tau.x, -tau.y);
+    } else {
+      const float2 v = a[r];
+      y = make_float2(-(tau.x * v.x - tau.y * v.y), -(tau.x * v.y + tau.y * v.x));
+    }
+    a[r] = y;
+  }
+}
+
+// One CTA per slice; RPL rows per lane (p <= 32 RPL).
+template <int RPL>
+__global__ void __launch_bounds__(HQR_THREADS) householder_qr_kernel(float* y_re, float* y_im,
+                                                                     int64_t sY, int p, int l) {
+  extern __shared__ float2 hqr_a[];   // Y, then Q: p x l column-major
+  __shared__ float2 tau_s[HQR_MAX_L];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float* yr = y_re + int64_t(blockIdx.x) * sY;
   float* yi = y_im + int64_t(blockIdx.x) * sY;
-  for (int e = threadIdx.x; e < p * l; e += blockDim.x)
-    Ys[(e / p) * ps + e % p] = make_float2(yr[e], yi[e]);
+  float2* A = hqr_a;
+  for (int e = threadIdx.x; e < p * l; e += HQR_THREADS) A[e] = make_float2(yr[e], yi[e]);
   __syncthreads();
-  int passes_left = 2;
-  bool shifted = false;
-  bool prev_shifted = false;
-  bool ok_all = true;
-  for (int it = 0; it < 5 && passes_left > 0; ++it) {
-    if (threadIdx.x == 0) fail = 0;
-    const bool f32 = passes_left == 1 && !shifted && !prev_shifted && it > 0;
-    if (f32) {
-      float* Gs = reinterpret_cast<float*>(G);
-      gram_smem_f32(Ys, ps, p, l, Gs);
-      __syncthreads();
-      if (!cholesky_rl<float>(Gs, l, &fail)) {
-        // not expected after a successful float64 pass; redo it in float64
-        prev_shifted = true;
-        continue;
-      }
-      for (int e = threadIdx.x; e < l * l; e += blockDim.x)
-        Ri[e] = make_float2(Gs[2 * e], Gs[2 * e + 1]);
-    } else {
-      float4* Gd = reinterpret_cast<float4*>(G);
-      gram_smem_df(Ys, ps, p, l, Gd);
-      __syncthreads();
-      if (shifted) {
-        if (threadIdx.x == 0) {
-          double tr = 0.0;
-          for (int j = 0; j < l; ++j) tr += double(Gd[j * l + j].x) + double(Gd[j * l + j].y);
-          const double sft =
-              11.0 * (double(p) * l + double(l) * (l + 1)) * 1.1102230246251565e-16 * tr;
-          const float sh = float(sft), sl = float(sft - double(sh));
-          for (int j = 0; j < l; ++j) {
-            const float4 g = Gd[j * l + j];
-            const dfloat d = df_add({g.x, g.y}, {sh, sl});
-            Gd[j * l + j] = make_float4(d.hi, d.lo, g.z, g.w);
-          }
-        }
-        __syncthreads();
-      }
-      if (!cholesky_df(Gd, l, &fail)) {
-        if (shifted) {
-          ok_all = false;
-          break;
-        }
-        shifted = true;
-        passes_left = 3;
-        continue;
-      }
-      // R in float32 (its float64-class Gram and factorisation made the
-      // factor accurate; the product below needs only float32)
-      for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
-        const float4 g = Gd[e];
-        Ri[e] = make_float2(g.x + g.y, g.z + g.w);
-      }
-    }
-    // Y <- Y R^{-1} row by row by forward substitution x R = y, in place
-    __syncthreads();
-    for (int r = threadIdx.x; r < p; r += blockDim.x) {
-      for (int j = 0; j < l; ++j) {
-        float2 acc = Ys[j * ps + r];
-        for (int i = 0; i < j; ++i) {
-          const float2 x = Ys[i * ps + r];
-          const float2 w = Ri[i * l + j];
-          acc.x -= x.x * w.x - x.y * w.y;
-          acc.y -= x.x * w.y + x.y * w.x;
-        }
-        const float d = Ri[j * l + j].x;
-        Ys[j * ps + r] = make_float2(acc.x / d, acc.y / d);
-      }
-    }
-    __syncthreads();
-    prev_shifted = shifted;
-    shifted = false;
-    --passes_left;
+  if (warp == 0) {
+    const float2 t = hqr_reflector(A, 0, p, lane);
+    if (lane == 0) tau_s[0] = t;
   }
-  if (!ok_all && threadIdx.x == 0 && status) atomicOr(status, TP_DEV_BREAKDOWN);
   __syncthreads();
-  for (int e = threadIdx.x; e < p * l; e += blockDim.x) {
-    const float2 v = Ys[(e / p) * ps + e % p];
-    yr[e] = v.x;
-    yi[e] = v.y;
+  // factorisation: step j applies H_j^H to columns j+1 .. l-1
+  for (int j = 0; j + 1 < l; ++j) {
+    const float2 tau = tau_s[j];
+    float2 v[RPL];
+    hqr_load_v<RPL>(A + int64_t(j) * p, j, p, lane, v);
+    for (int k = j + 1 + warp; k < l; k += HQR_WARPS) {
+      float2* c = A + int64_t(k) * p;
+      if (tau.x != 0.f || tau.y != 0.f) hqr_apply<RPL>(v, c, j, p, make_float2(tau.x, -tau.y), lane);
+      if (k == j + 1) {   // look-ahead: column j + 1 is final, form its reflector
+        __syncwarp();
+        const float2 t = hqr_reflector(c, k, p, lane);
+        if (lane == 0) tau_s[k] = t;
+      }
+    }
+    __syncthreads();
+  }
+  // Q = H_0 ... H_{l-1} [I; 0]: step i applies H_i to columns i+1 .. l-1,
+  // whose first (column i + 1) its owner first turns from reflector storage
+  // into H_{i+1} e_{i+1}
+  for (int i = l - 2; i >= 0; --i) {
+    const float2 tau = tau_s[i];
+    float2 v[RPL];
+    hqr_load_v<RPL>(A + int64_t(i) * p, i, p, lane, v);
+    for (int k = i + 1 + warp; k < l; k += HQR_WARPS) {
+      float2* c = A + int64_t(k) * p;
+      if (k == i + 1) {
+        hqr_materialize(c, k, p, tau_s[k], lane);
+        __syncwarp();
+      }
+      if (tau.x != 0.f || tau.y != 0.f) hqr_apply<RPL>(v, c, i, p, tau, lane);
+    }
+    __syncthreads();
+  }
+  if (warp == 0) hqr_materialize(A, 0, p, tau_s[0], lane);
+  __syncthreads();
+  for (int e = threadIdx.x; e < p * l; e += HQR_THREADS) {
+    const float2 q = A[e];
+    yr[e] = q.x;
+    yi[e] = q.y;
   }
 }
 
@@ -1067,13 +937,25 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
   TP_SET_SMEM(cholqr2_kernel, qr_smem);
   constexpr size_t kSmemCap = 200 * 1024;
   auto orth = [&](float* yr, float* yi, int64_t rows) {
-    const size_t fast_smem = size_t(l) * l * (16 + 8) + size_t(rows + 1) * l * 8;
-    if (fast_smem <= kSmemCap) {
-      TP_SET_SMEM(cholqr2_smem_kernel, fast_smem);
-      KernelScope ks("cholqr2", st);
-      cholqr2_smem_kernel<<<unsigned(h), QR_THREADS, fast_smem, st>>>(yr, yi, rows * l, int(rows),
-                                                                     int(l), status);
-    } else {
+    if (rows <= 256 && l <= HQR_MAX_L) {
+      const size_t smem = size_t(rows) * l * sizeof(float2);
+      KernelScope ks("householder_qr", st);
+      if (rows <= 64) {
+        TP_SET_SMEM(householder_qr_kernel<2>, smem);
+        householder_qr_kernel<2><<<unsigned(h), HQR_THREADS, smem, st>>>(yr, yi, rows * l,
+                                                                         int(rows), int(l));
+      } else if (rows <= 128) {
+        TP_SET_SMEM(householder_qr_kernel<4>, smem);
+        householder_qr_kernel<4><<<unsigned(h), HQR_THREADS, smem, st>>>(yr, yi, rows * l,
+                                                                         int(rows), int(l));
+      } else {
+        TP_SET_SMEM(householder_qr_kernel<8>, smem);
+        householder_qr_kernel<8><<<unsigned(h), HQR_THREADS, smem, st>>>(yr, yi, rows * l,
+                                                                         int(rows), int(l));
+      }
+      return launch_status("householder_qr_kernel");
+    }
+    {
       KernelScope ks("cholqr2", st);
       cholqr2_kernel<<<unsigned(h), QR_THREADS, qr_smem, st>>>(yr, yi, rows * l, int(rows),
                                                                int(l), status);

@@ -48,7 +48,9 @@ def run_both(X, k, p, q, seed, precision=tp.TP_FP32):
 
 @pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("n1,n2,n3,r,k,p,q", [(40, 30, 6, 3, 4, 3, 1), (30, 40, 7, 2, 3, 2, 0),
-                                              (64, 48, 16, 5, 6, 4, 2), (20, 20, 1, 4, 5, 5, 1)])
+                                              (64, 48, 16, 5, 6, 4, 2), (20, 20, 1, 4, 5, 5, 1),
+                                              # more than 256 rows: CholeskyQR2 in global memory
+                                              (300, 40, 4, 3, 4, 3, 1), (40, 300, 5, 3, 4, 4, 1)])
 def test_exact_low_rank_is_recovered(n1, n2, n3, r, k, p, q, precision):
     X = synth.lowrank_np(n1, n2, n3, r, seed=7)
     (U, S, V), (Ur, Sr, Vr) = run_both(X, k, p, q, seed=3, precision=precision)
@@ -109,14 +111,34 @@ def test_msi_workload_full_size(msi_oracle, precision):
 
 
 def test_breakdown_is_flagged_not_hung():
-    """An all-zero tensor makes every Gram matrix zero: CholeskyQR fails
-    even after the shift and must raise the device breakdown bit."""
+    """Slices of more than 256 rows are orthonormalised by CholeskyQR2 in
+    global memory.  An all-zero tensor makes every Gram matrix zero: the
+    Cholesky fails even after the shift and must raise the device breakdown
+    bit."""
     import torch
-    X = np.zeros((12, 10, 4), dtype=np.float32)
+    X = np.zeros((300, 10, 4), dtype=np.float32)
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     tp.tsvd_randomized(dev(X), 3, 2, 1, seed=0, status=st)
     torch.cuda.synchronize()
     assert int(st.item()) & 0x2
+
+
+def test_zero_tensor_householder_path():
+    """The shared-memory Householder QR cannot break down: an all-zero tensor
+    gives zero singular values, orthonormal U (the reflectors are all the
+    identity, so Q is the first columns of I) and no status bit."""
+    import torch
+    X = np.zeros((12, 10, 4), dtype=np.float32)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    U, S, V = tp.tsvd_randomized(dev(X), 3, 2, 1, seed=0, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    U, S, V = to_np(U), to_np(S), to_np(V)
+    assert np.all(np.isfinite(U)) and np.all(np.isfinite(V))
+    assert np.all(S == 0) and np.all(V == 0)
+    Uh = tensor_ref.half_spectrum(tensor_ref.fft3(U))
+    for f in range(Uh.shape[2]):
+        assert np.abs(Uh[:, :, f].conj().T @ Uh[:, :, f] - np.eye(3)).max() < 1e-6
 
 
 def test_per_frequency_ranks_match_oracle():
