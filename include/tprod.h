@@ -190,12 +190,19 @@ int tsvd(const float* X, int64_t n1, int64_t n2, int64_t n3,
  *                  multi-rank of Section 2): half-spectrum slice f keeps its
  *                  top min(max(r_f, 0), k) triplets and zeroes the rest (its
  *                  conjugate slice alike); NULL keeps k everywhere.
+ *   sketch_per_freq device int32[n3/2 + 1] or NULL: per-frequency sketch
+ *                  sizes: slice f sketches with the first
+ *                  l_f = min(max(s_f, 1), k + p) columns of the test matrix
+ *                  (its range finder, power iterations and core SVD work on
+ *                  l_f columns) and keeps at most min(k, l_f) triplets; NULL
+ *                  uses k + p everywhere.  The products run over k + p
+ *                  columns for every slice (the others held at zero).
  *   U  n1 x k x n3,  S  k x k x n3,  V  n2 x k x n3 (outputs).
  * Requires 1 <= k, p >= 0, q >= 0, k + p <= min(n1, n2, 96); n3 <= 512 or
  * n3 a product of the radices 2, 3, 5, 7, 11, 13.                           */
 int tsvd_randomized(const float* X, int64_t n1, int64_t n2, int64_t n3,
                     int k, int p, int q, uint64_t seed, int sketch_mode,
-                    const int32_t* rank_per_freq,
+                    const int32_t* rank_per_freq, const int32_t* sketch_per_freq,
                     float* U, float* S, float* V, const tp_opts* opts, void* stream);
 
 /* tcx: t-CX of Algorithm 4 with the t-project of Algorithm 3.  Lateral

@@ -82,10 +82,15 @@ def _orth(Y: np.ndarray) -> np.ndarray:
     return Q
 
 
-def tsvd_randomized_hat(X: np.ndarray, k: int, p: int, q: int, Omega: np.ndarray):
+def tsvd_randomized_hat(X: np.ndarray, k: int, p: int, q: int, Omega: np.ndarray,
+                        sketch_sizes=None):
     """Per half-spectrum slice: Y = X_hat Omega; q power iterations
     Q <- orth(X_hat^H Q), Q <- orth(X_hat Q); B = Q^H X_hat; SVD of B; keep k.
-    Omega is n2 x (k+p) x h.  Returns (Uh n1 x k x h, s k x h, Vh n2 x k x h)."""
+    Omega is n2 x (k+p) x h.  sketch_sizes (h integers, the per-frequency
+    sketch sizes of the multi-rank form of Section 2): slice f sketches with
+    the first l_f = min(max(size_f, 1), k + p) columns of Omega and keeps its
+    top min(k, l_f) triplets (the rest zero).  Returns (Uh n1 x k x h,
+    s k x h, Vh n2 x k x h)."""
     n1, n2, n3 = X.shape
     h = n3 // 2 + 1
     ell = k + p
@@ -95,18 +100,20 @@ def tsvd_randomized_hat(X: np.ndarray, k: int, p: int, q: int, Omega: np.ndarray
     Vh = np.zeros((n2, k, h), dtype=np.complex128)
     s = np.zeros((k, h))
     for f in range(h):
+        lf = ell if sketch_sizes is None else min(max(int(sketch_sizes[f]), 1), ell)
+        kf = min(k, lf)
         M = Xh[:, :, f]
         if _real_slice(f, n3):
             M = M.real.astype(np.complex128)
-        Q = _orth(M @ Omega[:, :, f])
+        Q = _orth(M @ Omega[:, :lf, f])
         for _ in range(q):
             Q = _orth(np.conj(M).T @ Q)
             Q = _orth(M @ Q)
         Bm = np.conj(Q).T @ M
         ub, sb, vbt = scipy.linalg.svd(Bm, full_matrices=False, lapack_driver="gesvd")
-        Uh[:, :, f] = (Q @ ub)[:, :k]
-        s[:, f] = sb[:k]
-        Vh[:, :, f] = np.conj(vbt).T[:, :k]
+        Uh[:, :kf, f] = (Q @ ub)[:, :kf]
+        s[:kf, f] = sb[:kf]
+        Vh[:, :kf, f] = np.conj(vbt).T[:, :kf]
     return Uh, s, Vh
 
 
@@ -128,12 +135,14 @@ def slice_sketch(X: np.ndarray, ell: int, seed: int) -> np.ndarray:
     return Om
 
 
-def tsvd_randomized(X: np.ndarray, k: int, p: int, q: int, Omega: np.ndarray, ranks=None):
+def tsvd_randomized(X: np.ndarray, k: int, p: int, q: int, Omega: np.ndarray, ranks=None,
+                    sketch_sizes=None):
     """Randomized tubal-rank-k t-SVD; same output form as ``tsvd`` with m = k.
     ranks (h integers): half-spectrum slice f keeps only its top
-    min(max(r_f, 0), k) triplets (the multi-rank of Section 2)."""
+    min(max(r_f, 0), k) triplets (the multi-rank of Section 2);
+    sketch_sizes: per-frequency sketch sizes (see tsvd_randomized_hat)."""
     n3 = X.shape[2]
-    Uh, s, Vh = tsvd_randomized_hat(X, k, p, q, Omega)
+    Uh, s, Vh = tsvd_randomized_hat(X, k, p, q, Omega, sketch_sizes)
     if ranks is not None:
         for f in range(s.shape[1]):
             r = min(max(int(ranks[f]), 0), k)

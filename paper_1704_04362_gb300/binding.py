@@ -66,7 +66,7 @@ _SIGS = {
                                _c_int, _c_int, _vp, _vp, _vp, _vp, _vp]),
     "tsvd": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _vp, _vp, _vp, _vp, _vp]),
     "tsvd_randomized": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_int, _c_int, _c_int, _c_u64,
-                                 _c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
+                                 _c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "tcomplete_svt": (_c_int, [_vp, _vp, _c_i64, _c_i64, _c_i64, _c_int, _dbl, _dbl,
                                _vp, _vp, _vp, _vp, _vp, _vp]),
     "tcx": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_i64, _c_u64, _c_int, _vp, _vp, _vp, _vp,
@@ -384,25 +384,31 @@ def tsvd(X, max_sweeps=0, status=None):
 
 
 def tsvd_randomized(X, k, p=10, q=2, seed=0, status=None, max_sweeps=0, ranks=None,
-                    sketch=0, precision=TP_FP32):
+                    sketch=0, precision=TP_FP32, sketch_sizes=None):
     """Randomized tubal-rank-k t-SVD: returns (U, S, V).  ranks: optional
-    device int32[n3 // 2 + 1] per-frequency ranks (each at most k); sketch:
-    TP_SKETCH_SIGNS (0) or TP_SKETCH_SLICES (1, picked lateral slices);
-    precision: TP_FP32 (products on the CUDA cores) or TP_TF32X3 / TP_BF16X3
-    (the products with X_hat on the tensor cores, split operands)."""
+    device int32[n3 // 2 + 1] per-frequency ranks (each at most k);
+    sketch_sizes: optional device int32[n3 // 2 + 1] per-frequency sketch
+    sizes (each at most k + p); sketch: TP_SKETCH_SIGNS (0) or
+    TP_SKETCH_SLICES (1, picked lateral slices); precision: TP_FP32 (products
+    on the CUDA cores) or TP_TF32X3 / TP_BF16X3 (the products with X_hat on
+    the tensor cores, split operands)."""
     torch = _torch()
     n1, n2, n3 = X.shape
-    rk = None
+    rk = sz = None
     if ranks is not None:
         if ranks.numel() != n3 // 2 + 1:
             raise TprodError("tsvd_randomized: ranks needs n3 // 2 + 1 entries")
         rk = _tensor_arg(ranks, "ranks", torch.int32)
+    if sketch_sizes is not None:
+        if sketch_sizes.numel() != n3 // 2 + 1:
+            raise TprodError("tsvd_randomized: sketch_sizes needs n3 // 2 + 1 entries")
+        sz = _tensor_arg(sketch_sizes, "sketch_sizes", torch.int32)
     U = empty_tensor(n1, k, n3, device=X.device)
     S = empty_tensor(k, k, n3, device=X.device)
     V = empty_tensor(n2, k, n3, device=X.device)
     o = _opts(TP_OP_TSVD_RANDOMIZED, (n1, n2, n3, k, p), precision, status, max_sweeps)
     rc = lib().tsvd_randomized(_tensor_arg(X, "X"), n1, n2, n3, int(k), int(p), int(q),
-                               int(seed) & ((1 << 64) - 1), int(sketch), rk,
+                               int(seed) & ((1 << 64) - 1), int(sketch), rk, sz,
                                _tensor_arg(U, "U"),
                                _tensor_arg(S, "S"), _tensor_arg(V, "V"), ctypes.byref(o),
                                _stream())

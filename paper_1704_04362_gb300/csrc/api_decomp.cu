@@ -33,7 +33,8 @@ int cur_tnn_run(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int
                 double* row_prob, const tp_opts* opts, cudaStream_t st);
 int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, int q,
              uint64_t seed, float* U, float* S, float* V, const tp_opts* opts, cudaStream_t st,
-             float* sig_out, const int32_t* rank_per_freq, int sketch_mode);
+             float* sig_out, const int32_t* rank_per_freq, int sketch_mode,
+             const int32_t* sketch_per_freq = nullptr);
 int tsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, float* U, float* S, float* V,
              const tp_opts* opts, cudaStream_t st);
 
@@ -80,8 +81,9 @@ int tsvd(const float* X, int64_t n1, int64_t n2, int64_t n3, float* U, float* S,
   return tsvd_run(X, n1, n2, n3, U, S, V, opts, as_stream(stream));
 }
 int tsvd_randomized(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, int q,
-                    uint64_t seed, int sketch_mode, const int32_t* rank_per_freq, float* U,
-                    float* S, float* V, const tp_opts* opts, void* stream) {
+                    uint64_t seed, int sketch_mode, const int32_t* rank_per_freq,
+                    const int32_t* sketch_per_freq, float* U, float* S, float* V,
+                    const tp_opts* opts, void* stream) {
   if (!X || !U || !S || !V) { set_error("tsvd_randomized: NULL pointer"); return TP_ENULL; }
   if (!dims3_ok(n1, n2, n3)) { set_error("tsvd_randomized: invalid sizes"); return TP_EINVAL; }
   const int64_t m = n1 < n2 ? n1 : n2;
@@ -98,7 +100,7 @@ int tsvd_randomized(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, i
     return TP_EINVAL;
   }
   return rsvd_run(X, n1, n2, n3, k, p, q, seed, U, S, V, opts, as_stream(stream), nullptr,
-                  rank_per_freq, sketch_mode);
+                  rank_per_freq, sketch_mode, sketch_per_freq);
 }
 int tcomplete_svt(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t n3,
                   int iters, double rho, double mu_max, float* L, float* E, float* Y, double* mu,

@@ -6,7 +6,8 @@
 namespace tp {
 int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, int q,
              uint64_t seed, float* U, float* S, float* V, const tp_opts* opts, cudaStream_t st,
-             float* sig_out, const int32_t* rank_per_freq, int sketch_mode);
+             float* sig_out, const int32_t* rank_per_freq, int sketch_mode,
+             const int32_t* sketch_per_freq = nullptr);
 size_t rsvd_ws(int64_t n1, int64_t n2, int64_t n3, int64_t k, int64_t p, int prec = TP_FP32);
 bool fft_supported(int64_t n3);
 size_t mlp_partial_count(int64_t B);

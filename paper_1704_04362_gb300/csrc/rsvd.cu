@@ -13,10 +13,10 @@
 // (shifted CholeskyQR, Fukaya et al. 2020) and one more pass is made; a
 // failure after that sets TP_DEV_BREAKDOWN.  Every product with X_hat is a plain column-major batched
 // complex GEMM because X_hat^H is formed once.
+#include <cfloat>
 #include <cmath>
 
 #include "dft_common.cuh"
-#include "jacobi_rot.cuh"
 #include "philox.cuh"
 
 namespace tp {
@@ -185,11 +185,20 @@ __device__ void right_solve(float* yr, float* yi, int p, int l, const double* R)
 
 // CholeskyQR2 (with a shifted retry) of every slice's p x l block.
 __global__ void __launch_bounds__(QR_THREADS) cholqr2_kernel(float* y_re, float* y_im, int64_t sY,
-                                                             int p, int l, int32_t* status) {
+                                                             int p, int lfull,
+                                                             const int32_t* lcols,
+                                                             int32_t* status) {
   extern __shared__ double G[];   // 2 * l * l
   __shared__ int fail;
+  // per-slice column count (the per-frequency sketch size): the columns from
+  // l on are set to zero
+  const int l = lcols ? min(max(int(lcols[blockIdx.x]), 1), lfull) : lfull;
   float* yr = y_re + int64_t(blockIdx.x) * sY;
   float* yi = y_im + int64_t(blockIdx.x) * sY;
+  for (int64_t e = int64_t(p) * l + threadIdx.x; e < int64_t(p) * lfull; e += blockDim.x) {
+    yr[e] = 0.f;
+    yi[e] = 0.f;
+  }
   int passes_left = 2;
   bool shifted = false;
   for (int it = 0; it < 4 && passes_left > 0; ++it) {
@@ -310,6 +319,41 @@ __device__ __forceinline__ void hqr_apply(const float2 (&v)[RPL], float2* c, int
   }
 }
 
+// hqr_apply on two columns at once (their sums interleave in the shuffles)
+template <int RPL>
+__device__ __forceinline__ void hqr_apply2(const float2 (&v)[RPL], float2* c0, float2* c1, int j,
+                                           int p, float2 f, int lane) {
+  float2 x0[RPL], x1[RPL];
+  float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int t = 0; t < RPL; ++t) {
+    const int r = lane + 32 * t;
+    const bool in = r >= j && r < p;
+    x0[t] = in ? c0[r] : make_float2(0.f, 0.f);
+    x1[t] = in ? c1[r] : make_float2(0.f, 0.f);
+    d[0] = fmaf(v[t].x, x0[t].x, fmaf(v[t].y, x0[t].y, d[0]));
+    d[1] = fmaf(v[t].x, x0[t].y, fmaf(-v[t].y, x0[t].x, d[1]));
+    d[2] = fmaf(v[t].x, x1[t].x, fmaf(v[t].y, x1[t].y, d[2]));
+    d[3] = fmaf(v[t].x, x1[t].y, fmaf(-v[t].y, x1[t].x, d[3]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) d[u] += __shfl_xor_sync(0xffffffffu, d[u], o);
+  const float g0r = f.x * d[0] - f.y * d[1], g0i = f.x * d[1] + f.y * d[0];
+  const float g1r = f.x * d[2] - f.y * d[3], g1i = f.x * d[3] + f.y * d[2];
+#pragma unroll
+  for (int t = 0; t < RPL; ++t) {
+    const int r = lane + 32 * t;
+    if (r >= j && r < p) {
+      c0[r] = make_float2(x0[t].x - (v[t].x * g0r - v[t].y * g0i),
+                          x0[t].y - (v[t].x * g0i + v[t].y * g0r));
+      c1[r] = make_float2(x1[t].x - (v[t].x * g1r - v[t].y * g1i),
+                          x1[t].y - (v[t].x * g1i + v[t].y * g1r));
+    }
+  }
+}
+
 // Column k of Q from its reflector (stored in place): H_k e_k restricted to
 // rows k.. -- 1 - tau at row k, -tau v below -- and zeros above.
 __device__ __forceinline__ void hqr_materialize(float2* a, int k, int p, float2 tau, int lane) {
@@ -330,10 +374,14 @@ __device__ __forceinline__ void hqr_materialize(float2* a, int k, int p, float2 
 // One CTA per slice; RPL rows per lane (p <= 32 RPL).
 template <int RPL>
 __global__ void __launch_bounds__(HQR_THREADS) householder_qr_kernel(float* y_re, float* y_im,
-                                                                     int64_t sY, int p, int l) {
+                                                                     int64_t sY, int p, int lfull,
+                                                                     const int32_t* lcols) {
   extern __shared__ float2 hqr_a[];   // Y, then Q: p x l column-major
   __shared__ float2 tau_s[HQR_MAX_L];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // per-slice column count (the per-frequency sketch size): the columns from
+  // l on are left zero
+  const int l = lcols ? min(max(int(lcols[blockIdx.x]), 1), lfull) : lfull;
   float* yr = y_re + int64_t(blockIdx.x) * sY;
   float* yi = y_im + int64_t(blockIdx.x) * sY;
   float2* A = hqr_a;
@@ -349,14 +397,21 @@ __global__ void __launch_bounds__(HQR_THREADS) householder_qr_kernel(float* y_re
     const float2 tau = tau_s[j];
     float2 v[RPL];
     hqr_load_v<RPL>(A + int64_t(j) * p, j, p, lane, v);
-    for (int k = j + 1 + warp; k < l; k += HQR_WARPS) {
+    const bool live = tau.x != 0.f || tau.y != 0.f;
+    const float2 f = make_float2(tau.x, -tau.y);
+    int k = j + 1 + warp;
+    if (warp == 0) {   // look-ahead: column j + 1 first, then its reflector
       float2* c = A + int64_t(k) * p;
-      if (tau.x != 0.f || tau.y != 0.f) hqr_apply<RPL>(v, c, j, p, make_float2(tau.x, -tau.y), lane);
-      if (k == j + 1) {   // look-ahead: column j + 1 is final, form its reflector
-        __syncwarp();
-        const float2 t = hqr_reflector(c, k, p, lane);
-        if (lane == 0) tau_s[k] = t;
-      }
+      if (live) hqr_apply<RPL>(v, c, j, p, f, lane);
+      __syncwarp();
+      const float2 t = hqr_reflector(c, k, p, lane);
+      if (lane == 0) tau_s[k] = t;
+      k += HQR_WARPS;
+    }
+    if (live) {
+      for (; k + HQR_WARPS < l; k += 2 * HQR_WARPS)
+        hqr_apply2<RPL>(v, A + int64_t(k) * p, A + int64_t(k + HQR_WARPS) * p, j, p, f, lane);
+      if (k < l) hqr_apply<RPL>(v, A + int64_t(k) * p, j, p, f, lane);
     }
     __syncthreads();
   }
@@ -367,13 +422,15 @@ __global__ void __launch_bounds__(HQR_THREADS) householder_qr_kernel(float* y_re
     const float2 tau = tau_s[i];
     float2 v[RPL];
     hqr_load_v<RPL>(A + int64_t(i) * p, i, p, lane, v);
-    for (int k = i + 1 + warp; k < l; k += HQR_WARPS) {
-      float2* c = A + int64_t(k) * p;
-      if (k == i + 1) {
-        hqr_materialize(c, k, p, tau_s[k], lane);
-        __syncwarp();
-      }
-      if (tau.x != 0.f || tau.y != 0.f) hqr_apply<RPL>(v, c, i, p, tau, lane);
+    int k = i + 1 + warp;
+    if (warp == 0) {
+      hqr_materialize(A + int64_t(k) * p, k, p, tau_s[k], lane);
+      __syncwarp();
+    }
+    if (tau.x != 0.f || tau.y != 0.f) {
+      for (; k + HQR_WARPS < l; k += 2 * HQR_WARPS)
+        hqr_apply2<RPL>(v, A + int64_t(k) * p, A + int64_t(k + HQR_WARPS) * p, i, p, tau, lane);
+      if (k < l) hqr_apply<RPL>(v, A + int64_t(k) * p, i, p, tau, lane);
     }
     __syncthreads();
   }
@@ -384,146 +441,300 @@ __global__ void __launch_bounds__(HQR_THREADS) householder_qr_kernel(float* y_re
     yr[e] = q.x;
     yi[e] = q.y;
   }
+  for (int e = p * l + threadIdx.x; e < p * lfull; e += HQR_THREADS) {
+    yr[e] = 0.f;
+    yi[e] = 0.f;
+  }
 }
 
-// Two-sided Jacobi on the Hermitian l x l matrix G (row stride ls) with the
-// rotations accumulated into W (W <- W K; W column-major, column stride ls),
-// float32.  Each step takes the
-// ll/2 disjoint round-robin pairs: first every pair's rotation from the
-// current G, then one pass that updates every 2 x 2 block (rows of pair i,
-// columns of pair j) with both rotations at once (K_i^H G K_j restricted to
-// the block; disjoint blocks, so no ordering within the pass) and W's
-// columns.  A pair is rotated while |G(a,b)| > tol sqrt(G(a,a) G(b,b)) (a
-// relative test: G is graded -- its diagonal spans the squared singular
-// values -- and a floor on the scale of the largest entry of G would leave
-// the small ones unresolved) and while |G(a,b)| exceeds the rounding floor of
-// the pair itself, a few ulp of max(G(a,a), G(b,b)).  Returns the number of sweeps that
-// rotated (stops after a quiet sweep or at max_sweeps).
-__device__ int jacobi2_fused(float2* G, float2* W, int l, int ls, float tol, int max_sweeps,
-                             float4* rot, int2* pq, int* rotated) {
-  const int ll = l + (l & 1), npairs = ll / 2;
-  int sweep = 0;
-  for (; sweep < max_sweeps; ++sweep) {
+// ---------------------------------------------------------------- core eigensolver
+__device__ __forceinline__ float eig_warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Householder reduction of the Hermitian l x l matrix G (row stride ls, both
+// triangles held) to a real symmetric tridiagonal T = Q^H G Q with
+// Q = H_0 H_1 ... H_{l-2}.  Step j takes the reflector H_j = I - tau_j v v^H
+// of column j below the diagonal (chosen as LAPACK's zlarfg chooses it, so
+// that the new off-diagonal beta_j is real; the last step, on a single
+// entry, only makes the last off-diagonal real) and applies H_j^H . H_j to
+// the trailing block as the rank-2 change A - v w^H - w v^H with y = tau A v
+// and w = y - (1/2) tau (y^H v) v.  On exit d and e hold T's diagonal and
+// off-diagonal; v_j (after its leading 1) sits in row j of G right of
+// column j + 1, tau_j in tau.
+__device__ void hermitian_tridiag(float2* G, int l, int ls, float* d, float* e, float2* tau,
+                                  float2* vbuf, float2* ybuf) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int j = 0; j + 1 < l; ++j) {
+    const int m = l - 1 - j;
+    float2* row = G + j * ls + j + 1;   // conj of column j below the diagonal
+    if (warp == 0) {
+      float s = 0.f;
+      for (int t = 1 + lane; t < m; t += 32) {
+        const float2 x = row[t];
+        s = fmaf(x.x, x.x, fmaf(x.y, x.y, s));
+      }
+      s = eig_warp_sum(s);
+      const float2 al = make_float2(row[0].x, -row[0].y);
+      float2 tj = make_float2(0.f, 0.f);
+      float beta = al.x;
+      float sr = 0.f, si = 0.f;   // 1 / (alpha - beta), 0 when H_j = I
+      if (!(s == 0.f && al.y == 0.f)) {
+        const float nrm = sqrtf(fmaf(al.x, al.x, fmaf(al.y, al.y, s)));
+        beta = al.x >= 0.f ? -nrm : nrm;
+        tj = make_float2((beta - al.x) / beta, -al.y / beta);
+        const float dr = al.x - beta, di = al.y, den = fmaf(dr, dr, di * di);
+        sr = dr / den;
+        si = -di / den;
+      }
+      for (int t = 1 + lane; t < m; t += 32) {
+        const float2 x = make_float2(row[t].x, -row[t].y);
+        const float2 v = make_float2(x.x * sr - x.y * si, x.x * si + x.y * sr);
+        row[t] = v;
+        vbuf[t] = v;
+      }
+      if (lane == 0) {
+        vbuf[0] = make_float2(1.f, 0.f);
+        tau[j] = tj;
+        e[j] = beta;
+      }
+    }
     __syncthreads();
-    if (threadIdx.x == 0) *rotated = 0;
-    for (int step = 0; step < ll - 1; ++step) {
-      __syncthreads();
-      for (int i = threadIdx.x; i < npairs; i += blockDim.x) {
-        int a, b;
-        if (i == 0) { a = ll - 1; b = step; }
-        else { a = (step + i) % (ll - 1); b = (step - i + (ll - 1)) % (ll - 1); }
-        if (a > b) { const int t = a; a = b; b = t; }
-        pq[i] = make_int2(a, b);
-        float cs = 1.f, sn = 0.f, er = 1.f, ei = 0.f;
-        if (b < l) {
-          const float al = G[a * ls + a].x, be = G[b * ls + b].x;
-          const float2 ga = G[a * ls + b];
-          const float g2 = ga.x * ga.x + ga.y * ga.y;
-          // float32 rounding leaves |G(a,b)| at a few ulp of the larger
-          // diagonal term: pairs below that cannot be resolved further
-          const float fl = 5e-7f * fmaxf(fabsf(al), fabsf(be));
-          if (g2 > tol * tol * fabsf(al * be) && g2 > fl * fl && g2 > 0.f) {
-            jrot::rotation(al, be, ga.x, ga.y, g2, cs, sn, er, ei);   // er, ei: e^{-i phi}
-            *rotated = 1;
+    const float2 tj = tau[j];
+    if (tj.x != 0.f || tj.y != 0.f) {   // block-uniform
+      // y = tau A v over the trailing block A = G(j+1:, j+1:), four threads a row
+      for (int base = 0; base < m; base += int(blockDim.x) >> 2) {
+        const int i = base + (tid >> 2), part = tid & 3;
+        float ar = 0.f, ai = 0.f;
+        if (i < m) {
+          const float2* Ai = G + (j + 1 + i) * ls + (j + 1);
+          for (int t = part; t < m; t += 4) {
+            const float2 a = Ai[t], v = vbuf[t];
+            ar = fmaf(a.x, v.x, fmaf(-a.y, v.y, ar));
+            ai = fmaf(a.x, v.y, fmaf(a.y, v.x, ai));
           }
         }
-        rot[i] = make_float4(cs, sn, er, ei);
+        ar += __shfl_xor_sync(0xffffffffu, ar, 1);
+        ai += __shfl_xor_sync(0xffffffffu, ai, 1);
+        ar += __shfl_xor_sync(0xffffffffu, ar, 2);
+        ai += __shfl_xor_sync(0xffffffffu, ai, 2);
+        if (i < m && part == 0)
+          ybuf[i] = make_float2(tj.x * ar - tj.y * ai, tj.x * ai + tj.y * ar);
       }
       __syncthreads();
-      // G blocks: new rows (a, b) = [c x_a - s e^{i phi} x_b, s x_a + c e^{i phi} x_b]
-      // of pair i, then new columns (a, b) = [c y_a - s e^{-i phi} y_b,
-      // s y_a + c e^{-i phi} y_b] of pair j (a warp per block row i, its lanes
-      // over j); W (column-major) takes the column rotation only (a warp per
-      // pair, its lanes along the two columns)
-      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-      for (int i = warp; i < npairs; i += nw) {
-        const int2 ri = pq[i];
-        const float4 Ri = rot[i];
-        const bool ip = ri.y < l;
-        for (int j = i + lane; j < npairs; j += 32) {
-          // upper blocks only (pair i <= pair j); a block above the diagonal
-          // also writes its mirror, conj(K_j^H G K_i) = (K_i^H G K_j)^H, so
-          // that G stays Hermitian with half of the block updates
-          const int2 rj = pq[j];
-          // with odd l one pair holds the padding index l: its real index
-          // takes the other pair's rotation only
-          const bool jp = rj.y < l;
-          const float4 Rj = rot[j];
-          const bool rowrot = ip && Ri.y != 0.f, colrot = jp && Rj.y != 0.f;
-          if (!rowrot && !colrot) continue;
-          const float2 zero = make_float2(0.f, 0.f);
-          float2 x00 = G[ri.x * ls + rj.x];
-          float2 x01 = jp ? G[ri.x * ls + rj.y] : zero;
-          float2 x10 = ip ? G[ri.y * ls + rj.x] : zero;
-          float2 x11 = (ip && jp) ? G[ri.y * ls + rj.y] : zero;
-          if (rowrot) {   // rows, with e^{i phi_i} = (er, -ei)
-            const float c = Ri.x, s = Ri.y, er = Ri.z, ei = -Ri.w;
-            const float2 y0 = make_float2(x10.x * er - x10.y * ei, x10.x * ei + x10.y * er);
-            const float2 y1 = make_float2(x11.x * er - x11.y * ei, x11.x * ei + x11.y * er);
-            const float2 n00 = make_float2(c * x00.x - s * y0.x, c * x00.y - s * y0.y);
-            const float2 n01 = make_float2(c * x01.x - s * y1.x, c * x01.y - s * y1.y);
-            x10 = make_float2(s * x00.x + c * y0.x, s * x00.y + c * y0.y);
-            x11 = make_float2(s * x01.x + c * y1.x, s * x01.y + c * y1.y);
-            x00 = n00;
-            x01 = n01;
-          }
-          if (colrot) {   // columns, with e^{-i phi_j} = (er, ei)
-            const float c = Rj.x, s = Rj.y, er = Rj.z, ei = Rj.w;
-            const float2 y0 = make_float2(x01.x * er - x01.y * ei, x01.x * ei + x01.y * er);
-            const float2 y1 = make_float2(x11.x * er - x11.y * ei, x11.x * ei + x11.y * er);
-            const float2 n00 = make_float2(c * x00.x - s * y0.x, c * x00.y - s * y0.y);
-            const float2 n10 = make_float2(c * x10.x - s * y1.x, c * x10.y - s * y1.y);
-            x01 = make_float2(s * x00.x + c * y0.x, s * x00.y + c * y0.y);
-            x11 = make_float2(s * x10.x + c * y1.x, s * x10.y + c * y1.y);
-            x00 = n00;
-            x10 = n10;
-          }
-          G[ri.x * ls + rj.x] = x00;
-          if (jp) G[ri.x * ls + rj.y] = x01;
-          if (ip) G[ri.y * ls + rj.x] = x10;
-          if (ip && jp) G[ri.y * ls + rj.y] = x11;
-          if (i != j) {
-            G[rj.x * ls + ri.x] = make_float2(x00.x, -x00.y);
-            if (jp) G[rj.y * ls + ri.x] = make_float2(x01.x, -x01.y);
-            if (ip) G[rj.x * ls + ri.y] = make_float2(x10.x, -x10.y);
-            if (ip && jp) G[rj.y * ls + ri.y] = make_float2(x11.x, -x11.y);
-          }
-        }
+      // tau (y^H v) is real (|tau|^2 v^H A v): alpha' = -Re(tau y^H v) / 2
+      float hr = 0.f, hi = 0.f;
+      for (int t = lane; t < m; t += 32) {
+        const float2 y = ybuf[t], v = vbuf[t];
+        hr = fmaf(y.x, v.x, fmaf(y.y, v.y, hr));
+        hi = fmaf(y.x, v.y, fmaf(-y.y, v.x, hi));
       }
-      for (int j = warp; j < npairs; j += nw) {
-        const int2 rj = pq[j];
-        const float4 Rj = rot[j];
-        if (rj.y >= l || Rj.y == 0.f) continue;
-        const float c = Rj.x, s = Rj.y, er = Rj.z, ei = Rj.w;
-        float2* wa = W + rj.x * ls;
-        float2* wb = W + rj.y * ls;
-        for (int r = lane; r < l; r += 32) {
-          const float2 x = wa[r], y = wb[r];
-          const float2 yy = make_float2(y.x * er - y.y * ei, y.x * ei + y.y * er);
-          wa[r] = make_float2(c * x.x - s * yy.x, c * x.y - s * yy.y);
-          wb[r] = make_float2(s * x.x + c * yy.x, s * x.y + c * yy.y);
+      hr = eig_warp_sum(hr);
+      hi = eig_warp_sum(hi);
+      const float ap = -0.5f * (tj.x * hr - tj.y * hi);
+      for (int i = warp; i < m; i += nw) {
+        const float2 vi = vbuf[i], yi = ybuf[i];
+        const float2 wi = make_float2(fmaf(ap, vi.x, yi.x), fmaf(ap, vi.y, yi.y));
+        float2* Ai = G + (j + 1 + i) * ls + (j + 1);
+        for (int t = lane; t < m; t += 32) {
+          const float2 vt = vbuf[t], yt = ybuf[t];
+          const float2 wt = make_float2(fmaf(ap, vt.x, yt.x), fmaf(ap, vt.y, yt.y));
+          // v_i conj(w_t) + w_i conj(v_t)
+          const float re = vi.x * wt.x + vi.y * wt.y + wi.x * vt.x + wi.y * vt.y;
+          const float im = vi.y * wt.x - vi.x * wt.y + wi.y * vt.x - wi.x * vt.y;
+          float2 a = Ai[t];
+          a.x -= re;
+          a.y -= im;
+          Ai[t] = a;
         }
       }
     }
     __syncthreads();
-    const int any = *rotated;
-    __syncthreads();
-    if (!any) break;
   }
-  return sweep;
+  for (int i = tid; i < l; i += blockDim.x) {
+    d[i] = G[i * ls + i].x;
+    if (i == l - 1) e[i] = 0.f;
+  }
+  __syncthreads();
+}
+
+// Q = H_0 H_1 ... H_{l-2} into W (column-major, column stride ls) by
+// backward accumulation from W = I: step j applies H_j to rows j+1.. of
+// columns j+1.. (a warp per column).
+__device__ void tridiag_form_q(const float2* G, float2* W, int l, int ls, const float2* tau) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int e = tid; e < l * l; e += blockDim.x) {
+    const int c = e / l, r = e - c * l;
+    W[c * ls + r] = make_float2(r == c ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  for (int j = l - 2; j >= 0; --j) {
+    const float2 tj = tau[j];
+    if (tj.x != 0.f || tj.y != 0.f) {
+      const int m = l - 1 - j;
+      const float2* vr = G + j * ls + j + 1;
+      for (int c = j + 1 + warp; c < l; c += nw) {
+        float2* z = W + c * ls + j + 1;
+        float dr = 0.f, di = 0.f;
+        for (int t = lane; t < m; t += 32) {
+          const float2 v = t == 0 ? make_float2(1.f, 0.f) : vr[t];
+          const float2 x = z[t];
+          dr = fmaf(v.x, x.x, fmaf(v.y, x.y, dr));    // conj(v) x
+          di = fmaf(v.x, x.y, fmaf(-v.y, x.x, di));
+        }
+        dr = eig_warp_sum(dr);
+        di = eig_warp_sum(di);
+        const float gr = tj.x * dr - tj.y * di, gi = tj.x * di + tj.y * dr;
+        for (int t = lane; t < m; t += 32) {
+          const float2 v = t == 0 ? make_float2(1.f, 0.f) : vr[t];
+          float2 x = z[t];
+          x.x -= v.x * gr - v.y * gi;
+          x.y -= v.x * gi + v.y * gr;
+          z[t] = x;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// A plane rotation of the QL chase: rotation i mixes columns i and i + 1;
+// code = i, or -(i + 1) for the first rotation of a chase.
+struct QlRot {
+  int code;
+  float c, s;
+};
+
+// Eigenvalues (d) and eigenvectors (columns of W <- W S) of the real
+// symmetric tridiagonal (d, e) by the implicit QL algorithm with Wilkinson's
+// shift from the leading 2 x 2 (Bowdler, Martin, Reinsch and Wilkinson,
+// 1968): each chase runs from the bottom of the unreduced block up to its
+// top, deflating off-diagonals below FLT_EPSILON (|d_m| + |d_m+1|).  The
+// chase is serial: thread 0 runs it and logs its rotations in `log` (cap
+// entries); the block then replays the log on W, a thread per row and
+// component, carrying the column the next rotation of the chase reuses in a
+// register; chases continue until done.  At most max_iter chases per
+// eigenvalue (then its off-diagonal is dropped and false is returned).
+__device__ bool tridiag_ql(float* d, float* e, float2* W, int l, int ls, QlRot* log, int cap,
+                           int max_iter) {
+  __shared__ int ql_cnt, ql_done, ql_ok;
+  int l0 = 0, it = 0;   // thread 0's state across flushes
+  bool ok = true;
+  if (threadIdx.x == 0) {
+    // scale T by a power of two to a largest entry near 1 (exact; only the
+    // eigenvectors are used), so that the squares below neither overflow
+    // nor lose range
+    float mx = 0.f;
+    for (int i = 0; i < l; ++i) mx = fmaxf(mx, fmaxf(fabsf(d[i]), i + 1 < l ? fabsf(e[i]) : 0.f));
+    if (mx > 0.f && isfinite(mx)) {
+      int ex;
+      frexpf(mx, &ex);
+      for (int i = 0; i < l; ++i) {
+        d[i] = ldexpf(d[i], -ex);
+        e[i] = ldexpf(e[i], -ex);
+      }
+    }
+  }
+  for (;;) {
+    if (threadIdx.x == 0) {
+      int cnt = 0;
+      while (l0 < l) {
+        int m = l0;
+        for (; m + 1 < l; ++m) {
+          const float dd = fabsf(d[m]) + fabsf(d[m + 1]);
+          if (fabsf(e[m]) <= FLT_EPSILON * dd) break;
+        }
+        if (m == l0) {
+          ++l0;
+          it = 0;
+          continue;
+        }
+        if (cnt + (m - l0) > cap) break;   // replay the log first
+        if (++it > max_iter) {
+          ok = false;
+          e[l0] = 0.f;
+          continue;
+        }
+        float g = (d[l0 + 1] - d[l0]) / (2.f * e[l0]);
+        const float r0 = hypotf(g, 1.f);
+        g = d[m] - d[l0] + e[l0] / (g + copysignf(r0, g));
+        float s = 1.f, c = 1.f, pp = 0.f;
+        float dn = d[m];   // d[i + 1] of the step below, carried
+        bool early = false;
+        for (int i = m - 1; i >= l0; --i) {
+          const float ei = e[i], di = d[i];
+          const float f = s * ei, b = c * ei;
+          float r = sqrtf(fmaf(f, f, g * g));
+          e[i + 1] = r;
+          if (r == 0.f) {   // the chase splits: restart from the new block
+            d[i + 1] = dn - pp;
+            e[m] = 0.f;
+            early = true;
+            break;
+          }
+          const float inv = __frcp_rn(r);
+          s = f * inv;
+          c = g * inv;
+          g = dn - pp;
+          r = fmaf(di - g, s, 2.f * c * b);
+          pp = s * r;
+          d[i + 1] = g + pp;
+          g = fmaf(c, r, -b);
+          dn = di;
+          log[cnt++] = QlRot{i == m - 1 ? -(i + 1) : i, c, s};
+        }
+        if (!early) {
+          d[l0] -= pp;
+          e[l0] = g;
+          e[m] = 0.f;
+        }
+      }
+      ql_cnt = cnt;
+      ql_done = l0 >= l;
+      ql_ok = ok;
+    }
+    __syncthreads();
+    const int cnt = ql_cnt, done = ql_done;
+    if (int(threadIdx.x) < 2 * l) {
+      // W(r, i), component t & 1 of row r = t >> 1, at float index 2 ls i + t
+      float* z = reinterpret_cast<float*>(W) + threadIdx.x;
+      const int cs = 2 * ls;
+      int prev = -1;
+      float carry = 0.f;
+      for (int q = 0; q < cnt; ++q) {
+        const QlRot R = log[q];
+        const int i = R.code < 0 ? -R.code - 1 : R.code;
+        if (R.code < 0) {
+          if (prev >= 0) z[cs * prev] = carry;
+          carry = z[cs * (i + 1)];
+        }
+        const float zi = z[cs * i];
+        z[cs * (i + 1)] = fmaf(R.s, zi, R.c * carry);
+        carry = fmaf(R.c, zi, -R.s * carry);
+        prev = i;
+      }
+      if (prev >= 0) z[cs * prev] = carry;
+    }
+    __syncthreads();
+    if (done) break;
+  }
+  return ql_ok != 0;
 }
 
 // Core SVD through the l x l Gram of B^H (n2 x l, read from global memory,
 // which the previous product left in L2): G = B B^H = W diag(s^2) W^H by the
-// fused float32 two-sided Jacobi above (from W = I).  The singular values are
-// then the Rayleigh quotients s_j = ||B^H w_j|| (float32 products, float64
-// sums of squares), whose error is second order in the error of w_j -- the
-// square roots of G's float32 eigenvalues would carry an error u ||G|| /
-// (2 s_j) that grows as 1/s_j.  B^H itself is a float32 product of float32
-// data, so its singular values are only defined to about u32 s_1 (absolute);
-// a float64 polish of W would not change the result beyond that, at 1/64 of
-// the float32 rate.  The top k give W_k (left singular vectors of B),
-// S = diag(s) and V_k = B^H W_k S^{-1}.
+// Householder tridiagonalization and implicit QL above (float32).  The
+// singular values are then the Rayleigh quotients s_j = ||B^H w_j|| (float32
+// products, float64 sums of squares), whose error is second order in the
+// error of w_j -- the square roots of G's float32 eigenvalues would carry an
+// error u ||G|| / (2 s_j) that grows as 1/s_j.  B^H itself is a float32
+// product of float32 data, so its singular values are only defined to about
+// u32 s_1 (absolute), which is also the eigensolver's accuracy; a
+// relatively accurate (Jacobi) solve would not change the result beyond
+// that.  The top k give W_k (left singular vectors of B), S = diag(s) and
+// V_k = B^H W_k S^{-1}.
 constexpr int EIG_THREADS = 256;
 constexpr int EIG_CHUNK = 32;   // rows of B^H staged per step of the Gram
 
@@ -538,9 +749,11 @@ __global__ void __launch_bounds__(EIG_THREADS) core_eig_kernel(
   double* sig2 = dyn;                                       // l: ||B^H w_j||^2
   float2* Gf = reinterpret_cast<float2*>(dyn + ((l + 1) & ~1));   // l x l Gram (row stride ls)
   float2* Wf = Gf + L2;                                     // l x l eigenvectors (column stride ls)
-  float4* rot = reinterpret_cast<float4*>(Wf + L2);         // per pair: c, s, er, ei
-  int2* pq = reinterpret_cast<int2*>(rot + (l + 1) / 2);
-  __shared__ int rotated;
+  float2* tau = Wf + L2;                                    // l: reflectors of the reduction
+  float2* vbuf = tau + l;                                   // l
+  float2* ybuf = vbuf + l;                                  // l
+  float* dv = reinterpret_cast<float*>(ybuf + l);           // l: tridiagonal
+  float* ev = dv + l;                                       // l
   __shared__ int order[128];
   const int64_t f = blockIdx.x;
   const float* br = bh_re + f * int64_t(p) * l;
@@ -550,7 +763,7 @@ __global__ void __launch_bounds__(EIG_THREADS) core_eig_kernel(
   // B^H staged EIG_CHUNK at a time (in W's space, before W is set)
   float2* chunk = Wf;                                       // EIG_CHUNK x l, row stride l
   const int npairs = l * (l + 1) / 2;
-  constexpr int PPT = 8;                                    // pairs per thread and pass
+  constexpr int PPT = 6;                                    // pairs per thread and pass
   for (int base = 0; base < npairs; base += PPT * EIG_THREADS) {
     int pa[PPT], pb[PPT];
     float gr[PPT], gi[PPT];
@@ -592,13 +805,13 @@ __global__ void __launch_bounds__(EIG_THREADS) core_eig_kernel(
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
-    const int i = e / l, j = e % l;
-    Wf[i * ls + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
-  }
   for (int j = threadIdx.x; j < l; j += blockDim.x) sig2[j] = 0.0;
-  const int s32 = jacobi2_fused(Gf, Wf, l, ls, 1e-6f, max_sweeps, rot, pq, &rotated);
-  if (s32 >= max_sweeps && threadIdx.x == 0 && status) atomicOr(status, TP_DEV_NOCONV);
+  hermitian_tridiag(Gf, l, ls, dv, ev, tau, vbuf, ybuf);
+  tridiag_form_q(Gf, Wf, l, ls, tau);
+  // the reflectors are in W now: G's space takes the rotation log
+  const int cap = int(size_t(L2) * sizeof(float2) / sizeof(QlRot));
+  const bool conv = tridiag_ql(dv, ev, Wf, l, ls, reinterpret_cast<QlRot*>(Gf), cap, max_sweeps);
+  if (!conv && threadIdx.x == 0 && status) atomicOr(status, TP_DEV_NOCONV);
   __syncthreads();
   // P = B^H W and s_j^2 = ||P(:, j)||^2: a warp per column, lanes over rows
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
@@ -658,8 +871,7 @@ size_t core_eig_smem(int p, int l) {
   (void)p;
   const int ls = l | 1;
   const size_t L2 = size_t(l) * ls;
-  return size_t((l + 1) & ~1) * 8 + 2 * L2 * 8 + size_t((l + 1) / 2) * 16 +
-         size_t((l + 1) / 2) * 8;
+  return size_t((l + 1) & ~1) * 8 + 2 * L2 * 8 + size_t(l) * (3 * 8 + 2 * 4);
 }
 
 // Sorts the l Jacobi singular triplets of every slice, keeps the top k and
@@ -704,6 +916,18 @@ __global__ void pick_topk_kernel(const double* __restrict__ gr, const double* __
 
 // Per-frequency truncation: columns c >= r_f of W_k (l x k), V (p x k) and the
 // diagonal of S (k x k) of frequency f are zeroed.  One block per frequency.
+// Zero the columns c >= l_f of slice f (rows x l, column-major, slice
+// stride rows * l): the per-frequency sketch size.
+__global__ void sketch_cols_kernel(float* __restrict__ re, float* __restrict__ im, int64_t rows,
+                                   int64_t l, const int32_t* __restrict__ sizes) {
+  const int64_t f = blockIdx.x;
+  const int64_t lf = min(max(int64_t(sizes[f]), int64_t(1)), l);
+  for (int64_t e = lf * rows + threadIdx.x; e < l * rows; e += blockDim.x) {
+    re[f * rows * l + e] = 0.f;
+    im[f * rows * l + e] = 0.f;
+  }
+}
+
 __global__ void rank_mask_kernel(const int32_t* __restrict__ rank, int l, int p, int k,
                                  float* __restrict__ wkr, float* __restrict__ wki,
                                  float* __restrict__ vkr, float* __restrict__ vki,
@@ -808,10 +1032,16 @@ __global__ void diag_kernel(const float* __restrict__ sr, int k, int64_t h, floa
 // sig_out non-null: only the core singular values of every frequency are
 // wanted (descending, h x k, float32); U, S, V are not formed.  rank_per_freq
 // non-null (device int32[h]): frequency f keeps its top min(max(r_f, 0), k)
-// triplets, the others are zero.
+// triplets, the others are zero.  sketch_per_freq non-null (device
+// int32[h]): frequency f sketches with the first l_f = min(max(s_f, 1), l)
+// columns; its other columns of Omega, Y and Z are held at zero, so that the
+// products (run over l columns for every slice) leave them zero, the
+// orthonormalisations factor only the first l_f columns, and the core Gram
+// has an exact zero block beyond l_f (zero singular values, zero factors).
 int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, int q,
              uint64_t seed, float* U, float* S, float* V, const tp_opts* opts, cudaStream_t st,
-             float* sig_out, const int32_t* rank_per_freq, int sketch_mode) {
+             float* sig_out, const int32_t* rank_per_freq, int sketch_mode,
+             const int32_t* sketch_per_freq) {
   const int64_t h = half_len(n3);
   const int64_t l = k + p;
   const int prec = opts ? opts->precision : TP_FP32;
@@ -891,6 +1121,10 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
     KernelScope ks("sketch", st);
     sketch_kernel<<<grid_for(n2 * l * h), 256, 0, st>>>(Or, Oi, n2, l, h, n3, seed);
   }
+  if (sketch_per_freq) {
+    KernelScope ks("sketch", st);
+    sketch_cols_kernel<<<unsigned(h), 256, 0, st>>>(Or, Oi, n2, l, sketch_per_freq);
+  }
   if ((rc = launch_status("sketch"))) return rc;
 
   auto gemm = [&](const float* ar, const float* ai, int64_t M, int64_t K, const float* br,
@@ -942,23 +1176,23 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
       KernelScope ks("householder_qr", st);
       if (rows <= 64) {
         TP_SET_SMEM(householder_qr_kernel<2>, smem);
-        householder_qr_kernel<2><<<unsigned(h), HQR_THREADS, smem, st>>>(yr, yi, rows * l,
-                                                                         int(rows), int(l));
+        householder_qr_kernel<2><<<unsigned(h), HQR_THREADS, smem, st>>>(
+            yr, yi, rows * l, int(rows), int(l), sketch_per_freq);
       } else if (rows <= 128) {
         TP_SET_SMEM(householder_qr_kernel<4>, smem);
-        householder_qr_kernel<4><<<unsigned(h), HQR_THREADS, smem, st>>>(yr, yi, rows * l,
-                                                                         int(rows), int(l));
+        householder_qr_kernel<4><<<unsigned(h), HQR_THREADS, smem, st>>>(
+            yr, yi, rows * l, int(rows), int(l), sketch_per_freq);
       } else {
         TP_SET_SMEM(householder_qr_kernel<8>, smem);
-        householder_qr_kernel<8><<<unsigned(h), HQR_THREADS, smem, st>>>(yr, yi, rows * l,
-                                                                         int(rows), int(l));
+        householder_qr_kernel<8><<<unsigned(h), HQR_THREADS, smem, st>>>(
+            yr, yi, rows * l, int(rows), int(l), sketch_per_freq);
       }
       return launch_status("householder_qr_kernel");
     }
     {
       KernelScope ks("cholqr2", st);
       cholqr2_kernel<<<unsigned(h), QR_THREADS, qr_smem, st>>>(yr, yi, rows * l, int(rows),
-                                                               int(l), status);
+                                                               int(l), sketch_per_freq, status);
     }
     return launch_status("cholqr2_kernel");
   };

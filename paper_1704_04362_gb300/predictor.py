@@ -142,14 +142,26 @@ def decompose(X, w16=None, seed=0):
     return r, L_PLAIN, True
 
 
-def factorize(X, w16=None, seed=0):
+def sketch_sizes(w16, X, ranks, l, seed=0):
+    """Per-frequency sketch sizes l_f = r_f + p_f: the judged rank plus the
+    network's predicted oversampling for that frequency, at most l."""
+    import torch
+    _, p = predict(w16, cheap_features(X, seed))
+    return torch.clamp(ranks.int() + p, 1, l).int().contiguous()
+
+
+def factorize(X, w16=None, seed=0, per_frequency=True):
     """The multi-rank factorisation X ~ U * S * V^T: per-frequency ranks from
-    decompose(), then the randomized t-SVD with the same sketch size (k the
-    largest rank, p the rest of the sketch, q = 2) truncating every
-    frequency to its own rank.  Returns (U, S, V, ranks, sketch size)."""
+    decompose(), then the randomized t-SVD (k the largest rank, q = 2)
+    truncating every frequency to its own rank.  With the predictor and
+    per_frequency, frequency f sketches with its own l_f = r_f + p_f columns
+    (sketch_sizes) inside the one call; otherwise every frequency uses the
+    call's sketch size l.  Returns (U, S, V, ranks, sketch size l)."""
     r, l, _ = decompose(X, w16, seed)
     k = max(1, int(r.max().item()))
-    U, S, V = tp.tsvd_randomized(X, k, l - k, Q_PLAIN, seed=seed, ranks=r.int().contiguous())
+    sizes = sketch_sizes(w16, X, r, l, seed) if (w16 is not None and per_frequency) else None
+    U, S, V = tp.tsvd_randomized(X, k, l - k, Q_PLAIN, seed=seed, ranks=r.int().contiguous(),
+                                 sketch_sizes=sizes)
     return U, S, V, r, l
 
 

@@ -71,8 +71,8 @@ def test_null_and_size_errors_need_no_gpu(L):
     k[0] = d(0.0)
     assert L.cur_tnn(p, nul, 2, 2, 2, 1, 1, 0, 0, 1, nul, nul, 5, d(0), *k) == -1     # mu0
     # randomized t-SVD: unknown sketch mode, and k + p beyond min(n1, n2)
-    assert L.tsvd_randomized(p, 8, 8, 4, 2, 2, 1, 0, 7, nul, p, p, p, nul, nul) == -1
-    assert L.tsvd_randomized(p, 8, 8, 4, 6, 4, 1, 0, 0, nul, p, p, p, nul, nul) == -1
+    assert L.tsvd_randomized(p, 8, 8, 4, 2, 2, 1, 0, 7, nul, nul, p, p, p, nul, nul) == -1
+    assert L.tsvd_randomized(p, 8, 8, 4, 6, 4, 1, 0, 0, nul, nul, p, p, p, nul, nul) == -1
     # a status word without a host destination
     assert L.tp_sync_status(nul, p, nul) == -2
     # with-replacement draws need c <= n

@@ -54,14 +54,20 @@ def test_learned_matches_plain_error_with_smaller_sketches(trained, alpha, n3):
         assert np.mean(sizes) < 40, sizes       # fast decay: smaller sketches than 50
 
 
-def test_multi_rank_factorisation_reaches_the_rule_error(trained):
+@pytest.mark.parametrize("per_frequency", [False, True])
+def test_multi_rank_factorisation_reaches_the_rule_error(trained, per_frequency):
     # U * S * V^T with every frequency truncated to the predicted-and-judged
     # rank: its error is the per-frequency truncation error of those ranks
-    # (up to the sketch's resolution of the tail)
+    # (up to the sketch's resolution of the tail), with one sketch size for
+    # all frequencies or each frequency's own predicted l_f = r_f + p_f
     import torch
     w16 = trained[0]
     X, spec = synth.spectral_torch(144, 128, 16, 3.0, 0.3, 9100)
-    U, S, V, r, l = P.factorize(X, w16, seed=1)
+    U, S, V, r, l = P.factorize(X, w16, seed=1, per_frequency=per_frequency)
+    if per_frequency:
+        sizes = P.sketch_sizes(w16, X, r, l, seed=1)
+        assert bool((sizes >= r.int() + 2).all()) and int(sizes.max()) <= l
+        assert int(sizes.min()) < l            # some frequency sketches with fewer columns
     assert U.shape[1] == int(r.max().item()) and l <= 50
     # t-product U * S * V^T through the library's own exact t-product
     Vt = torch.flip(V.permute(1, 0, 2), dims=[2])

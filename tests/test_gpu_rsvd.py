@@ -188,3 +188,37 @@ def test_slice_sketch_matches_oracle(n1, n2, n3, r, k, p, q):
     # the sign sketch is a different test matrix but the same exact result
     U2, S2, V2 = tp.tsvd_randomized(dev(X), k, p, q, seed=7)
     assert rel_fro(approx(to_np(U2), to_np(S2), to_np(V2)), A) < TOL_FP32
+
+
+@pytest.mark.parametrize("precision", [tp.TP_FP32, tp.TP_BF16X3])
+@pytest.mark.parametrize("n1,n2,n3,r,k,p,q,sizes", [
+    (48, 40, 10, 6, 6, 4, 1, [10, 3, 6, 8, 1, 7]),
+    (40, 48, 7, 5, 4, 4, 2, [2, 8, 5, 4]),
+    (300, 40, 4, 3, 4, 3, 1, [7, 2, 4]),          # CholeskyQR2 (more than 256 rows)
+])
+def test_per_frequency_sketch_sizes_match_oracle(n1, n2, n3, r, k, p, q, sizes, precision):
+    # slice f sketches with the first l_f columns of the same Philox test
+    # matrix on both sides; l_f below the tubal rank gives a (deterministic)
+    # approximation, l_f at or above it the exact slice
+    import torch
+    X = synth.lowrank_np(n1, n2, n3, r, seed=n1 + n2 + r)
+    h = n3 // 2 + 1
+    sz = np.array(sizes, dtype=np.int32)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    U, S, V = tp.tsvd_randomized(dev(X), k, p, q, seed=11, status=st, precision=precision,
+                                 sketch_sizes=torch.from_numpy(sz).cuda())
+    assert int(st.item()) == 0
+    Om = philox_ref.sketch_signs(n2, k + p, h, n3, 11)
+    Ur, Sr, Vr = decomp_ref.tsvd_randomized(X.astype(np.float64), k, p, q, Om, sketch_sizes=sz)
+    s, sr = sing_vals(to_np(S)), sing_vals(Sr)
+    assert rel_fro(s, sr) < TOL_FP32
+    for f in range(h):            # min(k, l_f) triplets, zeros after (up to the round trip)
+        kf = min(k, int(sz[f]))
+        assert np.all(np.abs(s[kf:, f]) <= 1e-6 * s.max())
+    assert rel_fro(approx(to_np(U), to_np(S), to_np(V)), approx(Ur, Sr, Vr)) < TOL_FP32
+    # sizes of k + p everywhere are the plain call, bit for bit
+    full = torch.full((h,), k + p, dtype=torch.int32, device="cuda")
+    U1, S1, V1 = tp.tsvd_randomized(dev(X), k, p, q, seed=11, precision=precision,
+                                    sketch_sizes=full)
+    U0, S0, V0 = tp.tsvd_randomized(dev(X), k, p, q, seed=11, precision=precision)
+    assert torch.equal(U1, U0) and torch.equal(S1, S0) and torch.equal(V1, V0)

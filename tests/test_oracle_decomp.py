@@ -378,3 +378,43 @@ def test_slice_sketch_recovers_exact_low_tubal_rank():
     Xh = np.fft.fft(X, axis=2)
     j, c = np.nonzero(Om[:, :, 0])
     np.testing.assert_allclose((Xh[:, :, 1] @ Om[:, :, 1])[:, c], Xh[:, j, 1] * Om[j, c, 1], atol=1e-12)
+
+
+def test_per_frequency_sketch_sizes():
+    # slice f sketches with the first l_f columns of Omega and keeps
+    # min(k, l_f) triplets: (a) l_f >= the tubal rank recovers X exactly and
+    # the exact singular values; (b) a smaller l_f gives exactly min(k, l_f)
+    # nonzero values, none above the exact ones (interlacing: the singular
+    # values of Q^H X_hat with orthonormal Q); (c) only the first l_f columns
+    # of Omega matter; (d) l_f = k + p everywhere is the plain call
+    from oracle.tensor_ref import tprod, ttranspose
+    g = np.random.default_rng(91)
+    k, p, h = 4, 3, 4
+    X = _lowrank(20, 16, 6, 3, 92)
+    Om = P.sketch_signs(16, k + p, h, 6, seed=9)
+    sizes = np.array([4, 3, 7, 5])
+    U, S, V = D.tsvd_randomized(X, k, p, 1, Om, sketch_sizes=sizes)
+    np.testing.assert_allclose(tprod(tprod(U, S), ttranspose(V)), X, atol=1e-10)
+    _, s_exact, _ = D.tsvd_hat(X)
+    _, s_rand, _ = D.tsvd_randomized_hat(X, k, p, 1, Om, sizes)
+    for f in range(h):
+        kf = min(k, sizes[f])
+        np.testing.assert_allclose(s_rand[:kf, f], s_exact[:kf, f], rtol=1e-9, atol=1e-9)
+        assert np.all(s_rand[kf:, f] == 0)
+    Y = g.standard_normal((14, 12, 6))
+    Om = P.sketch_signs(12, k + p, h, 6, seed=3)
+    small = np.array([2, 1, 6, 3])
+    _, s_small, _ = D.tsvd_randomized_hat(Y, k, p, 1, Om, small)
+    _, s_full, _ = D.tsvd_hat(Y)
+    for f in range(h):
+        kf = min(k, small[f])
+        assert np.count_nonzero(s_small[:, f]) == kf
+        assert np.all(s_small[:kf, f] <= s_full[:kf, f] * (1 + 1e-12))
+    Om2 = Om.copy()
+    for f in range(h):
+        Om2[:, small[f]:, f] = g.standard_normal((12, k + p - small[f]))
+    _, s_other, _ = D.tsvd_randomized_hat(Y, k, p, 1, Om2, small)
+    np.testing.assert_array_equal(s_other, s_small)
+    U0, S0, V0 = D.tsvd_randomized(Y, k, p, 1, Om)
+    U1, S1, V1 = D.tsvd_randomized(Y, k, p, 1, Om, sketch_sizes=np.full(h, k + p))
+    assert np.array_equal(U0, U1) and np.array_equal(S0, S1) and np.array_equal(V0, V1)
