@@ -485,11 +485,27 @@ def bench_learned(torch, train_count=192, eval_n3=(64, 128, 256), eval_n12=(1024
             r_l, l, fb = P.decompose(X, w16, seed=i)
             ms_p = P.time_call(lambda: P.decompose(X, None, seed=i), reps=2)
             ms_l = P.time_call(lambda: P.decompose(X, w16, seed=i), reps=2)
-            cases.append({"n3": n3, "alpha": a, "sketch_columns": l, "fell_back": bool(fb),
-                          "plain_ms": ms_p, "learned_ms": ms_l, "speedup": ms_p / ms_l,
-                          "plain_error": P.truncation_error(spec, r_p, n3),
-                          "learned_error": P.truncation_error(spec, r_l, n3),
-                          "ranks_equal_fraction": float((r_p == r_l).float().mean().item())})
+            case = {"n3": n3, "alpha": a, "sketch_columns": l, "fell_back": bool(fb),
+                    "plain_ms": ms_p, "learned_ms": ms_l, "speedup": ms_p / ms_l,
+                    "plain_error": P.truncation_error(spec, r_p, n3),
+                    "learned_error": P.truncation_error(spec, r_l, n3),
+                    "ranks_equal_fraction": float((r_p == r_l).float().mean().item())}
+            if i == 1:
+                # the whole multi-rank factorisation U * S * V^T: plain (50
+                # columns everywhere) against the predictor's per-frequency
+                # sketch sizes l_f = r_f + p_f in one call
+                fac = {}
+                for name, w in (("plain", None), ("learned", w16)):
+                    U, S, V, r, lc = P.factorize(X, w, seed=i)
+                    fac[name + "_ms"] = P.time_call(lambda: P.factorize(X, w, seed=i), reps=2)
+                    fac[name + "_error"] = _factor_error(tp_mod(), X, U, S, V)
+                    if w is not None:
+                        sz = P.sketch_sizes(w, X, r, lc, seed=i)
+                        fac["learned_sketch_sizes_mean"] = float(sz.float().mean().item())
+                    del U, S, V
+                fac["optimal_error"] = P.truncation_error(spec, r_l, n3)
+                case["factorisation"] = fac
+            cases.append(case)
             del X, spec
             torch.cuda.empty_cache()
     return {"workload": f"{n1}x{n2}x{{{','.join(str(v) for v in eval_n3)}}} tensors, "
@@ -500,6 +516,23 @@ def bench_learned(torch, train_count=192, eval_n3=(64, 128, 256), eval_n12=(1024
             "total_plain_ms": sum(c["plain_ms"] for c in cases),
             "total_learned_ms": sum(c["learned_ms"] for c in cases),
             "cases": cases}
+
+
+def tp_mod():
+    import paper_1704_04362_gb300 as tp
+    return tp
+
+
+def _factor_error(tp, X, U, S, V):
+    """||X - U * S * V^T||_F / ||X||_F through the library's t-product (V^T:
+    each frontal slice transposed, slices 2..n3 in reverse order)."""
+    import torch
+    Vt = torch.roll(torch.flip(V.permute(1, 0, 2), dims=[2]), 1, dims=2).contiguous()
+    US = tp.tprod(tp.as_tprod_layout(U), tp.as_tprod_layout(S))
+    R = tp.tprod(US, tp.as_tprod_layout(Vt))
+    err = float(torch.linalg.vector_norm(R - X) / torch.linalg.vector_norm(X))
+    del US, R, Vt
+    return err
 
 
 def bench_rsvd(args, tp, torch, with_cpu, forms=("bf16x3", "fp32", "tf32x3")):
@@ -795,7 +828,8 @@ def main():
                     help="iterations of the batched completion row (256 videos)")
     ap.add_argument("--only", default=None,
                     help="comma-separated rows to run instead of the headline step "
-                         "(rsvd, svt_batched, svt_batched_bf16x3, svt_video): profiling and "
+                         "(rsvd, svt_batched, svt_batched_bf16x3, svt_video, learned): "
+                         "profiling and "
                          "tuning runs, no headline line")
     ap.add_argument("--tune-file", default=None,
                     help="autotuner table: loaded before the run when the file exists, "
@@ -834,6 +868,8 @@ def main():
                 out = bench_svt_batched(tp, torch, iters=args.svt_iters)
             elif name == "svt_batched_bf16x3":
                 out = bench_svt_batched(tp, torch, iters=args.svt_iters, precision="bf16x3")
+            elif name == "learned":
+                out = bench_learned(torch)
             elif name == "svt_video":
                 # one 480 x 360 x 120 video (the largest of the batch): a
                 # single-tensor profiling case a few GB in size

@@ -372,12 +372,17 @@ __device__ __forceinline__ void hqr_materialize(float2* a, int k, int p, float2 
 }
 
 // One CTA per slice; RPL rows per lane (p <= 32 RPL).
+// keep_phase: column j of Q is multiplied by sign(R(j, j)) (R's diagonal is
+// real), so that for Y with nearly orthonormal columns Q(:, j) stays close
+// to Y(:, j) instead of possibly flipping its sign.
 template <int RPL>
 __global__ void __launch_bounds__(HQR_THREADS) householder_qr_kernel(float* y_re, float* y_im,
                                                                      int64_t sY, int p, int lfull,
-                                                                     const int32_t* lcols) {
+                                                                     const int32_t* lcols,
+                                                                     int keep_phase) {
   extern __shared__ float2 hqr_a[];   // Y, then Q: p x l column-major
   __shared__ float2 tau_s[HQR_MAX_L];
+  __shared__ float sgn_s[HQR_MAX_L];   // sign of R(j, j)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // per-slice column count (the per-frequency sketch size): the columns from
   // l on are left zero
@@ -389,7 +394,10 @@ __global__ void __launch_bounds__(HQR_THREADS) householder_qr_kernel(float* y_re
   __syncthreads();
   if (warp == 0) {
     const float2 t = hqr_reflector(A, 0, p, lane);
-    if (lane == 0) tau_s[0] = t;
+    if (lane == 0) {
+      tau_s[0] = t;
+      sgn_s[0] = A[0].x < 0.f ? -1.f : 1.f;
+    }
   }
   __syncthreads();
   // factorisation: step j applies H_j^H to columns j+1 .. l-1
@@ -405,7 +413,10 @@ __global__ void __launch_bounds__(HQR_THREADS) householder_qr_kernel(float* y_re
       if (live) hqr_apply<RPL>(v, c, j, p, f, lane);
       __syncwarp();
       const float2 t = hqr_reflector(c, k, p, lane);
-      if (lane == 0) tau_s[k] = t;
+      if (lane == 0) {
+        tau_s[k] = t;
+        sgn_s[k] = c[k].x < 0.f ? -1.f : 1.f;
+      }
       k += HQR_WARPS;
     }
     if (live) {
@@ -438,8 +449,9 @@ __global__ void __launch_bounds__(HQR_THREADS) householder_qr_kernel(float* y_re
   __syncthreads();
   for (int e = threadIdx.x; e < p * l; e += HQR_THREADS) {
     const float2 q = A[e];
-    yr[e] = q.x;
-    yi[e] = q.y;
+    const float sg = keep_phase ? sgn_s[e / p] : 1.f;
+    yr[e] = sg * q.x;
+    yi[e] = sg * q.y;
   }
   for (int e = p * l + threadIdx.x; e < p * lfull; e += HQR_THREADS) {
     yr[e] = 0.f;
@@ -974,6 +986,37 @@ int64_t split_ld(int64_t k, int prec) {
   return prec == TP_BF16X3 ? (k + 7) / 8 * 8 : (k + 3) / 4 * 4;
 }
 
+// Householder orthonormalisation of `batch` slices Y (p x l, column-major,
+// slice stride sY) in place, float32 in shared memory: p <= 256 and
+// l <= 96 (else TP_EUNSUPPORTED).  keep_phase multiplies column j by
+// sign(R(j, j)), so that nearly orthonormal columns stay close to their
+// input.
+int householder_orth_launch(float* yr, float* yi, int64_t sY, int p, int l, int64_t batch,
+                            bool keep_phase, cudaStream_t st) {
+  if (p > 256 || l > HQR_MAX_L || l > p) {
+    set_error("householder_orth: needs l <= p <= 256 and l <= %d", HQR_MAX_L);
+    return TP_EUNSUPPORTED;
+  }
+  if (batch <= 0 || l <= 0) return TP_OK;
+  const size_t smem = size_t(p) * l * sizeof(float2);
+  const int kp = keep_phase ? 1 : 0;
+  KernelScope ks("householder_qr", st);
+  if (p <= 64) {
+    TP_SET_SMEM(householder_qr_kernel<2>, smem);
+    householder_qr_kernel<2><<<unsigned(batch), HQR_THREADS, smem, st>>>(yr, yi, sY, p, l,
+                                                                         nullptr, kp);
+  } else if (p <= 128) {
+    TP_SET_SMEM(householder_qr_kernel<4>, smem);
+    householder_qr_kernel<4><<<unsigned(batch), HQR_THREADS, smem, st>>>(yr, yi, sY, p, l,
+                                                                         nullptr, kp);
+  } else {
+    TP_SET_SMEM(householder_qr_kernel<8>, smem);
+    householder_qr_kernel<8><<<unsigned(batch), HQR_THREADS, smem, st>>>(yr, yi, sY, p, l,
+                                                                         nullptr, kp);
+  }
+  return launch_status("householder_qr_kernel");
+}
+
 size_t rsvd_ws(int64_t n1, int64_t n2, int64_t n3, int64_t k, int64_t p, int prec) {
   const size_t h = size_t(half_len(n3));
   const size_t l = size_t(k + p);
@@ -1177,15 +1220,15 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
       if (rows <= 64) {
         TP_SET_SMEM(householder_qr_kernel<2>, smem);
         householder_qr_kernel<2><<<unsigned(h), HQR_THREADS, smem, st>>>(
-            yr, yi, rows * l, int(rows), int(l), sketch_per_freq);
+            yr, yi, rows * l, int(rows), int(l), sketch_per_freq, 0);
       } else if (rows <= 128) {
         TP_SET_SMEM(householder_qr_kernel<4>, smem);
         householder_qr_kernel<4><<<unsigned(h), HQR_THREADS, smem, st>>>(
-            yr, yi, rows * l, int(rows), int(l), sketch_per_freq);
+            yr, yi, rows * l, int(rows), int(l), sketch_per_freq, 0);
       } else {
         TP_SET_SMEM(householder_qr_kernel<8>, smem);
         householder_qr_kernel<8><<<unsigned(h), HQR_THREADS, smem, st>>>(
-            yr, yi, rows * l, int(rows), int(l), sketch_per_freq);
+            yr, yi, rows * l, int(rows), int(l), sketch_per_freq, 0);
       }
       return launch_status("householder_qr_kernel");
     }

@@ -30,6 +30,8 @@
 #include "jacobi_rot.cuh"
 
 namespace tp {
+int householder_orth_launch(float* yr, float* yi, int64_t sY, int p, int l, int64_t batch,
+                            bool keep_phase, cudaStream_t st);
 namespace {
 using jrot::rotation;
 
@@ -437,13 +439,15 @@ int jacobi_double_launch(double* gr, double* gi, int64_t sG, double* vr, double*
 int hybrid_svd(const float* xr, const float* xi, int64_t sX, int64_t ldx, bool conj, int p, int q,
                int batch, float* fr, float* fi, float* qr, float* qi, float* qsig, double* tr,
                double* ti, double* gr, double* gi, double* wr, double* wi, double* sig,
-               const int* real_flags, int max_sweeps, int32_t* status, cudaStream_t st) {
+               const int* real_flags, int max_sweeps, int32_t* status, cudaStream_t st,
+               bool polish) {
   int rc;
   const int64_t pq = int64_t(p) * q, qq = int64_t(q) * q;
-  // 1. float32 sweeps (a cluster of singular values at the float32 rounding
-  //    floor may stall here; step 4 decides convergence)
+  // 1. float32 sweeps (with the polish, a cluster of singular values at the
+  //    float32 rounding floor may stall here and step 4 decides convergence;
+  //    without it this step does)
   if ((rc = jacobi_launch<float>(fr, fi, pq, qr, qi, qq, qsig, p, q, batch, max_sweeps, real_flags,
-                                 nullptr, JAC_INIT_V, st)))
+                                 polish ? nullptr : status, JAC_INIT_V, st)))
     return rc;
   {
     KernelScope ks("svd_refine", st);
@@ -460,9 +464,10 @@ int hybrid_svd(const float* xr, const float* xi, int64_t sX, int64_t ldx, bool c
   //    orthogonal to float32 accuracy each sweep squares the residual, so two
   //    or three sweeps suffice, more only for clusters of singular values at
   //    the float32 rounding floor (rank-deficient input); the sweep cap and
-  //    TP_DEV_NOCONV apply here
-  return jacobi_launch<double>(gr, gi, pq, wr, wi, qq, sig, p, q, batch, max_sweeps, real_flags,
-                               status, JAC_NORMALIZE, st);
+  //    TP_DEV_NOCONV apply here.  Without the polish: no sweeps, only the
+  //    column norms (singular values) and unit columns of G.
+  return jacobi_launch<double>(gr, gi, pq, wr, wi, qq, sig, p, q, batch, polish ? max_sweeps : 0,
+                               real_flags, polish ? status : nullptr, JAC_NORMALIZE, st);
 }
 
 size_t tsvd_ws(int64_t n1, int64_t n2, int64_t n3) {
@@ -527,8 +532,11 @@ int tsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, float* U, float
   note_launches(1);
   if ((rc = launch_status("svd_prep"))) return rc;
   const int sweeps = (opts && opts->max_sweeps > 0) ? opts->max_sweeps : 30;
+  // slices of at most 256 x 96: no float64 sweeps; the vectors of G are
+  // re-orthonormalised by a Householder QR in descending order instead
+  const bool fast = p <= 256 && m <= 96;
   if ((rc = hybrid_svd(Xr, Xi, n1 * n2, n1, transpose, int(p), int(m), int(h), Fr, Fi, Qr, Qi, fsig,
-                       Tr, Ti, Gr, Gi, Wr, Wi, sig, flags, sweeps, status, st)))
+                       Tr, Ti, Gr, Gi, Wr, Wi, sig, flags, sweeps, status, st, !fast)))
     return rc;
   {
     KernelScope ks("svd_factors", st);
@@ -542,6 +550,17 @@ int tsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, float* U, float
           Wr, Wi, m * m, m, Gr, Gi, p * m, p, sig, int(m), n1, n2, int(m), Ur, Ui, Sr, Si, Vr, Vi);
   }
   if ((rc = launch_status("write_factors_kernel"))) return rc;
+  if (fast) {
+    // the G side (U when n1 >= n2, else V), sorted by descending singular
+    // value: its float32-converged columns are orthogonal to about
+    // u32 s_1 / (s_a s_b) -- loose only where s is small, and arbitrary for a
+    // cluster at the rounding floor (rank-deficient input); the QR keeps the
+    // leading columns and completes the rest to an orthonormal set
+    const int64_t rows = transpose ? n2 : n1;
+    if ((rc = householder_orth_launch(transpose ? Vr : Ur, transpose ? Vi : Ui, rows * m,
+                                      int(rows), int(m), h, true, st)))
+      return rc;
+  }
   if ((rc = launch_irdft(Ur, Ui, n1 * m, n1 * m, n3, U, st))) return rc;
   if ((rc = launch_irdft(Sr, Si, m * m, m * m, n3, S, st))) return rc;
   return launch_irdft(Vr, Vi, n2 * m, n2 * m, n3, V, st);

@@ -39,7 +39,8 @@ int svt_batched_run(int ntens, const tp_tensor_desc* d, int iters, double rho, d
 int hybrid_svd(const float* xr, const float* xi, int64_t sX, int64_t ldx, bool conj, int p, int q,
                int batch, float* fr, float* fi, float* qr, float* qi, float* qsig, double* tr,
                double* ti, double* gr, double* gi, double* wr, double* wi, double* sig,
-               const int* real_flags, int max_sweeps, int32_t* status, cudaStream_t st);
+               const int* real_flags, int max_sweeps, int32_t* status, cudaStream_t st,
+               bool polish = true);
 
 namespace {
 
