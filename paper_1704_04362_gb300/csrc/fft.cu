@@ -13,19 +13,24 @@
 // the Hermitian-completed spectra the same way and runs the forward FFT on
 // the conjugate.
 //
-// A block of 1024 threads owns 2P consecutive tubes (P packed sequences,
+// A block of 512 (forward) or 1024 (inverse) threads owns 2P consecutive tubes (P packed sequences,
 // P = 4 for n3 up to about 3000): the loads and stores move 8P-byte runs of
 // consecutive tubes, and every stage spreads the P N / R butterflies of all
 // sequences over all threads (out of place between two shared buffers, one
-// barrier per stage), so that a block keeps 32 warps busy instead of one
-// warp per sequence.  The grid is persistent over groups of tubes.
+// barrier per stage), so that a block keeps 16 or 32 warps busy instead of
+// one warp per sequence.  The grid is persistent over groups of tubes; the
+// forward transform loads the next group into registers (32 values a
+// thread) before transforming the current one, which hides the loads when
+// a long tube leaves room for one block per SM.
 #include "tp_internal.cuh"
 
 namespace tp {
 namespace {
 
-constexpr int FFT_THREADS = 1024;
+constexpr int FFT_THREADS = 512;        // forward: room for the prefetch registers
+constexpr int FFT_INV_THREADS = 1024;
 constexpr int FFT_P_MAX = 4;
+constexpr int FFT_PF = 32;   // prefetched input values per thread
 constexpr int MAX_STAGES = 16;
 
 struct FftPlan {
@@ -167,16 +172,45 @@ __global__ void __launch_bounds__(FFT_THREADS) fft_fwd_kernel(const float* __res
   float2* b1 = b0 + P * N;
   build_tw(tw, N);
   __syncthreads();
-  for (int64_t r0 = int64_t(blockIdx.x) * G; r0 < rows; r0 += int64_t(gridDim.x) * G) {
+  // a group that fits FFT_PF values per thread is loaded into registers one
+  // group ahead (issued before the current group's transform, so that the
+  // loads' latency hides behind it: one block per SM when n3 is long)
+  const bool pf = G * N <= FFT_PF * FFT_THREADS;
+  const int64_t gstride = int64_t(gridDim.x) * G;
+  float nxt[FFT_PF];
+  auto fetch = [&](int64_t rg) {
+#pragma unroll
+    for (int u = 0; u < FFT_PF; ++u) {
+      const int e = int(threadIdx.x) + u * FFT_THREADS;
+      const int t = e / G, c = e - t * G;
+      const int64_t r = rg + c;
+      nxt[u] = (e < G * N && r < rows) ? __ldg(X + r + rows * int64_t(t)) : 0.f;
+    }
+  };
+  if (pf && int64_t(blockIdx.x) * G < rows) fetch(int64_t(blockIdx.x) * G);
+  for (int64_t r0 = int64_t(blockIdx.x) * G; r0 < rows; r0 += gstride) {
     // tube c of the group goes to the real (c even) or imaginary (c odd)
     // part of sequence c/2; consecutive threads read consecutive tubes
-    for (int e = threadIdx.x; e < G * N; e += blockDim.x) {
-      const int t = e / G, c = e - t * G;
-      const int64_t r = r0 + c;
-      const float x = r < rows ? __ldg(X + r + rows * int64_t(t)) : 0.f;
-      reinterpret_cast<float*>(b0 + (c >> 1) * N + t)[c & 1] = x;
+    if (pf) {
+#pragma unroll
+      for (int u = 0; u < FFT_PF; ++u) {
+        const int e = int(threadIdx.x) + u * FFT_THREADS;
+        if (e < G * N) {
+          const int t = e / G, c = e - t * G;
+          reinterpret_cast<float*>(b0 + (c >> 1) * N + t)[c & 1] = nxt[u];
+        }
+      }
+      __syncthreads();
+      if (r0 + gstride < rows) fetch(r0 + gstride);
+    } else {
+      for (int e = threadIdx.x; e < G * N; e += blockDim.x) {
+        const int t = e / G, c = e - t * G;
+        const int64_t r = r0 + c;
+        const float x = r < rows ? __ldg(X + r + rows * int64_t(t)) : 0.f;
+        reinterpret_cast<float*>(b0 + (c >> 1) * N + t)[c & 1] = x;
+      }
+      __syncthreads();
     }
-    __syncthreads();
     const float2* Z = stockham_all(plan, tw, b0, b1, P);
     for (int e = threadIdx.x; e < G * h; e += blockDim.x) {
       const int k = e / G, c = e - k * G;
@@ -202,7 +236,7 @@ __global__ void __launch_bounds__(FFT_THREADS) fft_fwd_kernel(const float* __res
 
 // Inverse: half spectra in{re,im}[k*in_slice + r] to real tubes
 // out[r + rows*t] (imaginary parts of the k = 0 and k = n3/2 slices ignored).
-__global__ void __launch_bounds__(FFT_THREADS) fft_inv_kernel(const float* __restrict__ ire,
+__global__ void __launch_bounds__(FFT_INV_THREADS) fft_inv_kernel(const float* __restrict__ ire,
                                                               const float* __restrict__ iim,
                                                               int64_t rows, int64_t in_slice,
                                                               FftPlan plan, int P,
@@ -330,7 +364,7 @@ int launch_fft_inv(const float* ire, const float* iim, int64_t rows, int64_t in_
   TP_SET_SMEM(fft_inv_kernel, smem);
   {
     KernelScope ks("fft_inv", st);
-    fft_inv_kernel<<<fft_grid(rows, P, smem), FFT_THREADS, smem, st>>>(ire, iim, rows, in_slice,
+    fft_inv_kernel<<<fft_grid(rows, P, smem), FFT_INV_THREADS, smem, st>>>(ire, iim, rows, in_slice,
                                                                       plan, P, out);
   }
   return launch_status("fft_inv_kernel");

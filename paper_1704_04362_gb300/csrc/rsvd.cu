@@ -256,6 +256,32 @@ __device__ __forceinline__ float hqr_sum(float v) {
   return v;
 }
 
+// Two (four) warp sums at once by exchanging halves of the values at the
+// first (two) levels instead of reducing each value separately: 5 + 2
+// broadcasts (6 + 4) shuffles instead of 10 (20); every lane gets every sum.
+__device__ __forceinline__ void hqr_sum2(float& a, float& b, int lane) {
+  const bool up = lane & 16;
+  float k = up ? b : a;
+  k += __shfl_xor_sync(0xffffffffu, up ? a : b, 16);   // a in the low half, b in the high
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+  a = __shfl_sync(0xffffffffu, k, 0);
+  b = __shfl_sync(0xffffffffu, k, 16);
+}
+__device__ __forceinline__ void hqr_sum4(float (&d)[4], int lane) {
+  const bool up = lane & 16, mid = lane & 8;
+  float k0 = up ? d[2] : d[0], k1 = up ? d[3] : d[1];
+  k0 += __shfl_xor_sync(0xffffffffu, up ? d[0] : d[2], 16);
+  k1 += __shfl_xor_sync(0xffffffffu, up ? d[1] : d[3], 16);
+  float k = mid ? k1 : k0;
+  k += __shfl_xor_sync(0xffffffffu, mid ? k0 : k1, 8);
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+  // lanes 0-7 hold sum 0, 8-15 sum 1, 16-23 sum 2, 24-31 sum 3
+#pragma unroll
+  for (int u = 0; u < 4; ++u) d[u] = __shfl_sync(0xffffffffu, k, 8 * u);
+}
+
 // Reflector of column a (rows j .. p-1), one warp: rows j+1.. become v,
 // row j becomes beta; returns tau (0 when the column is already beta e_j with
 // beta real).
@@ -284,18 +310,26 @@ __device__ float2 hqr_reflector(float2* a, int j, int p, int lane) {
 }
 
 // v_j of column a into registers: row r = lane + 32 t, 1 at row j, 0 above.
-template <int RPL>
+// FULL: p == 32 RPL, so that every lane's rows exist; rows above j then
+// need no predicate (v is zero there, so they are read and rewritten
+// unchanged).
+template <int RPL, bool FULL>
 __device__ __forceinline__ void hqr_load_v(const float2* a, int j, int p, int lane,
                                            float2 (&v)[RPL]) {
 #pragma unroll
   for (int t = 0; t < RPL; ++t) {
     const int r = lane + 32 * t;
-    v[t] = (r <= j || r >= p) ? make_float2(r == j ? 1.f : 0.f, 0.f) : a[r];
+    if (FULL) {
+      const float2 x = a[r];
+      v[t] = r > j ? x : make_float2(r == j ? 1.f : 0.f, 0.f);
+    } else {
+      v[t] = (r <= j || r >= p) ? make_float2(r == j ? 1.f : 0.f, 0.f) : a[r];
+    }
   }
 }
 
 // c <- c - f v (v^H c) on rows j .. p-1 (f = conj(tau) applies H^H, f = tau H)
-template <int RPL>
+template <int RPL, bool FULL>
 __device__ __forceinline__ void hqr_apply(const float2 (&v)[RPL], float2* c, int j, int p,
                                           float2 f, int lane) {
   float2 x[RPL];
@@ -303,24 +337,23 @@ __device__ __forceinline__ void hqr_apply(const float2 (&v)[RPL], float2* c, int
 #pragma unroll
   for (int t = 0; t < RPL; ++t) {
     const int r = lane + 32 * t;
-    x[t] = (r >= j && r < p) ? c[r] : make_float2(0.f, 0.f);
+    x[t] = (FULL || (r >= j && r < p)) ? c[r] : make_float2(0.f, 0.f);
     dr = fmaf(v[t].x, x[t].x, fmaf(v[t].y, x[t].y, dr));    // Re(conj(v) x)
     di = fmaf(v[t].x, x[t].y, fmaf(-v[t].y, x[t].x, di));   // Im(conj(v) x)
   }
-  dr = hqr_sum(dr);
-  di = hqr_sum(di);
+  hqr_sum2(dr, di, lane);
   const float gr = f.x * dr - f.y * di, gi = f.x * di + f.y * dr;
 #pragma unroll
   for (int t = 0; t < RPL; ++t) {
     const int r = lane + 32 * t;
-    if (r >= j && r < p)
+    if (FULL || (r >= j && r < p))
       c[r] = make_float2(x[t].x - (v[t].x * gr - v[t].y * gi),
                          x[t].y - (v[t].x * gi + v[t].y * gr));
   }
 }
 
 // hqr_apply on two columns at once (their sums interleave in the shuffles)
-template <int RPL>
+template <int RPL, bool FULL>
 __device__ __forceinline__ void hqr_apply2(const float2 (&v)[RPL], float2* c0, float2* c1, int j,
                                            int p, float2 f, int lane) {
   float2 x0[RPL], x1[RPL];
@@ -328,7 +361,7 @@ __device__ __forceinline__ void hqr_apply2(const float2 (&v)[RPL], float2* c0, f
 #pragma unroll
   for (int t = 0; t < RPL; ++t) {
     const int r = lane + 32 * t;
-    const bool in = r >= j && r < p;
+    const bool in = FULL || (r >= j && r < p);
     x0[t] = in ? c0[r] : make_float2(0.f, 0.f);
     x1[t] = in ? c1[r] : make_float2(0.f, 0.f);
     d[0] = fmaf(v[t].x, x0[t].x, fmaf(v[t].y, x0[t].y, d[0]));
@@ -336,16 +369,13 @@ __device__ __forceinline__ void hqr_apply2(const float2 (&v)[RPL], float2* c0, f
     d[2] = fmaf(v[t].x, x1[t].x, fmaf(v[t].y, x1[t].y, d[2]));
     d[3] = fmaf(v[t].x, x1[t].y, fmaf(-v[t].y, x1[t].x, d[3]));
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-    for (int u = 0; u < 4; ++u) d[u] += __shfl_xor_sync(0xffffffffu, d[u], o);
+  hqr_sum4(d, lane);
   const float g0r = f.x * d[0] - f.y * d[1], g0i = f.x * d[1] + f.y * d[0];
   const float g1r = f.x * d[2] - f.y * d[3], g1i = f.x * d[3] + f.y * d[2];
 #pragma unroll
   for (int t = 0; t < RPL; ++t) {
     const int r = lane + 32 * t;
-    if (r >= j && r < p) {
+    if (FULL || (r >= j && r < p)) {
       c0[r] = make_float2(x0[t].x - (v[t].x * g0r - v[t].y * g0i),
                           x0[t].y - (v[t].x * g0i + v[t].y * g0r));
       c1[r] = make_float2(x1[t].x - (v[t].x * g1r - v[t].y * g1i),
@@ -375,7 +405,7 @@ __device__ __forceinline__ void hqr_materialize(float2* a, int k, int p, float2 
 // keep_phase: column j of Q is multiplied by sign(R(j, j)) (R's diagonal is
 // real), so that for Y with nearly orthonormal columns Q(:, j) stays close
 // to Y(:, j) instead of possibly flipping its sign.
-template <int RPL>
+template <int RPL, bool FULL>
 __global__ void __launch_bounds__(HQR_THREADS) householder_qr_kernel(float* y_re, float* y_im,
                                                                      int64_t sY, int p, int lfull,
                                                                      const int32_t* lcols,
@@ -404,13 +434,13 @@ __global__ void __launch_bounds__(HQR_THREADS) householder_qr_kernel(float* y_re
   for (int j = 0; j + 1 < l; ++j) {
     const float2 tau = tau_s[j];
     float2 v[RPL];
-    hqr_load_v<RPL>(A + int64_t(j) * p, j, p, lane, v);
+    hqr_load_v<RPL, FULL>(A + int64_t(j) * p, j, p, lane, v);
     const bool live = tau.x != 0.f || tau.y != 0.f;
     const float2 f = make_float2(tau.x, -tau.y);
     int k = j + 1 + warp;
     if (warp == 0) {   // look-ahead: column j + 1 first, then its reflector
       float2* c = A + int64_t(k) * p;
-      if (live) hqr_apply<RPL>(v, c, j, p, f, lane);
+      if (live) hqr_apply<RPL, FULL>(v, c, j, p, f, lane);
       __syncwarp();
       const float2 t = hqr_reflector(c, k, p, lane);
       if (lane == 0) {
@@ -421,8 +451,8 @@ __global__ void __launch_bounds__(HQR_THREADS) householder_qr_kernel(float* y_re
     }
     if (live) {
       for (; k + HQR_WARPS < l; k += 2 * HQR_WARPS)
-        hqr_apply2<RPL>(v, A + int64_t(k) * p, A + int64_t(k + HQR_WARPS) * p, j, p, f, lane);
-      if (k < l) hqr_apply<RPL>(v, A + int64_t(k) * p, j, p, f, lane);
+        hqr_apply2<RPL, FULL>(v, A + int64_t(k) * p, A + int64_t(k + HQR_WARPS) * p, j, p, f, lane);
+      if (k < l) hqr_apply<RPL, FULL>(v, A + int64_t(k) * p, j, p, f, lane);
     }
     __syncthreads();
   }
@@ -432,7 +462,7 @@ __global__ void __launch_bounds__(HQR_THREADS) householder_qr_kernel(float* y_re
   for (int i = l - 2; i >= 0; --i) {
     const float2 tau = tau_s[i];
     float2 v[RPL];
-    hqr_load_v<RPL>(A + int64_t(i) * p, i, p, lane, v);
+    hqr_load_v<RPL, FULL>(A + int64_t(i) * p, i, p, lane, v);
     int k = i + 1 + warp;
     if (warp == 0) {
       hqr_materialize(A + int64_t(k) * p, k, p, tau_s[k], lane);
@@ -440,8 +470,8 @@ __global__ void __launch_bounds__(HQR_THREADS) householder_qr_kernel(float* y_re
     }
     if (tau.x != 0.f || tau.y != 0.f) {
       for (; k + HQR_WARPS < l; k += 2 * HQR_WARPS)
-        hqr_apply2<RPL>(v, A + int64_t(k) * p, A + int64_t(k + HQR_WARPS) * p, i, p, tau, lane);
-      if (k < l) hqr_apply<RPL>(v, A + int64_t(k) * p, i, p, tau, lane);
+        hqr_apply2<RPL, FULL>(v, A + int64_t(k) * p, A + int64_t(k + HQR_WARPS) * p, i, p, tau, lane);
+      if (k < l) hqr_apply<RPL, FULL>(v, A + int64_t(k) * p, i, p, tau, lane);
     }
     __syncthreads();
   }
@@ -612,127 +642,132 @@ __device__ void tridiag_form_q(const float2* G, float2* W, int l, int ls, const 
   }
 }
 
-// A plane rotation of the QL chase: rotation i mixes columns i and i + 1;
-// code = i, or -(i + 1) for the first rotation of a chase.
+// Eigenvalues of the real symmetric tridiagonal (d, e) -- d[i * stride],
+// e[i * stride], e[l-1] = 0 -- by the implicit QL algorithm with
+// Wilkinson's shift from the leading 2 x 2 (Bowdler, Martin, Reinsch and
+// Wilkinson, 1968), run by one thread: each chase goes from the bottom of
+// the unreduced block to its top, deflating off-diagonals below
+// FLT_EPSILON (|d_m| + |d_m+1|), and its plane rotations are appended to
+// log (at most cap; rotation i mixes columns i and i + 1, code i, or
+// -(i + 1) for a chase's first rotation).  T is first scaled by a power of
+// two to a largest entry near 1 (exact; only the eigenvectors are used), so
+// that the squares stay in range and a plain square root and one
+// reciprocal form each rotation.  Returns false if an eigenvalue took more
+// than max_iter chases (its off-diagonal is then dropped) or the log was
+// full (the chase stops there); *count gets the log's length.
 struct QlRot {
   int code;
   float c, s;
 };
 
-// Eigenvalues (d) and eigenvectors (columns of W <- W S) of the real
-// symmetric tridiagonal (d, e) by the implicit QL algorithm with Wilkinson's
-// shift from the leading 2 x 2 (Bowdler, Martin, Reinsch and Wilkinson,
-// 1968): each chase runs from the bottom of the unreduced block up to its
-// top, deflating off-diagonals below FLT_EPSILON (|d_m| + |d_m+1|).  The
-// chase is serial: thread 0 runs it and logs its rotations in `log` (cap
-// entries); the block then replays the log on W, a thread per row and
-// component, carrying the column the next rotation of the chase reuses in a
-// register; chases continue until done.  At most max_iter chases per
-// eigenvalue (then its off-diagonal is dropped and false is returned).
-__device__ bool tridiag_ql(float* d, float* e, float2* W, int l, int ls, QlRot* log, int cap,
-                           int max_iter) {
-  __shared__ int ql_cnt, ql_done, ql_ok;
-  int l0 = 0, it = 0;   // thread 0's state across flushes
+__device__ bool ql_chase(float* __restrict__ d, float* __restrict__ e, int stride, int l,
+                         QlRot* __restrict__ log, int cap, int max_iter, int* count) {
+#define D(i) d[(i) * stride]
+#define E(i) e[(i) * stride]
+  float mx = 0.f;
+  for (int i = 0; i < l; ++i) mx = fmaxf(mx, fmaxf(fabsf(D(i)), fabsf(E(i))));
+  if (mx > 0.f && isfinite(mx)) {
+    int ex;
+    frexpf(mx, &ex);
+    for (int i = 0; i < l; ++i) {
+      D(i) = ldexpf(D(i), -ex);
+      E(i) = ldexpf(E(i), -ex);
+    }
+  }
   bool ok = true;
-  if (threadIdx.x == 0) {
-    // scale T by a power of two to a largest entry near 1 (exact; only the
-    // eigenvectors are used), so that the squares below neither overflow
-    // nor lose range
-    float mx = 0.f;
-    for (int i = 0; i < l; ++i) mx = fmaxf(mx, fmaxf(fabsf(d[i]), i + 1 < l ? fabsf(e[i]) : 0.f));
-    if (mx > 0.f && isfinite(mx)) {
-      int ex;
-      frexpf(mx, &ex);
-      for (int i = 0; i < l; ++i) {
-        d[i] = ldexpf(d[i], -ex);
-        e[i] = ldexpf(e[i], -ex);
+  int cnt = 0, l0 = 0, it = 0;
+  while (l0 < l) {
+    int m = l0;
+    for (; m + 1 < l; ++m) {
+      const float dd = fabsf(D(m)) + fabsf(D(m + 1));
+      if (fabsf(E(m)) <= FLT_EPSILON * dd) break;
+    }
+    if (m == l0) {
+      ++l0;
+      it = 0;
+      continue;
+    }
+    if (cnt + (m - l0) > cap || ++it > max_iter) {
+      ok = false;
+      E(l0) = 0.f;
+      continue;
+    }
+    float g = (D(l0 + 1) - D(l0)) / (2.f * E(l0));
+    const float r0 = hypotf(g, 1.f);
+    g = D(m) - D(l0) + E(l0) / (g + copysignf(r0, g));
+    float s = 1.f, c = 1.f, pp = 0.f;
+    float dn = D(m);   // d[i + 1] of the step below, carried
+    bool early = false;
+    // e[i] and d[i] of the next step are loaded a step ahead (a step writes
+    // only index i + 1), off the chain of dependent arithmetic
+    float ei_n = E(m - 1), di_n = D(m - 1);
+    for (int i = m - 1; i >= l0; --i) {
+      const float ei = ei_n, di = di_n;
+      if (i > l0) {
+        ei_n = E(i - 1);
+        di_n = D(i - 1);
       }
+      const float f = s * ei, b = c * ei;
+      float r = sqrtf(fmaf(f, f, g * g));
+      E(i + 1) = r;
+      if (r == 0.f) {   // the chase splits: restart from the new block
+        D(i + 1) = dn - pp;
+        E(m) = 0.f;
+        early = true;
+        break;
+      }
+      const float inv = __frcp_rn(r);
+      s = f * inv;
+      c = g * inv;
+      g = dn - pp;
+      r = fmaf(di - g, s, 2.f * c * b);
+      pp = s * r;
+      D(i + 1) = g + pp;
+      g = fmaf(c, r, -b);
+      dn = di;
+      log[cnt++] = QlRot{i == m - 1 ? -(i + 1) : i, c, s};
+    }
+    if (!early) {
+      D(l0) = D(l0) - pp;
+      E(l0) = g;
+      E(m) = 0.f;
     }
   }
-  for (;;) {
-    if (threadIdx.x == 0) {
-      int cnt = 0;
-      while (l0 < l) {
-        int m = l0;
-        for (; m + 1 < l; ++m) {
-          const float dd = fabsf(d[m]) + fabsf(d[m + 1]);
-          if (fabsf(e[m]) <= FLT_EPSILON * dd) break;
-        }
-        if (m == l0) {
-          ++l0;
-          it = 0;
-          continue;
-        }
-        if (cnt + (m - l0) > cap) break;   // replay the log first
-        if (++it > max_iter) {
-          ok = false;
-          e[l0] = 0.f;
-          continue;
-        }
-        float g = (d[l0 + 1] - d[l0]) / (2.f * e[l0]);
-        const float r0 = hypotf(g, 1.f);
-        g = d[m] - d[l0] + e[l0] / (g + copysignf(r0, g));
-        float s = 1.f, c = 1.f, pp = 0.f;
-        float dn = d[m];   // d[i + 1] of the step below, carried
-        bool early = false;
-        for (int i = m - 1; i >= l0; --i) {
-          const float ei = e[i], di = d[i];
-          const float f = s * ei, b = c * ei;
-          float r = sqrtf(fmaf(f, f, g * g));
-          e[i + 1] = r;
-          if (r == 0.f) {   // the chase splits: restart from the new block
-            d[i + 1] = dn - pp;
-            e[m] = 0.f;
-            early = true;
-            break;
-          }
-          const float inv = __frcp_rn(r);
-          s = f * inv;
-          c = g * inv;
-          g = dn - pp;
-          r = fmaf(di - g, s, 2.f * c * b);
-          pp = s * r;
-          d[i + 1] = g + pp;
-          g = fmaf(c, r, -b);
-          dn = di;
-          log[cnt++] = QlRot{i == m - 1 ? -(i + 1) : i, c, s};
-        }
-        if (!early) {
-          d[l0] -= pp;
-          e[l0] = g;
-          e[m] = 0.f;
-        }
-      }
-      ql_cnt = cnt;
-      ql_done = l0 >= l;
-      ql_ok = ok;
-    }
-    __syncthreads();
-    const int cnt = ql_cnt, done = ql_done;
-    if (int(threadIdx.x) < 2 * l) {
-      // W(r, i), component t & 1 of row r = t >> 1, at float index 2 ls i + t
-      float* z = reinterpret_cast<float*>(W) + threadIdx.x;
-      const int cs = 2 * ls;
-      int prev = -1;
-      float carry = 0.f;
-      for (int q = 0; q < cnt; ++q) {
-        const QlRot R = log[q];
-        const int i = R.code < 0 ? -R.code - 1 : R.code;
-        if (R.code < 0) {
-          if (prev >= 0) z[cs * prev] = carry;
-          carry = z[cs * (i + 1)];
-        }
-        const float zi = z[cs * i];
-        z[cs * (i + 1)] = fmaf(R.s, zi, R.c * carry);
-        carry = fmaf(R.c, zi, -R.s * carry);
-        prev = i;
-      }
+#undef D
+#undef E
+  *count = cnt;
+  return ok;
+}
+
+// W <- W S for the logged rotations (W column-major, column stride ls), a
+// thread per row and component (threads 0 .. 2l-1), one chunk of the log
+// (in shared memory) at a time: the column the next rotation of a chase
+// reuses is carried in a register (prev, carry) from chunk to chunk, and
+// ql_replay_end stores the last one.
+__device__ __forceinline__ void ql_replay(float2* W, int l, int ls,
+                                          const QlRot* __restrict__ log, int cnt, int& prev,
+                                          float& carry) {
+  if (int(threadIdx.x) >= 2 * l) return;
+  // W(r, i), component t & 1 of row r = t >> 1, at float index 2 ls i + t
+  float* __restrict__ z = reinterpret_cast<float*>(W) + threadIdx.x;
+  const int cs = 2 * ls;
+#pragma unroll 4
+  for (int q = 0; q < cnt; ++q) {
+    const QlRot R = log[q];
+    const int i = R.code < 0 ? -R.code - 1 : R.code;
+    if (R.code < 0) {   // a new chase: the previous one's last column first
       if (prev >= 0) z[cs * prev] = carry;
+      carry = z[cs * (i + 1)];
     }
-    __syncthreads();
-    if (done) break;
+    const float zi = z[cs * i];
+    z[cs * (i + 1)] = fmaf(R.s, zi, R.c * carry);
+    carry = fmaf(R.c, zi, -R.s * carry);
+    prev = i;
   }
-  return ql_ok != 0;
+}
+__device__ __forceinline__ void ql_replay_end(float2* W, int l, int ls, int prev, float carry) {
+  if (int(threadIdx.x) < 2 * l && prev >= 0)
+    reinterpret_cast<float*>(W)[threadIdx.x + 2 * ls * prev] = carry;
 }
 
 // Core SVD through the l x l Gram of B^H (n2 x l, read from global memory,
@@ -750,27 +785,22 @@ __device__ bool tridiag_ql(float* d, float* e, float2* W, int l, int ls, QlRot* 
 constexpr int EIG_THREADS = 256;
 constexpr int EIG_CHUNK = 32;   // rows of B^H staged per step of the Gram
 
-__global__ void __launch_bounds__(EIG_THREADS) core_eig_kernel(
-    const float* __restrict__ bh_re, const float* __restrict__ bh_im, int p, int l, int k,
-    int max_sweeps, float* __restrict__ wkr, float* __restrict__ wki, float* __restrict__ vkr,
-    float* __restrict__ vki, float* __restrict__ sr_out, float* __restrict__ si_out,
-    float2* __restrict__ pscratch, int32_t* status) {
+__global__ void __launch_bounds__(EIG_THREADS) core_tridiag_kernel(
+    const float* __restrict__ bh_re, const float* __restrict__ bh_im, int p, int l,
+    float* __restrict__ d_out, float* __restrict__ e_out, float2* __restrict__ z_out) {
   extern __shared__ double dyn[];
   const int ls = l | 1;                                     // odd stride
   const int L2 = l * ls;
-  double* sig2 = dyn;                                       // l: ||B^H w_j||^2
-  float2* Gf = reinterpret_cast<float2*>(dyn + ((l + 1) & ~1));   // l x l Gram (row stride ls)
-  float2* Wf = Gf + L2;                                     // l x l eigenvectors (column stride ls)
+  float2* Gf = reinterpret_cast<float2*>(dyn);              // l x l Gram (row stride ls)
+  float2* Wf = Gf + L2;                                     // l x l Q (column stride ls)
   float2* tau = Wf + L2;                                    // l: reflectors of the reduction
   float2* vbuf = tau + l;                                   // l
   float2* ybuf = vbuf + l;                                  // l
   float* dv = reinterpret_cast<float*>(ybuf + l);           // l: tridiagonal
   float* ev = dv + l;                                       // l
-  __shared__ int order[128];
   const int64_t f = blockIdx.x;
   const float* br = bh_re + f * int64_t(p) * l;
   const float* bi = bh_im + f * int64_t(p) * l;
-  float2* P = pscratch + f * int64_t(p) * l;                // B^H W (p x l), column-major
   // G(a, b) = sum_r conj(B^H(r, a)) B^H(r, b), a <= b, Hermitian fill: rows of
   // B^H staged EIG_CHUNK at a time (in W's space, before W is set)
   float2* chunk = Wf;                                       // EIG_CHUNK x l, row stride l
@@ -817,32 +847,113 @@ __global__ void __launch_bounds__(EIG_THREADS) core_eig_kernel(
     }
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < l; j += blockDim.x) sig2[j] = 0.0;
   hermitian_tridiag(Gf, l, ls, dv, ev, tau, vbuf, ybuf);
   tridiag_form_q(Gf, Wf, l, ls, tau);
-  // the reflectors are in W now: G's space takes the rotation log
-  const int cap = int(size_t(L2) * sizeof(float2) / sizeof(QlRot));
-  const bool conv = tridiag_ql(dv, ev, Wf, l, ls, reinterpret_cast<QlRot*>(Gf), cap, max_sweeps);
-  if (!conv && threadIdx.x == 0 && status) atomicOr(status, TP_DEV_NOCONV);
-  __syncthreads();
-  // P = B^H W and s_j^2 = ||P(:, j)||^2: a warp per column, lanes over rows
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-  for (int j = warp; j < l; j += nwarp) {
-    const float2* wj = Wf + j * ls;
-    double acc = 0.0;
-    for (int r = lane; r < p; r += 32) {
-      float pr = 0.f, pim = 0.f;
-      for (int m = 0; m < l; ++m) {
-        const float bre = __ldg(br + r + int64_t(p) * m), bim = __ldg(bi + r + int64_t(p) * m);
-        const float2 w = wj[m];
-        pr = fmaf(bre, w.x, fmaf(-bim, w.y, pr));
-        pim = fmaf(bre, w.y, fmaf(bim, w.x, pim));
-      }
-      P[r + int64_t(p) * j] = make_float2(pr, pim);
-      acc += double(pr) * pr + double(pim) * pim;
+  for (int i = threadIdx.x; i < l; i += blockDim.x) {
+    d_out[f * l + i] = dv[i];
+    e_out[f * l + i] = ev[i];
+  }
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int c = e / l, r = e - c * l;
+    z_out[f * l * l + e] = Wf[c * ls + r];
+  }
+}
+
+// The QL chase of every slice in a block of its own (lane 0 chases, d and e
+// in shared memory), away from the blocks that form and use the
+// eigenvectors: the chases of different slices run concurrently on every
+// SM, and no lane waits on another slice's chase.
+constexpr int QL_THREADS = 32;
+constexpr int QL_LOG_PER_L = 100;   // log capacity per slice: 100 l rotations
+
+__global__ void __launch_bounds__(QL_THREADS) core_ql_kernel(
+    const float* __restrict__ d_in, const float* __restrict__ e_in, int l,
+    QlRot* __restrict__ log, int32_t* __restrict__ log_count, int max_iter, int32_t* status) {
+  extern __shared__ float qsm[];   // d (l), e (l)
+  const int64_t f = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  float* d = qsm;
+  float* e = qsm + l;
+  for (int i = 0; i < l; ++i) {
+    d[i] = d_in[f * l + i];
+    e[i] = i + 1 < l ? e_in[f * l + i] : 0.f;
+  }
+  const int cap = QL_LOG_PER_L * l;
+  int cnt = 0;
+  const bool ok = ql_chase(d, e, 1, l, log + f * cap, cap, max_iter, &cnt);
+  log_count[f] = cnt;
+  if (!ok && status) atomicOr(status, TP_DEV_NOCONV);
+}
+
+constexpr int FIN_RB = 64;   // rows of B^H staged per step of P = B^H W
+
+__global__ void __launch_bounds__(EIG_THREADS) core_finish_kernel(
+    const float* __restrict__ bh_re, const float* __restrict__ bh_im, int p, int l, int k,
+    const float2* __restrict__ z_in, const QlRot* __restrict__ log,
+    const int32_t* __restrict__ log_count, float* __restrict__ wkr, float* __restrict__ wki,
+    float* __restrict__ vkr, float* __restrict__ vki, float* __restrict__ sr_out,
+    float* __restrict__ si_out, float2* __restrict__ pscratch) {
+  extern __shared__ double dyn[];
+  const int ls = l | 1;
+  double* sig2 = dyn;                                       // l: ||B^H w_j||^2
+  float2* Wf = reinterpret_cast<float2*>(dyn + ((l + 1) & ~1));   // l x l (column stride ls)
+  float2* stage = Wf + size_t(l) * ls;                      // FIN_RB x l: log chunks, rows of B^H
+  __shared__ int order[128];
+  const int64_t f = blockIdx.x;
+  const float* br = bh_re + f * int64_t(p) * l;
+  const float* bi = bh_im + f * int64_t(p) * l;
+  float2* P = pscratch + f * int64_t(p) * l;                // B^H W (p x l), column-major
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int c = e / l, r = e - c * l;
+    Wf[c * ls + r] = z_in[f * l * l + e];
+  }
+  for (int j = threadIdx.x; j < l; j += blockDim.x) sig2[j] = 0.0;
+  // replay the QL log on W, a chunk of it in shared memory at a time
+  {
+    QlRot* chunk = reinterpret_cast<QlRot*>(stage);
+    const int ccap = int(size_t(FIN_RB) * l * sizeof(float2) / sizeof(QlRot));
+    const QlRot* lg = log + f * int64_t(QL_LOG_PER_L) * l;
+    const int cnt = log_count[f];
+    int prev = -1;
+    float carry = 0.f;
+    for (int q0 = 0; q0 < cnt; q0 += ccap) {
+      const int nq = min(ccap, cnt - q0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < nq; e += blockDim.x) chunk[e] = lg[q0 + e];
+      __syncthreads();
+      ql_replay(Wf, l, ls, chunk, nq, prev, carry);
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) sig2[j] = acc;
+    ql_replay_end(Wf, l, ls, prev, carry);
+  }
+  // P = B^H W and s_j^2 = ||P(:, j)||^2, FIN_RB rows of B^H at a time in
+  // shared memory: a warp per column, lanes over rows
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (int r0 = 0; r0 < p; r0 += FIN_RB) {
+    const int nr = min(FIN_RB, p - r0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * l; e += blockDim.x) {
+      const int m = e / nr, rr = e - m * nr;
+      stage[m * FIN_RB + rr] = make_float2(__ldg(br + r0 + rr + int64_t(p) * m),
+                                           __ldg(bi + r0 + rr + int64_t(p) * m));
+    }
+    __syncthreads();
+    for (int j = warp; j < l; j += nwarp) {
+      const float2* wj = Wf + j * ls;
+      double acc = 0.0;
+      for (int rr = lane; rr < nr; rr += 32) {
+        float pr = 0.f, pim = 0.f;
+        for (int m = 0; m < l; ++m) {
+          const float2 b = stage[m * FIN_RB + rr];
+          const float2 w = wj[m];
+          pr = fmaf(b.x, w.x, fmaf(-b.y, w.y, pr));
+          pim = fmaf(b.x, w.y, fmaf(b.y, w.x, pim));
+        }
+        P[r0 + rr + int64_t(p) * j] = make_float2(pr, pim);
+        acc += double(pr) * pr + double(pim) * pim;
+      }
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) sig2[j] += acc;   // column j belongs to this warp in every chunk
+    }
   }
   __syncthreads();
   for (int j = threadIdx.x; j < l; j += blockDim.x) {
@@ -879,11 +990,13 @@ __global__ void __launch_bounds__(EIG_THREADS) core_eig_kernel(
   }
 }
 
-size_t core_eig_smem(int p, int l) {
-  (void)p;
-  const int ls = l | 1;
-  const size_t L2 = size_t(l) * ls;
-  return size_t((l + 1) & ~1) * 8 + 2 * L2 * 8 + size_t(l) * (3 * 8 + 2 * 4);
+size_t core_tridiag_smem(int l) {
+  const size_t L2 = size_t(l) * (l | 1);
+  return 2 * L2 * 8 + size_t(l) * (3 * 8 + 2 * 4);
+}
+size_t core_finish_smem(int l) {
+  const size_t L2 = size_t(l) * (l | 1);
+  return size_t((l + 1) & ~1) * 8 + L2 * 8 + size_t(FIN_RB) * l * 8;
 }
 
 // Sorts the l Jacobi singular triplets of every slice, keeps the top k and
@@ -979,6 +1092,29 @@ unsigned grid_for(int64_t n) {
   return unsigned(b);
 }
 
+// Launch of householder_qr_kernel with RPL = 2, 4 or 8 rows per lane (p
+// up to 64, 128, 256) and the predicate-free form when p fills the lanes.
+int launch_hqr(float* yr, float* yi, int64_t sY, int p, int l, const int32_t* lcols,
+               bool keep_phase, int64_t batch, cudaStream_t st) {
+  const size_t smem = size_t(p) * l * sizeof(float2);
+  const int kp = keep_phase ? 1 : 0;
+  const unsigned grid = unsigned(batch);
+  KernelScope ks("householder_qr", st);
+#define TP_HQR(R, F)                                                                      \
+  do {                                                                                    \
+    TP_SET_SMEM((householder_qr_kernel<R, F>), smem);                                     \
+    householder_qr_kernel<R, F><<<grid, HQR_THREADS, smem, st>>>(yr, yi, sY, p, l, lcols, kp); \
+  } while (0)
+  if (p == 64) TP_HQR(2, true);
+  else if (p < 64) TP_HQR(2, false);
+  else if (p == 128) TP_HQR(4, true);
+  else if (p < 128) TP_HQR(4, false);
+  else if (p == 256) TP_HQR(8, true);
+  else TP_HQR(8, false);
+#undef TP_HQR
+  return launch_status("householder_qr_kernel");
+}
+
 }  // namespace
 
 // K leading dimension of the split operand planes (16-byte rows for TMA).
@@ -998,23 +1134,7 @@ int householder_orth_launch(float* yr, float* yi, int64_t sY, int p, int l, int6
     return TP_EUNSUPPORTED;
   }
   if (batch <= 0 || l <= 0) return TP_OK;
-  const size_t smem = size_t(p) * l * sizeof(float2);
-  const int kp = keep_phase ? 1 : 0;
-  KernelScope ks("householder_qr", st);
-  if (p <= 64) {
-    TP_SET_SMEM(householder_qr_kernel<2>, smem);
-    householder_qr_kernel<2><<<unsigned(batch), HQR_THREADS, smem, st>>>(yr, yi, sY, p, l,
-                                                                         nullptr, kp);
-  } else if (p <= 128) {
-    TP_SET_SMEM(householder_qr_kernel<4>, smem);
-    householder_qr_kernel<4><<<unsigned(batch), HQR_THREADS, smem, st>>>(yr, yi, sY, p, l,
-                                                                         nullptr, kp);
-  } else {
-    TP_SET_SMEM(householder_qr_kernel<8>, smem);
-    householder_qr_kernel<8><<<unsigned(batch), HQR_THREADS, smem, st>>>(yr, yi, sY, p, l,
-                                                                         nullptr, kp);
-  }
-  return launch_status("householder_qr_kernel");
+  return launch_hqr(yr, yi, sY, p, l, nullptr, keep_phase, batch, st);
 }
 
 size_t rsvd_ws(int64_t n1, int64_t n2, int64_t n3, int64_t k, int64_t p, int prec) {
@@ -1035,6 +1155,7 @@ size_t rsvd_ws(int64_t n1, int64_t n2, int64_t n3, int64_t k, int64_t p, int pre
          + 2 * ws_bytes(size_t(n2) * l * h, 8)  // Jacobi G (float64)
          + 2 * ws_bytes(l * l * h, 8)           // Jacobi W (float64)
          + ws_bytes(l * h, 8) + ws_bytes(h, 4)  // singular values, real flags
+         + ws_bytes(size_t(QL_LOG_PER_L) * l * h, sizeof(QlRot)) + ws_bytes(h, 4)   // QL logs
          + 2 * ws_bytes(l * size_t(k) * h, 4)   // W_k
          + 2 * ws_bytes(size_t(n1) * k * h, 4)  // U_hat
          + 2 * ws_bytes(size_t(k) * k * h, 4)   // S_hat
@@ -1124,6 +1245,8 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
   double* Wi = ws.take<double>(size_t(l) * l * h);
   double* sig = ws.take<double>(size_t(l) * h);
   int* flags = ws.take<int>(size_t(h));
+  QlRot* qlog = ws.take<QlRot>(size_t(QL_LOG_PER_L) * l * h);
+  int32_t* qcnt = ws.take<int32_t>(size_t(h));
   float* Wkr = ws.take<float>(size_t(l) * k * h);
   float* Wki = ws.take<float>(size_t(l) * k * h);
   float* Ur = ws.take<float>(size_t(n1) * k * h);
@@ -1214,24 +1337,8 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
   TP_SET_SMEM(cholqr2_kernel, qr_smem);
   constexpr size_t kSmemCap = 200 * 1024;
   auto orth = [&](float* yr, float* yi, int64_t rows) {
-    if (rows <= 256 && l <= HQR_MAX_L) {
-      const size_t smem = size_t(rows) * l * sizeof(float2);
-      KernelScope ks("householder_qr", st);
-      if (rows <= 64) {
-        TP_SET_SMEM(householder_qr_kernel<2>, smem);
-        householder_qr_kernel<2><<<unsigned(h), HQR_THREADS, smem, st>>>(
-            yr, yi, rows * l, int(rows), int(l), sketch_per_freq, 0);
-      } else if (rows <= 128) {
-        TP_SET_SMEM(householder_qr_kernel<4>, smem);
-        householder_qr_kernel<4><<<unsigned(h), HQR_THREADS, smem, st>>>(
-            yr, yi, rows * l, int(rows), int(l), sketch_per_freq, 0);
-      } else {
-        TP_SET_SMEM(householder_qr_kernel<8>, smem);
-        householder_qr_kernel<8><<<unsigned(h), HQR_THREADS, smem, st>>>(
-            yr, yi, rows * l, int(rows), int(l), sketch_per_freq, 0);
-      }
-      return launch_status("householder_qr_kernel");
-    }
+    if (rows <= 256 && l <= HQR_MAX_L)
+      return launch_hqr(yr, yi, rows * l, int(rows), int(l), sketch_per_freq, false, h, st);
     {
       KernelScope ks("cholqr2", st);
       cholqr2_kernel<<<unsigned(h), QR_THREADS, qr_smem, st>>>(yr, yi, rows * l, int(rows),
@@ -1256,16 +1363,31 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
   }
   if ((rc = product(true, Yr, Yi, l, Zr, Zi))) return rc;      // B^H = X_hat^H Q
   const int sweeps = (opts && opts->max_sweeps > 0) ? opts->max_sweeps : 30;
-  const size_t eig_smem = core_eig_smem(int(n2), int(l));
-  if (eig_smem <= kSmemCap && l <= 128) {
-    TP_SET_SMEM(core_eig_kernel, eig_smem);
+  const size_t tri_smem = core_tridiag_smem(int(l)), fin_smem = core_finish_smem(int(l));
+  if (tri_smem <= kSmemCap && l <= 128) {
+    // d, e in sig's space, Q (then W) in Wr's, P = B^H W in Gr's
+    float* dg = reinterpret_cast<float*>(sig);
+    float* eg = dg + l * h;
+    float2* zg = reinterpret_cast<float2*>(Wr);
+    TP_SET_SMEM(core_tridiag_kernel, tri_smem);
+    TP_SET_SMEM(core_finish_kernel, fin_smem);
     {
-      KernelScope ks("core_eig", st);
-      core_eig_kernel<<<unsigned(h), EIG_THREADS, eig_smem, st>>>(
-          Zr, Zi, int(n2), int(l), k, sweeps, Wkr, Wki, Vr, Vi, Sr, Si,
-          reinterpret_cast<float2*>(Gr), status);
+      KernelScope ks("core_tridiag", st);
+      core_tridiag_kernel<<<unsigned(h), EIG_THREADS, tri_smem, st>>>(Zr, Zi, int(n2), int(l),
+                                                                      dg, eg, zg);
     }
-    if ((rc = launch_status("core_eig_kernel"))) return rc;
+    {
+      KernelScope ks("core_ql", st);
+      core_ql_kernel<<<unsigned(h), QL_THREADS, size_t(2) * l * sizeof(float), st>>>(
+          dg, eg, int(l), qlog, qcnt, sweeps, status);
+    }
+    {
+      KernelScope ks("core_finish", st);
+      core_finish_kernel<<<unsigned(h), EIG_THREADS, fin_smem, st>>>(
+          Zr, Zi, int(n2), int(l), k, zg, qlog, qcnt, Wkr, Wki, Vr, Vi, Sr, Si,
+          reinterpret_cast<float2*>(Gr));
+    }
+    if ((rc = launch_status("core_eig kernels"))) return rc;
   } else {
   {
     KernelScope ks("to_double", st);
