@@ -162,10 +162,10 @@ int tprod_sampled(const float* A, const float* B, float* Z,
  * rotation inside repeated singular values).  The per-slice one-sided
  * Jacobi sweeps in float32; V is re-orthonormalised in float64 (one
  * Newton-Schulz step) and G = X_hat V formed in float64.  Slices of at most
- * 256 x 96 then re-orthonormalise the vectors of G by a float32 Householder
- * QR in descending order (float32-level orthogonality; an orthonormal
- * completion for a cluster at the rounding floor); larger slices finish with
- * float64 sweeps.  The forward DFT is float32, so singular values are
+ * 4096 entries (p <= 256, m <= 96) then re-orthonormalise the vectors of G
+ * by a float32 Householder QR in descending order (float32-level
+ * orthogonality; an orthonormal completion for a cluster at the rounding
+ * floor); larger slices finish with float64 sweeps.  The forward DFT is float32, so singular values are
  * determined to about u32 s_1 either way.  Limits: m <= 512; n3 <= 512 or a
  * product of the radices 2..13.  */
 int tsvd(const float* X, int64_t n1, int64_t n2, int64_t n3,

@@ -532,9 +532,12 @@ int tsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, float* U, float
   note_launches(1);
   if ((rc = launch_status("svd_prep"))) return rc;
   const int sweeps = (opts && opts->max_sweeps > 0) ? opts->max_sweeps : 30;
-  // slices of at most 256 x 96: no float64 sweeps; the vectors of G are
-  // re-orthonormalised by a Householder QR in descending order instead
-  const bool fast = p <= 256 && m <= 96;
+  // slices of at most 4096 entries (and 256 x 96): no float64 sweeps; the
+  // vectors of G are re-orthonormalised by a float32 Householder QR in
+  // descending order instead.  The QR's own rounding grows as
+  // u32 sqrt(p m) (1.2e-5 of reconstruction at 256 x 96 against 3e-6 at
+  // 64 x 48), so larger slices keep the float64 sweeps.
+  const bool fast = p <= 256 && m <= 96 && p * m <= 4096;
   if ((rc = hybrid_svd(Xr, Xi, n1 * n2, n1, transpose, int(p), int(m), int(h), Fr, Fi, Qr, Qi, fsig,
                        Tr, Ti, Gr, Gi, Wr, Wi, sig, flags, sweeps, status, st, !fast)))
     return rc;

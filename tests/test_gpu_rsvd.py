@@ -50,7 +50,11 @@ def run_both(X, k, p, q, seed, precision=tp.TP_FP32):
 @pytest.mark.parametrize("n1,n2,n3,r,k,p,q", [(40, 30, 6, 3, 4, 3, 1), (30, 40, 7, 2, 3, 2, 0),
                                               (64, 48, 16, 5, 6, 4, 2), (20, 20, 1, 4, 5, 5, 1),
                                               # more than 256 rows: CholeskyQR2 in global memory
-                                              (300, 40, 4, 3, 4, 3, 1), (40, 300, 5, 3, 4, 4, 1)])
+                                              (300, 40, 4, 3, 4, 3, 1), (40, 300, 5, 3, 4, 4, 1),
+                                              # the Householder variants' row counts (64, 65,
+                                              # 129, 256 rows) and a one-column sketch
+                                              (64, 65, 3, 2, 3, 3, 1), (129, 256, 2, 4, 5, 3, 1),
+                                              (256, 70, 3, 5, 6, 2, 2), (12, 9, 5, 1, 1, 0, 1)])
 def test_exact_low_rank_is_recovered(n1, n2, n3, r, k, p, q, precision):
     X = synth.lowrank_np(n1, n2, n3, r, seed=7)
     (U, S, V), (Ur, Sr, Vr) = run_both(X, k, p, q, seed=3, precision=precision)

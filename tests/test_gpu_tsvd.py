@@ -19,7 +19,10 @@ def dev(x):
 
 
 SHAPES = [(64, 48, 16), (48, 64, 16), (5, 3, 4), (3, 5, 5), (7, 7, 1), (130, 40, 17),
-          (1, 1, 1), (2, 9, 2), (200, 100, 8)]
+          (1, 1, 1), (2, 9, 2), (200, 100, 8),
+          # the re-orthonormalised path's limit (4096 entries, 256 rows) and the
+          # float64 sweeps beyond it
+          (256, 16, 3), (64, 64, 2), (256, 96, 3), (96, 256, 2), (257, 40, 2)]
 
 
 @pytest.mark.parametrize("n1,n2,n3", SHAPES)
