@@ -405,11 +405,24 @@ __device__ __forceinline__ void hqr_materialize(float2* a, int k, int p, float2 
 // keep_phase: column j of Q is multiplied by sign(R(j, j)) (R's diagonal is
 // real), so that for Y with nearly orthonormal columns Q(:, j) stays close
 // to Y(:, j) instead of possibly flipping its sign.
+// Split planes (sp non-null): Q also leaves as the hi/lo planes (bf16 or
+// tf32, dftc::put_split) of the next tensor-core product's B operand,
+// K-major with leading dimension ldk >= p (rows p .. ldk-1 and the columns
+// from l on zero), slice stride ldk * lfull -- the operand split fused.
+struct HqrSplit {
+  float* p0;
+  float* p1;
+  float* p2;
+  float* p3;
+  int64_t ldk;
+  int bf16;
+};
+
 template <int RPL, bool FULL>
 __global__ void __launch_bounds__(HQR_THREADS) householder_qr_kernel(float* y_re, float* y_im,
                                                                      int64_t sY, int p, int lfull,
                                                                      const int32_t* lcols,
-                                                                     int keep_phase) {
+                                                                     int keep_phase, HqrSplit sp) {
   extern __shared__ float2 hqr_a[];   // Y, then Q: p x l column-major
   __shared__ float2 tau_s[HQR_MAX_L];
   __shared__ float sgn_s[HQR_MAX_L];   // sign of R(j, j)
@@ -486,6 +499,22 @@ __global__ void __launch_bounds__(HQR_THREADS) householder_qr_kernel(float* y_re
   for (int e = p * l + threadIdx.x; e < p * lfull; e += HQR_THREADS) {
     yr[e] = 0.f;
     yi[e] = 0.f;
+  }
+  if (sp.p0) {
+    const int64_t base = int64_t(blockIdx.x) * sp.ldk * lfull;
+    for (int64_t e = threadIdx.x; e < sp.ldk * lfull; e += HQR_THREADS) {
+      const int c = int(e / sp.ldk), r = int(e - int64_t(c) * sp.ldk);
+      float2 q = make_float2(0.f, 0.f);
+      if (r < p && c < l) {
+        q = A[c * p + r];
+        if (keep_phase) {
+          q.x *= sgn_s[c];
+          q.y *= sgn_s[c];
+        }
+      }
+      dftc::put_split(sp.p0, sp.p1, sp.bf16 != 0, base + e, q.x);
+      dftc::put_split(sp.p2, sp.p3, sp.bf16 != 0, base + e, q.y);
+    }
   }
 }
 
@@ -892,7 +921,9 @@ __global__ void __launch_bounds__(EIG_THREADS) core_finish_kernel(
     const float2* __restrict__ z_in, const QlRot* __restrict__ log,
     const int32_t* __restrict__ log_count, float* __restrict__ wkr, float* __restrict__ wki,
     float* __restrict__ vkr, float* __restrict__ vki, float* __restrict__ sr_out,
-    float* __restrict__ si_out, float2* __restrict__ pscratch) {
+    float* __restrict__ si_out, float2* __restrict__ pscratch, const int32_t* __restrict__ rank,
+    const float* __restrict__ q_re, const float* __restrict__ q_im, int n1,
+    float* __restrict__ ur, float* __restrict__ ui) {
   extern __shared__ double dyn[];
   const int ls = l | 1;
   double* sig2 = dyn;                                       // l: ||B^H w_j||^2
@@ -966,26 +997,59 @@ __global__ void __launch_bounds__(EIG_THREADS) core_finish_kernel(
     order[rank] = j;
   }
   __syncthreads();
+  // the slice keeps its top kr triplets (per-frequency rank), zeros after
+  const int kr = rank ? min(max(int(rank[f]), 0), k) : k;
   for (int e = threadIdx.x; e < l * k; e += blockDim.x) {
     const int i = e % l, c = e / l;
-    const float2 w = Wf[order[c] * ls + i];
+    const float2 w = c < kr ? Wf[order[c] * ls + i] : make_float2(0.f, 0.f);
     wkr[f * l * k + e] = w.x;
     wki[f * l * k + e] = w.y;
   }
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
     const int i = e % k, c = e / k;
-    sr_out[f * k * k + e] = (i == c) ? float(sqrt(sig2[order[c]])) : 0.f;
+    sr_out[f * k * k + e] = (i == c && c < kr) ? float(sqrt(sig2[order[c]])) : 0.f;
     si_out[f * k * k + e] = 0.f;
   }
   // V_k = B^H W_k S^{-1}: the columns of P in order, scaled
   for (int c = warp; c < k; c += nwarp) {
     const int j = order[c];
     const double sg = sqrt(sig2[j]);
-    const float inv = sg > 0.0 ? float(1.0 / sg) : 0.f;
+    const float inv = (sg > 0.0 && c < kr) ? float(1.0 / sg) : 0.f;
     for (int r = lane; r < p; r += 32) {
       const float2 v = P[r + int64_t(p) * j];
       vkr[f * int64_t(p) * k + r + int64_t(p) * c] = v.x * inv;
       vki[f * int64_t(p) * k + r + int64_t(p) * c] = v.y * inv;
+    }
+  }
+  // U_hat = Q W_k (ur non-null): FIN_RB rows of Q (n1 x l) at a time in
+  // shared memory, a warp per column
+  if (ur) {
+    const float* qrf = q_re + f * int64_t(n1) * l;
+    const float* qif = q_im + f * int64_t(n1) * l;
+    for (int r0 = 0; r0 < n1; r0 += FIN_RB) {
+      const int nr = min(FIN_RB, n1 - r0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < nr * l; e += blockDim.x) {
+        const int m = e / nr, rr = e - m * nr;
+        stage[m * FIN_RB + rr] = make_float2(__ldg(qrf + r0 + rr + int64_t(n1) * m),
+                                             __ldg(qif + r0 + rr + int64_t(n1) * m));
+      }
+      __syncthreads();
+      for (int c = warp; c < k; c += nwarp) {
+        const float2* wj = Wf + order[c] * ls;
+        for (int rr = lane; rr < nr; rr += 32) {
+          float pr = 0.f, pim = 0.f;
+          if (c < kr)
+            for (int m = 0; m < l; ++m) {
+              const float2 q = stage[m * FIN_RB + rr];
+              const float2 w = wj[m];
+              pr = fmaf(q.x, w.x, fmaf(-q.y, w.y, pr));
+              pim = fmaf(q.x, w.y, fmaf(q.y, w.x, pim));
+            }
+          ur[f * int64_t(n1) * k + r0 + rr + int64_t(n1) * c] = pr;
+          ui[f * int64_t(n1) * k + r0 + rr + int64_t(n1) * c] = pim;
+        }
+      }
     }
   }
 }
@@ -1095,7 +1159,7 @@ unsigned grid_for(int64_t n) {
 // Launch of householder_qr_kernel with RPL = 2, 4 or 8 rows per lane (p
 // up to 64, 128, 256) and the predicate-free form when p fills the lanes.
 int launch_hqr(float* yr, float* yi, int64_t sY, int p, int l, const int32_t* lcols,
-               bool keep_phase, int64_t batch, cudaStream_t st) {
+               bool keep_phase, int64_t batch, cudaStream_t st, HqrSplit sp = HqrSplit{}) {
   const size_t smem = size_t(p) * l * sizeof(float2);
   const int kp = keep_phase ? 1 : 0;
   const unsigned grid = unsigned(batch);
@@ -1103,7 +1167,8 @@ int launch_hqr(float* yr, float* yi, int64_t sY, int p, int l, const int32_t* lc
 #define TP_HQR(R, F)                                                                      \
   do {                                                                                    \
     TP_SET_SMEM((householder_qr_kernel<R, F>), smem);                                     \
-    householder_qr_kernel<R, F><<<grid, HQR_THREADS, smem, st>>>(yr, yi, sY, p, l, lcols, kp); \
+    householder_qr_kernel<R, F><<<grid, HQR_THREADS, smem, st>>>(yr, yi, sY, p, l, lcols, kp, \
+                                                                 sp);                            \
   } while (0)
   if (p == 64) TP_HQR(2, true);
   else if (p < 64) TP_HQR(2, false);
@@ -1324,21 +1389,32 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
   };
   // Y = X_hat B (hermitian = false) or X_hat^H B on the selected path, with B
   // given as float32 (br, bi: K x N column-major)
+  // the tensor-core forms: orth() on the Householder path also writes the
+  // next product's B planes (K = rows), so that product() skips its split
+  bool planes_ready = false;
   auto product = [&](bool hermitian, const float* br, const float* bi, int64_t N, float* cr,
                      float* ci) {
     const int64_t K = hermitian ? n1 : n2;
     if (!tc) return hermitian ? gemm(Hr, Hi, n2, n1, br, bi, N, cr, ci)
                               : gemm(Xr, Xi, n1, n2, br, bi, N, cr, ci);
-    int r2 = split(br, bi, K, N, 0, hermitian ? ln : lm, BP);
-    if (r2) return r2;
+    if (!planes_ready) {
+      int r2 = split(br, bi, K, N, 0, hermitian ? ln : lm, BP);
+      if (r2) return r2;
+    }
+    planes_ready = false;
     return gemm_tc(hermitian, N, cr, ci);
   };
   const size_t qr_smem = size_t(2) * l * l * sizeof(double);
   TP_SET_SMEM(cholqr2_kernel, qr_smem);
   constexpr size_t kSmemCap = 200 * 1024;
   auto orth = [&](float* yr, float* yi, int64_t rows) {
-    if (rows <= 256 && l <= HQR_MAX_L)
-      return launch_hqr(yr, yi, rows * l, int(rows), int(l), sketch_per_freq, false, h, st);
+    if (rows <= 256 && l <= HQR_MAX_L) {
+      HqrSplit sp{};
+      if (tc) sp = HqrSplit{BP[0], BP[1], BP[2], BP[3], split_ld(rows, prec), bf};
+      planes_ready = tc;
+      return launch_hqr(yr, yi, rows * l, int(rows), int(l), sketch_per_freq, false, h, st, sp);
+    }
+    planes_ready = false;
     {
       KernelScope ks("cholqr2", st);
       cholqr2_kernel<<<unsigned(h), QR_THREADS, qr_smem, st>>>(yr, yi, rows * l, int(rows),
@@ -1364,6 +1440,7 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
   if ((rc = product(true, Yr, Yi, l, Zr, Zi))) return rc;      // B^H = X_hat^H Q
   const int sweeps = (opts && opts->max_sweeps > 0) ? opts->max_sweeps : 30;
   const size_t tri_smem = core_tridiag_smem(int(l)), fin_smem = core_finish_smem(int(l));
+  bool u_formed = false;   // U_hat (ranks applied) already written by the core
   if (tri_smem <= kSmemCap && l <= 128) {
     // d, e in sig's space, Q (then W) in Wr's, P = B^H W in Gr's
     float* dg = reinterpret_cast<float*>(sig);
@@ -1383,11 +1460,15 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
     }
     {
       KernelScope ks("core_finish", st);
+      // the factors' U_hat = Q W_k and the per-frequency ranks in the same
+      // kernel (not for the singular values alone)
       core_finish_kernel<<<unsigned(h), EIG_THREADS, fin_smem, st>>>(
           Zr, Zi, int(n2), int(l), k, zg, qlog, qcnt, Wkr, Wki, Vr, Vi, Sr, Si,
-          reinterpret_cast<float2*>(Gr));
+          reinterpret_cast<float2*>(Gr), sig_out ? nullptr : rank_per_freq, Yr, Yi, int(n1),
+          sig_out ? nullptr : Ur, sig_out ? nullptr : Ui);
     }
     if ((rc = launch_status("core_eig kernels"))) return rc;
+    u_formed = !sig_out;
   } else {
   {
     KernelScope ks("to_double", st);
@@ -1414,15 +1495,17 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
     }
     return launch_status("diag_kernel");
   }
-  if (rank_per_freq) {
-    {
-      KernelScope ks("rank_mask", st);
-      rank_mask_kernel<<<unsigned(h), 256, 0, st>>>(rank_per_freq, int(l), int(n2), k, Wkr, Wki,
-                                                    Vr, Vi, Sr, Si);
+  if (!u_formed) {
+    if (rank_per_freq) {
+      {
+        KernelScope ks("rank_mask", st);
+        rank_mask_kernel<<<unsigned(h), 256, 0, st>>>(rank_per_freq, int(l), int(n2), k, Wkr,
+                                                      Wki, Vr, Vi, Sr, Si);
+      }
+      if ((rc = launch_status("rank_mask_kernel"))) return rc;
     }
-    if ((rc = launch_status("rank_mask_kernel"))) return rc;
+    if ((rc = gemm(Yr, Yi, n1, l, Wkr, Wki, k, Ur, Ui))) return rc;   // U_hat = Q W_k
   }
-  if ((rc = gemm(Yr, Yi, n1, l, Wkr, Wki, k, Ur, Ui))) return rc;    // U_hat = Q W_k
   if ((rc = launch_irdft(Ur, Ui, n1 * k, n1 * k, n3, U, st))) return rc;
   if ((rc = launch_irdft(Sr, Si, int64_t(k) * k, int64_t(k) * k, n3, S, st))) return rc;
   return launch_irdft(Vr, Vi, n2 * k, n2 * k, n3, V, st);
