@@ -63,6 +63,37 @@ __global__ void conj_transpose_kernel(const float* __restrict__ ir, const float*
 // f*s_src + r + ld_src*c) goes to f*s_dst + r + ld_dst*c of the hi/lo
 // planes (3xTF32 float or BF16x3 bf16 pairs), the imaginary part negated
 // when conj; rows [rows, ld_dst) are zero (the K padding of the tiles).
+// The split planes of X_hat transposed without conjugation, for the
+// tensor-core products X_hat B: element (i, j) of X_hat (n1 x n2,
+// column-major) goes to j + ldk i of each plane (K-major, rows j from n2 to
+// ldk zero), through a 32 x 32 shared-memory tile as conj_transpose_kernel
+// moves it.
+__global__ void transpose_split_kernel(const float* __restrict__ ir, const float* __restrict__ ii,
+                                       int64_t n1, int64_t n2, int64_t ldk, int bf16,
+                                       float* __restrict__ re_hi, float* __restrict__ re_lo,
+                                       float* __restrict__ im_hi, float* __restrict__ im_lo) {
+  __shared__ float tr[32][33], ti[32][33];
+  const int64_t f = blockIdx.z;
+  const int64_t i0 = int64_t(blockIdx.x) * 32, j0 = int64_t(blockIdx.y) * 32;
+  const float* sr = ir + f * n1 * n2;
+  const float* si = ii + f * n1 * n2;
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int64_t i = i0 + threadIdx.x, j = j0 + dy;
+    const bool in = i < n1 && j < n2;
+    tr[dy][threadIdx.x] = in ? sr[i + n1 * j] : 0.f;
+    ti[dy][threadIdx.x] = in ? si[i + n1 * j] : 0.f;
+  }
+  __syncthreads();
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int64_t j = j0 + threadIdx.x, i = i0 + dy;
+    if (i < n1 && j < ldk) {
+      const int64_t o = f * ldk * n1 + j + ldk * i;
+      dftc::put_split(re_hi, re_lo, bf16 != 0, o, tr[threadIdx.x][dy]);
+      dftc::put_split(im_hi, im_lo, bf16 != 0, o, ti[threadIdx.x][dy]);
+    }
+  }
+}
+
 __global__ void split_planes_kernel(const float* __restrict__ sr, const float* __restrict__ si,
                                     int64_t rows, int64_t cols, int64_t ld_src, int64_t s_src,
                                     int64_t h, int64_t ld_dst, int64_t s_dst, int conj, int bf16,
@@ -1331,7 +1362,7 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
   DftGather gx{X, n1 * n2, 1, 1, 0, n1 * n2, nullptr, nullptr, nullptr, 0, n3, Xr, Xi,
                n1 * n2, n1 * n2, nullptr, nullptr, 0};
   if ((rc = launch_rdft(gx, st))) return rc;
-  {
+  if (!tc) {   // X_hat^H for the CUDA-core products (the split forms take planes)
     KernelScope ks("conj_transpose", st);
     conj_transpose_kernel<<<dim3(unsigned((n1 + 31) / 32), unsigned((n2 + 31) / 32), unsigned(h)),
                             dim3(32, 8), 0, st>>>(Xr, Xi, n1, n2, Hr, Hi);
@@ -1426,7 +1457,14 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
   if (tc) {
     // X_hat (element (i, j) at j + lm i: the transpose of X_hat^H without
     // its conjugation) and conj(X_hat) (element (j, i) of X_hat^H at i + ln j)
-    if ((rc = split(Hr, Hi, n2, n1, 1, lm, XA))) return rc;
+    {
+      KernelScope ks("rsvd_split", st);
+      transpose_split_kernel<<<dim3(unsigned((n1 + 31) / 32), unsigned((lm + 31) / 32),
+                                    unsigned(h)),
+                               dim3(32, 8), 0, st>>>(Xr, Xi, n1, n2, lm, bf, XA[0], XA[1], XA[2],
+                                                     XA[3]);
+    }
+    if ((rc = launch_status("transpose_split_kernel"))) return rc;
     if ((rc = split(Xr, Xi, n1, n2, 1, ln, XH))) return rc;
   }
   if ((rc = product(false, Or, Oi, l, Yr, Yi))) return rc;     // Y = X_hat Omega
