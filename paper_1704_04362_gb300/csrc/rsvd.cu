@@ -711,8 +711,8 @@ __device__ void tridiag_form_q(const float2* G, float2* W, int l, int ls, const 
 // log (at most cap; rotation i mixes columns i and i + 1, code i, or
 // -(i + 1) for a chase's first rotation).  T is first scaled by a power of
 // two to a largest entry near 1 (exact; only the eigenvectors are used), so
-// that the squares stay in range and a plain square root and one
-// reciprocal form each rotation.  Returns false if an eigenvalue took more
+// that the squares stay in range and one refined reciprocal square root
+// forms each rotation.  Returns false if an eigenvalue took more
 // than max_iter chases (its off-diagonal is then dropped) or the log was
 // full (the chase stops there); *count gets the log's length.
 struct QlRot {
@@ -768,7 +768,20 @@ __device__ bool ql_chase(float* __restrict__ d, float* __restrict__ e, int strid
         di_n = D(i - 1);
       }
       const float f = s * ei, b = c * ei;
-      float r = sqrtf(fmaf(f, f, g * g));
+      // r = sqrt(f^2 + g^2) and 1/r from the hardware reciprocal square root
+      // refined by one Newton-Raphson step y (3 - x y^2) / 2 (subnormal x:
+      // the rounded square root and reciprocal)
+      const float x = fmaf(f, f, g * g);
+      float r, inv;
+      if (x >= FLT_MIN) {
+        float y = rsqrtf(x);
+        y *= fmaf(-0.5f * x, y * y, 1.5f);
+        inv = y;
+        r = x * y;
+      } else {
+        r = sqrtf(x);
+        inv = r > 0.f ? __frcp_rn(r) : 0.f;
+      }
       E(i + 1) = r;
       if (r == 0.f) {   // the chase splits: restart from the new block
         D(i + 1) = dn - pp;
@@ -776,7 +789,6 @@ __device__ bool ql_chase(float* __restrict__ d, float* __restrict__ e, int strid
         early = true;
         break;
       }
-      const float inv = __frcp_rn(r);
       s = f * inv;
       c = g * inv;
       g = dn - pp;
