@@ -226,3 +226,21 @@ def test_per_frequency_sketch_sizes_match_oracle(n1, n2, n3, r, k, p, q, sizes, 
                                     sketch_sizes=full)
     U0, S0, V0 = tp.tsvd_randomized(dev(X), k, p, q, seed=11, precision=precision)
     assert torch.equal(U1, U0) and torch.equal(S1, S0) and torch.equal(V1, V0)
+
+
+def test_core_iteration_cap_is_flagged():
+    """The core eigensolver's QL takes at most max_sweeps chases per
+    eigenvalue: a cap of one on a generic tensor must raise the device
+    non-convergence bit (its off-diagonals are dropped, nothing hangs) and
+    still give finite factors."""
+    import torch
+    X = synth.lowrank_np(48, 40, 6, 12, seed=31, noise=1e-2)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    U, S, V = tp.tsvd_randomized(dev(X), 8, 4, 1, seed=0, status=st, max_sweeps=1)
+    torch.cuda.synchronize()
+    assert int(st.item()) & 0x1
+    assert bool(torch.isfinite(U).all()) and bool(torch.isfinite(S).all())
+    st.zero_()
+    tp.tsvd_randomized(dev(X), 8, 4, 1, seed=0, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
