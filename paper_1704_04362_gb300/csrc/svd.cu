@@ -58,6 +58,7 @@ template <> struct Eps<double> { static constexpr double v = 1.12e-16; };
 constexpr int JAC_INIT_V = 1;      // start from V = I (else from the given V)
 constexpr int JAC_NORMALIZE = 2;   // on exit scale G's columns to unit length
 constexpr int JAC_SMEM = 4;        // work on shared-memory copies of G and V
+constexpr int JAC_MAX_Q = 512;     // columns of a slice (min(n1, n2) <= 512 at the entry points)
 
 template <class T>
 __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(T* g_re, T* g_im, int64_t sG, T* v_re,
@@ -110,9 +111,26 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(T* g_re, T* g_im, i
   T tol = T(8) * Eps<T>::v * sqrt(T(p));
   if (tol < T(sizeof(T) == 4 ? 1e-6 : 1e-13)) tol = T(sizeof(T) == 4 ? 1e-6 : 1e-13);
   const int qq = q + (q & 1);
+  // float64: squared column norms computed at the start of every sweep,
+  // then kept by each rotation (||a'||^2 = alpha - t |gamma|, ||b'||^2 =
+  // beta + t |gamma|), so that a pair needs only its inner product (float64
+  // runs at 1/64 of the float32 rate; float32 sweeps are latency-bound and
+  // compute the norms with the inner product instead)
+  constexpr bool keep = sizeof(T) == 8;
+  __shared__ T nrm[keep ? JAC_MAX_Q : 1];
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     if (tid == 0) rotated = 0;
+    if (keep) {
+      for (int j = warp; j < q; j += nw) {
+        const T* xr = Gr + int64_t(j) * p;
+        const T* xi = Gi + int64_t(j) * p;
+        T acc = 0;
+        for (int r = lane; r < p; r += 32) acc += xr[r] * xr[r] + xi[r] * xi[r];
+        acc = warp_sum_t(acc);
+        if (lane == 0) nrm[j] = acc;
+      }
+    }
     __syncthreads();
     for (int step = 0; step < qq - 1; ++step) {
       for (int i = warp; i < qq / 2; i += nw) {
@@ -131,15 +149,25 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(T* g_re, T* g_im, i
         T* br = Gr + int64_t(c2) * p;
         T* bi = Gi + int64_t(c2) * p;
         T alpha = 0, beta = 0, gr = 0, gi = 0;
-        for (int r = lane; r < p; r += 32) {
-          const T xr = ar[r], xi = ai[r], yr = br[r], yi = bi[r];
-          alpha += xr * xr + xi * xi;
-          beta += yr * yr + yi * yi;
-          gr += xr * yr + xi * yi;    // Re(conj(x) y)
-          gi += xr * yi - xi * yr;    // Im(conj(x) y)
+        if (keep) {
+          alpha = nrm[a] > T(0) ? nrm[a] : T(0);
+          beta = nrm[c2] > T(0) ? nrm[c2] : T(0);
+          for (int r = lane; r < p; r += 32) {
+            const T xr = ar[r], xi = ai[r], yr = br[r], yi = bi[r];
+            gr += xr * yr + xi * yi;    // Re(conj(x) y)
+            gi += xr * yi - xi * yr;    // Im(conj(x) y)
+          }
+        } else {
+          for (int r = lane; r < p; r += 32) {
+            const T xr = ar[r], xi = ai[r], yr = br[r], yi = bi[r];
+            alpha += xr * xr + xi * xi;
+            beta += yr * yr + yi * yi;
+            gr += xr * yr + xi * yi;
+            gi += xr * yi - xi * yr;
+          }
+          alpha = warp_sum_t(alpha);
+          beta = warp_sum_t(beta);
         }
-        alpha = warp_sum_t(alpha);
-        beta = warp_sum_t(beta);
         gr = warp_sum_t(gr);
         gi = warp_sum_t(gi);
         const T g2 = gr * gr + gi * gi;
@@ -147,6 +175,11 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(T* g_re, T* g_im, i
         if (lane == 0) rotated = 1;
         T cs, sn, er, ei;   // cos, sin and e^{-i phi}
         rotation(alpha, beta, gr, gi, g2, cs, sn, er, ei);
+        if (keep && lane == 0) {
+          const T tg = (sn / cs) * sqrt(g2);
+          nrm[a] = alpha - tg;
+          nrm[c2] = beta + tg;
+        }
         for (int r = lane; r < p; r += 32) {
           const T xr = ar[r], xi = ai[r];
           const T yr = br[r] * er - bi[r] * ei, yi = br[r] * ei + bi[r] * er;   // b~
@@ -383,6 +416,10 @@ int jacobi_launch(T* gr, T* gi, int64_t sG, T* vr, T* vi, int64_t sV, T* sig, in
                   int batch, int max_sweeps, const int* real_flags, int32_t* status, int flags,
                   cudaStream_t st) {
   if (batch <= 0 || q <= 0) return TP_OK;
+  if (q > JAC_MAX_Q) {
+    set_error("jacobi: %d columns, more than %d", q, JAC_MAX_Q);
+    return TP_EUNSUPPORTED;
+  }
   const size_t smem = jacobi_smem<T>(p, q);
   if (smem) {
     flags |= JAC_SMEM;
