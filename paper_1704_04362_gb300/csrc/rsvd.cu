@@ -1517,7 +1517,7 @@ int rsvd_run(const float* X, int64_t n1, int64_t n2, int64_t n3, int k, int p, i
           reinterpret_cast<float2*>(Gr), sig_out ? nullptr : rank_per_freq, Yr, Yi, int(n1),
           sig_out ? nullptr : Ur, sig_out ? nullptr : Ui);
     }
-    if ((rc = launch_status("core_eig kernels"))) return rc;
+    if ((rc = launch_status("core SVD kernels"))) return rc;
     u_formed = !sig_out;
   } else {
   {
