@@ -12,7 +12,9 @@
 // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t,
 // a' = c a - s b~, b' = s a + c b~.  Sweeps are capped (opts->max_sweeps); a
 // slice that reaches the cap sets TP_DEV_NOCONV.  G and V live in shared
-// memory when they fit, else in global memory.
+// memory when they fit, else in global memory.  With fewer slices than SMs a
+// cluster of CTAs shares each slice instead (jacobi_cluster_kernel: the
+// round-robin ordering on blocks of columns, one block pair per CTA).
 //
 // GB300 runs float64 at 1/64 of the float32 rate, so the t-SVD takes the
 // sweeps in float32 and finishes in float64:
@@ -237,6 +239,325 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(T* g_re, T* g_im, i
   }
 }
 
+// ---- sweeps of a few slices: one thread-block cluster per slice ----
+//
+// One CTA per slice leaves most SMs idle when there are few slices (t-CX /
+// t-CUR and the t-SVD of a short tube: 17 slices), and float64 runs at only
+// 2 FMA per clock per SM.  Here a cluster of JPC CTAs shares one slice: its q
+// columns are cut into 2 JPC blocks of bs = ceil(q / 2 JPC), and a sweep runs
+// the round-robin (circle) ordering on the blocks.  In each of its 2 JPC - 1
+// rounds every CTA owns one block pair and rotates its bs x bs cross pairs (bs
+// steps of bs disjoint pairs, one pair per warp); in round 0, where every
+// block appears once, it also rotates the internal pairs of its two blocks.
+// Each column pair thus meets once per sweep, as in the cyclic sweep.  G, V
+// and the kept squared norms live in global memory between rounds (L2
+// resident: the slices of this path are small) and are read through L2
+// (ld.global.cg), so that what another SM wrote in the previous round is seen
+// after the cluster barrier (release / acquire at cluster scope).  When the
+// block pair fits, a CTA copies it to shared memory for the round (SMEM).
+constexpr int JPC = 8;                 // CTAs per slice (portable cluster size)
+constexpr int JPC_BLOCKS = 2 * JPC;    // column blocks per slice
+constexpr int JPC_THREADS = 512;
+
+__device__ __forceinline__ void jpc_cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned jpc_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// an int in CTA `rank`'s shared memory at the address of `local`
+__device__ __forceinline__ int jpc_peek(const int* local, unsigned rank) {
+  const unsigned a = unsigned(__cvta_generic_to_shared(local));
+  unsigned remote;
+  int v;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(a), "r"(rank));
+  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(remote) : "memory");
+  return v;
+}
+
+template <bool S, class T>
+__device__ __forceinline__ T jld(const T* x) {
+  if constexpr (S) return *x;
+  else return __ldcg(x);
+}
+template <bool S, class T>
+__device__ __forceinline__ void jst(T* x, T v) {
+  if constexpr (S) *x = v;
+  else __stcg(x, v);
+}
+
+// One warp rotates columns (a, b) of G (p rows) and V (q rows) unless they
+// are orthogonal to tol.  float64 reads and keeps the squared norms na, nb;
+// float32 computes them with the inner product.
+template <bool S, class T>
+__device__ __forceinline__ bool jpc_pair(T* ar, T* ai, T* br, T* bi, T* var, T* vai, T* vbr,
+                                         T* vbi, T* na, T* nb, int p, int q, int lane, T tol) {
+  constexpr bool keep = sizeof(T) == 8;
+  T alpha = 0, beta = 0, gr = 0, gi = 0;
+  if (keep) {
+    alpha = jld<S>(na);
+    beta = jld<S>(nb);
+    alpha = alpha > T(0) ? alpha : T(0);
+    beta = beta > T(0) ? beta : T(0);
+  }
+  for (int r = lane; r < p; r += 32) {
+    const T xr = jld<S>(ar + r), xi = jld<S>(ai + r), yr = jld<S>(br + r), yi = jld<S>(bi + r);
+    if (!keep) {
+      alpha += xr * xr + xi * xi;
+      beta += yr * yr + yi * yi;
+    }
+    gr += xr * yr + xi * yi;
+    gi += xr * yi - xi * yr;
+  }
+  if (!keep) {
+    alpha = warp_sum_t(alpha);
+    beta = warp_sum_t(beta);
+  }
+  gr = warp_sum_t(gr);
+  gi = warp_sum_t(gi);
+  const T g2 = gr * gr + gi * gi;
+  if (!(g2 > tol * tol * alpha * beta) || g2 == T(0)) return false;
+  T cs, sn, er, ei;
+  rotation(alpha, beta, gr, gi, g2, cs, sn, er, ei);
+  if (keep && lane == 0) {
+    const T tg = (sn / cs) * sqrt(g2);
+    jst<S>(na, alpha - tg);
+    jst<S>(nb, beta + tg);
+  }
+  for (int r = lane; r < p; r += 32) {
+    const T xr = jld<S>(ar + r), xi = jld<S>(ai + r);
+    const T ur = jld<S>(br + r), ui = jld<S>(bi + r);
+    const T yr = ur * er - ui * ei, yi = ur * ei + ui * er;
+    jst<S>(ar + r, cs * xr - sn * yr);
+    jst<S>(ai + r, cs * xi - sn * yi);
+    jst<S>(br + r, sn * xr + cs * yr);
+    jst<S>(bi + r, sn * xi + cs * yi);
+  }
+  for (int r = lane; r < q; r += 32) {
+    const T xr = jld<S>(var + r), xi = jld<S>(vai + r);
+    const T ur = jld<S>(vbr + r), ui = jld<S>(vbi + r);
+    const T yr = ur * er - ui * ei, yi = ur * ei + ui * er;
+    jst<S>(var + r, cs * xr - sn * yr);
+    jst<S>(vai + r, cs * xi - sn * yi);
+    jst<S>(vbr + r, sn * xr + cs * yr);
+    jst<S>(vbi + r, sn * xi + cs * yi);
+  }
+  return true;
+}
+
+// Shared memory of a SMEM cluster CTA (the round's 2 bs columns of G and V
+// and their norms), or 0 when it does not fit.
+template <class T>
+size_t jacobi_cluster_smem(int p, int q) {
+  const size_t bs = size_t((q + JPC_BLOCKS - 1) / JPC_BLOCKS);
+  const size_t bytes = (4 * bs * size_t(p) + 4 * bs * size_t(q) + 2 * bs) * sizeof(T);
+  return bytes <= size_t(200) * 1024 ? bytes : 0;
+}
+
+// One-sided Jacobi of slice blockIdx.x / JPC with the flags of jacobi_kernel
+// (JAC_INIT_V, JAC_NORMALIZE): the result of jacobi_kernel<T>, one cluster per
+// slice.  nrm_ws: q values per slice of scratch (float64 only).
+template <class T, bool S>
+__global__ void __cluster_dims__(JPC, 1, 1) __launch_bounds__(JPC_THREADS)
+    jacobi_cluster_kernel(T* g_re, T* g_im, int64_t sG, T* v_re, T* v_im, int64_t sV, T* nrm_ws,
+                          T* sig, int p, int q, int max_sweeps, const int* real_flags,
+                          int32_t* status, int flags) {
+  extern __shared__ __align__(16) unsigned char jpc_smem[];
+  constexpr bool keep = sizeof(T) == 8;
+  const int c = int(jpc_rank());
+  const int64_t b = blockIdx.x / JPC;
+  T* const Gr = g_re + b * sG;
+  T* const Gi = g_im + b * sG;
+  T* const Vr = v_re + b * sV;
+  T* const Vi = v_im + b * sV;
+  T* const nrm = keep ? nrm_ws + b * q : nullptr;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = JPC_THREADS / 32;
+  const int bs = (q + JPC_BLOCKS - 1) / JPC_BLOCKS;
+  const int bs2 = bs + (bs & 1);   // positions of the internal round-robin
+  // the round's block pair in shared memory: local column l < bs is column
+  // i0 + l of the slice, l >= bs column j0 + l - bs
+  T* const sGr = reinterpret_cast<T*>(jpc_smem);
+  T* const sGi = sGr + 2 * bs * p;
+  T* const sVr = sGi + 2 * bs * p;
+  T* const sVi = sVr + 2 * bs * q;
+  T* const sN = sVi + 2 * bs * q;
+  __shared__ int rotated, any_s;
+
+  const bool real = real_flags ? real_flags[b] != 0 : false;
+  for (int j = c; j < q; j += JPC) {
+    if (flags & JAC_INIT_V) {
+      for (int r = tid; r < q; r += JPC_THREADS) {
+        Vr[int64_t(j) * q + r] = r == j ? T(1) : T(0);
+        Vi[int64_t(j) * q + r] = T(0);
+      }
+    } else if (real) {
+      for (int r = tid; r < q; r += JPC_THREADS) Vi[int64_t(j) * q + r] = T(0);
+    }
+    if (real)
+      for (int r = tid; r < p; r += JPC_THREADS) Gi[int64_t(j) * p + r] = T(0);
+  }
+  T tol = T(8) * Eps<T>::v * sqrt(T(p));
+  if (tol < T(keep ? 1e-13 : 1e-6)) tol = T(keep ? 1e-13 : 1e-6);
+  __threadfence();
+  jpc_cluster_sync();
+
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) rotated = 0;
+    if (keep) {
+      for (int j = c + JPC * warp; j < q; j += JPC * nw) {
+        const T* xr = Gr + int64_t(j) * p;
+        const T* xi = Gi + int64_t(j) * p;
+        T acc = 0;
+        for (int r = lane; r < p; r += 32) {
+          const T u = __ldcg(xr + r), v = __ldcg(xi + r);
+          acc += u * u + v * v;
+        }
+        acc = warp_sum_t(acc);
+        if (lane == 0) __stcg(nrm + j, acc);
+      }
+      __threadfence();
+    }
+    jpc_cluster_sync();
+    bool rot = false;
+    for (int round = 0; round < JPC_BLOCKS - 1; ++round) {
+      int I, J;
+      if (c == 0) {
+        I = JPC_BLOCKS - 1;
+        J = round;
+      } else {
+        I = (round + c) % (JPC_BLOCKS - 1);
+        J = (round - c + JPC_BLOCKS - 1) % (JPC_BLOCKS - 1);
+      }
+      const int i0 = I * bs, j0 = J * bs;
+      auto gcol = [&](int l) { return l < bs ? i0 + l : j0 + l - bs; };
+      if (S) {
+        for (int e = tid; e < 2 * bs * p; e += JPC_THREADS) {
+          const int l = e / p, g = gcol(l);
+          if (g < q) {
+            const int64_t o = int64_t(g) * p + (e - l * p);
+            sGr[e] = __ldcg(Gr + o);
+            sGi[e] = __ldcg(Gi + o);
+          }
+        }
+        for (int e = tid; e < 2 * bs * q; e += JPC_THREADS) {
+          const int l = e / q, g = gcol(l);
+          if (g < q) {
+            const int64_t o = int64_t(g) * q + (e - l * q);
+            sVr[e] = __ldcg(Vr + o);
+            sVi[e] = __ldcg(Vi + o);
+          }
+        }
+        if (keep)
+          for (int l = tid; l < 2 * bs; l += JPC_THREADS)
+            if (gcol(l) < q) sN[l] = __ldcg(nrm + gcol(l));
+        __syncthreads();
+      }
+      // rotates local columns (la, lb) of the block pair
+      auto pair = [&](int la, int lb) {
+        int ga = gcol(la), gb = gcol(lb);
+        if (ga >= q || gb >= q) return;
+        if (ga > gb) {
+          const int t = la; la = lb; lb = t;
+          const int u = ga; ga = gb; gb = u;
+        }
+        if (S)
+          rot |= jpc_pair<true, T>(sGr + la * p, sGi + la * p, sGr + lb * p, sGi + lb * p,
+                                   sVr + la * q, sVi + la * q, sVr + lb * q, sVi + lb * q,
+                                   sN + la, sN + lb, p, q, lane, tol);
+        else
+          rot |= jpc_pair<false, T>(Gr + int64_t(ga) * p, Gi + int64_t(ga) * p,
+                                    Gr + int64_t(gb) * p, Gi + int64_t(gb) * p,
+                                    Vr + int64_t(ga) * q, Vi + int64_t(ga) * q,
+                                    Vr + int64_t(gb) * q, Vi + int64_t(gb) * q,
+                                    keep ? nrm + ga : nullptr, keep ? nrm + gb : nullptr, p, q,
+                                    lane, tol);
+      };
+      if (round == 0) {
+        // internal pairs of both blocks: bs2 - 1 steps of bs2 / 2 pairs each
+        for (int step = 0; step < bs2 - 1; ++step) {
+          for (int k = warp; k < bs2; k += nw) {
+            const int off = k < bs2 / 2 ? 0 : bs;
+            const int i = k < bs2 / 2 ? k : k - bs2 / 2;
+            int x, y;
+            if (i == 0) {
+              x = bs2 - 1;
+              y = step;
+            } else {
+              x = (step + i) % (bs2 - 1);
+              y = (step - i + bs2 - 1) % (bs2 - 1);
+            }
+            if (x < bs && y < bs) pair(off + x, off + y);
+          }
+          __syncthreads();
+        }
+      }
+      // cross pairs: step t pairs column i of block I with (i + t) mod bs of J
+      for (int t = 0; t < bs; ++t) {
+        for (int i = warp; i < bs; i += nw) pair(i, bs + (i + t) % bs);
+        __syncthreads();
+      }
+      if (S) {
+        for (int e = tid; e < 2 * bs * p; e += JPC_THREADS) {
+          const int l = e / p, g = gcol(l);
+          if (g < q) {
+            const int64_t o = int64_t(g) * p + (e - l * p);
+            __stcg(Gr + o, sGr[e]);
+            __stcg(Gi + o, sGi[e]);
+          }
+        }
+        for (int e = tid; e < 2 * bs * q; e += JPC_THREADS) {
+          const int l = e / q, g = gcol(l);
+          if (g < q) {
+            const int64_t o = int64_t(g) * q + (e - l * q);
+            __stcg(Vr + o, sVr[e]);
+            __stcg(Vi + o, sVi[e]);
+          }
+        }
+        if (keep)
+          for (int l = tid; l < 2 * bs; l += JPC_THREADS)
+            if (gcol(l) < q) __stcg(nrm + gcol(l), sN[l]);
+        __syncthreads();   // the next round's loads overwrite the copies
+      }
+      if (rot && lane == 0) rotated = 1;
+      __threadfence();
+      jpc_cluster_sync();
+    }
+    if (tid == 0) {
+      int any = 0;
+      for (int r = 0; r < JPC; ++r) any |= jpc_peek(&rotated, unsigned(r));
+      any_s = any;
+    }
+    jpc_cluster_sync();   // every CTA has read every flag before any resets its own
+    if (!any_s) break;
+  }
+  if (sweep >= max_sweeps && c == 0 && tid == 0 && status) atomicOr(status, TP_DEV_NOCONV);
+  // singular values and (optionally) unit left vectors
+  for (int j = c + JPC * warp; j < q; j += JPC * nw) {
+    T* xr = Gr + int64_t(j) * p;
+    T* xi = Gi + int64_t(j) * p;
+    T acc = 0;
+    for (int r = lane; r < p; r += 32) {
+      const T u = __ldcg(xr + r), v = __ldcg(xi + r);
+      acc += u * u + v * v;
+    }
+    const T s = sqrt(warp_sum_t(acc));
+    if (lane == 0) sig[b * q + j] = s;
+    if (flags & JAC_NORMALIZE) {
+      const T inv = s > T(0) ? T(1) / s : T(0);
+      for (int r = lane; r < p; r += 32) {
+        xr[r] = __ldcg(xr + r) * inv;
+        xi[r] = __ldcg(xi + r) * inv;
+      }
+    }
+  }
+}
+
 // Gathers slice b of the half spectrum into the work matrix:
 // G = X_hat_k (n1 x n2) when n1 >= n2, else G = X_hat_k^H (n2 x n1).
 template <class T>
@@ -433,6 +754,35 @@ int jacobi_launch(T* gr, T* gi, int64_t sG, T* vr, T* vi, int64_t sV, T* sig, in
   return launch_status("jacobi_kernel");
 }
 
+// A cluster of CTAs per slice pays when the slices are fewer than the SMs and
+// wide enough to give every CTA of the cluster a block pair of columns.
+bool use_cluster(int q, int batch) {
+  return q >= 2 * JPC_BLOCKS && q <= JAC_MAX_Q && batch < sm_count();
+}
+
+template <class T>
+int jacobi_cluster_launch(T* gr, T* gi, int64_t sG, T* vr, T* vi, int64_t sV, T* nrm, T* sig,
+                          int p, int q, int batch, int max_sweeps, const int* real_flags,
+                          int32_t* status, int flags, cudaStream_t st) {
+  if (batch <= 0 || q <= 0) return TP_OK;
+  const size_t smem = jacobi_cluster_smem<T>(p, q);
+  const unsigned grid = unsigned(batch) * JPC;
+  {
+    KernelScope ks(sizeof(T) == 4 ? "jacobi_f32" : "jacobi_svd", st);
+    if (smem) {
+      if (int rc = set_smem_attr((const void*)jacobi_cluster_kernel<T, true>, smem,
+                                 "jacobi_cluster_kernel"))
+        return rc;
+      jacobi_cluster_kernel<T, true><<<grid, JPC_THREADS, smem, st>>>(
+          gr, gi, sG, vr, vi, sV, nrm, sig, p, q, max_sweeps, real_flags, status, flags);
+    } else {
+      jacobi_cluster_kernel<T, false><<<grid, JPC_THREADS, 0, st>>>(
+          gr, gi, sG, vr, vi, sV, nrm, sig, p, q, max_sweeps, real_flags, status, flags);
+    }
+  }
+  return launch_status("jacobi_cluster_kernel");
+}
+
 }  // namespace
 
 // float32 one-sided Jacobi from V = I (init_v) or from the given V (then G
@@ -483,8 +833,13 @@ int hybrid_svd(const float* xr, const float* xi, int64_t sX, int64_t ldx, bool c
   // 1. float32 sweeps (with the polish, a cluster of singular values at the
   //    float32 rounding floor may stall here and step 4 decides convergence;
   //    without it this step does)
-  if ((rc = jacobi_launch<float>(fr, fi, pq, qr, qi, qq, qsig, p, q, batch, max_sweeps, real_flags,
-                                 polish ? nullptr : status, JAC_INIT_V, st)))
+  //    (fewer slices than SMs: a cluster of CTAs per slice)
+  if ((rc = use_cluster(q, batch)
+                ? jacobi_cluster_launch<float>(fr, fi, pq, qr, qi, qq, nullptr, qsig, p, q, batch,
+                                               max_sweeps, real_flags, polish ? nullptr : status,
+                                               JAC_INIT_V, st)
+                : jacobi_launch<float>(fr, fi, pq, qr, qi, qq, qsig, p, q, batch, max_sweeps,
+                                       real_flags, polish ? nullptr : status, JAC_INIT_V, st)))
     return rc;
   {
     KernelScope ks("svd_refine", st);
@@ -502,7 +857,11 @@ int hybrid_svd(const float* xr, const float* xi, int64_t sX, int64_t ldx, bool c
   //    or three sweeps suffice, more only for clusters of singular values at
   //    the float32 rounding floor (rank-deficient input); the sweep cap and
   //    TP_DEV_NOCONV apply here.  Without the polish: no sweeps, only the
-  //    column norms (singular values) and unit columns of G.
+  //    column norms (singular values) and unit columns of G.  Fewer slices
+  //    than SMs: a cluster of CTAs per slice (T is free scratch by now).
+  if (polish && use_cluster(q, batch))
+    return jacobi_cluster_launch<double>(gr, gi, pq, wr, wi, qq, tr, sig, p, q, batch, max_sweeps,
+                                         real_flags, status, JAC_NORMALIZE, st);
   return jacobi_launch<double>(gr, gi, pq, wr, wi, qq, sig, p, q, batch, polish ? max_sweeps : 0,
                                real_flags, polish ? status : nullptr, JAC_NORMALIZE, st);
 }
