@@ -855,7 +855,7 @@ def main():
                     help="iterations of the batched completion row (256 videos)")
     ap.add_argument("--only", default=None,
                     help="comma-separated rows to run instead of the headline step "
-                         "(rsvd, svt_batched, svt_batched_bf16x3, svt_video, learned): "
+                         "(rsvd, svt_batched, svt_batched_bf16x3, svt_video, learned, tcx): "
                          "profiling and "
                          "tuning runs, no headline line")
     ap.add_argument("--tune-file", default=None,
@@ -897,6 +897,12 @@ def main():
                 out = bench_svt_batched(tp, torch, iters=args.svt_iters, precision="bf16x3")
             elif name == "learned":
                 out = bench_learned(torch)
+            elif name == "tcx":
+                # the t-CX row alone (its two Jacobi launches dominate)
+                from paper_1704_04362_gb300 import synth
+                Ad = tp.as_tprod_layout(synth.lowrank_np(256, 512, 32, 10, seed=3, noise=0.01))
+                out = {"workload": "256x512x32 tubal rank 10 + 1% noise, c = 64",
+                       "gpu_ms": time_gpu(lambda: tp.tcx(Ad, 64, seed=0), args.steps, torch)}
             elif name == "svt_video":
                 # one 480 x 360 x 120 video (the largest of the batch): a
                 # single-tensor profiling case a few GB in size

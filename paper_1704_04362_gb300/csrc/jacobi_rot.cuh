@@ -13,8 +13,10 @@ namespace jrot {
 // gr^2 + gi^2 > 0: with zeta = (beta - alpha) / (2 |gamma|),
 // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t,
 // and e^{-i phi} = conj(gamma) / |gamma|.
+// tg = t |gamma|: the change of the two squared norms, ||a'||^2 = alpha - tg
+// and ||b'||^2 = beta + tg.
 __device__ __forceinline__ void rotation(float alpha, float beta, float gr, float gi, float g2,
-                                         float& cs, float& sn, float& er, float& ei) {
+                                         float& cs, float& sn, float& er, float& ei, float& tg) {
   const float g = sqrtf(g2);
   const float zeta = (beta - alpha) / (2.f * g);
   const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
@@ -22,6 +24,12 @@ __device__ __forceinline__ void rotation(float alpha, float beta, float gr, floa
   sn = cs * t;
   er = gr / g;
   ei = -gi / g;
+  tg = t * g;
+}
+__device__ __forceinline__ void rotation(float alpha, float beta, float gr, float gi, float g2,
+                                         float& cs, float& sn, float& er, float& ei) {
+  float tg;
+  rotation(alpha, beta, gr, gi, g2, cs, sn, er, ei, tg);
 }
 
 // float64: the tangent only steers convergence, so it is formed in float32
@@ -35,7 +43,7 @@ __device__ __forceinline__ double rsqrt_nr(double v, double seed) {
 }
 __device__ __forceinline__ void rotation(double alpha, double beta, double gr, double gi,
                                          double g2, double& cs, double& sn, double& er,
-                                         double& ei) {
+                                         double& ei, double& tg) {
   int e;
   const double big = fabs(alpha) > fabs(beta) ? fabs(alpha) : fabs(beta);
   frexp(big, &e);
@@ -50,6 +58,7 @@ __device__ __forceinline__ void rotation(double alpha, double beta, double gr, d
     sn = cs * t;
     er = gr / g;
     ei = -gi / g;
+    tg = t * g;
     return;
   }
   const float gf = sqrtf(g2f);
@@ -64,6 +73,13 @@ __device__ __forceinline__ void rotation(double alpha, double beta, double gr, d
   const double rinv = rsqrt_nr(g2s, double(rsqrtf(float(g2s)))) * sc;
   er = gr * rinv;
   ei = -gi * rinv;
+  tg = t * (g2 * rinv);   // |gamma| = g2 / |gamma|: no float64 divide or square root
+}
+__device__ __forceinline__ void rotation(double alpha, double beta, double gr, double gi,
+                                         double g2, double& cs, double& sn, double& er,
+                                         double& ei) {
+  double tg;
+  rotation(alpha, beta, gr, gi, g2, cs, sn, er, ei, tg);
 }
 
 }  // namespace jrot

@@ -175,10 +175,9 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(T* g_re, T* g_im, i
         const T g2 = gr * gr + gi * gi;
         if (!(g2 > tol * tol * alpha * beta) || g2 == T(0)) continue;
         if (lane == 0) rotated = 1;
-        T cs, sn, er, ei;   // cos, sin and e^{-i phi}
-        rotation(alpha, beta, gr, gi, g2, cs, sn, er, ei);
+        T cs, sn, er, ei, tg;   // cos, sin, e^{-i phi} and t |gamma|
+        rotation(alpha, beta, gr, gi, g2, cs, sn, er, ei, tg);
         if (keep && lane == 0) {
-          const T tg = (sn / cs) * sqrt(g2);
           nrm[a] = alpha - tg;
           nrm[c2] = beta + tg;
         }
@@ -322,13 +321,13 @@ __device__ __forceinline__ bool jpc_pair(T* ar, T* ai, T* br, T* bi, T* var, T* 
   gi = warp_sum_t(gi);
   const T g2 = gr * gr + gi * gi;
   if (!(g2 > tol * tol * alpha * beta) || g2 == T(0)) return false;
-  T cs, sn, er, ei;
-  rotation(alpha, beta, gr, gi, g2, cs, sn, er, ei);
+  T cs, sn, er, ei, tg;
+  rotation(alpha, beta, gr, gi, g2, cs, sn, er, ei, tg);
   if (keep && lane == 0) {
-    const T tg = (sn / cs) * sqrt(g2);
     jst<S>(na, alpha - tg);
     jst<S>(nb, beta + tg);
   }
+#pragma unroll 4
   for (int r = lane; r < p; r += 32) {
     const T xr = jld<S>(ar + r), xi = jld<S>(ai + r);
     const T ur = jld<S>(br + r), ui = jld<S>(bi + r);
@@ -338,6 +337,7 @@ __device__ __forceinline__ bool jpc_pair(T* ar, T* ai, T* br, T* bi, T* var, T* 
     jst<S>(br + r, sn * xr + cs * yr);
     jst<S>(bi + r, sn * xi + cs * yi);
   }
+#pragma unroll 4
   for (int r = lane; r < q; r += 32) {
     const T xr = jld<S>(var + r), xi = jld<S>(vai + r);
     const T ur = jld<S>(vbr + r), ui = jld<S>(vbi + r);
