@@ -794,6 +794,19 @@ int jacobi_float_launch(float* gr, float* gi, int64_t sG, float* vr, float* vi, 
                               status, init_v ? JAC_INIT_V : 0, st);
 }
 
+// Whether jacobi_float_cluster_launch takes a batch of p x q slices (fewer
+// slices than SMs, q >= 32).
+bool jacobi_cluster_applies(int q, int batch) { return use_cluster(q, batch); }
+
+// jacobi_float_launch with a thread-block cluster per slice.
+int jacobi_float_cluster_launch(float* gr, float* gi, int64_t sG, float* vr, float* vi,
+                                int64_t sV, float* sig, int p, int q, int batch, int max_sweeps,
+                                const int* real_flags, int32_t* status, bool init_v,
+                                cudaStream_t st) {
+  return jacobi_cluster_launch<float>(gr, gi, sG, vr, vi, sV, nullptr, sig, p, q, batch,
+                                      max_sweeps, real_flags, status, init_v ? JAC_INIT_V : 0, st);
+}
+
 // C_b = op(A_b) B_b in float64 from float32 planes (see zgemm64_kernel).
 int zgemm64_from_float(const float* ar, const float* ai, int64_t sA, int64_t lda, bool conj_a,
                        const float* br, const float* bi, int64_t sB, int64_t ldb, double* cr,

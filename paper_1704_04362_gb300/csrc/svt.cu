@@ -38,6 +38,11 @@ int jacobi_float_launch(float* gr, float* gi, int64_t sG, float* vr, float* vi, 
                         float* sig, int p, int q, int batch, int max_sweeps,
                         const int* real_flags, int32_t* status, bool init_v, cudaStream_t st);
 bool jacobi_blocked_applies(int p, int q);
+bool jacobi_cluster_applies(int q, int batch);
+int jacobi_float_cluster_launch(float* gr, float* gi, int64_t sG, float* vr, float* vi,
+                                int64_t sV, float* sig, int p, int q, int batch, int max_sweeps,
+                                const int* real_flags, int32_t* status, bool init_v,
+                                cudaStream_t st);
 int jacobi_float_blocked_launch(float* gr, float* gi, int64_t sG, float* vr, float* vi,
                                 int64_t sV, float* sig, int p, int q, int batch, int max_sweeps,
                                 const int* real_flags, int32_t* status, bool init_v,
@@ -274,6 +279,9 @@ struct SvtTensor {
   int prec;
   int64_t lq;
   float *WP[4], *HP[4], *VP[4], *BP[4];
+  // a lone tensor (not one of a batch sharing the GPU): its Jacobi may spread
+  // each slice over a thread-block cluster when the slices are fewer than SMs
+  bool alone = false;
 };
 
 SvtTensor svt_carve(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t n3,
@@ -394,7 +402,10 @@ int svt_iteration(const SvtTensor& t, bool warm, double rho, double mu_max, int 
       if ((rc = launch_cgemm(gw, st))) return rc;
     }
   }
-  if (TP_SVT_BLOCKED && jacobi_blocked_applies(int(p), int(q)))
+  if (t.alone && jacobi_cluster_applies(int(q), int(h)))
+    rc = jacobi_float_cluster_launch(t.Gr, t.Gi, p * q, t.Vr, t.Vi, q * q, t.sig, int(p), int(q),
+                                     int(h), sweeps, t.flags, status, !warm, st);
+  else if (TP_SVT_BLOCKED && jacobi_blocked_applies(int(p), int(q)))
     rc = jacobi_float_blocked_launch(t.Gr, t.Gi, p * q, t.Vr, t.Vi, q * q, t.sig, int(p), int(q),
                                      int(h), sweeps, t.flags, status, !warm, st);
   else
@@ -465,6 +476,7 @@ int svt_run(const float* X, const uint8_t* mask, int64_t n1, int64_t n2, int64_t
   const int sweeps = (opts && opts->max_sweeps > 0) ? opts->max_sweeps : 30;
   SvtTensor t = svt_carve(X, mask, n1, n2, n3, L, E, Y, mu, ws, prec);
   t.lam = lam;
+  t.alone = true;
   if ((rc = svt_init(t, st))) return rc;
   for (int it = 0; it < iters; ++it)
     if ((rc = svt_iteration(t, it > 0, rho, mu_max, sweeps, status, st))) return rc;
