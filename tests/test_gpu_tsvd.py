@@ -22,7 +22,11 @@ SHAPES = [(64, 48, 16), (48, 64, 16), (5, 3, 4), (3, 5, 5), (7, 7, 1), (130, 40,
           (1, 1, 1), (2, 9, 2), (200, 100, 8),
           # the re-orthonormalised path's limit (4096 entries, 256 rows) and the
           # float64 sweeps beyond it
-          (256, 16, 3), (64, 64, 2), (256, 96, 3), (96, 256, 2), (257, 40, 2)]
+          (256, 16, 3), (64, 64, 2), (256, 96, 3), (96, 256, 2), (257, 40, 2),
+          # fewer slices than SMs and >= 32 columns: cluster-per-slice sweeps;
+          # block pairs too large for shared memory in float64 (1700 rows) and
+          # in both precisions (3300 rows, transposed)
+          (1700, 64, 2), (64, 3300, 2)]
 
 
 @pytest.mark.parametrize("n1,n2,n3", SHAPES)
@@ -66,6 +70,18 @@ def test_tsvd_exact_workload_and_sweep_cap_flag():
     looping."""
     import torch
     X = synth.iid_normal((64, 48, 16), seed=0)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    tp.tsvd(dev(X), status=st, max_sweeps=1)
+    torch.cuda.synchronize()
+    assert int(st.item()) & 0x1
+
+
+def test_cluster_float64_sweep_cap_flag():
+    """A slice pair of 257 x 40 takes the float64 sweeps (over 4096 entries)
+    on the cluster-per-slice path; a cap of 1 sweep must raise the device
+    non-convergence bit there."""
+    import torch
+    X = synth.iid_normal((257, 40, 2), seed=1)
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     tp.tsvd(dev(X), status=st, max_sweeps=1)
     torch.cuda.synchronize()
