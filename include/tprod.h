@@ -344,7 +344,12 @@ typedef struct {
  * The tensors run concurrently on side streams forked from `stream`; the
  * first iteration is launched directly and the remaining iters - 1 replay
  * one captured CUDA graph of an iteration over all tensors.  Results are
- * identical to ntens separate tcomplete_svt calls with the same arguments.
+ * identical to ntens separate tcomplete_svt calls with the same arguments
+ * for tensors with min(n1, n2) < 32 or at least as many half-spectrum slices
+ * as the GPU has SMs; otherwise a lone call spreads each slice's Jacobi over
+ * a thread-block cluster (another rotation order) and the two agree to
+ * float32 rounding (the batch keeps one CTA per slice: with the GPU full, it
+ * costs less SM time per slice).
  * Workspace: tp_workspace_query(TP_OP_TCOMPLETE_SVT_BATCHED, {n1, n2, n3 of
  * each tensor}, 3 ntens) (the sum of the tensors' own).  Synchronises
  * `stream` before returning (the graph and side streams are released).

@@ -22,15 +22,18 @@ def state_on_device(X, mask, L, E, Y, mu):
             torch.tensor([mu], dtype=torch.float64, device="cuda"))
 
 
-# the last two slices exceed the shared-memory Jacobi and take the blocked
-# one (128 columns in 8 blocks; 150 columns, transposed, with a ragged block)
+# the last two slices exceed the shared-memory Jacobi: in a batch they take
+# the blocked one (128 columns in 8 blocks; 150 columns, transposed, with a
+# ragged block), alone (fewer slices than SMs, >= 32 columns) the
+# cluster-per-slice sweeps
+@pytest.mark.parametrize("form", ["alone", "batch"])
 @pytest.mark.parametrize("precision", [tp.TP_FP32, tp.TP_TF32X3, tp.TP_BF16X3])
 @pytest.mark.parametrize("n1,n2,n3", [(20, 16, 6), (12, 30, 5), (24, 24, 1), (33, 17, 8),
                                       (160, 128, 4), (150, 200, 5)])
-def test_one_iteration_matches_oracle(n1, n2, n3, precision):
+def test_one_iteration_matches_oracle(n1, n2, n3, precision, form):
     """One iteration in each form: FP32, and the SVT's three GEMMs on the
     tensor cores with the 3xTF32 or BF16x3 split (held to that split's
-    tolerance)."""
+    tolerance); through tcomplete_svt and as a batch of one tensor."""
     import torch
     g = np.random.default_rng(n1 * n2 + n3)
     X = synth.lowrank_np(n1, n2, n3, 3, seed=n3, noise=0.01)
@@ -43,7 +46,10 @@ def test_one_iteration_matches_oracle(n1, n2, n3, precision):
     mu = 0.08
     Xd, Md, Ld, Ed, Yd, mud = state_on_device(X, mask, L0, E, Y, mu)
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
-    tp.tcomplete_svt(Xd, Md, 1, L=Ld, E=Ed, Y=Yd, mu=mud, status=st, precision=precision)
+    if form == "alone":
+        tp.tcomplete_svt(Xd, Md, 1, L=Ld, E=Ed, Y=Yd, mu=mud, status=st, precision=precision)
+    else:
+        tp.tcomplete_svt_batched([(Xd, Md, Ld, Ed, Yd, mud)], 1, status=st, precision=precision)
     assert int(st.item()) == 0
     Xo = np.where(mask, X.astype(np.float64), 0.0)
     Lr, Er, Yr, mur = completion_ref.admm_step(Xo, mask, L0.astype(np.float64),
@@ -176,8 +182,10 @@ def test_robust_form_recovers_low_rank_plus_sparse_and_tracks_oracle():
     assert rel_fro(to_np(L2), L0) < 1e-3 and rel_fro(to_np(E2), S0) < 1e-3
 
 
-def test_blocked_jacobi_slices_track_oracle_over_iterations():
-    # 160 x 128 slices take the blocked Jacobi, warm-started every iteration
+@pytest.mark.parametrize("form", ["alone", "batch"])
+def test_blocked_jacobi_slices_track_oracle_over_iterations(form):
+    # 160 x 128 slices, warm-started every iteration: in a batch the blocked
+    # Jacobi, alone the cluster-per-slice sweeps
     import torch
     X = synth.lowrank_np(160, 128, 4, 3, seed=62, noise=0.01)
     X = X / np.sqrt(np.mean(X.astype(np.float64) ** 2))
@@ -185,7 +193,10 @@ def test_blocked_jacobi_slices_track_oracle_over_iterations():
     Z = np.zeros_like(X)
     Xd, Md, Ld, Ed, Yd, mud = state_on_device(X, mask, Z, Z, Z, 1e-3)
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
-    tp.tcomplete_svt(Xd, Md, 30, L=Ld, E=Ed, Y=Yd, mu=mud, status=st)
+    if form == "alone":
+        tp.tcomplete_svt(Xd, Md, 30, L=Ld, E=Ed, Y=Yd, mu=mud, status=st)
+    else:
+        tp.tcomplete_svt_batched([(Xd, Md, Ld, Ed, Yd, mud)], 30, status=st)
     assert int(st.item()) == 0
     Lr, Er, Yr, mur = completion_ref.tcomplete_svt(X.astype(np.float64), mask, 30)
     assert rel_fro(to_np(Ld), Lr) < 1e-4                 # float32 state over 30 iterations
