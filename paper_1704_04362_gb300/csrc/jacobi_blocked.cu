@@ -55,9 +55,13 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_blocked_kernel(
     float* __restrict__ v_im, int64_t sV, float* __restrict__ sig, int p, int q, int max_sweeps,
     const int* __restrict__ real_flags, int32_t* __restrict__ status, int init_v) {
   extern __shared__ __align__(16) float jb_smem[];
-  float* const Sr = jb_smem;                      // [JB_C][p]: columns of G, later of V
-  float* const Si = jb_smem + size_t(JB_C) * p;
-  float* const Qr = jb_smem + size_t(2) * JB_C * p;   // Q(r, c) at c * JB_C + r
+  // staged columns of G at stride ld (the register path's 32 RPL >= p rows:
+  // its lanes move 4 consecutive rows with one 16-byte access and the zero
+  // rows past p need no guard), later those of V at stride q
+  const int ld = RPL > 0 ? 32 * RPL : p;
+  float* const Sr = jb_smem;                      // [JB_C][ld]
+  float* const Si = jb_smem + size_t(JB_C) * ld;
+  float* const Qr = jb_smem + size_t(2) * JB_C * ld;   // Q(r, c) at c * JB_C + r
   float* const Qi = Qr + JB_C * JB_C;
   __shared__ int any_rot, blk_rot;
   __shared__ float nrm[JB_C];   // squared norms of the staged columns
@@ -109,14 +113,18 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_blocked_kernel(
       for (int c = warp; c < nc; c += NW) {
         const float* gr_c = Gr + int64_t(jb_col(c, I, J, bI)) * p;
         const float* gi_c = Gi + int64_t(jb_col(c, I, J, bI)) * p;
-        float* sr_c = Sr + size_t(c) * p;
-        float* si_c = Si + size_t(c) * p;
+        float* sr_c = Sr + size_t(c) * ld;
+        float* si_c = Si + size_t(c) * ld;
         float acc = 0.f;
         for (int r = lane; r < p; r += 32) {
           const float xr = gr_c[r], xi = gi_c[r];
           sr_c[r] = xr;
           si_c[r] = xi;
           acc = fmaf(xr, xr, fmaf(xi, xi, acc));
+        }
+        for (int r = p + lane; r < ld; r += 32) {   // the padding rows (V's staging overwrote them)
+          sr_c[r] = 0.f;
+          si_c[r] = 0.f;
         }
         acc = jb_warp_sum(acc);
         if (lane == 0) nrm[c] = acc;
@@ -169,10 +177,10 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_blocked_kernel(
             a = base + min(x, y);
             c2 = base + max(x, y);
           }
-          float* const ar = Sr + size_t(a) * p;
-          float* const ai = Si + size_t(a) * p;
-          float* const br = Sr + size_t(c2) * p;
-          float* const bi = Si + size_t(c2) * p;
+          float* const ar = Sr + size_t(a) * ld;
+          float* const ai = Si + size_t(a) * ld;
+          float* const br = Sr + size_t(c2) * ld;
+          float* const bi = Si + size_t(c2) * ld;
           const float alpha = nrm[a], beta = nrm[c2];
           float gr = 0.f, gi = 0.f;
           for (int r = lane; r < p; r += 32) {
@@ -225,14 +233,15 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_blocked_kernel(
         const bool own = warp < bI;
         float xr[RPL > 0 ? RPL : 1], xi[RPL > 0 ? RPL : 1];
         float alpha = 0.f;
+        // lane's rows: 128 m + 4 lane + j (register k = 4 m + j)
         if (own) {
-          const float* ar = Sr + size_t(warp) * p;
-          const float* ai = Si + size_t(warp) * p;
+          const float4* ar = reinterpret_cast<const float4*>(Sr + size_t(warp) * ld);
+          const float4* ai = reinterpret_cast<const float4*>(Si + size_t(warp) * ld);
 #pragma unroll
-          for (int k = 0; k < RPL; ++k) {
-            const int r = lane + 32 * k;
-            xr[k] = r < p ? ar[r] : 0.f;
-            xi[k] = r < p ? ai[r] : 0.f;
+          for (int m = 0; m < RPL / 4; ++m) {
+            const float4 u = ar[32 * m + lane], v = ai[32 * m + lane];
+            xr[4 * m] = u.x; xr[4 * m + 1] = u.y; xr[4 * m + 2] = u.z; xr[4 * m + 3] = u.w;
+            xi[4 * m] = v.x; xi[4 * m + 1] = v.y; xi[4 * m + 2] = v.z; xi[4 * m + 3] = v.w;
           }
           alpha = nrm[warp];
         }
@@ -240,15 +249,18 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_blocked_kernel(
           const int jj = own ? (warp + t) % bI : 0;
           if (own && jj < bJ) {
             const int c2 = bI + jj;
-            float* const br = Sr + size_t(c2) * p;
-            float* const bi = Si + size_t(c2) * p;
+            float4* const br = reinterpret_cast<float4*>(Sr + size_t(c2) * ld);
+            float4* const bi = reinterpret_cast<float4*>(Si + size_t(c2) * ld);
             float yr[RPL > 0 ? RPL : 1], yi[RPL > 0 ? RPL : 1];
+#pragma unroll
+            for (int m = 0; m < RPL / 4; ++m) {
+              const float4 u = br[32 * m + lane], v = bi[32 * m + lane];
+              yr[4 * m] = u.x; yr[4 * m + 1] = u.y; yr[4 * m + 2] = u.z; yr[4 * m + 3] = u.w;
+              yi[4 * m] = v.x; yi[4 * m + 1] = v.y; yi[4 * m + 2] = v.z; yi[4 * m + 3] = v.w;
+            }
             float gr = 0.f, gi = 0.f;
 #pragma unroll
             for (int k = 0; k < RPL; ++k) {
-              const int r = lane + 32 * k;
-              yr[k] = r < p ? br[r] : 0.f;
-              yi[k] = r < p ? bi[r] : 0.f;
               gr = fmaf(xr[k], yr[k], fmaf(xi[k], yi[k], gr));    // Re(conj(x) y)
               gi = fmaf(xr[k], yi[k], fmaf(-xi[k], yr[k], gi));   // Im(conj(x) y)
             }
@@ -264,15 +276,19 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_blocked_kernel(
               if (lane == 0) nrm[c2] = beta + tg;
 #pragma unroll
               for (int k = 0; k < RPL; ++k) {
-                const int r = lane + 32 * k;
                 const float ur = yr[k] * er - yi[k] * ei, ui = yr[k] * ei + yi[k] * er;
                 const float x0 = xr[k], x1 = xi[k];
                 xr[k] = cs * x0 - sn * ur;
                 xi[k] = cs * x1 - sn * ui;
-                if (r < p) {
-                  br[r] = sn * x0 + cs * ur;
-                  bi[r] = sn * x1 + cs * ui;
-                }
+                yr[k] = sn * x0 + cs * ur;
+                yi[k] = sn * x1 + cs * ui;
+              }
+#pragma unroll
+              for (int m = 0; m < RPL / 4; ++m) {
+                br[32 * m + lane] = make_float4(yr[4 * m], yr[4 * m + 1], yr[4 * m + 2],
+                                                yr[4 * m + 3]);
+                bi[32 * m + lane] = make_float4(yi[4 * m], yi[4 * m + 1], yi[4 * m + 2],
+                                                yi[4 * m + 3]);
               }
               // the same column operation on Q (rows 0 .. nc-1; lane r < 32)
               float* const qa_r = Qr + warp * JB_C;
@@ -293,15 +309,12 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_blocked_kernel(
           __syncthreads();   // block J's columns change hands
         }
         if (own) {
-          float* const ar = Sr + size_t(warp) * p;
-          float* const ai = Si + size_t(warp) * p;
+          float4* const ar = reinterpret_cast<float4*>(Sr + size_t(warp) * ld);
+          float4* const ai = reinterpret_cast<float4*>(Si + size_t(warp) * ld);
 #pragma unroll
-          for (int k = 0; k < RPL; ++k) {
-            const int r = lane + 32 * k;
-            if (r < p) {
-              ar[r] = xr[k];
-              ai[r] = xi[k];
-            }
+          for (int m = 0; m < RPL / 4; ++m) {
+            ar[32 * m + lane] = make_float4(xr[4 * m], xr[4 * m + 1], xr[4 * m + 2], xr[4 * m + 3]);
+            ai[32 * m + lane] = make_float4(xi[4 * m], xi[4 * m + 1], xi[4 * m + 2], xi[4 * m + 3]);
           }
           if (lane == 0) nrm[warp] = alpha;
         }
@@ -311,8 +324,8 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_blocked_kernel(
         for (int c = warp; c < nc; c += NW) {
           float* gr_c = Gr + int64_t(jb_col(c, I, J, bI)) * p;
           float* gi_c = Gi + int64_t(jb_col(c, I, J, bI)) * p;
-          const float* sr_c = Sr + size_t(c) * p;
-          const float* si_c = Si + size_t(c) * p;
+          const float* sr_c = Sr + size_t(c) * ld;
+          const float* si_c = Si + size_t(c) * ld;
           for (int r = lane; r < p; r += 32) {
             gr_c[r] = sr_c[r];
             gi_c[r] = si_c[r];
@@ -411,7 +424,7 @@ template <int RPL>
 int jb_launch(float* gr, float* gi, int64_t sG, float* vr, float* vi, int64_t sV, float* sig,
               int p, int q, int batch, int max_sweeps, const int* real_flags, int32_t* status,
               bool init_v, cudaStream_t st) {
-  const size_t smem = jb_smem_bytes(p);
+  const size_t smem = jb_smem_bytes(RPL > 0 ? 32 * RPL : p);
   TP_SET_SMEM(jacobi_blocked_kernel<RPL>, smem);
   {
     KernelScope ks("jacobi_blocked", st);
@@ -437,9 +450,17 @@ int jacobi_float_blocked_launch(float* gr, float* gi, int64_t sG, float* vr, flo
                                 const int* real_flags, int32_t* status, bool init_v,
                                 cudaStream_t st) {
   if (batch <= 0 || q <= 0) return TP_OK;
+  // the register form's rows come in steps of 128 (the zero rows past p
+  // cost the same arithmetic as data rows)
+  if (p <= 128)
+    return jb_launch<4>(gr, gi, sG, vr, vi, sV, sig, p, q, batch, max_sweeps, real_flags, status,
+                        init_v, st);
   if (p <= 256)
     return jb_launch<8>(gr, gi, sG, vr, vi, sV, sig, p, q, batch, max_sweeps, real_flags, status,
                         init_v, st);
+  if (p <= 384)
+    return jb_launch<12>(gr, gi, sG, vr, vi, sV, sig, p, q, batch, max_sweeps, real_flags, status,
+                         init_v, st);
   if (p <= 512)
     return jb_launch<16>(gr, gi, sG, vr, vi, sV, sig, p, q, batch, max_sweeps, real_flags, status,
                          init_v, st);

@@ -22,14 +22,16 @@ def state_on_device(X, mask, L, E, Y, mu):
             torch.tensor([mu], dtype=torch.float64, device="cuda"))
 
 
-# the last two slices exceed the shared-memory Jacobi: in a batch they take
+# the last five slices exceed the shared-memory Jacobi: in a batch they take
 # the blocked one (128 columns in 8 blocks; 150 columns, transposed, with a
-# ragged block), alone (fewer slices than SMs, >= 32 columns) the
+# ragged block; then 128, 300 and 400 rows: the register form's row counts
+# up to 128, 384 and 512), alone (fewer slices than SMs, >= 32 columns) the
 # cluster-per-slice sweeps
 @pytest.mark.parametrize("form", ["alone", "batch"])
 @pytest.mark.parametrize("precision", [tp.TP_FP32, tp.TP_TF32X3, tp.TP_BF16X3])
 @pytest.mark.parametrize("n1,n2,n3", [(20, 16, 6), (12, 30, 5), (24, 24, 1), (33, 17, 8),
-                                      (160, 128, 4), (150, 200, 5)])
+                                      (160, 128, 4), (150, 200, 5), (120, 128, 3),
+                                      (300, 130, 3), (100, 400, 2)])
 def test_one_iteration_matches_oracle(n1, n2, n3, precision, form):
     """One iteration in each form: FP32, and the SVT's three GEMMs on the
     tensor cores with the 3xTF32 or BF16x3 split (held to that split's
