@@ -26,7 +26,8 @@ using jrot::rotation;
 constexpr int JB_THREADS = 512;   // 16 warps: one column pair each per round
 constexpr int JB_B = 16;          // columns per block; a block pair holds <= 32
 constexpr int JB_C = 2 * JB_B;
-constexpr size_t JB_SMEM_MAX = size_t(220) * 1024;
+constexpr size_t JB_SMEM_MAX = size_t(212) * 1024;   // dynamic; the static arrays take ~9 KB
+constexpr int JB_MAX_NB = 64;     // blocks of a slice whose block pairs keep records
 
 __device__ __forceinline__ float jb_warp_sum(float v) {
 #pragma unroll
@@ -64,6 +65,14 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_blocked_kernel(
   float* const Qr = jb_smem + size_t(2) * JB_C * ld;   // Q(r, c) at c * JB_C + r
   float* const Qi = Qr + JB_C * JB_C;
   __shared__ int any_rot, blk_rot;
+  // Skipping converged block pairs: bver[I] counts the block pairs that
+  // rotated block I's columns; pquiet[bp] holds the two blocks' counts when
+  // block pair bp last made no rotation.  While both counts are unchanged its
+  // columns are bit-identical to then, so its inner products are too and it
+  // would again rotate nothing: it is skipped (the result is the same as
+  // visiting it; a converged warm sweep mostly consists of such pairs).
+  __shared__ int bver[JB_MAX_NB];
+  __shared__ int pquiet[JB_MAX_NB * (JB_MAX_NB - 1) / 2];
   __shared__ float nrm[JB_C];   // squared norms of the staged columns
   const int64_t b = blockIdx.x;
   float* const Gr = g_re + b * sG;
@@ -89,6 +98,10 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_blocked_kernel(
   if (tol < 1e-6f) tol = 1e-6f;
   const int nb = (q + JB_B - 1) / JB_B;
   const int npair = nb == 1 ? 1 : nb * (nb - 1) / 2;
+  const bool rec = nb <= JB_MAX_NB;
+  for (int e = tid; e < JB_MAX_NB * (JB_MAX_NB - 1) / 2; e += JB_THREADS) pquiet[e] = -1;
+  for (int e = tid; e < JB_MAX_NB; e += JB_THREADS) bver[e] = 0;
+  __syncthreads();
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     if (tid == 0) any_rot = 0;
@@ -102,6 +115,8 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_blocked_kernel(
         }
         J = I + 1 + rem;
       }
+      const int key = rec ? (bver[I] & 0xffff) | ((J < 0 ? 0 : bver[J] & 0x7fff) << 16) : -2;
+      if (rec && pquiet[bp] == key) continue;   // uniform: written before the last barrier
       const int bI = min(JB_B, q - I * JB_B);
       const int bJ = J < 0 ? 0 : min(JB_B, q - J * JB_B);
       const int nc = bI + bJ;
@@ -399,7 +414,15 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_blocked_kernel(
         }
         if (tid == 0) any_rot = 1;
       }
-      __syncthreads();   // the staging area and blk_rot are reused by the next pair
+      if (tid == 0 && rec) {
+        if (blk_rot) {
+          ++bver[I];
+          if (J >= 0) ++bver[J];
+        } else {
+          pquiet[bp] = key;
+        }
+      }
+      __syncthreads();   // the staging area, blk_rot and the records are reused by the next pair
     }
     const int any = any_rot;
     __syncthreads();
