@@ -29,6 +29,8 @@
 //      of singular values at the float32 rounding floor (rank-deficient
 //      input), which float32 cannot resolve.
 // Steps 2-3 are batched float64 GEMMs spread over all SMs.
+#include <atomic>
+
 #include "jacobi_rot.cuh"
 
 namespace tp {
@@ -754,10 +756,37 @@ int jacobi_launch(T* gr, T* gi, int64_t sG, T* vr, T* vi, int64_t sV, T* sig, in
   return launch_status("jacobi_kernel");
 }
 
+// Whether the device can place a cluster of JPC CTAs at all (a partitioned
+// GPU may not): asked once per device; an error of the query itself leaves
+// the cluster form on (the query, not the launch, is what failed).
+bool cluster_fits() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cache[kMaxDev];   // 0 unknown, 1 fits, 2 does not
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+    cudaGetLastError();
+    return true;
+  }
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v == 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(JPC, 1, 1);
+    cfg.blockDim = dim3(JPC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = 0;   // the cluster size comes from the kernel's __cluster_dims__
+    int n = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(
+        &n, (const void*)jacobi_cluster_kernel<double, false>, &cfg);
+    if (e != cudaSuccess) cudaGetLastError();
+    v = (e == cudaSuccess && n < 1) ? 2 : 1;
+    cache[dev].store(v, std::memory_order_relaxed);
+  }
+  return v == 1;
+}
+
 // A cluster of CTAs per slice pays when the slices are fewer than the SMs and
 // wide enough to give every CTA of the cluster a block pair of columns.
 bool use_cluster(int q, int batch) {
-  return q >= 2 * JPC_BLOCKS && q <= JAC_MAX_Q && batch < sm_count();
+  return q >= 2 * JPC_BLOCKS && q <= JAC_MAX_Q && batch < sm_count() && cluster_fits();
 }
 
 template <class T>
